@@ -1,0 +1,790 @@
+/*
+ * pond_oracle.c -- plain, slow FP64 reference implementation of the regularized
+ * Particles-on-Demand finite-volume time step (Kallikounis, Dorschner, Karlin,
+ * "Particles on Demand for flows with strong discontinuities", arXiv 2203.05477).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the CPU
+ * baseline leg of the benchmark may load this file.  It shares no code, header,
+ * table or helper with the CUDA library; every formula below is written out from
+ * the paper, in population form, with no fusion or reordering beyond what the
+ * paper states:
+ *
+ *   - lattice:      Table I (D1Q4 Gauss-Hermite roots and weights, T_L = 1) and
+ *                   Eq. (wi) (D2Q16 as the tensor product W_i = w_ix w_iy);
+ *   - velocities:   Eq. (vlambda)   v_i = sqrt(T/T_L) c_i + u;
+ *   - moments:      Sec. II.B       rho, rho u, rho E;  Eq. (E) rho E = Cv rho T + rho u^2/2;
+ *   - equilibria:   Eqs. (feqPond), (geqPond)   f^eq = rho W_i,  g^eq = (Cv - D/2) T rho W_i;
+ *   - transform:    Eq. (f_transformed) with Eqs. (a0)-(a3): third-order Grad projection
+ *                   for f, second-order for g (a3 dropped), built from the lab moments M_k;
+ *   - FV update:    Eqs. (FinalUpdateDUGKS) in the co-moving frame (Sec. III.B.2);
+ *   - flux:         Eqs. (InterfacePop), (FluxTransf), (Fbarplus), the face predictor-
+ *                   corrector with limited slopes and MUSCL reconstruction (Sec. III.B.3),
+ *                   and Eq. (fluxEq);
+ *   - step order:   the algorithm summary of Sec. III.B.4;
+ *   - time step:    CFL = max|v_ia| dt/dx (Sec. IV).
+ *
+ * Readings where the paper is silent (each one is listed in the design notes):
+ *   R = 1, p = rho T, Cv = 1/(gamma-1); D in g^eq is the lattice dimension; the
+ *   overline (symmetrization) is the sum over distinct index permutations; the face
+ *   predictor before the first step is the mean of the two adjacent cell frames; the
+ *   corrector stops when |u_{k+1}-u_k|_inf <= tol sqrt(T_k) and |T_{k+1}-T_k| <= tol T_k,
+ *   or after exactly `fixed_iters` passes when that is > 0; the face populations use the
+ *   moments of the last pass, Grad-projected into the frame those moments define, with
+ *   the co-moving equilibria there; van Leer (default) or minmod limiter on one-sided
+ *   differences divided by the cell size; upwind cell = left/lower when v.n > 0, else
+ *   right/upper; ghost cells (2 layers) are copies (transmissive), wraps (periodic) or
+ *   the equilibrium at a prescribed state (inflow).
+ *
+ * Build: gcc -O2 -ffp-contract=off -fPIC -shared pond_oracle.c -lm
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#include <stdint.h>
+
+#define MAXQ 16
+#define MAXD 2
+#define NG 2
+
+/* ------------------------------------------------------------------ lattice */
+
+typedef struct {
+    int D, Q;
+    double TL;
+    double c[MAXQ][MAXD];
+    double W[MAXQ];
+} lattice;
+
+/* Table I: D1Q4 nodes +-sqrt(3 -+ sqrt 6) with weights (3 +- sqrt 6)/12, T_L = 1.
+ * D2Q16 (Eq. wi): population i = m*4 + n has c_i = (c_m, c_n), W_i = w_m w_n. */
+static void lattice_init(lattice *L, int D)
+{
+    double s6 = sqrt(6.0);
+    double c1[4] = {-sqrt(3.0 + s6), -sqrt(3.0 - s6), sqrt(3.0 - s6), sqrt(3.0 + s6)};
+    double w1[4] = {(3.0 - s6) / 12.0, (3.0 + s6) / 12.0, (3.0 + s6) / 12.0, (3.0 - s6) / 12.0};
+    memset(L, 0, sizeof(*L));
+    L->D = D;
+    L->TL = 1.0;
+    if (D == 1) {
+        L->Q = 4;
+        for (int m = 0; m < 4; ++m) { L->c[m][0] = c1[m]; L->W[m] = w1[m]; }
+    } else {
+        L->Q = 16;
+        for (int m = 0; m < 4; ++m)
+            for (int n = 0; n < 4; ++n) {
+                int i = m * 4 + n;
+                L->c[i][0] = c1[m];
+                L->c[i][1] = c1[n];
+                L->W[i] = w1[m] * w1[n];
+            }
+    }
+}
+
+static double kd(int a, int b) { return a == b ? 1.0 : 0.0; }
+
+/* ------------------------------------------------------- Grad transformation */
+
+/* Sec. II.C: populations f_in known in frame lambda = (u_in, T_in) are re-expressed in
+ * frame lambda' = (u_out, T_out) as the Grad projection Eq. (f_transformed) whose
+ * coefficients are Eqs. (a0)-(a3) evaluated with the lab moments M_k of f_in.
+ * order = 3 for f, 2 for g (the third-order term is dropped). */
+static void grad_transform(const lattice *L, int order, const double *f_in,
+                           const double *u_in, double T_in,
+                           const double *u_out, double T_out, double *f_out)
+{
+    const int D = L->D, Q = L->Q;
+    const double TL = L->TL;
+    double M0 = 0.0, M1[MAXD] = {0}, M2[MAXD][MAXD] = {{0}}, M3[MAXD][MAXD][MAXD] = {{{0}}};
+    const double sin_ = sqrt(T_in / TL);
+    for (int i = 0; i < Q; ++i) {
+        double v[MAXD];
+        for (int a = 0; a < D; ++a) v[a] = sin_ * L->c[i][a] + u_in[a];
+        M0 += f_in[i];
+        for (int a = 0; a < D; ++a) {
+            M1[a] += f_in[i] * v[a];
+            for (int b = 0; b < D; ++b) {
+                M2[a][b] += f_in[i] * v[a] * v[b];
+                for (int c = 0; c < D; ++c) M3[a][b][c] += f_in[i] * v[a] * v[b] * v[c];
+            }
+        }
+    }
+    const double *up = u_out;
+    const double r = sqrt(T_out / TL); /* (T'/T_L)^{1/2} */
+    double a0, a1[MAXD], a2[MAXD][MAXD], a3[MAXD][MAXD][MAXD];
+    /* Eq. (a0) */
+    a0 = M0;
+    /* Eq. (a1) */
+    for (int a = 0; a < D; ++a) a1[a] = (M1[a] - M0 * up[a]) / r;
+    /* Eq. (a2): overline(u' x a1) = u'_a a1_b + a1_a u'_b */
+    for (int a = 0; a < D; ++a)
+        for (int b = 0; b < D; ++b)
+            a2[a][b] = (M2[a][b] - M0 * T_out * kd(a, b) - r * (up[a] * a1[b] + a1[a] * up[b])
+                        - M0 * up[a] * up[b]) / (r * r);
+    /* Eq. (a3): each overline is the sum over the three distinct index placements */
+    memset(a3, 0, sizeof(a3));
+    if (order >= 3) {
+        double X[MAXD][MAXD];
+        for (int a = 0; a < D; ++a)
+            for (int b = 0; b < D; ++b) X[a][b] = M0 * TL * kd(a, b) + a2[a][b];
+        for (int a = 0; a < D; ++a)
+            for (int b = 0; b < D; ++b)
+                for (int c = 0; c < D; ++c) {
+                    double t1 = up[a] * X[b][c] + up[b] * X[a][c] + up[c] * X[a][b];
+                    double t2 = a1[a] * kd(b, c) + a1[b] * kd(a, c) + a1[c] * kd(a, b);
+                    double t3 = a1[a] * up[b] * up[c] + up[a] * a1[b] * up[c] + up[a] * up[b] * a1[c];
+                    a3[a][b][c] = (M3[a][b][c] - (r * r) * t1 - T_out * r * t2 - r * t3
+                                   - M0 * up[a] * up[b] * up[c]) / (r * r * r);
+                }
+    }
+    /* Eq. (f_transformed) */
+    for (int i = 0; i < Q; ++i) {
+        const double *c = L->c[i];
+        double s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        for (int a = 0; a < D; ++a) {
+            s1 += a1[a] * c[a];
+            for (int b = 0; b < D; ++b) {
+                s2 += a2[a][b] * (c[a] * c[b] - TL * kd(a, b));
+                if (order >= 3)
+                    for (int cc = 0; cc < D; ++cc)
+                        s3 += a3[a][b][cc] * (c[a] * c[b] * c[cc]
+                                              - TL * (c[a] * kd(b, cc) + c[b] * kd(a, cc) + c[cc] * kd(a, b)));
+            }
+        }
+        f_out[i] = L->W[i] * (a0 + s1 / TL + s2 / (2.0 * TL * TL) + s3 / (6.0 * TL * TL * TL));
+    }
+}
+
+/* Sec. II.B: rho, rho u, rho E of (f, g) given in frame (u, T). */
+static void conserved_moments(const lattice *L, const double *f, const double *g,
+                              const double *u, double T, double *rho, double *mom, double *rhoE)
+{
+    const int D = L->D, Q = L->Q;
+    double s = sqrt(T / L->TL);
+    double r = 0.0, m[MAXD] = {0}, e = 0.0;
+    for (int i = 0; i < Q; ++i) {
+        double v2 = 0.0;
+        for (int a = 0; a < D; ++a) {
+            double v = s * L->c[i][a] + u[a];
+            m[a] += f[i] * v;
+            v2 += v * v;
+        }
+        r += f[i];
+        e += 0.5 * v2 * f[i] + g[i];
+    }
+    *rho = r;
+    for (int a = 0; a < D; ++a) mom[a] = m[a];
+    *rhoE = e;
+}
+
+/* Eq. (E) solved for T with R = 1, Cv = 1/(gamma-1). */
+static double temperature_from(double rho, const double *mom, double rhoE, int D, double Cv)
+{
+    double k = 0.0;
+    for (int a = 0; a < D; ++a) k += mom[a] * mom[a];
+    return (rhoE - 0.5 * k / rho) / (Cv * rho);
+}
+
+/* Eqs. (feqPond), (geqPond) in the co-moving frame. */
+static void equilibria(const lattice *L, double rho, double T, double Cv, double *feq, double *geq)
+{
+    for (int i = 0; i < L->Q; ++i) {
+        feq[i] = rho * L->W[i];
+        geq[i] = (Cv - 0.5 * L->D) * T * rho * L->W[i];
+    }
+}
+
+/* Slope limiters named in Sec. III.B.3 (van Leer; minmod). a, b: one-sided slopes. */
+static double limiter(int kind, double a, double b)
+{
+    if (kind == 1) { /* minmod */
+        if (a * b <= 0.0) return 0.0;
+        return fabs(a) < fabs(b) ? a : b;
+    }
+    /* van Leer: (sgn a + sgn b) |a||b| / (|a| + |b|) */
+    double den = fabs(a) + fabs(b);
+    if (den == 0.0) return 0.0;
+    double sa = (a > 0.0) - (a < 0.0), sb = (b > 0.0) - (b < 0.0);
+    return (sa + sb) * fabs(a) * fabs(b) / den;
+}
+
+/* --------------------------------------------------------------- the solver */
+
+enum { BC_TRANSMISSIVE = 0, BC_PERIODIC = 1, BC_INFLOW = 2 };
+
+typedef struct oracle {
+    lattice L;
+    int D, Q, nx, ny;
+    int gx, gy;        /* ghost layers in x and y (gy = 0 in 1D) */
+    int px, py;        /* padded extents */
+    double dx, dy, gamma, Cv, tau, cfl, t_end;
+    int bc[4];         /* x-lo, x-hi, y-lo, y-hi */
+    double inflow[4][4];
+    int inflow_lo[4], inflow_hi[4];
+    int limiter;
+    double tol;
+    int max_iter, fixed_iters;
+    /* cell state (padded, AoS): populations in the cell frame (u, T) */
+    double *f, *g, *u, *T;
+    double *fp, *gp;   /* phi-bar-plus, Eq. (Fbarplus) */
+    /* faces: x-faces (nx+1) x ny, y-faces nx x (ny+1); gauge and populations */
+    double *xu, *xT, *yu, *yT;
+    double *xf, *xg, *yf, *yg;
+    double t, dt, last_dt;
+    long long steps, face_iters, face_count, nonconv, nonphys, fallbacks;
+} oracle;
+
+static int cidx(const oracle *o, int i, int j) { return (j + o->gy) * o->px + (i + o->gx); }
+static int xface(const oracle *o, int i, int j) { return j * (o->nx + 1) + i; }
+static int yface(const oracle *o, int i, int j) { return j * o->nx + i; }
+
+static void set_equilibrium_cell(oracle *o, int c, double rho, const double *u, double p)
+{
+    double T = p / rho;
+    equilibria(&o->L, rho, T, o->Cv, o->f + (size_t)c * o->Q, o->g + (size_t)c * o->Q);
+    for (int a = 0; a < o->D; ++a) o->u[(size_t)c * MAXD + a] = u[a];
+    o->T[c] = T;
+}
+
+static void copy_cell(oracle *o, int dst, int src)
+{
+    memcpy(o->f + (size_t)dst * o->Q, o->f + (size_t)src * o->Q, sizeof(double) * o->Q);
+    memcpy(o->g + (size_t)dst * o->Q, o->g + (size_t)src * o->Q, sizeof(double) * o->Q);
+    memcpy(o->u + (size_t)dst * MAXD, o->u + (size_t)src * MAXD, sizeof(double) * MAXD);
+    o->T[dst] = o->T[src];
+}
+
+static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+static int wrapi(int v, int n) { return ((v % n) + n) % n; }
+
+/* Two ghost layers: x-sides first (interior rows), then y-sides for every padded column. */
+static void fill_ghosts(oracle *o)
+{
+    for (int j = 0; j < o->ny; ++j)
+        for (int k = 1; k <= o->gx; ++k) {
+            for (int side = 0; side < 2; ++side) {
+                int i = side == 0 ? -k : o->nx - 1 + k;
+                int dst = cidx(o, i, j);
+                int b = o->bc[side];
+                if (b == BC_INFLOW && j >= o->inflow_lo[side] && j < o->inflow_hi[side]) {
+                    double uu[2] = {o->inflow[side][1], o->inflow[side][2]};
+                    set_equilibrium_cell(o, dst, o->inflow[side][0], uu, o->inflow[side][3]);
+                } else if (b == BC_PERIODIC) {
+                    copy_cell(o, dst, cidx(o, wrapi(i, o->nx), j));
+                } else {
+                    copy_cell(o, dst, cidx(o, clampi(i, 0, o->nx - 1), j));
+                }
+            }
+        }
+    if (o->D < 2) return;
+    for (int i = -o->gx; i < o->nx + o->gx; ++i)
+        for (int k = 1; k <= o->gy; ++k) {
+            for (int side = 2; side < 4; ++side) {
+                int j = side == 2 ? -k : o->ny - 1 + k;
+                int dst = cidx(o, i, j);
+                int b = o->bc[side];
+                int ic = clampi(i, 0, o->nx - 1);
+                if (b == BC_INFLOW && ic >= o->inflow_lo[side] && ic < o->inflow_hi[side]) {
+                    double uu[2] = {o->inflow[side][1], o->inflow[side][2]};
+                    set_equilibrium_cell(o, dst, o->inflow[side][0], uu, o->inflow[side][3]);
+                } else if (b == BC_PERIODIC) {
+                    copy_cell(o, dst, cidx(o, i, wrapi(j, o->ny)));
+                } else {
+                    copy_cell(o, dst, cidx(o, i, clampi(j, 0, o->ny - 1)));
+                }
+            }
+        }
+}
+
+oracle *oracle_create(int D, int nx, int ny, double dx, double dy, double gamma, double tau,
+                      double cfl, double t_end, const int *bc, const double *inflow,
+                      const int *inflow_range, int limiter_kind, double tol, int max_iter,
+                      int fixed_iters)
+{
+    if (D != 1 && D != 2) return NULL;
+    if (D == 1) ny = 1;
+    oracle *o = (oracle *)calloc(1, sizeof(oracle));
+    lattice_init(&o->L, D);
+    o->D = D; o->Q = o->L.Q; o->nx = nx; o->ny = ny;
+    o->gx = NG; o->gy = D == 2 ? NG : 0;
+    o->px = nx + 2 * o->gx; o->py = ny + 2 * o->gy;
+    o->dx = dx; o->dy = D == 2 ? dy : 1.0;
+    o->gamma = gamma; o->Cv = 1.0 / (gamma - 1.0);
+    o->tau = tau; o->cfl = cfl; o->t_end = t_end;
+    for (int s = 0; s < 4; ++s) {
+        o->bc[s] = bc ? bc[s] : BC_TRANSMISSIVE;
+        for (int q = 0; q < 4; ++q) o->inflow[s][q] = inflow ? inflow[s * 4 + q] : 0.0;
+        o->inflow_lo[s] = inflow_range ? inflow_range[2 * s] : 0;
+        o->inflow_hi[s] = inflow_range ? inflow_range[2 * s + 1] : 0;
+    }
+    o->limiter = limiter_kind; o->tol = tol; o->max_iter = max_iter; o->fixed_iters = fixed_iters;
+    size_t nc = (size_t)o->px * o->py;
+    o->f = calloc(nc * o->Q, sizeof(double));
+    o->g = calloc(nc * o->Q, sizeof(double));
+    o->fp = calloc(nc * o->Q, sizeof(double));
+    o->gp = calloc(nc * o->Q, sizeof(double));
+    o->u = calloc(nc * MAXD, sizeof(double));
+    o->T = calloc(nc, sizeof(double));
+    size_t nxf = (size_t)(nx + 1) * ny, nyf = (size_t)nx * (ny + 1);
+    o->xu = calloc(nxf * MAXD, sizeof(double)); o->xT = calloc(nxf, sizeof(double));
+    o->xf = calloc(nxf * o->Q, sizeof(double)); o->xg = calloc(nxf * o->Q, sizeof(double));
+    o->yu = calloc(nyf * MAXD, sizeof(double)); o->yT = calloc(nyf, sizeof(double));
+    o->yf = calloc(nyf * o->Q, sizeof(double)); o->yg = calloc(nyf * o->Q, sizeof(double));
+    return o;
+}
+
+void oracle_free(oracle *o)
+{
+    if (!o) return;
+    free(o->f); free(o->g); free(o->fp); free(o->gp); free(o->u); free(o->T);
+    free(o->xu); free(o->xT); free(o->xf); free(o->xg);
+    free(o->yu); free(o->yT); free(o->yf); free(o->yg);
+    free(o);
+}
+
+/* Face predictor before the first step: the frame of the pooled conserved moments of the
+ * two adjacent cells (their mean density, momentum and total energy). */
+static void pooled_frame(const oracle *o, int A, int B, double *u, double *T)
+{
+    double rA, rB, mA[MAXD] = {0}, mB[MAXD] = {0}, eA, eB, m[MAXD] = {0};
+    conserved_moments(&o->L, o->f + (size_t)A * o->Q, o->g + (size_t)A * o->Q, o->u + (size_t)A * MAXD, o->T[A], &rA, mA, &eA);
+    conserved_moments(&o->L, o->f + (size_t)B * o->Q, o->g + (size_t)B * o->Q, o->u + (size_t)B * MAXD, o->T[B], &rB, mB, &eB);
+    double r = 0.5 * (rA + rB), e = 0.5 * (eA + eB);
+    for (int a = 0; a < o->D; ++a) { m[a] = 0.5 * (mA[a] + mB[a]); u[a] = m[a] / r; }
+    *T = temperature_from(r, m, e, o->D, o->Cv);
+}
+
+/* Frame of the pooled conserved moments of n cells. */
+static void pooled_frame_n(const oracle *o, const int *cells, int n, double *u, double *T)
+{
+    double r = 0.0, m[MAXD] = {0}, e = 0.0;
+    for (int s = 0; s < n; ++s) {
+        int A = cells[s];
+        double rA, mA[MAXD] = {0}, eA;
+        conserved_moments(&o->L, o->f + (size_t)A * o->Q, o->g + (size_t)A * o->Q, o->u + (size_t)A * MAXD, o->T[A], &rA, mA, &eA);
+        r += rA / n; e += eA / n;
+        for (int a = 0; a < o->D; ++a) m[a] += mA[a] / n;
+    }
+    for (int a = 0; a < o->D; ++a) u[a] = m[a] / r;
+    *T = temperature_from(r, m, e, o->D, o->Cv);
+}
+
+static void init_face_gauges(oracle *o)
+{
+    for (int j = 0; j < o->ny; ++j)
+        for (int i = 0; i <= o->nx; ++i) {
+            int fidx = xface(o, i, j);
+            pooled_frame(o, cidx(o, i - 1, j), cidx(o, i, j), o->xu + (size_t)fidx * MAXD, o->xT + fidx);
+        }
+    if (o->D < 2) return;
+    for (int j = 0; j <= o->ny; ++j)
+        for (int i = 0; i < o->nx; ++i) {
+            int fidx = yface(o, i, j);
+            pooled_frame(o, cidx(o, i, j - 1), cidx(o, i, j), o->yu + (size_t)fidx * MAXD, o->yT + fidx);
+        }
+}
+
+/* Initial condition: equilibrium populations in each cell's co-moving frame, from
+ * primitive fields (rho, ux, uy, p) of size nx*ny (x fastest).  uy may be NULL in 1D. */
+void oracle_set_primitive(oracle *o, const double *rho, const double *ux, const double *uy,
+                          const double *p)
+{
+    for (int j = 0; j < o->ny; ++j)
+        for (int i = 0; i < o->nx; ++i) {
+            int k = j * o->nx + i;
+            double uu[2] = {ux[k], (o->D == 2 && uy) ? uy[k] : 0.0};
+            set_equilibrium_cell(o, cidx(o, i, j), rho[k], uu, p[k]);
+        }
+    fill_ghosts(o);
+    init_face_gauges(o);
+    o->t = 0.0; o->dt = 0.0; o->steps = 0;
+    o->face_iters = o->face_count = o->nonconv = o->nonphys = o->fallbacks = 0;
+}
+
+static int bad(double x) { return !(x == x) || isinf(x); }
+
+/* Algorithm step 1: express the populations of a cell in its own co-moving frame. */
+static void regauge_cell(oracle *o, int c)
+{
+    const lattice *L = &o->L;
+    double *f = o->f + (size_t)c * o->Q, *g = o->g + (size_t)c * o->Q;
+    double *u = o->u + (size_t)c * MAXD;
+    double rho, mom[MAXD] = {0}, rhoE;
+    conserved_moments(L, f, g, u, o->T[c], &rho, mom, &rhoE);
+    double un[MAXD] = {0};
+    for (int a = 0; a < o->D; ++a) un[a] = mom[a] / rho;
+    double Tn = temperature_from(rho, mom, rhoE, o->D, o->Cv);
+    if (!(rho > 0.0) || !(Tn > 0.0) || bad(rho) || bad(Tn)) { o->nonphys++; return; }
+    double fo[MAXQ], go[MAXQ];
+    grad_transform(L, 3, f, u, o->T[c], un, Tn, fo);
+    grad_transform(L, 2, g, u, o->T[c], un, Tn, go);
+    memcpy(f, fo, sizeof(double) * o->Q);
+    memcpy(g, go, sizeof(double) * o->Q);
+    for (int a = 0; a < o->D; ++a) u[a] = un[a];
+    o->T[c] = Tn;
+}
+
+/* CFL = max|v_ia| dt/dx with v_i = sqrt(T/T_L) c_i + u over all interior cells. */
+static double cfl_dt(const oracle *o)
+{
+    double cmax = 0.0;
+    for (int i = 0; i < o->Q; ++i)
+        for (int a = 0; a < o->D; ++a) cmax = fmax(cmax, fabs(o->L.c[i][a]));
+    double rate = 0.0;
+    for (int j = 0; j < o->ny; ++j)
+        for (int i = 0; i < o->nx; ++i) {
+            int c = cidx(o, i, j);
+            double s = sqrt(o->T[c] / o->L.TL) * cmax;
+            rate = fmax(rate, (fabs(o->u[(size_t)c * MAXD + 0]) + s) / o->dx);
+            if (o->D == 2) rate = fmax(rate, (fabs(o->u[(size_t)c * MAXD + 1]) + s) / o->dy);
+        }
+    return o->cfl / rate;
+}
+
+/* One face (Sec. III.B.3).  dir = 0: x-face, dir = 1: y-face.  Cells along the normal:
+ * LL, L, R, RR; tangential neighbours of L and R: Lm, Lp, Rm, Rp (2D only).
+ * Writes the face gauge (in/out) and the face populations phi (in the face frame). */
+static void solve_face(oracle *o, int dir, const int cells[8], double *gu, double *gT,
+                       double *face_f, double *face_g, double h)
+{
+    const lattice *L = &o->L;
+    const int D = o->D, Q = o->Q;
+    const double dn = dir == 0 ? o->dx : o->dy;   /* spacing along the normal */
+    const double dtg = dir == 0 ? o->dy : o->dx;  /* spacing along the tangent */
+    const int tdir = 1 - dir;
+    const int ncell = D == 2 ? 8 : 4;
+    double pf[8][MAXQ], pg[8][MAXQ];
+    double lam_u[MAXD] = {0}, lam_T = *gT;
+    for (int a = 0; a < D; ++a) lam_u[a] = gu[a];
+    double fbar[MAXQ], gbar[MAXQ];
+    /* the last pass that defined a frame: its populations, the frame it ran in, its moments */
+    double keep_f[MAXQ], keep_g[MAXQ], keep_in_u[MAXD] = {0}, keep_in_T = 0.0;
+    double keep_u[MAXD] = {0}, keep_T = 0.0, keep_rho = 0.0;
+    int have = 0, iters = 0, done = 0, restarted = 0;
+    for (int k = 0; k < o->max_iter && !done; ++k) {
+        /* regularized transformation of phi-bar-plus of every stencil cell into lambda_k */
+        for (int s = 0; s < ncell; ++s) {
+            int c = cells[s];
+            grad_transform(L, 3, o->fp + (size_t)c * Q, o->u + (size_t)c * MAXD, o->T[c], lam_u, lam_T, pf[s]);
+            grad_transform(L, 2, o->gp + (size_t)c * Q, o->u + (size_t)c * MAXD, o->T[c], lam_u, lam_T, pg[s]);
+        }
+        double sq = sqrt(lam_T / L->TL);
+        for (int i = 0; i < Q; ++i) {
+            double v[MAXD];
+            for (int a = 0; a < D; ++a) v[a] = sq * L->c[i][a] + lam_u[a];
+            /* upwind cell and its neighbours: [upstream, up, downstream, tangential-, tangential+] */
+            int up, lo, hi, tm, tp;
+            double off_n;
+            if (v[dir] > 0.0) { up = 1; lo = 0; hi = 2; tm = 4; tp = 5; off_n = 0.5 * dn; }
+            else              { up = 2; lo = 1; hi = 3; tm = 6; tp = 7; off_n = -0.5 * dn; }
+            /* departure point x' = x_b - v h, measured from the upwind cell centre */
+            double dxn = off_n - v[dir] * h;
+            double dxt = D == 2 ? -v[tdir] * h : 0.0;
+            for (int pop = 0; pop < 2; ++pop) {
+                double (*P)[MAXQ] = pop == 0 ? pf : pg;
+                double sn = limiter(o->limiter, (P[up][i] - P[lo][i]) / dn, (P[hi][i] - P[up][i]) / dn);
+                double st = 0.0;
+                if (D == 2)
+                    st = limiter(o->limiter, (P[up][i] - P[tm][i]) / dtg, (P[tp][i] - P[up][i]) / dtg);
+                double val = P[up][i] + dxn * sn + dxt * st;
+                if (pop == 0) fbar[i] = val; else gbar[i] = val;
+            }
+        }
+        /* Eqs. (correctorfieldsrhoDUGKS)-(correctorfieldsTDUGKS) */
+        double rho1, mom[MAXD] = {0}, rhoE, u1[MAXD] = {0};
+        conserved_moments(L, fbar, gbar, lam_u, lam_T, &rho1, mom, &rhoE);
+        for (int a = 0; a < D; ++a) u1[a] = mom[a] / rho1;
+        double T1 = temperature_from(rho1, mom, rhoE, D, o->Cv);
+        iters = k + 1;
+        if (!(T1 > 0.0) || bad(rho1) || bad(T1) || bad(u1[0]) || (D == 2 && bad(u1[1]))) {
+            /* this pass defines no frame: restart once from the pooled frame of the two
+             * cells next to the face, otherwise stop at the last pass that did */
+            o->fallbacks++;
+            if (!restarted) {
+                restarted = 1;
+                pooled_frame_n(o, cells, ncell, lam_u, &lam_T);
+                continue;
+            }
+            break;
+        }
+        memcpy(keep_f, fbar, sizeof(keep_f));
+        memcpy(keep_g, gbar, sizeof(keep_g));
+        for (int a = 0; a < D; ++a) { keep_in_u[a] = lam_u[a]; keep_u[a] = u1[a]; }
+        keep_in_T = lam_T; keep_T = T1; keep_rho = rho1;
+        have = 1;
+        if (o->fixed_iters > 0) {
+            done = iters >= o->fixed_iters;
+        } else {
+            double du = 0.0;
+            for (int a = 0; a < D; ++a) du = fmax(du, fabs(u1[a] - lam_u[a]));
+            done = du <= o->tol * sqrt(lam_T) && fabs(T1 - lam_T) <= o->tol * lam_T;
+        }
+        for (int a = 0; a < D; ++a) lam_u[a] = u1[a];
+        lam_T = T1;
+    }
+    o->face_iters += iters;
+    o->face_count += 1;
+    if (!done) o->nonconv++;
+    if (!have) { o->nonphys++; keep_T = NAN; keep_in_T = NAN; }
+    /* Eq. (FluxTransf) at the frame defined by the moments of the last valid pass, with the
+     * exact co-moving equilibria there: phi = (2 tau phibar + h phi^eq) / (2 tau + h). */
+    double fb2[MAXQ], gb2[MAXQ], feq[MAXQ], geq[MAXQ];
+    grad_transform(L, 3, keep_f, keep_in_u, keep_in_T, keep_u, keep_T, fb2);
+    grad_transform(L, 2, keep_g, keep_in_u, keep_in_T, keep_u, keep_T, gb2);
+    equilibria(L, keep_rho, keep_T, o->Cv, feq, geq);
+    double tau = o->tau;
+    for (int i = 0; i < Q; ++i) {
+        face_f[i] = (2.0 * tau * fb2[i] + h * feq[i]) / (2.0 * tau + h);
+        face_g[i] = (2.0 * tau * gb2[i] + h * geq[i]) / (2.0 * tau + h);
+    }
+    for (int a = 0; a < D; ++a) gu[a] = keep_u[a];
+    *gT = keep_T;
+}
+
+/* Adds the contribution (v_i . n) phi_i^{lambda_j} A/V of one face to the flux F of cell c. */
+static void add_face_flux(oracle *o, int c, const double *face_u, double face_T,
+                          const double *face_f, const double *face_g, int dir, double sign,
+                          double area_over_vol, double *Ff, double *Fg)
+{
+    const lattice *L = &o->L;
+    double pf[MAXQ], pg[MAXQ];
+    const double *uc = o->u + (size_t)c * MAXD;
+    grad_transform(L, 3, face_f, face_u, face_T, uc, o->T[c], pf);
+    grad_transform(L, 2, face_g, face_u, face_T, uc, o->T[c], pg);
+    double sq = sqrt(o->T[c] / L->TL);
+    for (int i = 0; i < o->Q; ++i) {
+        double vn = sign * (sq * L->c[i][dir] + uc[dir]);
+        Ff[i] += vn * pf[i] * area_over_vol;
+        Fg[i] += vn * pg[i] * area_over_vol;
+    }
+}
+
+static void stencil_x(const oracle *o, int i, int j, int cells[8])
+{
+    /* x-face i sits between cells (i-1, j) and (i, j) */
+    cells[0] = cidx(o, i - 2, j); cells[1] = cidx(o, i - 1, j);
+    cells[2] = cidx(o, i, j);     cells[3] = cidx(o, i + 1, j);
+    if (o->D == 2) {
+        cells[4] = cidx(o, i - 1, j - 1); cells[5] = cidx(o, i - 1, j + 1);
+        cells[6] = cidx(o, i, j - 1);     cells[7] = cidx(o, i, j + 1);
+    }
+}
+
+static void stencil_y(const oracle *o, int i, int j, int cells[8])
+{
+    /* y-face j sits between cells (i, j-1) and (i, j) */
+    cells[0] = cidx(o, i, j - 2); cells[1] = cidx(o, i, j - 1);
+    cells[2] = cidx(o, i, j);     cells[3] = cidx(o, i, j + 1);
+    cells[4] = cidx(o, i - 1, j - 1); cells[5] = cidx(o, i + 1, j - 1);
+    cells[6] = cidx(o, i - 1, j);     cells[7] = cidx(o, i + 1, j);
+}
+
+/* Advances n time steps (fewer when t_end > 0 is reached).  Returns the number taken. */
+int oracle_step(oracle *o, int n)
+{
+    const lattice *L = &o->L;
+    const int Q = o->Q, D = o->D;
+    int taken = 0;
+    for (int s = 0; s < n; ++s) {
+        if (o->t_end > 0.0 && o->t >= o->t_end) break;
+        /* 1. every cell in its local frame */
+        for (int j = 0; j < o->ny; ++j)
+            for (int i = 0; i < o->nx; ++i) regauge_cell(o, cidx(o, i, j));
+        fill_ghosts(o);
+        double dt = cfl_dt(o);
+        if (o->t_end > 0.0 && o->t + dt > o->t_end) dt = o->t_end - o->t;
+        const double h = 0.5 * dt, tau = o->tau;
+        /* 2a. phi-bar-plus at every cell (ghosts included), Eq. (Fbarplus) with Eq. (variableTransform) */
+        const double cp = (2.0 * tau - h) / (2.0 * tau + dt), ce = 3.0 * h / (2.0 * tau + dt);
+        for (int c = 0; c < o->px * o->py; ++c) {
+            double rho = 0.0;
+            for (int i = 0; i < Q; ++i) rho += o->f[(size_t)c * Q + i];
+            double feq[MAXQ], geq[MAXQ];
+            equilibria(L, rho, o->T[c], o->Cv, feq, geq);
+            for (int i = 0; i < Q; ++i) {
+                o->fp[(size_t)c * Q + i] = cp * o->f[(size_t)c * Q + i] + ce * feq[i];
+                o->gp[(size_t)c * Q + i] = cp * o->g[(size_t)c * Q + i] + ce * geq[i];
+            }
+        }
+        /* 2b. face populations at t_{n+1/2} in the co-moving face frame */
+        int cells[8];
+        for (int j = 0; j < o->ny; ++j)
+            for (int i = 0; i <= o->nx; ++i) {
+                int fi = xface(o, i, j);
+                stencil_x(o, i, j, cells);
+                solve_face(o, 0, cells, o->xu + (size_t)fi * MAXD, o->xT + fi,
+                           o->xf + (size_t)fi * Q, o->xg + (size_t)fi * Q, h);
+            }
+        if (D == 2)
+            for (int j = 0; j <= o->ny; ++j)
+                for (int i = 0; i < o->nx; ++i) {
+                    int fi = yface(o, i, j);
+                    stencil_y(o, i, j, cells);
+                    solve_face(o, 1, cells, o->yu + (size_t)fi * MAXD, o->yT + fi,
+                               o->yf + (size_t)fi * Q, o->yg + (size_t)fi * Q, h);
+                }
+        /* 3. flux into each cell's frame, Eq. (fluxEq), and update, Eqs. (FinalUpdateDUGKS) */
+        const double ca = (2.0 * tau - dt) / (2.0 * tau + dt), cb = 2.0 * dt / (2.0 * tau + dt);
+        for (int j = 0; j < o->ny; ++j)
+            for (int i = 0; i < o->nx; ++i) {
+                int c = cidx(o, i, j);
+                double Ff[MAXQ] = {0}, Fg[MAXQ] = {0};
+                int fl = xface(o, i, j), fr = xface(o, i + 1, j);
+                add_face_flux(o, c, o->xu + (size_t)fl * MAXD, o->xT[fl], o->xf + (size_t)fl * Q,
+                              o->xg + (size_t)fl * Q, 0, -1.0, 1.0 / o->dx, Ff, Fg);
+                add_face_flux(o, c, o->xu + (size_t)fr * MAXD, o->xT[fr], o->xf + (size_t)fr * Q,
+                              o->xg + (size_t)fr * Q, 0, +1.0, 1.0 / o->dx, Ff, Fg);
+                if (D == 2) {
+                    int fb = yface(o, i, j), ft = yface(o, i, j + 1);
+                    add_face_flux(o, c, o->yu + (size_t)fb * MAXD, o->yT[fb], o->yf + (size_t)fb * Q,
+                                  o->yg + (size_t)fb * Q, 1, -1.0, 1.0 / o->dy, Ff, Fg);
+                    add_face_flux(o, c, o->yu + (size_t)ft * MAXD, o->yT[ft], o->yf + (size_t)ft * Q,
+                                  o->yg + (size_t)ft * Q, 1, +1.0, 1.0 / o->dy, Ff, Fg);
+                }
+                double rho = 0.0;
+                for (int q = 0; q < Q; ++q) rho += o->f[(size_t)c * Q + q];
+                double feq[MAXQ], geq[MAXQ];
+                equilibria(L, rho, o->T[c], o->Cv, feq, geq);
+                for (int q = 0; q < Q; ++q) {
+                    double *fq = o->f + (size_t)c * Q + q, *gq = o->g + (size_t)c * Q + q;
+                    *fq = ca * *fq + cb * feq[q] - dt * Ff[q];
+                    *gq = ca * *gq + cb * geq[q] - dt * Fg[q];
+                }
+            }
+        o->t += dt;
+        o->last_dt = dt;
+        o->steps++;
+        taken++;
+    }
+    return taken;
+}
+
+/* --------------------------------------------------------------- read-back */
+
+/* Conserved fields per interior cell (x fastest); my may be NULL in 1D. */
+void oracle_conserved(const oracle *o, double *rho, double *mx, double *my, double *E)
+{
+    for (int j = 0; j < o->ny; ++j)
+        for (int i = 0; i < o->nx; ++i) {
+            int c = cidx(o, i, j), k = j * o->nx + i;
+            double r, m[MAXD] = {0}, e;
+            conserved_moments(&o->L, o->f + (size_t)c * o->Q, o->g + (size_t)c * o->Q,
+                              o->u + (size_t)c * MAXD, o->T[c], &r, m, &e);
+            rho[k] = r; mx[k] = m[0];
+            if (my) my[k] = o->D == 2 ? m[1] : 0.0;
+            E[k] = e;
+        }
+}
+
+/* Populations and frames of the interior cells, each first re-expressed in its own
+ * co-moving frame (algorithm step 1, on a copy; the stored state is not changed).
+ * f, g: [cells][Q]; u: [cells][D]; T: [cells]. */
+void oracle_regauged_state(const oracle *o, double *f, double *g, double *u, double *T)
+{
+    const lattice *L = &o->L;
+    for (int j = 0; j < o->ny; ++j)
+        for (int i = 0; i < o->nx; ++i) {
+            int c = cidx(o, i, j), k = j * o->nx + i;
+            const double *fc = o->f + (size_t)c * o->Q, *gc = o->g + (size_t)c * o->Q;
+            const double *uc = o->u + (size_t)c * MAXD;
+            double rho, mom[MAXD] = {0}, rhoE, un[MAXD] = {0};
+            conserved_moments(L, fc, gc, uc, o->T[c], &rho, mom, &rhoE);
+            for (int a = 0; a < o->D; ++a) un[a] = mom[a] / rho;
+            double Tn = temperature_from(rho, mom, rhoE, o->D, o->Cv);
+            grad_transform(L, 3, fc, uc, o->T[c], un, Tn, f + (size_t)k * o->Q);
+            grad_transform(L, 2, gc, uc, o->T[c], un, Tn, g + (size_t)k * o->Q);
+            for (int a = 0; a < o->D; ++a) u[(size_t)k * o->D + a] = un[a];
+            T[k] = Tn;
+        }
+}
+
+/* Raw state (populations as stored, in the frame of the previous step). */
+void oracle_raw_state(const oracle *o, double *f, double *g, double *u, double *T)
+{
+    for (int j = 0; j < o->ny; ++j)
+        for (int i = 0; i < o->nx; ++i) {
+            int c = cidx(o, i, j), k = j * o->nx + i;
+            memcpy(f + (size_t)k * o->Q, o->f + (size_t)c * o->Q, sizeof(double) * o->Q);
+            memcpy(g + (size_t)k * o->Q, o->g + (size_t)c * o->Q, sizeof(double) * o->Q);
+            for (int a = 0; a < o->D; ++a) u[(size_t)k * o->D + a] = o->u[(size_t)c * MAXD + a];
+            T[k] = o->T[c];
+        }
+}
+
+/* Overwrites the interior state with populations (f, g) given in frames (u, T). */
+void oracle_set_state(oracle *o, const double *f, const double *g, const double *u, const double *T)
+{
+    for (int j = 0; j < o->ny; ++j)
+        for (int i = 0; i < o->nx; ++i) {
+            int c = cidx(o, i, j), k = j * o->nx + i;
+            memcpy(o->f + (size_t)c * o->Q, f + (size_t)k * o->Q, sizeof(double) * o->Q);
+            memcpy(o->g + (size_t)c * o->Q, g + (size_t)k * o->Q, sizeof(double) * o->Q);
+            for (int a = 0; a < o->D; ++a) o->u[(size_t)c * MAXD + a] = u[(size_t)k * o->D + a];
+            o->T[c] = T[k];
+        }
+    fill_ghosts(o);
+    init_face_gauges(o);
+}
+
+/* Face gauges: x-faces [(nx+1)*ny][D+1] then (2D) y-faces [nx*(ny+1)][D+1], as (u..., T). */
+void oracle_face_gauges(const oracle *o, double *xg, double *yg)
+{
+    int D = o->D;
+    for (int k = 0; k < (o->nx + 1) * o->ny; ++k) {
+        for (int a = 0; a < D; ++a) xg[(size_t)k * (D + 1) + a] = o->xu[(size_t)k * MAXD + a];
+        xg[(size_t)k * (D + 1) + D] = o->xT[k];
+    }
+    if (D == 2 && yg)
+        for (int k = 0; k < o->nx * (o->ny + 1); ++k) {
+            for (int a = 0; a < D; ++a) yg[(size_t)k * (D + 1) + a] = o->yu[(size_t)k * MAXD + a];
+            yg[(size_t)k * (D + 1) + D] = o->yT[k];
+        }
+}
+
+/* Overwrites the face gauges (same layout as oracle_face_gauges). */
+void oracle_set_face_gauges(oracle *o, const double *xg, const double *yg)
+{
+    int D = o->D;
+    for (int k = 0; k < (o->nx + 1) * o->ny; ++k) {
+        for (int a = 0; a < D; ++a) o->xu[(size_t)k * MAXD + a] = xg[(size_t)k * (D + 1) + a];
+        o->xT[k] = xg[(size_t)k * (D + 1) + D];
+    }
+    if (D == 2 && yg)
+        for (int k = 0; k < o->nx * (o->ny + 1); ++k) {
+            for (int a = 0; a < D; ++a) o->yu[(size_t)k * MAXD + a] = yg[(size_t)k * (D + 1) + a];
+            o->yT[k] = yg[(size_t)k * (D + 1) + D];
+        }
+}
+
+/* time, last dt, steps, face iterations, faces solved, non-converged faces, non-physical
+ * events, corrector passes that defined no frame */
+void oracle_stats(const oracle *o, double *t, double *dt, long long *counts)
+{
+    *t = o->t; *dt = o->last_dt;
+    counts[0] = o->steps; counts[1] = o->face_iters; counts[2] = o->face_count;
+    counts[3] = o->nonconv; counts[4] = o->nonphys; counts[5] = o->fallbacks;
+}
+
+/* ------------------------------------------------ unit-level entry points */
+
+int oracle_lattice(int D, double *c, double *w, double *TL)
+{
+    lattice L;
+    if (D != 1 && D != 2) return 0;
+    lattice_init(&L, D);
+    for (int i = 0; i < L.Q; ++i) {
+        for (int a = 0; a < D; ++a) c[i * D + a] = L.c[i][a];
+        w[i] = L.W[i];
+    }
+    *TL = L.TL;
+    return L.Q;
+}
+
+void oracle_grad_transform(int D, int order, const double *f_in, const double *u_in, double T_in,
+                           const double *u_out, double T_out, double *f_out)
+{
+    lattice L;
+    lattice_init(&L, D);
+    grad_transform(&L, order, f_in, u_in, T_in, u_out, T_out, f_out);
+}
+
+double oracle_limiter(int kind, double a, double b) { return limiter(kind, a, b); }

@@ -1,0 +1,252 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the smoke check.
+
+This module holds only problem definitions: primitive fields (rho, u, p), grids,
+boundary conditions and random draws.  It contains none of the method's arithmetic,
+so both the CUDA library and the CPU oracle can be fed from it.
+
+Workloads (paper Sec. IV; sizes of the benchmark configurations):
+  - ``shock_tube``      two-state 1D Riemann problems (Sod, Lax, strong shock, jet ...)
+  - ``quadrants_2d``    2D four-quadrant Riemann problem with seeded quadrant states
+  - ``tube_batch``      thousands of 1D tubes of uneven length with seeded states
+  - ``shocked_interface_2d``  planar shock hitting a perturbed density interface
+  - ``jet_2d``          high-Mach jet entering a light ambient through a left inflow band
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+TRANSMISSIVE, PERIODIC, INFLOW = 0, 1, 2
+
+
+@dataclass
+class Problem:
+    dim: int
+    nx: int
+    ny: int
+    x0: float
+    x1: float
+    y0: float
+    y1: float
+    gamma: float
+    rho: np.ndarray
+    ux: np.ndarray
+    uy: np.ndarray
+    p: np.ndarray
+    bc: tuple = (TRANSMISSIVE,) * 4
+    inflow: np.ndarray = field(default_factory=lambda: np.zeros((4, 4)))
+    inflow_range: np.ndarray = field(default_factory=lambda: np.zeros((4, 2), dtype=np.int64))
+    name: str = ""
+
+    @property
+    def dx(self):
+        return (self.x1 - self.x0) / self.nx
+
+    @property
+    def dy(self):
+        return (self.y1 - self.y0) / self.ny if self.dim == 2 else 1.0
+
+    @property
+    def ncell(self):
+        return self.nx * self.ny
+
+
+def cell_centres(n, a, b):
+    return a + (np.arange(n) + 0.5) * (b - a) / n
+
+
+# Two-state tubes of the paper (Sec. IV.A-C): (left, right, gamma, x0, x1, x_split, t_end)
+PAPER_TUBES = {
+    "sod_classic": ((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 1.4, 0.0, 1.0, 0.5, 0.2),
+    "sod_paper": ((1.0, 0.0, 0.15), (0.125, 0.0, 0.015), 1.4, 0.0, 1.0, 0.5, 0.2),
+    "lax": ((0.445, 0.698, 3.528), (0.5, 0.0, 0.571), 1.4, 0.0, 1.0, 0.5, 0.14),
+    "strong_shock": ((1.0, 0.0, 1000.0), (1.0, 0.0, 0.01), 1.4, 0.0, 1.0, 0.5, 0.012),
+    "double_rarefaction": ((1.0, -2.0, 0.1), (1.0, 2.0, 0.1), 1.4, 0.0, 1.0, 0.5, 0.1),
+    "jet_1d": ((5.0, 30.0, 0.4127), (0.5, 0.0, 0.4127), 5.0 / 3.0, 0.0, 2.0, 0.1, 0.06),
+}
+
+
+def shock_tube(left, right, gamma, n, x0=0.0, x1=1.0, x_split=0.5, name=""):
+    """1D two-state Riemann problem; the left state holds where the cell centre < x_split."""
+    x = cell_centres(n, x0, x1)
+    L = x < x_split
+    rho = np.where(L, left[0], right[0]).astype(np.float64)
+    ux = np.where(L, left[1], right[1]).astype(np.float64)
+    p = np.where(L, left[2], right[2]).astype(np.float64)
+    return Problem(1, n, 1, x0, x1, 0.0, 1.0, float(gamma), rho, ux, np.zeros(n), p, name=name)
+
+
+def paper_tube(name, n):
+    left, right, g, x0, x1, xs, t_end = PAPER_TUBES[name]
+    return shock_tube(left, right, g, n, x0, x1, xs, name=name), t_end
+
+
+def sod_400():
+    """Shock tube on [0,1]: (1, 0, 1) | (0.125, 0, 0.1) at x = 0.5, gamma 1.4, 400 cells."""
+    return shock_tube((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 1.4, 400, name="sod_400")
+
+
+def quadrants_2d(n, seed, gamma=1.4, mach_max=3.0):
+    """2D four-quadrant Riemann problem on the unit square (n x n cells).
+
+    Each quadrant draws rho and p log-uniform in [0.1, 10] and a Mach number uniform in
+    [0, mach_max]; its velocity points towards the domain centre within +-45 degrees, so
+    that neighbouring quadrants meet in shocks, contacts and slip lines."""
+    rng = np.random.default_rng(seed)
+    r4 = np.exp(rng.uniform(np.log(0.1), np.log(10.0), 4))
+    p4 = np.exp(rng.uniform(np.log(0.1), np.log(10.0), 4))
+    M = rng.uniform(0.0, mach_max, 4)
+    cx = np.array([0.25, 0.75, 0.25, 0.75])
+    cy = np.array([0.25, 0.25, 0.75, 0.75])
+    th = np.arctan2(0.5 - cy, 0.5 - cx) + rng.uniform(-np.pi / 4, np.pi / 4, 4)
+    c = np.sqrt(gamma * p4 / r4)
+    u4, v4 = M * c * np.cos(th), M * c * np.sin(th)
+    x = cell_centres(n, 0.0, 1.0)
+    X, Y = np.meshgrid(x, x)  # rows are y
+    q = ((X > 0.5).astype(np.int64) + 2 * (Y > 0.5).astype(np.int64)).ravel()
+    return Problem(2, n, n, 0.0, 1.0, 0.0, 1.0, gamma, r4[q], u4[q], v4[q], p4[q],
+                   name="quadrants_%d_seed%d" % (n, seed))
+
+
+def lax_liu_2d(n):
+    """The 2D Riemann configuration of Sec. IV.C (symmetric under x <-> y)."""
+    x = cell_centres(n, 0.0, 1.0)
+    X, Y = np.meshgrid(x, x)
+    rho = np.select([(X > 0.5) & (Y > 0.5), (X <= 0.5) & (Y > 0.5), (X <= 0.5) & (Y <= 0.5)],
+                    [0.5313, 1.0, 0.8], 1.0).ravel()
+    ux = np.where((X <= 0.5) & (Y > 0.5), 0.7276, 0.0).ravel()
+    uy = np.where((X > 0.5) & (Y <= 0.5), 0.7276, 0.0).ravel()
+    p = np.where((X > 0.5) & (Y > 0.5), 0.4, 1.0).ravel()
+    return Problem(2, n, n, 0.0, 1.0, 0.0, 1.0, 1.4, rho, ux, uy, p, name="lax_liu_%d" % n)
+
+
+def smooth_periodic(dim, nx, ny, seed, amp=0.1, gamma=1.4, modes=3):
+    """Smooth random periodic fields (a few Fourier modes of relative amplitude amp)."""
+    rng = np.random.default_rng(seed)
+    x = cell_centres(nx, 0.0, 1.0)
+    y = cell_centres(ny, 0.0, 1.0) if dim == 2 else np.array([0.5])
+    X, Y = np.meshgrid(x, y)
+
+    def field_(scale):
+        f = np.zeros_like(X)
+        for _ in range(modes):
+            kx, ky = rng.integers(1, 3), (rng.integers(0, 3) if dim == 2 else 0)
+            ph = rng.uniform(0, 2 * np.pi)
+            f += rng.uniform(-1, 1) * np.sin(2 * np.pi * (kx * X + ky * Y) + ph)
+        return scale * f / modes
+
+    rho = np.exp(field_(amp)).ravel()
+    p = np.exp(field_(amp)).ravel()
+    ux = (rng.uniform(-1, 1) + field_(amp)).ravel()
+    uy = ((rng.uniform(-1, 1) + field_(amp)) if dim == 2 else np.zeros_like(X)).ravel()
+    return Problem(dim, nx, ny if dim == 2 else 1, 0.0, 1.0, 0.0, 1.0, gamma, rho, ux, uy, p,
+                   bc=(PERIODIC,) * 4, name="smooth_periodic")
+
+
+@dataclass
+class TubeBatch:
+    lengths: np.ndarray   # cells per tube
+    gammas: np.ndarray
+    left: np.ndarray      # (n, 3) rho, u, p
+    right: np.ndarray
+
+    @property
+    def total_cells(self):
+        return int(self.lengths.sum())
+
+
+def tube_batch(n_tubes, seed, len_min=200, len_max=8000, ratio_max=1e5, mach_max=20.0):
+    """Independent 1D shock tubes: lengths log-uniform in [len_min, len_max]; rho_L, p_L
+    log-uniform in [0.1, 10]; density and pressure ratios log-uniform in [1, ratio_max];
+    sides swapped with probability 1/2; a velocity jump of Mach up to mach_max (with
+    respect to the left sound speed), split symmetrically or put on one side; gamma in
+    {1.4, 5/3}.  Each tube spans [0, 1] with the split at its middle."""
+    rng = np.random.default_rng(seed)
+    lengths = np.rint(np.exp(rng.uniform(np.log(len_min), np.log(len_max), n_tubes))).astype(np.int64)
+    gam = np.where(rng.integers(0, 2, n_tubes) == 0, 1.4, 5.0 / 3.0)
+    rl = np.exp(rng.uniform(np.log(0.1), np.log(10.0), n_tubes))
+    pl = np.exp(rng.uniform(np.log(0.1), np.log(10.0), n_tubes))
+    rr = rl / np.exp(rng.uniform(0.0, np.log(ratio_max), n_tubes))
+    pr = pl / np.exp(rng.uniform(0.0, np.log(ratio_max), n_tubes))
+    du = rng.uniform(0.0, mach_max, n_tubes) * np.sqrt(gam * pl / rl)
+    split = rng.integers(0, 3, n_tubes)  # 0 symmetric, 1 left moves, 2 right moves
+    ul = np.where(split == 0, 0.5 * du, np.where(split == 1, du, 0.0))
+    ur = np.where(split == 0, -0.5 * du, np.where(split == 2, -du, 0.0))
+    swap = rng.integers(0, 2, n_tubes) == 1
+    left = np.stack([np.where(swap, rr, rl), np.where(swap, -ur, ul), np.where(swap, pr, pl)], 1)
+    right = np.stack([np.where(swap, rl, rr), np.where(swap, -ul, ur), np.where(swap, pl, pr)], 1)
+    return TubeBatch(lengths, gam, left, right)
+
+
+def tube_batch_fields(batch: TubeBatch):
+    """Concatenated primitive fields of a tube batch (tube-major, x fastest)."""
+    rho, ux, p = [], [], []
+    for k in range(len(batch.lengths)):
+        n = int(batch.lengths[k])
+        x = cell_centres(n, 0.0, 1.0)
+        L = x < 0.5
+        rho.append(np.where(L, batch.left[k, 0], batch.right[k, 0]))
+        ux.append(np.where(L, batch.left[k, 1], batch.right[k, 1]))
+        p.append(np.where(L, batch.left[k, 2], batch.right[k, 2]))
+    return np.concatenate(rho), np.concatenate(ux), np.concatenate(p)
+
+
+def shocked_interface_2d(nx, ny, seed, gamma=1.4):
+    """Planar shock (Mach in [1.5, 3]) moving +x through light gas (rho 1, p 1) towards a
+    heavy-gas interface (Atwood number in [0.5, 0.9]) at x = 1 + 0.05 sin(2 pi m y),
+    m in {2..8}; domain [0, 4] x [0, 1]; left inflow at the post-shock state, right
+    transmissive, periodic in y.  The post-shock state is the Rankine-Hugoniot one."""
+    rng = np.random.default_rng(seed)
+    M = rng.uniform(1.5, 3.0)
+    A = rng.uniform(0.5, 0.9)
+    m = int(rng.integers(2, 9))
+    rho1, p1 = 1.0, 1.0
+    rho_h = (1.0 + A) / (1.0 - A)
+    g = gamma
+    c1 = np.sqrt(g * p1 / rho1)
+    p2 = p1 * (2.0 * g * M * M - (g - 1.0)) / (g + 1.0)
+    rho2 = rho1 * (g + 1.0) * M * M / ((g - 1.0) * M * M + 2.0)
+    u2 = M * c1 * (1.0 - rho1 / rho2)
+    x = cell_centres(nx, 0.0, 4.0)
+    y = cell_centres(ny, 0.0, 1.0)
+    X, Y = np.meshgrid(x, y)
+    xi = 1.0 + 0.05 * np.sin(2.0 * np.pi * m * Y)
+    post = X < 0.5
+    heavy = X >= xi
+    rho = np.where(post, rho2, np.where(heavy, rho_h, rho1)).ravel()
+    ux = np.where(post, u2, 0.0).ravel()
+    p = np.where(post, p2, p1).ravel()
+    inflow = np.zeros((4, 4))
+    inflow[0] = (rho2, u2, 0.0, p2)
+    rngs = np.zeros((4, 2), dtype=np.int64)
+    rngs[0] = (0, ny)
+    return Problem(2, nx, ny, 0.0, 4.0, 0.0, 1.0, gamma, rho, ux, np.zeros_like(ux), p,
+                   bc=(INFLOW, TRANSMISSIVE, PERIODIC, PERIODIC), inflow=inflow,
+                   inflow_range=rngs, name="shocked_interface_%dx%d_seed%d" % (nx, ny, seed))
+
+
+def jet_2d(n, seed, gamma=5.0 / 3.0, mach=80.0, density_ratio=10.0):
+    """Jet of Mach 80 and density 10 x ambient entering [0,1] x [-0.5,0.5] (n x n cells)
+    through a left inflow band |y| <= 0.05; ambient rho 1 at rest with p drawn uniform in
+    [0.1, 1]; jet temperature = r x ambient temperature with r log-uniform in [0.01, 1];
+    transmissive elsewhere."""
+    rng = np.random.default_rng(seed)
+    p_amb = rng.uniform(0.1, 1.0)
+    r = np.exp(rng.uniform(np.log(0.01), 0.0))
+    rho_amb = 1.0
+    T_amb = p_amb / rho_amb
+    rho_j = density_ratio * rho_amb
+    T_j = r * T_amb
+    p_j = rho_j * T_j
+    u_j = mach * np.sqrt(gamma * T_j)
+    N = n * n
+    inflow = np.zeros((4, 4))
+    inflow[0] = (rho_j, u_j, 0.0, p_j)
+    y = cell_centres(n, -0.5, 0.5)
+    band = np.nonzero(np.abs(y) <= 0.05)[0]
+    rngs = np.zeros((4, 2), dtype=np.int64)
+    rngs[0] = (band.min(), band.max() + 1)
+    return Problem(2, n, n, 0.0, 1.0, -0.5, 0.5, gamma, np.full(N, rho_amb), np.zeros(N),
+                   np.zeros(N), np.full(N, p_amb), bc=(INFLOW, TRANSMISSIVE, TRANSMISSIVE, TRANSMISSIVE),
+                   inflow=inflow, inflow_range=rngs, name="jet_%d_seed%d" % (n, seed))

@@ -1,0 +1,23 @@
+"""Helpers shared by the tests (problem -> oracle solver, error norms)."""
+import numpy as np
+
+import oracle as O
+
+
+def oracle_for(problem, *, tau, cfl, t_end=0.0, tol=1e-10, max_iter=16, fixed_iters=0, limiter=0):
+    s = O.make_solver(problem.dim, problem.nx, problem.ny, dx=problem.dx, dy=problem.dy,
+                      gamma=problem.gamma, tau=tau, cfl=cfl, t_end=t_end, bc=problem.bc,
+                      inflow=problem.inflow, inflow_range=problem.inflow_range, limiter=limiter,
+                      tol=tol, max_iter=max_iter, fixed_iters=fixed_iters)
+    s.set_primitive(problem.rho, problem.ux, problem.uy if problem.dim == 2 else None, problem.p)
+    return s
+
+
+def rel_l1(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).sum() / max(np.abs(np.asarray(b)).sum(), 1e-300))
+
+
+def hermite_coeffs_1d(f, c):
+    """Hermite moments a_k = sum_i f_i He_k(c_i), k = 0..3 (probabilists' Hermite)."""
+    He = [np.ones_like(c), c, c * c - 1.0, c ** 3 - 3.0 * c]
+    return np.array([np.dot(f, h) for h in He])

@@ -1,0 +1,175 @@
+"""Pins for the oracle's finite-volume PonD step (Sec. III.B) against what the physics
+and the paper fix: conservation by the finite-volume form, Galilean invariance of a
+uniform flow in any gauge, the closed-form Crank-Nicolson relaxation of Eqs.
+(FinalUpdateDUGKS), the BGK shear viscosity nu = tau T, the exact Riemann solution of
+the paper's shock tubes, and the symmetries of the problems."""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle.riemann import cell_averaged_profile
+from paper_2203_05477_gb300 import inputs as I
+from tests.common import oracle_for, rel_l1
+
+
+@pytest.mark.parametrize("dim,nx,ny,steps", [(1, 64, 1, 300), (2, 12, 10, 25)])
+def test_conservation_periodic(dim, nx, ny, steps):
+    pb = I.smooth_periodic(dim, nx, ny, seed=3, amp=0.15)
+    s = oracle_for(pb, tau=1e-4, cfl=0.3, tol=1e-12, max_iter=30)
+    before = [v.sum() for v in s.conserved()]
+    s.step(steps)
+    after = [v.sum() for v in s.conserved()]
+    st = s.stats()
+    assert st["nonphysical"] == 0
+    for k, (a, b) in enumerate(zip(before, after)):
+        if dim == 1 and k == 2:
+            continue
+        assert abs(b - a) <= 1e-12 * max(abs(a), before[0]), (k, a, b)
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+@pytest.mark.parametrize("mach", [0.0, 5.0, 80.0])
+def test_uniform_flow_any_gauge(dim, mach):
+    n = 8
+    g = 5.0 / 3.0
+    T = 0.7
+    u = mach * np.sqrt(g * T)
+    N = n * (n if dim == 2 else 1)
+    pb = I.Problem(dim, n, n if dim == 2 else 1, 0, 1, 0, 1, g, np.full(N, 1.3), np.full(N, u),
+                   np.full(N, 0.3 * u), np.full(N, 1.3 * T), bc=(I.PERIODIC,) * 4)
+    # lab-frame moments lose about 3 log10(Mach) digits (the M_3 terms scale as rho u^3)
+    tol = 1e-13 * max(1.0, mach) ** 3
+    s = oracle_for(pb, tau=1e-5, cfl=0.2, tol=tol, max_iter=60)
+    # a deliberately wrong face predictor: the corrector must find the uniform frame
+    xg, yg = s.face_gauges()
+    xg[:, 0] += 0.3 * np.sqrt(T)
+    xg[:, -1] *= 1.5
+    if yg is not None:
+        yg[:, -1] *= 0.6
+    s.set_face_gauges(xg, yg)
+    r0 = s.conserved()
+    s.step(10)
+    r1 = s.conserved()
+    for a, b in zip(r0, r1):
+        np.testing.assert_allclose(b, a, rtol=1e-12, atol=1e-12 * np.abs(r0[3]).max())
+    xg, yg = s.face_gauges()
+    np.testing.assert_allclose(xg[:, 0], u, rtol=1e-10, atol=1e-10)
+    np.testing.assert_allclose(xg[:, -1], T, rtol=1e-10)
+    assert s.stats()["nonconverged"] == 0
+
+
+def test_homogeneous_relaxation_is_crank_nicolson():
+    """Identical non-equilibrium cells on a periodic line: all fluxes cancel, so Eqs.
+    (FinalUpdateDUGKS) reduce to f <- a f + (1 - a) f^eq with a = (2 tau - dt)/(2 tau + dt)."""
+    n, g, tau = 6, 1.4, 3e-4
+    c, W, _ = O.lattice(1)
+    c = c[:, 0]
+    rho, u, T = 1.2, 0.4, 0.9
+    cv = 1.0 / (g - 1.0)
+    eps, eta, zeta = 0.05, -0.02, 0.01
+    He = [np.ones(4), c, c * c - 1, c ** 3 - 3 * c]
+    f = W * (rho + eps * He[2] / 2 + eta * He[3] / 6)
+    b0 = (cv - 0.5) * rho * T - T * eps / 2
+    gp = W * (b0 + zeta * He[2] / 2)
+    s = O.make_solver(1, n, dx=1.0 / n, gamma=g, tau=tau, cfl=0.3, bc=(1, 1, 0, 0), tol=1e-13, max_iter=40)
+    s.set_primitive(np.full(n, rho), np.full(n, u), None, np.full(n, rho * T))
+    s.set_state(np.tile(f, (n, 1)), np.tile(gp, (n, 1)), np.full((n, 1), u), np.full(n, T))
+    steps = 7
+    s.step(steps)
+    dt = s.stats()["dt"]
+    a = (2 * tau - dt) / (2 * tau + dt)
+    fr, gr, ur, Tr = s.regauged_state()
+    np.testing.assert_allclose(Tr, T, rtol=1e-12)
+    np.testing.assert_allclose(ur[:, 0], u, rtol=1e-12)
+    a2 = fr @ He[2]
+    a3 = fr @ He[3]
+    g2 = gr @ He[2]
+    np.testing.assert_allclose(a2, eps * a ** steps, rtol=1e-9)
+    np.testing.assert_allclose(a3, eta * a ** steps, rtol=1e-9)
+    np.testing.assert_allclose(g2, zeta * a ** steps, rtol=1e-9)
+
+
+def test_shear_wave_viscosity():
+    """A small transverse velocity wave u_y = A sin(2 pi x) decays at nu k^2 with the BGK
+    kinematic viscosity nu = tau T (Pr = 1, mu = tau p; Sec. II.B and III.A)."""
+    nx, ny, tau = 32, 2, 0.02
+    x = I.cell_centres(nx, 0, 1)
+    X, _ = np.meshgrid(x, I.cell_centres(ny, 0, 1))
+    N = nx * ny
+    pb = I.Problem(2, nx, ny, 0, 1, 0, 2.0 / nx * 1.0, 1.4, np.ones(N), np.zeros(N),
+                   (1e-3 * np.sin(2 * np.pi * X)).ravel(), np.ones(N), bc=(I.PERIODIC,) * 4)
+    s = oracle_for(pb, tau=tau, cfl=0.2, tol=1e-12, max_iter=30)
+    ts, amps = [], []
+    for _ in range(5):
+        s.step(40)
+        r, mx, my, E = s.conserved()
+        uy = (my / r).reshape(ny, nx)[0]
+        ts.append(s.stats()["t"])
+        amps.append(2 * np.mean(uy * np.sin(2 * np.pi * x)))
+    rate = -np.polyfit(ts, np.log(amps), 1)[0]
+    assert rate == pytest.approx(tau * 1.0 * (2 * np.pi) ** 2, rel=0.02)
+
+
+def _tube_error(name, n, tau=1e-5, cfl=0.2):
+    pb, t_end = I.paper_tube(name, n)
+    s = oracle_for(pb, tau=tau, cfl=cfl, t_end=t_end)
+    s.step(10 ** 6)
+    st = s.stats()
+    r, u, _, p = s.primitive()
+    x0, x1 = pb.x0, pb.x1
+    left, right, g, _, _, xs, _ = I.PAPER_TUBES[name]
+    re, ue, pe = cell_averaged_profile(left, right, g, np.linspace(x0, x1, n + 1), xs, st["t"])
+    return st, r, u, p, re, ue, pe, pb
+
+
+def test_sod_400_against_exact_solution():
+    pb = I.sod_400()
+    s = oracle_for(pb, tau=1e-5, cfl=0.5, t_end=0.2)
+    s.step(10 ** 6)
+    st = s.stats()
+    assert st["t"] == pytest.approx(0.2, abs=1e-14) and st["nonphysical"] == 0
+    r, u, _, p = s.primitive()
+    re, ue, pe = cell_averaged_profile((1, 0, 1), (0.125, 0, 0.1), 1.4, np.linspace(0, 1, 401), 0.5, 0.2)
+    assert rel_l1(r, re) < 5e-3 and rel_l1(p, pe) < 5e-3
+    # shock position (steepest density drop right of the contact) within 2 cells
+    x = I.cell_centres(400, 0, 1)
+    k_num = 300 + int(np.argmin(np.diff(r[300:])))
+    k_ex = 300 + int(np.argmin(np.diff(re[300:])))
+    assert abs(k_num - k_ex) <= 2, (x[k_num], x[k_ex])
+
+
+def test_sod_converges_under_refinement():
+    errs = []
+    for n in (100, 200, 400):
+        st, r, u, p, re, ue, pe, _ = _tube_error("sod_paper", n)
+        errs.append(rel_l1(r, re))
+    assert errs[0] > errs[1] > errs[2]
+
+
+@pytest.mark.parametrize("name,n,tol_rho,tol_p", [
+    ("lax", 300, 2.5e-2, 1e-2),
+    ("strong_shock", 400, 8e-2, 2e-2),
+])
+def test_paper_tubes_against_exact_solution(name, n, tol_rho, tol_p):
+    st, r, u, p, re, ue, pe, _ = _tube_error(name, n)
+    assert st["nonphysical"] == 0
+    assert rel_l1(r, re) < tol_rho and rel_l1(p, pe) < tol_p
+
+
+def test_lax_liu_symmetry_and_y_uniformity():
+    pb = I.lax_liu_2d(16)
+    s = oracle_for(pb, tau=1e-5, cfl=0.2)
+    s.step(8)
+    r = s.conserved()[0].reshape(16, 16)
+    np.testing.assert_allclose(r, r.T, rtol=1e-12)
+    # y-uniform data stays exactly y-uniform
+    tube, _ = I.paper_tube("sod_paper", 24)
+    ny = 4
+    N = 24 * ny
+    pb2 = I.Problem(2, 24, ny, 0, 1, 0, ny / 24, 1.4, np.tile(tube.rho, ny), np.tile(tube.ux, ny),
+                    np.zeros(N), np.tile(tube.p, ny), bc=(0, 0, 1, 1))
+    s2 = oracle_for(pb2, tau=1e-5, cfl=0.2)
+    s2.step(10)
+    for fld in s2.conserved():
+        fld = fld.reshape(ny, 24)
+        assert np.abs(fld - fld[0][None]).max() <= 1e-14 * max(np.abs(fld).max(), 1.0)
