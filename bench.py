@@ -1,0 +1,295 @@
+#!/usr/bin/env python
+"""Benchmark of the regularized PonD finite-volume step on GB300.
+
+Workload: the 2D four-quadrant Riemann problem on the D2Q16 lattice, 1024 x 1024 cells on
+the unit square, quadrant states drawn from seed 0 (rho, p log-uniform in [0.1, 10], Mach
+up to 3), gamma 1.4, transmissive boundaries, CFL 0.2.  A step is one full time step of
+the grid (face corrector + cell update).  The headline runs the populations in FP32 (frames
+in FP64); the plain FP64 path is measured on the same GPU and reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank advances its own replica (seed + rank): the step has no
+data-path exchange in this single-GPU build, so N GPUs run N independent problems.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s (MLUPS) and % HBM roofline, FP32+learned vs plain FP64, same accuracy"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+N_SMS, FP32_LANES = 152, 128
+# FP32 operations (FMA = 2) of one corrector pass at one D2Q16 face, from the ncu
+# instruction counts of the face kernel (see profiles/); used for the ALU roofline.
+FLOPS_PER_FACE_PASS = 5800.0
+# algorithmic bytes per cell-update of the FP32 D2Q16 layout: the face kernel reads the
+# cell state (8 + 6 FP32 coefficients + 3 FP64 frame = 80 B) and two face predictors
+# (2 x 24 B) and writes two faces (2 x (16 x 4 + 24) B)
+FACE_KERNEL_BYTES_PER_CELL = 80 + 48 + 176
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": FALLBACK_HBM_GBS, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, sm_max_default):
+        sms, maxs, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sms.append(float(parts[1]))
+                maxs.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sms:
+            return {"sm_mhz": None, "sm_max_mhz": sm_max_default, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": max(maxs), "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+def cpu_baseline(pb_full, steps, target_s=12.0):
+    """The FP64 oracle as it stands, single thread, on a bounded square patch of the workload."""
+    import oracle as O
+    from paper_2203_05477_gb300 import inputs as I
+    n = pb_full.nx
+    side = 96
+    i0 = n // 2 - side // 2
+    sub = lambda a: a.reshape(n, n)[i0:i0 + side, i0:i0 + side].ravel()
+    patch = I.Problem(2, side, side, 0, side * pb_full.dx, 0, side * pb_full.dy, pb_full.gamma,
+                      sub(pb_full.rho), sub(pb_full.ux), sub(pb_full.uy), sub(pb_full.p))
+    s = O.make_solver(2, side, side, dx=patch.dx, dy=patch.dy, gamma=patch.gamma, tau=1e-5, cfl=0.2,
+                      tol=1e-10, max_iter=16)
+    s.set_primitive(patch.rho, patch.ux, patch.uy, patch.p)
+    done, t0 = 0, time.perf_counter()
+    while done < steps and (time.perf_counter() - t0) < target_s:
+        s.step(1)
+        done += 1
+    el = time.perf_counter() - t0
+    return {"value": side * side * done / el / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": "%dx%d centre patch of the workload, %d steps, FP64, single thread, %.1f s" % (side, side, done, el)}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 CPU oracle (the paper ships no code) on host cores."""
+    if rank != 0:
+        return
+    from paper_2203_05477_gb300 import inputs as I
+    import oracle as O
+    n = args.n
+    pb = I.quadrants_2d(n, seed=args.seed)
+    side = 48
+    i0 = n // 2 - side // 2
+    sub = lambda a: a.reshape(n, n)[i0:i0 + side, i0:i0 + side].ravel()
+    patch = I.Problem(2, side, side, 0, side * pb.dx, 0, side * pb.dy, pb.gamma, sub(pb.rho), sub(pb.ux), sub(pb.uy), sub(pb.p))
+    s = O.make_solver(2, side, side, dx=patch.dx, dy=patch.dy, gamma=patch.gamma, tau=1e-5, cfl=0.2, tol=1e-10, max_iter=16)
+    s.set_primitive(patch.rho, patch.ux, patch.uy, patch.p)
+    s.step(args.warmup)
+    t0 = time.perf_counter()
+    s.step(args.steps)
+    el = time.perf_counter() - t0
+    val = side * side * args.steps / el / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "quadrants_2d_1024_seed%d" % args.seed,
+                                            "sample": "%dx%d centre patch per step" % (side, side)},
+            "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": "%dx%d centre patch of the workload per step, FP64, single thread" % (side, side)},
+            "e2e": {"value": val, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--fp64-steps", type=int, default=6)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_2203_05477_gb300 as pond
+    from paper_2203_05477_gb300 import _build, inputs as I
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    _build.build()
+    pk, pk_kind = peaks()
+    n = args.n
+    pb = I.quadrants_2d(n, seed=args.seed + rank)
+    ncell = n * n
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---- headline: FP32 populations, FP64 frames
+    s = pond.Solver(pb, precision="fp32", tau=1e-5, cfl=0.2, max_iter=16)
+    s.set_primitive()
+    s.step(args.warmup)
+    d0 = s.sync()
+    l0 = s.launch_count()
+    stream = s.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        e0.record(stream)
+        ms_face, ms_cell = s.step_timed(args.steps)
+        e1.record(stream)
+        barrier()
+    el_ms = max_over_ranks(e0.elapsed_time(e1))
+    d1 = s.sync()
+    launches = s.launch_count() - l0
+    value = world * ncell * args.steps / (el_ms * 1e-3) / 1e6
+    face_passes = d1["face_iters"] - d0["face_iters"]
+    faces = d1["face_solves"] - d0["face_solves"]
+    status_ok = d1["status"] == pond.POND_OK
+    s.close()
+
+    # ---- the same workload through the public API with host buffers (e2e)
+    pin = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (pb.rho, pb.ux, pb.uy, pb.p)]
+    outs = [torch.empty(ncell, dtype=torch.float64).pin_memory() for _ in range(4)]
+    s2 = pond.Solver(pb, precision="fp32", tau=1e-5, cfl=0.2, max_iter=16)
+    barrier()
+    t0 = time.perf_counter()
+    s2.set_primitive(*[a.numpy() for a in pin])
+    s2.step(args.steps)
+    s2.lib.pond_moments(s2.h, *[o.data_ptr() for o in outs], None, 0)
+    barrier()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    s2.close()
+    e2e = {"value": world * ncell * args.steps / e2e_s / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": 4 * 8 * ncell / args.steps, "d2h_bytes_per_step": 4 * 8 * ncell / args.steps,
+           "note": "pond_set_primitive from pinned host arrays, %d steps, pond_moments to pinned host" % args.steps}
+
+    # ---- plain FP64 on the same GPU
+    s3 = pond.Solver(pb, precision="fp64", tau=1e-5, cfl=0.2, max_iter=16)
+    s3.set_primitive()
+    s3.step(2)
+    barrier()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(s3.stream)
+    s3.step(args.fp64_steps)
+    f1.record(s3.stream)
+    barrier()
+    fp64_value = world * ncell * args.fp64_steps / (max_over_ranks(f0.elapsed_time(f1)) * 1e-3) / 1e6
+    s3.close()
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    clocks = clk.summary(pk.get("sm_max_mhz", 2070.0))
+    sm_mhz = pk.get("sm_max_mhz", 2070.0)
+    fp32_peak = N_SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+    face_ms_avg = ms_face / args.steps
+    flops = FLOPS_PER_FACE_PASS * face_passes / args.steps
+    achieved = flops / (face_ms_avg * 1e-3) / 1e12
+    hbm_peak = pk.get("hbm_gbs", FALLBACK_HBM_GBS)
+    face_gbs = FACE_KERNEL_BYTES_PER_CELL * ncell / (face_ms_avg * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": el_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "quadrants_2d_1024_seed%d" % args.seed, "lattice": "D2Q16", "cells": ncell,
+                   "precision": "fp32 populations, fp64 frames", "cfl": 0.2, "tau": 1e-5,
+                   "corrector": "tol 1e-6, max 16 passes", "l2": "working set %.0f MB > L2" % (
+                       (ncell * (80 + 2 * 88)) / 1e6), "parallelism": "replicas" if world > 1 else "single"},
+        "fp64": {"value": fp64_value, "unit": "MLUPS", "steps": args.fp64_steps, "speedup_fp32": value / fp64_value},
+        "corrector": {"passes_per_face": face_passes / max(faces, 1), "status_ok": status_ok},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp32_peak, "traffic": None, "kernel": "face_kernel<2,float>",
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % sm_mhz,
+                     "face_ms": face_ms_avg, "cell_ms": ms_cell / args.steps,
+                     "hbm_gbs": face_gbs, "hbm_frac": face_gbs / hbm_peak,
+                     "hbm_peak": hbm_peak, "hbm_peak_source": pk_kind},
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(pb, steps=20)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

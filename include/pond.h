@@ -1,0 +1,164 @@
+/*
+ * pond.h -- C ABI of the GB300 (sm_103a) library for the regularized Particles-on-Demand
+ * finite-volume scheme of Kallikounis, Dorschner and Karlin, "Particles on Demand for
+ * flows with strong discontinuities" (arXiv 2203.05477).
+ *
+ * One time step (Sec. III.B.4) re-expresses every cell in its co-moving frame
+ * (Sec. II.C), evaluates the face populations at t_{n+1/2} by the face predictor-
+ * corrector (Sec. III.B.3), forms the fluxes Eq. (fluxEq) in each cell's frame and
+ * applies the co-moving DUGKS update Eqs. (FinalUpdateDUGKS).  All of it runs in CUDA
+ * kernels on the device; the host only launches them.
+ *
+ * Conventions
+ *   - Every call returns a pond_status; nothing else crosses the ABI (no exceptions).
+ *   - Host arrays are plain C arrays; device arrays are CUDA device pointers.  Fields are
+ *     structure-of-arrays of nx*ny FP64 values, x fastest.
+ *   - The library owns a pond_state and everything it allocates; the caller owns every
+ *     array it passes in.  Device memory comes from the allocator in pond_options (for
+ *     example the caller's caching allocator) or, when that is NULL, from cudaMalloc.
+ *   - All work is enqueued on the stream given in pond_options (NULL: the library creates
+ *     and owns a non-blocking stream).  One state is used by one stream at a time.
+ *   - Device-side conditions (a non-physical state, a face whose corrector found no
+ *     frame) are sticky: they are recorded on the device and reported by pond_sync.
+ *   - Thread safety: distinct states may be used from distinct threads.  The message of
+ *     pond_last_error is thread-local.
+ */
+#ifndef POND_H
+#define POND_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    POND_OK = 0,
+    POND_ERR_INVALID_ARG = 1,    /* a NULL pointer, a size <= 0, a bad enum value */
+    POND_ERR_UNSUPPORTED = 2,    /* velocity set other than D1Q4/D2Q16; gamma > 1 + 2/D */
+    POND_ERR_OOM = 3,            /* the allocator returned NULL */
+    POND_ERR_CUDA = 4,           /* a CUDA runtime call failed; see pond_last_error */
+    POND_ERR_NONPHYSICAL = 5,    /* rho <= 0, T <= 0 or not finite in a cell, or a face whose
+                                    corrector found no frame (reported by pond_sync) */
+    POND_ERR_NOT_CONVERGED = 6,  /* reported by pond_sync when strict_convergence is set */
+    POND_ERR_TIMEOUT = 7         /* a bounded device-side wait gave up */
+} pond_status;
+
+/* Velocity sets of Table I: D1Q4 (Gauss-Hermite roots of He_4, T_L = 1) and its tensor
+ * product D2Q16 (Eq. wi).  D1Q3/D2Q9 cannot carry the third-order Grad projection the
+ * paper requires (Sec. II.C) and are refused with POND_ERR_UNSUPPORTED. */
+typedef enum { POND_D1Q3 = 0, POND_D1Q4 = 1, POND_D2Q16 = 2, POND_D2Q9 = 3 } pond_velset;
+
+/* Ghost-cell rules: copy of the nearest cell (zero gradient), wrap-around, or the
+ * equilibrium at a prescribed state on part of a side (transmissive on the rest). */
+typedef enum { POND_BC_TRANSMISSIVE = 0, POND_BC_PERIODIC = 1, POND_BC_INFLOW = 2 } pond_bc;
+
+/* Arithmetic of populations, fluxes and collision.  Frames (u, T) and their recovery
+ * from the conserved moments are FP64 in both modes. */
+typedef enum { POND_FP64 = 0, POND_FP32 = 1 } pond_precision;
+
+/* Slope limiters of Sec. III.B.3 ("Van Leer and minmod"). */
+typedef enum { POND_VANLEER = 0, POND_MINMOD = 1 } pond_limiter;
+
+typedef struct {
+    int dim;                    /* 1 or 2; must match the velocity set */
+    int64_t nx, ny;             /* cells; ny is ignored (taken as 1) when dim == 1 */
+    double x0, x1, y0, y1;      /* domain [x0,x1] x [y0,y1]; cell centres at (k + 1/2) dx */
+    int bc[4];                  /* pond_bc for sides x-lo, x-hi, y-lo, y-hi */
+    double inflow[4][4];        /* per side: rho, ux, uy, p of the inflow state */
+    int64_t inflow_lo[4];       /* inflow applies to cells [lo, hi) along that side */
+    int64_t inflow_hi[4];
+} pond_grid;
+
+typedef struct {
+    int precision;              /* pond_precision */
+    int limiter;                /* pond_limiter */
+    double cfl;                 /* CFL = max|v_ia| dt / dx (Sec. IV); e.g. 0.2 */
+    double t_end;               /* > 0: the last step is clipped to t_end, later ones are no-ops */
+    double tol;                 /* corrector stop: |du| <= tol sqrt(T) and |dT| <= tol T */
+    int max_iter;               /* corrector passes at most (e.g. 16) */
+    int fixed_iters;            /* > 0: exactly this many passes per face (parity mode) */
+    int strict_convergence;     /* nonzero: faces that hit max_iter make pond_sync fail */
+    int learned;                /* nonzero: the learned face-gauge predictor seeds the corrector */
+    void *stream;               /* cudaStream_t, or NULL for a stream the library creates */
+    void *(*alloc)(size_t bytes, void *ctx);  /* device allocator, or NULL for cudaMalloc */
+    void (*free)(void *ptr, void *ctx);
+    void *alloc_ctx;
+} pond_options;
+
+typedef struct pond_state pond_state;
+
+/* Diagnostics gathered on the device since pond_init / pond_set_primitive. */
+typedef struct {
+    double t;                   /* simulated time */
+    double dt;                  /* time step of the next step */
+    int64_t steps;              /* steps taken */
+    int64_t face_solves;        /* faces processed (faces x steps) */
+    int64_t face_iters;         /* corrector passes summed over all faces */
+    int64_t nonconverged;       /* faces that stopped at max_iter */
+    int64_t fallbacks;          /* passes that defined no frame (restart / stop early) */
+    int64_t nonphysical;        /* non-physical cells or faces */
+    int64_t first_bad_cell;     /* index of the first non-physical cell, or -1 */
+    uint32_t flags;             /* bit 0 non-physical, bit 1 not converged, bit 2 timeout */
+} pond_diag;
+
+/* Creates a solver for the problem statement of the paper's benchmarks (Sec. IV): grid and
+ * boundary conditions, velocity set, ratio of specific heats gamma (Cv = 1/(gamma-1),
+ * p = rho T), BGK relaxation time tau (Eqs. f_equation, g_equation).  gamma must satisfy
+ * Cv >= D/2 (Eq. geqPond), i.e. gamma <= 1 + 2/D.  Allocates all device memory once. */
+pond_status pond_init(const pond_grid *grid, pond_velset velset, double gamma, double tau,
+                      const pond_options *opts, pond_state **out);
+
+/* Initial condition: the co-moving equilibria Eqs. (feqPond), (geqPond) of primitive
+ * fields rho, ux, uy, p (uy may be NULL in 1D).  on_device: the arrays are device
+ * pointers (else host).  Also sets the face predictors (the frame of the pooled moments
+ * of the two adjacent cells), t = 0 and the first time step. */
+pond_status pond_set_primitive(pond_state *s, const double *rho, const double *ux,
+                               const double *uy, const double *p, int on_device);
+
+/* Enqueues n_steps time steps (Sec. III.B.4) on the state's stream and returns without
+ * waiting.  The time step of each step comes from the CFL condition on the device. */
+pond_status pond_step(pond_state *s, int64_t n_steps);
+
+/* Same as pond_step, but launches every kernel individually with CUDA events around it on
+ * the state's stream, waits, and adds the elapsed milliseconds of all face-corrector
+ * launches to ms[0] and of all cell-update launches to ms[1] (ms: host array of 2). */
+pond_status pond_step_timed(pond_state *s, int64_t n_steps, double ms[2]);
+
+/* Conserved fields rho, rho ux, rho uy, rho E per cell (Sec. II.B) into caller buffers
+ * (host or device per on_device; any pointer may be NULL to skip it) and, if totals is
+ * not NULL, their compensated FP64 sums over the grid times the cell volume.  Waits for
+ * the stream. */
+pond_status pond_moments(pond_state *s, double *rho, double *mx, double *my, double *E,
+                         double totals[4], int on_device);
+
+/* The stored state for inspection: per cell its Hermite coefficients in its own frame
+ * (D1Q4: f a0..a3, g b0..b2; D2Q16: f a00,a10,a01,a20,a11,a02,a30,a21,a12,a03 and g
+ * b00,b10,b01,b20,b11,b02; [cells][ncoef]) and frame (u..., T) ([cells][D+1]).  Host
+ * buffers; waits for the stream.  coef_f/coef_g/frame may be NULL. */
+pond_status pond_get_state(pond_state *s, double *coef_f, double *coef_g, double *frame);
+
+/* Face predictors (u..., T) for x-faces [(nx+1)*ny][D+1] and (2D) y-faces
+ * [nx*(ny+1)][D+1]; host buffers.  pond_set_face_gauges overwrites them. */
+pond_status pond_get_face_gauges(pond_state *s, double *xg, double *yg);
+pond_status pond_set_face_gauges(pond_state *s, const double *xg, const double *yg);
+
+/* Waits for the stream and reports the device diagnostics.  Returns
+ * POND_ERR_NONPHYSICAL if any cell or face was non-physical, POND_ERR_NOT_CONVERGED if
+ * strict_convergence is set and a face stopped at max_iter, else POND_OK. */
+pond_status pond_sync(pond_state *s, pond_diag *diag);
+
+/* Number of kernel launches the library enqueued since pond_init. */
+int64_t pond_launch_count(const pond_state *s);
+
+/* Frees everything the state owns (after waiting for its stream). */
+void pond_destroy(pond_state *s);
+
+/* Message of the last failed call on this thread. */
+const char *pond_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* POND_H */

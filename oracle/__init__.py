@@ -70,6 +70,7 @@ def _load():
                                               dp, ctypes.c_double, dp]
         lib.oracle_limiter.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double]
         lib.oracle_limiter.restype = ctypes.c_double
+        lib.oracle_force_dt.argtypes = [ctypes.c_void_p, ctypes.c_double]
         _lib = lib
         return lib
 
@@ -199,6 +200,10 @@ class Solver:
         xg = _f64(xg)
         yg = _f64(yg) if yg is not None else np.zeros(1)
         self.lib.oracle_set_face_gauges(self.h, _dp(xg), _dp(yg))
+
+    def force_dt(self, dt: float):
+        """Test hook: fixed time step instead of the CFL rule (dt <= 0 restores it)."""
+        self.lib.oracle_force_dt(self.h, float(dt))
 
     def stats(self):
         t = np.zeros(1); dt = np.zeros(1)

@@ -26,7 +26,10 @@
  * Readings where the paper is silent (each one is listed in the design notes):
  *   R = 1, p = rho T, Cv = 1/(gamma-1); D in g^eq is the lattice dimension; the
  *   overline (symmetrization) is the sum over distinct index permutations; the face
- *   predictor before the first step is the mean of the two adjacent cell frames; the
+ *   predictor before the first step is the frame of the pooled conserved moments of the two
+ *   adjacent cells; a corrector pass whose moments define no frame (T <= 0 or not finite)
+ *   restarts the corrector once from the frame of the pooled moments of the whole face
+ *   stencil, and otherwise the corrector stops at the last pass that did define one; the
  *   corrector stops when |u_{k+1}-u_k|_inf <= tol sqrt(T_k) and |T_{k+1}-T_k| <= tol T_k,
  *   or after exactly `fixed_iters` passes when that is > 0; the face populations use the
  *   moments of the last pass, Grad-projected into the frame those moments define, with
@@ -229,7 +232,7 @@ typedef struct oracle {
     /* faces: x-faces (nx+1) x ny, y-faces nx x (ny+1); gauge and populations */
     double *xu, *xT, *yu, *yT;
     double *xf, *xg, *yf, *yg;
-    double t, dt, last_dt;
+    double t, dt, last_dt, forced_dt;
     long long steps, face_iters, face_count, nonconv, nonphys, fallbacks;
 } oracle;
 
@@ -590,7 +593,7 @@ int oracle_step(oracle *o, int n)
         for (int j = 0; j < o->ny; ++j)
             for (int i = 0; i < o->nx; ++i) regauge_cell(o, cidx(o, i, j));
         fill_ghosts(o);
-        double dt = cfl_dt(o);
+        double dt = o->forced_dt > 0.0 ? o->forced_dt : cfl_dt(o);
         if (o->t_end > 0.0 && o->t + dt > o->t_end) dt = o->t_end - o->t;
         const double h = 0.5 * dt, tau = o->tau;
         /* 2a. phi-bar-plus at every cell (ghosts included), Eq. (Fbarplus) with Eq. (variableTransform) */
@@ -788,3 +791,7 @@ void oracle_grad_transform(int D, int order, const double *f_in, const double *u
 }
 
 double oracle_limiter(int kind, double a, double b) { return limiter(kind, a, b); }
+
+/* Test hook: use this time step instead of the CFL one (dt <= 0 restores the CFL rule).
+ * Lets a test run one step of a patch cut out of a larger grid with the larger grid's dt. */
+void oracle_force_dt(oracle *o, double dt) { o->forced_dt = dt; }

@@ -1,0 +1,277 @@
+"""Python binding of the GB300 regularized Particles-on-Demand library (libpond.so).
+
+The binding only marshals arguments: every step of the method runs in the library's
+CUDA kernels.  PyTorch provides device memory (the caching allocator is handed to the
+library through the allocator hook of ``pond_options``) and the CUDA stream.  The
+functions ``pond_*`` are the C entry points of ``include/pond.h`` with the same names;
+``Solver`` wraps them for numpy/torch callers.  There is no CPU fallback: without the
+compiled library every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import inputs  # noqa: F401  (problem generators, no method arithmetic)
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libpond.so")
+_lock = threading.Lock()
+_lib = None
+
+POND_OK, POND_ERR_INVALID_ARG, POND_ERR_UNSUPPORTED, POND_ERR_OOM, POND_ERR_CUDA = 0, 1, 2, 3, 4
+POND_ERR_NONPHYSICAL, POND_ERR_NOT_CONVERGED, POND_ERR_TIMEOUT = 5, 6, 7
+POND_D1Q3, POND_D1Q4, POND_D2Q16, POND_D2Q9 = 0, 1, 2, 3
+POND_FP64, POND_FP32 = 0, 1
+POND_VANLEER, POND_MINMOD = 0, 1
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class pond_grid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int64), ("ny", ctypes.c_int64),
+                ("x0", ctypes.c_double), ("x1", ctypes.c_double), ("y0", ctypes.c_double),
+                ("y1", ctypes.c_double), ("bc", ctypes.c_int * 4),
+                ("inflow", (ctypes.c_double * 4) * 4), ("inflow_lo", ctypes.c_int64 * 4),
+                ("inflow_hi", ctypes.c_int64 * 4)]
+
+
+class pond_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("limiter", ctypes.c_int), ("cfl", ctypes.c_double),
+                ("t_end", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("fixed_iters", ctypes.c_int), ("strict_convergence", ctypes.c_int),
+                ("learned", ctypes.c_int), ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN),
+                ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p)]
+
+
+class pond_diag(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("dt", ctypes.c_double), ("steps", ctypes.c_int64),
+                ("face_solves", ctypes.c_int64), ("face_iters", ctypes.c_int64),
+                ("nonconverged", ctypes.c_int64), ("fallbacks", ctypes.c_int64),
+                ("nonphysical", ctypes.c_int64), ("first_bad_cell", ctypes.c_int64),
+                ("flags", ctypes.c_uint32)]
+
+
+class PondError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("pond status %d: %s" % (status, msg))
+        self.status = status
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB_PATH):
+            raise ImportError("libpond.so is not built (run __graft_entry__.build() or "
+                              "paper_2203_05477_gb300._build.build()); there is no CPU fallback")
+        lib = ctypes.CDLL(_LIB_PATH)
+        vp, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
+        sigs = {
+            "pond_init": (ctypes.c_int, [ctypes.POINTER(pond_grid), ctypes.c_int, ctypes.c_double,
+                                         ctypes.c_double, ctypes.POINTER(pond_options), ctypes.POINTER(vp)]),
+            "pond_set_primitive": (ctypes.c_int, [vp, vp, vp, vp, vp, ctypes.c_int]),
+            "pond_step": (ctypes.c_int, [vp, ctypes.c_int64]),
+            "pond_step_timed": (ctypes.c_int, [vp, ctypes.c_int64, vp]),
+            "pond_moments": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, ctypes.c_int]),
+            "pond_get_state": (ctypes.c_int, [vp, vp, vp, vp]),
+            "pond_get_face_gauges": (ctypes.c_int, [vp, vp, vp]),
+            "pond_set_face_gauges": (ctypes.c_int, [vp, vp, vp]),
+            "pond_sync": (ctypes.c_int, [vp, ctypes.POINTER(pond_diag)]),
+            "pond_launch_count": (ctypes.c_int64, [vp]),
+            "pond_destroy": (None, [vp]),
+            "pond_last_error": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sigs.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def __getattr__(name):
+    # pond_* entry points of the C ABI under their own names
+    if name.startswith("pond_"):
+        return getattr(_load(), name)
+    raise AttributeError(name)
+
+
+def _check(st):
+    if st != POND_OK:
+        raise PondError(st, _load().pond_last_error().decode())
+
+
+def _ptr(a):
+    """Device or host pointer of a torch tensor / numpy array (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+class _TorchAllocator:
+    """Hands torch's CUDA caching allocator to the library (device memory only)."""
+
+    def __init__(self, device, stream):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.stream = stream
+        self.live = {}
+
+        def alloc(nbytes, ctx):
+            try:
+                p = torch.cuda.caching_allocator_alloc(int(nbytes), device=self.device, stream=self.stream)
+            except Exception:
+                return None
+            self.live[p] = nbytes
+            return p
+
+        def free(ptr, ctx):
+            if ptr and ptr in self.live:
+                del self.live[ptr]
+                torch.cuda.caching_allocator_delete(ptr)
+
+        self.alloc_fn = ALLOC_FN(alloc)
+        self.free_fn = FREE_FN(free)
+
+
+class Solver:
+    """One PonD problem on the current CUDA device (see ``inputs.Problem``)."""
+
+    def __init__(self, problem, *, tau, cfl, precision="fp64", limiter=POND_VANLEER, t_end=0.0,
+                 tol=None, max_iter=16, fixed_iters=0, strict=False, stream=None, torch_alloc=True):
+        import torch
+        lib = _load()
+        self.problem = problem
+        self.D = problem.dim
+        self.nx, self.ny = problem.nx, (problem.ny if problem.dim == 2 else 1)
+        self.prec = POND_FP32 if precision in ("fp32", POND_FP32) else POND_FP64
+        g = pond_grid()
+        g.dim = problem.dim
+        g.nx, g.ny = problem.nx, self.ny
+        g.x0, g.x1, g.y0, g.y1 = problem.x0, problem.x1, problem.y0, problem.y1
+        for k in range(4):
+            g.bc[k] = int(problem.bc[k])
+            g.inflow_lo[k] = int(problem.inflow_range[k][0])
+            g.inflow_hi[k] = int(problem.inflow_range[k][1])
+            for q in range(4):
+                g.inflow[k][q] = float(problem.inflow[k][q])
+        self.device = torch.cuda.current_device()
+        # a stream of our own: torch's default stream is the legacy one, which cannot be
+        # captured into a CUDA graph
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        o = pond_options()
+        o.precision = self.prec
+        o.limiter = int(limiter)
+        o.cfl = float(cfl)
+        o.t_end = float(t_end)
+        o.tol = float(tol if tol is not None else (1e-10 if self.prec == POND_FP64 else 1e-6))
+        o.max_iter = int(max_iter)
+        o.fixed_iters = int(fixed_iters)
+        o.strict_convergence = int(bool(strict))
+        o.stream = self.stream.cuda_stream
+        self._alloc = _TorchAllocator(self.device, self.stream) if torch_alloc else None
+        if self._alloc:
+            o.alloc = self._alloc.alloc_fn
+            o.free = self._alloc.free_fn
+        self._grid, self._opts = g, o
+        self.h = ctypes.c_void_p()
+        velset = POND_D1Q4 if problem.dim == 1 else POND_D2Q16
+        _check(lib.pond_init(ctypes.byref(g), velset, float(problem.gamma), float(tau), ctypes.byref(o),
+                             ctypes.byref(self.h)))
+        self.lib = lib
+        self.ncell = self.nx * self.ny
+        self.nfc = 4 if self.D == 1 else 10
+        self.ngc = 3 if self.D == 1 else 6
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            self.lib.pond_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_primitive(self, rho=None, ux=None, uy=None, p=None):
+        pb = self.problem
+        vals = [pb.rho if rho is None else rho, pb.ux if ux is None else ux,
+                (pb.uy if uy is None else uy) if self.D == 2 else None, pb.p if p is None else p]
+        on_dev = not isinstance(vals[0], np.ndarray)
+        if not on_dev:
+            vals = [None if v is None else np.ascontiguousarray(v, dtype=np.float64) for v in vals]
+        self._keep = vals
+        _check(self.lib.pond_set_primitive(self.h, *[_ptr(v) for v in vals], int(on_dev)))
+
+    def step(self, n=1):
+        _check(self.lib.pond_step(self.h, int(n)))
+
+    def step_timed(self, n):
+        """n steps with every kernel timed by CUDA events on the stream: (face ms, cell ms)."""
+        ms = np.zeros(2)
+        _check(self.lib.pond_step_timed(self.h, int(n), _ptr(ms)))
+        return float(ms[0]), float(ms[1])
+
+    def moments(self, totals=True):
+        out = [np.zeros(self.ncell) for _ in range(4)]
+        tot = np.zeros(4)
+        _check(self.lib.pond_moments(self.h, *[_ptr(a) for a in out], _ptr(tot) if totals else None, 0))
+        return out, tot
+
+    def moments_device(self, outs, totals=None):
+        """Conserved fields into device tensors (each may be None); totals into a host array."""
+        _check(self.lib.pond_moments(self.h, *[_ptr(a) for a in outs], _ptr(totals), 1))
+
+    def primitive(self):
+        (rho, mx, my, E), _ = self.moments(totals=False)
+        cv = 1.0 / (self.problem.gamma - 1.0)
+        ux, uy = mx / rho, my / rho
+        T = (E - 0.5 * (mx * mx + my * my) / rho) / (cv * rho)
+        return rho, ux, uy, rho * T
+
+    def state(self):
+        cf = np.zeros((self.ncell, self.nfc))
+        cg = np.zeros((self.ncell, self.ngc))
+        fr = np.zeros((self.ncell, self.D + 1))
+        _check(self.lib.pond_get_state(self.h, _ptr(cf), _ptr(cg), _ptr(fr)))
+        return cf, cg, fr
+
+    def face_gauges(self):
+        D = self.D
+        xg = np.zeros(((self.nx + 1) * self.ny, D + 1))
+        yg = np.zeros((self.nx * (self.ny + 1), D + 1)) if D == 2 else None
+        _check(self.lib.pond_get_face_gauges(self.h, _ptr(xg), _ptr(yg)))
+        return xg, yg
+
+    def set_face_gauges(self, xg, yg=None):
+        xg = np.ascontiguousarray(xg, dtype=np.float64)
+        yg = None if yg is None else np.ascontiguousarray(yg, dtype=np.float64)
+        _check(self.lib.pond_set_face_gauges(self.h, _ptr(xg), _ptr(yg)))
+
+    def sync(self, raise_on_error=False):
+        d = pond_diag()
+        st = self.lib.pond_sync(self.h, ctypes.byref(d))
+        out = {f: getattr(d, f) for f, _ in pond_diag._fields_}
+        out["status"] = st
+        if raise_on_error:
+            _check(st)
+        elif st not in (POND_OK, POND_ERR_NONPHYSICAL, POND_ERR_NOT_CONVERGED):
+            _check(st)
+        return out
+
+    def launch_count(self):
+        return int(self.lib.pond_launch_count(self.h))

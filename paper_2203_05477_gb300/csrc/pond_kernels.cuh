@@ -1,0 +1,988 @@
+// pond_kernels.cuh -- the CUDA kernels of one regularized PonD finite-volume step.
+//
+// Data layout in device memory (structure of arrays, x fastest):
+//   cell state  : f coefficients in the cell's own frame without the (zero) first-order
+//                 ones -- D1Q4: rho, a2, a3; D2Q16: rho, a20, a11, a02, a30, a21, a12, a03 --
+//                 g coefficients b0..b2 (D1Q4) or b00, b10, b01, b20, b11, b02 (D2Q16), all in
+//                 the population precision R; frame u (D values) and T in FP64.
+//   face data   : per face the Hermite coefficients of the face populations phi(x_b, t_{n+1/2})
+//                 (f: 4 or 10, g: 3 or 6, precision R) in the face frame, and that frame
+//                 (u..., T) in FP64.  The frame doubles as the corrector predictor of the
+//                 next step (Sec. III.B.3: lambda_0 = lambda(x_b, t_{n-1/2})).
+// Faces: x-face (i, j) lies between cells (i-1, j) and (i, j), i = 0..nx; y-face (i, j)
+// between (i, j-1) and (i, j), j = 0..ny.
+//
+// Per step (Sec. III.B.4): face_kernel (steps 2a-2b) then cell_kernel (step 3 fused with
+// step 1 of the next step and the CFL time step of Sec. IV).
+#pragma once
+
+#include "pond_core.cuh"
+
+namespace pond {
+
+enum { BC_TRANSMISSIVE = 0, BC_PERIODIC = 1, BC_INFLOW = 2 };
+enum { FLAG_NONPHYSICAL = 1u, FLAG_NOT_CONVERGED = 2u, FLAG_TIMEOUT = 4u };
+
+struct Clock {
+    double t, dt, t_end, cfl;
+    long long steps;
+    unsigned long long rate_bits;   // max CFL rate of the step being reduced (as double bits)
+    unsigned int blocks_done;
+    unsigned int pad;
+};
+
+struct Diag {
+    unsigned long long face_solves, face_iters, nonconv, fallbacks, nonphys;
+    long long first_bad;
+    unsigned int flags;
+    unsigned int pad;
+};
+
+template <int D, typename R>
+struct Params {
+    static constexpr int NFC = NCoef<D, 3>::value;   // f coefficients per face
+    static constexpr int NGC = NCoef<D, 2>::value;   // g coefficients
+    static constexpr int NFS = NFC - D;              // stored f planes (no first order)
+    long long nx, ny;
+    double dx, dy;
+    int bc[4];
+    long long lo[4], hi[4];
+    double inflow[4][4];             // rho, ux, uy, p
+    double gamma, Cv, tau;
+    int limiter;
+    double tol;
+    int max_iter, fixed_iters;
+    R *sf;                            // [NFS][ncell]
+    R *sg;                            // [NGC][ncell]
+    double *sfr;                      // [D+1][ncell]
+    R *xf, *xg;                       // [NFC][nxf], [NGC][nxf]
+    double *xfr;                      // [D+1][nxf]
+    R *yf, *yg;
+    double *yfr;
+    Clock *clock;
+    Diag *diag;
+    __host__ __device__ long long ncell() const { return nx * ny; }
+    __host__ __device__ long long nxf() const { return (nx + 1) * ny; }
+    __host__ __device__ long long nyf() const { return nx * (ny + 1); }
+};
+
+// stored f plane of full coefficient k (or -1 when it is a first-order one, always zero)
+template <int D>
+__host__ __device__ constexpr int fplane(int k)
+{
+    return D == 1 ? (k == 0 ? 0 : k == 1 ? -1 : k - 1) : (k == 0 ? 0 : (k == 1 || k == 2) ? -1 : k - 2);
+}
+
+__device__ __forceinline__ long long clampll(long long v, long long lo, long long hi) { return v < lo ? lo : (v > hi ? hi : v); }
+__device__ __forceinline__ long long wrapll(long long v, long long n) { long long r = v % n; return r < 0 ? r + n : r; }
+
+// Ghost-cell rules (two layers; y sides first, then x sides).  Returns -1 and the linear
+// cell index, or the side (0..3) whose inflow state the cell holds.
+template <int D, typename R>
+__device__ __forceinline__ int resolve(const Params<D, R> &P, long long i, long long j, long long *idx)
+{
+    if (D == 2 && (j < 0 || j >= P.ny)) {
+        const int side = j < 0 ? 2 : 3;
+        const long long ic = clampll(i, 0, P.nx - 1);
+        if (P.bc[side] == BC_INFLOW && ic >= P.lo[side] && ic < P.hi[side]) return side;
+        j = P.bc[side] == BC_PERIODIC ? wrapll(j, P.ny) : clampll(j, 0, P.ny - 1);
+    }
+    if (i < 0 || i >= P.nx) {
+        const int side = i < 0 ? 0 : 1;
+        if (P.bc[side] == BC_INFLOW && j >= P.lo[side] && j < P.hi[side]) return side;
+        i = P.bc[side] == BC_PERIODIC ? wrapll(i, P.nx) : clampll(i, 0, P.nx - 1);
+    }
+    *idx = j * P.nx + i;
+    return -1;
+}
+
+// Cell data as staged for the face corrector: phi-bar-plus coefficients (Eq. Fbarplus) in
+// the cell frame, the frame, and the density.
+template <int D, typename R>
+struct StagedCell {
+    R A[NCoef<D, 3>::value];
+    R B[NCoef<D, 2>::value];
+    double u[D];
+    R T;
+};
+
+// Loads cell (i, j) (ghosts resolved) and forms phi-bar-plus = cp phi~ + ce phi^eq with
+// phi^eq the co-moving equilibria (rho, 0, ...) and ((Cv - D/2) rho T, 0, ...).
+template <int D, typename R>
+__device__ __forceinline__ void load_cell_bar_plus(const Params<D, R> &P, long long i, long long j, R cp, R ce,
+                                                   StagedCell<D, R> &c)
+{
+    constexpr int NFC = NCoef<D, 3>::value, NGC = NCoef<D, 2>::value;
+    long long idx = 0;
+    const int side = resolve(P, i, j, &idx);
+    double rho, T;
+    if (side >= 0) {
+        rho = P.inflow[side][0];
+        T = P.inflow[side][3] / rho;
+        c.u[0] = P.inflow[side][1];
+        if constexpr (D == 2) c.u[1] = P.inflow[side][2];
+#pragma unroll
+        for (int k = 0; k < NFC; ++k) c.A[k] = R(0);
+#pragma unroll
+        for (int k = 0; k < NGC; ++k) c.B[k] = R(0);
+        c.A[0] = R(rho);
+        c.B[0] = R((P.Cv - 0.5 * D) * rho * T);
+    } else {
+        const long long n = P.ncell();
+#pragma unroll
+        for (int k = 0; k < NFC; ++k) {
+            const int pl = fplane<D>(k);
+            c.A[k] = pl < 0 ? R(0) : P.sf[pl * n + idx];
+        }
+#pragma unroll
+        for (int k = 0; k < NGC; ++k) c.B[k] = P.sg[k * n + idx];
+#pragma unroll
+        for (int a = 0; a < D; ++a) c.u[a] = P.sfr[a * n + idx];
+        T = P.sfr[D * n + idx];
+        rho = double(c.A[0]);
+    }
+    const R r = c.A[0];
+    c.A[0] = cp * r + ce * r;
+#pragma unroll
+    for (int k = 1; k < NFC; ++k) c.A[k] = cp * c.A[k];
+    c.B[0] = cp * c.B[0] + ce * R((P.Cv - 0.5 * D) * rho * T);
+#pragma unroll
+    for (int k = 1; k < NGC; ++k) c.B[k] = cp * c.B[k];
+    c.T = R(T);
+}
+
+// ------------------------------------------------------------------ face corrector
+
+template <int D>
+struct FaceTile;
+template <>
+struct FaceTile<1> { static constexpr int TX = 128, TY = 1, THREADS = 128; };
+template <>
+struct FaceTile<2> { static constexpr int TX = 32, TY = 4, THREADS = 256; };
+
+// transposes coefficient arrays so that index r always refers to the face normal
+template <int D, int N, typename R>
+__device__ __forceinline__ void orient(const R *in, R *out, bool swap)
+{
+    if (D == 1 || !swap) {
+#pragma unroll
+        for (int k = 0; k < NCoef<D, N>::value; ++k) out[k] = in[k];
+    } else {
+#pragma unroll
+        for (int r = 0; r <= N; ++r)
+#pragma unroll
+            for (int s = 0; s + r <= N; ++s) out[hidx(r, s)] = in[hidx(s, r)];
+    }
+}
+
+// frame map of a staged cell into the corrector frame: s = sqrt(Tc/Tl), e = s^2 - 1,
+// d = (uc - ul)/sqrt(Tl) with velocities relative to the face reference
+template <int D, typename R>
+__device__ __forceinline__ void cell_maps(R Tc, const R *dc, R Tl, R invTl, R rsqTl, const R *dl,
+                                          Map1<R> &X, Map1<R> &Y)
+{
+    const R s = sqrt(Tc * invTl);
+    const R e = (Tc - Tl) * invTl;
+    X = Map1<R>(s, e, (dc[0] - dl[0]) * rsqTl);
+    if (D == 2) Y = Map1<R>(s, e, (dc[1] - dl[1]) * rsqTl);
+    else Y = X;
+}
+
+// One corrector pass at a face (Sec. III.B.3) in frame (dl, Tl) (velocity relative to the
+// face reference uref): every stencil cell's phi-bar-plus is re-expressed in that frame,
+// limited slopes are formed per population, each population is reconstructed by MUSCL
+// at its departure point x_b - v_i dt/2 in the upwind cell, and the Hermite moments of
+// the reconstructed f-bar and g-bar are returned (Phi: f, order 3; Psi: g, order 2).
+// Stencil slots: 0 LL, 1 L, 2 R, 3 RR, 4 L-t, 5 L+t, 6 R-t, 7 R+t (t: tangential).
+template <int D, typename R>
+__device__ __forceinline__ void corrector_pass(const StagedCell<D, R> *const *cells, const R (*dc)[D],
+                                               const R *dl, R Tl, R un_abs, R ut_abs, R h_dn, R h_dt,
+                                               bool swap, int limiter, R *Phi, R *Psi)
+{
+    constexpr int NFC = NCoef<D, 3>::value, NGC = NCoef<D, 2>::value;
+    const R invTl = R(1) / Tl;
+    const R rsqTl = sqrt(invTl);
+    const R sqTl = Tl * rsqTl;
+    // the two cells next to the face, in the corrector frame
+    R FL[NFC], FR[NFC], GL[NGC], GR[NGC];
+    {
+        Map1<R> X(R(1), R(0), R(0)), Y(R(1), R(0), R(0));
+        R tmp[NFC], tmpg[NGC];
+        cell_maps<D, R>(cells[1]->T, dc[1], Tl, invTl, rsqTl, dl, X, Y);
+        orient<D, 3, R>(cells[1]->A, tmp, swap);
+        orient<D, 2, R>(cells[1]->B, tmpg, swap);
+        shift_scale<D, 3, R>(tmp, X, Y, FL);
+        shift_scale<D, 2, R>(tmpg, X, Y, GL);
+        cell_maps<D, R>(cells[2]->T, dc[2], Tl, invTl, rsqTl, dl, X, Y);
+        orient<D, 3, R>(cells[2]->A, tmp, swap);
+        orient<D, 2, R>(cells[2]->B, tmpg, swap);
+        shift_scale<D, 3, R>(tmp, X, Y, FR);
+        shift_scale<D, 2, R>(tmpg, X, Y, GR);
+    }
+#pragma unroll
+    for (int k = 0; k < NFC; ++k) Phi[k] = R(0);
+#pragma unroll
+    for (int k = 0; k < NGC; ++k) Psi[k] = R(0);
+
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const R vn = sqTl * R(node_c(m)) + un_abs;
+        const bool left = vn > R(0);
+        // departure point along the normal, in cells, from the upwind cell centre
+        const R offn = (left ? R(0.5) : R(-0.5)) - vn * h_dn;
+        // outer normal neighbour and tangential neighbours of the upwind cell, in the frame
+        constexpr int NS = D == 2 ? 3 : 1;
+        R FS[NS][NFC], GS[NS][NGC];
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+            const int slot = q == 0 ? (left ? 0 : 3) : (q == 1 ? (left ? 4 : 6) : (left ? 5 : 7));
+            Map1<R> X(R(1), R(0), R(0)), Y(R(1), R(0), R(0));
+            R tmp[NFC], tmpg[NGC];
+            cell_maps<D, R>(cells[slot]->T, dc[slot], Tl, invTl, rsqTl, dl, X, Y);
+            orient<D, 3, R>(cells[slot]->A, tmp, swap);
+            orient<D, 2, R>(cells[slot]->B, tmpg, swap);
+            shift_scale<D, 3, R>(tmp, X, Y, FS[q]);
+            shift_scale<D, 2, R>(tmpg, X, Y, GS[q]);
+        }
+        // select upwind (up), upstream (lo) and downstream (hi) along the normal
+        R Fup[NFC], Flo[NFC], Fhi[NFC], Gup[NGC], Glo[NGC], Ghi[NGC];
+#pragma unroll
+        for (int k = 0; k < NFC; ++k) {
+            Fup[k] = left ? FL[k] : FR[k];
+            Flo[k] = left ? FS[0][k] : FL[k];
+            Fhi[k] = left ? FR[k] : FS[0][k];
+        }
+#pragma unroll
+        for (int k = 0; k < NGC; ++k) {
+            Gup[k] = left ? GL[k] : GR[k];
+            Glo[k] = left ? GS[0][k] : GL[k];
+            Ghi[k] = left ? GR[k] : GS[0][k];
+        }
+        if constexpr (D == 1) {
+            // populations at node m of the three cells (unweighted: the limiter is
+            // homogeneous of degree one, so the weight w_m factors out)
+            R fu = R(0), fl = R(0), fh = R(0), gu = R(0), gl = R(0), gh = R(0);
+#pragma unroll
+            for (int a = 0; a <= 3; ++a) {
+                const R hn = R(hen(a, m));
+                fu += Fup[a] * hn; fl += Flo[a] * hn; fh += Fhi[a] * hn;
+                if (a <= 2) { gu += Gup[a] * hn; gl += Glo[a] * hn; gh += Ghi[a] * hn; }
+            }
+            const R fb = fu + offn * limit<R>(limiter, fu - fl, fh - fu);
+            const R gb = gu + offn * limit<R>(limiter, gu - gl, gh - gu);
+#pragma unroll
+            for (int a = 0; a <= 3; ++a) Phi[a] += R(node_w(m) * he(a, m)) * fb;
+#pragma unroll
+            for (int a = 0; a <= 2; ++a) Psi[a] += R(node_w(m) * he(a, m)) * gb;
+        } else {
+            // column collapse C_b = sum_a A_ab He_a(c_m)/a! for the five cells
+            R Cu[4], Cl[4], Ch[4], Cm[4], Cp[4], Du[3], Dl[3], Dh[3], Dm[3], Dp[3];
+#pragma unroll
+            for (int b = 0; b <= 3; ++b) {
+                R cu = R(0), cl = R(0), ch = R(0), cm = R(0), cpp = R(0);
+#pragma unroll
+                for (int a = 0; a + b <= 3; ++a) {
+                    const R hn = R(hen(a, m));
+                    cu += Fup[hidx(a, b)] * hn; cl += Flo[hidx(a, b)] * hn; ch += Fhi[hidx(a, b)] * hn;
+                    cm += FS[1][hidx(a, b)] * hn; cpp += FS[2][hidx(a, b)] * hn;
+                }
+                Cu[b] = cu; Cl[b] = cl; Ch[b] = ch; Cm[b] = cm; Cp[b] = cpp;
+            }
+#pragma unroll
+            for (int b = 0; b <= 2; ++b) {
+                R cu = R(0), cl = R(0), ch = R(0), cm = R(0), cpp = R(0);
+#pragma unroll
+                for (int a = 0; a + b <= 2; ++a) {
+                    const R hn = R(hen(a, m));
+                    cu += Gup[hidx(a, b)] * hn; cl += Glo[hidx(a, b)] * hn; ch += Ghi[hidx(a, b)] * hn;
+                    cm += GS[1][hidx(a, b)] * hn; cpp += GS[2][hidx(a, b)] * hn;
+                }
+                Du[b] = cu; Dl[b] = cl; Dh[b] = ch; Dm[b] = cm; Dp[b] = cpp;
+            }
+            R S[4] = {R(0), R(0), R(0), R(0)}, SG[3] = {R(0), R(0), R(0)};
+#pragma unroll
+            for (int n = 0; n < 4; ++n) {
+                const R vt = sqTl * R(node_c(n)) + ut_abs;
+                const R offt = -vt * h_dt;
+                R fu = R(0), fl = R(0), fh = R(0), fm = R(0), fp = R(0);
+#pragma unroll
+                for (int b = 0; b <= 3; ++b) {
+                    const R hn = R(hen(b, n));
+                    fu += Cu[b] * hn; fl += Cl[b] * hn; fh += Ch[b] * hn; fm += Cm[b] * hn; fp += Cp[b] * hn;
+                }
+                R gu = R(0), gl = R(0), gh = R(0), gm = R(0), gp = R(0);
+#pragma unroll
+                for (int b = 0; b <= 2; ++b) {
+                    const R hn = R(hen(b, n));
+                    gu += Du[b] * hn; gl += Dl[b] * hn; gh += Dh[b] * hn; gm += Dm[b] * hn; gp += Dp[b] * hn;
+                }
+                const R fb = fu + offn * limit<R>(limiter, fu - fl, fh - fu) + offt * limit<R>(limiter, fu - fm, fp - fu);
+                const R gb = gu + offn * limit<R>(limiter, gu - gl, gh - gu) + offt * limit<R>(limiter, gu - gm, gp - gu);
+#pragma unroll
+                for (int b = 0; b <= 3; ++b) S[b] += R(node_w(n) * he(b, n)) * fb;
+#pragma unroll
+                for (int b = 0; b <= 2; ++b) SG[b] += R(node_w(n) * he(b, n)) * gb;
+            }
+#pragma unroll
+            for (int a = 0; a <= 3; ++a)
+#pragma unroll
+                for (int b = 0; a + b <= 3; ++b) Phi[hidx(a, b)] += R(node_w(m) * he(a, m)) * S[b];
+#pragma unroll
+            for (int a = 0; a <= 2; ++a)
+#pragma unroll
+                for (int b = 0; a + b <= 2; ++b) Psi[hidx(a, b)] += R(node_w(m) * he(a, m)) * SG[b];
+        }
+    }
+}
+
+// Frame defined by the moments of a pass (Eqs. correctorfieldsrhoDUGKS-TDUGKS), relative
+// to the pass frame: rho, du (D) and T.  Returns false if it defines no frame.
+template <int D, typename R>
+__device__ __forceinline__ bool pass_frame(const R *Phi, const R *Psi, R Tl, R Cv, R &rho, R *du, R &T)
+{
+    rho = Phi[0];
+    const R sq = sqrt(Tl);
+    R k2 = R(0), tr;
+    if constexpr (D == 1) {
+        du[0] = sq * Phi[1] / rho;
+        k2 = du[0] * du[0];
+        tr = Phi[2] + Phi[0];
+    } else {
+        du[0] = sq * Phi[hidx(1, 0)] / rho;
+        du[1] = sq * Phi[hidx(0, 1)] / rho;
+        k2 = du[0] * du[0] + du[1] * du[1];
+        tr = Phi[hidx(2, 0)] + Phi[hidx(0, 2)] + R(2) * Phi[0];
+    }
+    // internal energy in the pass frame: T/2 sum f |c|^2 + sum g - rho |du|^2 / 2
+    T = (R(0.5) * Tl * tr + Psi[0] - R(0.5) * rho * k2) / (Cv * rho);
+    bool ok = T > R(0) && isfinite(T) && isfinite(rho);
+#pragma unroll
+    for (int a = 0; a < D; ++a) ok = ok && isfinite(du[a]);
+    return ok;
+}
+
+template <int D, typename R>
+__global__ void __launch_bounds__(FaceTile<D>::THREADS)
+face_kernel(const Params<D, R> P)
+{
+    constexpr int TX = FaceTile<D>::TX, TY = FaceTile<D>::TY;
+    constexpr int BX = TX + 3, BY = D == 2 ? TY + 3 : 1;
+    constexpr int NFC = NCoef<D, 3>::value, NGC = NCoef<D, 2>::value;
+    __shared__ StagedCell<D, R> tile[BY * BX];
+
+    const double dt = P.clock->dt;
+    if (!(dt > 0.0)) return;  // t_end reached: the step is a no-op
+    const double h = 0.5 * dt, tau = P.tau;
+    const R cp = R((2.0 * tau - h) / (2.0 * tau + dt));
+    const R ce = R(3.0 * h / (2.0 * tau + dt));
+
+    const long long i0 = (long long)blockIdx.x * TX, j0 = (long long)blockIdx.y * TY;
+    // stage phi-bar-plus of the box [i0-2, i0+TX] x [j0-2, j0+TY] (1D: [i0-2, i0+TX])
+    for (int t = threadIdx.x; t < BX * BY; t += blockDim.x) {
+        const int bx = t % BX, by = t / BX;
+        const long long ci = i0 - 2 + bx, cj = D == 2 ? j0 - 2 + by : 0;
+        load_cell_bar_plus<D, R>(P, ci, cj, cp, ce, tile[t]);
+    }
+    __syncthreads();
+
+    // face of this thread
+    int dir = 0, tx = threadIdx.x, ty = 0;
+    if (D == 2) {
+        dir = threadIdx.x >= TX * TY ? 1 : 0;
+        const int t = threadIdx.x - dir * TX * TY;
+        tx = t % TX;
+        ty = t / TX;
+    }
+    const long long fi = i0 + tx, fj = j0 + ty;
+    bool active;
+    long long fidx;
+    if (dir == 0) { active = fi <= P.nx && fj < P.ny; fidx = fj * (P.nx + 1) + fi; }
+    else { active = fi < P.nx && fj <= P.ny; fidx = fj * P.nx + fi; }
+
+    unsigned long long my_iters = 0, my_nonconv = 0, my_fallbacks = 0, my_nonphys = 0;
+    if (active) {
+        // stencil slots in the staged box (box coords of cell (i, j) = (i - i0 + 2, j - j0 + 2))
+        const StagedCell<D, R> *cells[8];
+        auto at = [&](long long ci, long long cj) -> const StagedCell<D, R> * {
+            const int bx = int(ci - i0 + 2), by = D == 2 ? int(cj - j0 + 2) : 0;
+            return &tile[by * BX + bx];
+        };
+        if (dir == 0) {
+            cells[0] = at(fi - 2, fj); cells[1] = at(fi - 1, fj); cells[2] = at(fi, fj); cells[3] = at(fi + 1, fj);
+            if (D == 2) {
+                cells[4] = at(fi - 1, fj - 1); cells[5] = at(fi - 1, fj + 1);
+                cells[6] = at(fi, fj - 1); cells[7] = at(fi, fj + 1);
+            }
+        } else {
+            cells[0] = at(fi, fj - 2); cells[1] = at(fi, fj - 1); cells[2] = at(fi, fj); cells[3] = at(fi, fj + 1);
+            cells[4] = at(fi - 1, fj - 1); cells[5] = at(fi + 1, fj - 1);
+            cells[6] = at(fi - 1, fj); cells[7] = at(fi + 1, fj);
+        }
+        constexpr int NCELL = D == 2 ? 8 : 4;
+        const bool swap = dir == 1;
+        R *Fout = dir == 0 ? P.xf : P.yf;
+        R *Gout = dir == 0 ? P.xg : P.yg;
+        double *Frm = dir == 0 ? P.xfr : P.yfr;
+        const long long nf = dir == 0 ? P.nxf() : P.nyf();
+        const int na = swap ? 1 : 0, ta = swap ? 0 : 1;  // normal / tangential axes
+        const double dn = swap ? P.dy : P.dx, dtg = swap ? P.dx : P.dy;
+        const R h_dn = R(h / dn), h_dt = R(D == 2 ? h / dtg : 0.0);
+        // face reference velocity: the predictor; all velocities below are relative to it
+        double uref[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) uref[a] = Frm[a * nf + fidx];
+        const R Tpred = R(Frm[D * nf + fidx]);
+        R dc[NCELL][D];
+#pragma unroll
+        for (int s = 0; s < NCELL; ++s) {
+            dc[s][0] = R(cells[s]->u[na] - uref[na]);
+            if constexpr (D == 2) dc[s][1] = R(cells[s]->u[ta] - uref[ta]);
+        }
+        R uref_t = R(0);
+        if constexpr (D == 2) uref_t = R(uref[ta]);
+        const R uref_n = R(uref[na]);
+        const R Cv = R(P.Cv);
+
+        R dl[D], Tl = Tpred;
+#pragma unroll
+        for (int a = 0; a < D; ++a) dl[a] = R(0);
+        R keep_dl[D], keep_T = R(0), out_du[D], out_T = R(0), out_rho = R(0);
+        bool have = false, done = false, restarted = false, last_valid = false;
+        int iters = 0;
+        R Phi[NFC], Psi[NGC];
+        for (int k = 0; k < P.max_iter && !done; ++k) {
+            corrector_pass<D, R>(cells, dc, dl, Tl, uref_n + dl[0], D == 2 ? uref_t + dl[D - 1] : R(0),
+                                 h_dn, h_dt, swap, P.limiter, Phi, Psi);
+            R rho1, du[D], T1;
+            const bool ok = pass_frame<D, R>(Phi, Psi, Tl, Cv, rho1, du, T1);
+            iters = k + 1;
+            if (!ok) {
+                ++my_fallbacks;
+                last_valid = false;
+                if (!restarted) {
+                    // restart once from the frame of the pooled conserved moments of the stencil
+                    restarted = true;
+                    R r = R(0), m[D], e = R(0);
+#pragma unroll
+                    for (int a = 0; a < D; ++a) m[a] = R(0);
+#pragma unroll
+                    for (int s = 0; s < NCELL; ++s) {
+                        const R rc = cells[s]->A[0];
+                        R v2 = R(0);
+#pragma unroll
+                        for (int a = 0; a < D; ++a) { m[a] += rc * dc[s][a]; v2 += dc[s][a] * dc[s][a]; }
+                        r += rc;
+                        e += rc * (Cv * cells[s]->T + R(0.5) * v2);
+                    }
+                    r /= R(NCELL); e /= R(NCELL);
+                    R k2 = R(0);
+#pragma unroll
+                    for (int a = 0; a < D; ++a) { m[a] /= R(NCELL); dl[a] = m[a] / r; k2 += m[a] * m[a]; }
+                    Tl = (e - R(0.5) * k2 / r) / (Cv * r);
+                    continue;
+                }
+                break;
+            }
+            have = true;
+            last_valid = true;
+#pragma unroll
+            for (int a = 0; a < D; ++a) { keep_dl[a] = dl[a]; out_du[a] = du[a]; }
+            keep_T = Tl; out_T = T1; out_rho = rho1;
+            if (P.fixed_iters > 0) {
+                done = iters >= P.fixed_iters;
+            } else {
+                bool c = fabs(T1 - Tl) <= R(P.tol) * Tl;
+                const R sq = sqrt(Tl);
+#pragma unroll
+                for (int a = 0; a < D; ++a) c = c && fabs(du[a]) <= R(P.tol) * sq;
+                done = c;
+            }
+#pragma unroll
+            for (int a = 0; a < D; ++a) dl[a] += du[a];
+            Tl = T1;
+        }
+        my_iters = iters;
+        if (!done) ++my_nonconv;
+        if (have) {
+            if (!last_valid) {
+                // the last pass defined no frame: recompute the last valid one
+                corrector_pass<D, R>(cells, dc, keep_dl, keep_T, uref_n + keep_dl[0],
+                                     D == 2 ? uref_t + keep_dl[D - 1] : R(0), h_dn, h_dt, swap, P.limiter, Phi, Psi);
+            }
+            // Eq. (FluxTransf) in the frame of the last valid pass's moments, with the exact
+            // co-moving equilibria there: phi = (2 tau phibar + h phi^eq)/(2 tau + h)
+            const R invT = R(1) / out_T;
+            Map1<R> X(sqrt(keep_T * invT), (keep_T - out_T) * invT, -out_du[0] * sqrt(invT));
+            Map1<R> Y = X;
+            if (D == 2) Y = Map1<R>(sqrt(keep_T * invT), (keep_T - out_T) * invT, -out_du[D - 1] * sqrt(invT));
+            R Fo[NFC], Go[NGC];
+            shift_scale<D, 3, R>(Phi, X, Y, Fo);
+            shift_scale<D, 2, R>(Psi, X, Y, Go);
+            const R wb = R(2.0 * tau / (2.0 * tau + h)), we = R(h / (2.0 * tau + h));
+            Fo[0] = wb * Fo[0] + we * out_rho;
+#pragma unroll
+            for (int k = 1; k < NFC; ++k) Fo[k] = wb * Fo[k];
+            Go[0] = wb * Go[0] + we * R((P.Cv - 0.5 * D) * double(out_rho) * double(out_T));
+#pragma unroll
+            for (int k = 1; k < NGC; ++k) Go[k] = wb * Go[k];
+            R Fw[NFC], Gw[NGC];
+            orient<D, 3, R>(Fo, Fw, swap);
+            orient<D, 2, R>(Go, Gw, swap);
+#pragma unroll
+            for (int k = 0; k < NFC; ++k) Fout[k * nf + fidx] = Fw[k];
+#pragma unroll
+            for (int k = 0; k < NGC; ++k) Gout[k * nf + fidx] = Gw[k];
+            Frm[na * nf + fidx] = uref[na] + double(keep_dl[0]) + double(out_du[0]);
+            if constexpr (D == 2) Frm[ta * nf + fidx] = uref[ta] + double(keep_dl[1]) + double(out_du[1]);
+            Frm[D * nf + fidx] = double(out_T);
+        } else {
+            ++my_nonphys;
+            const R nan = R(__longlong_as_double(0x7ff8000000000000ll));
+#pragma unroll
+            for (int k = 0; k < NFC; ++k) Fout[k * nf + fidx] = nan;
+#pragma unroll
+            for (int k = 0; k < NGC; ++k) Gout[k * nf + fidx] = nan;
+            Frm[D * nf + fidx] = double(nan);
+        }
+    }
+    // warp-aggregated diagnostics
+    const unsigned mask = 0xffffffffu;
+    unsigned long long n_act = active ? 1ull : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        my_iters += __shfl_down_sync(mask, my_iters, o);
+        my_nonconv += __shfl_down_sync(mask, my_nonconv, o);
+        my_fallbacks += __shfl_down_sync(mask, my_fallbacks, o);
+        my_nonphys += __shfl_down_sync(mask, my_nonphys, o);
+        n_act += __shfl_down_sync(mask, n_act, o);
+    }
+    if ((threadIdx.x & 31) == 0 && n_act) {
+        atomicAdd(&P.diag->face_iters, my_iters);
+        atomicAdd(&P.diag->face_solves, n_act);
+        if (my_nonconv) { atomicAdd(&P.diag->nonconv, my_nonconv); atomicOr(&P.diag->flags, FLAG_NOT_CONVERGED); }
+        if (my_fallbacks) atomicAdd(&P.diag->fallbacks, my_fallbacks);
+        if (my_nonphys) { atomicAdd(&P.diag->nonphys, my_nonphys); atomicOr(&P.diag->flags, FLAG_NONPHYSICAL); }
+    }
+}
+
+// ---------------------------------------------------------------- cell update
+
+// Adds -sign * (dt/dx_n) * H[v_n phi] for one face to the f (H) and g (G) Hermite moments
+// of the cell, phi given by face coefficients in the face frame.  The face populations are
+// first re-expressed in the cell frame (Eq. fluxEq), then multiplied by v_n = sqrt(T) c_n + u_n
+// using c He_r(c) = He_{r+1}(c) + r He_{r-1}(c); He_4 vanishes on the D1Q4 nodes and the
+// Grad forms have no moments above their order, so the product closes on the same orders.
+template <int D, typename R>
+__device__ __forceinline__ void add_face_flux(const Params<D, R> &P, const R *Fc, const R *Gc, const double *ub, double Tb,
+                                              const double *uc, double Tc, int axis, R scale, R sqTc, R un,
+                                              R *H, R *G)
+{
+    constexpr int NFC = NCoef<D, 3>::value, NGC = NCoef<D, 2>::value;
+    const double invT = 1.0 / Tc, rsq = sqrt(invT);
+    const R s = R(sqrt(Tb * invT)), e = R((Tb - Tc) * invT);
+    Map1<R> X(s, e, R((ub[0] - uc[0]) * rsq));
+    Map1<R> Y = X;
+    if (D == 2) Y = Map1<R>(s, e, R((ub[D - 1] - uc[D - 1]) * rsq));
+    R Fp[NFC], Gp[NGC];
+    shift_scale<D, 3, R>(Fc, X, Y, Fp);
+    shift_scale<D, 2, R>(Gc, X, Y, Gp);
+    if constexpr (D == 1) {
+#pragma unroll
+        for (int r = 0; r <= 3; ++r) {
+            R v = un * Fp[r];
+            if (r + 1 <= 3) v += sqTc * Fp[r + 1];
+            if (r >= 1) v += sqTc * R(r) * Fp[r - 1];
+            H[r] -= scale * v;
+        }
+#pragma unroll
+        for (int r = 0; r <= 2; ++r) {
+            R v = un * Gp[r];
+            if (r + 1 <= 2) v += sqTc * Gp[r + 1];
+            if (r >= 1) v += sqTc * R(r) * Gp[r - 1];
+            G[r] -= scale * v;
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r <= 3; ++r)
+#pragma unroll
+            for (int q = 0; q + r <= 3; ++q) {
+                const int k = hidx(r, q);
+                R v = un * Fp[k];
+                if (axis == 0) {
+                    if (r + q + 1 <= 3) v += sqTc * Fp[hidx(r + 1, q)];
+                    if (r >= 1) v += sqTc * R(r) * Fp[hidx(r - 1, q)];
+                } else {
+                    if (r + q + 1 <= 3) v += sqTc * Fp[hidx(r, q + 1)];
+                    if (q >= 1) v += sqTc * R(q) * Fp[hidx(r, q - 1)];
+                }
+                H[k] -= scale * v;
+            }
+#pragma unroll
+        for (int r = 0; r <= 2; ++r)
+#pragma unroll
+            for (int q = 0; q + r <= 2; ++q) {
+                const int k = hidx(r, q);
+                R v = un * Gp[k];
+                if (axis == 0) {
+                    if (r + q + 1 <= 2) v += sqTc * Gp[hidx(r + 1, q)];
+                    if (r >= 1) v += sqTc * R(r) * Gp[hidx(r - 1, q)];
+                } else {
+                    if (r + q + 1 <= 2) v += sqTc * Gp[hidx(r, q + 1)];
+                    if (q >= 1) v += sqTc * R(q) * Gp[hidx(r, q - 1)];
+                }
+                G[k] -= scale * v;
+            }
+    }
+}
+
+template <int D>
+struct CellBlock { static constexpr int THREADS = 256; };
+
+// CFL rate of a cell frame: max over axes of (|u_a| + sqrt(T/T_L) max|c|)/dx_a
+__device__ __forceinline__ double cell_rate(const double *u, double T, double dx, double dy, int D)
+{
+    const double c = sqrt(T) * kCHi;
+    double r = (fabs(u[0]) + c) / dx;
+    if (D == 2) r = fmax(r, (fabs(u[1]) + c) / dy);
+    return r;
+}
+
+// block max of a non-negative double, then the last block turns the grid max into the
+// next time step (CFL condition, clipped to t_end) and advances the clock
+__device__ __forceinline__ void reduce_rate_and_advance(Clock *clock, double rate, bool advance)
+{
+    __shared__ double red[32];
+    __shared__ bool last;
+    double r = rate;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_down_sync(0xffffffffu, r, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = r;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int nw = (blockDim.x + 31) >> 5;
+        r = threadIdx.x < nw ? red[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_down_sync(0xffffffffu, r, o));
+        if (threadIdx.x == 0) {
+            // non-negative doubles order like their bit patterns; NaN (bits above +inf) wins
+            atomicMax(&clock->rate_bits, (unsigned long long)__double_as_longlong(r));
+            __threadfence();
+            const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
+            last = atomicAdd(&clock->blocks_done, 1u) == nb - 1;
+        }
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        const double rmax = __longlong_as_double((long long)atomicAdd(&clock->rate_bits, 0ull));
+        double t = clock->t;
+        if (advance) {
+            t += clock->dt;
+            clock->t = t;
+            clock->steps += 1;
+        }
+        double dt = clock->cfl / rmax;
+        if (clock->t_end > 0.0) {
+            if (t >= clock->t_end) dt = 0.0;
+            else if (t + dt > clock->t_end) dt = clock->t_end - t;
+        }
+        clock->dt = dt;
+        clock->rate_bits = 0ull;
+        clock->blocks_done = 0u;
+    }
+}
+
+// Step 3 of Sec. III.B.4 (flux into the cell frame, Eq. fluxEq; update, Eqs.
+// FinalUpdateDUGKS) fused with step 1 of the next step (re-expression in the new co-moving
+// frame, recovered in FP64 from the conserved moments) and the CFL reduction.
+template <int D, typename R>
+__global__ void __launch_bounds__(CellBlock<D>::THREADS)
+cell_kernel(const Params<D, R> P)
+{
+    constexpr int NFC = NCoef<D, 3>::value, NGC = NCoef<D, 2>::value;
+    const double dt = P.clock->dt;
+    if (!(dt > 0.0)) return;
+    const long long n = P.ncell();
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double rate = 0.0;
+    if (c < n) {
+        const long long i = c % P.nx, j = c / P.nx;
+        double uc[D], Tc;
+#pragma unroll
+        for (int a = 0; a < D; ++a) uc[a] = P.sfr[a * n + c];
+        Tc = P.sfr[D * n + c];
+        const R rho = P.sf[c];
+        const double tau = P.tau;
+        const R ca = R((2.0 * tau - dt) / (2.0 * tau + dt)), cb = R(2.0 * dt / (2.0 * tau + dt));
+        // collision part of Eqs. (FinalUpdateDUGKS) in Hermite moments of the cell frame
+        R H[NFC], G[NGC];
+#pragma unroll
+        for (int k = 0; k < NFC; ++k) {
+            const int pl = fplane<D>(k);
+            H[k] = pl < 0 ? R(0) : ca * P.sf[pl * n + c];
+        }
+        H[0] += cb * rho;
+#pragma unroll
+        for (int k = 0; k < NGC; ++k) G[k] = ca * P.sg[k * n + c];
+        G[0] += cb * R((P.Cv - 0.5 * D) * double(rho) * Tc);
+        // fluxes through the 2D faces
+        const R sqTc = R(sqrt(Tc));
+        const long long nxf = P.nxf();
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            const long long f = j * (P.nx + 1) + i + side;
+            R Fc[NFC], Gc[NGC];
+            double ub[D];
+#pragma unroll
+            for (int k = 0; k < NFC; ++k) Fc[k] = P.xf[k * nxf + f];
+#pragma unroll
+            for (int k = 0; k < NGC; ++k) Gc[k] = P.xg[k * nxf + f];
+#pragma unroll
+            for (int a = 0; a < D; ++a) ub[a] = P.xfr[a * nxf + f];
+            const double Tb = P.xfr[D * nxf + f];
+            add_face_flux<D, R>(P, Fc, Gc, ub, Tb, uc, Tc, 0, R((side ? 1.0 : -1.0) * dt / P.dx), sqTc, R(uc[0]), H, G);
+        }
+        if constexpr (D == 2) {
+            const long long nyf = P.nyf();
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+                const long long f = (j + side) * P.nx + i;
+                R Fc[NFC], Gc[NGC];
+                double ub[D];
+#pragma unroll
+                for (int k = 0; k < NFC; ++k) Fc[k] = P.yf[k * nyf + f];
+#pragma unroll
+                for (int k = 0; k < NGC; ++k) Gc[k] = P.yg[k * nyf + f];
+#pragma unroll
+                for (int a = 0; a < D; ++a) ub[a] = P.yfr[a * nyf + f];
+                const double Tb = P.yfr[D * nyf + f];
+                add_face_flux<D, R>(P, Fc, Gc, ub, Tb, uc, Tc, 1, R((side ? 1.0 : -1.0) * dt / P.dy), sqTc, R(uc[1]), H, G);
+            }
+        }
+        // step 1 of the next step: the new co-moving frame from the conserved moments, in FP64
+        const double rn = double(H[0]);
+        double du[D], k2 = 0.0, tr;
+        if constexpr (D == 1) {
+            du[0] = sqrt(Tc) * double(H[1]) / rn;
+            k2 = du[0] * du[0];
+            tr = double(H[2]) + rn;
+        } else {
+            du[0] = sqrt(Tc) * double(H[hidx(1, 0)]) / rn;
+            du[1] = sqrt(Tc) * double(H[hidx(0, 1)]) / rn;
+            k2 = du[0] * du[0] + du[1] * du[1];
+            tr = double(H[hidx(2, 0)]) + double(H[hidx(0, 2)]) + 2.0 * rn;
+        }
+        const double Tn = (0.5 * Tc * tr + double(G[0]) - 0.5 * rn * k2) / (P.Cv * rn);
+        double un[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) un[a] = uc[a] + du[a];
+        bool ok = rn > 0.0 && Tn > 0.0 && isfinite(rn) && isfinite(Tn);
+        if (!ok) {
+            atomicOr(&P.diag->flags, FLAG_NONPHYSICAL);
+            atomicAdd(&P.diag->nonphys, 1ull);
+            atomicCAS((unsigned long long *)&P.diag->first_bad, (unsigned long long)-1ll, (unsigned long long)c);
+        }
+        // Grad projection into the new frame (f third order, g second order)
+        const double invT = 1.0 / Tn, rsq = sqrt(invT);
+        const R s = R(sqrt(Tc * invT)), e = R((Tc - Tn) * invT);
+        Map1<R> X(s, e, R(-du[0] * rsq));
+        Map1<R> Y = X;
+        if (D == 2) Y = Map1<R>(s, e, R(-du[D - 1] * rsq));
+        R Ho[NFC], Go[NGC];
+        shift_scale<D, 3, R>(H, X, Y, Ho);
+        shift_scale<D, 2, R>(G, X, Y, Go);
+#pragma unroll
+        for (int k = 0; k < NFC; ++k) {
+            const int pl = fplane<D>(k);
+            if (pl >= 0) P.sf[pl * n + c] = Ho[k];
+        }
+#pragma unroll
+        for (int k = 0; k < NGC; ++k) P.sg[k * n + c] = Go[k];
+#pragma unroll
+        for (int a = 0; a < D; ++a) P.sfr[a * n + c] = un[a];
+        P.sfr[D * n + c] = Tn;
+        rate = ok ? cell_rate(un, Tn, P.dx, P.dy, D) : __longlong_as_double(0x7ff8000000000000ll);
+    }
+    reduce_rate_and_advance(P.clock, rate, true);
+}
+
+// ------------------------------------------------------------ initial condition
+
+// Equilibria of Eqs. (feqPond), (geqPond) in each cell's frame from primitive fields.
+template <int D, typename R>
+__global__ void init_cells_kernel(const Params<D, R> P, const double *rho, const double *ux, const double *uy, const double *p)
+{
+    constexpr int NFS = Params<D, R>::NFS, NGC = NCoef<D, 2>::value;
+    const long long n = P.ncell();
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double rate = 0.0;
+    if (c < n) {
+        const double r = rho[c], T = p[c] / r;
+        double u[2] = {ux[c], (D == 2 && uy) ? uy[c] : 0.0};
+        P.sf[c] = R(r);
+#pragma unroll
+        for (int k = 1; k < NFS; ++k) P.sf[k * n + c] = R(0);
+        P.sg[c] = R((P.Cv - 0.5 * D) * r * T);
+#pragma unroll
+        for (int k = 1; k < NGC; ++k) P.sg[k * n + c] = R(0);
+#pragma unroll
+        for (int a = 0; a < D; ++a) P.sfr[a * n + c] = u[a];
+        P.sfr[D * n + c] = T;
+        const bool ok = r > 0.0 && T > 0.0 && isfinite(r) && isfinite(T);
+        if (!ok) {
+            atomicOr(&P.diag->flags, FLAG_NONPHYSICAL);
+            atomicAdd(&P.diag->nonphys, 1ull);
+            atomicCAS((unsigned long long *)&P.diag->first_bad, (unsigned long long)-1ll, (unsigned long long)c);
+        }
+        rate = ok ? cell_rate(u, T, P.dx, P.dy, D) : __longlong_as_double(0x7ff8000000000000ll);
+    }
+    reduce_rate_and_advance(P.clock, rate, false);
+}
+
+// conserved moments (rho, rho u, rho E) of a resolved cell, from its stored state
+template <int D, typename R>
+__device__ __forceinline__ void cell_conserved(const Params<D, R> &P, long long i, long long j, double &r, double *m, double &E)
+{
+    long long idx = 0;
+    const int side = resolve(P, i, j, &idx);
+    double u[2] = {0.0, 0.0}, T;
+    if (side >= 0) {
+        r = P.inflow[side][0];
+        T = P.inflow[side][3] / r;
+        u[0] = P.inflow[side][1];
+        u[1] = P.inflow[side][2];
+    } else {
+        const long long n = P.ncell();
+        r = double(P.sf[idx]);
+#pragma unroll
+        for (int a = 0; a < D; ++a) u[a] = P.sfr[a * n + idx];
+        T = P.sfr[D * n + idx];
+    }
+    double k2 = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) { m[a] = r * u[a]; k2 += u[a] * u[a]; }
+    E = r * (P.Cv * T + 0.5 * k2);
+}
+
+// face predictor before the first step: frame of the pooled moments of the two cells
+template <int D, typename R>
+__global__ void init_faces_kernel(const Params<D, R> P)
+{
+    const long long nxf = P.nxf(), nyf = D == 2 ? P.nyf() : 0;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nxf + nyf) return;
+    const bool xdir = t < nxf;
+    const long long f = xdir ? t : t - nxf;
+    long long ai, aj, bi, bj;
+    if (xdir) { const long long i = f % (P.nx + 1), j = f / (P.nx + 1); ai = i - 1; aj = j; bi = i; bj = j; }
+    else { const long long i = f % P.nx, j = f / P.nx; ai = i; aj = j - 1; bi = i; bj = j; }
+    double ra, ma[2] = {0, 0}, Ea, rb, mb[2] = {0, 0}, Eb;
+    cell_conserved<D, R>(P, ai, aj, ra, ma, Ea);
+    cell_conserved<D, R>(P, bi, bj, rb, mb, Eb);
+    const double r = 0.5 * (ra + rb), E = 0.5 * (Ea + Eb);
+    double k2 = 0.0, u[2];
+#pragma unroll
+    for (int a = 0; a < D; ++a) { const double m = 0.5 * (ma[a] + mb[a]); u[a] = m / r; k2 += m * m; }
+    double *Frm = xdir ? P.xfr : P.yfr;
+    const long long nf = xdir ? nxf : nyf;
+#pragma unroll
+    for (int a = 0; a < D; ++a) Frm[a * nf + f] = u[a];
+    Frm[D * nf + f] = (E - 0.5 * k2 / r) / (P.Cv * r);
+}
+
+// ---------------------------------------------------------------- read-back kernels
+
+// conserved fields per cell (lab frame, FP64)
+template <int D, typename R>
+__global__ void conserved_kernel(const Params<D, R> P, double *rho, double *mx, double *my, double *E)
+{
+    const long long n = P.ncell();
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    double r, m[2] = {0, 0}, e;
+    cell_conserved<D, R>(P, c % P.nx, c / P.nx, r, m, e);
+    if (rho) rho[c] = r;
+    if (mx) mx[c] = m[0];
+    if (my) my[c] = D == 2 ? m[1] : 0.0;
+    if (E) E[c] = e;
+}
+
+// stored state as full coefficient arrays [cells][NFC], [cells][NGC] and frames [cells][D+1]
+template <int D, typename R>
+__global__ void export_state_kernel(const Params<D, R> P, double *cf, double *cg, double *fr)
+{
+    constexpr int NFC = NCoef<D, 3>::value, NGC = NCoef<D, 2>::value;
+    const long long n = P.ncell();
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    if (cf)
+#pragma unroll
+        for (int k = 0; k < NFC; ++k) {
+            const int pl = fplane<D>(k);
+            cf[c * NFC + k] = pl < 0 ? 0.0 : double(P.sf[pl * n + c]);
+        }
+    if (cg)
+#pragma unroll
+        for (int k = 0; k < NGC; ++k) cg[c * NGC + k] = double(P.sg[k * n + c]);
+    if (fr)
+#pragma unroll
+        for (int a = 0; a <= D; ++a) fr[c * (D + 1) + a] = P.sfr[a * n + c];
+}
+
+// Compensated (double-double) sums of four fields scaled by vol: per-block partials
+// (hi, lo) into part[block][8]; a single block then folds the partials into out[4].
+__device__ __forceinline__ void two_sum(double a, double b, double &s, double &e)
+{
+    s = a + b;
+    const double bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void dd_add(double &hi, double &lo, double bh, double bl)
+{
+    double s, e;
+    two_sum(hi, bh, s, e);
+    e += lo + bl;
+    hi = s + e;
+    lo = e - (hi - s);
+}
+
+__global__ void dd_partial_kernel(const double *a0, const double *a1, const double *a2, const double *a3, long long n,
+                                  double *part)
+{
+    __shared__ double sh[4][2][256];
+    double hi[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0};
+    const double *src[4] = {a0, a1, a2, a3};
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (src[k]) dd_add(hi[k], lo[k], src[k][c], 0.0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) { sh[k][0][threadIdx.x] = hi[k]; sh[k][1][threadIdx.x] = lo[k]; }
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                double h = sh[k][0][threadIdx.x], l = sh[k][1][threadIdx.x];
+                dd_add(h, l, sh[k][0][threadIdx.x + s], sh[k][1][threadIdx.x + s]);
+                sh[k][0][threadIdx.x] = h;
+                sh[k][1][threadIdx.x] = l;
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) { part[blockIdx.x * 8 + 2 * k] = sh[k][0][0]; part[blockIdx.x * 8 + 2 * k + 1] = sh[k][1][0]; }
+}
+
+__global__ void dd_final_kernel(const double *part, int nparts, double vol, double *out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int k = 0; k < 4; ++k) {
+        double hi = 0.0, lo = 0.0;
+        for (int b = 0; b < nparts; ++b) dd_add(hi, lo, part[b * 8 + 2 * k], part[b * 8 + 2 * k + 1]);
+        out[k] = (hi + lo) * vol;
+    }
+}
+
+}  // namespace pond

@@ -21,3 +21,24 @@ def hermite_coeffs_1d(f, c):
     """Hermite moments a_k = sum_i f_i He_k(c_i), k = 0..3 (probabilists' Hermite)."""
     He = [np.ones_like(c), c, c * c - 1.0, c ** 3 - 3.0 * c]
     return np.array([np.dot(f, h) for h in He])
+
+
+def hermite_of_pops(f, D):
+    """Hermite moments of populations f [cells, Q] on D1Q4 / D2Q16 in the library's packed
+    order (1D: a0..a3; 2D: 00 10 01 20 11 02 30 21 12 03), all orders up to 3."""
+    c, W, _ = O.lattice(D)
+    He = lambda k, x: [np.ones_like(x), x, x * x - 1.0, x ** 3 - 3.0 * x][k]
+    if D == 1:
+        return np.stack([f @ He(k, c[:, 0]) for k in range(4)], 1)
+    cols = []
+    for n in range(4):
+        for s in range(n + 1):
+            r = n - s
+            cols.append(f @ (He(r, c[:, 0]) * He(s, c[:, 1])))
+    return np.stack(cols, 1)
+
+
+def max_rel(a, b):
+    """max |a - b| / max |b| (field-wise relative error)."""
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))

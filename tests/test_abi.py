@@ -1,0 +1,72 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, exports every entry point
+that include/pond.h declares, and validates its arguments before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2203_05477_gb300 as pond
+from paper_2203_05477_gb300 import _build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return ctypes.CDLL(pond.library_path())
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(pond_\w+)\s*\(", text))
+    return sorted(names)
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_symbols()
+    assert "pond_init" in names and "pond_step" in names and "pond_moments" in names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def _grid(dim=1, nx=8):
+    g = pond.pond_grid()
+    g.dim, g.nx, g.ny, g.x0, g.x1, g.y0, g.y1 = dim, nx, 1 if dim == 1 else nx, 0.0, 1.0, 0.0, 1.0
+    return g
+
+
+def _opts():
+    o = pond.pond_options()
+    o.precision, o.limiter, o.cfl, o.tol, o.max_iter = pond.POND_FP64, 0, 0.2, 1e-10, 16
+    return o
+
+
+@pytest.mark.parametrize("velset,dim,gamma,want", [
+    (pond.POND_D1Q3, 1, 1.4, pond.POND_ERR_UNSUPPORTED),
+    (pond.POND_D2Q9, 2, 1.4, pond.POND_ERR_UNSUPPORTED),
+    (pond.POND_D1Q4, 2, 1.4, pond.POND_ERR_INVALID_ARG),     # dim mismatch
+    (pond.POND_D2Q16, 2, 2.5, pond.POND_ERR_UNSUPPORTED),    # gamma > 1 + 2/D
+    (pond.POND_D1Q4, 1, 1.0, pond.POND_ERR_INVALID_ARG),
+])
+def test_init_rejects_bad_arguments(lib, velset, dim, gamma, want):
+    L = pond._load()
+    g, o = _grid(dim), _opts()
+    h = ctypes.c_void_p()
+    st = L.pond_init(ctypes.byref(g), velset, gamma, 1e-5, ctypes.byref(o), ctypes.byref(h))
+    assert st == want
+    assert not h.value
+    assert L.pond_last_error()
+
+
+def test_null_arguments(lib):
+    L = pond._load()
+    h = ctypes.c_void_p()
+    assert L.pond_init(None, pond.POND_D1Q4, 1.4, 1e-5, None, ctypes.byref(h)) == pond.POND_ERR_INVALID_ARG
+    assert L.pond_step(None, 1) == pond.POND_ERR_INVALID_ARG
+    assert L.pond_sync(None, None) == pond.POND_ERR_INVALID_ARG

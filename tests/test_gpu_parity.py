@@ -1,0 +1,258 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle, element by element,
+on the same seeded inputs.  FP64 mode: 1e-12 relative in corrector parity mode (a fixed
+number of corrector passes, so rounding cannot change iteration counts).  FP32 mode:
+1e-4 relative L1 on density, pressure and velocity with shocks within one cell."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_2203_05477_gb300 as pond  # noqa: E402
+from paper_2203_05477_gb300 import inputs as I  # noqa: E402
+from tests.common import hermite_of_pops, max_rel, oracle_for, rel_l1  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+
+
+def gpu_for(pb, **kw):
+    s = pond.Solver(pb, **kw)
+    s.set_primitive()
+    return s
+
+
+def compare_fp64(gs, os_, tol=FP64_TOL, what="conserved"):
+    (r, mx, my, E), _ = gs.moments(totals=False)
+    ro, mxo, myo, Eo = os_.conserved()
+    scale_m = max(np.abs(mxo).max(), np.abs(myo).max(), np.sqrt(np.abs(Eo * ro).max()))
+    assert max_rel(r, ro) <= tol, ("rho", max_rel(r, ro))
+    assert np.abs(mx - mxo).max() <= tol * scale_m, ("mx", np.abs(mx - mxo).max() / scale_m)
+    assert np.abs(my - myo).max() <= tol * scale_m, ("my", np.abs(my - myo).max() / scale_m)
+    assert max_rel(E, Eo) <= tol, ("E", max_rel(E, Eo))
+    # the stored state: Hermite coefficients of each cell in its own frame, and the frame
+    cf, cg, fr = gs.state()
+    fo, go, uo, To = os_.regauged_state()
+    D = gs.D
+    Af = hermite_of_pops(fo, D)
+    Ag = hermite_of_pops(go, D)[:, : cg.shape[1]]
+    rho_scale = np.abs(ro)[:, None]
+    e_scale = (np.abs(ro) * np.abs(To))[:, None]
+    assert np.abs(cf - Af).max() <= 10 * tol * max(1.0, np.abs(Af / rho_scale).max()) * rho_scale.max()
+    assert (np.abs(cg - Ag) / e_scale).max() <= 10 * tol * max(1.0, (np.abs(Ag) / e_scale).max())
+    assert max_rel(fr[:, D], To) <= tol
+    for a in range(D):
+        assert np.abs(fr[:, a] - uo[:, a]).max() <= tol * max(1.0, np.abs(uo).max(), np.sqrt(To.max()))
+    # face predictors for the next step
+    xg, yg = gs.face_gauges()
+    xo, yo = os_.face_gauges()
+    assert max_rel(xg[:, -1], xo[:, -1]) <= 10 * tol
+    if D == 2:
+        assert max_rel(yg[:, -1], yo[:, -1]) <= 10 * tol
+
+
+def parity_cases_1d():
+    sod = I.sod_400()
+    lax, _ = I.paper_tube("lax", 150)
+    strong, _ = I.paper_tube("strong_shock", 120)
+    jet, _ = I.paper_tube("jet_1d", 160)
+    periodic = I.smooth_periodic(1, 97, 1, seed=5, amp=0.15)
+    tiny = I.shock_tube((1.0, 0.3, 1.0), (0.5, -0.2, 0.4), 1.4, 3)
+    return [("sod_400", sod, 0.5), ("lax", lax, 0.2), ("strong", strong, 0.2), ("jet", jet, 0.2),
+            ("periodic_97", periodic, 0.3), ("tiny_3", tiny, 0.3)]
+
+
+@pytest.mark.parametrize("name,pb,cfl", parity_cases_1d(), ids=[c[0] for c in parity_cases_1d()])
+@pytest.mark.parametrize("steps", [1, 12])
+def test_fp64_parity_1d(name, pb, cfl, steps):
+    kw = dict(tau=1e-5, cfl=cfl, fixed_iters=3, max_iter=8)
+    gs = gpu_for(pb, precision="fp64", **kw)
+    os_ = oracle_for(pb, **kw)
+    gs.step(steps)
+    os_.step(steps)
+    d = gs.sync()
+    st = os_.stats()
+    assert d["steps"] == st["steps"]
+    assert d["t"] == pytest.approx(st["t"], rel=1e-13)
+    assert d["face_iters"] == st["face_iters"] and d["fallbacks"] == st["fallbacks"]
+    assert d["nonphysical"] == st["nonphysical"] == 0
+    compare_fp64(gs, os_)
+
+
+def parity_cases_2d():
+    return [
+        ("quadrants_29x29", I.quadrants_2d(29, seed=0)),
+        ("lax_liu_24", I.lax_liu_2d(24)),
+        ("periodic_19x13", I.smooth_periodic(2, 19, 13, seed=2, amp=0.15)),
+        ("shocked_interface_37x13", I.shocked_interface_2d(37, 13, seed=1)),
+        ("jet_24", I.jet_2d(24, seed=3)),
+        ("strip_1x6", I.Problem(2, 1, 6, 0, 1, 0, 6, 1.4, np.linspace(1, 2, 6), np.zeros(6), np.linspace(-0.2, 0.2, 6),
+                                np.ones(6), bc=(I.PERIODIC, I.PERIODIC, I.TRANSMISSIVE, I.TRANSMISSIVE))),
+    ]
+
+
+@pytest.mark.parametrize("name,pb", parity_cases_2d(), ids=[c[0] for c in parity_cases_2d()])
+def test_fp64_parity_2d(name, pb):
+    kw = dict(tau=1e-5, cfl=0.2, fixed_iters=3, max_iter=8)
+    gs = gpu_for(pb, precision="fp64", **kw)
+    os_ = oracle_for(pb, **kw)
+    for chunk in (1, 3):
+        gs.step(chunk)
+        os_.step(chunk)
+        d = gs.sync()
+        st = os_.stats()
+        assert d["steps"] == st["steps"] and d["face_iters"] == st["face_iters"]
+        assert d["fallbacks"] == st["fallbacks"]
+        compare_fp64(gs, os_)
+
+
+def test_fp64_parity_converged_corrector():
+    """Convergence mode (tol 1e-10): iteration counts may differ by rounding, so the
+    bound is the corrector tolerance, not round-off."""
+    pb = I.sod_400()
+    kw = dict(tau=1e-5, cfl=0.5, t_end=0.2, tol=1e-10, max_iter=16)
+    gs = gpu_for(pb, precision="fp64", **kw)
+    os_ = oracle_for(pb, **kw)
+    gs.step(700)
+    os_.step(700)
+    d = gs.sync()
+    assert d["t"] == pytest.approx(0.2, abs=1e-14) and d["steps"] == os_.stats()["steps"]
+    compare_fp64(gs, os_, tol=1e-8)
+
+
+def shock_cell(r, start):
+    return start + int(np.argmax(np.abs(np.diff(r[start:]))))
+
+
+def test_fp32_against_fp64_oracle_sod():
+    pb = I.sod_400()
+    gs = gpu_for(pb, precision="fp32", tau=1e-5, cfl=0.5, t_end=0.2)
+    os_ = oracle_for(pb, tau=1e-5, cfl=0.5, t_end=0.2, tol=1e-10)
+    gs.step(700)
+    os_.step(700)
+    d = gs.sync()
+    assert d["status"] == pond.POND_OK, d
+    r, u, _, p = gs.primitive()
+    ro, uo, _, po = os_.primitive()
+    assert rel_l1(r, ro) < 1e-4 and rel_l1(p, po) < 1e-4
+    assert np.abs(u - uo).sum() / np.abs(uo).sum() < 1e-4
+    assert abs(shock_cell(r, 300) - shock_cell(ro, 300)) <= 1
+
+
+@pytest.mark.parametrize("seed", [0, 3])
+def test_fp32_against_fp64_oracle_quadrants(seed):
+    pb = I.quadrants_2d(32, seed=seed)
+    gs = gpu_for(pb, precision="fp32", tau=1e-5, cfl=0.2)
+    os_ = oracle_for(pb, tau=1e-5, cfl=0.2, tol=1e-10)
+    gs.step(40)
+    os_.step(40)
+    d = gs.sync()
+    assert d["status"] == pond.POND_OK, d
+    r, ux, uy, p = gs.primitive()
+    ro, uxo, uyo, po = os_.primitive()
+    assert rel_l1(r, ro) < 1e-4 and rel_l1(p, po) < 1e-4
+    sp, spo = np.hypot(ux, uy), np.hypot(uxo, uyo)
+    assert np.abs(sp - spo).sum() / np.abs(spo).sum() < 1e-4
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("fp32", 2e-6)])
+@pytest.mark.parametrize("dim", [1, 2])
+def test_conservation_periodic(precision, tol, dim):
+    pb = I.smooth_periodic(dim, 64 if dim == 1 else 24, 20, seed=7, amp=0.15)
+    gs = gpu_for(pb, precision=precision, tau=1e-4, cfl=0.3)
+    _, t0 = gs.moments()
+    gs.step(200 if dim == 1 else 40)
+    _, t1 = gs.moments()
+    assert gs.sync()["status"] == pond.POND_OK
+    for k in range(4):
+        if dim == 1 and k == 2:
+            continue
+        assert abs(t1[k] - t0[k]) <= tol * max(abs(t0[k]), t0[0]), (k, t0[k], t1[k])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_uniform_mach80_any_gauge(precision):
+    n, g, T = 16, 5.0 / 3.0, 0.02
+    u = 80 * np.sqrt(g * T)
+    N = n * n
+    pb = I.Problem(2, n, n, 0, 1, 0, 1, g, np.full(N, 2.0), np.full(N, u), np.full(N, -0.4 * u), np.full(N, 2.0 * T),
+                   bc=(I.PERIODIC,) * 4)
+    gs = gpu_for(pb, precision=precision, tau=1e-5, cfl=0.2, max_iter=40,
+                 tol=1e-9 if precision == "fp64" else 1e-6)
+    xg, yg = gs.face_gauges()
+    xg[:, 0] += 0.5 * np.sqrt(T)
+    yg[:, -1] *= 1.7
+    gs.set_face_gauges(xg, yg)
+    gs.step(20)
+    d = gs.sync()
+    assert d["status"] == pond.POND_OK, d
+    r, ux, uy, p = gs.primitive()
+    tol = 1e-9 if precision == "fp64" else 2e-5
+    assert max_rel(r, np.full(N, 2.0)) < tol and max_rel(p, np.full(N, 2.0 * T)) < 10 * tol
+    assert np.abs(ux - u).max() < tol * u and np.abs(uy + 0.4 * u).max() < tol * u
+
+
+def test_graph_replay_matches_single_launches():
+    pb = I.quadrants_2d(40, seed=3)
+    a = gpu_for(pb, precision="fp32", tau=1e-5, cfl=0.2)
+    b = gpu_for(pb, precision="fp32", tau=1e-5, cfl=0.2)
+    a.step(70)            # two captured 32-step graphs + 6 launches
+    for _ in range(70):
+        b.step(1)
+    ca, ga, fa = a.state()
+    cb, gb, fb = b.state()
+    assert np.array_equal(ca, cb) and np.array_equal(ga, gb) and np.array_equal(fa, fb)
+    assert a.launch_count() == b.launch_count()
+
+
+def test_nonphysical_input_is_reported():
+    pb = I.sod_400()
+    gs = pond.Solver(pb, precision="fp64", tau=1e-5, cfl=0.5)
+    rho = pb.rho.copy()
+    rho[17] = -1.0
+    gs.set_primitive(rho=rho)
+    d = gs.sync()
+    assert d["status"] == pond.POND_ERR_NONPHYSICAL and d["first_bad_cell"] == 17
+    # the device and the context stay usable
+    ok = gpu_for(pb, precision="fp64", tau=1e-5, cfl=0.5)
+    ok.step(3)
+    assert ok.sync()["status"] == pond.POND_OK
+
+
+def test_full_size_sampled_first_step():
+    """The bench workload (1024^2 quadrants, FP32 and FP64) checked on sampled cells: one
+    step depends only on a radius-3 neighbourhood, so the oracle runs that step on patches
+    cut from the same initial condition with the full grid's first time step."""
+    n, cfl = 1024, 0.2
+    pb = I.quadrants_2d(n, seed=0)
+    g = pb.gamma
+    T = pb.p / pb.rho
+    rate = ((np.maximum(np.abs(pb.ux), np.abs(pb.uy)) + np.sqrt(T) * 2.3344142183389773) / pb.dx).max()
+    dt = cfl / rate
+    rng = np.random.default_rng(0)
+    samples = [(int(i), int(j)) for i, j in rng.integers(0, n, (6, 2))] + [(511, 511), (512, 512), (0, 0), (n - 1, 700)]
+    results = {}
+    for prec in ("fp64", "fp32"):
+        gs = gpu_for(pb, precision=prec, tau=1e-5, cfl=cfl, fixed_iters=3, max_iter=8)
+        gs.step(1)
+        assert gs.sync()["dt"] > 0
+        results[prec] = gs.moments(totals=False)[0]
+        gs.close()
+    m = 4
+    for (i, j) in samples:
+        i0, i1 = max(0, i - m), min(n, i + m + 1)
+        j0, j1 = max(0, j - m), min(n, j + m + 1)
+        sub = lambda a: a.reshape(n, n)[j0:j1, i0:i1].ravel()
+        patch = I.Problem(2, i1 - i0, j1 - j0, 0, (i1 - i0) * pb.dx, 0, (j1 - j0) * pb.dy, g,
+                          sub(pb.rho), sub(pb.ux), sub(pb.uy), sub(pb.p))
+        os_ = oracle_for(patch, tau=1e-5, cfl=cfl, fixed_iters=3, max_iter=8)
+        os_.force_dt(dt)
+        os_.step(1)
+        ro = os_.conserved()
+        k_patch = (j - j0) * (i1 - i0) + (i - i0)
+        k = j * n + i
+        for fld in range(4):
+            ref = ro[fld][k_patch]
+            scale = max(abs(ref), abs(ro[0][k_patch]), abs(ro[3][k_patch]))
+            assert abs(results["fp64"][fld][k] - ref) <= FP64_TOL * scale, ("fp64", i, j, fld)
+            assert abs(results["fp32"][fld][k] - ref) <= 1e-5 * scale, ("fp32", i, j, fld)
