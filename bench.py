@@ -166,6 +166,8 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--fp64-steps", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true",
+                    help="FP32 timed steps only (no e2e, FP64 or CPU legs): the profiling case")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -222,6 +224,13 @@ def main():
     faces = d1["face_solves"] - d0["face_solves"]
     status_ok = d1["status"] == pond.POND_OK
     s.close()
+
+    if args.quick:
+        if rank == 0:
+            print(json.dumps({"quick": True, "value": value, "unit": "MLUPS", "ms_per_step": el_ms / args.steps,
+                              "face_ms": ms_face / args.steps, "cell_ms": ms_cell / args.steps,
+                              "passes_per_face": face_passes / max(faces, 1), "status_ok": status_ok}), flush=True)
+        return
 
     # ---- the same workload through the public API with host buffers (e2e)
     pin = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (pb.rho, pb.ux, pb.uy, pb.p)]

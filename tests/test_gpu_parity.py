@@ -30,16 +30,24 @@ def compare_fp64(gs, os_, tol=FP64_TOL, what="conserved"):
     assert np.abs(mx - mxo).max() <= tol * scale_m, ("mx", np.abs(mx - mxo).max() / scale_m)
     assert np.abs(my - myo).max() <= tol * scale_m, ("my", np.abs(my - myo).max() / scale_m)
     assert max_rel(E, Eo) <= tol, ("E", max_rel(E, Eo))
-    # the stored state: Hermite coefficients of each cell in its own frame, and the frame
+    # the stored state: Hermite coefficients of each cell in its own frame, and the frame.
+    # The oracle evaluates Eqs. (a0)-(a3) with lab-frame moments M_k, whose terms grow like
+    # rho |u|^k: its coefficient of order k carries a rounding error ~ eps rho (1 + M)^k
+    # (M = |u| / sqrt(T)), which bounds what can be compared at high Mach.
     cf, cg, fr = gs.state()
     fo, go, uo, To = os_.regauged_state()
     D = gs.D
     Af = hermite_of_pops(fo, D)
     Ag = hermite_of_pops(go, D)[:, : cg.shape[1]]
-    rho_scale = np.abs(ro)[:, None]
+    mach = np.sqrt((uo ** 2).sum(1) / To)
+    order = np.array([0, 1, 2, 3] if D == 1 else [0, 1, 1, 2, 2, 2, 3, 3, 3, 3])
+    cond = (1.0 + mach)[:, None] ** order[None, :]
+    allow_f = 10 * tol * np.abs(ro)[:, None] * np.maximum(1.0, np.abs(Af) / np.abs(ro)[:, None]) + 1e-14 * np.abs(ro)[:, None] * cond
+    assert (np.abs(cf - Af) <= allow_f).all(), np.abs(cf - Af).max()
     e_scale = (np.abs(ro) * np.abs(To))[:, None]
-    assert np.abs(cf - Af).max() <= 10 * tol * max(1.0, np.abs(Af / rho_scale).max()) * rho_scale.max()
-    assert (np.abs(cg - Ag) / e_scale).max() <= 10 * tol * max(1.0, (np.abs(Ag) / e_scale).max())
+    ng = cg.shape[1]
+    allow_g = 10 * tol * e_scale * np.maximum(1.0, np.abs(Ag) / e_scale) + 1e-14 * e_scale * cond[:, :ng]
+    assert (np.abs(cg - Ag) <= allow_g).all(), np.abs(cg - Ag).max()
     assert max_rel(fr[:, D], To) <= tol
     for a in range(D):
         assert np.abs(fr[:, a] - uo[:, a]).max() <= tol * max(1.0, np.abs(uo).max(), np.sqrt(To.max()))
