@@ -151,6 +151,9 @@ pond_status reset_clock(pond_state *s)
     c.dt = 0.0;
     c.t_end = s->opts.t_end;
     c.cfl = s->opts.cfl;
+    c.tau = s->tau;
+    c.dx = (s->grid.x1 - s->grid.x0) / double(s->grid.nx);
+    c.dy = s->D == 2 ? (s->grid.y1 - s->grid.y0) / double(s->grid.ny) : 1.0;
     pond::Diag d{};
     d.first_bad = -1;
     CUDA_TRY(cudaMemcpyAsync(s->clock, &c, sizeof(c), cudaMemcpyHostToDevice, s->stream));

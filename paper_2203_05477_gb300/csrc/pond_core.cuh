@@ -41,6 +41,29 @@ __host__ __device__ constexpr double hen(int k, int m)
     return k == 0 ? 1.0 : k == 1 ? he(1, m) : k == 2 ? he(2, m) * 0.5 : he(3, m) * (1.0 / 6.0);
 }
 
+// node tables for loops over m that are not unrolled: c_m, He_a(c_m)/a!, w_m He_a(c_m)
+template <typename R>
+struct NodeTab {
+    R c[4];
+    R hen[4][4];
+    R whe[4][4];
+};
+#define POND_NODE_TAB(T)                                                                               \
+    {{T(node_c(0)), T(node_c(1)), T(node_c(2)), T(node_c(3))},                                         \
+     {{T(hen(0, 0)), T(hen(1, 0)), T(hen(2, 0)), T(hen(3, 0))},                                        \
+      {T(hen(0, 1)), T(hen(1, 1)), T(hen(2, 1)), T(hen(3, 1))},                                        \
+      {T(hen(0, 2)), T(hen(1, 2)), T(hen(2, 2)), T(hen(3, 2))},                                        \
+      {T(hen(0, 3)), T(hen(1, 3)), T(hen(2, 3)), T(hen(3, 3))}},                                       \
+     {{T(node_w(0) * he(0, 0)), T(node_w(0) * he(1, 0)), T(node_w(0) * he(2, 0)), T(node_w(0) * he(3, 0))}, \
+      {T(node_w(1) * he(0, 1)), T(node_w(1) * he(1, 1)), T(node_w(1) * he(2, 1)), T(node_w(1) * he(3, 1))}, \
+      {T(node_w(2) * he(0, 2)), T(node_w(2) * he(1, 2)), T(node_w(2) * he(2, 2)), T(node_w(2) * he(3, 2))}, \
+      {T(node_w(3) * he(0, 3)), T(node_w(3) * he(1, 3)), T(node_w(3) * he(2, 3)), T(node_w(3) * he(3, 3))}}}
+__constant__ NodeTab<float> kTabF = POND_NODE_TAB(float);
+__constant__ NodeTab<double> kTabD = POND_NODE_TAB(double);
+template <typename R> __device__ __forceinline__ const NodeTab<R> &node_tab();
+template <> __device__ __forceinline__ const NodeTab<float> &node_tab<float>() { return kTabF; }
+template <> __device__ __forceinline__ const NodeTab<double> &node_tab<double>() { return kTabD; }
+
 // index of A_rs (r + s <= 3) in the packed 2D coefficient array: order n = r + s blocks,
 // s increasing inside a block: 00 | 10 01 | 20 11 02 | 30 21 12 03
 __host__ __device__ constexpr int hidx(int r, int s) { return (r + s) * (r + s + 1) / 2 + s; }
@@ -134,7 +157,8 @@ __device__ __forceinline__ R vanleer(R a, R b)
 {
     // (sgn a + sgn b)|a||b|/(|a|+|b|) = 2ab/(a+b) when ab > 0, else 0
     const R ab = a * b;
-    return ab > R(0) ? R(2) * ab / (a + b) : R(0);
+    if constexpr (sizeof(R) == 4) return ab > R(0) ? __fdividef(R(2) * ab, a + b) : R(0);
+    else return ab > R(0) ? R(2) * ab / (a + b) : R(0);
 }
 template <typename R>
 __device__ __forceinline__ R minmod(R a, R b)

@@ -25,11 +25,31 @@ enum { FLAG_NONPHYSICAL = 1u, FLAG_NOT_CONVERGED = 2u, FLAG_TIMEOUT = 4u };
 
 struct Clock {
     double t, dt, t_end, cfl;
+    double tau, dx, dy;
+    // constants of the step about to run, set with dt (Eqs. FinalUpdateDUGKS, Fbarplus,
+    // FluxTransf): update ca = (2tau-dt)/(2tau+dt), cb = 2dt/(2tau+dt); phi-bar-plus
+    // cp = (2tau-h)/(2tau+dt), ce = 3h/(2tau+dt); face populations wb = 2tau/(2tau+h),
+    // we = h/(2tau+h); departure offsets h/dx, h/dy; h = dt/2
+    double ca, cb, cp, ce, wb, we, h_dx, h_dy;
     long long steps;
     unsigned long long rate_bits;   // max CFL rate of the step being reduced (as double bits)
     unsigned int blocks_done;
     unsigned int pad;
 };
+
+__host__ __device__ inline void set_step_constants(Clock &c, double dt)
+{
+    const double tau = c.tau, h = 0.5 * dt;
+    c.dt = dt;
+    c.ca = (2.0 * tau - dt) / (2.0 * tau + dt);
+    c.cb = 2.0 * dt / (2.0 * tau + dt);
+    c.cp = (2.0 * tau - h) / (2.0 * tau + dt);
+    c.ce = 3.0 * h / (2.0 * tau + dt);
+    c.wb = 2.0 * tau / (2.0 * tau + h);
+    c.we = h / (2.0 * tau + h);
+    c.h_dx = h / c.dx;
+    c.h_dy = h / c.dy;
+}
 
 struct Diag {
     unsigned long long face_solves, face_iters, nonconv, fallbacks, nonphys;
@@ -224,80 +244,90 @@ __device__ __forceinline__ void corrector_pass(const StagedCell<D, R> *const *ce
 #pragma unroll
     for (int k = 0; k < NGC; ++k) Psi[k] = R(0);
 
-#pragma unroll
+    const NodeTab<R> &tab = node_tab<R>();
+#pragma unroll 1
     for (int m = 0; m < 4; ++m) {
-        const R vn = sqTl * R(node_c(m)) + un_abs;
+        const R vn = sqTl * tab.c[m] + un_abs;
         const bool left = vn > R(0);
         // departure point along the normal, in cells, from the upwind cell centre
         const R offn = (left ? R(0.5) : R(-0.5)) - vn * h_dn;
-        // outer normal neighbour and tangential neighbours of the upwind cell, in the frame
-        constexpr int NS = D == 2 ? 3 : 1;
-        R FS[NS][NFC], GS[NS][NGC];
-#pragma unroll
-        for (int q = 0; q < NS; ++q) {
-            const int slot = q == 0 ? (left ? 0 : 3) : (q == 1 ? (left ? 4 : 6) : (left ? 5 : 7));
-            Map1<R> X(R(1), R(0), R(0)), Y(R(1), R(0), R(0));
-            R tmp[NFC], tmpg[NGC];
-            cell_maps<D, R>(cells[slot]->T, dc[slot], Tl, invTl, rsqTl, dl, X, Y);
-            orient<D, 3, R>(cells[slot]->A, tmp, swap);
-            orient<D, 2, R>(cells[slot]->B, tmpg, swap);
-            shift_scale<D, 3, R>(tmp, X, Y, FS[q]);
-            shift_scale<D, 2, R>(tmpg, X, Y, GS[q]);
-        }
-        // select upwind (up), upstream (lo) and downstream (hi) along the normal
-        R Fup[NFC], Flo[NFC], Fhi[NFC], Gup[NGC], Glo[NGC], Ghi[NGC];
-#pragma unroll
-        for (int k = 0; k < NFC; ++k) {
-            Fup[k] = left ? FL[k] : FR[k];
-            Flo[k] = left ? FS[0][k] : FL[k];
-            Fhi[k] = left ? FR[k] : FS[0][k];
-        }
-#pragma unroll
-        for (int k = 0; k < NGC; ++k) {
-            Gup[k] = left ? GL[k] : GR[k];
-            Glo[k] = left ? GS[0][k] : GL[k];
-            Ghi[k] = left ? GR[k] : GS[0][k];
-        }
         if constexpr (D == 1) {
-            // populations at node m of the three cells (unweighted: the limiter is
-            // homogeneous of degree one, so the weight w_m factors out)
-            R fu = R(0), fl = R(0), fh = R(0), gu = R(0), gl = R(0), gh = R(0);
+            // outer normal neighbour of the upwind cell, in the frame
+            R FS[NFC], GS[NGC];
+            {
+                const int slot = left ? 0 : 3;
+                Map1<R> X(R(1), R(0), R(0)), Y(R(1), R(0), R(0));
+                cell_maps<D, R>(cells[slot]->T, dc[slot], Tl, invTl, rsqTl, dl, X, Y);
+                shift_scale<D, 3, R>(cells[slot]->A, X, Y, FS);
+                shift_scale<D, 2, R>(cells[slot]->B, X, Y, GS);
+            }
+            // populations at node m (unweighted: the limiter is homogeneous of degree one,
+            // so the weight w_m factors out) of L, R and the outer neighbour
+            R fL = R(0), fR = R(0), fS = R(0), gL = R(0), gR = R(0), gS = R(0);
 #pragma unroll
             for (int a = 0; a <= 3; ++a) {
-                const R hn = R(hen(a, m));
-                fu += Fup[a] * hn; fl += Flo[a] * hn; fh += Fhi[a] * hn;
-                if (a <= 2) { gu += Gup[a] * hn; gl += Glo[a] * hn; gh += Ghi[a] * hn; }
+                const R hn = tab.hen[m][a];
+                fL += FL[a] * hn; fR += FR[a] * hn; fS += FS[a] * hn;
+                if (a <= 2) { gL += GL[a] * hn; gR += GR[a] * hn; gS += GS[a] * hn; }
             }
+            const R fu = left ? fL : fR, fl = left ? fS : fL, fh = left ? fR : fS;
+            const R gu = left ? gL : gR, gl = left ? gS : gL, gh = left ? gR : gS;
             const R fb = fu + offn * limit<R>(limiter, fu - fl, fh - fu);
             const R gb = gu + offn * limit<R>(limiter, gu - gl, gh - gu);
 #pragma unroll
-            for (int a = 0; a <= 3; ++a) Phi[a] += R(node_w(m) * he(a, m)) * fb;
+            for (int a = 0; a <= 3; ++a) Phi[a] += tab.whe[m][a] * fb;
 #pragma unroll
-            for (int a = 0; a <= 2; ++a) Psi[a] += R(node_w(m) * he(a, m)) * gb;
+            for (int a = 0; a <= 2; ++a) Psi[a] += tab.whe[m][a] * gb;
         } else {
-            // column collapse C_b = sum_a A_ab He_a(c_m)/a! for the five cells
-            R Cu[4], Cl[4], Ch[4], Cm[4], Cp[4], Du[3], Dl[3], Dh[3], Dm[3], Dp[3];
+            // column collapse C_b = sum_a A_ab He_a(c_m)/a! of a coefficient set
+            auto collapse_f = [&](const R *A, R *C) {
 #pragma unroll
-            for (int b = 0; b <= 3; ++b) {
-                R cu = R(0), cl = R(0), ch = R(0), cm = R(0), cpp = R(0);
+                for (int b2 = 0; b2 <= 3; ++b2) {
+                    R acc = R(0);
 #pragma unroll
-                for (int a = 0; a + b <= 3; ++a) {
-                    const R hn = R(hen(a, m));
-                    cu += Fup[hidx(a, b)] * hn; cl += Flo[hidx(a, b)] * hn; ch += Fhi[hidx(a, b)] * hn;
-                    cm += FS[1][hidx(a, b)] * hn; cpp += FS[2][hidx(a, b)] * hn;
+                    for (int a2 = 0; a2 + b2 <= 3; ++a2) acc += A[hidx(a2, b2)] * tab.hen[m][a2];
+                    C[b2] = acc;
                 }
-                Cu[b] = cu; Cl[b] = cl; Ch[b] = ch; Cm[b] = cm; Cp[b] = cpp;
+            };
+            auto collapse_g = [&](const R *A, R *C) {
+#pragma unroll
+                for (int b2 = 0; b2 <= 2; ++b2) {
+                    R acc = R(0);
+#pragma unroll
+                    for (int a2 = 0; a2 + b2 <= 2; ++a2) acc += A[hidx(a2, b2)] * tab.hen[m][a2];
+                    C[b2] = acc;
+                }
+            };
+            R CL[4], CR[4], DL[3], DR[3];
+            collapse_f(FL, CL); collapse_f(FR, CR); collapse_g(GL, DL); collapse_g(GR, DR);
+            // outer normal neighbour (q = 0) and tangential neighbours (q = 1, 2) of the
+            // upwind cell: transformed into the frame and collapsed one at a time
+            R CS[3][4], DS[3][3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const int slot = q == 0 ? (left ? 0 : 3) : (q == 1 ? (left ? 4 : 6) : (left ? 5 : 7));
+                Map1<R> X(R(1), R(0), R(0)), Y(R(1), R(0), R(0));
+                R tmp[NFC], tmpg[NGC], tr[NFC], trg[NGC];
+                cell_maps<D, R>(cells[slot]->T, dc[slot], Tl, invTl, rsqTl, dl, X, Y);
+                orient<D, 3, R>(cells[slot]->A, tmp, swap);
+                orient<D, 2, R>(cells[slot]->B, tmpg, swap);
+                shift_scale<D, 3, R>(tmp, X, Y, tr);
+                shift_scale<D, 2, R>(tmpg, X, Y, trg);
+                collapse_f(tr, CS[q]);
+                collapse_g(trg, DS[q]);
+            }
+            R Cu[4], Cl[4], Ch[4], Du[3], Dl[3], Dh[3];
+#pragma unroll
+            for (int b2 = 0; b2 <= 3; ++b2) {
+                Cu[b2] = left ? CL[b2] : CR[b2];
+                Cl[b2] = left ? CS[0][b2] : CL[b2];
+                Ch[b2] = left ? CR[b2] : CS[0][b2];
             }
 #pragma unroll
-            for (int b = 0; b <= 2; ++b) {
-                R cu = R(0), cl = R(0), ch = R(0), cm = R(0), cpp = R(0);
-#pragma unroll
-                for (int a = 0; a + b <= 2; ++a) {
-                    const R hn = R(hen(a, m));
-                    cu += Gup[hidx(a, b)] * hn; cl += Glo[hidx(a, b)] * hn; ch += Ghi[hidx(a, b)] * hn;
-                    cm += GS[1][hidx(a, b)] * hn; cpp += GS[2][hidx(a, b)] * hn;
-                }
-                Du[b] = cu; Dl[b] = cl; Dh[b] = ch; Dm[b] = cm; Dp[b] = cpp;
+            for (int b2 = 0; b2 <= 2; ++b2) {
+                Du[b2] = left ? DL[b2] : DR[b2];
+                Dl[b2] = left ? DS[0][b2] : DL[b2];
+                Dh[b2] = left ? DR[b2] : DS[0][b2];
             }
             R S[4] = {R(0), R(0), R(0), R(0)}, SG[3] = {R(0), R(0), R(0)};
 #pragma unroll
@@ -306,31 +336,31 @@ __device__ __forceinline__ void corrector_pass(const StagedCell<D, R> *const *ce
                 const R offt = -vt * h_dt;
                 R fu = R(0), fl = R(0), fh = R(0), fm = R(0), fp = R(0);
 #pragma unroll
-                for (int b = 0; b <= 3; ++b) {
-                    const R hn = R(hen(b, n));
-                    fu += Cu[b] * hn; fl += Cl[b] * hn; fh += Ch[b] * hn; fm += Cm[b] * hn; fp += Cp[b] * hn;
+                for (int b2 = 0; b2 <= 3; ++b2) {
+                    const R hn = R(hen(b2, n));
+                    fu += Cu[b2] * hn; fl += Cl[b2] * hn; fh += Ch[b2] * hn; fm += CS[1][b2] * hn; fp += CS[2][b2] * hn;
                 }
                 R gu = R(0), gl = R(0), gh = R(0), gm = R(0), gp = R(0);
 #pragma unroll
-                for (int b = 0; b <= 2; ++b) {
-                    const R hn = R(hen(b, n));
-                    gu += Du[b] * hn; gl += Dl[b] * hn; gh += Dh[b] * hn; gm += Dm[b] * hn; gp += Dp[b] * hn;
+                for (int b2 = 0; b2 <= 2; ++b2) {
+                    const R hn = R(hen(b2, n));
+                    gu += Du[b2] * hn; gl += Dl[b2] * hn; gh += Dh[b2] * hn; gm += DS[1][b2] * hn; gp += DS[2][b2] * hn;
                 }
                 const R fb = fu + offn * limit<R>(limiter, fu - fl, fh - fu) + offt * limit<R>(limiter, fu - fm, fp - fu);
                 const R gb = gu + offn * limit<R>(limiter, gu - gl, gh - gu) + offt * limit<R>(limiter, gu - gm, gp - gu);
 #pragma unroll
-                for (int b = 0; b <= 3; ++b) S[b] += R(node_w(n) * he(b, n)) * fb;
+                for (int b2 = 0; b2 <= 3; ++b2) S[b2] += R(node_w(n) * he(b2, n)) * fb;
 #pragma unroll
-                for (int b = 0; b <= 2; ++b) SG[b] += R(node_w(n) * he(b, n)) * gb;
+                for (int b2 = 0; b2 <= 2; ++b2) SG[b2] += R(node_w(n) * he(b2, n)) * gb;
             }
 #pragma unroll
-            for (int a = 0; a <= 3; ++a)
+            for (int a2 = 0; a2 <= 3; ++a2)
 #pragma unroll
-                for (int b = 0; a + b <= 3; ++b) Phi[hidx(a, b)] += R(node_w(m) * he(a, m)) * S[b];
+                for (int b2 = 0; a2 + b2 <= 3; ++b2) Phi[hidx(a2, b2)] += tab.whe[m][a2] * S[b2];
 #pragma unroll
-            for (int a = 0; a <= 2; ++a)
+            for (int a2 = 0; a2 <= 2; ++a2)
 #pragma unroll
-                for (int b = 0; a + b <= 2; ++b) Psi[hidx(a, b)] += R(node_w(m) * he(a, m)) * SG[b];
+                for (int b2 = 0; a2 + b2 <= 2; ++b2) Psi[hidx(a2, b2)] += tab.whe[m][a2] * SG[b2];
         }
     }
 }
@@ -362,7 +392,10 @@ __device__ __forceinline__ bool pass_frame(const R *Phi, const R *Psi, R Tl, R C
 }
 
 template <int D, typename R>
-__global__ void __launch_bounds__(FaceTile<D>::THREADS)
+#ifndef POND_FACE_MIN_BLOCKS
+#define POND_FACE_MIN_BLOCKS 2
+#endif
+__global__ void __launch_bounds__(FaceTile<D>::THREADS, (D == 2 && sizeof(R) == 4) ? POND_FACE_MIN_BLOCKS : 1)
 face_kernel(const Params<D, R> P)
 {
     constexpr int TX = FaceTile<D>::TX, TY = FaceTile<D>::TY;
@@ -370,11 +403,9 @@ face_kernel(const Params<D, R> P)
     constexpr int NFC = NCoef<D, 3>::value, NGC = NCoef<D, 2>::value;
     __shared__ StagedCell<D, R> tile[BY * BX];
 
-    const double dt = P.clock->dt;
-    if (!(dt > 0.0)) return;  // t_end reached: the step is a no-op
-    const double h = 0.5 * dt, tau = P.tau;
-    const R cp = R((2.0 * tau - h) / (2.0 * tau + dt));
-    const R ce = R(3.0 * h / (2.0 * tau + dt));
+    const Clock &K = *P.clock;
+    if (!(K.dt > 0.0)) return;  // t_end reached: the step is a no-op
+    const R cp = R(K.cp), ce = R(K.ce);
 
     const long long i0 = (long long)blockIdx.x * TX, j0 = (long long)blockIdx.y * TY;
     // stage phi-bar-plus of the box [i0-2, i0+TX] x [j0-2, j0+TY] (1D: [i0-2, i0+TX])
@@ -425,8 +456,7 @@ face_kernel(const Params<D, R> P)
         double *Frm = dir == 0 ? P.xfr : P.yfr;
         const long long nf = dir == 0 ? P.nxf() : P.nyf();
         const int na = swap ? 1 : 0, ta = swap ? 0 : 1;  // normal / tangential axes
-        const double dn = swap ? P.dy : P.dx, dtg = swap ? P.dx : P.dy;
-        const R h_dn = R(h / dn), h_dt = R(D == 2 ? h / dtg : 0.0);
+        const R h_dn = R(swap ? K.h_dy : K.h_dx), h_dt = R(D == 2 ? (swap ? K.h_dx : K.h_dy) : 0.0);
         // face reference velocity: the predictor; all velocities below are relative to it
         double uref[D];
 #pragma unroll
@@ -441,7 +471,7 @@ face_kernel(const Params<D, R> P)
         R uref_t = R(0);
         if constexpr (D == 2) uref_t = R(uref[ta]);
         const R uref_n = R(uref[na]);
-        const R Cv = R(P.Cv);
+        const R Cv = R(P.Cv), tolR = R(P.tol);
 
         R dl[D], Tl = Tpred;
 #pragma unroll
@@ -491,10 +521,10 @@ face_kernel(const Params<D, R> P)
             if (P.fixed_iters > 0) {
                 done = iters >= P.fixed_iters;
             } else {
-                bool c = fabs(T1 - Tl) <= R(P.tol) * Tl;
+                bool c = fabs(T1 - Tl) <= tolR * Tl;
                 const R sq = sqrt(Tl);
 #pragma unroll
-                for (int a = 0; a < D; ++a) c = c && fabs(du[a]) <= R(P.tol) * sq;
+                for (int a = 0; a < D; ++a) c = c && fabs(du[a]) <= tolR * sq;
                 done = c;
             }
 #pragma unroll
@@ -518,11 +548,11 @@ face_kernel(const Params<D, R> P)
             R Fo[NFC], Go[NGC];
             shift_scale<D, 3, R>(Phi, X, Y, Fo);
             shift_scale<D, 2, R>(Psi, X, Y, Go);
-            const R wb = R(2.0 * tau / (2.0 * tau + h)), we = R(h / (2.0 * tau + h));
+            const R wb = R(K.wb), we = R(K.we);
             Fo[0] = wb * Fo[0] + we * out_rho;
 #pragma unroll
             for (int k = 1; k < NFC; ++k) Fo[k] = wb * Fo[k];
-            Go[0] = wb * Go[0] + we * R((P.Cv - 0.5 * D) * double(out_rho) * double(out_T));
+            Go[0] = wb * Go[0] + we * (Cv - R(0.5 * D)) * out_rho * out_T;
 #pragma unroll
             for (int k = 1; k < NGC; ++k) Go[k] = wb * Go[k];
             R Fw[NFC], Gw[NGC];
@@ -567,22 +597,24 @@ face_kernel(const Params<D, R> P)
 
 // ---------------------------------------------------------------- cell update
 
-// Adds -sign * (dt/dx_n) * H[v_n phi] for one face to the f (H) and g (G) Hermite moments
-// of the cell, phi given by face coefficients in the face frame.  The face populations are
-// first re-expressed in the cell frame (Eq. fluxEq), then multiplied by v_n = sqrt(T) c_n + u_n
+// Adds -scale * H[v_n phi] for one face to the f (H) and g (G) Hermite moments of the
+// cell, phi given by face coefficients in the face frame.  The face populations are first
+// re-expressed in the cell frame (Eq. fluxEq), then multiplied by v_n = sqrt(T) c_n + u_n
 // using c He_r(c) = He_{r+1}(c) + r He_{r-1}(c); He_4 vanishes on the D1Q4 nodes and the
 // Grad forms have no moments above their order, so the product closes on the same orders.
+// invTc, rsqTc: 1/T and 1/sqrt(T) of the cell frame.
 template <int D, typename R>
-__device__ __forceinline__ void add_face_flux(const Params<D, R> &P, const R *Fc, const R *Gc, const double *ub, double Tb,
-                                              const double *uc, double Tc, int axis, R scale, R sqTc, R un,
-                                              R *H, R *G)
+__device__ __forceinline__ void add_face_flux(const R *Fc, const R *Gc, const double *ub, double Tb,
+                                              const double *uc, double Tc, R invTc, R rsqTc, int axis, R scale,
+                                              R sqTc, R un, R *H, R *G)
 {
     constexpr int NFC = NCoef<D, 3>::value, NGC = NCoef<D, 2>::value;
-    const double invT = 1.0 / Tc, rsq = sqrt(invT);
-    const R s = R(sqrt(Tb * invT)), e = R((Tb - Tc) * invT);
-    Map1<R> X(s, e, R((ub[0] - uc[0]) * rsq));
+    const R Tbr = R(Tb), Tcr = R(Tc);
+    const R s = sqrt(Tbr * invTc), e = (Tbr - Tcr) * invTc;
+    // velocity differences in FP64: the frames can move at high Mach
+    Map1<R> X(s, e, R(ub[0] - uc[0]) * rsqTc);
     Map1<R> Y = X;
-    if (D == 2) Y = Map1<R>(s, e, R((ub[D - 1] - uc[D - 1]) * rsq));
+    if constexpr (D == 2) Y = Map1<R>(s, e, R(ub[1] - uc[1]) * rsqTc);
     R Fp[NFC], Gp[NGC];
     shift_scale<D, 3, R>(Fc, X, Y, Fp);
     shift_scale<D, 2, R>(Gc, X, Y, Gp);
@@ -639,9 +671,11 @@ template <int D>
 struct CellBlock { static constexpr int THREADS = 256; };
 
 // CFL rate of a cell frame: max over axes of (|u_a| + sqrt(T/T_L) max|c|)/dx_a
+template <typename R>
 __device__ __forceinline__ double cell_rate(const double *u, double T, double dx, double dy, int D)
 {
-    const double c = sqrt(T) * kCHi;
+    // FP64 populations: FP64 time step; FP32 populations: the root in FP32 is enough
+    const double c = (sizeof(R) == 8 ? sqrt(T) : double(sqrtf(float(T)))) * kCHi;
     double r = (fabs(u[0]) + c) / dx;
     if (D == 2) r = fmax(r, (fabs(u[1]) + c) / dy);
     return r;
@@ -664,7 +698,7 @@ __device__ __forceinline__ void reduce_rate_and_advance(Clock *clock, double rat
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_down_sync(0xffffffffu, r, o));
         if (threadIdx.x == 0) {
-            // non-negative doubles order like their bit patterns; NaN (bits above +inf) wins
+            // non-negative doubles order like their bit patterns
             atomicMax(&clock->rate_bits, (unsigned long long)__double_as_longlong(r));
             __threadfence();
             const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
@@ -686,7 +720,7 @@ __device__ __forceinline__ void reduce_rate_and_advance(Clock *clock, double rat
             if (t >= clock->t_end) dt = 0.0;
             else if (t + dt > clock->t_end) dt = clock->t_end - t;
         }
-        clock->dt = dt;
+        set_step_constants(*clock, dt);
         clock->rate_bits = 0ull;
         clock->blocks_done = 0u;
     }
@@ -694,26 +728,29 @@ __device__ __forceinline__ void reduce_rate_and_advance(Clock *clock, double rat
 
 // Step 3 of Sec. III.B.4 (flux into the cell frame, Eq. fluxEq; update, Eqs.
 // FinalUpdateDUGKS) fused with step 1 of the next step (re-expression in the new co-moving
-// frame, recovered in FP64 from the conserved moments) and the CFL reduction.
+// frame from the conserved moments) and the CFL reduction.  The frame (u, T) is held and
+// advanced in FP64 (u' = u + du, T' = T (1 + dT/T)); its increments are formed from the
+// Hermite moments relative to the old frame, so no kinetic energy of the frame enters.
 template <int D, typename R>
 __global__ void __launch_bounds__(CellBlock<D>::THREADS)
 cell_kernel(const Params<D, R> P)
 {
     constexpr int NFC = NCoef<D, 3>::value, NGC = NCoef<D, 2>::value;
-    const double dt = P.clock->dt;
-    if (!(dt > 0.0)) return;
+    const Clock &K = *P.clock;
+    if (!(K.dt > 0.0)) return;
     const long long n = P.ncell();
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double rate = 0.0;
     if (c < n) {
         const long long i = c % P.nx, j = c / P.nx;
-        double uc[D], Tc;
+        double uc[D];
 #pragma unroll
         for (int a = 0; a < D; ++a) uc[a] = P.sfr[a * n + c];
-        Tc = P.sfr[D * n + c];
+        const double Tc = P.sfr[D * n + c];
         const R rho = P.sf[c];
-        const double tau = P.tau;
-        const R ca = R((2.0 * tau - dt) / (2.0 * tau + dt)), cb = R(2.0 * dt / (2.0 * tau + dt));
+        const R ca = R(K.ca), cb = R(K.cb), Cv = R(P.Cv);
+        const R Tcr = R(Tc);
+        const R invTc = R(1) / Tcr, rsqTc = sqrt(invTc), sqTc = Tcr * rsqTc;
         // collision part of Eqs. (FinalUpdateDUGKS) in Hermite moments of the cell frame
         R H[NFC], G[NGC];
 #pragma unroll
@@ -724,10 +761,10 @@ cell_kernel(const Params<D, R> P)
         H[0] += cb * rho;
 #pragma unroll
         for (int k = 0; k < NGC; ++k) G[k] = ca * P.sg[k * n + c];
-        G[0] += cb * R((P.Cv - 0.5 * D) * double(rho) * Tc);
+        G[0] += cb * (Cv - R(0.5 * D)) * rho * Tcr;
         // fluxes through the 2D faces
-        const R sqTc = R(sqrt(Tc));
         const long long nxf = P.nxf();
+        const R sx = R(K.dt / P.dx);
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
             const long long f = j * (P.nx + 1) + i + side;
@@ -740,10 +777,11 @@ cell_kernel(const Params<D, R> P)
 #pragma unroll
             for (int a = 0; a < D; ++a) ub[a] = P.xfr[a * nxf + f];
             const double Tb = P.xfr[D * nxf + f];
-            add_face_flux<D, R>(P, Fc, Gc, ub, Tb, uc, Tc, 0, R((side ? 1.0 : -1.0) * dt / P.dx), sqTc, R(uc[0]), H, G);
+            add_face_flux<D, R>(Fc, Gc, ub, Tb, uc, Tc, invTc, rsqTc, 0, side ? sx : -sx, sqTc, R(uc[0]), H, G);
         }
         if constexpr (D == 2) {
             const long long nyf = P.nyf();
+            const R sy = R(K.dt / P.dy);
 #pragma unroll
             for (int side = 0; side < 2; ++side) {
                 const long long f = (j + side) * P.nx + i;
@@ -756,38 +794,44 @@ cell_kernel(const Params<D, R> P)
 #pragma unroll
                 for (int a = 0; a < D; ++a) ub[a] = P.yfr[a * nyf + f];
                 const double Tb = P.yfr[D * nyf + f];
-                add_face_flux<D, R>(P, Fc, Gc, ub, Tb, uc, Tc, 1, R((side ? 1.0 : -1.0) * dt / P.dy), sqTc, R(uc[1]), H, G);
+                add_face_flux<D, R>(Fc, Gc, ub, Tb, uc, Tc, invTc, rsqTc, 1, side ? sy : -sy, sqTc, R(uc[1]), H, G);
             }
         }
-        // step 1 of the next step: the new co-moving frame from the conserved moments, in FP64
-        const double rn = double(H[0]);
-        double du[D], k2 = 0.0, tr;
+        // step 1 of the next step: the new co-moving frame from the conserved moments
+        const R rn = H[0];
+        const R irn = R(1) / rn;
+        R du[D], k2 = R(0), trH;
         if constexpr (D == 1) {
-            du[0] = sqrt(Tc) * double(H[1]) / rn;
+            du[0] = sqTc * H[1] * irn;
             k2 = du[0] * du[0];
-            tr = double(H[2]) + rn;
+            trH = H[2];
         } else {
-            du[0] = sqrt(Tc) * double(H[hidx(1, 0)]) / rn;
-            du[1] = sqrt(Tc) * double(H[hidx(0, 1)]) / rn;
+            du[0] = sqTc * H[hidx(1, 0)] * irn;
+            du[1] = sqTc * H[hidx(0, 1)] * irn;
             k2 = du[0] * du[0] + du[1] * du[1];
-            tr = double(H[hidx(2, 0)]) + double(H[hidx(0, 2)]) + 2.0 * rn;
+            trH = H[hidx(2, 0)] + H[hidx(0, 2)];
         }
-        const double Tn = (0.5 * Tc * tr + double(G[0]) - 0.5 * rn * k2) / (P.Cv * rn);
+        // T'/T - 1 = (1/2 tr H + G0/T - (Cv - D/2) rho' - rho' |du|^2/(2T)) / (Cv rho')
+        const R dT = (R(0.5) * trH + G[0] * invTc - (Cv - R(0.5 * D)) * rn - R(0.5) * rn * k2 * invTc) / (Cv * rn);
+        const double Tn = Tc + Tc * double(dT);
         double un[D];
 #pragma unroll
-        for (int a = 0; a < D; ++a) un[a] = uc[a] + du[a];
-        bool ok = rn > 0.0 && Tn > 0.0 && isfinite(rn) && isfinite(Tn);
+        for (int a = 0; a < D; ++a) un[a] = uc[a] + double(du[a]);
+        const bool ok = rn > R(0) && Tn > 0.0 && isfinite(double(rn)) && isfinite(Tn);
         if (!ok) {
             atomicOr(&P.diag->flags, FLAG_NONPHYSICAL);
             atomicAdd(&P.diag->nonphys, 1ull);
             atomicCAS((unsigned long long *)&P.diag->first_bad, (unsigned long long)-1ll, (unsigned long long)c);
         }
-        // Grad projection into the new frame (f third order, g second order)
-        const double invT = 1.0 / Tn, rsq = sqrt(invT);
-        const R s = R(sqrt(Tc * invT)), e = R((Tc - Tn) * invT);
-        Map1<R> X(s, e, R(-du[0] * rsq));
+        // Grad projection into the new frame (f third order, g second order):
+        // s^2 = T/T' = 1/(1 + dT/T), e = s^2 - 1, d = -du/sqrt(T')
+        const R Tr = R(1) + dT;
+        const R s2 = R(1) / Tr;
+        const R s = sqrt(s2), e = -dT * s2;
+        const R rsqn = rsqTc * s;
+        Map1<R> X(s, e, -du[0] * rsqn);
         Map1<R> Y = X;
-        if (D == 2) Y = Map1<R>(s, e, R(-du[D - 1] * rsq));
+        if constexpr (D == 2) Y = Map1<R>(s, e, -du[1] * rsqn);
         R Ho[NFC], Go[NGC];
         shift_scale<D, 3, R>(H, X, Y, Ho);
         shift_scale<D, 2, R>(G, X, Y, Go);
@@ -801,7 +845,7 @@ cell_kernel(const Params<D, R> P)
 #pragma unroll
         for (int a = 0; a < D; ++a) P.sfr[a * n + c] = un[a];
         P.sfr[D * n + c] = Tn;
-        rate = ok ? cell_rate(un, Tn, P.dx, P.dy, D) : __longlong_as_double(0x7ff8000000000000ll);
+        rate = ok ? cell_rate<R>(un, Tn, P.dx, P.dy, D) : 0.0;
     }
     reduce_rate_and_advance(P.clock, rate, true);
 }
@@ -834,7 +878,7 @@ __global__ void init_cells_kernel(const Params<D, R> P, const double *rho, const
             atomicAdd(&P.diag->nonphys, 1ull);
             atomicCAS((unsigned long long *)&P.diag->first_bad, (unsigned long long)-1ll, (unsigned long long)c);
         }
-        rate = ok ? cell_rate(u, T, P.dx, P.dy, D) : __longlong_as_double(0x7ff8000000000000ll);
+        rate = ok ? cell_rate<R>(u, T, P.dx, P.dy, D) : 0.0;
     }
     reduce_rate_and_advance(P.clock, rate, false);
 }
