@@ -126,6 +126,36 @@ def cpu_baseline(pb_full, steps, target_s=12.0):
             "sample": "%dx%d centre patch of the workload, %d steps, FP64, single thread, %.1f s" % (side, side, done, el)}
 
 
+TUBE_BYTES_PER_CELL = 112  # state (3+3 FP32 + 2 FP64) and face predictor (2 FP64), read and written
+
+
+def bench_tubes(args, n_tubes=4096, seed=0):
+    """The batched-tube workload: 4096 D1Q4 tubes of 200-8000 cells (seeded states with density
+    and pressure ratios up to 1e5 and velocity jumps up to Mach 20), FP32, one launch per call."""
+    import torch
+    import paper_2203_05477_gb300 as pond
+    from paper_2203_05477_gb300 import inputs as I
+    bt = I.tube_batch(n_tubes, seed=seed)
+    rho, ux, p = I.tube_batch_fields(bt)
+    s = pond.BatchSolver(bt.lengths, bt.gammas, precision="fp32", tau=1e-5, cfl=0.2, max_iter=16)
+    s.set_primitive(rho, ux, None, p)
+    s.step(max(1, args.warmup))
+    d0 = s.sync()
+    torch.cuda.synchronize()
+    steps = args.tube_steps
+    ms, _ = s.step_timed(steps)
+    d1 = s.sync()
+    ncell = int(bt.lengths.sum())
+    mlups = ncell * steps / (ms * 1e-3) / 1e6
+    gbs = TUBE_BYTES_PER_CELL * ncell * steps / (ms * 1e-3) / 1e9
+    out = {"workload": "tubes_4096_seed%d" % seed, "cells": ncell, "steps": steps, "value": mlups, "unit": "MLUPS",
+           "ms_per_step": ms / steps, "hbm_gbs": gbs, "bytes_per_cell_update": TUBE_BYTES_PER_CELL,
+           "launches": 1, "passes_per_face": (d1["face_iters"] - d0["face_iters"]) / max(1, d1["face_solves"] - d0["face_solves"]),
+           "nonphysical_events": d1["nonphysical"], "status_ok": d1["status"] == pond.POND_OK}
+    s.close()
+    return out
+
+
 def run_reference(args, rank, world):
     """Reference arm: the FP64 CPU oracle (the paper ships no code) on host cores."""
     if rank != 0:
@@ -166,6 +196,9 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--fp64-steps", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tube-steps", type=int, default=100)
+    ap.add_argument("--workload", default="quadrants", choices=["quadrants", "tubes"],
+                    help="tubes: only the batched-tube measurement (profiling case)")
     ap.add_argument("--quick", action="store_true",
                     help="FP32 timed steps only (no e2e, FP64 or CPU legs): the profiling case")
     args = ap.parse_args()
@@ -186,6 +219,10 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     _build.build()
     pk, pk_kind = peaks()
+    if args.workload == "tubes":
+        if rank == 0:
+            print(json.dumps(bench_tubes(args)), flush=True)
+        return
     n = args.n
     pb = I.quadrants_2d(n, seed=args.seed + rank)
     ncell = n * n
@@ -293,6 +330,9 @@ def main():
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
+    tubes = bench_tubes(args)
+    tubes["hbm_frac"] = tubes["hbm_gbs"] / hbm_peak
+    line["tubes"] = tubes
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(pb, steps=20)
     print(json.dumps(line), flush=True)

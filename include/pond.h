@@ -144,6 +144,22 @@ pond_status pond_get_state(pond_state *s, double *coef_f, double *coef_g, double
 pond_status pond_get_face_gauges(pond_state *s, double *xg, double *yg);
 pond_status pond_set_face_gauges(pond_state *s, const double *xg, const double *yg);
 
+/* Batched 1D shock tubes (D1Q4): n_tubes independent tubes, tube k with lengths[k] cells
+ * of width dx[k] (NULL: 1/lengths[k], i.e. every tube spans [0, 1]) and ratio of specific
+ * heats gammas[k], transmissive ends, one relaxation time tau.  Each tube keeps its own
+ * time and CFL time step.  The other calls take concatenated arrays (tube after tube, x
+ * fastest): pond_set_primitive (uy NULL), pond_moments (my left zero; totals summed over
+ * tubes), pond_get_state, pond_get_face_gauges (tube k has lengths[k] + 1 faces).
+ * pond_step(n) advances every tube by n of its own steps in one persistent kernel launch
+ * (one CTA per tube, no inter-CTA synchronization).  Used for the batched-tube workload of
+ * the paper's 1D benchmarks (Sec. IV.A-IV.B). */
+pond_status pond_init_batch(int64_t n_tubes, const int64_t *lengths, const double *gammas, const double *dx,
+                            double tau, const pond_options *opts, pond_state **out);
+
+/* Per-tube simulated time t[k] and next time step dt[k] of a batch (host arrays, may be
+ * NULL); waits for the stream. */
+pond_status pond_batch_times(pond_state *s, double *t, double *dt);
+
 /* Waits for the stream and reports the device diagnostics.  Returns
  * POND_ERR_NONPHYSICAL if any cell or face was non-physical, POND_ERR_NOT_CONVERGED if
  * strict_convergence is set and a face stopped at max_iter, else POND_OK. */

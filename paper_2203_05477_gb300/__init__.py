@@ -88,6 +88,9 @@ def _load():
             "pond_set_face_gauges": (ctypes.c_int, [vp, vp, vp]),
             "pond_sync": (ctypes.c_int, [vp, ctypes.POINTER(pond_diag)]),
             "pond_launch_count": (ctypes.c_int64, [vp]),
+            "pond_init_batch": (ctypes.c_int, [ctypes.c_int64, vp, vp, vp, ctypes.c_double,
+                                               ctypes.POINTER(pond_options), ctypes.POINTER(vp)]),
+            "pond_batch_times": (ctypes.c_int, [vp, vp, vp]),
             "pond_destroy": (None, [vp]),
             "pond_last_error": (ctypes.c_char_p, []),
         }
@@ -275,3 +278,69 @@ class Solver:
 
     def launch_count(self):
         return int(self.lib.pond_launch_count(self.h))
+
+
+class BatchSolver(Solver):
+    """Many independent 1D shock tubes (D1Q4) advanced by one persistent launch per call."""
+
+    def __init__(self, lengths, gammas, *, tau, cfl, dx=None, precision="fp32", limiter=POND_VANLEER,
+                 tol=None, max_iter=16, fixed_iters=0, stream=None, torch_alloc=True):
+        import torch
+        lib = _load()
+        self.lengths = np.ascontiguousarray(lengths, dtype=np.int64)
+        self.gammas = np.ascontiguousarray(gammas, dtype=np.float64)
+        self.dxs = None if dx is None else np.ascontiguousarray(dx, dtype=np.float64)
+        self.n_tubes = len(self.lengths)
+        self.D = 1
+        self.prec = POND_FP32 if precision in ("fp32", POND_FP32) else POND_FP64
+        self.device = torch.cuda.current_device()
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        o = pond_options()
+        o.precision = self.prec
+        o.limiter = int(limiter)
+        o.cfl = float(cfl)
+        o.tol = float(tol if tol is not None else (1e-10 if self.prec == POND_FP64 else 1e-6))
+        o.max_iter = int(max_iter)
+        o.fixed_iters = int(fixed_iters)
+        o.stream = self.stream.cuda_stream
+        self._alloc = _TorchAllocator(self.device, self.stream) if torch_alloc else None
+        if self._alloc:
+            o.alloc = self._alloc.alloc_fn
+            o.free = self._alloc.free_fn
+        self._opts = o
+        self.h = ctypes.c_void_p()
+        _check(lib.pond_init_batch(self.n_tubes, _ptr(self.lengths), _ptr(self.gammas), _ptr(self.dxs), float(tau),
+                                   ctypes.byref(o), ctypes.byref(self.h)))
+        self.lib = lib
+        self.ncell = int(self.lengths.sum())
+        self.nx, self.ny = self.ncell, 1
+        self.nfc, self.ngc = 4, 3
+        self.offsets = np.concatenate([[0], np.cumsum(self.lengths)])
+
+    def set_primitive(self, rho, ux, uy=None, p=None):
+        vals = [rho, ux, None, p]
+        on_dev = not isinstance(rho, np.ndarray)
+        if not on_dev:
+            vals = [None if v is None else np.ascontiguousarray(v, dtype=np.float64) for v in vals]
+        self._keep = vals
+        _check(self.lib.pond_set_primitive(self.h, *[_ptr(v) for v in vals], int(on_dev)))
+
+    def times(self):
+        t = np.zeros(self.n_tubes)
+        dt = np.zeros(self.n_tubes)
+        _check(self.lib.pond_batch_times(self.h, _ptr(t), _ptr(dt)))
+        return t, dt
+
+    def face_gauges(self):
+        g = np.zeros((int((self.lengths + 1).sum()), 2))
+        _check(self.lib.pond_get_face_gauges(self.h, _ptr(g), None))
+        return g, None
+
+    def primitive_tube(self, k, gamma):
+        (rho, mx, _, E), _ = self.moments(totals=False)
+        a, b = self.offsets[k], self.offsets[k + 1]
+        r, m, e = rho[a:b], mx[a:b], E[a:b]
+        cv = 1.0 / (gamma - 1.0)
+        u = m / r
+        T = (e - 0.5 * m * m / r) / (cv * r)
+        return r, u, r * T

@@ -10,12 +10,13 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <cmath>
 #include <type_traits>
 #include <new>
 #include <vector>
 
 #include "../../include/pond.h"
-#include "pond_kernels.cuh"
+#include "pond_batch.cuh"
 
 namespace {
 
@@ -61,6 +62,11 @@ struct pond_state {
     int64_t launches = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
+    // batched tubes
+    bool batch = false;
+    int64_t n_tubes = 0, ncell = 0, nface = 0, steps_taken = 0;
+    int cur = 0;
+    alignas(16) unsigned char tparams[sizeof(pond::TubeParams<double>)];
 };
 
 namespace {
@@ -345,6 +351,226 @@ pond_status face_gauges_impl(pond_state *s, double *xg, double *yg, const double
     return POND_OK;
 }
 
+// ------------------------------------------------------------------ batched tubes
+
+template <typename R>
+pond::TubeParams<R> &tparams_of(pond_state *s) { return *reinterpret_cast<pond::TubeParams<R> *>(s->tparams); }
+
+template <typename R>
+pond_status batch_setup(pond_state *s, const int64_t *lengths, const double *gammas, const double *dxs)
+{
+    using TP = pond::TubeParams<R>;
+    TP P{};
+    const int64_t nt = s->n_tubes;
+    std::vector<long long> coff(nt), foff(nt);
+    std::vector<int> len(nt), order(nt);
+    std::vector<double> cv(nt), dx(nt);
+    long long nc = 0, nf = 0;
+    for (int64_t k = 0; k < nt; ++k) {
+        coff[k] = nc;
+        foff[k] = nf;
+        len[k] = int(lengths[k]);
+        nc += lengths[k];
+        nf += lengths[k] + 1;
+        cv[k] = 1.0 / (gammas[k] - 1.0);
+        dx[k] = dxs ? dxs[k] : 1.0 / double(lengths[k]);
+        order[k] = int(k);
+    }
+    // longest tubes first: the CTA scheduler then balances the rest
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return len[a] > len[b]; });
+    s->ncell = nc;
+    s->nface = nf;
+    size_t off = 0;
+    auto take = [&](size_t b) { size_t o = off; off = align_up(off + b, 256); return o; };
+    const size_t o_coff = take(8 * nt), o_foff = take(8 * nt), o_len = take(4 * nt), o_ord = take(4 * nt);
+    const size_t o_cv = take(8 * nt), o_dx = take(8 * nt), o_t = take(8 * nt), o_dt = take(8 * nt), o_tot = take(32 * nt);
+    size_t o_sf[2], o_sg[2], o_sfr[2];
+    for (int b = 0; b < 2; ++b) {
+        o_sf[b] = take(sizeof(R) * 3 * nc);
+        o_sg[b] = take(sizeof(R) * 3 * nc);
+        o_sfr[b] = take(8 * 2 * nc);
+    }
+    const size_t o_fu = take(8 * nf), o_fT = take(8 * nf);
+    const size_t o_diag = take(sizeof(pond::Diag)), o_clock = take(sizeof(pond::Clock));
+    const size_t stage = std::max<size_t>(4 * size_t(nc), 7 * size_t(nc)) + 2 * size_t(nf) + 8;
+    const size_t o_stage = take(8 * stage);
+    s->bytes = off;
+    s->base = static_cast<char *>(dev_alloc(s, off));
+    if (!s->base) return fail(POND_ERR_OOM, "device allocation of %zu bytes failed", off);
+    char *B = s->base;
+    CUDA_TRY(cudaMemsetAsync(B, 0, off, s->stream));
+    CUDA_TRY(cudaMemcpyAsync(B + o_coff, coff.data(), 8 * nt, cudaMemcpyHostToDevice, s->stream));
+    CUDA_TRY(cudaMemcpyAsync(B + o_foff, foff.data(), 8 * nt, cudaMemcpyHostToDevice, s->stream));
+    CUDA_TRY(cudaMemcpyAsync(B + o_len, len.data(), 4 * nt, cudaMemcpyHostToDevice, s->stream));
+    CUDA_TRY(cudaMemcpyAsync(B + o_ord, order.data(), 4 * nt, cudaMemcpyHostToDevice, s->stream));
+    CUDA_TRY(cudaMemcpyAsync(B + o_cv, cv.data(), 8 * nt, cudaMemcpyHostToDevice, s->stream));
+    CUDA_TRY(cudaMemcpyAsync(B + o_dx, dx.data(), 8 * nt, cudaMemcpyHostToDevice, s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));  // the host vectors go out of scope
+    P.n_tubes = int(nt);
+    P.cell_off = reinterpret_cast<const long long *>(B + o_coff);
+    P.face_off = reinterpret_cast<const long long *>(B + o_foff);
+    P.len = reinterpret_cast<const int *>(B + o_len);
+    P.order = reinterpret_cast<const int *>(B + o_ord);
+    P.Cv = reinterpret_cast<const double *>(B + o_cv);
+    P.dx = reinterpret_cast<const double *>(B + o_dx);
+    P.t = reinterpret_cast<double *>(B + o_t);
+    P.dt = reinterpret_cast<double *>(B + o_dt);
+    P.totals = reinterpret_cast<double *>(B + o_tot);
+    for (int b = 0; b < 2; ++b) {
+        P.sf[b] = reinterpret_cast<R *>(B + o_sf[b]);
+        P.sg[b] = reinterpret_cast<R *>(B + o_sg[b]);
+        P.sfr[b] = reinterpret_cast<double *>(B + o_sfr[b]);
+    }
+    P.fu = reinterpret_cast<double *>(B + o_fu);
+    P.fT = reinterpret_cast<double *>(B + o_fT);
+    P.diag = reinterpret_cast<pond::Diag *>(B + o_diag);
+    P.tau = s->tau;
+    P.cfl = s->opts.cfl;
+    P.limiter = s->opts.limiter;
+    P.tol = s->opts.tol;
+    P.max_iter = s->opts.max_iter;
+    P.fixed_iters = s->opts.fixed_iters;
+    P.ncell = nc;
+    P.nface = nf;
+    s->diag = P.diag;
+    s->clock = reinterpret_cast<pond::Clock *>(B + o_clock);
+    s->stage = reinterpret_cast<double *>(B + o_stage);
+    s->stage_doubles = stage;
+    new (s->tparams) TP(P);
+    return POND_OK;
+}
+
+template <typename R>
+pond_status batch_set_primitive(pond_state *s, const double *rho, const double *ux, const double *p, int on_device)
+{
+    auto &P = tparams_of<R>(s);
+    const long long n = s->ncell;
+    const double *dr = rho, *du = ux, *dp = p;
+    if (!on_device) {
+        CUDA_TRY(cudaMemcpyAsync(s->stage, rho, 8 * n, cudaMemcpyHostToDevice, s->stream));
+        CUDA_TRY(cudaMemcpyAsync(s->stage + n, ux, 8 * n, cudaMemcpyHostToDevice, s->stream));
+        CUDA_TRY(cudaMemcpyAsync(s->stage + 2 * n, p, 8 * n, cudaMemcpyHostToDevice, s->stream));
+        dr = s->stage; du = s->stage + n; dp = s->stage + 2 * n;
+    }
+    pond::Diag d{};
+    d.first_bad = -1;
+    CUDA_TRY(cudaMemcpyAsync(s->diag, &d, sizeof(d), cudaMemcpyHostToDevice, s->stream));
+    s->cur = 0;
+    s->steps_taken = 0;
+    pond::tube_init_kernel<R><<<unsigned(s->n_tubes), pond::kTubeThreads, 0, s->stream>>>(P, 0, dr, du, dp);
+    s->launches += 1;
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return POND_OK;
+}
+
+template <typename R>
+pond_status batch_step(pond_state *s, int64_t n_steps, double *ms)
+{
+    if (n_steps <= 0) return POND_OK;
+    auto &P = tparams_of<R>(s);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (ms) {
+        CUDA_TRY(cudaEventCreate(&e0));
+        CUDA_TRY(cudaEventCreate(&e1));
+        CUDA_TRY(cudaEventRecord(e0, s->stream));
+    }
+    pond::tube_kernel<R><<<unsigned(s->n_tubes), pond::kTubeThreads, 0, s->stream>>>(P, int(n_steps), s->cur);
+    s->launches += 1;
+    CUDA_TRY(cudaGetLastError());
+    s->cur ^= int(n_steps & 1);
+    s->steps_taken += n_steps;
+    if (ms) {
+        CUDA_TRY(cudaEventRecord(e1, s->stream));
+        CUDA_TRY(cudaEventSynchronize(e1));
+        float a = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&a, e0, e1));
+        ms[0] += a;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    return POND_OK;
+}
+
+template <typename R>
+pond_status batch_moments(pond_state *s, double *rho, double *mx, double *my, double *E, double *totals, int on_device)
+{
+    auto &P = tparams_of<R>(s);
+    const long long n = s->ncell;
+    double *o[3] = {rho, mx, E};
+    double *d[3];
+    for (int k = 0; k < 3; ++k) d[k] = (on_device && o[k]) ? o[k] : (o[k] ? s->stage + k * n : nullptr);
+    pond::tube_conserved_kernel<R><<<unsigned(s->n_tubes), pond::kTubeThreads, 0, s->stream>>>(P, s->cur, d[0], d[1], d[2]);
+    s->launches += 1;
+    CUDA_TRY(cudaGetLastError());
+    if (my) {
+        if (on_device) CUDA_TRY(cudaMemsetAsync(my, 0, 8 * n, s->stream));
+        else std::memset(my, 0, 8 * n);
+    }
+    if (!on_device)
+        for (int k = 0; k < 3; ++k)
+            if (o[k]) CUDA_TRY(cudaMemcpyAsync(o[k], d[k], 8 * n, cudaMemcpyDeviceToHost, s->stream));
+    if (totals) {
+        std::vector<double> tt(size_t(4 * s->n_tubes));
+        CUDA_TRY(cudaMemcpyAsync(tt.data(), P.totals, 32 * s->n_tubes, cudaMemcpyDeviceToHost, s->stream));
+        CUDA_TRY(cudaStreamSynchronize(s->stream));
+        for (int q = 0; q < 4; ++q) {  // Neumaier summation over tubes
+            double sum = 0.0, comp = 0.0;
+            for (int64_t k = 0; k < s->n_tubes; ++k) {
+                const double v = tt[size_t(4 * k + q)], t2 = sum + v;
+                comp += std::fabs(sum) >= std::fabs(v) ? (sum - t2) + v : (v - t2) + sum;
+                sum = t2;
+            }
+            totals[q] = sum + comp;
+        }
+    }
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return POND_OK;
+}
+
+template <typename R>
+pond_status batch_get_state(pond_state *s, double *cf, double *cg, double *fr)
+{
+    auto &P = tparams_of<R>(s);
+    const long long n = s->ncell;
+    double *dcf = s->stage, *dcg = s->stage + 4 * n, *dfr = s->stage + 7 * n;
+    if (s->stage_doubles < size_t(9 * n)) return fail(POND_ERR_OOM, "staging too small");
+    pond::tube_export_kernel<R><<<unsigned((n + 255) / 256), 256, 0, s->stream>>>(P, s->cur, dcf, dcg, dfr);
+    s->launches += 1;
+    CUDA_TRY(cudaGetLastError());
+    if (cf) CUDA_TRY(cudaMemcpyAsync(cf, dcf, 8 * 4 * n, cudaMemcpyDeviceToHost, s->stream));
+    if (cg) CUDA_TRY(cudaMemcpyAsync(cg, dcg, 8 * 3 * n, cudaMemcpyDeviceToHost, s->stream));
+    if (fr) CUDA_TRY(cudaMemcpyAsync(fr, dfr, 8 * 2 * n, cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return POND_OK;
+}
+
+template <typename R>
+pond_status batch_face_gauges(pond_state *s, double *out, const double *in)
+{
+    auto &P = tparams_of<R>(s);
+    const long long nf = s->nface;
+    std::vector<double> u(nf), T(nf);
+    if (in) {
+        for (long long f = 0; f < nf; ++f) { u[f] = in[2 * f]; T[f] = in[2 * f + 1]; }
+        CUDA_TRY(cudaMemcpyAsync(P.fu, u.data(), 8 * nf, cudaMemcpyHostToDevice, s->stream));
+        CUDA_TRY(cudaMemcpyAsync(P.fT, T.data(), 8 * nf, cudaMemcpyHostToDevice, s->stream));
+        CUDA_TRY(cudaStreamSynchronize(s->stream));
+    } else {
+        CUDA_TRY(cudaMemcpyAsync(u.data(), P.fu, 8 * nf, cudaMemcpyDeviceToHost, s->stream));
+        CUDA_TRY(cudaMemcpyAsync(T.data(), P.fT, 8 * nf, cudaMemcpyDeviceToHost, s->stream));
+        CUDA_TRY(cudaStreamSynchronize(s->stream));
+        for (long long f = 0; f < nf; ++f) { out[2 * f] = u[f]; out[2 * f + 1] = T[f]; }
+    }
+    return POND_OK;
+}
+
+template <typename Fn>
+pond_status dispatch_batch(pond_state *s, Fn &&fn)
+{
+    return s->prec == POND_FP32 ? fn(float{}) : fn(double{});
+}
+
 template <typename Fn>
 pond_status dispatch(pond_state *s, Fn &&fn)
 {
@@ -414,6 +640,7 @@ pond_status pond_set_primitive(pond_state *s, const double *rho, const double *u
 {
     if (pond_status st = check_state(s)) return st;
     if (!rho || !ux || !p || (s->D == 2 && !uy)) return fail(POND_ERR_INVALID_ARG, "rho, ux, p (and uy in 2D) must not be NULL");
+    if (s->batch) return dispatch_batch(s, [&](auto r) { return batch_set_primitive<decltype(r)>(s, rho, ux, p, on_device); });
     return dispatch(s, [&](auto d, auto r) { return set_primitive_impl<decltype(d)::value, decltype(r)>(s, rho, ux, uy, p, on_device); });
 }
 
@@ -421,6 +648,7 @@ pond_status pond_step(pond_state *s, int64_t n_steps)
 {
     if (pond_status st = check_state(s)) return st;
     if (n_steps < 0) return fail(POND_ERR_INVALID_ARG, "n_steps must be >= 0");
+    if (s->batch) return dispatch_batch(s, [&](auto r) { return batch_step<decltype(r)>(s, n_steps, nullptr); });
     return dispatch(s, [&](auto d, auto r) { return step_impl<decltype(d)::value, decltype(r)>(s, n_steps); });
 }
 
@@ -428,18 +656,21 @@ pond_status pond_step_timed(pond_state *s, int64_t n_steps, double ms[2])
 {
     if (pond_status st = check_state(s)) return st;
     if (n_steps < 0 || !ms) return fail(POND_ERR_INVALID_ARG, "n_steps must be >= 0 and ms not NULL");
+    if (s->batch) return dispatch_batch(s, [&](auto r) { return batch_step<decltype(r)>(s, n_steps, ms); });
     return dispatch(s, [&](auto d, auto r) { return step_timed_impl<decltype(d)::value, decltype(r)>(s, n_steps, ms); });
 }
 
 pond_status pond_moments(pond_state *s, double *rho, double *mx, double *my, double *E, double totals[4], int on_device)
 {
     if (pond_status st = check_state(s)) return st;
+    if (s->batch) return dispatch_batch(s, [&](auto r) { return batch_moments<decltype(r)>(s, rho, mx, my, E, totals, on_device); });
     return dispatch(s, [&](auto d, auto r) { return moments_impl<decltype(d)::value, decltype(r)>(s, rho, mx, my, E, totals, on_device); });
 }
 
 pond_status pond_get_state(pond_state *s, double *coef_f, double *coef_g, double *frame)
 {
     if (pond_status st = check_state(s)) return st;
+    if (s->batch) return dispatch_batch(s, [&](auto r) { return batch_get_state<decltype(r)>(s, coef_f, coef_g, frame); });
     return dispatch(s, [&](auto d, auto r) { return get_state_impl<decltype(d)::value, decltype(r)>(s, coef_f, coef_g, frame); });
 }
 
@@ -447,6 +678,7 @@ pond_status pond_get_face_gauges(pond_state *s, double *xg, double *yg)
 {
     if (pond_status st = check_state(s)) return st;
     if (!xg && !yg) return POND_OK;
+    if (s->batch) return xg ? dispatch_batch(s, [&](auto r) { return batch_face_gauges<decltype(r)>(s, xg, nullptr); }) : POND_OK;
     return dispatch(s, [&](auto d, auto r) { return face_gauges_impl<decltype(d)::value, decltype(r)>(s, xg, yg, nullptr, nullptr); });
 }
 
@@ -454,6 +686,7 @@ pond_status pond_set_face_gauges(pond_state *s, const double *xg, const double *
 {
     if (pond_status st = check_state(s)) return st;
     if (!xg && !yg) return POND_OK;
+    if (s->batch) return xg ? dispatch_batch(s, [&](auto r) { return batch_face_gauges<decltype(r)>(s, nullptr, xg); }) : POND_OK;
     return dispatch(s, [&](auto d, auto r) { return face_gauges_impl<decltype(d)::value, decltype(r)>(s, nullptr, nullptr, xg, yg); });
 }
 
@@ -466,6 +699,11 @@ pond_status pond_sync(pond_state *s, pond_diag *diag)
     CUDA_TRY(cudaMemcpyAsync(&d, s->diag, sizeof(d), cudaMemcpyDeviceToHost, s->stream));
     CUDA_TRY(cudaStreamSynchronize(s->stream));
     CUDA_TRY(cudaGetLastError());
+    if (s->batch) {
+        c.t = 0.0;
+        c.dt = 0.0;
+        c.steps = s->steps_taken;
+    }
     if (diag) {
         diag->t = c.t;
         diag->dt = c.dt;
@@ -482,6 +720,57 @@ pond_status pond_sync(pond_state *s, pond_diag *diag)
                                                       (unsigned long long)d.nonphys, (long long)d.first_bad);
     if (s->opts.strict_convergence && (d.flags & pond::FLAG_NOT_CONVERGED))
         return fail(POND_ERR_NOT_CONVERGED, "%llu faces stopped at max_iter", (unsigned long long)d.nonconv);
+    return POND_OK;
+}
+
+pond_status pond_init_batch(int64_t n_tubes, const int64_t *lengths, const double *gammas, const double *dx, double tau,
+                            const pond_options *opts, pond_state **out)
+{
+    if (!lengths || !gammas || !opts || !out || n_tubes <= 0) return fail(POND_ERR_INVALID_ARG, "bad batch arguments");
+    *out = nullptr;
+    if (n_tubes > (int64_t(1) << 31) - 1) return fail(POND_ERR_INVALID_ARG, "too many tubes");
+    for (int64_t k = 0; k < n_tubes; ++k) {
+        if (lengths[k] < 1 || lengths[k] > (int64_t(1) << 30)) return fail(POND_ERR_INVALID_ARG, "tube %lld: bad length", (long long)k);
+        if (!(gammas[k] > 1.0)) return fail(POND_ERR_INVALID_ARG, "tube %lld: gamma must exceed 1", (long long)k);
+        if (1.0 / (gammas[k] - 1.0) < 0.5) return fail(POND_ERR_UNSUPPORTED, "tube %lld: gamma > 3 makes Cv - 1/2 negative", (long long)k);
+        if (dx && !(dx[k] > 0.0)) return fail(POND_ERR_INVALID_ARG, "tube %lld: dx must be positive", (long long)k);
+    }
+    if (!(tau > 0.0)) return fail(POND_ERR_INVALID_ARG, "tau must be positive");
+    if (opts->precision != POND_FP32 && opts->precision != POND_FP64) return fail(POND_ERR_INVALID_ARG, "bad precision");
+    if (opts->limiter != POND_VANLEER && opts->limiter != POND_MINMOD) return fail(POND_ERR_INVALID_ARG, "bad limiter");
+    if (!(opts->cfl > 0.0) || opts->max_iter < 1 || opts->fixed_iters < 0) return fail(POND_ERR_INVALID_ARG, "bad cfl/max_iter/fixed_iters");
+    pond_state *s = new (std::nothrow) pond_state();
+    if (!s) return fail(POND_ERR_OOM, "host allocation failed");
+    s->batch = true;
+    s->D = 1;
+    s->prec = opts->precision;
+    s->opts = *opts;
+    s->tau = tau;
+    s->n_tubes = n_tubes;
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e != cudaSuccess) { delete s; return fail(POND_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e)); }
+    if (opts->stream) {
+        s->stream = static_cast<cudaStream_t>(opts->stream);
+    } else {
+        e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { delete s; return fail(POND_ERR_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e)); }
+        s->own_stream = true;
+    }
+    pond_status st = dispatch_batch(s, [&](auto r) { return batch_setup<decltype(r)>(s, lengths, gammas, dx); });
+    if (st != POND_OK) { pond_destroy(s); return st; }
+    *out = s;
+    return POND_OK;
+}
+
+pond_status pond_batch_times(pond_state *s, double *t, double *dt)
+{
+    if (pond_status st = check_state(s)) return st;
+    if (!s->batch) return fail(POND_ERR_INVALID_ARG, "not a batch state");
+    const double *dtp = s->prec == POND_FP32 ? tparams_of<float>(s).dt : tparams_of<double>(s).dt;
+    const double *tp = s->prec == POND_FP32 ? tparams_of<float>(s).t : tparams_of<double>(s).t;
+    if (t) CUDA_TRY(cudaMemcpyAsync(t, tp, 8 * s->n_tubes, cudaMemcpyDeviceToHost, s->stream));
+    if (dt) CUDA_TRY(cudaMemcpyAsync(dt, dtp, 8 * s->n_tubes, cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
     return POND_OK;
 }
 

@@ -1,0 +1,356 @@
+// pond_batch.cuh -- many independent 1D shock tubes (D1Q4) advanced in one persistent launch.
+//
+// Each CTA owns one tube for the whole run and loops over the time steps itself: the
+// tube's time step comes from its own CFL maximum (a CTA reduction), so tubes never wait
+// on one another and no inter-CTA synchronization exists.  Per step the tube is streamed
+// in chunks of kChunk cells: the chunk and a halo of two cells are staged in shared memory
+// (phi-bar-plus, Eq. Fbarplus), the face corrector (Sec. III.B.3) writes the face
+// populations to shared memory, and the cell update (Eqs. fluxEq, FinalUpdateDUGKS, with
+// the re-expression in the new co-moving frame) writes the new state into the other of two
+// state buffers, so later chunks still read the old state.  Face populations never reach
+// global memory; per cell and step the traffic is the state read and written once and the
+// face predictor read and written once.
+#pragma once
+
+#include "pond_kernels.cuh"
+
+namespace pond {
+
+constexpr int kTubeThreads = 256;
+constexpr int kChunk = 256;
+
+template <typename R>
+struct TubeParams {
+    int n_tubes;
+    const long long *cell_off;    // first cell of tube k in the concatenated arrays
+    const long long *face_off;    // first face of tube k (a tube of L cells has L + 1 faces)
+    const int *len;
+    const int *order;             // CTA b processes tube order[b] (longest first)
+    const double *Cv;            // per tube: 1/(gamma - 1)
+    const double *dx;            // per tube
+    double tau, cfl;
+    int limiter;
+    double tol;
+    int max_iter, fixed_iters;
+    long long ncell, nface;
+    R *sf[2];                     // [3][ncell] rho, a2, a3  (two buffers)
+    R *sg[2];                     // [3][ncell] b0, b1, b2
+    double *sfr[2];               // [2][ncell] u, T
+    double *fu, *fT;              // face predictors [nface]
+    double *t, *dt;               // per tube
+    double *totals;               // per tube [4]: rho, rho u, 0, rho E summed times dx
+    Diag *diag;
+};
+
+template <typename R>
+__device__ __forceinline__ void tube_stage(const TubeParams<R> &P, int cur, long long c, double Cv, R cp, R ce,
+                                           double uref, StagedCell<1, R> &o)
+{
+    const long long n = P.ncell;
+    const R rho = P.sf[cur][c];
+    o.A[0] = cp * rho + ce * rho;
+    o.A[1] = R(0);
+    o.A[2] = cp * P.sf[cur][n + c];
+    o.A[3] = cp * P.sf[cur][2 * n + c];
+    const double T = P.sfr[cur][n + c];
+    o.B[0] = cp * P.sg[cur][c] + ce * R((Cv - 0.5) * double(rho) * T);
+    o.B[1] = cp * P.sg[cur][n + c];
+    o.B[2] = cp * P.sg[cur][2 * n + c];
+    o.du[0] = R(P.sfr[cur][c] - uref);
+    o.T = R(T);
+}
+
+// per-step constants of one tube (Eqs. FinalUpdateDUGKS, Fbarplus, FluxTransf)
+struct TubeStep {
+    double dt, cp, ce, wb, we, ca, cb, h_dx, dt_dx;
+};
+
+template <typename R>
+__global__ void __launch_bounds__(kTubeThreads)
+tube_kernel(const TubeParams<R> P, int steps, int cur0)
+{
+    __shared__ StagedCell<1, R> tile[kChunk + 4];
+    __shared__ R faceF[kChunk + 1][4];
+    __shared__ R faceG[kChunk + 1][3];
+    __shared__ double faceU[kChunk + 1], faceT[kChunk + 1];
+    __shared__ TubeStep ks;
+    __shared__ double uref_s;
+    __shared__ double red[kTubeThreads / 32];
+
+    const int tube = P.order[blockIdx.x];
+    const long long c_off = P.cell_off[tube], f_off = P.face_off[tube];
+    const int L = P.len[tube];
+    const double Cv = P.Cv[tube], dx = P.dx[tube];
+    const double tau = P.tau;
+    unsigned long long my_iters = 0, my_faces = 0, my_nonconv = 0, my_fallbacks = 0, my_nonphys = 0;
+
+    for (int step = 0; step < steps; ++step) {
+        const int cur = (cur0 + step) & 1, nxt = cur ^ 1;
+        if (threadIdx.x == 0) {
+            const double dt = P.dt[tube], h = 0.5 * dt;
+            ks.dt = dt;
+            ks.ca = (2.0 * tau - dt) / (2.0 * tau + dt);
+            ks.cb = 2.0 * dt / (2.0 * tau + dt);
+            ks.cp = (2.0 * tau - h) / (2.0 * tau + dt);
+            ks.ce = 3.0 * h / (2.0 * tau + dt);
+            ks.wb = 2.0 * tau / (2.0 * tau + h);
+            ks.we = h / (2.0 * tau + h);
+            ks.h_dx = h / dx;
+            ks.dt_dx = dt / dx;
+        }
+        __syncthreads();
+        const R cp = R(ks.cp), ce = R(ks.ce), ca = R(ks.ca), cb = R(ks.cb), CvR = R(Cv);
+        FaceCfg<R> cfg;
+        cfg.h_dn = R(ks.h_dx);
+        cfg.h_dt = R(0);
+        cfg.Cv = CvR;
+        cfg.tol = R(P.tol);
+        cfg.wb = R(ks.wb);
+        cfg.we = R(ks.we);
+        cfg.limiter = P.limiter;
+        cfg.max_iter = P.max_iter;
+        cfg.fixed_iters = P.fixed_iters;
+        float rate = 0.f;
+        double rate_d = 0.0;
+        for (int c0 = 0; c0 < L; c0 += kChunk) {
+            const int nc = min(kChunk, L - c0);
+            if (threadIdx.x == 0) uref_s = P.sfr[cur][c_off + c0];
+            __syncthreads();
+            const double utile = uref_s;
+            // stage cells c0-2 .. c0+nc+1 (zero-gradient ends)
+            for (int t = threadIdx.x; t < nc + 4; t += blockDim.x) {
+                const int k = min(max(c0 - 2 + t, 0), L - 1);
+                tube_stage<R>(P, cur, c_off + k, Cv, cp, ce, utile, tile[t]);
+            }
+            __syncthreads();
+            // faces c0 .. c0+nc: face k lies between cells k-1 and k
+            for (int f = threadIdx.x; f <= nc; f += blockDim.x) {
+                const long long k = c0 + f;
+                const StagedCell<1, R> *cells[8] = {&tile[f], &tile[f + 1], &tile[f + 2], &tile[f + 3],
+                                                    nullptr, nullptr, nullptr, nullptr};
+                const double uref = P.fu[f_off + k];
+                FaceOut<1, R> o;
+                solve_face<1, R>(cells, false, &uref, R(P.fT[f_off + k]), &utile, cfg, o);
+                const bool owned = f < nc || k == L;
+                if (owned) {
+                    my_iters += o.iters;
+                    my_faces += 1;
+                    my_fallbacks += o.fallbacks;
+                    if (!o.done) ++my_nonconv;
+                }
+                if (o.have) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) faceF[f][q] = o.F[q];
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) faceG[f][q] = o.G[q];
+                    faceU[f] = o.u[0];
+                    faceT[f] = o.T;
+                } else {
+                    if (owned) ++my_nonphys;
+                    const R nan = R(__longlong_as_double(0x7ff8000000000000ll));
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) faceF[f][q] = nan;
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) faceG[f][q] = nan;
+                    faceU[f] = uref;
+                    faceT[f] = double(nan);
+                }
+                if (owned) {
+                    P.fu[f_off + k] = faceU[f];
+                    P.fT[f_off + k] = faceT[f];
+                }
+            }
+            __syncthreads();
+            // cells c0 .. c0+nc-1
+            const long long n = P.ncell;
+            for (int t = threadIdx.x; t < nc; t += blockDim.x) {
+                const long long c = c_off + c0 + t;
+                const double uc[1] = {P.sfr[cur][c]};
+                const double Tc = P.sfr[cur][n + c];
+                const R rho = P.sf[cur][c];
+                const R Tcr = R(Tc), invTc = R(1) / Tcr, rsqTc = sqrt(invTc), sqTc = Tcr * rsqTc;
+                R H[4], G[3];
+                H[0] = ca * rho + cb * rho;
+                H[1] = R(0);
+                H[2] = ca * P.sf[cur][n + c];
+                H[3] = ca * P.sf[cur][2 * n + c];
+                G[0] = ca * P.sg[cur][c] + cb * (CvR - R(0.5)) * rho * Tcr;
+                G[1] = ca * P.sg[cur][n + c];
+                G[2] = ca * P.sg[cur][2 * n + c];
+                const R sx = R(ks.dt_dx);
+#pragma unroll
+                for (int side = 0; side < 2; ++side) {
+                    const int f = t + side;
+                    const double ub[1] = {faceU[f]};
+                    add_face_flux<1, R>(faceF[f], faceG[f], ub, faceT[f], uc, Tc, invTc, rsqTc, 0, side ? sx : -sx,
+                                        sqTc, R(uc[0]), H, G);
+                }
+                R Ho[4], Go[3];
+                double un[1], Tn;
+                const bool ok = cell_finish<1, R>(H, G, uc, Tc, invTc, sqTc, CvR, Ho, Go, un, Tn);
+                if (!ok) {
+                    ++my_nonphys;
+                    atomicCAS((unsigned long long *)&P.diag->first_bad, (unsigned long long)-1ll, (unsigned long long)c);
+                }
+                P.sf[nxt][c] = Ho[0];
+                P.sf[nxt][n + c] = Ho[2];
+                P.sf[nxt][2 * n + c] = Ho[3];
+                P.sg[nxt][c] = Go[0];
+                P.sg[nxt][n + c] = Go[1];
+                P.sg[nxt][2 * n + c] = Go[2];
+                P.sfr[nxt][c] = un[0];
+                P.sfr[nxt][n + c] = Tn;
+                if (ok) {
+                    if constexpr (sizeof(R) == 8) rate_d = fmax(rate_d, (fabs(un[0]) + sqrt(Tn) * kCHi) / dx);
+                    else rate = fmaxf(rate, (fabsf(float(un[0])) + sqrtf(float(Tn)) * float(kCHi)) * float(1.0 / dx));
+                }
+            }
+            __syncthreads();
+        }
+        // the tube's next time step from its CFL maximum (Sec. IV)
+        double r = sizeof(R) == 8 ? rate_d : double(rate);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_down_sync(0xffffffffu, r, o));
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = r;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double rm = 0.0;
+            for (int w = 0; w < kTubeThreads / 32; ++w) rm = fmax(rm, red[w]);
+            P.t[tube] += ks.dt;
+            P.dt[tube] = P.cfl / rm;
+        }
+        __syncthreads();
+    }
+    // warp-aggregated diagnostics
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        my_iters += __shfl_down_sync(0xffffffffu, my_iters, o);
+        my_faces += __shfl_down_sync(0xffffffffu, my_faces, o);
+        my_nonconv += __shfl_down_sync(0xffffffffu, my_nonconv, o);
+        my_fallbacks += __shfl_down_sync(0xffffffffu, my_fallbacks, o);
+        my_nonphys += __shfl_down_sync(0xffffffffu, my_nonphys, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (my_faces) { atomicAdd(&P.diag->face_iters, my_iters); atomicAdd(&P.diag->face_solves, my_faces); }
+        if (my_nonconv) { atomicAdd(&P.diag->nonconv, my_nonconv); atomicOr(&P.diag->flags, FLAG_NOT_CONVERGED); }
+        if (my_fallbacks) atomicAdd(&P.diag->fallbacks, my_fallbacks);
+        if (my_nonphys) { atomicAdd(&P.diag->nonphys, my_nonphys); atomicOr(&P.diag->flags, FLAG_NONPHYSICAL); }
+    }
+}
+
+// initial condition of every tube: co-moving equilibria (Eqs. feqPond, geqPond), the face
+// predictors (pooled moments of the two adjacent cells, zero-gradient ends), t = 0 and the
+// first time step
+template <typename R>
+__global__ void __launch_bounds__(kTubeThreads)
+tube_init_kernel(const TubeParams<R> P, int cur, const double *rho, const double *ux, const double *p)
+{
+    __shared__ double red[kTubeThreads / 32];
+    const int tube = blockIdx.x;
+    const long long c_off = P.cell_off[tube], f_off = P.face_off[tube];
+    const int L = P.len[tube];
+    const double Cv = P.Cv[tube], dx = P.dx[tube];
+    const long long n = P.ncell;
+    double rate = 0.0;
+    unsigned long long bad = 0;
+    for (int k = threadIdx.x; k < L; k += blockDim.x) {
+        const long long c = c_off + k;
+        const double r = rho[c], T = p[c] / r, u = ux[c];
+        P.sf[cur][c] = R(r);
+        P.sf[cur][n + c] = R(0);
+        P.sf[cur][2 * n + c] = R(0);
+        P.sg[cur][c] = R((Cv - 0.5) * r * T);
+        P.sg[cur][n + c] = R(0);
+        P.sg[cur][2 * n + c] = R(0);
+        P.sfr[cur][c] = u;
+        P.sfr[cur][n + c] = T;
+        if (r > 0.0 && T > 0.0 && isfinite(r) && isfinite(T)) {
+            rate = fmax(rate, (fabs(u) + sqrt(T) * kCHi) / dx);
+        } else {
+            ++bad;
+            atomicCAS((unsigned long long *)&P.diag->first_bad, (unsigned long long)-1ll, (unsigned long long)c);
+        }
+    }
+    for (int k = threadIdx.x; k <= L; k += blockDim.x) {
+        const long long a = c_off + max(k - 1, 0), b = c_off + min(k, L - 1);
+        const double ra = rho[a], rb = rho[b], ua = ux[a], ub = ux[b];
+        const double Ea = p[a] * Cv + 0.5 * ra * ua * ua, Eb = p[b] * Cv + 0.5 * rb * ub * ub;
+        const double r = 0.5 * (ra + rb), m = 0.5 * (ra * ua + rb * ub), E = 0.5 * (Ea + Eb);
+        P.fu[f_off + k] = m / r;
+        P.fT[f_off + k] = (E - 0.5 * m * m / r) / (Cv * r);
+    }
+    if (bad) { atomicAdd(&P.diag->nonphys, bad); atomicOr(&P.diag->flags, FLAG_NONPHYSICAL); }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rate = fmax(rate, __shfl_down_sync(0xffffffffu, rate, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = rate;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double rm = 0.0;
+        for (int w = 0; w < kTubeThreads / 32; ++w) rm = fmax(rm, red[w]);
+        P.t[tube] = 0.0;
+        P.dt[tube] = P.cfl / rm;
+    }
+}
+
+// conserved fields of every tube (lab frame, FP64) and the per-tube sums times dx
+template <typename R>
+__global__ void __launch_bounds__(kTubeThreads)
+tube_conserved_kernel(const TubeParams<R> P, int cur, double *rho, double *mx, double *E)
+{
+    __shared__ double red[3][kTubeThreads / 32];
+    const int tube = blockIdx.x;
+    const long long c_off = P.cell_off[tube];
+    const int L = P.len[tube];
+    const double Cv = P.Cv[tube], dx = P.dx[tube];
+    const long long n = P.ncell;
+    double s[3] = {0, 0, 0};
+    for (int k = threadIdx.x; k < L; k += blockDim.x) {
+        const long long c = c_off + k;
+        const double r = double(P.sf[cur][c]), u = P.sfr[cur][c], T = P.sfr[cur][n + c];
+        const double v[3] = {r, r * u, r * (Cv * T + 0.5 * u * u)};
+        if (rho) rho[c] = v[0];
+        if (mx) mx[c] = v[1];
+        if (E) E[c] = v[2];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) s[q] += v[q];
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s[q] += __shfl_down_sync(0xffffffffu, s[q], o);
+        if ((threadIdx.x & 31) == 0) red[q][threadIdx.x >> 5] = s[q];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot[3] = {0, 0, 0};
+        for (int w = 0; w < kTubeThreads / 32; ++w)
+            for (int q = 0; q < 3; ++q) tot[q] += red[q][w];
+        P.totals[4 * tube + 0] = tot[0] * dx;
+        P.totals[4 * tube + 1] = tot[1] * dx;
+        P.totals[4 * tube + 2] = 0.0;
+        P.totals[4 * tube + 3] = tot[2] * dx;
+    }
+}
+
+// stored state as full coefficient arrays [cells][4], [cells][3] and frames [cells][2]
+template <typename R>
+__global__ void tube_export_kernel(const TubeParams<R> P, int cur, double *cf, double *cg, double *fr)
+{
+    const long long n = P.ncell;
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    if (cf) {
+        cf[4 * c] = double(P.sf[cur][c]);
+        cf[4 * c + 1] = 0.0;
+        cf[4 * c + 2] = double(P.sf[cur][n + c]);
+        cf[4 * c + 3] = double(P.sf[cur][2 * n + c]);
+    }
+    if (cg)
+        for (int q = 0; q < 3; ++q) cg[3 * c + q] = double(P.sg[cur][q * n + c]);
+    if (fr) {
+        fr[2 * c] = P.sfr[cur][c];
+        fr[2 * c + 1] = P.sfr[cur][n + c];
+    }
+}
+
+}  // namespace pond

@@ -30,7 +30,7 @@ struct Clock {
     // FluxTransf): update ca = (2tau-dt)/(2tau+dt), cb = 2dt/(2tau+dt); phi-bar-plus
     // cp = (2tau-h)/(2tau+dt), ce = 3h/(2tau+dt); face populations wb = 2tau/(2tau+h),
     // we = h/(2tau+h); departure offsets h/dx, h/dy; h = dt/2
-    double ca, cb, cp, ce, wb, we, h_dx, h_dy;
+    double ca, cb, cp, ce, wb, we, h_dx, h_dy, dt_dx, dt_dy, inv_dx, inv_dy;
     long long steps;
     unsigned long long rate_bits;   // max CFL rate of the step being reduced (as double bits)
     unsigned int blocks_done;
@@ -49,6 +49,10 @@ __host__ __device__ inline void set_step_constants(Clock &c, double dt)
     c.we = h / (2.0 * tau + h);
     c.h_dx = h / c.dx;
     c.h_dy = h / c.dy;
+    c.dt_dx = dt / c.dx;
+    c.dt_dy = dt / c.dy;
+    c.inv_dx = 1.0 / c.dx;
+    c.inv_dy = 1.0 / c.dy;
 }
 
 struct Diag {
@@ -122,25 +126,39 @@ template <int D, typename R>
 struct StagedCell {
     R A[NCoef<D, 3>::value];
     R B[NCoef<D, 2>::value];
-    double u[D];
+    R du[D];    // frame velocity relative to the tile reference velocity
     R T;
 };
 
 // Loads cell (i, j) (ghosts resolved) and forms phi-bar-plus = cp phi~ + ce phi^eq with
 // phi^eq the co-moving equilibria (rho, 0, ...) and ((Cv - D/2) rho T, 0, ...).
 template <int D, typename R>
+__device__ __forceinline__ void cell_velocity(const Params<D, R> &P, long long i, long long j, double *u)
+{
+    long long idx = 0;
+    const int side = resolve(P, i, j, &idx);
+    if (side >= 0) {
+        u[0] = P.inflow[side][1];
+        if constexpr (D == 2) u[1] = P.inflow[side][2];
+    } else {
+#pragma unroll
+        for (int a = 0; a < D; ++a) u[a] = P.sfr[a * P.ncell() + idx];
+    }
+}
+
+template <int D, typename R>
 __device__ __forceinline__ void load_cell_bar_plus(const Params<D, R> &P, long long i, long long j, R cp, R ce,
-                                                   StagedCell<D, R> &c)
+                                                   const double *utile, StagedCell<D, R> &c)
 {
     constexpr int NFC = NCoef<D, 3>::value, NGC = NCoef<D, 2>::value;
     long long idx = 0;
     const int side = resolve(P, i, j, &idx);
-    double rho, T;
+    double rho, T, u[D];
     if (side >= 0) {
         rho = P.inflow[side][0];
         T = P.inflow[side][3] / rho;
-        c.u[0] = P.inflow[side][1];
-        if constexpr (D == 2) c.u[1] = P.inflow[side][2];
+        u[0] = P.inflow[side][1];
+        if constexpr (D == 2) u[1] = P.inflow[side][2];
 #pragma unroll
         for (int k = 0; k < NFC; ++k) c.A[k] = R(0);
 #pragma unroll
@@ -157,10 +175,12 @@ __device__ __forceinline__ void load_cell_bar_plus(const Params<D, R> &P, long l
 #pragma unroll
         for (int k = 0; k < NGC; ++k) c.B[k] = P.sg[k * n + idx];
 #pragma unroll
-        for (int a = 0; a < D; ++a) c.u[a] = P.sfr[a * n + idx];
+        for (int a = 0; a < D; ++a) u[a] = P.sfr[a * n + idx];
         T = P.sfr[D * n + idx];
         rho = double(c.A[0]);
     }
+#pragma unroll
+    for (int a = 0; a < D; ++a) c.du[a] = R(u[a] - utile[a]);
     const R r = c.A[0];
     c.A[0] = cp * r + ce * r;
 #pragma unroll
@@ -391,6 +411,144 @@ __device__ __forceinline__ bool pass_frame(const R *Phi, const R *Psi, R Tl, R C
     return ok;
 }
 
+template <typename R>
+struct FaceCfg {
+    R h_dn, h_dt;      // h/dx along the normal and the tangent
+    R Cv, tol, wb, we;
+    int limiter, max_iter, fixed_iters;
+};
+
+template <int D, typename R>
+struct FaceOut {
+    R F[NCoef<D, 3>::value];   // f, g coefficients of phi(x_b, t_{n+1/2}) in the face frame (x, y order)
+    R G[NCoef<D, 2>::value];
+    double u[D];
+    double T;
+    int iters, fallbacks;
+    bool done, have;
+};
+
+// The face predictor-corrector of Sec. III.B.3 at one face.  cells: stencil slots 0 LL,
+// 1 L, 2 R, 3 RR, 4 L-t, 5 L+t, 6 R-t, 7 R+t (staged phi-bar-plus, velocities relative to
+// utile); swap: the face normal is y; uref, Tpred: the predictor lambda_0 (x, y order).
+// Passes run until the frame converges (or fixed_iters passes); a pass whose moments define
+// no frame restarts the corrector once from the frame of the pooled moments of the
+// stencil, else the corrector stops at the last pass that did.  The face populations are
+// Eq. (FluxTransf) at the frame of the last valid pass's moments.
+template <int D, typename R>
+__device__ __forceinline__ void solve_face(const StagedCell<D, R> *const *cells, bool swap, const double *uref, R Tpred,
+                                           const double *utile, const FaceCfg<R> &cfg, FaceOut<D, R> &o)
+{
+    o.fallbacks = 0;
+    constexpr int NCELL = D == 2 ? 8 : 4;
+    constexpr int NFC = NCoef<D, 3>::value, NGC = NCoef<D, 2>::value;
+    const int na = swap ? 1 : 0, ta = swap ? 0 : 1;  // normal / tangential axes
+    const R h_dn = cfg.h_dn, h_dt = cfg.h_dt;
+    R dref[D];
+    dref[0] = R(uref[na] - utile[na]);
+    if constexpr (D == 2) dref[1] = R(uref[ta] - utile[ta]);
+    R dc[NCELL][D];
+#pragma unroll
+    for (int s = 0; s < NCELL; ++s) {
+        dc[s][0] = cells[s]->du[na] - dref[0];
+        if constexpr (D == 2) dc[s][1] = cells[s]->du[ta] - dref[1];
+    }
+    R uref_t = R(0);
+    if constexpr (D == 2) uref_t = R(uref[ta]);
+    const R uref_n = R(uref[na]);
+    const R Cv = cfg.Cv, tolR = cfg.tol;
+
+    R dl[D], Tl = Tpred;
+#pragma unroll
+    for (int a = 0; a < D; ++a) dl[a] = R(0);
+    R keep_dl[D], keep_T = R(0), out_du[D], out_T = R(0), out_rho = R(0);
+    bool have = false, done = false, restarted = false, last_valid = false;
+    int iters = 0;
+    R Phi[NFC], Psi[NGC];
+    for (int k = 0; k < cfg.max_iter && !done; ++k) {
+        corrector_pass<D, R>(cells, dc, dl, Tl, uref_n + dl[0], D == 2 ? uref_t + dl[D - 1] : R(0),
+                             h_dn, h_dt, swap, cfg.limiter, Phi, Psi);
+        R rho1, du[D], T1;
+        const bool ok = pass_frame<D, R>(Phi, Psi, Tl, Cv, rho1, du, T1);
+        iters = k + 1;
+        if (!ok) {
+            ++o.fallbacks;
+            last_valid = false;
+            if (!restarted) {
+                // restart once from the frame of the pooled conserved moments of the stencil
+                restarted = true;
+                R r = R(0), m[D], e = R(0);
+#pragma unroll
+                for (int a = 0; a < D; ++a) m[a] = R(0);
+#pragma unroll
+                for (int s = 0; s < NCELL; ++s) {
+                    const R rc = cells[s]->A[0];
+                    R v2 = R(0);
+#pragma unroll
+                    for (int a = 0; a < D; ++a) { m[a] += rc * dc[s][a]; v2 += dc[s][a] * dc[s][a]; }
+                    r += rc;
+                    e += rc * (Cv * cells[s]->T + R(0.5) * v2);
+                }
+                r /= R(NCELL); e /= R(NCELL);
+                R k2 = R(0);
+#pragma unroll
+                for (int a = 0; a < D; ++a) { m[a] /= R(NCELL); dl[a] = m[a] / r; k2 += m[a] * m[a]; }
+                Tl = (e - R(0.5) * k2 / r) / (Cv * r);
+                continue;
+            }
+            break;
+        }
+        have = true;
+        last_valid = true;
+#pragma unroll
+        for (int a = 0; a < D; ++a) { keep_dl[a] = dl[a]; out_du[a] = du[a]; }
+        keep_T = Tl; out_T = T1; out_rho = rho1;
+        if (cfg.fixed_iters > 0) {
+            done = iters >= cfg.fixed_iters;
+        } else {
+            bool c = fabs(T1 - Tl) <= tolR * Tl;
+            const R sq = sqrt(Tl);
+#pragma unroll
+            for (int a = 0; a < D; ++a) c = c && fabs(du[a]) <= tolR * sq;
+            done = c;
+        }
+#pragma unroll
+        for (int a = 0; a < D; ++a) dl[a] += du[a];
+        Tl = T1;
+    }
+    o.iters = iters;
+    o.done = done;
+    o.have = have;
+    if (have) {
+        if (!last_valid) {
+            // the last pass defined no frame: recompute the last valid one
+            corrector_pass<D, R>(cells, dc, keep_dl, keep_T, uref_n + keep_dl[0],
+                                 D == 2 ? uref_t + keep_dl[D - 1] : R(0), h_dn, h_dt, swap, cfg.limiter, Phi, Psi);
+        }
+        // Eq. (FluxTransf) in the frame of the last valid pass's moments, with the exact
+        // co-moving equilibria there: phi = (2 tau phibar + h phi^eq)/(2 tau + h)
+        const R invT = R(1) / out_T;
+        Map1<R> X(sqrt(keep_T * invT), (keep_T - out_T) * invT, -out_du[0] * sqrt(invT));
+        Map1<R> Y = X;
+        if (D == 2) Y = Map1<R>(sqrt(keep_T * invT), (keep_T - out_T) * invT, -out_du[D - 1] * sqrt(invT));
+        R Fo[NFC], Go[NGC];
+        shift_scale<D, 3, R>(Phi, X, Y, Fo);
+        shift_scale<D, 2, R>(Psi, X, Y, Go);
+        const R wb = cfg.wb, we = cfg.we;
+        Fo[0] = wb * Fo[0] + we * out_rho;
+#pragma unroll
+        for (int k = 1; k < NFC; ++k) Fo[k] = wb * Fo[k];
+        Go[0] = wb * Go[0] + we * (Cv - R(0.5 * D)) * out_rho * out_T;
+#pragma unroll
+        for (int k = 1; k < NGC; ++k) Go[k] = wb * Go[k];
+        orient<D, 3, R>(Fo, o.F, swap);
+        orient<D, 2, R>(Go, o.G, swap);
+        o.u[na] = uref[na] + double(keep_dl[0]) + double(out_du[0]);
+        if constexpr (D == 2) o.u[ta] = uref[ta] + double(keep_dl[1]) + double(out_du[1]);
+        o.T = double(out_T);
+    }
+}
+
 template <int D, typename R>
 #ifndef POND_FACE_MIN_BLOCKS
 #define POND_FACE_MIN_BLOCKS 2
@@ -402,17 +560,21 @@ face_kernel(const Params<D, R> P)
     constexpr int BX = TX + 3, BY = D == 2 ? TY + 3 : 1;
     constexpr int NFC = NCoef<D, 3>::value, NGC = NCoef<D, 2>::value;
     __shared__ StagedCell<D, R> tile[BY * BX];
+    __shared__ double utile[D];
 
     const Clock &K = *P.clock;
     if (!(K.dt > 0.0)) return;  // t_end reached: the step is a no-op
     const R cp = R(K.cp), ce = R(K.ce);
 
     const long long i0 = (long long)blockIdx.x * TX, j0 = (long long)blockIdx.y * TY;
+    // reference velocity of the tile: staged velocities are differences from it
+    if (threadIdx.x == 0) cell_velocity<D, R>(P, i0, j0, utile);
+    __syncthreads();
     // stage phi-bar-plus of the box [i0-2, i0+TX] x [j0-2, j0+TY] (1D: [i0-2, i0+TX])
     for (int t = threadIdx.x; t < BX * BY; t += blockDim.x) {
         const int bx = t % BX, by = t / BX;
         const long long ci = i0 - 2 + bx, cj = D == 2 ? j0 - 2 + by : 0;
-        load_cell_bar_plus<D, R>(P, ci, cj, cp, ce, tile[t]);
+        load_cell_bar_plus<D, R>(P, ci, cj, cp, ce, utile, tile[t]);
     }
     __syncthreads();
 
@@ -449,122 +611,30 @@ face_kernel(const Params<D, R> P)
             cells[4] = at(fi - 1, fj - 1); cells[5] = at(fi + 1, fj - 1);
             cells[6] = at(fi - 1, fj); cells[7] = at(fi + 1, fj);
         }
-        constexpr int NCELL = D == 2 ? 8 : 4;
         const bool swap = dir == 1;
         R *Fout = dir == 0 ? P.xf : P.yf;
         R *Gout = dir == 0 ? P.xg : P.yg;
         double *Frm = dir == 0 ? P.xfr : P.yfr;
         const long long nf = dir == 0 ? P.nxf() : P.nyf();
-        const int na = swap ? 1 : 0, ta = swap ? 0 : 1;  // normal / tangential axes
-        const R h_dn = R(swap ? K.h_dy : K.h_dx), h_dt = R(D == 2 ? (swap ? K.h_dx : K.h_dy) : 0.0);
-        // face reference velocity: the predictor; all velocities below are relative to it
         double uref[D];
 #pragma unroll
         for (int a = 0; a < D; ++a) uref[a] = Frm[a * nf + fidx];
-        const R Tpred = R(Frm[D * nf + fidx]);
-        R dc[NCELL][D];
+        FaceOut<D, R> o;
+        FaceCfg<R> cfg;
+        cfg.h_dn = R(swap ? K.h_dy : K.h_dx);
+        cfg.h_dt = R(D == 2 ? (swap ? K.h_dx : K.h_dy) : 0.0);
+        cfg.Cv = R(P.Cv); cfg.tol = R(P.tol); cfg.wb = R(K.wb); cfg.we = R(K.we);
+        cfg.limiter = P.limiter; cfg.max_iter = P.max_iter; cfg.fixed_iters = P.fixed_iters;
+        solve_face<D, R>(cells, swap, uref, R(Frm[D * nf + fidx]), utile, cfg, o);
+        my_iters = o.iters; my_nonconv = o.done ? 0 : 1; my_fallbacks = o.fallbacks;
+        if (o.have) {
 #pragma unroll
-        for (int s = 0; s < NCELL; ++s) {
-            dc[s][0] = R(cells[s]->u[na] - uref[na]);
-            if constexpr (D == 2) dc[s][1] = R(cells[s]->u[ta] - uref[ta]);
-        }
-        R uref_t = R(0);
-        if constexpr (D == 2) uref_t = R(uref[ta]);
-        const R uref_n = R(uref[na]);
-        const R Cv = R(P.Cv), tolR = R(P.tol);
-
-        R dl[D], Tl = Tpred;
+            for (int k = 0; k < NFC; ++k) Fout[k * nf + fidx] = o.F[k];
 #pragma unroll
-        for (int a = 0; a < D; ++a) dl[a] = R(0);
-        R keep_dl[D], keep_T = R(0), out_du[D], out_T = R(0), out_rho = R(0);
-        bool have = false, done = false, restarted = false, last_valid = false;
-        int iters = 0;
-        R Phi[NFC], Psi[NGC];
-        for (int k = 0; k < P.max_iter && !done; ++k) {
-            corrector_pass<D, R>(cells, dc, dl, Tl, uref_n + dl[0], D == 2 ? uref_t + dl[D - 1] : R(0),
-                                 h_dn, h_dt, swap, P.limiter, Phi, Psi);
-            R rho1, du[D], T1;
-            const bool ok = pass_frame<D, R>(Phi, Psi, Tl, Cv, rho1, du, T1);
-            iters = k + 1;
-            if (!ok) {
-                ++my_fallbacks;
-                last_valid = false;
-                if (!restarted) {
-                    // restart once from the frame of the pooled conserved moments of the stencil
-                    restarted = true;
-                    R r = R(0), m[D], e = R(0);
+            for (int k = 0; k < NGC; ++k) Gout[k * nf + fidx] = o.G[k];
 #pragma unroll
-                    for (int a = 0; a < D; ++a) m[a] = R(0);
-#pragma unroll
-                    for (int s = 0; s < NCELL; ++s) {
-                        const R rc = cells[s]->A[0];
-                        R v2 = R(0);
-#pragma unroll
-                        for (int a = 0; a < D; ++a) { m[a] += rc * dc[s][a]; v2 += dc[s][a] * dc[s][a]; }
-                        r += rc;
-                        e += rc * (Cv * cells[s]->T + R(0.5) * v2);
-                    }
-                    r /= R(NCELL); e /= R(NCELL);
-                    R k2 = R(0);
-#pragma unroll
-                    for (int a = 0; a < D; ++a) { m[a] /= R(NCELL); dl[a] = m[a] / r; k2 += m[a] * m[a]; }
-                    Tl = (e - R(0.5) * k2 / r) / (Cv * r);
-                    continue;
-                }
-                break;
-            }
-            have = true;
-            last_valid = true;
-#pragma unroll
-            for (int a = 0; a < D; ++a) { keep_dl[a] = dl[a]; out_du[a] = du[a]; }
-            keep_T = Tl; out_T = T1; out_rho = rho1;
-            if (P.fixed_iters > 0) {
-                done = iters >= P.fixed_iters;
-            } else {
-                bool c = fabs(T1 - Tl) <= tolR * Tl;
-                const R sq = sqrt(Tl);
-#pragma unroll
-                for (int a = 0; a < D; ++a) c = c && fabs(du[a]) <= tolR * sq;
-                done = c;
-            }
-#pragma unroll
-            for (int a = 0; a < D; ++a) dl[a] += du[a];
-            Tl = T1;
-        }
-        my_iters = iters;
-        if (!done) ++my_nonconv;
-        if (have) {
-            if (!last_valid) {
-                // the last pass defined no frame: recompute the last valid one
-                corrector_pass<D, R>(cells, dc, keep_dl, keep_T, uref_n + keep_dl[0],
-                                     D == 2 ? uref_t + keep_dl[D - 1] : R(0), h_dn, h_dt, swap, P.limiter, Phi, Psi);
-            }
-            // Eq. (FluxTransf) in the frame of the last valid pass's moments, with the exact
-            // co-moving equilibria there: phi = (2 tau phibar + h phi^eq)/(2 tau + h)
-            const R invT = R(1) / out_T;
-            Map1<R> X(sqrt(keep_T * invT), (keep_T - out_T) * invT, -out_du[0] * sqrt(invT));
-            Map1<R> Y = X;
-            if (D == 2) Y = Map1<R>(sqrt(keep_T * invT), (keep_T - out_T) * invT, -out_du[D - 1] * sqrt(invT));
-            R Fo[NFC], Go[NGC];
-            shift_scale<D, 3, R>(Phi, X, Y, Fo);
-            shift_scale<D, 2, R>(Psi, X, Y, Go);
-            const R wb = R(K.wb), we = R(K.we);
-            Fo[0] = wb * Fo[0] + we * out_rho;
-#pragma unroll
-            for (int k = 1; k < NFC; ++k) Fo[k] = wb * Fo[k];
-            Go[0] = wb * Go[0] + we * (Cv - R(0.5 * D)) * out_rho * out_T;
-#pragma unroll
-            for (int k = 1; k < NGC; ++k) Go[k] = wb * Go[k];
-            R Fw[NFC], Gw[NGC];
-            orient<D, 3, R>(Fo, Fw, swap);
-            orient<D, 2, R>(Go, Gw, swap);
-#pragma unroll
-            for (int k = 0; k < NFC; ++k) Fout[k * nf + fidx] = Fw[k];
-#pragma unroll
-            for (int k = 0; k < NGC; ++k) Gout[k * nf + fidx] = Gw[k];
-            Frm[na * nf + fidx] = uref[na] + double(keep_dl[0]) + double(out_du[0]);
-            if constexpr (D == 2) Frm[ta * nf + fidx] = uref[ta] + double(keep_dl[1]) + double(out_du[1]);
-            Frm[D * nf + fidx] = double(out_T);
+            for (int a = 0; a < D; ++a) Frm[a * nf + fidx] = o.u[a];
+            Frm[D * nf + fidx] = o.T;
         } else {
             ++my_nonphys;
             const R nan = R(__longlong_as_double(0x7ff8000000000000ll));
@@ -672,13 +742,20 @@ struct CellBlock { static constexpr int THREADS = 256; };
 
 // CFL rate of a cell frame: max over axes of (|u_a| + sqrt(T/T_L) max|c|)/dx_a
 template <typename R>
-__device__ __forceinline__ double cell_rate(const double *u, double T, double dx, double dy, int D)
+__device__ __forceinline__ double cell_rate(const double *u, double T, double inv_dx, double inv_dy, int D)
 {
-    // FP64 populations: FP64 time step; FP32 populations: the root in FP32 is enough
-    const double c = (sizeof(R) == 8 ? sqrt(T) : double(sqrtf(float(T)))) * kCHi;
-    double r = (fabs(u[0]) + c) / dx;
-    if (D == 2) r = fmax(r, (fabs(u[1]) + c) / dy);
-    return r;
+    // FP64 populations: FP64 time step; FP32 populations: the rate in FP32 is enough
+    if constexpr (sizeof(R) == 8) {
+        const double c = sqrt(T) * kCHi;
+        double r = (fabs(u[0]) + c) * inv_dx;
+        if (D == 2) r = fmax(r, (fabs(u[1]) + c) * inv_dy);
+        return r;
+    } else {
+        const float c = sqrtf(float(T)) * float(kCHi);
+        float r = (fabsf(float(u[0])) + c) * float(inv_dx);
+        if (D == 2) r = fmaxf(r, (fabsf(float(u[1])) + c) * float(inv_dy));
+        return double(r);
+    }
 }
 
 // block max of a non-negative double, then the last block turns the grid max into the
@@ -726,6 +803,46 @@ __device__ __forceinline__ void reduce_rate_and_advance(Clock *clock, double rat
     }
 }
 
+// Step 1 of the next step after the update: the new co-moving frame from the conserved
+// moments (H: f, G: g Hermite moments in the old cell frame (uc, Tc)) and the Grad
+// projection into it (f third order, g second order).  The frame is advanced in FP64 by
+// increments formed relative to the old frame: u' = u + du, T' = T (1 + dT/T).
+template <int D, typename R>
+__device__ __forceinline__ bool cell_finish(const R *H, const R *G, const double *uc, double Tc, R invTc, R sqTc, R Cv,
+                                            R *Ho, R *Go, double *un, double &Tn)
+{
+    const R rsqTc = invTc * sqTc;
+    const R rn = H[0];
+    const R irn = R(1) / rn;
+    R du[D], k2 = R(0), trH;
+    if constexpr (D == 1) {
+        du[0] = sqTc * H[1] * irn;
+        k2 = du[0] * du[0];
+        trH = H[2];
+    } else {
+        du[0] = sqTc * H[hidx(1, 0)] * irn;
+        du[1] = sqTc * H[hidx(0, 1)] * irn;
+        k2 = du[0] * du[0] + du[1] * du[1];
+        trH = H[hidx(2, 0)] + H[hidx(0, 2)];
+    }
+    // T'/T - 1 = (1/2 tr H + G0/T - (Cv - D/2) rho' - rho' |du|^2/(2T)) / (Cv rho')
+    const R dT = (R(0.5) * trH + G[0] * invTc - (Cv - R(0.5 * D)) * rn - R(0.5) * rn * k2 * invTc) / (Cv * rn);
+    Tn = Tc + Tc * double(dT);
+#pragma unroll
+    for (int a = 0; a < D; ++a) un[a] = uc[a] + double(du[a]);
+    const bool ok = rn > R(0) && Tn > 0.0 && isfinite(double(rn)) && isfinite(Tn);
+    // s^2 = T/T' = 1/(1 + dT/T), e = s^2 - 1, d = -du/sqrt(T')
+    const R s2 = R(1) / (R(1) + dT);
+    const R sc = sqrt(s2), e = -dT * s2;
+    const R rsqn = rsqTc * sc;
+    Map1<R> X(sc, e, -du[0] * rsqn);
+    Map1<R> Y = X;
+    if constexpr (D == 2) Y = Map1<R>(sc, e, -du[1] * rsqn);
+    shift_scale<D, 3, R>(H, X, Y, Ho);
+    shift_scale<D, 2, R>(G, X, Y, Go);
+    return ok;
+}
+
 // Step 3 of Sec. III.B.4 (flux into the cell frame, Eq. fluxEq; update, Eqs.
 // FinalUpdateDUGKS) fused with step 1 of the next step (re-expression in the new co-moving
 // frame from the conserved moments) and the CFL reduction.  The frame (u, T) is held and
@@ -764,7 +881,7 @@ cell_kernel(const Params<D, R> P)
         G[0] += cb * (Cv - R(0.5 * D)) * rho * Tcr;
         // fluxes through the 2D faces
         const long long nxf = P.nxf();
-        const R sx = R(K.dt / P.dx);
+        const R sx = R(K.dt_dx);
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
             const long long f = j * (P.nx + 1) + i + side;
@@ -781,7 +898,7 @@ cell_kernel(const Params<D, R> P)
         }
         if constexpr (D == 2) {
             const long long nyf = P.nyf();
-            const R sy = R(K.dt / P.dy);
+            const R sy = R(K.dt_dy);
 #pragma unroll
             for (int side = 0; side < 2; ++side) {
                 const long long f = (j + side) * P.nx + i;
@@ -797,44 +914,14 @@ cell_kernel(const Params<D, R> P)
                 add_face_flux<D, R>(Fc, Gc, ub, Tb, uc, Tc, invTc, rsqTc, 1, side ? sy : -sy, sqTc, R(uc[1]), H, G);
             }
         }
-        // step 1 of the next step: the new co-moving frame from the conserved moments
-        const R rn = H[0];
-        const R irn = R(1) / rn;
-        R du[D], k2 = R(0), trH;
-        if constexpr (D == 1) {
-            du[0] = sqTc * H[1] * irn;
-            k2 = du[0] * du[0];
-            trH = H[2];
-        } else {
-            du[0] = sqTc * H[hidx(1, 0)] * irn;
-            du[1] = sqTc * H[hidx(0, 1)] * irn;
-            k2 = du[0] * du[0] + du[1] * du[1];
-            trH = H[hidx(2, 0)] + H[hidx(0, 2)];
-        }
-        // T'/T - 1 = (1/2 tr H + G0/T - (Cv - D/2) rho' - rho' |du|^2/(2T)) / (Cv rho')
-        const R dT = (R(0.5) * trH + G[0] * invTc - (Cv - R(0.5 * D)) * rn - R(0.5) * rn * k2 * invTc) / (Cv * rn);
-        const double Tn = Tc + Tc * double(dT);
-        double un[D];
-#pragma unroll
-        for (int a = 0; a < D; ++a) un[a] = uc[a] + double(du[a]);
-        const bool ok = rn > R(0) && Tn > 0.0 && isfinite(double(rn)) && isfinite(Tn);
+        R Ho[NFC], Go[NGC];
+        double un[D], Tn;
+        const bool ok = cell_finish<D, R>(H, G, uc, Tc, invTc, sqTc, Cv, Ho, Go, un, Tn);
         if (!ok) {
             atomicOr(&P.diag->flags, FLAG_NONPHYSICAL);
             atomicAdd(&P.diag->nonphys, 1ull);
             atomicCAS((unsigned long long *)&P.diag->first_bad, (unsigned long long)-1ll, (unsigned long long)c);
         }
-        // Grad projection into the new frame (f third order, g second order):
-        // s^2 = T/T' = 1/(1 + dT/T), e = s^2 - 1, d = -du/sqrt(T')
-        const R Tr = R(1) + dT;
-        const R s2 = R(1) / Tr;
-        const R s = sqrt(s2), e = -dT * s2;
-        const R rsqn = rsqTc * s;
-        Map1<R> X(s, e, -du[0] * rsqn);
-        Map1<R> Y = X;
-        if constexpr (D == 2) Y = Map1<R>(s, e, -du[1] * rsqn);
-        R Ho[NFC], Go[NGC];
-        shift_scale<D, 3, R>(H, X, Y, Ho);
-        shift_scale<D, 2, R>(G, X, Y, Go);
 #pragma unroll
         for (int k = 0; k < NFC; ++k) {
             const int pl = fplane<D>(k);
@@ -845,7 +932,7 @@ cell_kernel(const Params<D, R> P)
 #pragma unroll
         for (int a = 0; a < D; ++a) P.sfr[a * n + c] = un[a];
         P.sfr[D * n + c] = Tn;
-        rate = ok ? cell_rate<R>(un, Tn, P.dx, P.dy, D) : 0.0;
+        rate = ok ? cell_rate<R>(un, Tn, K.inv_dx, K.inv_dy, D) : 0.0;
     }
     reduce_rate_and_advance(P.clock, rate, true);
 }
@@ -878,7 +965,7 @@ __global__ void init_cells_kernel(const Params<D, R> P, const double *rho, const
             atomicAdd(&P.diag->nonphys, 1ull);
             atomicCAS((unsigned long long *)&P.diag->first_bad, (unsigned long long)-1ll, (unsigned long long)c);
         }
-        rate = ok ? cell_rate<R>(u, T, P.dx, P.dy, D) : 0.0;
+        rate = ok ? cell_rate<R>(u, T, 1.0 / P.dx, 1.0 / P.dy, D) : 0.0;
     }
     reduce_rate_and_advance(P.clock, rate, false);
 }

@@ -1,0 +1,92 @@
+"""Batched 1D shock tubes (one persistent launch, one CTA per tube, own time step per tube)
+against the FP64 oracle run tube by tube."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_2203_05477_gb300 as pond  # noqa: E402
+from paper_2203_05477_gb300 import inputs as I  # noqa: E402
+from tests.common import hermite_of_pops, max_rel, oracle_for, rel_l1  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def small_batch():
+    # lengths below, at and above the 256-cell chunk, a 3-cell tube, mixed gamma
+    lengths = np.array([3, 37, 256, 257, 300, 600, 1029])
+    bt = I.tube_batch(len(lengths), seed=11, ratio_max=1e2, mach_max=3.0)
+    bt.lengths = lengths
+    return bt
+
+
+def run_pair(bt, precision, steps, **kw):
+    gs = pond.BatchSolver(bt.lengths, bt.gammas, precision=precision, **kw)
+    rho, ux, p = I.tube_batch_fields(bt)
+    gs.set_primitive(rho, ux, None, p)
+    gs.step(steps)
+    oracles = []
+    for k in range(len(bt.lengths)):
+        pb = I.shock_tube(bt.left[k], bt.right[k], bt.gammas[k], int(bt.lengths[k]))
+        os_ = oracle_for(pb, **kw)
+        os_.step(steps)
+        oracles.append(os_)
+    return gs, oracles
+
+
+@pytest.mark.parametrize("steps", [1, 9])
+def test_batch_fp64_parity(steps):
+    bt = small_batch()
+    kw = dict(tau=1e-5, cfl=0.2, fixed_iters=3, max_iter=8)
+    gs, oracles = run_pair(bt, "fp64", steps, **kw)
+    d = gs.sync()
+    assert d["status"] == pond.POND_OK, d
+    (rho, mx, _, E), tot = gs.moments()
+    t, dt = gs.times()
+    cf, cg, fr = gs.state()
+    xg, _ = gs.face_gauges()
+    fo_off = np.concatenate([[0], np.cumsum(bt.lengths + 1)])
+    iters = 0
+    for k, os_ in enumerate(oracles):
+        a, b = gs.offsets[k], gs.offsets[k + 1]
+        ro, mo, _, Eo = os_.conserved()
+        st = os_.stats()
+        iters += st["face_iters"]
+        assert t[k] == pytest.approx(st["t"], rel=1e-13)
+        assert max_rel(rho[a:b], ro) <= 1e-12 and max_rel(E[a:b], Eo) <= 1e-12
+        assert np.abs(mx[a:b] - mo).max() <= 1e-12 * max(np.abs(mo).max(), np.sqrt(np.abs(Eo * ro).max()))
+        fo, go, uo, To = os_.regauged_state()
+        Af = hermite_of_pops(fo, 1)
+        assert np.abs(cf[a:b] - Af).max() <= 1e-11 * np.abs(ro).max()
+        assert max_rel(fr[a:b, 1], To) <= 1e-12
+        xo, _ = os_.face_gauges()
+        assert max_rel(xg[fo_off[k]:fo_off[k + 1], 1], xo[:, 1]) <= 1e-11
+    assert d["face_iters"] == iters
+
+
+def test_batch_fp32_against_fp64_oracle():
+    bt = small_batch()
+    gs, oracles = run_pair(bt, "fp32", 60, tau=1e-5, cfl=0.2, max_iter=16)
+    d = gs.sync()
+    assert d["status"] == pond.POND_OK, d
+    for k, os_ in enumerate(oracles):
+        if bt.lengths[k] < 30:
+            continue
+        r, u, p = gs.primitive_tube(k, bt.gammas[k])
+        ro, uo, _, po = os_.primitive()
+        assert rel_l1(r, ro) < 1e-4 and rel_l1(p, po) < 1e-4
+        assert np.abs(u - uo).sum() / max(np.abs(uo).sum(), 1e-30) < 1e-4
+
+
+def test_single_tube_batch_matches_grid_solver():
+    pb = I.sod_400()
+    kw = dict(tau=1e-5, cfl=0.5, fixed_iters=3, max_iter=8)
+    b = pond.BatchSolver([400], [1.4], precision="fp64", **kw)
+    b.set_primitive(pb.rho, pb.ux, None, pb.p)
+    g = pond.Solver(pb, precision="fp64", **kw)
+    g.set_primitive()
+    b.step(25)
+    g.step(25)
+    (rb, mb, _, Eb), _ = b.moments(totals=False)
+    (rg, mg, _, Eg), _ = g.moments(totals=False)
+    assert max_rel(rb, rg) <= 1e-13 and max_rel(Eb, Eg) <= 1e-13
