@@ -160,6 +160,11 @@ pond_status pond_init_batch(int64_t n_tubes, const int64_t *lengths, const doubl
  * NULL); waits for the stream. */
 pond_status pond_batch_times(pond_state *s, double *t, double *dt);
 
+/* Per-tube status of a batch (0 running, 1 stopped: the tube reached a non-physical state
+ * and is no longer advanced) and the number of steps each tube has taken (host arrays,
+ * may be NULL); waits for the stream. */
+pond_status pond_batch_status(pond_state *s, int32_t *status, int64_t *steps_done);
+
 /* Waits for the stream and reports the device diagnostics.  Returns
  * POND_ERR_NONPHYSICAL if any cell or face was non-physical, POND_ERR_NOT_CONVERGED if
  * strict_convergence is set and a face stopped at max_iter, else POND_OK. */

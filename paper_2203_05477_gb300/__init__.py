@@ -91,6 +91,7 @@ def _load():
             "pond_init_batch": (ctypes.c_int, [ctypes.c_int64, vp, vp, vp, ctypes.c_double,
                                                ctypes.POINTER(pond_options), ctypes.POINTER(vp)]),
             "pond_batch_times": (ctypes.c_int, [vp, vp, vp]),
+            "pond_batch_status": (ctypes.c_int, [vp, vp, vp]),
             "pond_destroy": (None, [vp]),
             "pond_last_error": (ctypes.c_char_p, []),
         }
@@ -330,6 +331,12 @@ class BatchSolver(Solver):
         dt = np.zeros(self.n_tubes)
         _check(self.lib.pond_batch_times(self.h, _ptr(t), _ptr(dt)))
         return t, dt
+
+    def status(self):
+        st = np.zeros(self.n_tubes, dtype=np.int32)
+        done = np.zeros(self.n_tubes, dtype=np.int64)
+        _check(self.lib.pond_batch_status(self.h, _ptr(st), _ptr(done)))
+        return st, done
 
     def face_gauges(self):
         g = np.zeros((int((self.lengths + 1).sum()), 2))

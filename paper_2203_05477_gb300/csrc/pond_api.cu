@@ -384,6 +384,7 @@ pond_status batch_setup(pond_state *s, const int64_t *lengths, const double *gam
     auto take = [&](size_t b) { size_t o = off; off = align_up(off + b, 256); return o; };
     const size_t o_coff = take(8 * nt), o_foff = take(8 * nt), o_len = take(4 * nt), o_ord = take(4 * nt);
     const size_t o_cv = take(8 * nt), o_dx = take(8 * nt), o_t = take(8 * nt), o_dt = take(8 * nt), o_tot = take(32 * nt);
+    const size_t o_status = take(4 * nt), o_done = take(8 * nt);
     size_t o_sf[2], o_sg[2], o_sfr[2];
     for (int b = 0; b < 2; ++b) {
         o_sf[b] = take(sizeof(R) * 3 * nc);
@@ -416,6 +417,8 @@ pond_status batch_setup(pond_state *s, const int64_t *lengths, const double *gam
     P.t = reinterpret_cast<double *>(B + o_t);
     P.dt = reinterpret_cast<double *>(B + o_dt);
     P.totals = reinterpret_cast<double *>(B + o_tot);
+    P.status = reinterpret_cast<int *>(B + o_status);
+    P.steps_done = reinterpret_cast<long long *>(B + o_done);
     for (int b = 0; b < 2; ++b) {
         P.sf[b] = reinterpret_cast<R *>(B + o_sf[b]);
         P.sg[b] = reinterpret_cast<R *>(B + o_sg[b]);
@@ -759,6 +762,18 @@ pond_status pond_init_batch(int64_t n_tubes, const int64_t *lengths, const doubl
     pond_status st = dispatch_batch(s, [&](auto r) { return batch_setup<decltype(r)>(s, lengths, gammas, dx); });
     if (st != POND_OK) { pond_destroy(s); return st; }
     *out = s;
+    return POND_OK;
+}
+
+pond_status pond_batch_status(pond_state *s, int32_t *status, int64_t *steps_done)
+{
+    if (pond_status st = check_state(s)) return st;
+    if (!s->batch) return fail(POND_ERR_INVALID_ARG, "not a batch state");
+    const int *sp = s->prec == POND_FP32 ? tparams_of<float>(s).status : tparams_of<double>(s).status;
+    const long long *dp = s->prec == POND_FP32 ? tparams_of<float>(s).steps_done : tparams_of<double>(s).steps_done;
+    if (status) CUDA_TRY(cudaMemcpyAsync(status, sp, 4 * s->n_tubes, cudaMemcpyDeviceToHost, s->stream));
+    if (steps_done) CUDA_TRY(cudaMemcpyAsync(steps_done, dp, 8 * s->n_tubes, cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
     return POND_OK;
 }
 

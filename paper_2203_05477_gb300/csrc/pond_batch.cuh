@@ -17,7 +17,7 @@
 namespace pond {
 
 constexpr int kTubeThreads = 256;
-constexpr int kChunk = 256;
+constexpr int kChunk = kTubeThreads - 1;  // kChunk + 1 faces: one per thread
 
 template <typename R>
 struct TubeParams {
@@ -39,11 +39,13 @@ struct TubeParams {
     double *fu, *fT;              // face predictors [nface]
     double *t, *dt;               // per tube
     double *totals;               // per tube [4]: rho, rho u, 0, rho E summed times dx
+    int *status;                  // per tube: 0 running, 1 stopped after a non-physical state
+    long long *steps_done;        // per tube: steps taken
     Diag *diag;
 };
 
 template <typename R>
-__device__ __forceinline__ void tube_stage(const TubeParams<R> &P, int cur, long long c, double Cv, R cp, R ce,
+__device__ __forceinline__ void tube_stage(const TubeParams<R> &P, int cur, long long c, R Cvh, R cp, R ce,
                                            double uref, StagedCell<1, R> &o)
 {
     const long long n = P.ncell;
@@ -53,7 +55,7 @@ __device__ __forceinline__ void tube_stage(const TubeParams<R> &P, int cur, long
     o.A[2] = cp * P.sf[cur][n + c];
     o.A[3] = cp * P.sf[cur][2 * n + c];
     const double T = P.sfr[cur][n + c];
-    o.B[0] = cp * P.sg[cur][c] + ce * R((Cv - 0.5) * double(rho) * T);
+    o.B[0] = cp * P.sg[cur][c] + ce * Cvh * rho * R(T);
     o.B[1] = cp * P.sg[cur][n + c];
     o.B[2] = cp * P.sg[cur][2 * n + c];
     o.du[0] = R(P.sfr[cur][c] - uref);
@@ -62,11 +64,11 @@ __device__ __forceinline__ void tube_stage(const TubeParams<R> &P, int cur, long
 
 // per-step constants of one tube (Eqs. FinalUpdateDUGKS, Fbarplus, FluxTransf)
 struct TubeStep {
-    double dt, cp, ce, wb, we, ca, cb, h_dx, dt_dx;
+    double dt, cp, ce, wb, we, ca, cb, h_dx, dt_dx, inv_dx;
 };
 
 template <typename R>
-__global__ void __launch_bounds__(kTubeThreads)
+__global__ void __launch_bounds__(kTubeThreads, sizeof(R) == 4 ? 3 : 1)
 tube_kernel(const TubeParams<R> P, int steps, int cur0)
 {
     __shared__ StagedCell<1, R> tile[kChunk + 4];
@@ -76,8 +78,11 @@ tube_kernel(const TubeParams<R> P, int steps, int cur0)
     __shared__ TubeStep ks;
     __shared__ double uref_s;
     __shared__ double red[kTubeThreads / 32];
+    __shared__ int tube_bad;
 
     const int tube = P.order[blockIdx.x];
+    if (P.status[tube] != 0) return;  // stopped earlier: its state is not advanced any more
+    if (threadIdx.x == 0) tube_bad = 0;
     const long long c_off = P.cell_off[tube], f_off = P.face_off[tube];
     const int L = P.len[tube];
     const double Cv = P.Cv[tube], dx = P.dx[tube];
@@ -97,6 +102,7 @@ tube_kernel(const TubeParams<R> P, int steps, int cur0)
             ks.we = h / (2.0 * tau + h);
             ks.h_dx = h / dx;
             ks.dt_dx = dt / dx;
+            ks.inv_dx = 1.0 / dx;
         }
         __syncthreads();
         const R cp = R(ks.cp), ce = R(ks.ce), ca = R(ks.ca), cb = R(ks.cb), CvR = R(Cv);
@@ -120,7 +126,7 @@ tube_kernel(const TubeParams<R> P, int steps, int cur0)
             // stage cells c0-2 .. c0+nc+1 (zero-gradient ends)
             for (int t = threadIdx.x; t < nc + 4; t += blockDim.x) {
                 const int k = min(max(c0 - 2 + t, 0), L - 1);
-                tube_stage<R>(P, cur, c_off + k, Cv, cp, ce, utile, tile[t]);
+                tube_stage<R>(P, cur, c_off + k, CvR - R(0.5), cp, ce, utile, tile[t]);
             }
             __syncthreads();
             // faces c0 .. c0+nc: face k lies between cells k-1 and k
@@ -147,6 +153,7 @@ tube_kernel(const TubeParams<R> P, int steps, int cur0)
                     faceT[f] = o.T;
                 } else {
                     if (owned) ++my_nonphys;
+                    tube_bad = 1;
                     const R nan = R(__longlong_as_double(0x7ff8000000000000ll));
 #pragma unroll
                     for (int q = 0; q < 4; ++q) faceF[f][q] = nan;
@@ -190,6 +197,7 @@ tube_kernel(const TubeParams<R> P, int steps, int cur0)
                 const bool ok = cell_finish<1, R>(H, G, uc, Tc, invTc, sqTc, CvR, Ho, Go, un, Tn);
                 if (!ok) {
                     ++my_nonphys;
+                    tube_bad = 1;
                     atomicCAS((unsigned long long *)&P.diag->first_bad, (unsigned long long)-1ll, (unsigned long long)c);
                 }
                 P.sf[nxt][c] = Ho[0];
@@ -202,7 +210,7 @@ tube_kernel(const TubeParams<R> P, int steps, int cur0)
                 P.sfr[nxt][n + c] = Tn;
                 if (ok) {
                     if constexpr (sizeof(R) == 8) rate_d = fmax(rate_d, (fabs(un[0]) + sqrt(Tn) * kCHi) / dx);
-                    else rate = fmaxf(rate, (fabsf(float(un[0])) + sqrtf(float(Tn)) * float(kCHi)) * float(1.0 / dx));
+                    else rate = fmaxf(rate, (fabsf(float(un[0])) + sqrtf(float(Tn)) * float(kCHi)) * float(ks.inv_dx));
                 }
             }
             __syncthreads();
@@ -218,8 +226,11 @@ tube_kernel(const TubeParams<R> P, int steps, int cur0)
             for (int w = 0; w < kTubeThreads / 32; ++w) rm = fmax(rm, red[w]);
             P.t[tube] += ks.dt;
             P.dt[tube] = P.cfl / rm;
+            P.steps_done[tube] += 1;
+            if (tube_bad) P.status[tube] = 1;
         }
         __syncthreads();
+        if (tube_bad) break;  // a non-physical tube stops; pond_sync reports it
     }
     // warp-aggregated diagnostics
 #pragma unroll
@@ -246,6 +257,7 @@ __global__ void __launch_bounds__(kTubeThreads)
 tube_init_kernel(const TubeParams<R> P, int cur, const double *rho, const double *ux, const double *p)
 {
     __shared__ double red[kTubeThreads / 32];
+    __shared__ int any_bad;
     const int tube = blockIdx.x;
     const long long c_off = P.cell_off[tube], f_off = P.face_off[tube];
     const int L = P.len[tube];
@@ -253,6 +265,8 @@ tube_init_kernel(const TubeParams<R> P, int cur, const double *rho, const double
     const long long n = P.ncell;
     double rate = 0.0;
     unsigned long long bad = 0;
+    if (threadIdx.x == 0) any_bad = 0;
+    __syncthreads();
     for (int k = threadIdx.x; k < L; k += blockDim.x) {
         const long long c = c_off + k;
         const double r = rho[c], T = p[c] / r, u = ux[c];
@@ -279,7 +293,7 @@ tube_init_kernel(const TubeParams<R> P, int cur, const double *rho, const double
         P.fu[f_off + k] = m / r;
         P.fT[f_off + k] = (E - 0.5 * m * m / r) / (Cv * r);
     }
-    if (bad) { atomicAdd(&P.diag->nonphys, bad); atomicOr(&P.diag->flags, FLAG_NONPHYSICAL); }
+    if (bad) { atomicAdd(&P.diag->nonphys, bad); atomicOr(&P.diag->flags, FLAG_NONPHYSICAL); any_bad = 1; }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) rate = fmax(rate, __shfl_down_sync(0xffffffffu, rate, o));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = rate;
@@ -289,6 +303,8 @@ tube_init_kernel(const TubeParams<R> P, int cur, const double *rho, const double
         for (int w = 0; w < kTubeThreads / 32; ++w) rm = fmax(rm, red[w]);
         P.t[tube] = 0.0;
         P.dt[tube] = P.cfl / rm;
+        P.steps_done[tube] = 0;
+        P.status[tube] = any_bad;
     }
 }
 
