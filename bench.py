@@ -32,9 +32,10 @@ METRIC = "cell-updates/s (MLUPS) and % HBM roofline, FP32+learned vs plain FP64,
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 N_SMS, FP32_LANES = 152, 128
-# FP32 operations (FMA = 2) of one corrector pass at one D2Q16 face, from the ncu
-# instruction counts of the face kernel (see profiles/); used for the ALU roofline.
-FLOPS_PER_FACE_PASS = 5800.0
+# FP32 operations (FMA = 2) of one corrector pass at one D2Q16 face (per-face overhead
+# included), from the ncu instruction counts of the face kernel; used for the ALU roofline
+FACE_KERNEL_DRAM_BYTES = 136.7e6 + 178.4e6  # ncu dram read + write of one launch at 1024^2
+FLOPS_PER_FACE_PASS = 4550.0
 # algorithmic bytes per cell-update of the FP32 D2Q16 layout: the face kernel reads the
 # cell state (8 + 6 FP32 coefficients + 3 FP64 frame = 80 B) and two face predictors
 # (2 x 24 B) and writes two faces (2 x (16 x 4 + 24) B)
@@ -325,7 +326,7 @@ def main():
         "fp64": {"value": fp64_value, "unit": "MLUPS", "steps": args.fp64_steps, "speedup_fp32": value / fp64_value},
         "corrector": {"passes_per_face": face_passes / max(faces, 1), "status_ok": status_ok},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp32_peak, "traffic": None, "kernel": "face_kernel<2,float>",
+                     "frac": achieved / fp32_peak, "traffic": FACE_KERNEL_DRAM_BYTES, "kernel": "face_kernel<2,float>",
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % sm_mhz,
                      "face_ms": face_ms_avg, "cell_ms": ms_cell / args.steps,
                      "hbm_gbs": face_gbs, "hbm_frac": face_gbs / hbm_peak,
