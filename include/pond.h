@@ -165,6 +165,44 @@ pond_status pond_batch_times(pond_state *s, double *t, double *dt);
  * may be NULL); waits for the stream. */
 pond_status pond_batch_status(pond_state *s, int32_t *status, int64_t *steps_done);
 
+/* ---- Learned face-gauge predictor (D2Q16 grids).  Not part of the paper: a small MLP
+ * (48 -> 64 -> 64 -> 3, BF16 tensor-core GEMMs with FP32 accumulation) predicts each face's
+ * converged corrector frame from its stencil, and the prediction replaces the previous
+ * half step's frame as the corrector's starting point.  The corrector and its convergence
+ * test are unchanged.  Parameters: POND_MLP_PARAMS FP32 values laid out
+ * W1[64][48] b1[64] W2[64][64] b2[64] W3[16][64] b3[16]; a new state starts from seeded
+ * random W1, W2 and zero W3, b (prediction = the previous frame). */
+#define POND_MLP_PARAMS 8336
+#define POND_MLP_FEATURES 48
+#define POND_MLP_PAIR_STRIDE 52   /* a training pair: 48 features, 3 targets, 1 pad */
+
+/* Runs n_steps plain steps and samples (features, converged face frame) pairs from every
+ * every-th converged face into pairs (device, [cap][POND_MLP_PAIR_STRIDE] floats); the
+ * number written (at most cap) goes to *n_out. */
+pond_status pond_gauge_collect(pond_state *s, int64_t n_steps, float *pairs, int64_t cap, int every, int64_t *n_out);
+
+/* Trains the state's network on n pairs (device) with Adam (learning rate lr) and mean
+ * squared error, in minibatches of `batch` consecutive pairs (the caller shuffles), for
+ * `epochs` epochs; loss_out (host, may be NULL) receives the mean loss of each epoch. */
+pond_status pond_gauge_train(pond_state *s, const float *pairs, int64_t n, int epochs, int batch, float lr,
+                             float *loss_out);
+
+/* Switches the learned predictor on (nonzero) or off for the following steps. */
+pond_status pond_gauge_enable(pond_state *s, int on);
+
+/* Copies the network parameters from / to host arrays of POND_MLP_PARAMS floats. */
+pond_status pond_gauge_set_params(pond_state *s, const float *params);
+pond_status pond_gauge_get_params(pond_state *s, float *params);
+
+/* Stand-alone network calls on device arrays, enqueued on `stream` (NULL: legacy default
+ * stream) and waited for: forward pass of n rows x[n][ldx] (first 48 columns) into
+ * out[n][16]; and the gradient of the mean squared error against the targets held in
+ * columns 48..50 of y[n][ldy] into grad[POND_MLP_PARAMS] and the loss into *loss (device
+ * floats).  pond_mlp_gradient allocates its activation scratch with cudaMalloc. */
+pond_status pond_mlp_forward(const float *params, const float *x, int ldx, int64_t n, float *out, void *stream);
+pond_status pond_mlp_gradient(const float *params, const float *x, int ldx, const float *y, int ldy, int64_t n,
+                              float *grad, float *loss, void *stream);
+
 /* Waits for the stream and reports the device diagnostics.  Returns
  * POND_ERR_NONPHYSICAL if any cell or face was non-physical, POND_ERR_NOT_CONVERGED if
  * strict_convergence is set and a face stopped at max_iter, else POND_OK. */

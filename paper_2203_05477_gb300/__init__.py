@@ -27,6 +27,7 @@ POND_ERR_NONPHYSICAL, POND_ERR_NOT_CONVERGED, POND_ERR_TIMEOUT = 5, 6, 7
 POND_D1Q3, POND_D1Q4, POND_D2Q16, POND_D2Q9 = 0, 1, 2, 3
 POND_FP64, POND_FP32 = 0, 1
 POND_VANLEER, POND_MINMOD = 0, 1
+MLP_PARAMS, MLP_FEATURES, MLP_PAIR_STRIDE = 8336, 48, 52
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
@@ -92,6 +93,13 @@ def _load():
                                                ctypes.POINTER(pond_options), ctypes.POINTER(vp)]),
             "pond_batch_times": (ctypes.c_int, [vp, vp, vp]),
             "pond_batch_status": (ctypes.c_int, [vp, vp, vp]),
+            "pond_gauge_collect": (ctypes.c_int, [vp, ctypes.c_int64, vp, ctypes.c_int64, ctypes.c_int, vp]),
+            "pond_gauge_train": (ctypes.c_int, [vp, vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_float, vp]),
+            "pond_gauge_enable": (ctypes.c_int, [vp, ctypes.c_int]),
+            "pond_gauge_set_params": (ctypes.c_int, [vp, vp]),
+            "pond_gauge_get_params": (ctypes.c_int, [vp, vp]),
+            "pond_mlp_forward": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int64, vp, vp]),
+            "pond_mlp_gradient": (ctypes.c_int, [vp, vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int64, vp, vp, vp]),
             "pond_destroy": (None, [vp]),
             "pond_last_error": (ctypes.c_char_p, []),
         }
@@ -280,6 +288,35 @@ class Solver:
     def launch_count(self):
         return int(self.lib.pond_launch_count(self.h))
 
+    # ---- learned face-gauge predictor (D2Q16)
+    def gauge_collect(self, n_steps, cap, every=4):
+        """Runs n_steps plain steps and returns the sampled training pairs (device tensor)."""
+        import torch
+        pairs = torch.empty((int(cap), MLP_PAIR_STRIDE), dtype=torch.float32, device="cuda")
+        n = ctypes.c_int64()
+        _check(self.lib.pond_gauge_collect(self.h, int(n_steps), pairs.data_ptr(), int(cap), int(every), ctypes.byref(n)))
+        return pairs[: n.value]
+
+    def gauge_train(self, pairs, epochs=10, batch=4096, lr=1e-3):
+        pairs = pairs.contiguous()
+        losses = np.zeros(int(epochs), dtype=np.float32)
+        _check(self.lib.pond_gauge_train(self.h, pairs.data_ptr(), int(pairs.shape[0]), int(epochs), int(batch),
+                                         float(lr), _ptr(losses)))
+        return losses
+
+    def gauge_enable(self, on=True):
+        _check(self.lib.pond_gauge_enable(self.h, int(bool(on))))
+
+    def gauge_params(self):
+        p = np.zeros(MLP_PARAMS, dtype=np.float32)
+        _check(self.lib.pond_gauge_get_params(self.h, _ptr(p)))
+        return p
+
+    def set_gauge_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == MLP_PARAMS
+        _check(self.lib.pond_gauge_set_params(self.h, _ptr(p)))
+
 
 class BatchSolver(Solver):
     """Many independent 1D shock tubes (D1Q4) advanced by one persistent launch per call."""
@@ -351,3 +388,25 @@ class BatchSolver(Solver):
         u = m / r
         T = (e - 0.5 * m * m / r) / (cv * r)
         return r, u, r * T
+
+
+def mlp_forward(params, x):
+    """Forward pass of the predictor network on device tensors: params [8336], x [n][>=48]."""
+    import torch
+    n, ld = x.shape
+    out = torch.empty((n, 16), dtype=torch.float32, device=x.device)
+    st = torch.cuda.current_stream().cuda_stream
+    _check(_load().pond_mlp_forward(params.data_ptr(), x.data_ptr(), int(ld), int(n), out.data_ptr(), st))
+    return out
+
+
+def mlp_gradient(params, x, y):
+    """Mean squared error and its gradient; targets in columns 48..50 of y."""
+    import torch
+    n, ldx = x.shape
+    grad = torch.empty(MLP_PARAMS, dtype=torch.float32, device=x.device)
+    loss = torch.zeros(1, dtype=torch.float32, device=x.device)
+    st = torch.cuda.current_stream().cuda_stream
+    _check(_load().pond_mlp_gradient(params.data_ptr(), x.data_ptr(), int(ldx), y.data_ptr(), int(y.shape[1]), int(n),
+                                     grad.data_ptr(), loss.data_ptr(), st))
+    return float(loss.item()), grad

@@ -8,7 +8,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libpond.so")
 SOURCES = ["pond_api.cu"]
-HEADERS = ["pond_core.cuh", "pond_kernels.cuh", "pond_batch.cuh"]
+HEADERS = ["pond_core.cuh", "pond_kernels.cuh", "pond_batch.cuh", "pond_tc.cuh", "pond_mlp.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -17,6 +17,7 @@
 
 #include "../../include/pond.h"
 #include "pond_batch.cuh"
+#include <cuda_bf16.h>
 
 namespace {
 
@@ -62,6 +63,16 @@ struct pond_state {
     int64_t launches = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
+    // learned face-gauge predictor
+    float *mlp = nullptr, *mlp_m = nullptr, *mlp_v = nullptr, *mlp_grad = nullptr, *mlp_loss = nullptr;
+    unsigned int *mlp_err = nullptr;
+    unsigned long long *pair_count = nullptr;
+    char *mlp_block = nullptr;
+    char *train_scratch = nullptr;
+    int64_t train_rows = 0;
+    bool learned = false;
+    int adam_t = 0;
+    int sms = 152;
     // batched tubes
     bool batch = false;
     int64_t n_tubes = 0, ncell = 0, nface = 0, steps_taken = 0;
@@ -196,13 +207,69 @@ pond_status set_primitive_impl(pond_state *s, const double *rho, const double *u
     return POND_OK;
 }
 
+// network parameters: seeded Xavier-uniform W1, W2; zero W3 and biases (the untrained
+// predictor returns the previous half step's frame)
+void mlp_default_params(std::vector<float> &p)
+{
+    namespace M = pond::mlp;
+    p.assign(M::kParams, 0.f);
+    uint64_t st = 0x243F6A8885A308D3ull;
+    auto uni = [&]() {
+        st = st * 6364136223846793005ull + 1442695040888963407ull;
+        return float((st >> 40) & 0xFFFFFF) / float(1 << 24) * 2.f - 1.f;
+    };
+    const float a1 = std::sqrt(6.f / float(M::kUsed + M::kHid)), a2 = std::sqrt(6.f / float(2 * M::kHid));
+    for (int o = 0; o < M::kHid; ++o)
+        for (int i = 0; i < M::kUsed; ++i) p[M::oW1 + o * M::kIn + i] = a1 * uni();
+    for (int e = 0; e < M::kHid * M::kHid; ++e) p[M::oW2 + e] = a2 * uni();
+}
+
+pond_status mlp_setup(pond_state *s)
+{
+    namespace M = pond::mlp;
+    size_t off = 0;
+    auto take = [&](size_t b) { size_t o = off; off = align_up(off + b, 256); return o; };
+    const size_t o_p = take(4 * M::kParams), o_m = take(4 * M::kParams), o_v = take(4 * M::kParams),
+                 o_g = take(4 * M::kParams), o_l = take(64), o_e = take(64), o_c = take(64);
+    s->mlp_block = static_cast<char *>(dev_alloc(s, off));
+    if (!s->mlp_block) return fail(POND_ERR_OOM, "device allocation of %zu bytes failed", off);
+    CUDA_TRY(cudaMemsetAsync(s->mlp_block, 0, off, s->stream));
+    s->mlp = reinterpret_cast<float *>(s->mlp_block + o_p);
+    s->mlp_m = reinterpret_cast<float *>(s->mlp_block + o_m);
+    s->mlp_v = reinterpret_cast<float *>(s->mlp_block + o_v);
+    s->mlp_grad = reinterpret_cast<float *>(s->mlp_block + o_g);
+    s->mlp_loss = reinterpret_cast<float *>(s->mlp_block + o_l);
+    s->mlp_err = reinterpret_cast<unsigned int *>(s->mlp_block + o_e);
+    s->pair_count = reinterpret_cast<unsigned long long *>(s->mlp_block + o_c);
+    std::vector<float> p;
+    mlp_default_params(p);
+    CUDA_TRY(cudaMemcpyAsync(s->mlp, p.data(), 4 * M::kParams, cudaMemcpyHostToDevice, s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    CUDA_TRY(cudaFuncSetAttribute(pond::mlp::tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, M::kTileSmem));
+    CUDA_TRY(cudaFuncSetAttribute(pond::gauge_predict_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, M::kTileSmem));
+    CUDA_TRY(cudaFuncSetAttribute(pond::gauge_predict_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, M::kTileSmem));
+    int sms = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device));
+    s->sms = sms;
+    return POND_OK;
+}
+
 template <int D, typename R>
-void launch_step(pond_state *s)
+void launch_step(pond_state *s, bool collect = false)
 {
     auto &P = params_of<D, R>(s);
     using FT = pond::FaceTile<D>;
     dim3 fg(unsigned((P.nx + 1 + FT::TX - 1) / FT::TX), D == 2 ? unsigned((P.ny + 1 + FT::TY - 1) / FT::TY) : 1u);
-    pond::face_kernel<D, R><<<fg, FT::THREADS, 0, s->stream>>>(P);
+    if constexpr (D == 2) {
+        if (s->learned) {
+            pond::gauge_predict_kernel<R><<<unsigned(2 * s->sms), pond::mlp::kThreads, pond::mlp::kTileSmem, s->stream>>>(P);
+            s->launches += 1;
+        }
+        if (collect) pond::face_kernel<D, R, true><<<fg, FT::THREADS, 0, s->stream>>>(P);
+        else pond::face_kernel<D, R><<<fg, FT::THREADS, 0, s->stream>>>(P);
+    } else {
+        pond::face_kernel<D, R><<<fg, FT::THREADS, 0, s->stream>>>(P);
+    }
     pond::cell_kernel<D, R><<<blocks_for(P.ncell(), pond::CellBlock<D>::THREADS), pond::CellBlock<D>::THREADS, 0, s->stream>>>(P);
 }
 
@@ -213,21 +280,25 @@ pond_status step_impl(pond_state *s, int64_t n_steps)
     if (left >= kGraphSteps) {
         if (!s->graph_exec) {
             CUDA_TRY(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+            const int64_t before = s->launches;
             for (int k = 0; k < kGraphSteps; ++k) launch_step<D, R>(s);
+            s->launches = before;
             cudaGraph_t g = nullptr;
             CUDA_TRY(cudaStreamEndCapture(s->stream, &g));
             s->graph = g;
             CUDA_TRY(cudaGraphInstantiate(&s->graph_exec, g, 0));
         }
+        const int per_step = 2 + ((D == 2 && s->learned) ? 1 : 0);
         while (left >= kGraphSteps) {
             CUDA_TRY(cudaGraphLaunch(s->graph_exec, s->stream));
-            s->launches += 2 * kGraphSteps;
+            s->launches += per_step * kGraphSteps;
             left -= kGraphSteps;
         }
     }
     for (; left > 0; --left) {
+        const int64_t before = s->launches;
         launch_step<D, R>(s);
-        s->launches += 2;
+        s->launches = before + 2 + ((D == 2 && s->learned) ? 1 : 0);
     }
     CUDA_TRY(cudaGetLastError());
     return POND_OK;
@@ -244,6 +315,12 @@ pond_status step_timed_impl(pond_state *s, int64_t n_steps, double *ms)
     for (auto &e : ev) CUDA_TRY(cudaEventCreate(&e));
     CUDA_TRY(cudaEventRecord(ev[0], s->stream));
     for (int64_t k = 0; k < n_steps; ++k) {
+        if constexpr (D == 2) {
+            if (s->learned) {
+                pond::gauge_predict_kernel<R><<<unsigned(2 * s->sms), pond::mlp::kThreads, pond::mlp::kTileSmem, s->stream>>>(P);
+                s->launches += 1;
+            }
+        }
         pond::face_kernel<D, R><<<fg, FT::THREADS, 0, s->stream>>>(P);
         CUDA_TRY(cudaEventRecord(ev[2 * k + 1], s->stream));
         pond::cell_kernel<D, R><<<cb, pond::CellBlock<D>::THREADS, 0, s->stream>>>(P);
@@ -633,6 +710,14 @@ pond_status pond_init(const pond_grid *grid, pond_velset velset, double gamma, d
         s->own_stream = true;
     }
     pond_status st = dispatch(s, [&](auto d, auto r) { return setup<decltype(d)::value, decltype(r)>(s); });
+    if (st == POND_OK && D == 2) {
+        st = mlp_setup(s);
+        if (st == POND_OK) {
+            auto wire = [&](auto &P) { P.mlp = s->mlp; P.mlp_err = s->mlp_err; P.pair_count = s->pair_count; P.pair_every = 1; };
+            if (s->prec == POND_FP32) wire(params_of<2, float>(s));
+            else wire(params_of<2, double>(s));
+        }
+    }
     if (st == POND_OK) st = reset_clock(s);
     if (st != POND_OK) { pond_destroy(s); return st; }
     *out = s;
@@ -789,6 +874,210 @@ pond_status pond_batch_times(pond_state *s, double *t, double *dt)
     return POND_OK;
 }
 
+// ------------------------------------------------------------ learned predictor
+
+}  // extern "C"
+
+namespace {
+
+pond_status check_gauge(pond_state *s)
+{
+    if (pond_status st = check_state(s)) return st;
+    if (s->batch || s->D != 2 || !s->mlp) return fail(POND_ERR_UNSUPPORTED, "the learned predictor needs a D2Q16 grid state");
+    return POND_OK;
+}
+
+template <typename R>
+pond_status gauge_collect_impl(pond_state *s, int64_t n_steps, float *pairs, int64_t cap, int every, int64_t *n_out)
+{
+    auto &P = params_of<2, R>(s);
+    CUDA_TRY(cudaMemsetAsync(s->pair_count, 0, sizeof(unsigned long long), s->stream));
+    P.pairs = pairs;
+    P.pair_cap = cap;
+    P.pair_every = every;
+    for (int64_t k = 0; k < n_steps; ++k) {
+        launch_step<2, R>(s, true);
+        s->launches += 2;
+    }
+    P.pairs = nullptr;
+    CUDA_TRY(cudaGetLastError());
+    unsigned long long cnt = 0;
+    CUDA_TRY(cudaMemcpyAsync(&cnt, s->pair_count, sizeof(cnt), cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    if (n_out) *n_out = int64_t(std::min<unsigned long long>(cnt, (unsigned long long)cap));
+    return POND_OK;
+}
+
+// activation scratch of a training minibatch of `rows` rows: out, H1, H2, dOut, dZ1, dZ2
+struct TrainScratch {
+    float *out;
+    __nv_bfloat16 *H1, *H2, *dOut, *dZ1, *dZ2;
+    static size_t bytes(int64_t rows) { return size_t(rows) * (16 * 4 + 2 * (64 + 64 + 16 + 64 + 64)) + 1024; }
+    static TrainScratch carve(char *base, int64_t rows)
+    {
+        TrainScratch t;
+        size_t off = 0;
+        auto take = [&](size_t b) { size_t o = off; off = align_up(off + b, 256); return base + o; };
+        t.out = reinterpret_cast<float *>(take(size_t(rows) * 64));
+        t.H1 = reinterpret_cast<__nv_bfloat16 *>(take(size_t(rows) * 128));
+        t.H2 = reinterpret_cast<__nv_bfloat16 *>(take(size_t(rows) * 128));
+        t.dOut = reinterpret_cast<__nv_bfloat16 *>(take(size_t(rows) * 32));
+        t.dZ1 = reinterpret_cast<__nv_bfloat16 *>(take(size_t(rows) * 128));
+        t.dZ2 = reinterpret_cast<__nv_bfloat16 *>(take(size_t(rows) * 128));
+        return t;
+    }
+};
+
+// one gradient evaluation: forward, loss, backward through the activations, weight grads
+pond_status mlp_grad_launch(const float *prm, const float *x, int ldx, const float *y, int ldy, int64_t n,
+                            const TrainScratch &t, float *grad, float *loss, unsigned int *err, cudaStream_t st)
+{
+    namespace M = pond::mlp;
+    const unsigned tiles = unsigned((n + M::kRows - 1) / M::kRows);
+    M::tile_kernel<<<tiles, M::kThreads, M::kTileSmem, st>>>(prm, x, ldx, y, ldy, n, t.out, t.H1, t.H2, t.dOut, t.dZ1,
+                                                               t.dZ2, loss, err);
+    M::wgrad_kernel<<<3, M::kThreads, 0, st>>>(x, ldx, t.H1, t.H2, t.dOut, t.dZ1, t.dZ2, n, grad, err);
+    CUDA_TRY(cudaGetLastError());
+    return POND_OK;
+}
+
+__device__ unsigned int g_standalone_err;
+
+}  // namespace
+
+extern "C" {
+
+pond_status pond_gauge_collect(pond_state *s, int64_t n_steps, float *pairs, int64_t cap, int every, int64_t *n_out)
+{
+    if (pond_status st = check_gauge(s)) return st;
+    if (!pairs || cap <= 0 || every < 1 || n_steps < 0) return fail(POND_ERR_INVALID_ARG, "bad collect arguments");
+    return s->prec == POND_FP32 ? gauge_collect_impl<float>(s, n_steps, pairs, cap, every, n_out)
+                                : gauge_collect_impl<double>(s, n_steps, pairs, cap, every, n_out);
+}
+
+pond_status pond_gauge_train(pond_state *s, const float *pairs, int64_t n, int epochs, int batch, float lr, float *loss_out)
+{
+    namespace M = pond::mlp;
+    if (pond_status st = check_gauge(s)) return st;
+    if (!pairs || n <= 0 || epochs < 1 || batch < 1 || !(lr > 0.f)) return fail(POND_ERR_INVALID_ARG, "bad train arguments");
+    if (s->train_rows < batch) {
+        dev_free(s, s->train_scratch);
+        s->train_scratch = static_cast<char *>(dev_alloc(s, TrainScratch::bytes(batch)));
+        if (!s->train_scratch) return fail(POND_ERR_OOM, "training scratch allocation failed");
+        s->train_rows = batch;
+    }
+    CUDA_TRY(cudaFuncSetAttribute(M::tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, M::kTileSmem));
+    const TrainScratch t = TrainScratch::carve(s->train_scratch, batch);
+    CUDA_TRY(cudaMemsetAsync(s->mlp_err, 0, sizeof(unsigned int), s->stream));
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    for (int ep = 0; ep < epochs; ++ep) {
+        CUDA_TRY(cudaMemsetAsync(s->mlp_loss, 0, sizeof(float), s->stream));
+        int64_t nb = 0;
+        for (int64_t b0 = 0; b0 < n; b0 += batch, ++nb) {
+            const int64_t rows = std::min<int64_t>(batch, n - b0);
+            const float *xb = pairs + b0 * M::kPairStride;
+            pond_status st = mlp_grad_launch(s->mlp, xb, M::kPairStride, xb, M::kPairStride, rows, t, s->mlp_grad,
+                                             s->mlp_loss, s->mlp_err, s->stream);
+            if (st != POND_OK) return st;
+            ++s->adam_t;
+            const float bc1 = 1.f - std::pow(b1, float(s->adam_t)), bc2 = 1.f - std::pow(b2, float(s->adam_t));
+            M::adam_kernel<<<(M::kParams + 255) / 256, 256, 0, s->stream>>>(s->mlp, s->mlp_grad, s->mlp_m, s->mlp_v, lr, b1,
+                                                                             b2, eps, bc1, bc2);
+            s->launches += 3;
+        }
+        CUDA_TRY(cudaGetLastError());
+        float l = 0.f;
+        CUDA_TRY(cudaMemcpyAsync(&l, s->mlp_loss, sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+        CUDA_TRY(cudaStreamSynchronize(s->stream));
+        if (loss_out) loss_out[ep] = l / float(nb);
+    }
+    unsigned int err = 0;
+    CUDA_TRY(cudaMemcpy(&err, s->mlp_err, sizeof(err), cudaMemcpyDeviceToHost));
+    if (err) return fail(POND_ERR_TIMEOUT, "a tensor-core wait timed out during training");
+    return POND_OK;
+}
+
+pond_status pond_gauge_enable(pond_state *s, int on)
+{
+    if (pond_status st = check_gauge(s)) return st;
+    if (bool(on) != s->learned) {
+        // the captured step graph depends on the set of kernels
+        if (s->graph_exec) { cudaGraphExecDestroy(s->graph_exec); s->graph_exec = nullptr; }
+        if (s->graph) { cudaGraphDestroy(s->graph); s->graph = nullptr; }
+    }
+    s->learned = on != 0;
+    return POND_OK;
+}
+
+pond_status pond_gauge_set_params(pond_state *s, const float *params)
+{
+    if (pond_status st = check_gauge(s)) return st;
+    if (!params) return fail(POND_ERR_INVALID_ARG, "params is NULL");
+    CUDA_TRY(cudaMemcpyAsync(s->mlp, params, 4 * pond::mlp::kParams, cudaMemcpyHostToDevice, s->stream));
+    CUDA_TRY(cudaMemsetAsync(s->mlp_m, 0, 4 * pond::mlp::kParams, s->stream));
+    CUDA_TRY(cudaMemsetAsync(s->mlp_v, 0, 4 * pond::mlp::kParams, s->stream));
+    s->adam_t = 0;
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return POND_OK;
+}
+
+pond_status pond_gauge_get_params(pond_state *s, float *params)
+{
+    if (pond_status st = check_gauge(s)) return st;
+    if (!params) return fail(POND_ERR_INVALID_ARG, "params is NULL");
+    CUDA_TRY(cudaMemcpyAsync(params, s->mlp, 4 * pond::mlp::kParams, cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return POND_OK;
+}
+
+pond_status pond_mlp_forward(const float *params, const float *x, int ldx, int64_t n, float *out, void *stream)
+{
+    namespace M = pond::mlp;
+    if (!params || !x || !out || n <= 0 || ldx < M::kIn) return fail(POND_ERR_INVALID_ARG, "bad forward arguments");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CUDA_TRY(cudaFuncSetAttribute(M::tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, M::kTileSmem));
+    unsigned int *err = nullptr;
+    CUDA_TRY(cudaGetSymbolAddress(reinterpret_cast<void **>(&err), g_standalone_err));
+    CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(unsigned int), st));
+    M::tile_kernel<<<unsigned((n + M::kRows - 1) / M::kRows), M::kThreads, M::kTileSmem, st>>>(
+        params, x, ldx, nullptr, 0, n, out, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, err);
+    CUDA_TRY(cudaGetLastError());
+    unsigned int e = 0;
+    CUDA_TRY(cudaMemcpyAsync(&e, err, sizeof(e), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (e) return fail(POND_ERR_TIMEOUT, "a tensor-core wait timed out");
+    return POND_OK;
+}
+
+pond_status pond_mlp_gradient(const float *params, const float *x, int ldx, const float *y, int ldy, int64_t n, float *grad,
+                              float *loss, void *stream)
+{
+    namespace M = pond::mlp;
+    if (!params || !x || !y || !grad || !loss || n <= 0 || ldx < M::kIn || ldy < M::kIn + M::kOut)
+        return fail(POND_ERR_INVALID_ARG, "bad gradient arguments");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CUDA_TRY(cudaFuncSetAttribute(M::tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, M::kTileSmem));
+    char *scratch = nullptr;
+    CUDA_TRY(cudaMalloc(&scratch, TrainScratch::bytes(n)));
+    unsigned int *err = nullptr;
+    pond_status r = POND_OK;
+    cudaError_t ce = cudaGetSymbolAddress(reinterpret_cast<void **>(&err), g_standalone_err);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(err, 0, sizeof(unsigned int), st);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(loss, 0, sizeof(float), st);
+    if (ce != cudaSuccess) r = fail(POND_ERR_CUDA, "%s", cudaGetErrorString(ce));
+    if (r == POND_OK) r = mlp_grad_launch(params, x, ldx, y, ldy, n, TrainScratch::carve(scratch, n), grad, loss, err, st);
+    unsigned int e = 0;
+    if (r == POND_OK) {
+        ce = cudaMemcpyAsync(&e, err, sizeof(e), cudaMemcpyDeviceToHost, st);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+        if (ce != cudaSuccess) r = fail(POND_ERR_CUDA, "%s", cudaGetErrorString(ce));
+        else if (e) r = fail(POND_ERR_TIMEOUT, "a tensor-core wait timed out");
+    }
+    cudaStreamSynchronize(st);
+    cudaFree(scratch);
+    return r;
+}
+
 int64_t pond_launch_count(const pond_state *s) { return s ? s->launches : 0; }
 
 void pond_destroy(pond_state *s)
@@ -798,6 +1087,8 @@ void pond_destroy(pond_state *s)
     if (s->graph_exec) cudaGraphExecDestroy(s->graph_exec);
     if (s->graph) cudaGraphDestroy(s->graph);
     dev_free(s, s->base);
+    dev_free(s, s->mlp_block);
+    dev_free(s, s->train_scratch);
     if (s->own_stream) cudaStreamDestroy(s->stream);
     delete s;
 }

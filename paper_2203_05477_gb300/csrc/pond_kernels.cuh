@@ -17,6 +17,7 @@
 #pragma once
 
 #include "pond_core.cuh"
+#include "pond_mlp.cuh"
 
 namespace pond {
 
@@ -85,6 +86,13 @@ struct Params {
     double *yfr;
     Clock *clock;
     Diag *diag;
+    // learned face-gauge predictor: parameters, and sampling of training pairs
+    const float *mlp;
+    float *pairs;
+    unsigned long long *pair_count;
+    long long pair_cap;
+    int pair_every;
+    unsigned int *mlp_err;
     __host__ __device__ long long ncell() const { return nx * ny; }
     __host__ __device__ long long nxf() const { return (nx + 1) * ny; }
     __host__ __device__ long long nyf() const { return nx * (ny + 1); }
@@ -549,10 +557,12 @@ __device__ __forceinline__ void solve_face(const StagedCell<D, R> *const *cells,
     }
 }
 
-template <int D, typename R>
 #ifndef POND_FACE_MIN_BLOCKS
 #define POND_FACE_MIN_BLOCKS 2
 #endif
+// COLLECT: also write (features, converged frame) pairs of sampled converged faces for the
+// learned predictor (a separate instantiation, so the plain kernel carries none of it)
+template <int D, typename R, bool COLLECT = false>
 __global__ void __launch_bounds__(FaceTile<D>::THREADS, (D == 2 && sizeof(R) == 4) ? POND_FACE_MIN_BLOCKS : 1)
 face_kernel(const Params<D, R> P)
 {
@@ -625,8 +635,35 @@ face_kernel(const Params<D, R> P)
         cfg.h_dt = R(D == 2 ? (swap ? K.h_dx : K.h_dy) : 0.0);
         cfg.Cv = R(P.Cv); cfg.tol = R(P.tol); cfg.wb = R(K.wb); cfg.we = R(K.we);
         cfg.limiter = P.limiter; cfg.max_iter = P.max_iter; cfg.fixed_iters = P.fixed_iters;
-        solve_face<D, R>(cells, swap, uref, R(Frm[D * nf + fidx]), utile, cfg, o);
+        const double Tp = Frm[D * nf + fidx];
+        solve_face<D, R>(cells, swap, uref, R(Tp), utile, cfg, o);
         my_iters = o.iters; my_nonconv = o.done ? 0 : 1; my_fallbacks = o.fallbacks;
+        if constexpr (COLLECT && D == 2) {
+            const unsigned long long hsh = (unsigned long long)(fidx * 2 + dir + 1) * 0x9E3779B97F4A7C15ull ^
+                                           (unsigned long long)(K.steps + 1) * 0xBF58476D1CE4E5B9ull;
+            if (o.have && o.done && Tp > 0.0 && ((hsh >> 33) % (unsigned long long)P.pair_every) == 0) {
+                const int na = swap ? 1 : 0, ta = 1 - na;
+                const float dn = float(uref[na] - utile[na]), dt_ = float(uref[ta] - utile[ta]);
+                mlp::SlotPrim sp[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    sp[q] = {float(cells[q]->A[0]), float(cells[q]->du[na]) - dn, float(cells[q]->du[ta]) - dt_,
+                             float(cells[q]->T)};
+                float f[mlp::kIn];
+                mlp::features(sp, float(Tp), float(cfg.h_dn), f);
+                const unsigned long long slot = atomicAdd(P.pair_count, 1ull);
+                if (slot < (unsigned long long)P.pair_cap) {
+                    float *row = P.pairs + slot * mlp::kPairStride;
+#pragma unroll
+                    for (int q = 0; q < mlp::kIn; ++q) row[q] = f[q];
+                    const double rs = 1.0 / sqrt(Tp);
+                    row[mlp::kIn + 0] = float((o.u[na] - uref[na]) * rs);
+                    row[mlp::kIn + 1] = float((o.u[ta] - uref[ta]) * rs);
+                    row[mlp::kIn + 2] = float(log(o.T / Tp));
+                    row[mlp::kIn + 3] = 0.f;
+                }
+            }
+        }
         if (o.have) {
 #pragma unroll
             for (int k = 0; k < NFC; ++k) Fout[k * nf + fidx] = o.F[k];
@@ -1019,6 +1056,110 @@ __global__ void init_faces_kernel(const Params<D, R> P)
 #pragma unroll
     for (int a = 0; a < D; ++a) Frm[a * nf + f] = u[a];
     Frm[D * nf + f] = (E - 0.5 * k2 / r) / (P.Cv * r);
+}
+
+// ------------------------------------------------------- learned gauge predictor
+
+// Before the face corrector of a step: every face's predictor frame is replaced by the
+// learned prediction of its converged frame (features as in mlp::features).  Persistent
+// CTAs stage the network once and loop over tiles of 128 faces.
+template <typename R>
+__global__ void __launch_bounds__(mlp::kThreads)
+gauge_predict_kernel(const Params<2, R> P)
+{
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    const Clock &K = *P.clock;
+    if (!(K.dt > 0.0)) return;
+    const long long nxf = P.nxf(), nyf = P.nyf(), nf = nxf + nyf;
+    if (threadIdx.x < 32) tc::tmem_alloc(&tmem_base, 128);
+    if (threadIdx.x == 0) tc::mbar_init(&mbar, 1);
+    mlp::stage_weights(P.mlp, sm, false);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_base;
+    uint32_t phase = 0;
+    bool ok = true;
+    const long long ntiles = (nf + mlp::kRows - 1) / mlp::kRows;
+    for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const long long t = tile * mlp::kRows + threadIdx.x;
+        const bool valid = t < nf;
+        float f[mlp::kIn];
+        double uref[2] = {0.0, 0.0}, Tp = 0.0;
+        int dir = 0;
+        long long fidx = 0;
+        if (valid) {
+            dir = t < nxf ? 0 : 1;
+            fidx = dir ? t - nxf : t;
+            long long ci[8], cj[8];
+            if (dir == 0) {
+                const long long i = fidx % (P.nx + 1), j = fidx / (P.nx + 1);
+                const long long di[8] = {-2, -1, 0, 1, -1, -1, 0, 0}, dj[8] = {0, 0, 0, 0, -1, 1, -1, 1};
+#pragma unroll
+                for (int q = 0; q < 8; ++q) { ci[q] = i + di[q]; cj[q] = j + dj[q]; }
+            } else {
+                const long long i = fidx % P.nx, j = fidx / P.nx;
+                const long long di[8] = {0, 0, 0, 0, -1, 1, -1, 1}, dj[8] = {-2, -1, 0, 1, -1, -1, 0, 0};
+#pragma unroll
+                for (int q = 0; q < 8; ++q) { ci[q] = i + di[q]; cj[q] = j + dj[q]; }
+            }
+            const double *Frm = dir ? P.yfr : P.xfr;
+            const long long nfd = dir ? nyf : nxf;
+            uref[0] = Frm[fidx];
+            uref[1] = Frm[nfd + fidx];
+            Tp = Frm[2 * nfd + fidx];
+            const int na = dir, ta = 1 - dir;
+            mlp::SlotPrim sp[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                long long idx = 0;
+                const int side = resolve(P, ci[q], cj[q], &idx);
+                double rho, u[2], T;
+                if (side >= 0) {
+                    rho = P.inflow[side][0];
+                    u[0] = P.inflow[side][1];
+                    u[1] = P.inflow[side][2];
+                    T = P.inflow[side][3] / rho;
+                } else {
+                    const long long n = P.ncell();
+                    rho = double(P.sf[idx]);
+                    u[0] = P.sfr[idx];
+                    u[1] = P.sfr[n + idx];
+                    T = P.sfr[2 * n + idx];
+                }
+                sp[q] = {float(rho), float(u[na] - uref[na]), float(u[ta] - uref[ta]), float(T)};
+            }
+            mlp::features(sp, float(Tp), float(dir ? K.h_dy : K.h_dx), f);
+        } else {
+#pragma unroll
+            for (int q = 0; q < mlp::kIn; ++q) f[q] = 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < mlp::kIn; ++q) mlp::put_bf16(sm + mlp::sA1, threadIdx.x, q, mlp::kIn, f[q]);
+        float out[mlp::kOutP];
+        ok = mlp::forward_tile(P.mlp, sm, tmem, &mbar, phase, out);
+        if (ok && valid && Tp > 0.0) {
+            const int na = dir, ta = 1 - dir;
+            const double sq = sqrt(Tp);
+            const float y0 = fminf(fmaxf(out[0], -5.f), 5.f), y1 = fminf(fmaxf(out[1], -5.f), 5.f);
+            const float y2 = fminf(fmaxf(out[2], -5.f), 5.f);
+            double un[2];
+            un[na] = uref[na] + sq * double(y0);
+            un[ta] = uref[ta] + sq * double(y1);
+            double *Frm = dir ? P.yfr : P.xfr;
+            const long long nfd = dir ? nyf : nxf;
+            Frm[fidx] = un[0];
+            Frm[nfd + fidx] = un[1];
+            Frm[2 * nfd + fidx] = Tp * double(__expf(y2));
+        }
+    }
+    if (!ok && threadIdx.x == 0) atomicOr(P.mlp_err, 1u);
+    mlp::drain(&mbar, phase, ok);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x < 32) tc::tmem_free(tmem, 128);
 }
 
 // ---------------------------------------------------------------- read-back kernels

@@ -1,0 +1,124 @@
+// pond_tc.cuh -- 5th-generation tensor-core primitives (tcgen05, TMEM) for sm_103a.
+//
+// Operands live in shared memory as BF16 in the K-major layout without swizzle: the tile
+// is cut into 8-row x 8-element "core matrices" of 128 contiguous bytes (8 rows of 16 B);
+// core matrices adjacent along K are LBO = 128 B apart and 8-row groups are
+// SBO = (K/8) * 128 B apart.  One tcgen05.mma (kind::f16, K = 16) consumes two core
+// matrices along K, so successive K steps advance the descriptors by 256 B.  Accumulators
+// are FP32 in tensor memory: an M = 128 tile occupies lanes 0..127, row i in lane i; warp w
+// of the CTA reads lanes 32 (w % 4) .. 32 (w % 4) + 31.
+//
+// Every wait on an mbarrier is bounded; on time-out the caller records an error, releases
+// its tensor memory and returns.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace pond {
+namespace tc {
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+
+// byte offset of element (r, k) of a K-major, unswizzled BF16 operand with K columns
+__host__ __device__ constexpr uint32_t kmajor_offset(uint32_t r, uint32_t k, uint32_t K)
+{
+    return (r >> 3) * (K / 8) * 128u + (k >> 3) * 128u + (r & 7u) * 16u + (k & 7u) * 2u;
+}
+
+// shared-memory matrix descriptor: start address, leading (K) and stride (8-row) byte
+// offsets, descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    return uint64_t((saddr >> 4) & 0x3FFFu) | (uint64_t((lbo >> 4) & 0x3FFFu) << 16) |
+           (uint64_t((sbo >> 4) & 0x3FFFu) << 32) | (uint64_t(1) << 46);
+}
+
+// instruction descriptor of kind::f16: D FP32, A and B BF16, both K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_bf16(uint32_t M, uint32_t N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void commit(uint64_t *mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(mbar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *mbar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(mbar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// bounded wait for the given phase parity; false on time-out
+__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, long long max_polls)
+{
+    const uint32_t a = smem_addr(mbar);
+    for (long long i = 0; i < max_polls; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// smem written by ordinary stores, about to be read by the tensor core (async proxy)
+__device__ __forceinline__ void fence_smem_to_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// tensor-memory allocation by one full warp; the base address lands in *dst (shared)
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(dst)), "r"(ncols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_free(uint32_t base, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base), "r"(ncols) : "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's lane (warp-collective)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// D[128 x N] (+)= A[128 x K] B[N x K]^T; issued by one thread; A, B K-major in shared memory
+__device__ __forceinline__ void gemm_issue(uint32_t d_tmem, const void *A, const void *B, uint32_t K, uint32_t N,
+                                           bool accumulate)
+{
+    const uint32_t id = idesc_bf16(128, N);
+    const uint32_t sbo = (K / 8) * 128u;
+    const uint32_t a0 = smem_addr(A), b0 = smem_addr(B);
+    for (uint32_t ks = 0; ks < K / 16; ++ks) {
+        const uint64_t ad = smem_desc(a0 + ks * 256u, 128u, sbo);
+        const uint64_t bd = smem_desc(b0 + ks * 256u, 128u, sbo);
+        mma_bf16(d_tmem, ad, bd, id, (accumulate || ks > 0) ? 1u : 0u);
+    }
+}
+
+}  // namespace tc
+}  // namespace pond

@@ -1,0 +1,94 @@
+"""The learned face-gauge predictor: tensor-core forward and backward against the FP64
+reference network (same bfloat16 rounding points), training, and what the trained network
+changes in the solver (corrector passes per face; results within the FP32 tolerance)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_2203_05477_gb300 as pond  # noqa: E402
+from oracle import gauge_mlp as G  # noqa: E402
+from paper_2203_05477_gb300 import inputs as I  # noqa: E402
+from tests.common import rel_l1  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def batch(n, seed):
+    rng = np.random.default_rng(seed)
+    X = np.zeros((n, pond.MLP_PAIR_STRIDE), dtype=np.float32)
+    X[:, :34] = rng.standard_normal((n, 34)).astype(np.float32)
+    X[:, 33] = 1.0
+    X[:, 48:51] = rng.standard_normal((n, 3)).astype(np.float32)
+    return X
+
+
+@pytest.mark.parametrize("n", [1, 128, 300])
+def test_forward_matches_reference(n):
+    p = G.init_params(5).astype(np.float32)
+    X = batch(n, 6)
+    out = pond.mlp_forward(torch.from_numpy(p).cuda(), torch.from_numpy(X).cuda()).cpu().numpy()
+    ref, _ = G.forward(p.astype(np.float64), X.astype(np.float64), quantize=True)
+    # FP32 accumulation against FP64: a hidden activation may round to the other bfloat16
+    # neighbour (2^-8 relative); bound the output error by 1% of its scale
+    scale = np.abs(ref).max()
+    assert np.abs(out - ref).max() <= 1e-2 * scale, np.abs(out - ref).max() / scale
+
+
+@pytest.mark.parametrize("n", [130, 1000])
+def test_gradient_matches_reference(n):
+    p = G.init_params(7).astype(np.float32)
+    X = batch(n, 8)
+    loss, g = pond.mlp_gradient(torch.from_numpy(p).cuda(), torch.from_numpy(X).cuda(), torch.from_numpy(X).cuda())
+    g = g.cpu().numpy()
+    lref, gref = G.loss_and_grad(p.astype(np.float64), X.astype(np.float64), X[:, 48:51].astype(np.float64), quantize=True)
+    assert loss == pytest.approx(lref, rel=1e-2)
+    for lo, hi in [(G.O_W1, G.O_B1), (G.O_B1, G.O_W2), (G.O_W2, G.O_B2), (G.O_B2, G.O_W3), (G.O_W3, G.O_B3), (G.O_B3, G.NPARAMS)]:
+        scale = max(np.abs(gref[lo:hi]).max(), 1e-12)
+        assert np.abs(g[lo:hi] - gref[lo:hi]).max() <= 3e-2 * scale, (lo, np.abs(g[lo:hi] - gref[lo:hi]).max() / scale)
+
+
+def test_training_fits_a_smooth_target():
+    n = 8192
+    X = batch(n, 9)
+    rng = np.random.default_rng(10)
+    A = rng.standard_normal((34, 3)).astype(np.float32) * 0.2
+    X[:, 48:51] = np.tanh(X[:, :34] @ A)
+    pb = I.quadrants_2d(16, seed=0)
+    s = pond.Solver(pb, precision="fp32", tau=1e-5, cfl=0.2)
+    losses = s.gauge_train(torch.from_numpy(X).cuda(), epochs=30, batch=1024, lr=3e-3)
+    assert losses[-1] < 0.1 * losses[0], losses
+
+
+def test_learned_predictor_in_the_solver():
+    """Collect pairs from the plain FP32 solver on one seed, train on the GPU, run another
+    seed with and without the learned predictor: the corrector still judges convergence,
+    so the fields agree to the FP32 tolerance; report the passes per face."""
+    train_pb = I.quadrants_2d(256, seed=1)
+    s = pond.Solver(train_pb, precision="fp32", tau=1e-5, cfl=0.2)
+    s.set_primitive()
+    pairs = s.gauge_collect(200, cap=400_000, every=2)
+    assert pairs.shape[0] > 10_000
+    perm = torch.randperm(pairs.shape[0], device=pairs.device)
+    losses = s.gauge_train(pairs[perm].contiguous(), epochs=8, batch=4096, lr=2e-3)
+    assert losses[-1] < losses[0]
+    params = s.gauge_params()
+    s.close()
+    test_pb = I.quadrants_2d(256, seed=2)
+    res = {}
+    for learned in (False, True):
+        g = pond.Solver(test_pb, precision="fp32", tau=1e-5, cfl=0.2)
+        g.set_primitive()
+        if learned:
+            g.set_gauge_params(params)
+            g.gauge_enable(True)
+        g.step(150)
+        d = g.sync()
+        assert d["status"] == pond.POND_OK, d
+        res[learned] = (g.primitive(), d["face_iters"] / d["face_solves"], d["nonconverged"])
+        g.close()
+    (r0, u0, v0, p0), pass0, nc0 = res[False]
+    (r1, u1, v1, p1), pass1, nc1 = res[True]
+    assert rel_l1(r1, r0) < 1e-4 and rel_l1(p1, p0) < 1e-4
+    print("passes per face: plain %.4f learned %.4f; non-converged faces %d / %d" % (pass0, pass1, nc0, nc1))
+    assert pass1 <= 1.5 * pass0
