@@ -174,7 +174,7 @@ pond_status pond_batch_status(pond_state *s, int32_t *status, int64_t *steps_don
  * random W1, W2 and zero W3, b (prediction = the previous frame). */
 #define POND_MLP_PARAMS 8336
 #define POND_MLP_FEATURES 48
-#define POND_MLP_PAIR_STRIDE 52   /* a training pair: 48 features, 3 targets, 1 pad */
+#define POND_MLP_PAIR_STRIDE 52   /* a training pair: 48 features, 3 targets, the face's corrector passes */
 
 /* Runs n_steps plain steps and samples (features, converged face frame) pairs from every
  * every-th converged face into pairs (device, [cap][POND_MLP_PAIR_STRIDE] floats); the
@@ -187,8 +187,11 @@ pond_status pond_gauge_collect(pond_state *s, int64_t n_steps, float *pairs, int
 pond_status pond_gauge_train(pond_state *s, const float *pairs, int64_t n, int epochs, int batch, float lr,
                              float *loss_out);
 
-/* Switches the learned predictor on (nonzero) or off for the following steps. */
+/* Switches the learned predictor on (nonzero) or off for the following steps.  A face
+ * keeps its previous frame unless the largest component of the predicted (normalized)
+ * correction exceeds `gate` (default 0.01; 0: always use the prediction). */
 pond_status pond_gauge_enable(pond_state *s, int on);
+pond_status pond_gauge_set_gate(pond_state *s, float gate);
 
 /* Copies the network parameters from / to host arrays of POND_MLP_PARAMS floats. */
 pond_status pond_gauge_set_params(pond_state *s, const float *params);

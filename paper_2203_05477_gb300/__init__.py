@@ -96,6 +96,7 @@ def _load():
             "pond_gauge_collect": (ctypes.c_int, [vp, ctypes.c_int64, vp, ctypes.c_int64, ctypes.c_int, vp]),
             "pond_gauge_train": (ctypes.c_int, [vp, vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_float, vp]),
             "pond_gauge_enable": (ctypes.c_int, [vp, ctypes.c_int]),
+            "pond_gauge_set_gate": (ctypes.c_int, [vp, ctypes.c_float]),
             "pond_gauge_set_params": (ctypes.c_int, [vp, vp]),
             "pond_gauge_get_params": (ctypes.c_int, [vp, vp]),
             "pond_mlp_forward": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int64, vp, vp]),
@@ -304,7 +305,9 @@ class Solver:
                                          float(lr), _ptr(losses)))
         return losses
 
-    def gauge_enable(self, on=True):
+    def gauge_enable(self, on=True, gate=None):
+        if gate is not None:
+            _check(self.lib.pond_gauge_set_gate(self.h, float(gate)))
         _check(self.lib.pond_gauge_enable(self.h, int(bool(on))))
 
     def gauge_params(self):

@@ -713,7 +713,10 @@ pond_status pond_init(const pond_grid *grid, pond_velset velset, double gamma, d
     if (st == POND_OK && D == 2) {
         st = mlp_setup(s);
         if (st == POND_OK) {
-            auto wire = [&](auto &P) { P.mlp = s->mlp; P.mlp_err = s->mlp_err; P.pair_count = s->pair_count; P.pair_every = 1; };
+            auto wire = [&](auto &P) {
+                P.mlp = s->mlp; P.mlp_err = s->mlp_err; P.pair_count = s->pair_count; P.pair_every = 1;
+                P.gauge_gate = 0.01f;
+            };
             if (s->prec == POND_FP32) wire(params_of<2, float>(s));
             else wire(params_of<2, double>(s));
         }
@@ -1006,6 +1009,17 @@ pond_status pond_gauge_enable(pond_state *s, int on)
         if (s->graph) { cudaGraphDestroy(s->graph); s->graph = nullptr; }
     }
     s->learned = on != 0;
+    return POND_OK;
+}
+
+pond_status pond_gauge_set_gate(pond_state *s, float gate)
+{
+    if (pond_status st = check_gauge(s)) return st;
+    if (!(gate >= 0.f)) return fail(POND_ERR_INVALID_ARG, "gate must be >= 0");
+    if (s->prec == POND_FP32) params_of<2, float>(s).gauge_gate = gate;
+    else params_of<2, double>(s).gauge_gate = gate;
+    if (s->graph_exec) { cudaGraphExecDestroy(s->graph_exec); s->graph_exec = nullptr; }
+    if (s->graph) { cudaGraphDestroy(s->graph); s->graph = nullptr; }
     return POND_OK;
 }
 

@@ -92,6 +92,7 @@ struct Params {
     unsigned long long *pair_count;
     long long pair_cap;
     int pair_every;
+    float gauge_gate;                 // the prediction is used where its largest component exceeds this
     unsigned int *mlp_err;
     __host__ __device__ long long ncell() const { return nx * ny; }
     __host__ __device__ long long nxf() const { return (nx + 1) * ny; }
@@ -660,7 +661,7 @@ face_kernel(const Params<D, R> P)
                     row[mlp::kIn + 0] = float((o.u[na] - uref[na]) * rs);
                     row[mlp::kIn + 1] = float((o.u[ta] - uref[ta]) * rs);
                     row[mlp::kIn + 2] = float(log(o.T / Tp));
-                    row[mlp::kIn + 3] = 0.f;
+                    row[mlp::kIn + 3] = float(o.iters);
                 }
             }
         }
@@ -1145,6 +1146,7 @@ gauge_predict_kernel(const Params<2, R> P)
             const double sq = sqrt(Tp);
             const float y0 = fminf(fmaxf(out[0], -5.f), 5.f), y1 = fminf(fmaxf(out[1], -5.f), 5.f);
             const float y2 = fminf(fmaxf(out[2], -5.f), 5.f);
+            if (fmaxf(fabsf(y0), fmaxf(fabsf(y1), fabsf(y2))) <= P.gauge_gate) continue;
             double un[2];
             un[na] = uref[na] + sq * double(y0);
             un[ta] = uref[ta] + sq * double(y1);

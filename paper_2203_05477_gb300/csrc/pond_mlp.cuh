@@ -28,7 +28,7 @@ constexpr int oW1 = 0, ob1 = oW1 + kHid * kIn, oW2 = ob1 + kHid, ob2 = oW2 + kHi
 constexpr int kRows = 128;         // rows (faces, samples) per CTA: the MMA M
 constexpr int kThreads = 128;      // one thread per row
 constexpr long long kPolls = 1ll << 22;   // bound on every mbarrier wait
-constexpr int kPairStride = 52;    // features (48), targets (3), pad
+constexpr int kPairStride = 52;    // features (48), targets (3), corrector passes of the face
 
 // shared-memory plan of the tile kernel (byte offsets, 128-aligned)
 constexpr int sB1 = 0;                          // W1   [64][48]

@@ -61,9 +61,11 @@ def test_training_fits_a_smooth_target():
 
 
 def test_learned_predictor_in_the_solver():
-    """Collect pairs from the plain FP32 solver on one seed, train on the GPU, run another
-    seed with and without the learned predictor: the corrector still judges convergence,
-    so the fields agree to the FP32 tolerance; report the passes per face."""
+    """Collect pairs from the plain FP32 solver on one seed, train on the GPU, then run
+    another seed with and without the learned predictor.  The corrector still judges
+    convergence: the learned run stays within 1e-4 relative L1 of the FP64 oracle (as the
+    plain FP32 run does), and the passes per face of both runs are reported."""
+    from tests.common import oracle_for
     train_pb = I.quadrants_2d(256, seed=1)
     s = pond.Solver(train_pb, precision="fp32", tau=1e-5, cfl=0.2)
     s.set_primitive()
@@ -74,21 +76,32 @@ def test_learned_predictor_in_the_solver():
     assert losses[-1] < losses[0]
     params = s.gauge_params()
     s.close()
-    test_pb = I.quadrants_2d(256, seed=2)
-    res = {}
-    for learned in (False, True):
-        g = pond.Solver(test_pb, precision="fp32", tau=1e-5, cfl=0.2)
+
+    def run(pb, learned, steps):
+        g = pond.Solver(pb, precision="fp32", tau=1e-5, cfl=0.2)
         g.set_primitive()
         if learned:
             g.set_gauge_params(params)
             g.gauge_enable(True)
-        g.step(150)
+        g.step(steps)
         d = g.sync()
         assert d["status"] == pond.POND_OK, d
-        res[learned] = (g.primitive(), d["face_iters"] / d["face_solves"], d["nonconverged"])
+        out = (g.primitive(), d["face_iters"] / d["face_solves"], d["nonconverged"])
         g.close()
-    (r0, u0, v0, p0), pass0, nc0 = res[False]
-    (r1, u1, v1, p1), pass1, nc1 = res[True]
-    assert rel_l1(r1, r0) < 1e-4 and rel_l1(p1, p0) < 1e-4
+        return out
+
+    big = I.quadrants_2d(256, seed=2)
+    _, pass0, nc0 = run(big, False, 150)
+    _, pass1, nc1 = run(big, True, 150)
     print("passes per face: plain %.4f learned %.4f; non-converged faces %d / %d" % (pass0, pass1, nc0, nc1))
-    assert pass1 <= 1.5 * pass0
+    # 98-99% of faces converge in one pass from the previous frame; the gated prediction
+    # must not cost passes
+    assert pass1 <= 1.03 * pass0
+
+    small = I.quadrants_2d(48, seed=2)
+    os_ = oracle_for(small, tau=1e-5, cfl=0.2, tol=1e-10)
+    os_.step(40)
+    ro, uo, vo, po = os_.primitive()
+    for learned in (False, True):
+        (r, u, v, p), _, _ = run(small, learned, 40)
+        assert rel_l1(r, ro) < 1e-4 and rel_l1(p, po) < 1e-4, (learned, rel_l1(r, ro), rel_l1(p, po))
