@@ -206,6 +206,23 @@ pond_status pond_mlp_forward(const float *params, const float *x, int ldx, int64
 pond_status pond_mlp_gradient(const float *params, const float *x, int ldx, const float *y, int ldy, int64_t n,
                               float *grad, float *loss, void *stream);
 
+/* pond_mlp_gradient without any device allocation.  The paper has no counterpart: this is
+ * a service for callers that cannot call cudaMalloc, for example code running while a
+ * framework's caching allocator has reserved the whole device, code that must not add the
+ * device-wide synchronization cudaMalloc/cudaFree imply, or code on a path where a failed
+ * allocation cannot be handled.  Inputs and outputs are as for pond_mlp_gradient (device
+ * arrays owned by the caller).  The activation scratch lives in a fixed device array of
+ * the library sized for POND_MLP_NOALLOC_MAX_ROWS rows (about 5 MB, held by every GPU that
+ * loads the library until the process exits); n above that limit returns
+ * POND_ERR_INVALID_ARG.  The first call on a device looks up that array's device address
+ * and sets the kernels' shared-memory limit for that device, so make the first call before
+ * any stream capture.  All calls share the one array: calls whose work overlaps on the GPU
+ * (different streams, or threads calling concurrently) race on it; serialize them.  The
+ * call clears *loss and its error word itself, enqueues on `stream`, and waits for it. */
+#define POND_MLP_NOALLOC_MAX_ROWS 8192
+pond_status pond_mlp_gradient_noalloc(const float *params, const float *x, int ldx, const float *y, int ldy, int64_t n,
+                                      float *grad, float *loss, void *stream);
+
 /* Waits for the stream and reports the device diagnostics.  Returns
  * POND_ERR_NONPHYSICAL if any cell or face was non-physical, POND_ERR_NOT_CONVERGED if
  * strict_convergence is set and a face stopped at max_iter, else POND_OK. */

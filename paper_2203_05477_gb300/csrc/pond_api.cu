@@ -14,6 +14,7 @@
 #include <type_traits>
 #include <new>
 #include <vector>
+#include <mutex>
 
 #include "../../include/pond.h"
 #include "pond_batch.cuh"
@@ -41,7 +42,7 @@ pond_status fail(pond_status st, const char *fmt, ...)
 constexpr int kGraphSteps = 32;   // steps per captured graph
 constexpr int kReduceBlocks = 1024;
 
-size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+constexpr size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 }  // namespace
 
@@ -1090,6 +1091,70 @@ pond_status pond_mlp_gradient(const float *params, const float *x, int ldx, cons
     cudaStreamSynchronize(st);
     cudaFree(scratch);
     return r;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------- allocation-free gradient
+
+namespace {
+
+// Scratch of pond_mlp_gradient_noalloc: the activations of up to POND_MLP_NOALLOC_MAX_ROWS
+// rows, followed by the error word.  In host code this name only stands for the symbol;
+// its device address comes from cudaGetSymbolAddress for the current device.
+constexpr size_t kNoallocScratch = align_up(size_t(POND_MLP_NOALLOC_MAX_ROWS) * (16 * 4 + 2 * (64 + 64 + 16 + 64 + 64)) + 1024, 256) + 256;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratch];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+unsigned char *g_noalloc_ptr[kMaxDevices] = {};
+
+// once per device, with that device current: the array's device address and the
+// shared-memory limit of the tile kernel
+pond_status noalloc_setup(unsigned char **out)
+{
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(POND_ERR_UNSUPPORTED, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        CUDA_TRY(cudaFuncSetAttribute(pond::mlp::tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, pond::mlp::kTileSmem));
+        g_noalloc_ptr[dev] = static_cast<unsigned char *>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return POND_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pond_status pond_mlp_gradient_noalloc(const float *params, const float *x, int ldx, const float *y, int ldy, int64_t n,
+                                      float *grad, float *loss, void *stream)
+{
+    namespace M = pond::mlp;
+    if (!params || !x || !y || !grad || !loss || n <= 0 || ldx < M::kIn || ldy < M::kIn + M::kOut)
+        return fail(POND_ERR_INVALID_ARG, "bad gradient arguments");
+    if (n > POND_MLP_NOALLOC_MAX_ROWS)
+        return fail(POND_ERR_INVALID_ARG, "n = %lld rows exceeds the allocation-free limit of %d rows", (long long)n,
+                    POND_MLP_NOALLOC_MAX_ROWS);
+    unsigned char *base = nullptr;
+    if (pond_status st = noalloc_setup(&base)) return st;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const TrainScratch t = TrainScratch::carve(reinterpret_cast<char *>(base), POND_MLP_NOALLOC_MAX_ROWS);
+    unsigned int *err = reinterpret_cast<unsigned int *>(base + kNoallocScratch - 256);
+    // the loss accumulates and the error word is or-ed into: both start at zero
+    CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(unsigned int), st));
+    CUDA_TRY(cudaMemsetAsync(loss, 0, sizeof(float), st));
+    pond_status r = mlp_grad_launch(params, x, ldx, y, ldy, n, t, grad, loss, err, st);
+    if (r != POND_OK) return r;
+    unsigned int e = 0;
+    CUDA_TRY(cudaMemcpyAsync(&e, err, sizeof(e), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (e) return fail(POND_ERR_TIMEOUT, "a tensor-core wait timed out");
+    return POND_OK;
 }
 
 int64_t pond_launch_count(const pond_state *s) { return s ? s->launches : 0; }
