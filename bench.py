@@ -194,13 +194,14 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--fp64-steps", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--tube-steps", type=int, default=100)
     ap.add_argument("--workload", default="quadrants", choices=["quadrants", "tubes"],
                     help="tubes: only the batched-tube measurement (profiling case)")
@@ -290,6 +291,41 @@ def main():
            "h2d_bytes_per_step": 4 * 8 * ncell / args.steps, "d2h_bytes_per_step": 4 * 8 * ncell / args.steps,
            "note": "pond_set_primitive from pinned host arrays, %d steps, pond_moments to pinned host" % args.steps}
 
+    # ---- FP32 with the learned face-gauge predictor (trained here on another seed)
+    learned = None
+    if not args.no_learned:
+        import torch as _t
+        t_tr = time.perf_counter()
+        tr = pond.Solver(I.quadrants_2d(256, seed=args.seed + 101), precision="fp32", tau=1e-5, cfl=0.2)
+        tr.set_primitive()
+        pairs = tr.gauge_collect(100, cap=300_000, every=2)
+        perm = _t.randperm(pairs.shape[0], device=pairs.device)
+        losses = tr.gauge_train(pairs[perm].contiguous(), epochs=6, batch=4096, lr=2e-3)
+        params = tr.gauge_params()
+        tr.close()
+        t_tr = time.perf_counter() - t_tr
+        sl = pond.Solver(pb, precision="fp32", tau=1e-5, cfl=0.2, max_iter=16)
+        sl.set_primitive()
+        sl.set_gauge_params(params)
+        sl.gauge_enable(True)
+        sl.step(args.warmup)
+        dl0 = sl.sync()
+        l0e, l1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        l0e.record(sl.stream)
+        lf, lc = sl.step_timed(args.steps)
+        l1e.record(sl.stream)
+        barrier()
+        dl1 = sl.sync()
+        lms = max_over_ranks(l0e.elapsed_time(l1e))
+        learned = {"value": world * ncell * args.steps / (lms * 1e-3) / 1e6, "unit": "MLUPS",
+                   "passes_per_face": (dl1["face_iters"] - dl0["face_iters"]) / max(1, dl1["face_solves"] - dl0["face_solves"]),
+                   "predictor_and_face_ms": lf / args.steps, "cell_ms": lc / args.steps,
+                   "train": {"pairs": int(pairs.shape[0]), "epochs": 6, "loss_first": float(losses[0]),
+                             "loss_last": float(losses[-1]), "seconds": t_tr},
+                   "status_ok": dl1["status"] == pond.POND_OK}
+        sl.close()
+
     # ---- plain FP64 on the same GPU
     s3 = pond.Solver(pb, precision="fp64", tau=1e-5, cfl=0.2, max_iter=16)
     s3.set_primitive()
@@ -324,6 +360,7 @@ def main():
                    "corrector": "tol 1e-6, max 16 passes", "l2": "working set %.0f MB > L2" % (
                        (ncell * (80 + 2 * 88)) / 1e6), "parallelism": "replicas" if world > 1 else "single"},
         "fp64": {"value": fp64_value, "unit": "MLUPS", "steps": args.fp64_steps, "speedup_fp32": value / fp64_value},
+        "fp32_learned": learned,
         "corrector": {"passes_per_face": face_passes / max(faces, 1), "status_ok": status_ok},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp32_peak, "traffic": FACE_KERNEL_DRAM_BYTES, "kernel": "face_kernel<2,float>",
