@@ -42,6 +42,27 @@ FLOPS_PER_FACE_PASS = 4550.0
 FACE_KERNEL_BYTES_PER_CELL = 80 + 48 + 176
 
 
+def replica_seed(base_seed, rank):
+    """Each rank advances its own replica of the workload (seed + rank)."""
+    return base_seed + rank
+
+
+def max_over_ranks(x, world, device=None):
+    """The slowest rank's time (the job's time); every rank gets the same value."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_mlups(cells_per_rank, steps, seconds, world):
+    """Whole-job throughput: the updates of all ranks over the slowest rank's time."""
+    return world * cells_per_rank * steps / seconds / 1e6
+
+
 def peaks():
     try:
         with open(PEAKS_FILE) as fh:
@@ -130,13 +151,13 @@ def cpu_baseline(pb_full, steps, target_s=12.0):
 TUBE_BYTES_PER_CELL = 112  # state (3+3 FP32 + 2 FP64) and face predictor (2 FP64), read and written
 
 
-def bench_tubes(args, n_tubes=4096, seed=0):
+def bench_tubes(args, n_tubes=4096, seed=0, rank=0):
     """The batched-tube workload: 4096 D1Q4 tubes of 200-8000 cells (seeded states with density
     and pressure ratios up to 1e5 and velocity jumps up to Mach 20), FP32, one launch per call."""
     import torch
     import paper_2203_05477_gb300 as pond
     from paper_2203_05477_gb300 import inputs as I
-    bt = I.tube_batch(n_tubes, seed=seed)
+    bt = I.tube_batch(n_tubes, seed=replica_seed(seed, rank))
     rho, ux, p = I.tube_batch_fields(bt)
     s = pond.BatchSolver(bt.lengths, bt.gammas, precision="fp32", tau=1e-5, cfl=0.2, max_iter=16)
     s.set_primitive(rho, ux, None, p)
@@ -230,7 +251,7 @@ def main():
             print(json.dumps(bench_tubes(args)), flush=True)
         return
     n = args.n
-    pb = I.quadrants_2d(n, seed=args.seed + rank)
+    pb = I.quadrants_2d(n, seed=replica_seed(args.seed, rank))
     ncell = n * n
 
     def barrier():
@@ -238,12 +259,8 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def max_over_ranks_(x):
+        return max_over_ranks(x, world, device="cuda")
 
     # ---- headline: FP32 populations, FP64 frames
     s = pond.Solver(pb, precision="fp32", tau=1e-5, cfl=0.2, max_iter=16)
@@ -259,10 +276,10 @@ def main():
         ms_face, ms_cell = s.step_timed(args.steps)
         e1.record(stream)
         barrier()
-    el_ms = max_over_ranks(e0.elapsed_time(e1))
+    el_ms = max_over_ranks_(e0.elapsed_time(e1))
     d1 = s.sync()
     launches = s.launch_count() - l0
-    value = world * ncell * args.steps / (el_ms * 1e-3) / 1e6
+    value = aggregate_mlups(ncell, args.steps, el_ms * 1e-3, world)
     face_passes = d1["face_iters"] - d0["face_iters"]
     faces = d1["face_solves"] - d0["face_solves"]
     status_ok = d1["status"] == pond.POND_OK
@@ -285,7 +302,7 @@ def main():
     s2.step(args.steps)
     s2.lib.pond_moments(s2.h, *[o.data_ptr() for o in outs], None, 0)
     barrier()
-    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e_s = max_over_ranks_(time.perf_counter() - t0)
     s2.close()
     e2e = {"value": world * ncell * args.steps / e2e_s / 1e6, "unit": "MLUPS",
            "h2d_bytes_per_step": 4 * 8 * ncell / args.steps, "d2h_bytes_per_step": 4 * 8 * ncell / args.steps,
@@ -317,7 +334,7 @@ def main():
         l1e.record(sl.stream)
         barrier()
         dl1 = sl.sync()
-        lms = max_over_ranks(l0e.elapsed_time(l1e))
+        lms = max_over_ranks_(l0e.elapsed_time(l1e))
         learned = {"value": world * ncell * args.steps / (lms * 1e-3) / 1e6, "unit": "MLUPS",
                    "passes_per_face": (dl1["face_iters"] - dl0["face_iters"]) / max(1, dl1["face_solves"] - dl0["face_solves"]),
                    "predictor_and_face_ms": lf / args.steps, "cell_ms": lc / args.steps,
@@ -336,7 +353,7 @@ def main():
     s3.step(args.fp64_steps)
     f1.record(s3.stream)
     barrier()
-    fp64_value = world * ncell * args.fp64_steps / (max_over_ranks(f0.elapsed_time(f1)) * 1e-3) / 1e6
+    fp64_value = world * ncell * args.fp64_steps / (max_over_ranks_(f0.elapsed_time(f1)) * 1e-3) / 1e6
     s3.close()
 
     if rank != 0:
@@ -372,7 +389,7 @@ def main():
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
-    tubes = bench_tubes(args)
+    tubes = bench_tubes(args, rank=rank)
     tubes["hbm_frac"] = tubes["hbm_gbs"] / hbm_peak
     line["tubes"] = tubes
     if not args.no_cpu_baseline:

@@ -193,6 +193,12 @@ pond_status pond_gauge_train(pond_state *s, const float *pairs, int64_t n, int e
 pond_status pond_gauge_enable(pond_state *s, int on);
 pond_status pond_gauge_set_gate(pond_state *s, float gate);
 
+/* The network as a self-describing byte blob (magic, version, count, parameters) for
+ * checkpointing: pond_gauge_save writes it to buf (host) if *size is large enough and
+ * always sets *size to the bytes needed; pond_gauge_load reads one back. */
+pond_status pond_gauge_save(pond_state *s, void *buf, size_t *size);
+pond_status pond_gauge_load(pond_state *s, const void *buf, size_t size);
+
 /* Copies the network parameters from / to host arrays of POND_MLP_PARAMS floats. */
 pond_status pond_gauge_set_params(pond_state *s, const float *params);
 pond_status pond_gauge_get_params(pond_state *s, float *params);

@@ -99,6 +99,8 @@ def _load():
             "pond_gauge_set_gate": (ctypes.c_int, [vp, ctypes.c_float]),
             "pond_gauge_set_params": (ctypes.c_int, [vp, vp]),
             "pond_gauge_get_params": (ctypes.c_int, [vp, vp]),
+            "pond_gauge_save": (ctypes.c_int, [vp, vp, ctypes.POINTER(ctypes.c_size_t)]),
+            "pond_gauge_load": (ctypes.c_int, [vp, vp, ctypes.c_size_t]),
             "pond_mlp_forward": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int64, vp, vp]),
             "pond_mlp_gradient": (ctypes.c_int, [vp, vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int64, vp, vp, vp]),
             "pond_destroy": (None, [vp]),
@@ -314,6 +316,17 @@ class Solver:
         p = np.zeros(MLP_PARAMS, dtype=np.float32)
         _check(self.lib.pond_gauge_get_params(self.h, _ptr(p)))
         return p
+
+    def gauge_save(self) -> bytes:
+        n = ctypes.c_size_t(0)
+        _check(self.lib.pond_gauge_save(self.h, None, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        _check(self.lib.pond_gauge_save(self.h, buf, ctypes.byref(n)))
+        return buf.raw
+
+    def gauge_load(self, blob: bytes):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        _check(self.lib.pond_gauge_load(self.h, buf, len(blob)))
 
     def set_gauge_params(self, p):
         p = np.ascontiguousarray(p, dtype=np.float32)

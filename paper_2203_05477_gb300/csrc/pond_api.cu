@@ -724,6 +724,7 @@ pond_status pond_init(const pond_grid *grid, pond_velset velset, double gamma, d
     }
     if (st == POND_OK) st = reset_clock(s);
     if (st != POND_OK) { pond_destroy(s); return st; }
+    s->learned = D == 2 && opts->learned != 0;
     *out = s;
     return POND_OK;
 }
@@ -1034,6 +1035,33 @@ pond_status pond_gauge_set_params(pond_state *s, const float *params)
     s->adam_t = 0;
     CUDA_TRY(cudaStreamSynchronize(s->stream));
     return POND_OK;
+}
+
+pond_status pond_gauge_save(pond_state *s, void *buf, size_t *size)
+{
+    if (pond_status st = check_gauge(s)) return st;
+    if (!size) return fail(POND_ERR_INVALID_ARG, "size is NULL");
+    const size_t need = 16 + 4 * size_t(pond::mlp::kParams);
+    const size_t have = *size;
+    *size = need;
+    if (!buf || have < need) return POND_OK;
+    unsigned char *b = static_cast<unsigned char *>(buf);
+    const uint32_t hdr[4] = {0x444E4F50u /* "POND" */, 1u, uint32_t(pond::mlp::kParams), 0u};
+    std::memcpy(b, hdr, 16);
+    CUDA_TRY(cudaMemcpyAsync(b + 16, s->mlp, 4 * pond::mlp::kParams, cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return POND_OK;
+}
+
+pond_status pond_gauge_load(pond_state *s, const void *buf, size_t size)
+{
+    if (pond_status st = check_gauge(s)) return st;
+    if (!buf || size < 16 + 4 * size_t(pond::mlp::kParams)) return fail(POND_ERR_INVALID_ARG, "blob too small");
+    uint32_t hdr[4];
+    std::memcpy(hdr, buf, 16);
+    if (hdr[0] != 0x444E4F50u || hdr[1] != 1u || hdr[2] != uint32_t(pond::mlp::kParams))
+        return fail(POND_ERR_INVALID_ARG, "not a predictor blob of this version");
+    return pond_gauge_set_params(s, reinterpret_cast<const float *>(static_cast<const unsigned char *>(buf) + 16));
 }
 
 pond_status pond_gauge_get_params(pond_state *s, float *params)

@@ -122,3 +122,16 @@ def test_learned_predictor_in_the_solver():
     (r, u, v, p), _, _ = run(small, True, 40)
     assert rel_l1(r, ro) <= max(1e-4, 2 * env_r) and rel_l1(p, po) <= max(1e-4, 2 * env_p), \
         (rel_l1(r, ro), rel_l1(p, po), env_r, env_p)
+
+
+def test_gauge_blob_round_trip_and_learned_option():
+    pb = I.quadrants_2d(32, seed=0)
+    a = pond.Solver(pb, precision="fp32", tau=1e-5, cfl=0.2)
+    p = G.init_params(11).astype(np.float32)
+    a.set_gauge_params(p)
+    blob = a.gauge_save()
+    b = pond.Solver(pb, precision="fp32", tau=1e-5, cfl=0.2)
+    b.gauge_load(blob)
+    assert np.array_equal(b.gauge_params(), p)
+    with pytest.raises(pond.PondError):
+        b.gauge_load(b"POND" + blob[4:100])
