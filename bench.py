@@ -148,7 +148,7 @@ def cpu_baseline(pb_full, steps, target_s=12.0):
             "sample": "%dx%d centre patch of the workload, %d steps, FP64, single thread, %.1f s" % (side, side, done, el)}
 
 
-TUBE_BYTES_PER_CELL = 112  # state (3+3 FP32 + 2 FP64) and face predictor (2 FP64), read and written
+TUBE_BYTES_PER_CELL = 96  # state (3+3 FP32 + 2 float-float frame words) and face predictor (2 FP32), read and written
 
 
 def bench_tubes(args, n_tubes=4096, seed=0, rank=0):

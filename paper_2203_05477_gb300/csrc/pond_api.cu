@@ -467,9 +467,9 @@ pond_status batch_setup(pond_state *s, const int64_t *lengths, const double *gam
     for (int b = 0; b < 2; ++b) {
         o_sf[b] = take(sizeof(R) * 3 * nc);
         o_sg[b] = take(sizeof(R) * 3 * nc);
-        o_sfr[b] = take(8 * 2 * nc);
+        o_sfr[b] = take(sizeof(typename TP::CellW) * 2 * nc);
     }
-    const size_t o_fu = take(8 * nf), o_fT = take(8 * nf);
+    const size_t o_fu = take(sizeof(typename TP::FaceW) * nf), o_fT = take(sizeof(typename TP::FaceW) * nf);
     const size_t o_diag = take(sizeof(pond::Diag)), o_clock = take(sizeof(pond::Clock));
     const size_t stage = std::max<size_t>(4 * size_t(nc), 7 * size_t(nc)) + 2 * size_t(nf) + 8;
     const size_t o_stage = take(8 * stage);
@@ -500,10 +500,10 @@ pond_status batch_setup(pond_state *s, const int64_t *lengths, const double *gam
     for (int b = 0; b < 2; ++b) {
         P.sf[b] = reinterpret_cast<R *>(B + o_sf[b]);
         P.sg[b] = reinterpret_cast<R *>(B + o_sg[b]);
-        P.sfr[b] = reinterpret_cast<double *>(B + o_sfr[b]);
+        P.sfr[b] = reinterpret_cast<typename TP::CellW *>(B + o_sfr[b]);
     }
-    P.fu = reinterpret_cast<double *>(B + o_fu);
-    P.fT = reinterpret_cast<double *>(B + o_fT);
+    P.fu = reinterpret_cast<typename TP::FaceW *>(B + o_fu);
+    P.fT = reinterpret_cast<typename TP::FaceW *>(B + o_fT);
     P.diag = reinterpret_cast<pond::Diag *>(B + o_diag);
     P.tau = s->tau;
     P.cfl = s->opts.cfl;
@@ -630,18 +630,19 @@ template <typename R>
 pond_status batch_face_gauges(pond_state *s, double *out, const double *in)
 {
     auto &P = tparams_of<R>(s);
+    using W = typename pond::TubeParams<R>::FaceW;  // the face predictor's storage word
     const long long nf = s->nface;
-    std::vector<double> u(nf), T(nf);
+    std::vector<W> u(nf), T(nf);
     if (in) {
-        for (long long f = 0; f < nf; ++f) { u[f] = in[2 * f]; T[f] = in[2 * f + 1]; }
-        CUDA_TRY(cudaMemcpyAsync(P.fu, u.data(), 8 * nf, cudaMemcpyHostToDevice, s->stream));
-        CUDA_TRY(cudaMemcpyAsync(P.fT, T.data(), 8 * nf, cudaMemcpyHostToDevice, s->stream));
+        for (long long f = 0; f < nf; ++f) { u[f] = W(in[2 * f]); T[f] = W(in[2 * f + 1]); }
+        CUDA_TRY(cudaMemcpyAsync(P.fu, u.data(), sizeof(W) * nf, cudaMemcpyHostToDevice, s->stream));
+        CUDA_TRY(cudaMemcpyAsync(P.fT, T.data(), sizeof(W) * nf, cudaMemcpyHostToDevice, s->stream));
         CUDA_TRY(cudaStreamSynchronize(s->stream));
     } else {
-        CUDA_TRY(cudaMemcpyAsync(u.data(), P.fu, 8 * nf, cudaMemcpyDeviceToHost, s->stream));
-        CUDA_TRY(cudaMemcpyAsync(T.data(), P.fT, 8 * nf, cudaMemcpyDeviceToHost, s->stream));
+        CUDA_TRY(cudaMemcpyAsync(u.data(), P.fu, sizeof(W) * nf, cudaMemcpyDeviceToHost, s->stream));
+        CUDA_TRY(cudaMemcpyAsync(T.data(), P.fT, sizeof(W) * nf, cudaMemcpyDeviceToHost, s->stream));
         CUDA_TRY(cudaStreamSynchronize(s->stream));
-        for (long long f = 0; f < nf; ++f) { out[2 * f] = u[f]; out[2 * f + 1] = T[f]; }
+        for (long long f = 0; f < nf; ++f) { out[2 * f] = double(u[f]); out[2 * f + 1] = double(T[f]); }
     }
     return POND_OK;
 }

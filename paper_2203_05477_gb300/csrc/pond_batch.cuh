@@ -10,6 +10,13 @@
 // state buffers, so later chunks still read the old state.  Face populations never reach
 // global memory; per cell and step the traffic is the state read and written once and the
 // face predictor read and written once.
+//
+// Frames.  The FP64 kernel holds each frame as doubles.  The FP32 kernel holds a cell frame
+// (u, T) as float-float pairs (value = hi + lo, |lo| <= ulp(hi) / 2; Dekker's error-free
+// addition) and the face predictor as plain floats, so its inner loops issue no FP64
+// instruction: a face frame and the cells it reads are handled as FP32 offsets from one
+// reference velocity per chunk, and the increments that the face solve and the cell update
+// return are added to the pairs without rounding error in the running sums.
 #pragma once
 
 #include "pond_kernels.cuh"
@@ -18,6 +25,57 @@ namespace pond {
 
 constexpr int kTubeThreads = 256;
 constexpr int kChunk = kTubeThreads - 1;  // kChunk + 1 faces: one per thread
+
+struct __align__(8) ffloat {
+    float hi, lo;
+};
+
+// storage words of the frames: cell frames and face predictors
+template <typename R>
+struct TubeWords;
+template <>
+struct TubeWords<double> {
+    using cell = double;
+    using face = double;
+};
+template <>
+struct TubeWords<float> {
+    using cell = ffloat;
+    using face = float;
+};
+
+__host__ __device__ __forceinline__ double fr_value(double x) { return x; }
+__host__ __device__ __forceinline__ double fr_value(float x) { return double(x); }
+__host__ __device__ __forceinline__ double fr_value(ffloat x) { return double(x.hi) + double(x.lo); }
+__host__ __device__ __forceinline__ void fr_store(double &w, double v) { w = v; }
+__host__ __device__ __forceinline__ void fr_store(float &w, double v) { w = float(v); }
+__host__ __device__ __forceinline__ void fr_store(ffloat &w, double v)
+{
+    w.hi = float(v);
+    w.lo = float(v - double(w.hi));
+}
+// leading value in the working precision
+__device__ __forceinline__ double fr_lead(double x) { return x; }
+__device__ __forceinline__ float fr_lead(ffloat x) { return x.hi; }
+// x - ref in the working precision
+__device__ __forceinline__ double fr_rel(double x, double ref) { return x - ref; }
+__device__ __forceinline__ float fr_rel(ffloat x, ffloat ref) { return (x.hi - ref.hi) + (x.lo - ref.lo); }
+__device__ __forceinline__ float fr_rel(float x, ffloat ref) { return (x - ref.hi) - ref.lo; }
+// ref + d rounded to a face word
+__device__ __forceinline__ double fr_face(double ref, double d) { return ref + d; }
+__device__ __forceinline__ float fr_face(ffloat ref, float d) { return ref.hi + (ref.lo + d); }
+// x + d: error-free sum of the leading words (Knuth's two-sum), then renormalised
+__device__ __forceinline__ double fr_add(double x, double d) { return x + d; }
+__device__ __forceinline__ ffloat fr_add(ffloat x, float d)
+{
+    const float s = __fadd_rn(x.hi, d);
+    const float bb = __fsub_rn(s, x.hi);
+    const float err = __fadd_rn(__fsub_rn(x.hi, __fsub_rn(s, bb)), __fsub_rn(d, bb)) + x.lo;
+    ffloat o;
+    o.hi = __fadd_rn(s, err);
+    o.lo = __fsub_rn(err, __fsub_rn(o.hi, s));
+    return o;
+}
 
 template <typename R>
 struct TubeParams {
@@ -28,6 +86,8 @@ struct TubeParams {
     const int *order;             // CTA b processes tube order[b] (longest first)
     const double *Cv;            // per tube: 1/(gamma - 1)
     const double *dx;            // per tube
+    using CellW = typename TubeWords<R>::cell;
+    using FaceW = typename TubeWords<R>::face;
     double tau, cfl;
     int limiter;
     double tol;
@@ -35,8 +95,8 @@ struct TubeParams {
     long long ncell, nface;
     R *sf[2];                     // [3][ncell] rho, a2, a3  (two buffers)
     R *sg[2];                     // [3][ncell] b0, b1, b2
-    double *sfr[2];               // [2][ncell] u, T
-    double *fu, *fT;              // face predictors [nface]
+    CellW *sfr[2];                // [2][ncell] u, T
+    FaceW *fu, *fT;               // face predictors [nface]
     double *t, *dt;               // per tube
     double *totals;               // per tube [4]: rho, rho u, 0, rho E summed times dx
     int *status;                  // per tube: 0 running, 1 stopped after a non-physical state
@@ -46,7 +106,7 @@ struct TubeParams {
 
 template <typename R>
 __device__ __forceinline__ void tube_stage(const TubeParams<R> &P, int cur, long long c, R Cvh, R cp, R ce,
-                                           double uref, StagedCell<1, R> &o)
+                                           typename TubeWords<R>::cell uref, StagedCell<1, R> &o)
 {
     const long long n = P.ncell;
     const R rho = P.sf[cur][c];
@@ -54,17 +114,20 @@ __device__ __forceinline__ void tube_stage(const TubeParams<R> &P, int cur, long
     o.A[1] = R(0);
     o.A[2] = cp * P.sf[cur][n + c];
     o.A[3] = cp * P.sf[cur][2 * n + c];
-    const double T = P.sfr[cur][n + c];
-    o.B[0] = cp * P.sg[cur][c] + ce * Cvh * rho * R(T);
+    const R T = fr_lead(P.sfr[cur][n + c]);
+    o.B[0] = cp * P.sg[cur][c] + ce * Cvh * rho * T;
     o.B[1] = cp * P.sg[cur][n + c];
     o.B[2] = cp * P.sg[cur][2 * n + c];
-    o.du[0] = R(P.sfr[cur][c] - uref);
-    o.T = R(T);
+    o.du[0] = R(fr_rel(P.sfr[cur][c], uref));
+    o.T = T;
 }
 
-// per-step constants of one tube (Eqs. FinalUpdateDUGKS, Fbarplus, FluxTransf)
+// per-step constants of one tube (Eqs. FinalUpdateDUGKS, Fbarplus, FluxTransf), formed in
+// FP64 by one thread and kept in the working precision
+template <typename R>
 struct TubeStep {
-    double dt, cp, ce, wb, we, ca, cb, h_dx, dt_dx, inv_dx;
+    double dt;
+    R cp, ce, wb, we, ca, cb, h_dx, dt_dx, inv_dx;
 };
 
 template <typename R>
@@ -72,12 +135,13 @@ __global__ void __launch_bounds__(kTubeThreads, sizeof(R) == 4 ? 3 : 1)
 tube_kernel(const TubeParams<R> P, int steps, int cur0)
 {
     __shared__ StagedCell<1, R> tile[kChunk + 4];
+    using CellW = typename TubeWords<R>::cell;
     __shared__ R faceF[kChunk + 1][4];
     __shared__ R faceG[kChunk + 1][3];
-    __shared__ double faceU[kChunk + 1], faceT[kChunk + 1];
-    __shared__ TubeStep ks;
-    __shared__ double uref_s;
-    __shared__ double red[kTubeThreads / 32];
+    __shared__ R faceU[kChunk + 1], faceT[kChunk + 1];  // face frame: velocity relative to utile, T
+    __shared__ TubeStep<R> ks;
+    __shared__ CellW uref_s;
+    __shared__ R red[kTubeThreads / 32];
     __shared__ int tube_bad;
 
     const int tube = P.order[blockIdx.x];
@@ -87,6 +151,7 @@ tube_kernel(const TubeParams<R> P, int steps, int cur0)
     const int L = P.len[tube];
     const double Cv = P.Cv[tube], dx = P.dx[tube];
     const double tau = P.tau;
+    const R CvR = R(Cv), tolR = R(P.tol);
     unsigned long long my_iters = 0, my_faces = 0, my_nonconv = 0, my_fallbacks = 0, my_nonphys = 0;
 
     for (int step = 0; step < steps; ++step) {
@@ -94,35 +159,34 @@ tube_kernel(const TubeParams<R> P, int steps, int cur0)
         if (threadIdx.x == 0) {
             const double dt = P.dt[tube], h = 0.5 * dt;
             ks.dt = dt;
-            ks.ca = (2.0 * tau - dt) / (2.0 * tau + dt);
-            ks.cb = 2.0 * dt / (2.0 * tau + dt);
-            ks.cp = (2.0 * tau - h) / (2.0 * tau + dt);
-            ks.ce = 3.0 * h / (2.0 * tau + dt);
-            ks.wb = 2.0 * tau / (2.0 * tau + h);
-            ks.we = h / (2.0 * tau + h);
-            ks.h_dx = h / dx;
-            ks.dt_dx = dt / dx;
-            ks.inv_dx = 1.0 / dx;
+            ks.ca = R((2.0 * tau - dt) / (2.0 * tau + dt));
+            ks.cb = R(2.0 * dt / (2.0 * tau + dt));
+            ks.cp = R((2.0 * tau - h) / (2.0 * tau + dt));
+            ks.ce = R(3.0 * h / (2.0 * tau + dt));
+            ks.wb = R(2.0 * tau / (2.0 * tau + h));
+            ks.we = R(h / (2.0 * tau + h));
+            ks.h_dx = R(h / dx);
+            ks.dt_dx = R(dt / dx);
+            ks.inv_dx = R(1.0 / dx);
         }
         __syncthreads();
-        const R cp = R(ks.cp), ce = R(ks.ce), ca = R(ks.ca), cb = R(ks.cb), CvR = R(Cv);
+        const R cp = ks.cp, ce = ks.ce, ca = ks.ca, cb = ks.cb;
         FaceCfg<R> cfg;
-        cfg.h_dn = R(ks.h_dx);
+        cfg.h_dn = ks.h_dx;
         cfg.h_dt = R(0);
         cfg.Cv = CvR;
-        cfg.tol = R(P.tol);
-        cfg.wb = R(ks.wb);
-        cfg.we = R(ks.we);
+        cfg.tol = tolR;
+        cfg.wb = ks.wb;
+        cfg.we = ks.we;
         cfg.limiter = P.limiter;
         cfg.max_iter = P.max_iter;
         cfg.fixed_iters = P.fixed_iters;
-        float rate = 0.f;
-        double rate_d = 0.0;
+        R rate = R(0);
         for (int c0 = 0; c0 < L; c0 += kChunk) {
             const int nc = min(kChunk, L - c0);
             if (threadIdx.x == 0) uref_s = P.sfr[cur][c_off + c0];
             __syncthreads();
-            const double utile = uref_s;
+            const CellW utile = uref_s;
             // stage cells c0-2 .. c0+nc+1 (zero-gradient ends)
             for (int t = threadIdx.x; t < nc + 4; t += blockDim.x) {
                 const int k = min(max(c0 - 2 + t, 0), L - 1);
@@ -134,9 +198,10 @@ tube_kernel(const TubeParams<R> P, int steps, int cur0)
                 const long long k = c0 + f;
                 const StagedCell<1, R> *cells[8] = {&tile[f], &tile[f + 1], &tile[f + 2], &tile[f + 3],
                                                     nullptr, nullptr, nullptr, nullptr};
-                const double uref = P.fu[f_off + k];
+                const R dref[1] = {R(fr_rel(P.fu[f_off + k], utile))};
+                const R uabs[1] = {R(fr_lead(P.fu[f_off + k]))};
                 FaceOut<1, R> o;
-                solve_face<1, R>(cells, false, &uref, R(P.fT[f_off + k]), &utile, cfg, o);
+                solve_face<1, R>(cells, false, dref, uabs, R(P.fT[f_off + k]), cfg, o);
                 const bool owned = f < nc || k == L;
                 if (owned) {
                     my_iters += o.iters;
@@ -149,33 +214,34 @@ tube_kernel(const TubeParams<R> P, int steps, int cur0)
                     for (int q = 0; q < 4; ++q) faceF[f][q] = o.F[q];
 #pragma unroll
                     for (int q = 0; q < 3; ++q) faceG[f][q] = o.G[q];
-                    faceU[f] = o.u[0];
+                    faceU[f] = dref[0] + o.du[0];
                     faceT[f] = o.T;
+                    if (owned) {
+                        P.fu[f_off + k] = fr_face(utile, faceU[f]);
+                        P.fT[f_off + k] = o.T;
+                    }
                 } else {
                     if (owned) ++my_nonphys;
                     tube_bad = 1;
-                    const R nan = R(__longlong_as_double(0x7ff8000000000000ll));
+                    const R nan = R(__int_as_float(0x7fc00000));
 #pragma unroll
                     for (int q = 0; q < 4; ++q) faceF[f][q] = nan;
 #pragma unroll
                     for (int q = 0; q < 3; ++q) faceG[f][q] = nan;
-                    faceU[f] = uref;
-                    faceT[f] = double(nan);
-                }
-                if (owned) {
-                    P.fu[f_off + k] = faceU[f];
-                    P.fT[f_off + k] = faceT[f];
+                    faceU[f] = dref[0];
+                    faceT[f] = nan;
+                    if (owned) P.fT[f_off + k] = nan;
                 }
             }
             __syncthreads();
-            // cells c0 .. c0+nc-1
+            // cells c0 .. c0+nc-1 (cell c0 + t is staged in tile[t + 2])
             const long long n = P.ncell;
             for (int t = threadIdx.x; t < nc; t += blockDim.x) {
                 const long long c = c_off + c0 + t;
-                const double uc[1] = {P.sfr[cur][c]};
-                const double Tc = P.sfr[cur][n + c];
+                const CellW uc = P.sfr[cur][c], Tc = P.sfr[cur][n + c];
+                const R duc = tile[t + 2].du[0];
                 const R rho = P.sf[cur][c];
-                const R Tcr = R(Tc), invTc = R(1) / Tcr, rsqTc = sqrt(invTc), sqTc = Tcr * rsqTc;
+                const R Tcr = R(fr_lead(Tc)), invTc = R(1) / Tcr, rsqTc = sqrt(invTc), sqTc = Tcr * rsqTc;
                 R H[4], G[3];
                 H[0] = ca * rho + cb * rho;
                 H[1] = R(0);
@@ -184,17 +250,21 @@ tube_kernel(const TubeParams<R> P, int steps, int cur0)
                 G[0] = ca * P.sg[cur][c] + cb * (CvR - R(0.5)) * rho * Tcr;
                 G[1] = ca * P.sg[cur][n + c];
                 G[2] = ca * P.sg[cur][2 * n + c];
-                const R sx = R(ks.dt_dx);
+                const R sx = ks.dt_dx;
+                const R ucr = R(fr_lead(uc));
 #pragma unroll
                 for (int side = 0; side < 2; ++side) {
                     const int f = t + side;
-                    const double ub[1] = {faceU[f]};
-                    add_face_flux<1, R>(faceF[f], faceG[f], ub, faceT[f], uc, Tc, invTc, rsqTc, 0, side ? sx : -sx,
-                                        sqTc, R(uc[0]), H, G);
+                    const R dv[1] = {faceU[f] - duc};
+                    add_face_flux<1, R>(faceF[f], faceG[f], dv, faceT[f], Tcr, invTc, rsqTc, 0, side ? sx : -sx, sqTc,
+                                        ucr, H, G);
                 }
-                R Ho[4], Go[3];
-                double un[1], Tn;
-                const bool ok = cell_finish<1, R>(H, G, uc, Tc, invTc, sqTc, CvR, Ho, Go, un, Tn);
+                R Ho[4], Go[3], du[1], dT;
+                bool ok = cell_finish<1, R>(H, G, invTc, sqTc, CvR, Ho, Go, du, dT);
+                const CellW un = fr_add(uc, du[0]);
+                const CellW Tn = fr_add(Tc, Tcr * dT);
+                const R unr = R(fr_lead(un)), Tnr = R(fr_lead(Tn));
+                ok = ok && Tnr > R(0) && isfinite(Tnr);
                 if (!ok) {
                     ++my_nonphys;
                     tube_bad = 1;
@@ -206,26 +276,26 @@ tube_kernel(const TubeParams<R> P, int steps, int cur0)
                 P.sg[nxt][c] = Go[0];
                 P.sg[nxt][n + c] = Go[1];
                 P.sg[nxt][2 * n + c] = Go[2];
-                P.sfr[nxt][c] = un[0];
+                P.sfr[nxt][c] = un;
                 P.sfr[nxt][n + c] = Tn;
                 if (ok) {
-                    if constexpr (sizeof(R) == 8) rate_d = fmax(rate_d, (fabs(un[0]) + sqrt(Tn) * kCHi) / dx);
-                    else rate = fmaxf(rate, (fabsf(float(un[0])) + sqrtf(float(Tn)) * float(kCHi)) * float(ks.inv_dx));
+                    if constexpr (sizeof(R) == 8) rate = fmax(rate, (fabs(unr) + sqrt(Tnr) * kCHi) / dx);
+                    else rate = fmaxf(rate, (fabsf(unr) + sqrtf(Tnr) * float(kCHi)) * ks.inv_dx);
                 }
             }
             __syncthreads();
         }
         // the tube's next time step from its CFL maximum (Sec. IV)
-        double r = sizeof(R) == 8 ? rate_d : double(rate);
+        R r = rate;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_down_sync(0xffffffffu, r, o));
+        for (int o = 16; o > 0; o >>= 1) r = max(r, __shfl_down_sync(0xffffffffu, r, o));
         if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = r;
         __syncthreads();
         if (threadIdx.x == 0) {
-            double rm = 0.0;
-            for (int w = 0; w < kTubeThreads / 32; ++w) rm = fmax(rm, red[w]);
+            R rm = R(0);
+            for (int w = 0; w < kTubeThreads / 32; ++w) rm = max(rm, red[w]);
             P.t[tube] += ks.dt;
-            P.dt[tube] = P.cfl / rm;
+            P.dt[tube] = P.cfl / double(rm);
             P.steps_done[tube] += 1;
             if (tube_bad) P.status[tube] = 1;
         }
@@ -276,8 +346,8 @@ tube_init_kernel(const TubeParams<R> P, int cur, const double *rho, const double
         P.sg[cur][c] = R((Cv - 0.5) * r * T);
         P.sg[cur][n + c] = R(0);
         P.sg[cur][2 * n + c] = R(0);
-        P.sfr[cur][c] = u;
-        P.sfr[cur][n + c] = T;
+        fr_store(P.sfr[cur][c], u);
+        fr_store(P.sfr[cur][n + c], T);
         if (r > 0.0 && T > 0.0 && isfinite(r) && isfinite(T)) {
             rate = fmax(rate, (fabs(u) + sqrt(T) * kCHi) / dx);
         } else {
@@ -290,8 +360,8 @@ tube_init_kernel(const TubeParams<R> P, int cur, const double *rho, const double
         const double ra = rho[a], rb = rho[b], ua = ux[a], ub = ux[b];
         const double Ea = p[a] * Cv + 0.5 * ra * ua * ua, Eb = p[b] * Cv + 0.5 * rb * ub * ub;
         const double r = 0.5 * (ra + rb), m = 0.5 * (ra * ua + rb * ub), E = 0.5 * (Ea + Eb);
-        P.fu[f_off + k] = m / r;
-        P.fT[f_off + k] = (E - 0.5 * m * m / r) / (Cv * r);
+        fr_store(P.fu[f_off + k], m / r);
+        fr_store(P.fT[f_off + k], (E - 0.5 * m * m / r) / (Cv * r));
     }
     if (bad) { atomicAdd(&P.diag->nonphys, bad); atomicOr(&P.diag->flags, FLAG_NONPHYSICAL); any_bad = 1; }
 #pragma unroll
@@ -322,7 +392,7 @@ tube_conserved_kernel(const TubeParams<R> P, int cur, double *rho, double *mx, d
     double s[3] = {0, 0, 0};
     for (int k = threadIdx.x; k < L; k += blockDim.x) {
         const long long c = c_off + k;
-        const double r = double(P.sf[cur][c]), u = P.sfr[cur][c], T = P.sfr[cur][n + c];
+        const double r = double(P.sf[cur][c]), u = fr_value(P.sfr[cur][c]), T = fr_value(P.sfr[cur][n + c]);
         const double v[3] = {r, r * u, r * (Cv * T + 0.5 * u * u)};
         if (rho) rho[c] = v[0];
         if (mx) mx[c] = v[1];
@@ -364,8 +434,8 @@ __global__ void tube_export_kernel(const TubeParams<R> P, int cur, double *cf, d
     if (cg)
         for (int q = 0; q < 3; ++q) cg[3 * c + q] = double(P.sg[cur][q * n + c]);
     if (fr) {
-        fr[2 * c] = P.sfr[cur][c];
-        fr[2 * c + 1] = P.sfr[cur][n + c];
+        fr[2 * c] = fr_value(P.sfr[cur][c]);
+        fr[2 * c + 1] = fr_value(P.sfr[cur][n + c]);
     }
 }
 

@@ -431,31 +431,30 @@ template <int D, typename R>
 struct FaceOut {
     R F[NCoef<D, 3>::value];   // f, g coefficients of phi(x_b, t_{n+1/2}) in the face frame (x, y order)
     R G[NCoef<D, 2>::value];
-    double u[D];
-    double T;
+    R du[D];                   // face frame velocity minus the predictor's (x, y order)
+    R T;
     int iters, fallbacks;
     bool done, have;
 };
 
 // The face predictor-corrector of Sec. III.B.3 at one face.  cells: stencil slots 0 LL,
 // 1 L, 2 R, 3 RR, 4 L-t, 5 L+t, 6 R-t, 7 R+t (staged phi-bar-plus, velocities relative to
-// utile); swap: the face normal is y; uref, Tpred: the predictor lambda_0 (x, y order).
+// the tile reference); swap: the face normal is y; the predictor lambda_0 is given by its
+// velocity minus the tile reference (dref) and its absolute velocity (uabs, used only for
+// upwinding and departure points), both in face axes (normal, tangential), and Tpred.
 // Passes run until the frame converges (or fixed_iters passes); a pass whose moments define
 // no frame restarts the corrector once from the frame of the pooled moments of the
 // stencil, else the corrector stops at the last pass that did.  The face populations are
 // Eq. (FluxTransf) at the frame of the last valid pass's moments.
 template <int D, typename R>
-__device__ __forceinline__ void solve_face(const StagedCell<D, R> *const *cells, bool swap, const double *uref, R Tpred,
-                                           const double *utile, const FaceCfg<R> &cfg, FaceOut<D, R> &o)
+__device__ __forceinline__ void solve_face(const StagedCell<D, R> *const *cells, bool swap, const R *dref, const R *uabs,
+                                           R Tpred, const FaceCfg<R> &cfg, FaceOut<D, R> &o)
 {
     o.fallbacks = 0;
     constexpr int NCELL = D == 2 ? 8 : 4;
     constexpr int NFC = NCoef<D, 3>::value, NGC = NCoef<D, 2>::value;
     const int na = swap ? 1 : 0, ta = swap ? 0 : 1;  // normal / tangential axes
     const R h_dn = cfg.h_dn, h_dt = cfg.h_dt;
-    R dref[D];
-    dref[0] = R(uref[na] - utile[na]);
-    if constexpr (D == 2) dref[1] = R(uref[ta] - utile[ta]);
     R dc[NCELL][D];
 #pragma unroll
     for (int s = 0; s < NCELL; ++s) {
@@ -463,8 +462,8 @@ __device__ __forceinline__ void solve_face(const StagedCell<D, R> *const *cells,
         if constexpr (D == 2) dc[s][1] = cells[s]->du[ta] - dref[1];
     }
     R uref_t = R(0);
-    if constexpr (D == 2) uref_t = R(uref[ta]);
-    const R uref_n = R(uref[na]);
+    if constexpr (D == 2) uref_t = uabs[1];
+    const R uref_n = uabs[0];
     const R Cv = cfg.Cv, tolR = cfg.tol;
 
     R dl[D], Tl = Tpred;
@@ -552,9 +551,9 @@ __device__ __forceinline__ void solve_face(const StagedCell<D, R> *const *cells,
         for (int k = 1; k < NGC; ++k) Go[k] = wb * Go[k];
         orient<D, 3, R>(Fo, o.F, swap);
         orient<D, 2, R>(Go, o.G, swap);
-        o.u[na] = uref[na] + double(keep_dl[0]) + double(out_du[0]);
-        if constexpr (D == 2) o.u[ta] = uref[ta] + double(keep_dl[1]) + double(out_du[1]);
-        o.T = double(out_T);
+        o.du[na] = keep_dl[0] + out_du[0];
+        if constexpr (D == 2) o.du[ta] = keep_dl[1] + out_du[1];
+        o.T = out_T;
     }
 }
 
@@ -637,14 +636,21 @@ face_kernel(const Params<D, R> P)
         cfg.Cv = R(P.Cv); cfg.tol = R(P.tol); cfg.wb = R(K.wb); cfg.we = R(K.we);
         cfg.limiter = P.limiter; cfg.max_iter = P.max_iter; cfg.fixed_iters = P.fixed_iters;
         const double Tp = Frm[D * nf + fidx];
-        solve_face<D, R>(cells, swap, uref, R(Tp), utile, cfg, o);
+        const int na = swap ? 1 : 0, ta = 1 - na;
+        R dref[D], uabs[D];
+        dref[0] = R(uref[na] - utile[na]);
+        uabs[0] = R(uref[na]);
+        if constexpr (D == 2) {
+            dref[1] = R(uref[ta] - utile[ta]);
+            uabs[1] = R(uref[ta]);
+        }
+        solve_face<D, R>(cells, swap, dref, uabs, R(Tp), cfg, o);
         my_iters = o.iters; my_nonconv = o.done ? 0 : 1; my_fallbacks = o.fallbacks;
         if constexpr (COLLECT && D == 2) {
             const unsigned long long hsh = (unsigned long long)(fidx * 2 + dir + 1) * 0x9E3779B97F4A7C15ull ^
                                            (unsigned long long)(K.steps + 1) * 0xBF58476D1CE4E5B9ull;
             if (o.have && o.done && Tp > 0.0 && ((hsh >> 33) % (unsigned long long)P.pair_every) == 0) {
-                const int na = swap ? 1 : 0, ta = 1 - na;
-                const float dn = float(uref[na] - utile[na]), dt_ = float(uref[ta] - utile[ta]);
+                const float dn = float(dref[0]), dt_ = float(dref[D - 1]);
                 mlp::SlotPrim sp[8];
 #pragma unroll
                 for (int q = 0; q < 8; ++q)
@@ -658,9 +664,9 @@ face_kernel(const Params<D, R> P)
 #pragma unroll
                     for (int q = 0; q < mlp::kIn; ++q) row[q] = f[q];
                     const double rs = 1.0 / sqrt(Tp);
-                    row[mlp::kIn + 0] = float((o.u[na] - uref[na]) * rs);
-                    row[mlp::kIn + 1] = float((o.u[ta] - uref[ta]) * rs);
-                    row[mlp::kIn + 2] = float(log(o.T / Tp));
+                    row[mlp::kIn + 0] = float(double(o.du[na]) * rs);
+                    row[mlp::kIn + 1] = float(double(o.du[ta]) * rs);
+                    row[mlp::kIn + 2] = float(log(double(o.T) / Tp));
                     row[mlp::kIn + 3] = float(o.iters);
                 }
             }
@@ -671,8 +677,8 @@ face_kernel(const Params<D, R> P)
 #pragma unroll
             for (int k = 0; k < NGC; ++k) Gout[k * nf + fidx] = o.G[k];
 #pragma unroll
-            for (int a = 0; a < D; ++a) Frm[a * nf + fidx] = o.u[a];
-            Frm[D * nf + fidx] = o.T;
+            for (int a = 0; a < D; ++a) Frm[a * nf + fidx] = uref[a] + double(o.du[a]);
+            Frm[D * nf + fidx] = double(o.T);
         } else {
             ++my_nonphys;
             const R nan = R(__longlong_as_double(0x7ff8000000000000ll));
@@ -712,17 +718,14 @@ face_kernel(const Params<D, R> P)
 // Grad forms have no moments above their order, so the product closes on the same orders.
 // invTc, rsqTc: 1/T and 1/sqrt(T) of the cell frame.
 template <int D, typename R>
-__device__ __forceinline__ void add_face_flux(const R *Fc, const R *Gc, const double *ub, double Tb,
-                                              const double *uc, double Tc, R invTc, R rsqTc, int axis, R scale,
-                                              R sqTc, R un, R *H, R *G)
+__device__ __forceinline__ void add_face_flux(const R *Fc, const R *Gc, const R *dv, R Tbr, R Tcr, R invTc, R rsqTc,
+                                              int axis, R scale, R sqTc, R un, R *H, R *G)
 {
     constexpr int NFC = NCoef<D, 3>::value, NGC = NCoef<D, 2>::value;
-    const R Tbr = R(Tb), Tcr = R(Tc);
     const R s = sqrt(Tbr * invTc), e = (Tbr - Tcr) * invTc;
-    // velocity differences in FP64: the frames can move at high Mach
-    Map1<R> X(s, e, R(ub[0] - uc[0]) * rsqTc);
+    Map1<R> X(s, e, dv[0] * rsqTc);
     Map1<R> Y = X;
-    if constexpr (D == 2) Y = Map1<R>(s, e, R(ub[1] - uc[1]) * rsqTc);
+    if constexpr (D == 2) Y = Map1<R>(s, e, dv[1] * rsqTc);
     R Fp[NFC], Gp[NGC];
     shift_scale<D, 3, R>(Fc, X, Y, Fp);
     shift_scale<D, 2, R>(Gc, X, Y, Gp);
@@ -842,17 +845,17 @@ __device__ __forceinline__ void reduce_rate_and_advance(Clock *clock, double rat
 }
 
 // Step 1 of the next step after the update: the new co-moving frame from the conserved
-// moments (H: f, G: g Hermite moments in the old cell frame (uc, Tc)) and the Grad
-// projection into it (f third order, g second order).  The frame is advanced in FP64 by
-// increments formed relative to the old frame: u' = u + du, T' = T (1 + dT/T).
+// moments (H: f, G: g Hermite moments in the old cell frame) and the Grad projection into
+// it (f third order, g second order).  The frame changes by increments formed relative to
+// the old frame, du and dT (T' = T (1 + dT)), which the caller applies to its own
+// representation of the frame.
 template <int D, typename R>
-__device__ __forceinline__ bool cell_finish(const R *H, const R *G, const double *uc, double Tc, R invTc, R sqTc, R Cv,
-                                            R *Ho, R *Go, double *un, double &Tn)
+__device__ __forceinline__ bool cell_finish(const R *H, const R *G, R invTc, R sqTc, R Cv, R *Ho, R *Go, R *du, R &dT)
 {
     const R rsqTc = invTc * sqTc;
     const R rn = H[0];
     const R irn = R(1) / rn;
-    R du[D], k2 = R(0), trH;
+    R k2 = R(0), trH;
     if constexpr (D == 1) {
         du[0] = sqTc * H[1] * irn;
         k2 = du[0] * du[0];
@@ -864,11 +867,8 @@ __device__ __forceinline__ bool cell_finish(const R *H, const R *G, const double
         trH = H[hidx(2, 0)] + H[hidx(0, 2)];
     }
     // T'/T - 1 = (1/2 tr H + G0/T - (Cv - D/2) rho' - rho' |du|^2/(2T)) / (Cv rho')
-    const R dT = (R(0.5) * trH + G[0] * invTc - (Cv - R(0.5 * D)) * rn - R(0.5) * rn * k2 * invTc) / (Cv * rn);
-    Tn = Tc + Tc * double(dT);
-#pragma unroll
-    for (int a = 0; a < D; ++a) un[a] = uc[a] + double(du[a]);
-    const bool ok = rn > R(0) && Tn > 0.0 && isfinite(double(rn)) && isfinite(Tn);
+    dT = (R(0.5) * trH + G[0] * invTc - (Cv - R(0.5 * D)) * rn - R(0.5) * rn * k2 * invTc) / (Cv * rn);
+    const bool ok = rn > R(0) && R(1) + dT > R(0) && isfinite(double(rn)) && isfinite(double(dT));
     // s^2 = T/T' = 1/(1 + dT/T), e = s^2 - 1, d = -du/sqrt(T')
     const R s2 = R(1) / (R(1) + dT);
     const R sc = sqrt(s2), e = -dT * s2;
@@ -923,16 +923,15 @@ cell_kernel(const Params<D, R> P)
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
             const long long f = j * (P.nx + 1) + i + side;
-            R Fc[NFC], Gc[NGC];
-            double ub[D];
+            R Fc[NFC], Gc[NGC], dv[D];
 #pragma unroll
             for (int k = 0; k < NFC; ++k) Fc[k] = P.xf[k * nxf + f];
 #pragma unroll
             for (int k = 0; k < NGC; ++k) Gc[k] = P.xg[k * nxf + f];
 #pragma unroll
-            for (int a = 0; a < D; ++a) ub[a] = P.xfr[a * nxf + f];
-            const double Tb = P.xfr[D * nxf + f];
-            add_face_flux<D, R>(Fc, Gc, ub, Tb, uc, Tc, invTc, rsqTc, 0, side ? sx : -sx, sqTc, R(uc[0]), H, G);
+            for (int a = 0; a < D; ++a) dv[a] = R(P.xfr[a * nxf + f] - uc[a]);  // FP64: frames can move at high Mach
+            const R Tb = R(P.xfr[D * nxf + f]);
+            add_face_flux<D, R>(Fc, Gc, dv, Tb, Tcr, invTc, rsqTc, 0, side ? sx : -sx, sqTc, R(uc[0]), H, G);
         }
         if constexpr (D == 2) {
             const long long nyf = P.nyf();
@@ -940,21 +939,24 @@ cell_kernel(const Params<D, R> P)
 #pragma unroll
             for (int side = 0; side < 2; ++side) {
                 const long long f = (j + side) * P.nx + i;
-                R Fc[NFC], Gc[NGC];
-                double ub[D];
+                R Fc[NFC], Gc[NGC], dv[D];
 #pragma unroll
                 for (int k = 0; k < NFC; ++k) Fc[k] = P.yf[k * nyf + f];
 #pragma unroll
                 for (int k = 0; k < NGC; ++k) Gc[k] = P.yg[k * nyf + f];
 #pragma unroll
-                for (int a = 0; a < D; ++a) ub[a] = P.yfr[a * nyf + f];
-                const double Tb = P.yfr[D * nyf + f];
-                add_face_flux<D, R>(Fc, Gc, ub, Tb, uc, Tc, invTc, rsqTc, 1, side ? sy : -sy, sqTc, R(uc[1]), H, G);
+                for (int a = 0; a < D; ++a) dv[a] = R(P.yfr[a * nyf + f] - uc[a]);
+                const R Tb = R(P.yfr[D * nyf + f]);
+                add_face_flux<D, R>(Fc, Gc, dv, Tb, Tcr, invTc, rsqTc, 1, side ? sy : -sy, sqTc, R(uc[1]), H, G);
             }
         }
-        R Ho[NFC], Go[NGC];
-        double un[D], Tn;
-        const bool ok = cell_finish<D, R>(H, G, uc, Tc, invTc, sqTc, Cv, Ho, Go, un, Tn);
+        R Ho[NFC], Go[NGC], du[D], dT;
+        bool ok = cell_finish<D, R>(H, G, invTc, sqTc, Cv, Ho, Go, du, dT);
+        double un[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) un[a] = uc[a] + double(du[a]);
+        const double Tn = Tc + Tc * double(dT);
+        ok = ok && Tn > 0.0 && isfinite(Tn);
         if (!ok) {
             atomicOr(&P.diag->flags, FLAG_NONPHYSICAL);
             atomicAdd(&P.diag->nonphys, 1ull);
