@@ -37,7 +37,7 @@ N_SMS, FP32_LANES = 152, 128
 FACE_KERNEL_DRAM_BYTES = 136.7e6 + 178.4e6  # ncu dram read + write of one launch at 1024^2
 FLOPS_PER_FACE_PASS = 4550.0
 # algorithmic bytes per cell-update of the FP32 D2Q16 layout: the face kernel reads the
-# cell state (8 + 6 FP32 coefficients + 3 FP64 frame = 80 B) and two face predictors
+# cell state (8 + 6 FP32 coefficients + 3 float-float frame words = 80 B) and two face predictors
 # (2 x 24 B) and writes two faces (2 x (16 x 4 + 24) B)
 FACE_KERNEL_BYTES_PER_CELL = 80 + 48 + 176
 
@@ -262,7 +262,7 @@ def main():
     def max_over_ranks_(x):
         return max_over_ranks(x, world, device="cuda")
 
-    # ---- headline: FP32 populations, FP64 frames
+    # ---- headline: FP32 populations, float-float frames
     s = pond.Solver(pb, precision="fp32", tau=1e-5, cfl=0.2, max_iter=16)
     s.set_primitive()
     s.step(args.warmup)
@@ -373,7 +373,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": el_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "quadrants_2d_1024_seed%d" % args.seed, "lattice": "D2Q16", "cells": ncell,
-                   "precision": "fp32 populations, fp64 frames", "cfl": 0.2, "tau": 1e-5,
+                   "precision": "fp32 populations, float-float frames", "cfl": 0.2, "tau": 1e-5,
                    "corrector": "tol 1e-6, max 16 passes", "l2": "working set %.0f MB > L2" % (
                        (ncell * (80 + 2 * 88)) / 1e6), "parallelism": "replicas" if world > 1 else "single"},
         "fp64": {"value": fp64_value, "unit": "MLUPS", "steps": args.fp64_steps, "speedup_fp32": value / fp64_value},

@@ -121,16 +121,20 @@ pond_status setup(pond_state *s)
     P.tau = s->tau;
     P.limiter = s->opts.limiter;
     P.tol = s->opts.tol;
+    P.Cv_r = R(P.Cv);
+    P.Cvh_r = R(P.Cv - 0.5 * D);
+    P.tol_r = R(P.tol);
     P.max_iter = s->opts.max_iter;
     P.fixed_iters = s->opts.fixed_iters;
     const long long n = P.ncell(), nxf = P.nxf(), nyf = D == 2 ? P.nyf() : 0;
+    using W = typename P_t::W;
     constexpr int NFC = P_t::NFC, NGC = P_t::NGC, NFS = P_t::NFS;
     size_t off = 0;
     auto take = [&](size_t b) { size_t o = off; off = align_up(off + b, 256); return o; };
-    const size_t o_sf = take(sizeof(R) * NFS * n), o_sg = take(sizeof(R) * NGC * n), o_sfr = take(8 * (D + 1) * n);
-    const size_t o_xf = take(sizeof(R) * NFC * nxf), o_xg = take(sizeof(R) * NGC * nxf), o_xfr = take(8 * (D + 1) * nxf);
+    const size_t o_sf = take(sizeof(R) * NFS * n), o_sg = take(sizeof(R) * NGC * n), o_sfr = take(sizeof(W) * (D + 1) * n);
+    const size_t o_xf = take(sizeof(R) * NFC * nxf), o_xg = take(sizeof(R) * NGC * nxf), o_xfr = take(sizeof(W) * (D + 1) * nxf);
     size_t o_yf = 0, o_yg = 0, o_yfr = 0;
-    if (D == 2) { o_yf = take(sizeof(R) * NFC * nyf); o_yg = take(sizeof(R) * NGC * nyf); o_yfr = take(8 * (D + 1) * nyf); }
+    if (D == 2) { o_yf = take(sizeof(R) * NFC * nyf); o_yg = take(sizeof(R) * NGC * nyf); o_yfr = take(sizeof(W) * (D + 1) * nyf); }
     const size_t o_clock = take(sizeof(pond::Clock)), o_diag = take(sizeof(pond::Diag));
     size_t stage = 4 * size_t(n);
     stage = std::max<size_t>(stage, size_t(NFC + NGC + D + 1) * size_t(n));
@@ -142,14 +146,14 @@ pond_status setup(pond_state *s)
     if (!s->base) return fail(POND_ERR_OOM, "device allocation of %zu bytes failed", off);
     P.sf = reinterpret_cast<R *>(s->base + o_sf);
     P.sg = reinterpret_cast<R *>(s->base + o_sg);
-    P.sfr = reinterpret_cast<double *>(s->base + o_sfr);
+    P.sfr = reinterpret_cast<W *>(s->base + o_sfr);
     P.xf = reinterpret_cast<R *>(s->base + o_xf);
     P.xg = reinterpret_cast<R *>(s->base + o_xg);
-    P.xfr = reinterpret_cast<double *>(s->base + o_xfr);
+    P.xfr = reinterpret_cast<W *>(s->base + o_xfr);
     if (D == 2) {
         P.yf = reinterpret_cast<R *>(s->base + o_yf);
         P.yg = reinterpret_cast<R *>(s->base + o_yg);
-        P.yfr = reinterpret_cast<double *>(s->base + o_yfr);
+        P.yfr = reinterpret_cast<W *>(s->base + o_yfr);
     }
     P.clock = reinterpret_cast<pond::Clock *>(s->base + o_clock);
     P.diag = reinterpret_cast<pond::Diag *>(s->base + o_diag);
@@ -404,26 +408,27 @@ template <int D, typename R>
 pond_status face_gauges_impl(pond_state *s, double *xg, double *yg, const double *xin, const double *yin)
 {
     auto &P = params_of<D, R>(s);
+    using W = typename pond::Params<D, R>::W;
     const long long nxf = P.nxf(), nyf = D == 2 ? P.nyf() : 0;
     const int w = D + 1;
     for (int dir = 0; dir < D; ++dir) {
         const long long nf = dir == 0 ? nxf : nyf;
-        double *dev = dir == 0 ? P.xfr : P.yfr;
-        std::vector<double> h(size_t(w) * nf);
+        W *dev = dir == 0 ? P.xfr : P.yfr;
+        std::vector<W> h(size_t(w) * nf);
         if (xin || yin) {
             const double *src = dir == 0 ? xin : yin;
             if (!src) continue;
             for (long long f = 0; f < nf; ++f)
-                for (int a = 0; a < w; ++a) h[size_t(a) * nf + f] = src[f * w + a];
-            CUDA_TRY(cudaMemcpyAsync(dev, h.data(), 8 * w * nf, cudaMemcpyHostToDevice, s->stream));
+                for (int a = 0; a < w; ++a) pond::fr_store(h[size_t(a) * nf + f], src[f * w + a]);
+            CUDA_TRY(cudaMemcpyAsync(dev, h.data(), sizeof(W) * w * nf, cudaMemcpyHostToDevice, s->stream));
             CUDA_TRY(cudaStreamSynchronize(s->stream));
         } else {
             double *dst = dir == 0 ? xg : yg;
             if (!dst) continue;
-            CUDA_TRY(cudaMemcpyAsync(h.data(), dev, 8 * w * nf, cudaMemcpyDeviceToHost, s->stream));
+            CUDA_TRY(cudaMemcpyAsync(h.data(), dev, sizeof(W) * w * nf, cudaMemcpyDeviceToHost, s->stream));
             CUDA_TRY(cudaStreamSynchronize(s->stream));
             for (long long f = 0; f < nf; ++f)
-                for (int a = 0; a < w; ++a) dst[f * w + a] = h[size_t(a) * nf + f];
+                for (int a = 0; a < w; ++a) dst[f * w + a] = pond::fr_value(h[size_t(a) * nf + f]);
         }
     }
     return POND_OK;

@@ -12,11 +12,9 @@
 // face predictor read and written once.
 //
 // Frames.  The FP64 kernel holds each frame as doubles.  The FP32 kernel holds a cell frame
-// (u, T) as float-float pairs (value = hi + lo, |lo| <= ulp(hi) / 2; Dekker's error-free
-// addition) and the face predictor as plain floats, so its inner loops issue no FP64
-// instruction: a face frame and the cells it reads are handled as FP32 offsets from one
-// reference velocity per chunk, and the increments that the face solve and the cell update
-// return are added to the pairs without rounding error in the running sums.
+// (u, T) as a float-float pair and the face predictor as plain floats, so its inner loops
+// issue no FP64 instruction: a face frame and the cells it reads are handled as FP32
+// offsets from one reference velocity per chunk.
 #pragma once
 
 #include "pond_kernels.cuh"
@@ -25,57 +23,6 @@ namespace pond {
 
 constexpr int kTubeThreads = 256;
 constexpr int kChunk = kTubeThreads - 1;  // kChunk + 1 faces: one per thread
-
-struct __align__(8) ffloat {
-    float hi, lo;
-};
-
-// storage words of the frames: cell frames and face predictors
-template <typename R>
-struct TubeWords;
-template <>
-struct TubeWords<double> {
-    using cell = double;
-    using face = double;
-};
-template <>
-struct TubeWords<float> {
-    using cell = ffloat;
-    using face = float;
-};
-
-__host__ __device__ __forceinline__ double fr_value(double x) { return x; }
-__host__ __device__ __forceinline__ double fr_value(float x) { return double(x); }
-__host__ __device__ __forceinline__ double fr_value(ffloat x) { return double(x.hi) + double(x.lo); }
-__host__ __device__ __forceinline__ void fr_store(double &w, double v) { w = v; }
-__host__ __device__ __forceinline__ void fr_store(float &w, double v) { w = float(v); }
-__host__ __device__ __forceinline__ void fr_store(ffloat &w, double v)
-{
-    w.hi = float(v);
-    w.lo = float(v - double(w.hi));
-}
-// leading value in the working precision
-__device__ __forceinline__ double fr_lead(double x) { return x; }
-__device__ __forceinline__ float fr_lead(ffloat x) { return x.hi; }
-// x - ref in the working precision
-__device__ __forceinline__ double fr_rel(double x, double ref) { return x - ref; }
-__device__ __forceinline__ float fr_rel(ffloat x, ffloat ref) { return (x.hi - ref.hi) + (x.lo - ref.lo); }
-__device__ __forceinline__ float fr_rel(float x, ffloat ref) { return (x - ref.hi) - ref.lo; }
-// ref + d rounded to a face word
-__device__ __forceinline__ double fr_face(double ref, double d) { return ref + d; }
-__device__ __forceinline__ float fr_face(ffloat ref, float d) { return ref.hi + (ref.lo + d); }
-// x + d: error-free sum of the leading words (Knuth's two-sum), then renormalised
-__device__ __forceinline__ double fr_add(double x, double d) { return x + d; }
-__device__ __forceinline__ ffloat fr_add(ffloat x, float d)
-{
-    const float s = __fadd_rn(x.hi, d);
-    const float bb = __fsub_rn(s, x.hi);
-    const float err = __fadd_rn(__fsub_rn(x.hi, __fsub_rn(s, bb)), __fsub_rn(d, bb)) + x.lo;
-    ffloat o;
-    o.hi = __fadd_rn(s, err);
-    o.lo = __fsub_rn(err, __fsub_rn(o.hi, s));
-    return o;
-}
 
 template <typename R>
 struct TubeParams {
@@ -86,8 +33,8 @@ struct TubeParams {
     const int *order;             // CTA b processes tube order[b] (longest first)
     const double *Cv;            // per tube: 1/(gamma - 1)
     const double *dx;            // per tube
-    using CellW = typename TubeWords<R>::cell;
-    using FaceW = typename TubeWords<R>::face;
+    using CellW = typename FrameWords<R>::word;
+    using FaceW = typename FrameWords<R>::pred;
     double tau, cfl;
     int limiter;
     double tol;
@@ -106,7 +53,7 @@ struct TubeParams {
 
 template <typename R>
 __device__ __forceinline__ void tube_stage(const TubeParams<R> &P, int cur, long long c, R Cvh, R cp, R ce,
-                                           typename TubeWords<R>::cell uref, StagedCell<1, R> &o)
+                                           typename FrameWords<R>::word uref, StagedCell<1, R> &o)
 {
     const long long n = P.ncell;
     const R rho = P.sf[cur][c];
@@ -135,7 +82,7 @@ __global__ void __launch_bounds__(kTubeThreads, sizeof(R) == 4 ? 3 : 1)
 tube_kernel(const TubeParams<R> P, int steps, int cur0)
 {
     __shared__ StagedCell<1, R> tile[kChunk + 4];
-    using CellW = typename TubeWords<R>::cell;
+    using CellW = typename FrameWords<R>::word;
     __shared__ R faceF[kChunk + 1][4];
     __shared__ R faceG[kChunk + 1][3];
     __shared__ R faceU[kChunk + 1], faceT[kChunk + 1];  // face frame: velocity relative to utile, T

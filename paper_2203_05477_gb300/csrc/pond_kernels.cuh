@@ -21,39 +21,120 @@
 
 namespace pond {
 
+// ------------------------------------------------------------------ frame words
+//
+// Frames (u, T) are stored in FP64 words when the populations are FP64.  With FP32
+// populations they are float-float pairs, value = hi + lo with |lo| <= ulp(hi)/2 (Dekker's
+// double-length arithmetic): about 48 significant bits, with every operation on the FP32
+// pipes.  GB300 runs FP64 at 1/64 of the FP32 rate, so this keeps FP64 instructions out of
+// the stencil loops.  Frame arithmetic only ever forms differences of nearby frames and adds
+// FP32 increments formed relative to the old frame, which is what the pairs do exactly.
+
+struct __align__(8) ffloat {
+    float hi, lo;
+};
+
+// storage words of a frame component: word for cell and face frames, pred for a face
+// predictor that only seeds the corrector
+template <typename R>
+struct FrameWords;
+template <>
+struct FrameWords<double> {
+    using word = double;
+    using pred = double;
+};
+template <>
+struct FrameWords<float> {
+    using word = ffloat;
+    using pred = float;
+};
+
+__host__ __device__ __forceinline__ double fr_value(double x) { return x; }
+__host__ __device__ __forceinline__ double fr_value(float x) { return double(x); }
+__host__ __device__ __forceinline__ double fr_value(ffloat x) { return double(x.hi) + double(x.lo); }
+__host__ __device__ __forceinline__ void fr_store(double &w, double v) { w = v; }
+__host__ __device__ __forceinline__ void fr_store(float &w, double v) { w = float(v); }
+__host__ __device__ __forceinline__ void fr_store(ffloat &w, double v)
+{
+    w.hi = float(v);
+    w.lo = float(v - double(w.hi));
+}
+// a working-precision value as a word
+__device__ __forceinline__ double fr_word(double v) { return v; }
+__device__ __forceinline__ ffloat fr_word(float v) { return ffloat{v, 0.f}; }
+// leading value in the working precision
+__device__ __forceinline__ double fr_lead(double x) { return x; }
+__device__ __forceinline__ float fr_lead(ffloat x) { return x.hi; }
+// x - ref in the working precision
+__device__ __forceinline__ double fr_rel(double x, double ref) { return x - ref; }
+__device__ __forceinline__ float fr_rel(ffloat x, ffloat ref) { return (x.hi - ref.hi) + (x.lo - ref.lo); }
+__device__ __forceinline__ float fr_rel(float x, ffloat ref) { return (x - ref.hi) - ref.lo; }
+// ref + d rounded to a face word
+__device__ __forceinline__ double fr_face(double ref, double d) { return ref + d; }
+__device__ __forceinline__ float fr_face(ffloat ref, float d) { return ref.hi + (ref.lo + d); }
+// x + d: error-free sum of the leading words (Knuth's two-sum), then renormalised
+__device__ __forceinline__ double fr_add(double x, double d) { return x + d; }
+__device__ __forceinline__ ffloat fr_add(ffloat x, float d)
+{
+    const float s = __fadd_rn(x.hi, d);
+    const float bb = __fsub_rn(s, x.hi);
+    const float err = __fadd_rn(__fsub_rn(x.hi, __fsub_rn(s, bb)), __fsub_rn(d, bb)) + x.lo;
+    ffloat o;
+    o.hi = __fadd_rn(s, err);
+    o.lo = __fsub_rn(err, __fsub_rn(o.hi, s));
+    return o;
+}
+
+
 enum { BC_TRANSMISSIVE = 0, BC_PERIODIC = 1, BC_INFLOW = 2 };
 enum { FLAG_NONPHYSICAL = 1u, FLAG_NOT_CONVERGED = 2u, FLAG_TIMEOUT = 4u };
+
+// constants of the step about to run, set with dt (Eqs. FinalUpdateDUGKS, Fbarplus,
+// FluxTransf): update ca = (2tau-dt)/(2tau+dt), cb = 2dt/(2tau+dt); phi-bar-plus
+// cp = (2tau-h)/(2tau+dt), ce = 3h/(2tau+dt); face populations wb = 2tau/(2tau+h),
+// we = h/(2tau+h); departure offsets h/dx, h/dy; h = dt/2
+template <typename T>
+struct StepC {
+    T ca, cb, cp, ce, wb, we, h_dx, h_dy, dt_dx, dt_dy, inv_dx, inv_dy;
+};
 
 struct Clock {
     double t, dt, t_end, cfl;
     double tau, dx, dy;
-    // constants of the step about to run, set with dt (Eqs. FinalUpdateDUGKS, Fbarplus,
-    // FluxTransf): update ca = (2tau-dt)/(2tau+dt), cb = 2dt/(2tau+dt); phi-bar-plus
-    // cp = (2tau-h)/(2tau+dt), ce = 3h/(2tau+dt); face populations wb = 2tau/(2tau+h),
-    // we = h/(2tau+h); departure offsets h/dx, h/dy; h = dt/2
-    double ca, cb, cp, ce, wb, we, h_dx, h_dy, dt_dx, dt_dy, inv_dx, inv_dy;
+    StepC<double> kd;               // formed in FP64
+    StepC<float> kf;                // the same rounded to FP32
     long long steps;
     unsigned long long rate_bits;   // max CFL rate of the step being reduced (as double bits)
     unsigned int blocks_done;
     unsigned int pad;
 };
 
+template <typename R>
+__host__ __device__ __forceinline__ const StepC<R> &step_c(const Clock &K)
+{
+    if constexpr (sizeof(R) == 8) return K.kd;
+    else return K.kf;
+}
+
 __host__ __device__ inline void set_step_constants(Clock &c, double dt)
 {
     const double tau = c.tau, h = 0.5 * dt;
     c.dt = dt;
-    c.ca = (2.0 * tau - dt) / (2.0 * tau + dt);
-    c.cb = 2.0 * dt / (2.0 * tau + dt);
-    c.cp = (2.0 * tau - h) / (2.0 * tau + dt);
-    c.ce = 3.0 * h / (2.0 * tau + dt);
-    c.wb = 2.0 * tau / (2.0 * tau + h);
-    c.we = h / (2.0 * tau + h);
-    c.h_dx = h / c.dx;
-    c.h_dy = h / c.dy;
-    c.dt_dx = dt / c.dx;
-    c.dt_dy = dt / c.dy;
-    c.inv_dx = 1.0 / c.dx;
-    c.inv_dy = 1.0 / c.dy;
+    StepC<double> &k = c.kd;
+    k.ca = (2.0 * tau - dt) / (2.0 * tau + dt);
+    k.cb = 2.0 * dt / (2.0 * tau + dt);
+    k.cp = (2.0 * tau - h) / (2.0 * tau + dt);
+    k.ce = 3.0 * h / (2.0 * tau + dt);
+    k.wb = 2.0 * tau / (2.0 * tau + h);
+    k.we = h / (2.0 * tau + h);
+    k.h_dx = h / c.dx;
+    k.h_dy = h / c.dy;
+    k.dt_dx = dt / c.dx;
+    k.dt_dy = dt / c.dy;
+    k.inv_dx = 1.0 / c.dx;
+    k.inv_dy = 1.0 / c.dy;
+    c.kf = StepC<float>{float(k.ca),   float(k.cb),   float(k.cp),    float(k.ce),    float(k.wb),     float(k.we),
+                        float(k.h_dx), float(k.h_dy), float(k.dt_dx), float(k.dt_dy), float(k.inv_dx), float(k.inv_dy)};
 }
 
 struct Diag {
@@ -73,17 +154,19 @@ struct Params {
     int bc[4];
     long long lo[4], hi[4];
     double inflow[4][4];             // rho, ux, uy, p
+    using W = typename FrameWords<R>::word;
     double gamma, Cv, tau;
+    R Cv_r, Cvh_r, tol_r;             // Cv, Cv - D/2 and tol in the working precision
     int limiter;
     double tol;
     int max_iter, fixed_iters;
     R *sf;                            // [NFS][ncell]
     R *sg;                            // [NGC][ncell]
-    double *sfr;                      // [D+1][ncell]
+    W *sfr;                           // [D+1][ncell]
     R *xf, *xg;                       // [NFC][nxf], [NGC][nxf]
-    double *xfr;                      // [D+1][nxf]
+    W *xfr;                           // [D+1][nxf]
     R *yf, *yg;
-    double *yfr;
+    W *yfr;
     Clock *clock;
     Diag *diag;
     // learned face-gauge predictor: parameters, and sampling of training pairs
@@ -142,13 +225,14 @@ struct StagedCell {
 // Loads cell (i, j) (ghosts resolved) and forms phi-bar-plus = cp phi~ + ce phi^eq with
 // phi^eq the co-moving equilibria (rho, 0, ...) and ((Cv - D/2) rho T, 0, ...).
 template <int D, typename R>
-__device__ __forceinline__ void cell_velocity(const Params<D, R> &P, long long i, long long j, double *u)
+__device__ __forceinline__ void cell_velocity(const Params<D, R> &P, long long i, long long j,
+                                              typename FrameWords<R>::word *u)
 {
     long long idx = 0;
     const int side = resolve(P, i, j, &idx);
     if (side >= 0) {
-        u[0] = P.inflow[side][1];
-        if constexpr (D == 2) u[1] = P.inflow[side][2];
+        fr_store(u[0], P.inflow[side][1]);
+        if constexpr (D == 2) fr_store(u[1], P.inflow[side][2]);
     } else {
 #pragma unroll
         for (int a = 0; a < D; ++a) u[a] = P.sfr[a * P.ncell() + idx];
@@ -157,23 +241,25 @@ __device__ __forceinline__ void cell_velocity(const Params<D, R> &P, long long i
 
 template <int D, typename R>
 __device__ __forceinline__ void load_cell_bar_plus(const Params<D, R> &P, long long i, long long j, R cp, R ce,
-                                                   const double *utile, StagedCell<D, R> &c)
+                                                   const typename FrameWords<R>::word *utile, StagedCell<D, R> &c)
 {
     constexpr int NFC = NCoef<D, 3>::value, NGC = NCoef<D, 2>::value;
+    using W = typename FrameWords<R>::word;
     long long idx = 0;
     const int side = resolve(P, i, j, &idx);
-    double rho, T, u[D];
+    W u[D];
+    R T;
     if (side >= 0) {
-        rho = P.inflow[side][0];
-        T = P.inflow[side][3] / rho;
-        u[0] = P.inflow[side][1];
-        if constexpr (D == 2) u[1] = P.inflow[side][2];
+        const double rho = P.inflow[side][0], Td = P.inflow[side][3] / rho;
+        fr_store(u[0], P.inflow[side][1]);
+        if constexpr (D == 2) fr_store(u[1], P.inflow[side][2]);
 #pragma unroll
         for (int k = 0; k < NFC; ++k) c.A[k] = R(0);
 #pragma unroll
         for (int k = 0; k < NGC; ++k) c.B[k] = R(0);
         c.A[0] = R(rho);
-        c.B[0] = R((P.Cv - 0.5 * D) * rho * T);
+        c.B[0] = R((P.Cv - 0.5 * D) * rho * Td);
+        T = R(Td);
     } else {
         const long long n = P.ncell();
 #pragma unroll
@@ -185,19 +271,18 @@ __device__ __forceinline__ void load_cell_bar_plus(const Params<D, R> &P, long l
         for (int k = 0; k < NGC; ++k) c.B[k] = P.sg[k * n + idx];
 #pragma unroll
         for (int a = 0; a < D; ++a) u[a] = P.sfr[a * n + idx];
-        T = P.sfr[D * n + idx];
-        rho = double(c.A[0]);
+        T = R(fr_lead(P.sfr[D * n + idx]));
     }
 #pragma unroll
-    for (int a = 0; a < D; ++a) c.du[a] = R(u[a] - utile[a]);
+    for (int a = 0; a < D; ++a) c.du[a] = R(fr_rel(u[a], utile[a]));
     const R r = c.A[0];
     c.A[0] = cp * r + ce * r;
 #pragma unroll
     for (int k = 1; k < NFC; ++k) c.A[k] = cp * c.A[k];
-    c.B[0] = cp * c.B[0] + ce * R((P.Cv - 0.5 * D) * rho * T);
+    c.B[0] = cp * c.B[0] + ce * (P.Cvh_r * r * T);
 #pragma unroll
     for (int k = 1; k < NGC; ++k) c.B[k] = cp * c.B[k];
-    c.T = R(T);
+    c.T = T;
 }
 
 // ------------------------------------------------------------------ face corrector
@@ -284,11 +369,13 @@ __device__ __forceinline__ void corrector_pass(const StagedCell<D, R> *const *ce
             // outer normal neighbour of the upwind cell, in the frame
             R FS[NFC], GS[NGC];
             {
-                const int slot = left ? 0 : 3;
+                // slot 0 or 3, chosen by selects so that no array is indexed at run time
+                const StagedCell<D, R> *sc = left ? cells[0] : cells[3];
+                const R dcs[1] = {left ? dc[0][0] : dc[3][0]};
                 Map1<R> X(R(1), R(0), R(0)), Y(R(1), R(0), R(0));
-                cell_maps<D, R>(cells[slot]->T, dc[slot], Tl, invTl, rsqTl, dl, X, Y);
-                shift_scale<D, 3, R>(cells[slot]->A, X, Y, FS);
-                shift_scale<D, 2, R>(cells[slot]->B, X, Y, GS);
+                cell_maps<D, R>(sc->T, dcs, Tl, invTl, rsqTl, dl, X, Y);
+                shift_scale<D, 3, R>(sc->A, X, Y, FS);
+                shift_scale<D, 2, R>(sc->B, X, Y, GS);
             }
             // populations at node m (unweighted: the limiter is homogeneous of degree one,
             // so the weight w_m factors out) of L, R and the outer neighbour
@@ -334,12 +421,18 @@ __device__ __forceinline__ void corrector_pass(const StagedCell<D, R> *const *ce
             R CS[3][4], DS[3][3];
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
-                const int slot = q == 0 ? (left ? 0 : 3) : (q == 1 ? (left ? 4 : 6) : (left ? 5 : 7));
+                // slot (left, right upwind): q = 0 (0, 3), q = 1 (4, 6), q = 2 (5, 7); chosen by
+                // selects so that no array is indexed at run time
+                constexpr int sa[3] = {0, 4, 5}, sb[3] = {3, 6, 7};
+                const StagedCell<D, R> *sc = left ? cells[sa[q]] : cells[sb[q]];
+                R dcs[D];
+#pragma unroll
+                for (int a = 0; a < D; ++a) dcs[a] = left ? dc[sa[q]][a] : dc[sb[q]][a];
                 Map1<R> X(R(1), R(0), R(0)), Y(R(1), R(0), R(0));
                 R tmp[NFC], tmpg[NGC], tr[NFC], trg[NGC];
-                cell_maps<D, R>(cells[slot]->T, dc[slot], Tl, invTl, rsqTl, dl, X, Y);
-                orient<D, 3, R>(cells[slot]->A, tmp, swap);
-                orient<D, 2, R>(cells[slot]->B, tmpg, swap);
+                cell_maps<D, R>(sc->T, dcs, Tl, invTl, rsqTl, dl, X, Y);
+                orient<D, 3, R>(sc->A, tmp, swap);
+                orient<D, 2, R>(sc->B, tmpg, swap);
                 shift_scale<D, 3, R>(tmp, X, Y, tr);
                 shift_scale<D, 2, R>(tmpg, X, Y, trg);
                 collapse_f(tr, CS[q]);
@@ -569,12 +662,14 @@ face_kernel(const Params<D, R> P)
     constexpr int TX = FaceTile<D>::TX, TY = FaceTile<D>::TY;
     constexpr int BX = TX + 3, BY = D == 2 ? TY + 3 : 1;
     constexpr int NFC = NCoef<D, 3>::value, NGC = NCoef<D, 2>::value;
+    using W = typename FrameWords<R>::word;
     __shared__ StagedCell<D, R> tile[BY * BX];
-    __shared__ double utile[D];
+    __shared__ W utile[D];
 
     const Clock &K = *P.clock;
     if (!(K.dt > 0.0)) return;  // t_end reached: the step is a no-op
-    const R cp = R(K.cp), ce = R(K.ce);
+    const StepC<R> &KC = step_c<R>(K);
+    const R cp = KC.cp, ce = KC.ce;
 
     const long long i0 = (long long)blockIdx.x * TX, j0 = (long long)blockIdx.y * TY;
     // reference velocity of the tile: staged velocities are differences from it
@@ -624,32 +719,33 @@ face_kernel(const Params<D, R> P)
         const bool swap = dir == 1;
         R *Fout = dir == 0 ? P.xf : P.yf;
         R *Gout = dir == 0 ? P.xg : P.yg;
-        double *Frm = dir == 0 ? P.xfr : P.yfr;
+        W *Frm = dir == 0 ? P.xfr : P.yfr;
         const long long nf = dir == 0 ? P.nxf() : P.nyf();
-        double uref[D];
+        W uref[D];
 #pragma unroll
         for (int a = 0; a < D; ++a) uref[a] = Frm[a * nf + fidx];
         FaceOut<D, R> o;
         FaceCfg<R> cfg;
-        cfg.h_dn = R(swap ? K.h_dy : K.h_dx);
-        cfg.h_dt = R(D == 2 ? (swap ? K.h_dx : K.h_dy) : 0.0);
-        cfg.Cv = R(P.Cv); cfg.tol = R(P.tol); cfg.wb = R(K.wb); cfg.we = R(K.we);
+        cfg.h_dn = swap ? KC.h_dy : KC.h_dx;
+        cfg.h_dt = D == 2 ? (swap ? KC.h_dx : KC.h_dy) : R(0);
+        cfg.Cv = P.Cv_r; cfg.tol = P.tol_r; cfg.wb = KC.wb; cfg.we = KC.we;
         cfg.limiter = P.limiter; cfg.max_iter = P.max_iter; cfg.fixed_iters = P.fixed_iters;
-        const double Tp = Frm[D * nf + fidx];
+        const W Tpw = Frm[D * nf + fidx];
+        const R Tp = R(fr_lead(Tpw));
         const int na = swap ? 1 : 0, ta = 1 - na;
         R dref[D], uabs[D];
-        dref[0] = R(uref[na] - utile[na]);
-        uabs[0] = R(uref[na]);
+        dref[0] = R(fr_rel(uref[na], utile[na]));
+        uabs[0] = R(fr_lead(uref[na]));
         if constexpr (D == 2) {
-            dref[1] = R(uref[ta] - utile[ta]);
-            uabs[1] = R(uref[ta]);
+            dref[1] = R(fr_rel(uref[ta], utile[ta]));
+            uabs[1] = R(fr_lead(uref[ta]));
         }
-        solve_face<D, R>(cells, swap, dref, uabs, R(Tp), cfg, o);
+        solve_face<D, R>(cells, swap, dref, uabs, Tp, cfg, o);
         my_iters = o.iters; my_nonconv = o.done ? 0 : 1; my_fallbacks = o.fallbacks;
         if constexpr (COLLECT && D == 2) {
             const unsigned long long hsh = (unsigned long long)(fidx * 2 + dir + 1) * 0x9E3779B97F4A7C15ull ^
                                            (unsigned long long)(K.steps + 1) * 0xBF58476D1CE4E5B9ull;
-            if (o.have && o.done && Tp > 0.0 && ((hsh >> 33) % (unsigned long long)P.pair_every) == 0) {
+            if (o.have && o.done && Tp > R(0) && ((hsh >> 33) % (unsigned long long)P.pair_every) == 0) {
                 const float dn = float(dref[0]), dt_ = float(dref[D - 1]);
                 mlp::SlotPrim sp[8];
 #pragma unroll
@@ -663,10 +759,10 @@ face_kernel(const Params<D, R> P)
                     float *row = P.pairs + slot * mlp::kPairStride;
 #pragma unroll
                     for (int q = 0; q < mlp::kIn; ++q) row[q] = f[q];
-                    const double rs = 1.0 / sqrt(Tp);
+                    const double rs = 1.0 / sqrt(double(Tp));
                     row[mlp::kIn + 0] = float(double(o.du[na]) * rs);
                     row[mlp::kIn + 1] = float(double(o.du[ta]) * rs);
-                    row[mlp::kIn + 2] = float(log(double(o.T) / Tp));
+                    row[mlp::kIn + 2] = float(log(double(o.T) / double(Tp)));
                     row[mlp::kIn + 3] = float(o.iters);
                 }
             }
@@ -677,8 +773,8 @@ face_kernel(const Params<D, R> P)
 #pragma unroll
             for (int k = 0; k < NGC; ++k) Gout[k * nf + fidx] = o.G[k];
 #pragma unroll
-            for (int a = 0; a < D; ++a) Frm[a * nf + fidx] = uref[a] + double(o.du[a]);
-            Frm[D * nf + fidx] = double(o.T);
+            for (int a = 0; a < D; ++a) Frm[a * nf + fidx] = fr_add(uref[a], o.du[a]);
+            Frm[D * nf + fidx] = fr_word(o.T);
         } else {
             ++my_nonphys;
             const R nan = R(__longlong_as_double(0x7ff8000000000000ll));
@@ -686,7 +782,7 @@ face_kernel(const Params<D, R> P)
             for (int k = 0; k < NFC; ++k) Fout[k * nf + fidx] = nan;
 #pragma unroll
             for (int k = 0; k < NGC; ++k) Gout[k * nf + fidx] = nan;
-            Frm[D * nf + fidx] = double(nan);
+            fr_store(Frm[D * nf + fidx], double(nan));
         }
     }
     // warp-aggregated diagnostics
@@ -781,22 +877,15 @@ __device__ __forceinline__ void add_face_flux(const R *Fc, const R *Gc, const R 
 template <int D>
 struct CellBlock { static constexpr int THREADS = 256; };
 
-// CFL rate of a cell frame: max over axes of (|u_a| + sqrt(T/T_L) max|c|)/dx_a
+// CFL rate of a cell frame: max over axes of (|u_a| + sqrt(T/T_L) max|c|)/dx_a, in the
+// working precision (FP32 populations: the rate in FP32 is enough)
 template <typename R>
-__device__ __forceinline__ double cell_rate(const double *u, double T, double inv_dx, double inv_dy, int D)
+__device__ __forceinline__ double cell_rate(const R *u, R T, R inv_dx, R inv_dy, int D)
 {
-    // FP64 populations: FP64 time step; FP32 populations: the rate in FP32 is enough
-    if constexpr (sizeof(R) == 8) {
-        const double c = sqrt(T) * kCHi;
-        double r = (fabs(u[0]) + c) * inv_dx;
-        if (D == 2) r = fmax(r, (fabs(u[1]) + c) * inv_dy);
-        return r;
-    } else {
-        const float c = sqrtf(float(T)) * float(kCHi);
-        float r = (fabsf(float(u[0])) + c) * float(inv_dx);
-        if (D == 2) r = fmaxf(r, (fabsf(float(u[1])) + c) * float(inv_dy));
-        return double(r);
-    }
+    const R c = sqrt(T) * R(kCHi);
+    R r = (fabs(u[0]) + c) * inv_dx;
+    if (D == 2) r = max(r, (fabs(u[1]) + c) * inv_dy);
+    return double(r);
 }
 
 // block max of a non-negative double, then the last block turns the grid max into the
@@ -896,15 +985,17 @@ cell_kernel(const Params<D, R> P)
     const long long n = P.ncell();
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double rate = 0.0;
+    using W = typename FrameWords<R>::word;
+    const StepC<R> &KC = step_c<R>(K);
     if (c < n) {
         const long long i = c % P.nx, j = c / P.nx;
-        double uc[D];
+        W uc[D];
 #pragma unroll
         for (int a = 0; a < D; ++a) uc[a] = P.sfr[a * n + c];
-        const double Tc = P.sfr[D * n + c];
+        const W Tc = P.sfr[D * n + c];
         const R rho = P.sf[c];
-        const R ca = R(K.ca), cb = R(K.cb), Cv = R(P.Cv);
-        const R Tcr = R(Tc);
+        const R ca = KC.ca, cb = KC.cb, Cv = P.Cv_r;
+        const R Tcr = R(fr_lead(Tc));
         const R invTc = R(1) / Tcr, rsqTc = sqrt(invTc), sqTc = Tcr * rsqTc;
         // collision part of Eqs. (FinalUpdateDUGKS) in Hermite moments of the cell frame
         R H[NFC], G[NGC];
@@ -919,7 +1010,7 @@ cell_kernel(const Params<D, R> P)
         G[0] += cb * (Cv - R(0.5 * D)) * rho * Tcr;
         // fluxes through the 2D faces
         const long long nxf = P.nxf();
-        const R sx = R(K.dt_dx);
+        const R sx = KC.dt_dx;
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
             const long long f = j * (P.nx + 1) + i + side;
@@ -929,13 +1020,13 @@ cell_kernel(const Params<D, R> P)
 #pragma unroll
             for (int k = 0; k < NGC; ++k) Gc[k] = P.xg[k * nxf + f];
 #pragma unroll
-            for (int a = 0; a < D; ++a) dv[a] = R(P.xfr[a * nxf + f] - uc[a]);  // FP64: frames can move at high Mach
-            const R Tb = R(P.xfr[D * nxf + f]);
-            add_face_flux<D, R>(Fc, Gc, dv, Tb, Tcr, invTc, rsqTc, 0, side ? sx : -sx, sqTc, R(uc[0]), H, G);
+            for (int a = 0; a < D; ++a) dv[a] = R(fr_rel(P.xfr[a * nxf + f], uc[a]));
+            const R Tb = R(fr_lead(P.xfr[D * nxf + f]));
+            add_face_flux<D, R>(Fc, Gc, dv, Tb, Tcr, invTc, rsqTc, 0, side ? sx : -sx, sqTc, R(fr_lead(uc[0])), H, G);
         }
         if constexpr (D == 2) {
             const long long nyf = P.nyf();
-            const R sy = R(K.dt_dy);
+            const R sy = KC.dt_dy;
 #pragma unroll
             for (int side = 0; side < 2; ++side) {
                 const long long f = (j + side) * P.nx + i;
@@ -945,18 +1036,23 @@ cell_kernel(const Params<D, R> P)
 #pragma unroll
                 for (int k = 0; k < NGC; ++k) Gc[k] = P.yg[k * nyf + f];
 #pragma unroll
-                for (int a = 0; a < D; ++a) dv[a] = R(P.yfr[a * nyf + f] - uc[a]);
-                const R Tb = R(P.yfr[D * nyf + f]);
-                add_face_flux<D, R>(Fc, Gc, dv, Tb, Tcr, invTc, rsqTc, 1, side ? sy : -sy, sqTc, R(uc[1]), H, G);
+                for (int a = 0; a < D; ++a) dv[a] = R(fr_rel(P.yfr[a * nyf + f], uc[a]));
+                const R Tb = R(fr_lead(P.yfr[D * nyf + f]));
+                add_face_flux<D, R>(Fc, Gc, dv, Tb, Tcr, invTc, rsqTc, 1, side ? sy : -sy, sqTc, R(fr_lead(uc[1])), H, G);
             }
         }
         R Ho[NFC], Go[NGC], du[D], dT;
         bool ok = cell_finish<D, R>(H, G, invTc, sqTc, Cv, Ho, Go, du, dT);
-        double un[D];
+        W un[D];
+        R unr[D];
 #pragma unroll
-        for (int a = 0; a < D; ++a) un[a] = uc[a] + double(du[a]);
-        const double Tn = Tc + Tc * double(dT);
-        ok = ok && Tn > 0.0 && isfinite(Tn);
+        for (int a = 0; a < D; ++a) {
+            un[a] = fr_add(uc[a], du[a]);
+            unr[a] = R(fr_lead(un[a]));
+        }
+        const W Tn = fr_add(Tc, Tcr * dT);
+        const R Tnr = R(fr_lead(Tn));
+        ok = ok && Tnr > R(0) && isfinite(Tnr);
         if (!ok) {
             atomicOr(&P.diag->flags, FLAG_NONPHYSICAL);
             atomicAdd(&P.diag->nonphys, 1ull);
@@ -972,7 +1068,7 @@ cell_kernel(const Params<D, R> P)
 #pragma unroll
         for (int a = 0; a < D; ++a) P.sfr[a * n + c] = un[a];
         P.sfr[D * n + c] = Tn;
-        rate = ok ? cell_rate<R>(un, Tn, K.inv_dx, K.inv_dy, D) : 0.0;
+        rate = ok ? cell_rate<R>(unr, Tnr, KC.inv_dx, KC.inv_dy, D) : 0.0;
     }
     reduce_rate_and_advance(P.clock, rate, true);
 }
@@ -997,15 +1093,16 @@ __global__ void init_cells_kernel(const Params<D, R> P, const double *rho, const
 #pragma unroll
         for (int k = 1; k < NGC; ++k) P.sg[k * n + c] = R(0);
 #pragma unroll
-        for (int a = 0; a < D; ++a) P.sfr[a * n + c] = u[a];
-        P.sfr[D * n + c] = T;
+        for (int a = 0; a < D; ++a) fr_store(P.sfr[a * n + c], u[a]);
+        fr_store(P.sfr[D * n + c], T);
         const bool ok = r > 0.0 && T > 0.0 && isfinite(r) && isfinite(T);
         if (!ok) {
             atomicOr(&P.diag->flags, FLAG_NONPHYSICAL);
             atomicAdd(&P.diag->nonphys, 1ull);
             atomicCAS((unsigned long long *)&P.diag->first_bad, (unsigned long long)-1ll, (unsigned long long)c);
         }
-        rate = ok ? cell_rate<R>(u, T, 1.0 / P.dx, 1.0 / P.dy, D) : 0.0;
+        const R ur[2] = {R(u[0]), R(u[1])};
+        rate = ok ? cell_rate<R>(ur, R(T), R(1.0 / P.dx), R(1.0 / P.dy), D) : 0.0;
     }
     reduce_rate_and_advance(P.clock, rate, false);
 }
@@ -1026,8 +1123,8 @@ __device__ __forceinline__ void cell_conserved(const Params<D, R> &P, long long 
         const long long n = P.ncell();
         r = double(P.sf[idx]);
 #pragma unroll
-        for (int a = 0; a < D; ++a) u[a] = P.sfr[a * n + idx];
-        T = P.sfr[D * n + idx];
+        for (int a = 0; a < D; ++a) u[a] = fr_value(P.sfr[a * n + idx]);
+        T = fr_value(P.sfr[D * n + idx]);
     }
     double k2 = 0.0;
 #pragma unroll
@@ -1054,11 +1151,11 @@ __global__ void init_faces_kernel(const Params<D, R> P)
     double k2 = 0.0, u[2];
 #pragma unroll
     for (int a = 0; a < D; ++a) { const double m = 0.5 * (ma[a] + mb[a]); u[a] = m / r; k2 += m * m; }
-    double *Frm = xdir ? P.xfr : P.yfr;
+    typename FrameWords<R>::word *Frm = xdir ? P.xfr : P.yfr;
     const long long nf = xdir ? nxf : nyf;
 #pragma unroll
-    for (int a = 0; a < D; ++a) Frm[a * nf + f] = u[a];
-    Frm[D * nf + f] = (E - 0.5 * k2 / r) / (P.Cv * r);
+    for (int a = 0; a < D; ++a) fr_store(Frm[a * nf + f], u[a]);
+    fr_store(Frm[D * nf + f], (E - 0.5 * k2 / r) / (P.Cv * r));
 }
 
 // ------------------------------------------------------- learned gauge predictor
@@ -1108,11 +1205,11 @@ gauge_predict_kernel(const Params<2, R> P)
 #pragma unroll
                 for (int q = 0; q < 8; ++q) { ci[q] = i + di[q]; cj[q] = j + dj[q]; }
             }
-            const double *Frm = dir ? P.yfr : P.xfr;
+            const auto *Frm = dir ? P.yfr : P.xfr;
             const long long nfd = dir ? nyf : nxf;
-            uref[0] = Frm[fidx];
-            uref[1] = Frm[nfd + fidx];
-            Tp = Frm[2 * nfd + fidx];
+            uref[0] = fr_value(Frm[fidx]);
+            uref[1] = fr_value(Frm[nfd + fidx]);
+            Tp = fr_value(Frm[2 * nfd + fidx]);
             const int na = dir, ta = 1 - dir;
             mlp::SlotPrim sp[8];
 #pragma unroll
@@ -1128,13 +1225,13 @@ gauge_predict_kernel(const Params<2, R> P)
                 } else {
                     const long long n = P.ncell();
                     rho = double(P.sf[idx]);
-                    u[0] = P.sfr[idx];
-                    u[1] = P.sfr[n + idx];
-                    T = P.sfr[2 * n + idx];
+                    u[0] = fr_value(P.sfr[idx]);
+                    u[1] = fr_value(P.sfr[n + idx]);
+                    T = fr_value(P.sfr[2 * n + idx]);
                 }
                 sp[q] = {float(rho), float(u[na] - uref[na]), float(u[ta] - uref[ta]), float(T)};
             }
-            mlp::features(sp, float(Tp), float(dir ? K.h_dy : K.h_dx), f);
+            mlp::features(sp, float(Tp), dir ? K.kf.h_dy : K.kf.h_dx, f);
         } else {
 #pragma unroll
             for (int q = 0; q < mlp::kIn; ++q) f[q] = 0.f;
@@ -1152,11 +1249,11 @@ gauge_predict_kernel(const Params<2, R> P)
             double un[2];
             un[na] = uref[na] + sq * double(y0);
             un[ta] = uref[ta] + sq * double(y1);
-            double *Frm = dir ? P.yfr : P.xfr;
+            auto *Frm = dir ? P.yfr : P.xfr;
             const long long nfd = dir ? nyf : nxf;
-            Frm[fidx] = un[0];
-            Frm[nfd + fidx] = un[1];
-            Frm[2 * nfd + fidx] = Tp * double(__expf(y2));
+            fr_store(Frm[fidx], un[0]);
+            fr_store(Frm[nfd + fidx], un[1]);
+            fr_store(Frm[2 * nfd + fidx], Tp * double(__expf(y2)));
         }
     }
     if (!ok && threadIdx.x == 0) atomicOr(P.mlp_err, 1u);
@@ -1202,7 +1299,7 @@ __global__ void export_state_kernel(const Params<D, R> P, double *cf, double *cg
         for (int k = 0; k < NGC; ++k) cg[c * NGC + k] = double(P.sg[k * n + c]);
     if (fr)
 #pragma unroll
-        for (int a = 0; a <= D; ++a) fr[c * (D + 1) + a] = P.sfr[a * n + c];
+        for (int a = 0; a <= D; ++a) fr[c * (D + 1) + a] = fr_value(P.sfr[a * n + c]);
 }
 
 // Compensated (double-double) sums of four fields scaled by vol: per-block partials
