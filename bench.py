@@ -34,7 +34,7 @@ FALLBACK_HBM_GBS = 6800.0
 N_SMS, FP32_LANES = 152, 128
 # FP32 operations (FMA = 2) of one corrector pass at one D2Q16 face (per-face overhead
 # included), from the ncu instruction counts of the face kernel; used for the ALU roofline
-FACE_KERNEL_DRAM_BYTES = 136.7e6 + 178.4e6  # ncu dram read + write of one launch at 1024^2
+FACE_KERNEL_DRAM_BYTES = 137.0e6 + 176.1e6  # ncu dram read + write of one launch at 1024^2
 FLOPS_PER_FACE_PASS = 4550.0
 # algorithmic bytes per cell-update of the FP32 D2Q16 layout: the face kernel reads the
 # cell state (8 + 6 FP32 coefficients + 3 float-float frame words = 80 B) and two face predictors

@@ -187,6 +187,14 @@ pond_status reset_clock(pond_state *s)
 
 unsigned blocks_for(long long n, int threads) { return unsigned((n + threads - 1) / threads); }
 
+// persistent CTAs of the learned predictor: kInferCtasPerSm per SM, at most one per tile
+unsigned predict_blocks(const pond_state *s)
+{
+    const long long nf = (s->grid.nx + 1) * s->grid.ny + s->grid.nx * (s->grid.ny + 1);
+    const long long tiles = (nf + pond::mlp::kRows - 1) / pond::mlp::kRows;
+    return unsigned(std::min<long long>(tiles, (long long)pond::mlp::kInferCtasPerSm * s->sms));
+}
+
 template <int D, typename R>
 pond_status set_primitive_impl(pond_state *s, const double *rho, const double *ux, const double *uy, const double *p, int on_device)
 {
@@ -251,8 +259,8 @@ pond_status mlp_setup(pond_state *s)
     CUDA_TRY(cudaMemcpyAsync(s->mlp, p.data(), 4 * M::kParams, cudaMemcpyHostToDevice, s->stream));
     CUDA_TRY(cudaStreamSynchronize(s->stream));
     CUDA_TRY(cudaFuncSetAttribute(pond::mlp::tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, M::kTileSmem));
-    CUDA_TRY(cudaFuncSetAttribute(pond::gauge_predict_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, M::kTileSmem));
-    CUDA_TRY(cudaFuncSetAttribute(pond::gauge_predict_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, M::kTileSmem));
+    CUDA_TRY(cudaFuncSetAttribute(pond::gauge_predict_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, M::kInferSmem));
+    CUDA_TRY(cudaFuncSetAttribute(pond::gauge_predict_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, M::kInferSmem));
     int sms = 0;
     CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device));
     s->sms = sms;
@@ -267,7 +275,7 @@ void launch_step(pond_state *s, bool collect = false)
     dim3 fg(unsigned((P.nx + 1 + FT::TX - 1) / FT::TX), D == 2 ? unsigned((P.ny + 1 + FT::TY - 1) / FT::TY) : 1u);
     if constexpr (D == 2) {
         if (s->learned) {
-            pond::gauge_predict_kernel<R><<<unsigned(2 * s->sms), pond::mlp::kThreads, pond::mlp::kTileSmem, s->stream>>>(P);
+            pond::gauge_predict_kernel<R><<<predict_blocks(s), pond::mlp::kThreads, pond::mlp::kInferSmem, s->stream>>>(P);
             s->launches += 1;
         }
         if (collect) pond::face_kernel<D, R, true><<<fg, FT::THREADS, 0, s->stream>>>(P);
@@ -322,7 +330,7 @@ pond_status step_timed_impl(pond_state *s, int64_t n_steps, double *ms)
     for (int64_t k = 0; k < n_steps; ++k) {
         if constexpr (D == 2) {
             if (s->learned) {
-                pond::gauge_predict_kernel<R><<<unsigned(2 * s->sms), pond::mlp::kThreads, pond::mlp::kTileSmem, s->stream>>>(P);
+                pond::gauge_predict_kernel<R><<<predict_blocks(s), pond::mlp::kThreads, pond::mlp::kInferSmem, s->stream>>>(P);
                 s->launches += 1;
             }
         }

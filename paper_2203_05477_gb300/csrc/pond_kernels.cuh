@@ -1162,20 +1162,22 @@ __global__ void init_faces_kernel(const Params<D, R> P)
 
 // Before the face corrector of a step: every face's predictor frame is replaced by the
 // learned prediction of its converged frame (features as in mlp::features).  Persistent
-// CTAs stage the network once and loop over tiles of 128 faces.
+// CTAs (mlp::kInferCtasPerSm per SM) stage the network once and loop over tiles of 128
+// faces; the features are formed in FP32 from the frame words.
 template <typename R>
-__global__ void __launch_bounds__(mlp::kThreads)
+__global__ void __launch_bounds__(mlp::kThreads, mlp::kInferCtasPerSm)
 gauge_predict_kernel(const Params<2, R> P)
 {
+    using W = typename FrameWords<R>::word;
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ uint64_t mbar;
     __shared__ uint32_t tmem_base;
     const Clock &K = *P.clock;
     if (!(K.dt > 0.0)) return;
-    const long long nxf = P.nxf(), nyf = P.nyf(), nf = nxf + nyf;
-    if (threadIdx.x < 32) tc::tmem_alloc(&tmem_base, 128);
+    const long long nxf = P.nxf(), nyf = P.nyf(), nf = nxf + nyf, n = P.ncell();
+    if (threadIdx.x < 32) tc::tmem_alloc(&tmem_base, mlp::kInferTmemCols);
     if (threadIdx.x == 0) tc::mbar_init(&mbar, 1);
-    mlp::stage_weights(P.mlp, sm, false);
+    mlp::stage_infer(P.mlp, sm);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
@@ -1187,7 +1189,8 @@ gauge_predict_kernel(const Params<2, R> P)
         const long long t = tile * mlp::kRows + threadIdx.x;
         const bool valid = t < nf;
         float f[mlp::kIn];
-        double uref[2] = {0.0, 0.0}, Tp = 0.0;
+        W uref[2];
+        R Tp = R(0);
         int dir = 0;
         long long fidx = 0;
         if (valid) {
@@ -1196,40 +1199,40 @@ gauge_predict_kernel(const Params<2, R> P)
             long long ci[8], cj[8];
             if (dir == 0) {
                 const long long i = fidx % (P.nx + 1), j = fidx / (P.nx + 1);
-                const long long di[8] = {-2, -1, 0, 1, -1, -1, 0, 0}, dj[8] = {0, 0, 0, 0, -1, 1, -1, 1};
+                const int di[8] = {-2, -1, 0, 1, -1, -1, 0, 0}, dj[8] = {0, 0, 0, 0, -1, 1, -1, 1};
 #pragma unroll
                 for (int q = 0; q < 8; ++q) { ci[q] = i + di[q]; cj[q] = j + dj[q]; }
             } else {
                 const long long i = fidx % P.nx, j = fidx / P.nx;
-                const long long di[8] = {0, 0, 0, 0, -1, 1, -1, 1}, dj[8] = {-2, -1, 0, 1, -1, -1, 0, 0};
+                const int di[8] = {0, 0, 0, 0, -1, 1, -1, 1}, dj[8] = {-2, -1, 0, 1, -1, -1, 0, 0};
 #pragma unroll
                 for (int q = 0; q < 8; ++q) { ci[q] = i + di[q]; cj[q] = j + dj[q]; }
             }
-            const auto *Frm = dir ? P.yfr : P.xfr;
+            const W *Frm = dir ? P.yfr : P.xfr;
             const long long nfd = dir ? nyf : nxf;
-            uref[0] = fr_value(Frm[fidx]);
-            uref[1] = fr_value(Frm[nfd + fidx]);
-            Tp = fr_value(Frm[2 * nfd + fidx]);
+            uref[0] = Frm[fidx];
+            uref[1] = Frm[nfd + fidx];
+            Tp = R(fr_lead(Frm[2 * nfd + fidx]));
             const int na = dir, ta = 1 - dir;
             mlp::SlotPrim sp[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 long long idx = 0;
                 const int side = resolve(P, ci[q], cj[q], &idx);
-                double rho, u[2], T;
+                W u[2];
+                float rho, T;
                 if (side >= 0) {
-                    rho = P.inflow[side][0];
-                    u[0] = P.inflow[side][1];
-                    u[1] = P.inflow[side][2];
-                    T = P.inflow[side][3] / rho;
+                    rho = float(P.inflow[side][0]);
+                    fr_store(u[0], P.inflow[side][1]);
+                    fr_store(u[1], P.inflow[side][2]);
+                    T = float(P.inflow[side][3] / P.inflow[side][0]);
                 } else {
-                    const long long n = P.ncell();
-                    rho = double(P.sf[idx]);
-                    u[0] = fr_value(P.sfr[idx]);
-                    u[1] = fr_value(P.sfr[n + idx]);
-                    T = fr_value(P.sfr[2 * n + idx]);
+                    rho = float(P.sf[idx]);
+                    u[0] = P.sfr[idx];
+                    u[1] = P.sfr[n + idx];
+                    T = float(fr_lead(P.sfr[2 * n + idx]));
                 }
-                sp[q] = {float(rho), float(u[na] - uref[na]), float(u[ta] - uref[ta]), float(T)};
+                sp[q] = {rho, float(fr_rel(u[na], uref[na])), float(fr_rel(u[ta], uref[ta])), T};
             }
             mlp::features(sp, float(Tp), dir ? K.kf.h_dy : K.kf.h_dx, f);
         } else {
@@ -1237,30 +1240,28 @@ gauge_predict_kernel(const Params<2, R> P)
             for (int q = 0; q < mlp::kIn; ++q) f[q] = 0.f;
         }
 #pragma unroll
-        for (int q = 0; q < mlp::kIn; ++q) mlp::put_bf16(sm + mlp::sA1, threadIdx.x, q, mlp::kIn, f[q]);
+        for (int k0 = 0; k0 < mlp::kIn; k0 += 8) mlp::put_bf16x8(sm + mlp::iX, threadIdx.x, k0, mlp::kIn, f + k0);
         float out[mlp::kOutP];
-        ok = mlp::forward_tile(P.mlp, sm, tmem, &mbar, phase, out);
-        if (ok && valid && Tp > 0.0) {
+        ok = mlp::forward_infer(sm, tmem, &mbar, phase, out);
+        if (ok && valid && Tp > R(0)) {
             const int na = dir, ta = 1 - dir;
-            const double sq = sqrt(Tp);
             const float y0 = fminf(fmaxf(out[0], -5.f), 5.f), y1 = fminf(fmaxf(out[1], -5.f), 5.f);
             const float y2 = fminf(fmaxf(out[2], -5.f), 5.f);
             if (fmaxf(fabsf(y0), fmaxf(fabsf(y1), fabsf(y2))) <= P.gauge_gate) continue;
-            double un[2];
-            un[na] = uref[na] + sq * double(y0);
-            un[ta] = uref[ta] + sq * double(y1);
-            auto *Frm = dir ? P.yfr : P.xfr;
+            const R sq = sqrt(Tp);
+            W *Frm = dir ? P.yfr : P.xfr;
             const long long nfd = dir ? nyf : nxf;
-            fr_store(Frm[fidx], un[0]);
-            fr_store(Frm[nfd + fidx], un[1]);
-            fr_store(Frm[2 * nfd + fidx], Tp * double(__expf(y2)));
+            const W un = fr_add(uref[na], sq * R(y0)), ut = fr_add(uref[ta], sq * R(y1));
+            Frm[na * nfd + fidx] = un;
+            Frm[ta * nfd + fidx] = ut;
+            Frm[2 * nfd + fidx] = fr_word(R(Tp * R(__expf(y2))));
         }
     }
     if (!ok && threadIdx.x == 0) atomicOr(P.mlp_err, 1u);
     mlp::drain(&mbar, phase, ok);
     tc::fence_before_sync();
     __syncthreads();
-    if (threadIdx.x < 32) tc::tmem_free(tmem, 128);
+    if (threadIdx.x < 32) tc::tmem_free(tmem, mlp::kInferTmemCols);
 }
 
 // ---------------------------------------------------------------- read-back kernels

@@ -43,6 +43,18 @@ constexpr int sA4 = sA3 + kRows * kHid * 2;     // dOut [128][16]
 constexpr int sA5 = sA4 + kRows * kOutP * 2;    // dZ2  [128][64]
 constexpr int kTileSmem = sA5 + kRows * kHid * 2;
 
+// shared-memory plan of the inference kernel: weights, one input tile, one hidden tile
+// (H1, then H2 over it once the second GEMM has read H1) and the biases in FP32
+constexpr int iW1 = 0;                          // W1 [64][48]
+constexpr int iW2 = iW1 + kHid * kIn * 2;       // W2 [64][64]
+constexpr int iW3 = iW2 + kHid * kHid * 2;      // W3 [16][64]
+constexpr int iX = iW3 + kOutP * kHid * 2;      // X  [128][48]
+constexpr int iH = iX + kRows * kIn * 2;        // H  [128][64]
+constexpr int iBias = iH + kRows * kHid * 2;    // b1 [64], b2 [64], b3 [16]
+constexpr int kInferSmem = iBias + (2 * kHid + kOutP) * 4;
+constexpr int kInferCtasPerSm = 4;              // 4 x 45.6 KB shared memory, 4 x 64 TMEM columns
+constexpr uint32_t kInferTmemCols = 64;
+
 __device__ __forceinline__ void put_bf16(unsigned char *base, uint32_t r, uint32_t k, uint32_t K, float v)
 {
     *reinterpret_cast<__nv_bfloat16 *>(base + tc::kmajor_offset(r, k, K)) = __float2bfloat16_rn(v);
@@ -50,6 +62,34 @@ __device__ __forceinline__ void put_bf16(unsigned char *base, uint32_t r, uint32
 __device__ __forceinline__ float get_bf16(const unsigned char *base, uint32_t r, uint32_t k, uint32_t K)
 {
     return __bfloat162float(*reinterpret_cast<const __nv_bfloat16 *>(base + tc::kmajor_offset(r, k, K)));
+}
+
+// 8 consecutive values k0 .. k0+7 (k0 a multiple of 8) of row r: one 16-byte store, since
+// they form one row of a core matrix
+__device__ __forceinline__ void put_bf16x8(unsigned char *base, uint32_t r, uint32_t k0, uint32_t K, const float *v)
+{
+    uint4 w;
+    uint32_t *u = reinterpret_cast<uint32_t *>(&w);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const __nv_bfloat162 p = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);  // .x (k0 + 2i) at the lower address
+        u[i] = *reinterpret_cast<const uint32_t *>(&p);
+    }
+    *reinterpret_cast<uint4 *>(base + tc::kmajor_offset(r, k0, K)) = w;
+}
+
+// weights and biases of the inference kernel
+__device__ __forceinline__ void stage_infer(const float *prm, unsigned char *sm)
+{
+    for (int e = threadIdx.x; e < kHid * kIn; e += blockDim.x) put_bf16(sm + iW1, e / kIn, e % kIn, kIn, prm[oW1 + e]);
+    for (int e = threadIdx.x; e < kHid * kHid; e += blockDim.x) put_bf16(sm + iW2, e / kHid, e % kHid, kHid, prm[oW2 + e]);
+    for (int e = threadIdx.x; e < kOutP * kHid; e += blockDim.x) put_bf16(sm + iW3, e / kHid, e % kHid, kHid, prm[oW3 + e]);
+    float *bias = reinterpret_cast<float *>(sm + iBias);
+    for (int e = threadIdx.x; e < kHid; e += blockDim.x) {
+        bias[e] = prm[ob1 + e];
+        bias[kHid + e] = prm[ob2 + e];
+        if (e < kOutP) bias[2 * kHid + e] = prm[ob3 + e];
+    }
 }
 
 // stage the weights (B operands) of the forward pass and, for training, of the backward pass
@@ -102,6 +142,31 @@ __device__ __forceinline__ void read_row(uint32_t tmem, uint32_t col, int nchunk
 {
     const uint32_t lane = (threadIdx.x & ~31u) << 16;
     for (int c = 0; c < nchunks; ++c) tc::tmem_ld16(tmem + lane + col + 16u * c, v + 16 * c);
+}
+
+// Forward pass of the 128 rows staged in iX, accumulators in 64 TMEM columns.  out: this
+// thread's row of the output layer (16 values, 3 used).  Returns false on time-out.
+__device__ __forceinline__ bool forward_infer(unsigned char *sm, uint32_t tmem, uint64_t *mbar, uint32_t &phase,
+                                              float *out)
+{
+    const uint32_t r = threadIdx.x;
+    const uint32_t lane = (threadIdx.x & ~31u) << 16;
+    const float *bias = reinterpret_cast<const float *>(sm + iBias);
+    float v[kHid];
+    for (int layer = 0; layer < 2; ++layer) {
+        if (!run_gemm(tmem, sm + (layer ? iH : iX), sm + (layer ? iW2 : iW1), layer ? kHid : kIn, kHid, mbar, phase))
+            return false;
+        tc::tmem_ld64(tmem + lane, v);
+#pragma unroll
+        for (int j = 0; j < kHid; ++j) v[j] = fmaxf(v[j] + bias[layer * kHid + j], 0.f);
+#pragma unroll
+        for (int k0 = 0; k0 < kHid; k0 += 8) put_bf16x8(sm + iH, r, k0, kHid, v + k0);
+    }
+    if (!run_gemm(tmem, sm + iH, sm + iW3, kHid, kOutP, mbar, phase)) return false;
+    tc::tmem_ld16(tmem + lane, out);
+#pragma unroll
+    for (int j = 0; j < kOutP; ++j) out[j] += bias[2 * kHid + j];
+    return true;
 }
 
 // Forward pass of the 128 rows staged in sA1 (weights in sB1..sB3).  out: this thread's
