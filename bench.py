@@ -36,6 +36,7 @@ N_SMS, FP32_LANES = 152, 128
 # included), from the ncu instruction counts of the face kernel; used for the ALU roofline
 FACE_KERNEL_DRAM_BYTES = 137.0e6 + 176.1e6  # ncu dram read + write of one launch at 1024^2
 FLOPS_PER_FACE_PASS = 4550.0
+FACE_TRAFFIC_VARIANT = 0  # the face-kernel variant the ncu traffic figure was taken on
 # algorithmic bytes per cell-update of the FP32 D2Q16 layout: the face kernel reads the
 # cell state (8 + 6 FP32 coefficients + 3 float-float frame words = 80 B) and two face predictors
 # (2 x 24 B) and writes two faces (2 x (16 x 4 + 24) B)
@@ -161,6 +162,9 @@ def bench_tubes(args, n_tubes=4096, seed=0, rank=0):
     rho, ux, p = I.tube_batch_fields(bt)
     s = pond.BatchSolver(bt.lengths, bt.gammas, precision="fp32", tau=1e-5, cfl=0.2, max_iter=16)
     s.set_primitive(rho, ux, None, p)
+    # tuned over the full step count: as tubes stop, the longest tubes set the launch's
+    # length, so a short window from the initial state does not rank the variants right
+    tune = None if args.no_tune else s.autotune(steps=args.tube_steps)
     s.step(max(1, args.warmup))
     d0 = s.sync()
     torch.cuda.synchronize()
@@ -177,7 +181,8 @@ def bench_tubes(args, n_tubes=4096, seed=0, rank=0):
            "ms_per_step": ms / steps, "hbm_gbs": gbs, "bytes_per_cell_update": TUBE_BYTES_PER_CELL,
            "launches": 1, "passes_per_face": (d1["face_iters"] - d0["face_iters"]) / max(1, d1["face_solves"] - d0["face_solves"]),
            "tubes_stopped": int(status.sum()), "cell_updates": updates,
-           "note": "tubes that reach a non-physical state stop and are reported; throughput counts performed updates"}
+           "note": "tubes that reach a non-physical state stop and are reported; throughput counts performed updates",
+           "variant": s.variants()[tune["tube"] if tune else 0], "autotune_ms": tune["ms"] if tune else None}
     s.close()
     return out
 
@@ -224,6 +229,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--tube-steps", type=int, default=100)
+    ap.add_argument("--no-tune", action="store_true", help="skip the kernel-variant autotuner (use the defaults)")
     ap.add_argument("--workload", default="quadrants", choices=["quadrants", "tubes"],
                     help="tubes: only the batched-tube measurement (profiling case)")
     ap.add_argument("--quick", action="store_true",
@@ -265,6 +271,10 @@ def main():
     # ---- headline: FP32 populations, float-float frames
     s = pond.Solver(pb, precision="fp32", tau=1e-5, cfl=0.2, max_iter=16)
     s.set_primitive()
+    # the autotuner times every compiled face/cell variant on this state and restores it
+    tune = None if args.no_tune else s.autotune(steps=3)
+    fv, cv = (tune["face"], tune["cell"]) if tune else (0, 0)
+    variant_names = s.variants()
     s.step(args.warmup)
     d0 = s.sync()
     l0 = s.launch_count()
@@ -296,6 +306,7 @@ def main():
     pin = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (pb.rho, pb.ux, pb.uy, pb.p)]
     outs = [torch.empty(ncell, dtype=torch.float64).pin_memory() for _ in range(4)]
     s2 = pond.Solver(pb, precision="fp32", tau=1e-5, cfl=0.2, max_iter=16)
+    s2.set_variants(fv, cv)
     barrier()
     t0 = time.perf_counter()
     s2.set_primitive(*[a.numpy() for a in pin])
@@ -322,6 +333,7 @@ def main():
         tr.close()
         t_tr = time.perf_counter() - t_tr
         sl = pond.Solver(pb, precision="fp32", tau=1e-5, cfl=0.2, max_iter=16)
+        sl.set_variants(fv, cv)
         sl.set_primitive()
         sl.set_gauge_params(params)
         sl.gauge_enable(True)
@@ -346,6 +358,7 @@ def main():
     # ---- plain FP64 on the same GPU
     s3 = pond.Solver(pb, precision="fp64", tau=1e-5, cfl=0.2, max_iter=16)
     s3.set_primitive()
+    tune64 = None if args.no_tune else s3.autotune(steps=2)
     s3.step(2)
     barrier()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -378,9 +391,14 @@ def main():
                        (ncell * (80 + 2 * 88)) / 1e6), "parallelism": "replicas" if world > 1 else "single"},
         "fp64": {"value": fp64_value, "unit": "MLUPS", "steps": args.fp64_steps, "speedup_fp32": value / fp64_value},
         "fp32_learned": learned,
+        "autotune": None if tune is None else {
+            "face": variant_names[fv], "cell": variant_names[len(variant_names) - 3 + cv],
+            "ms_per_launch": tune["ms"],
+            "fp64": None if tune64 is None else {"face": tune64["face"], "cell": tune64["cell"]}},
         "corrector": {"passes_per_face": face_passes / max(faces, 1), "status_ok": status_ok},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp32_peak, "traffic": FACE_KERNEL_DRAM_BYTES, "kernel": "face_kernel<2,float>",
+                     "frac": achieved / fp32_peak, "traffic": FACE_KERNEL_DRAM_BYTES if fv == FACE_TRAFFIC_VARIANT else None,
+                     "kernel": "face_kernel<2,float> (%s)" % variant_names[fv],
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % sm_mhz,
                      "face_ms": face_ms_avg, "cell_ms": ms_cell / args.steps,
                      "hbm_gbs": face_gbs, "hbm_frac": face_gbs / hbm_peak,

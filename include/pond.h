@@ -229,6 +229,37 @@ pond_status pond_mlp_gradient(const float *params, const float *x, int ldx, cons
 pond_status pond_mlp_gradient_noalloc(const float *params, const float *x, int ldx, const float *y, int ldy, int64_t n,
                                       float *grad, float *loss, void *stream);
 
+/* ---- Kernel-variant autotuning.  Not part of the paper.  Each step kernel is compiled in
+   several variants: tile shapes and CTAs per SM of the face corrector, block sizes of the
+   cell update, thread counts of the persistent tube kernel.  pond_autotune times every
+   variant on this state's own current data (steps timed steps each, after one untimed
+   step) and keeps the fastest face and cell (or tube) variant for the following steps.
+   The state is copied aside first (one extra device allocation of the state's size, freed
+   before returning) and restored afterwards, so tuning leaves the solution unchanged.
+   cache_path (may be NULL) names a text file of "key<TAB>face cell tube" lines; a line
+   whose key (device name and SM count, problem kind, precision, size, learned flag)
+   matches this state is used without timing, and a new choice is appended.  File errors
+   only disable the cache.  Call it outside stream capture.  Errors: INVALID_ARG
+   (steps < 1), OOM, CUDA. */
+#define POND_TUNE_MAX 16
+typedef struct {
+    int n;                    /* entries of ms filled (0 when taken from the cache) */
+    int face, cell, tube;     /* chosen variant indices */
+    int from_cache;           /* 1: the choice came from cache_path */
+    double ms[POND_TUNE_MAX]; /* mean ms per launch, in pond_variant_name order */
+} pond_tune_result;
+pond_status pond_autotune(pond_state *s, int steps, const char *cache_path, pond_tune_result *out);
+
+/* Number of variants of this state and the name of variant i: for a grid, the face
+   variants first, then the cell variants; for a batch, the tube variants.  The name points
+   to a thread-local buffer ("" when i is out of range). */
+int pond_variant_count(const pond_state *s);
+const char *pond_variant_name(const pond_state *s, int i);
+
+/* Selects variants by index (face, cell for a grid; tube for a batch; the others are
+   ignored).  Errors: INVALID_ARG for an index out of range. */
+pond_status pond_set_variants(pond_state *s, int face, int cell, int tube);
+
 /* Waits for the stream and reports the device diagnostics.  Returns
  * POND_ERR_NONPHYSICAL if any cell or face was non-physical, POND_ERR_NOT_CONVERGED if
  * strict_convergence is set and a face stopped at max_iter, else POND_OK. */

@@ -57,6 +57,14 @@ class pond_diag(ctypes.Structure):
                 ("flags", ctypes.c_uint32)]
 
 
+POND_TUNE_MAX = 16
+
+
+class pond_tune_result(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("face", ctypes.c_int), ("cell", ctypes.c_int), ("tube", ctypes.c_int),
+                ("from_cache", ctypes.c_int), ("ms", ctypes.c_double * POND_TUNE_MAX)]
+
+
 class PondError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__("pond status %d: %s" % (status, msg))
@@ -103,6 +111,10 @@ def _load():
             "pond_gauge_load": (ctypes.c_int, [vp, vp, ctypes.c_size_t]),
             "pond_mlp_forward": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int64, vp, vp]),
             "pond_mlp_gradient": (ctypes.c_int, [vp, vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int64, vp, vp, vp]),
+            "pond_autotune": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_char_p, ctypes.POINTER(pond_tune_result)]),
+            "pond_variant_count": (ctypes.c_int, [vp]),
+            "pond_variant_name": (ctypes.c_char_p, [vp, ctypes.c_int]),
+            "pond_set_variants": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
             "pond_destroy": (None, [vp]),
             "pond_last_error": (ctypes.c_char_p, []),
         }
@@ -290,6 +302,24 @@ class Solver:
 
     def launch_count(self):
         return int(self.lib.pond_launch_count(self.h))
+
+    # ---- kernel-variant autotuning
+    def variants(self):
+        """Names of the compiled kernel variants (face then cell variants; tube variants for a batch)."""
+        return [self.lib.pond_variant_name(self.h, i).decode() for i in range(self.lib.pond_variant_count(self.h))]
+
+    def autotune(self, steps=3, cache=None):
+        """Times every variant on the current state (restored afterwards) and keeps the fastest;
+        returns the choice and the per-variant mean ms per launch."""
+        r = pond_tune_result()
+        path = None if cache is None else os.fsencode(cache)
+        _check(self.lib.pond_autotune(self.h, int(steps), path, ctypes.byref(r)))
+        names = self.variants()
+        return {"face": r.face, "cell": r.cell, "tube": r.tube, "from_cache": bool(r.from_cache),
+                "ms": {names[i]: r.ms[i] for i in range(r.n)}}
+
+    def set_variants(self, face=0, cell=0, tube=0):
+        _check(self.lib.pond_set_variants(self.h, int(face), int(cell), int(tube)))
 
     # ---- learned face-gauge predictor (D2Q16)
     def gauge_collect(self, n_steps, cap, every=4):

@@ -15,9 +15,12 @@
 #include <new>
 #include <vector>
 #include <mutex>
+#include <string>
 
 #include "../../include/pond.h"
-#include "pond_batch.cuh"
+#include "pond_launch.cuh"
+#include "pond_mlp_train.cuh"
+#include "pond_reduce.cuh"
 #include <cuda_bf16.h>
 
 namespace {
@@ -74,6 +77,8 @@ struct pond_state {
     bool learned = false;
     int adam_t = 0;
     int sms = 152;
+    // kernel variants in use (indices into the lists of pond_launch.cuh), set by the autotuner
+    int face_v = 0, cell_v = 0, tube_v = 0;
     // batched tubes
     bool batch = false;
     int64_t n_tubes = 0, ncell = 0, nface = 0, steps_taken = 0;
@@ -271,19 +276,14 @@ template <int D, typename R>
 void launch_step(pond_state *s, bool collect = false)
 {
     auto &P = params_of<D, R>(s);
-    using FT = pond::FaceTile<D>;
-    dim3 fg(unsigned((P.nx + 1 + FT::TX - 1) / FT::TX), D == 2 ? unsigned((P.ny + 1 + FT::TY - 1) / FT::TY) : 1u);
     if constexpr (D == 2) {
         if (s->learned) {
             pond::gauge_predict_kernel<R><<<predict_blocks(s), pond::mlp::kThreads, pond::mlp::kInferSmem, s->stream>>>(P);
             s->launches += 1;
         }
-        if (collect) pond::face_kernel<D, R, true><<<fg, FT::THREADS, 0, s->stream>>>(P);
-        else pond::face_kernel<D, R><<<fg, FT::THREADS, 0, s->stream>>>(P);
-    } else {
-        pond::face_kernel<D, R><<<fg, FT::THREADS, 0, s->stream>>>(P);
     }
-    pond::cell_kernel<D, R><<<blocks_for(P.ncell(), pond::CellBlock<D>::THREADS), pond::CellBlock<D>::THREADS, 0, s->stream>>>(P);
+    pond::launch_face<D, R>(s->face_v, D == 2 && collect, P, s->stream);
+    pond::launch_cell<D, R>(s->cell_v, P, s->stream);
 }
 
 template <int D, typename R>
@@ -321,9 +321,6 @@ template <int D, typename R>
 pond_status step_timed_impl(pond_state *s, int64_t n_steps, double *ms)
 {
     auto &P = params_of<D, R>(s);
-    using FT = pond::FaceTile<D>;
-    dim3 fg(unsigned((P.nx + 1 + FT::TX - 1) / FT::TX), D == 2 ? unsigned((P.ny + 1 + FT::TY - 1) / FT::TY) : 1u);
-    const unsigned cb = blocks_for(P.ncell(), pond::CellBlock<D>::THREADS);
     std::vector<cudaEvent_t> ev(size_t(2 * n_steps + 1));
     for (auto &e : ev) CUDA_TRY(cudaEventCreate(&e));
     CUDA_TRY(cudaEventRecord(ev[0], s->stream));
@@ -334,9 +331,9 @@ pond_status step_timed_impl(pond_state *s, int64_t n_steps, double *ms)
                 s->launches += 1;
             }
         }
-        pond::face_kernel<D, R><<<fg, FT::THREADS, 0, s->stream>>>(P);
+        pond::launch_face<D, R>(s->face_v, false, P, s->stream);
         CUDA_TRY(cudaEventRecord(ev[2 * k + 1], s->stream));
-        pond::cell_kernel<D, R><<<cb, pond::CellBlock<D>::THREADS, 0, s->stream>>>(P);
+        pond::launch_cell<D, R>(s->cell_v, P, s->stream);
         CUDA_TRY(cudaEventRecord(ev[2 * k + 2], s->stream));
     }
     s->launches += 2 * n_steps;
@@ -569,7 +566,7 @@ pond_status batch_step(pond_state *s, int64_t n_steps, double *ms)
         CUDA_TRY(cudaEventCreate(&e1));
         CUDA_TRY(cudaEventRecord(e0, s->stream));
     }
-    pond::tube_kernel<R><<<unsigned(s->n_tubes), pond::kTubeThreads, 0, s->stream>>>(P, int(n_steps), s->cur);
+    pond::launch_tube<R>(s->tube_v, unsigned(s->n_tubes), P, int(n_steps), s->cur, s->stream);
     s->launches += 1;
     CUDA_TRY(cudaGetLastError());
     s->cur ^= int(n_steps & 1);
@@ -1196,6 +1193,259 @@ pond_status pond_mlp_gradient_noalloc(const float *params, const float *x, int l
     CUDA_TRY(cudaMemcpyAsync(&e, err, sizeof(e), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
     if (e) return fail(POND_ERR_TIMEOUT, "a tensor-core wait timed out");
+    return POND_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ autotuner
+//
+// Each step kernel exists in several compiled variants (pond_launch.cuh).  The tuner times
+// them on the state's own data: the device block is copied aside, every variant runs from
+// that copy (so all see the same state and the same corrector work), and the copy is put
+// back at the end, so tuning leaves the solution untouched.  The face variants are timed
+// with the cell kernel fixed, then the cell variants with the chosen face kernel.  Choices
+// can be kept in a cache file of lines "key<TAB>face cell tube", the key naming the device,
+// the problem kind and its size.
+
+namespace {
+
+void drop_graph(pond_state *s)
+{
+    if (s->graph_exec) cudaGraphExecDestroy(s->graph_exec);
+    if (s->graph) cudaGraphDestroy(s->graph);
+    s->graph_exec = nullptr;
+    s->graph = nullptr;
+}
+
+std::string tune_key(const pond_state *s)
+{
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, s->device);
+    char buf[512];
+    if (s->batch)
+        std::snprintf(buf, sizeof(buf), "%s|sm%d|tubes|%s|%lld|%lld", prop.name, prop.multiProcessorCount,
+                      s->prec == POND_FP32 ? "fp32" : "fp64", (long long)s->n_tubes, (long long)s->ncell);
+    else
+        std::snprintf(buf, sizeof(buf), "%s|sm%d|D%d|%s|%lldx%lld|learned%d", prop.name, prop.multiProcessorCount, s->D,
+                      s->prec == POND_FP32 ? "fp32" : "fp64", (long long)s->grid.nx, (long long)s->grid.ny,
+                      s->learned ? 1 : 0);
+    for (char *c = buf; *c; ++c)
+        if (*c == '\t' || *c == '\n') *c = ' ';
+    return buf;
+}
+
+// the last entry for key in the cache file; false if there is none
+bool cache_lookup(const char *path, const std::string &key, int v[3])
+{
+    FILE *f = path ? std::fopen(path, "r") : nullptr;
+    if (!f) return false;
+    bool found = false;
+    char line[1024];
+    while (std::fgets(line, sizeof(line), f)) {
+        char *tab = std::strchr(line, '\t');
+        if (!tab) continue;
+        *tab = '\0';
+        int a = 0, b = 0, c = 0;
+        if (key == line && std::sscanf(tab + 1, "%d %d %d", &a, &b, &c) == 3) {
+            v[0] = a; v[1] = b; v[2] = c;
+            found = true;
+        }
+    }
+    std::fclose(f);
+    return found;
+}
+
+void cache_store(const char *path, const std::string &key, const int v[3])
+{
+    FILE *f = path ? std::fopen(path, "a") : nullptr;
+    if (!f) return;
+    std::fprintf(f, "%s\t%d %d %d\n", key.c_str(), v[0], v[1], v[2]);
+    std::fclose(f);
+}
+
+int variant_total(const pond_state *s)
+{
+    if (s->batch) return s->prec == POND_FP32 ? pond::tube_variants<float>() : pond::tube_variants<double>();
+    int nf = 0;
+    if (s->D == 2) nf = s->prec == POND_FP32 ? pond::face_variants<2, float>() : pond::face_variants<2, double>();
+    else nf = s->prec == POND_FP32 ? pond::face_variants<1, float>() : pond::face_variants<1, double>();
+    return nf + pond::kCellVariants;
+}
+
+// mean ms per launch of the face (which = 0) or cell (which = 1) kernel over `steps` steps
+// after one untimed step, starting from the saved block
+template <int D, typename R>
+pond_status time_grid_variant(pond_state *s, const char *saved, int steps, int which, double *ms)
+{
+    auto &P = params_of<D, R>(s);
+    CUDA_TRY(cudaMemcpyAsync(s->base, saved, s->bytes, cudaMemcpyDeviceToDevice, s->stream));
+    launch_step<D, R>(s);
+    std::vector<cudaEvent_t> ev(size_t(2 * steps));
+    for (auto &e : ev) CUDA_TRY(cudaEventCreate(&e));
+    for (int k = 0; k < steps; ++k) {
+        if constexpr (D == 2) {
+            if (s->learned)
+                pond::gauge_predict_kernel<R><<<predict_blocks(s), pond::mlp::kThreads, pond::mlp::kInferSmem, s->stream>>>(P);
+        }
+        if (which == 0) CUDA_TRY(cudaEventRecord(ev[2 * k], s->stream));
+        pond::launch_face<D, R>(s->face_v, false, P, s->stream);
+        if (which == 0) CUDA_TRY(cudaEventRecord(ev[2 * k + 1], s->stream));
+        if (which == 1) CUDA_TRY(cudaEventRecord(ev[2 * k], s->stream));
+        pond::launch_cell<D, R>(s->cell_v, P, s->stream);
+        if (which == 1) CUDA_TRY(cudaEventRecord(ev[2 * k + 1], s->stream));
+    }
+    s->launches += int64_t(steps + 1) * (2 + ((D == 2 && s->learned) ? 1 : 0));
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaEventSynchronize(ev.back()));
+    double sum = 0.0;
+    for (int k = 0; k < steps; ++k) {
+        float a = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&a, ev[2 * k], ev[2 * k + 1]));
+        sum += a;
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    *ms = sum / steps;
+    return POND_OK;
+}
+
+template <int D, typename R>
+pond_status tune_grid(pond_state *s, const char *saved, int steps, pond_tune_result *res)
+{
+    const int nf = pond::face_variants<D, R>();
+    double best = 0.0;
+    int bf = 0;
+    for (int v = 0; v < nf; ++v) {
+        s->face_v = v;
+        double ms = 0.0;
+        if (pond_status st = time_grid_variant<D, R>(s, saved, steps, 0, &ms)) return st;
+        if (res && res->n < POND_TUNE_MAX) res->ms[res->n++] = ms;
+        if (v == 0 || ms < best) { best = ms; bf = v; }
+    }
+    s->face_v = bf;
+    int bc = 0;
+    for (int v = 0; v < pond::kCellVariants; ++v) {
+        s->cell_v = v;
+        double ms = 0.0;
+        if (pond_status st = time_grid_variant<D, R>(s, saved, steps, 1, &ms)) return st;
+        if (res && res->n < POND_TUNE_MAX) res->ms[res->n++] = ms;
+        if (v == 0 || ms < best) { best = ms; bc = v; }
+    }
+    s->cell_v = bc;
+    return POND_OK;
+}
+
+template <typename R>
+pond_status tune_batch(pond_state *s, const char *saved, int steps, pond_tune_result *res)
+{
+    auto &P = tparams_of<R>(s);
+    const int nv = pond::tube_variants<R>();
+    double best = 0.0;
+    int bv = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    for (int v = 0; v < nv; ++v) {
+        CUDA_TRY(cudaMemcpyAsync(s->base, saved, s->bytes, cudaMemcpyDeviceToDevice, s->stream));
+        CUDA_TRY(cudaEventRecord(e0, s->stream));
+        pond::launch_tube<R>(v, unsigned(s->n_tubes), P, steps, s->cur, s->stream);
+        CUDA_TRY(cudaEventRecord(e1, s->stream));
+        s->launches += 1;
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(cudaEventSynchronize(e1));
+        float a = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&a, e0, e1));
+        if (res && res->n < POND_TUNE_MAX) res->ms[res->n++] = a / steps;
+        if (v == 0 || a < best) { best = a; bv = v; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    s->tube_v = bv;
+    return POND_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pond_status pond_autotune(pond_state *s, int steps, const char *cache_path, pond_tune_result *out)
+{
+    if (pond_status st = check_state(s)) return st;
+    if (steps < 1) return fail(POND_ERR_INVALID_ARG, "steps must be at least 1");
+    pond_tune_result res{};
+    const std::string key = tune_key(s);
+    int v[3] = {0, 0, 0};
+    if (cache_lookup(cache_path, key, v) && pond_set_variants(s, v[0], v[1], v[2]) == POND_OK) {
+        res.from_cache = 1;
+    } else {
+        CUDA_TRY(cudaStreamSynchronize(s->stream));
+        char *saved = static_cast<char *>(dev_alloc(s, s->bytes));
+        if (!saved) return fail(POND_ERR_OOM, "device allocation of %zu bytes for the tuning copy failed", s->bytes);
+        pond_status st = POND_OK;
+        if (cudaMemcpyAsync(saved, s->base, s->bytes, cudaMemcpyDeviceToDevice, s->stream) != cudaSuccess)
+            st = fail(POND_ERR_CUDA, "saving the state for tuning failed");
+        if (st == POND_OK) {
+            if (s->batch) st = dispatch_batch(s, [&](auto r) { return tune_batch<decltype(r)>(s, saved, steps, &res); });
+            else st = dispatch(s, [&](auto d, auto r) { return tune_grid<decltype(d)::value, decltype(r)>(s, saved, steps, &res); });
+        }
+        // put the state back whatever happened, then release the copy
+        const cudaError_t e1 = cudaMemcpyAsync(s->base, saved, s->bytes, cudaMemcpyDeviceToDevice, s->stream);
+        const cudaError_t e2 = cudaStreamSynchronize(s->stream);
+        dev_free(s, saved);
+        if (st != POND_OK) return st;
+        if (e1 != cudaSuccess || e2 != cudaSuccess) return fail(POND_ERR_CUDA, "restoring the state after tuning failed");
+        v[0] = s->face_v; v[1] = s->cell_v; v[2] = s->tube_v;
+        cache_store(cache_path, key, v);
+    }
+    drop_graph(s);
+    res.face = s->face_v;
+    res.cell = s->cell_v;
+    res.tube = s->tube_v;
+    if (out) *out = res;
+    return POND_OK;
+}
+
+int pond_variant_count(const pond_state *s) { return s ? variant_total(s) : 0; }
+
+const char *pond_variant_name(const pond_state *s, int i)
+{
+    thread_local char buf[128];
+    buf[0] = '\0';
+    if (!s || i < 0 || i >= variant_total(s)) return buf;
+    const bool f32 = s->prec == POND_FP32;
+    if (s->batch) {
+        if (f32) pond::tube_name<float>(i, buf, sizeof(buf));
+        else pond::tube_name<double>(i, buf, sizeof(buf));
+        return buf;
+    }
+    const int nf = variant_total(s) - pond::kCellVariants;
+    if (i >= nf) {
+        pond::cell_name(i - nf, buf, sizeof(buf));
+    } else if (s->D == 2) {
+        if (f32) pond::FaceNames<2, float, pond::FaceList<2, float>::type>::name(i, buf, sizeof(buf));
+        else pond::FaceNames<2, double, pond::FaceList<2, double>::type>::name(i, buf, sizeof(buf));
+    } else {
+        if (f32) pond::FaceNames<1, float, pond::FaceList<1, float>::type>::name(i, buf, sizeof(buf));
+        else pond::FaceNames<1, double, pond::FaceList<1, double>::type>::name(i, buf, sizeof(buf));
+    }
+    return buf;
+}
+
+pond_status pond_set_variants(pond_state *s, int face, int cell, int tube)
+{
+    if (pond_status st = check_state(s)) return st;
+    if (s->batch) {
+        const int nv = s->prec == POND_FP32 ? pond::tube_variants<float>() : pond::tube_variants<double>();
+        if (tube < 0 || tube >= nv) return fail(POND_ERR_INVALID_ARG, "tube variant %d out of range", tube);
+        s->tube_v = tube;
+    } else {
+        const int nf = variant_total(s) - pond::kCellVariants;
+        if (face < 0 || face >= nf || cell < 0 || cell >= pond::kCellVariants)
+            return fail(POND_ERR_INVALID_ARG, "face/cell variant (%d, %d) out of range", face, cell);
+        s->face_v = face;
+        s->cell_v = cell;
+    }
+    drop_graph(s);
     return POND_OK;
 }
 

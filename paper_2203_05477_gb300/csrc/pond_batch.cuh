@@ -3,7 +3,7 @@
 // Each CTA owns one tube for the whole run and loops over the time steps itself: the
 // tube's time step comes from its own CFL maximum (a CTA reduction), so tubes never wait
 // on one another and no inter-CTA synchronization exists.  Per step the tube is streamed
-// in chunks of kChunk cells: the chunk and a halo of two cells are staged in shared memory
+// in chunks of THREADS - 1 cells: the chunk and a halo of two cells are staged in shared memory
 // (phi-bar-plus, Eq. Fbarplus), the face corrector (Sec. III.B.3) writes the face
 // populations to shared memory, and the cell update (Eqs. fluxEq, FinalUpdateDUGKS, with
 // the re-expression in the new co-moving frame) writes the new state into the other of two
@@ -21,8 +21,7 @@
 
 namespace pond {
 
-constexpr int kTubeThreads = 256;
-constexpr int kChunk = kTubeThreads - 1;  // kChunk + 1 faces: one per thread
+constexpr int kTubeThreads = 256;  // CTA size of the per-tube set-up and read-back kernels
 
 template <typename R>
 struct TubeParams {
@@ -77,10 +76,13 @@ struct TubeStep {
     R cp, ce, wb, we, ca, cb, h_dx, dt_dx, inv_dx;
 };
 
-template <typename R>
-__global__ void __launch_bounds__(kTubeThreads, sizeof(R) == 4 ? 3 : 1)
+// THREADS threads per tube, chunks of THREADS - 1 cells (THREADS faces: one per thread),
+// MINB CTAs per SM for the register budget; the autotuner picks the variant
+template <typename R, int THREADS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB)
 tube_kernel(const TubeParams<R> P, int steps, int cur0)
 {
+    constexpr int kChunk = THREADS - 1;
     __shared__ StagedCell<1, R> tile[kChunk + 4];
     using CellW = typename FrameWords<R>::word;
     __shared__ R faceF[kChunk + 1][4];
@@ -88,7 +90,7 @@ tube_kernel(const TubeParams<R> P, int steps, int cur0)
     __shared__ R faceU[kChunk + 1], faceT[kChunk + 1];  // face frame: velocity relative to utile, T
     __shared__ TubeStep<R> ks;
     __shared__ CellW uref_s;
-    __shared__ R red[kTubeThreads / 32];
+    __shared__ R red[THREADS / 32];
     __shared__ int tube_bad;
 
     const int tube = P.order[blockIdx.x];
@@ -240,7 +242,7 @@ tube_kernel(const TubeParams<R> P, int steps, int cur0)
         __syncthreads();
         if (threadIdx.x == 0) {
             R rm = R(0);
-            for (int w = 0; w < kTubeThreads / 32; ++w) rm = max(rm, red[w]);
+            for (int w = 0; w < THREADS / 32; ++w) rm = max(rm, red[w]);
             P.t[tube] += ks.dt;
             P.dt[tube] = P.cfl / double(rm);
             P.steps_done[tube] += 1;

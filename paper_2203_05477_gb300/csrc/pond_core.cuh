@@ -58,8 +58,8 @@ struct NodeTab {
       {T(node_w(1) * he(0, 1)), T(node_w(1) * he(1, 1)), T(node_w(1) * he(2, 1)), T(node_w(1) * he(3, 1))}, \
       {T(node_w(2) * he(0, 2)), T(node_w(2) * he(1, 2)), T(node_w(2) * he(2, 2)), T(node_w(2) * he(3, 2))}, \
       {T(node_w(3) * he(0, 3)), T(node_w(3) * he(1, 3)), T(node_w(3) * he(2, 3)), T(node_w(3) * he(3, 3))}}}
-__constant__ NodeTab<float> kTabF = POND_NODE_TAB(float);
-__constant__ NodeTab<double> kTabD = POND_NODE_TAB(double);
+static __constant__ NodeTab<float> kTabF = POND_NODE_TAB(float);
+static __constant__ NodeTab<double> kTabD = POND_NODE_TAB(double);
 template <typename R> __device__ __forceinline__ const NodeTab<R> &node_tab();
 template <> __device__ __forceinline__ const NodeTab<float> &node_tab<float>() { return kTabF; }
 template <> __device__ __forceinline__ const NodeTab<double> &node_tab<double>() { return kTabD; }

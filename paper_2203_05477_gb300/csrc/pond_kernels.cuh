@@ -287,12 +287,6 @@ __device__ __forceinline__ void load_cell_bar_plus(const Params<D, R> &P, long l
 
 // ------------------------------------------------------------------ face corrector
 
-template <int D>
-struct FaceTile;
-template <>
-struct FaceTile<1> { static constexpr int TX = 128, TY = 1, THREADS = 128; };
-template <>
-struct FaceTile<2> { static constexpr int TX = 32, TY = 4, THREADS = 256; };
 
 // transposes coefficient arrays so that index r always refers to the face normal
 template <int D, int N, typename R>
@@ -650,16 +644,22 @@ __device__ __forceinline__ void solve_face(const StagedCell<D, R> *const *cells,
     }
 }
 
-#ifndef POND_FACE_MIN_BLOCKS
-#define POND_FACE_MIN_BLOCKS 2
-#endif
+// Tile variants of the face kernel: TX x TY cells per CTA (one thread per x face and one
+// per y face in 2D, one per face in 1D) and MINB CTAs per SM for the register budget.  The
+// autotuner picks one per problem.
+template <int D, int TX_, int TY_, int MINB_>
+struct FaceVariant {
+    static constexpr int TX = TX_, TY = D == 2 ? TY_ : 1, MINB = MINB_;
+    static constexpr int THREADS = D == 2 ? 2 * TX_ * TY_ : TX_;
+};
+
 // COLLECT: also write (features, converged frame) pairs of sampled converged faces for the
 // learned predictor (a separate instantiation, so the plain kernel carries none of it)
-template <int D, typename R, bool COLLECT = false>
-__global__ void __launch_bounds__(FaceTile<D>::THREADS, (D == 2 && sizeof(R) == 4) ? POND_FACE_MIN_BLOCKS : 1)
+template <int D, typename R, bool COLLECT, typename V>
+__global__ void __launch_bounds__(V::THREADS, V::MINB)
 face_kernel(const Params<D, R> P)
 {
-    constexpr int TX = FaceTile<D>::TX, TY = FaceTile<D>::TY;
+    constexpr int TX = V::TX, TY = V::TY;
     constexpr int BX = TX + 3, BY = D == 2 ? TY + 3 : 1;
     constexpr int NFC = NCoef<D, 3>::value, NGC = NCoef<D, 2>::value;
     using W = typename FrameWords<R>::word;
@@ -874,8 +874,6 @@ __device__ __forceinline__ void add_face_flux(const R *Fc, const R *Gc, const R 
     }
 }
 
-template <int D>
-struct CellBlock { static constexpr int THREADS = 256; };
 
 // CFL rate of a cell frame: max over axes of (|u_a| + sqrt(T/T_L) max|c|)/dx_a, in the
 // working precision (FP32 populations: the rate in FP32 is enough)
@@ -972,11 +970,11 @@ __device__ __forceinline__ bool cell_finish(const R *H, const R *G, R invTc, R s
 
 // Step 3 of Sec. III.B.4 (flux into the cell frame, Eq. fluxEq; update, Eqs.
 // FinalUpdateDUGKS) fused with step 1 of the next step (re-expression in the new co-moving
-// frame from the conserved moments) and the CFL reduction.  The frame (u, T) is held and
-// advanced in FP64 (u' = u + du, T' = T (1 + dT/T)); its increments are formed from the
-// Hermite moments relative to the old frame, so no kinetic energy of the frame enters.
-template <int D, typename R>
-__global__ void __launch_bounds__(CellBlock<D>::THREADS)
+// frame from the conserved moments) and the CFL reduction.  The frame (u, T) advances by
+// increments formed from the Hermite moments relative to the old frame (u' = u + du,
+// T' = T (1 + dT/T)), so no kinetic energy of the frame enters.
+template <int D, typename R, int THREADS>
+__global__ void __launch_bounds__(THREADS)
 cell_kernel(const Params<D, R> P)
 {
     constexpr int NFC = NCoef<D, 3>::value, NGC = NCoef<D, 2>::value;
@@ -1301,62 +1299,6 @@ __global__ void export_state_kernel(const Params<D, R> P, double *cf, double *cg
     if (fr)
 #pragma unroll
         for (int a = 0; a <= D; ++a) fr[c * (D + 1) + a] = fr_value(P.sfr[a * n + c]);
-}
-
-// Compensated (double-double) sums of four fields scaled by vol: per-block partials
-// (hi, lo) into part[block][8]; a single block then folds the partials into out[4].
-__device__ __forceinline__ void two_sum(double a, double b, double &s, double &e)
-{
-    s = a + b;
-    const double bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
-}
-__device__ __forceinline__ void dd_add(double &hi, double &lo, double bh, double bl)
-{
-    double s, e;
-    two_sum(hi, bh, s, e);
-    e += lo + bl;
-    hi = s + e;
-    lo = e - (hi - s);
-}
-
-__global__ void dd_partial_kernel(const double *a0, const double *a1, const double *a2, const double *a3, long long n,
-                                  double *part)
-{
-    __shared__ double sh[4][2][256];
-    double hi[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0};
-    const double *src[4] = {a0, a1, a2, a3};
-    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            if (src[k]) dd_add(hi[k], lo[k], src[k][c], 0.0);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) { sh[k][0][threadIdx.x] = hi[k]; sh[k][1][threadIdx.x] = lo[k]; }
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                double h = sh[k][0][threadIdx.x], l = sh[k][1][threadIdx.x];
-                dd_add(h, l, sh[k][0][threadIdx.x + s], sh[k][1][threadIdx.x + s]);
-                sh[k][0][threadIdx.x] = h;
-                sh[k][1][threadIdx.x] = l;
-            }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) { part[blockIdx.x * 8 + 2 * k] = sh[k][0][0]; part[blockIdx.x * 8 + 2 * k + 1] = sh[k][1][0]; }
-}
-
-__global__ void dd_final_kernel(const double *part, int nparts, double vol, double *out)
-{
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    for (int k = 0; k < 4; ++k) {
-        double hi = 0.0, lo = 0.0;
-        for (int b = 0; b < nparts; ++b) dd_add(hi, lo, part[b * 8 + 2 * k], part[b * 8 + 2 * k + 1]);
-        out[k] = (hi + lo) * vol;
-    }
 }
 
 }  // namespace pond

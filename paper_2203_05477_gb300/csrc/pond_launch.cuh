@@ -1,0 +1,96 @@
+// pond_launch.cuh -- the compiled variants of the step kernels: lists, names and the
+// declarations of their launchers.
+//
+// These lists are the autotuner's search space: tile shapes of the face kernel (cells per
+// CTA, CTAs per SM), block sizes of the cell kernel, and thread counts of the persistent
+// tube kernel.  Entry 0 of each list is the default used before (or without) tuning.  The
+// launchers are defined in pond_variants.cuh and instantiated in separate translation
+// units (pond_v*.cu), so the heavy kernels compile in parallel.
+#pragma once
+
+#include <cstdio>
+
+#include "pond_batch.cuh"
+
+namespace pond {
+
+template <typename... Vs>
+struct VList {
+    static constexpr int size = sizeof...(Vs);
+};
+
+// ---------------------------------------------------------------- face kernel
+
+template <int D, typename R>
+struct FaceList;
+template <>
+struct FaceList<2, float> {
+    using type = VList<FaceVariant<2, 32, 4, 2>, FaceVariant<2, 16, 8, 2>, FaceVariant<2, 64, 2, 2>,
+                       FaceVariant<2, 16, 4, 4>, FaceVariant<2, 32, 4, 1>>;
+};
+template <>
+struct FaceList<2, double> {
+    using type = VList<FaceVariant<2, 32, 4, 1>, FaceVariant<2, 16, 8, 1>, FaceVariant<2, 16, 4, 2>>;
+};
+template <typename R>
+struct FaceList<1, R> {
+    using type = VList<FaceVariant<1, 128, 1, 1>, FaceVariant<1, 64, 1, 2>, FaceVariant<1, 256, 1, 1>>;
+};
+
+template <int D, typename R, typename V, typename... Rest>
+void face_name_at(int v, char *buf, size_t n)
+{
+    if (v <= 0 || sizeof...(Rest) == 0) {
+        if (D == 2) std::snprintf(buf, n, "face %dx%d cells, %d threads, %d CTA/SM", V::TX, V::TY, V::THREADS, V::MINB);
+        else std::snprintf(buf, n, "face %d cells, %d threads, %d CTA/SM", V::TX, V::THREADS, V::MINB);
+    } else if constexpr (sizeof...(Rest) > 0) {
+        face_name_at<D, R, Rest...>(v - 1, buf, n);
+    }
+}
+
+template <int D, typename R, typename L>
+struct FaceNames;
+template <int D, typename R, typename... Vs>
+struct FaceNames<D, R, VList<Vs...>> {
+    static void name(int v, char *buf, size_t n) { face_name_at<D, R, Vs...>(v, buf, n); }
+};
+
+template <int D, typename R>
+constexpr int face_variants() { return FaceList<D, R>::type::size; }
+
+// the face kernel of variant v; with collect, the pair-collecting kernel of variant 0
+// (defined in pond_variants.cuh, instantiated in the pond_v*.cu translation units)
+template <int D, typename R>
+void launch_face(int v, bool collect, const Params<D, R> &P, cudaStream_t st);
+
+// ---------------------------------------------------------------- cell kernel
+
+constexpr int kCellBlocks[3] = {256, 128, 512};
+constexpr int kCellVariants = 3;
+
+template <int D, typename R>
+void launch_cell(int v, const Params<D, R> &P, cudaStream_t st);
+
+inline void cell_name(int v, char *buf, size_t n)
+{
+    std::snprintf(buf, n, "cell %d threads", kCellBlocks[(v >= 0 && v < kCellVariants) ? v : 0]);
+}
+
+// ---------------------------------------------------------------- tube kernel
+
+template <typename R>
+constexpr int tube_variants() { return sizeof(R) == 4 ? 4 : 2; }
+
+template <typename R>
+void launch_tube(int v, unsigned n_tubes, const TubeParams<R> &P, int steps, int cur, cudaStream_t st);
+
+template <typename R>
+void tube_name(int v, char *buf, size_t n)
+{
+    static const int f32[4][2] = {{256, 3}, {128, 6}, {128, 4}, {512, 1}}, f64[2][2] = {{256, 1}, {128, 2}};
+    const int k = (v >= 0 && v < tube_variants<R>()) ? v : 0;
+    const int *c = sizeof(R) == 4 ? f32[k] : f64[k];
+    std::snprintf(buf, n, "tube %d threads, %d CTA/SM", c[0], c[1]);
+}
+
+}  // namespace pond

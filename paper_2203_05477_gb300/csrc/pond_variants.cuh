@@ -1,0 +1,77 @@
+// pond_variants.cuh -- definitions of the variant launchers declared in pond_launch.cuh.
+// Included only by the pond_v*.cu translation units, each of which instantiates the
+// launchers (and so the kernels) of one dimension and precision.
+#pragma once
+
+#include "pond_launch.cuh"
+
+namespace pond {
+
+template <int D, typename R, bool COLLECT, typename V>
+void launch_face_one(const Params<D, R> &P, cudaStream_t st)
+{
+    const dim3 g(unsigned((P.nx + 1 + V::TX - 1) / V::TX), D == 2 ? unsigned((P.ny + 1 + V::TY - 1) / V::TY) : 1u);
+    face_kernel<D, R, COLLECT, V><<<g, V::THREADS, 0, st>>>(P);
+}
+
+template <int D, typename R, typename V, typename... Rest>
+void launch_face_at(int v, const Params<D, R> &P, cudaStream_t st)
+{
+    if constexpr (sizeof...(Rest) == 0) {
+        launch_face_one<D, R, false, V>(P, st);
+    } else {
+        if (v <= 0) launch_face_one<D, R, false, V>(P, st);
+        else launch_face_at<D, R, Rest...>(v - 1, P, st);
+    }
+}
+
+template <int D, typename R, typename L>
+struct FaceLaunch;
+template <int D, typename R, typename... Vs>
+struct FaceLaunch<D, R, VList<Vs...>> {
+    static void launch(int v, const Params<D, R> &P, cudaStream_t st) { launch_face_at<D, R, Vs...>(v, P, st); }
+};
+
+// the face kernel of variant v; with collect, the pair-collecting kernel of variant 0
+template <int D, typename R>
+void launch_face(int v, bool collect, const Params<D, R> &P, cudaStream_t st)
+{
+    if (collect) {
+        using V0 = FaceVariant<D, D == 2 ? 32 : 128, 4, D == 2 && sizeof(R) == 4 ? 2 : 1>;
+        launch_face_one<D, R, true, V0>(P, st);
+    } else {
+        FaceLaunch<D, R, typename FaceList<D, R>::type>::launch(v, P, st);
+    }
+}
+
+template <int D, typename R>
+void launch_cell(int v, const Params<D, R> &P, cudaStream_t st)
+{
+    const long long n = P.ncell();
+    auto blocks = [&](int t) { return unsigned((n + t - 1) / t); };
+    switch (v) {
+    case 1: cell_kernel<D, R, 128><<<blocks(128), 128, 0, st>>>(P); break;
+    case 2: cell_kernel<D, R, 512><<<blocks(512), 512, 0, st>>>(P); break;
+    default: cell_kernel<D, R, 256><<<blocks(256), 256, 0, st>>>(P); break;
+    }
+}
+
+template <typename R>
+void launch_tube(int v, unsigned n_tubes, const TubeParams<R> &P, int steps, int cur, cudaStream_t st)
+{
+    if constexpr (sizeof(R) == 4) {
+        switch (v) {
+        case 1: tube_kernel<R, 128, 6><<<n_tubes, 128, 0, st>>>(P, steps, cur); break;
+        case 2: tube_kernel<R, 128, 4><<<n_tubes, 128, 0, st>>>(P, steps, cur); break;
+        case 3: tube_kernel<R, 512, 1><<<n_tubes, 512, 0, st>>>(P, steps, cur); break;
+        default: tube_kernel<R, 256, 3><<<n_tubes, 256, 0, st>>>(P, steps, cur); break;
+        }
+    } else {
+        switch (v) {
+        case 1: tube_kernel<R, 128, 2><<<n_tubes, 128, 0, st>>>(P, steps, cur); break;
+        default: tube_kernel<R, 256, 1><<<n_tubes, 256, 0, st>>>(P, steps, cur); break;
+        }
+    }
+}
+
+}  // namespace pond

@@ -1,0 +1,134 @@
+"""Kernel variants and the autotuner.  Every compiled variant of the face, cell and tube
+kernels reproduces the FP64 oracle at 1e-12 in corrector parity mode, on sizes that leave
+ragged tiles for every tile shape; FP32 variants agree with each other to FP32 rounding;
+tuning restores the state it times on; a cache file short-cuts a second tuning."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_2203_05477_gb300 as pond  # noqa: E402
+from paper_2203_05477_gb300 import inputs as I  # noqa: E402
+from tests.common import max_rel, oracle_for, rel_l1  # noqa: E402
+from tests.test_gpu_batch import run_pair, small_batch  # noqa: E402
+from tests.test_gpu_parity import compare_fp64, gpu_for  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+KW64 = dict(tau=1e-5, cfl=0.2, fixed_iters=3, max_iter=8)
+
+
+def split(names):
+    nf = sum(1 for n in names if n.startswith("face"))
+    return nf, len(names) - nf
+
+
+@pytest.mark.parametrize("name,pb", [
+    ("shocked_interface_37x13", I.shocked_interface_2d(37, 13, seed=1)),
+    ("quadrants_29x29", I.quadrants_2d(29, seed=0)),
+    ("lax_150", I.paper_tube("lax", 150)[0]),
+], ids=lambda x: x if isinstance(x, str) else "")
+def test_every_grid_variant_matches_oracle_fp64(name, pb):
+    os_ = oracle_for(pb, **KW64)
+    os_.step(4)
+    gs = gpu_for(pb, precision="fp64", **KW64)
+    nf, nc = split(gs.variants())
+    assert nf >= 3 and nc == 3
+    for f in range(nf):
+        for c in range(nc):
+            if f and c != f % nc:
+                continue  # every face variant once, every cell variant with face variant 0
+            gs.set_variants(face=f, cell=c)
+            gs.set_primitive()
+            gs.step(4)
+            d = gs.sync()
+            assert d["steps"] == 4 and d["nonphysical"] == 0, (f, c, d)
+            compare_fp64(gs, os_)
+
+
+def _prims(s):
+    return [np.asarray(a) for a in s.primitive()]  # rho, ux, uy, p
+
+
+def test_fp32_grid_variants_agree():
+    pb = I.quadrants_2d(61, seed=0)
+    kw = dict(tau=1e-5, cfl=0.2, max_iter=16, tol=1e-6)
+    gs = gpu_for(pb, precision="fp32", **kw)
+    nf, nc = split(gs.variants())
+    gs.step(10)
+    ref = _prims(gs)
+    for f in range(nf):
+        c = f % nc
+        gs.set_variants(face=f, cell=c)
+        gs.set_primitive()
+        gs.step(10)
+        assert gs.sync()["nonphysical"] == 0
+        got = _prims(gs)
+        for a, b in zip(got, ref):
+            assert rel_l1(a, b) <= 1e-5, (gs.variants()[f], rel_l1(a, b))
+
+
+def test_autotune_restores_state_and_uses_cache(tmp_path):
+    pb = I.quadrants_2d(64, seed=0)
+    kw = dict(tau=1e-5, cfl=0.2, max_iter=16, tol=1e-6)
+    gs = gpu_for(pb, precision="fp32", **kw)
+    gs.step(3)
+    assert gs.sync()["nonphysical"] == 0
+    before = gs.state()
+    gb = gs.face_gauges()
+    t0 = gs.sync()["t"]
+    cache = tmp_path / "tune.txt"
+    r = gs.autotune(steps=2, cache=str(cache))
+    assert not r["from_cache"] and len(r["ms"]) == len(gs.variants())
+    assert all(v > 0 for v in r["ms"].values())
+    after = gs.state()
+    for a, b in zip(after, before):
+        assert np.array_equal(a, b)
+    for a, b in zip(gs.face_gauges(), gb):
+        assert np.array_equal(a, b)
+    assert gs.sync()["t"] == t0
+    # the tuned solver continues like an untuned one
+    ref = gpu_for(pb, precision="fp32", **kw)
+    ref.step(3 + 40)
+    gs.step(40)
+    for a, b in zip(_prims(gs), _prims(ref)):
+        assert rel_l1(a, b) <= 1e-5
+    # a second solver of the same problem takes the choice from the cache without timing
+    other = gpu_for(pb, precision="fp32", **kw)
+    r2 = other.autotune(steps=2, cache=str(cache))
+    assert r2["from_cache"] and (r2["face"], r2["cell"]) == (r["face"], r["cell"])
+    assert len(cache.read_text().splitlines()) == 1
+
+
+def test_every_tube_variant_matches_oracle_fp64():
+    bt = small_batch()
+    gs, oracles = run_pair(bt, "fp64", 5, **KW64)
+    rho0, ux0, p0 = I.tube_batch_fields(bt)
+    names = gs.variants()
+    assert len(names) >= 2 and all(n.startswith("tube") for n in names)
+    for v in range(len(names)):
+        gs.set_variants(tube=v)
+        gs.set_primitive(rho0, ux0, None, p0)
+        gs.step(5)
+        assert gs.sync()["status"] == pond.POND_OK
+        (rho, mx, _, E), _ = gs.moments()
+        for k, os_ in enumerate(oracles):
+            a, b = gs.offsets[k], gs.offsets[k + 1]
+            ro, mo, _, Eo = os_.conserved()
+            assert max_rel(rho[a:b], ro) <= 1e-12 and max_rel(E[a:b], Eo) <= 1e-12, (names[v], k)
+
+
+def test_tube_autotune_restores_state():
+    bt = small_batch()
+    gs = pond.BatchSolver(bt.lengths, bt.gammas, precision="fp32", tau=1e-5, cfl=0.2, max_iter=16, tol=1e-6)
+    rho0, ux0, p0 = I.tube_batch_fields(bt)
+    gs.set_primitive(rho0, ux0, None, p0)
+    gs.step(4)
+    before = gs.state()
+    t_before = gs.times()
+    r = gs.autotune(steps=3)
+    assert 0 <= r["tube"] < len(gs.variants()) and len(r["ms"]) == len(gs.variants())
+    for a, b in zip(gs.state(), before):
+        assert np.array_equal(a, b)
+    for a, b in zip(gs.times(), t_before):
+        assert np.array_equal(a, b)
