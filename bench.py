@@ -34,9 +34,9 @@ FALLBACK_HBM_GBS = 6800.0
 N_SMS, FP32_LANES = 152, 128
 # FP32 operations (FMA = 2) of one corrector pass at one D2Q16 face (per-face overhead
 # included), from the ncu instruction counts of the face kernel; used for the ALU roofline
-FACE_KERNEL_DRAM_BYTES = 137.0e6 + 176.1e6  # ncu dram read + write of one launch at 1024^2
+# ncu dram read + write of one face-kernel launch at 1024^2, per tile variant measured
+FACE_KERNEL_DRAM_BYTES = {0: 137.0e6 + 176.1e6, 1: 136.4e6 + 179.6e6}
 FLOPS_PER_FACE_PASS = 4550.0
-FACE_TRAFFIC_VARIANT = 0  # the face-kernel variant the ncu traffic figure was taken on
 # algorithmic bytes per cell-update of the FP32 D2Q16 layout: the face kernel reads the
 # cell state (8 + 6 FP32 coefficients + 3 float-float frame words = 80 B) and two face predictors
 # (2 x 24 B) and writes two faces (2 x (16 x 4 + 24) B)
@@ -397,7 +397,7 @@ def main():
             "fp64": None if tune64 is None else {"face": tune64["face"], "cell": tune64["cell"]}},
         "corrector": {"passes_per_face": face_passes / max(faces, 1), "status_ok": status_ok},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp32_peak, "traffic": FACE_KERNEL_DRAM_BYTES if fv == FACE_TRAFFIC_VARIANT else None,
+                     "frac": achieved / fp32_peak, "traffic": FACE_KERNEL_DRAM_BYTES.get(fv),
                      "kernel": "face_kernel<2,float> (%s)" % variant_names[fv],
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % sm_mhz,
                      "face_ms": face_ms_avg, "cell_ms": ms_cell / args.steps,
