@@ -50,12 +50,16 @@ typedef enum {
  * paper requires (Sec. II.C) and are refused with POND_ERR_UNSUPPORTED. */
 typedef enum { POND_D1Q3 = 0, POND_D1Q4 = 1, POND_D2Q16 = 2, POND_D2Q9 = 3 } pond_velset;
 
-/* Ghost-cell rules: copy of the nearest cell (zero gradient), wrap-around, or the
- * equilibrium at a prescribed state on part of a side (transmissive on the rest). */
-typedef enum { POND_BC_TRANSMISSIVE = 0, POND_BC_PERIODIC = 1, POND_BC_INFLOW = 2 } pond_bc;
+/* Ghost-cell rules (two layers): copy of the nearest cell (zero gradient), wrap-around,
+ * the equilibrium at a prescribed state on part of a side (transmissive on the rest), or a
+ * reflective wall: ghost k mirrors the k-th cell from the wall, with the normal component
+ * of every particle velocity and of the frame velocity reversed (the two-blast-wave and
+ * explosion-in-a-box cases of Sec. IV). */
+typedef enum { POND_BC_TRANSMISSIVE = 0, POND_BC_PERIODIC = 1, POND_BC_INFLOW = 2, POND_BC_REFLECTIVE = 3 } pond_bc;
 
-/* Arithmetic of populations, fluxes and collision.  Frames (u, T) and their recovery
- * from the conserved moments are FP64 in both modes. */
+/* Arithmetic of populations, fluxes and collision.  Frames (u, T) advance by increments
+ * formed relative to the old frame; they are FP64 words in FP64 mode and float-float pairs
+ * (about 48 significant bits) in FP32 mode. */
 typedef enum { POND_FP64 = 0, POND_FP32 = 1 } pond_precision;
 
 /* Slope limiters of Sec. III.B.3 ("Van Leer and minmod"). */

@@ -22,7 +22,7 @@ _LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-BC_TRANSMISSIVE, BC_PERIODIC, BC_INFLOW = 0, 1, 2
+BC_TRANSMISSIVE, BC_PERIODIC, BC_INFLOW, BC_REFLECTIVE = 0, 1, 2, 3
 VANLEER, MINMOD = 0, 1
 
 

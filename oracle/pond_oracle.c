@@ -35,8 +35,9 @@
  *   moments of the last pass, Grad-projected into the frame those moments define, with
  *   the co-moving equilibria there; van Leer (default) or minmod limiter on one-sided
  *   differences divided by the cell size; upwind cell = left/lower when v.n > 0, else
- *   right/upper; ghost cells (2 layers) are copies (transmissive), wraps (periodic) or
- *   the equilibrium at a prescribed state (inflow).
+ *   right/upper; ghost cells (2 layers) are copies (transmissive), wraps (periodic),
+ *   the equilibrium at a prescribed state (inflow), or mirror images (reflective walls:
+ *   the normal component of every particle velocity and of the frame velocity reversed).
  *
  * Build: gcc -O2 -ffp-contract=off -fPIC -shared pond_oracle.c -lm
  */
@@ -212,7 +213,7 @@ static double limiter(int kind, double a, double b)
 
 /* --------------------------------------------------------------- the solver */
 
-enum { BC_TRANSMISSIVE = 0, BC_PERIODIC = 1, BC_INFLOW = 2 };
+enum { BC_TRANSMISSIVE = 0, BC_PERIODIC = 1, BC_INFLOW = 2, BC_REFLECTIVE = 3 };
 
 typedef struct oracle {
     lattice L;
@@ -256,6 +257,32 @@ static void copy_cell(oracle *o, int dst, int src)
     o->T[dst] = o->T[src];
 }
 
+/* Specular reflection at a wall normal to axis: the ghost holds the mirror image of the
+ * source cell, population v_i taking the value of the population with the normal
+ * component of c reversed, and the frame velocity's normal component reversed (reading
+ * of reflective walls, Sec. IV, two-blast-wave and explosion-in-a-box cases). */
+static void mirror_cell(oracle *o, int dst, int src, int axis)
+{
+    const lattice *L = &o->L;
+    double f[MAXQ], g[MAXQ];
+    for (int i = 0; i < o->Q; ++i) {
+        int j = -1;
+        for (int k = 0; k < o->Q; ++k) {
+            int same = L->c[k][axis] == -L->c[i][axis];
+            for (int a = 0; a < o->D; ++a)
+                if (a != axis && L->c[k][a] != L->c[i][a]) same = 0;
+            if (same) j = k;
+        }
+        f[i] = o->f[(size_t)src * o->Q + j];
+        g[i] = o->g[(size_t)src * o->Q + j];
+    }
+    memcpy(o->f + (size_t)dst * o->Q, f, sizeof(double) * o->Q);
+    memcpy(o->g + (size_t)dst * o->Q, g, sizeof(double) * o->Q);
+    memcpy(o->u + (size_t)dst * MAXD, o->u + (size_t)src * MAXD, sizeof(double) * MAXD);
+    o->u[(size_t)dst * MAXD + axis] = -o->u[(size_t)src * MAXD + axis];
+    o->T[dst] = o->T[src];
+}
+
 static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 static int wrapi(int v, int n) { return ((v % n) + n) % n; }
 
@@ -273,6 +300,10 @@ static void fill_ghosts(oracle *o)
                     set_equilibrium_cell(o, dst, o->inflow[side][0], uu, o->inflow[side][3]);
                 } else if (b == BC_PERIODIC) {
                     copy_cell(o, dst, cidx(o, wrapi(i, o->nx), j));
+                } else if (b == BC_REFLECTIVE) {
+                    /* ghost -k mirrors cell k-1; ghost nx-1+k mirrors cell nx-k (clamped
+                     * into the grid when it is thinner than the ghost layers) */
+                    mirror_cell(o, dst, cidx(o, clampi(side == 0 ? k - 1 : o->nx - k, 0, o->nx - 1), j), 0);
                 } else {
                     copy_cell(o, dst, cidx(o, clampi(i, 0, o->nx - 1), j));
                 }
@@ -291,6 +322,8 @@ static void fill_ghosts(oracle *o)
                     set_equilibrium_cell(o, dst, o->inflow[side][0], uu, o->inflow[side][3]);
                 } else if (b == BC_PERIODIC) {
                     copy_cell(o, dst, cidx(o, i, wrapi(j, o->ny)));
+                } else if (b == BC_REFLECTIVE) {
+                    mirror_cell(o, dst, cidx(o, i, clampi(side == 2 ? k - 1 : o->ny - k, 0, o->ny - 1)), 1);
                 } else {
                     copy_cell(o, dst, cidx(o, i, clampi(j, 0, o->ny - 1)));
                 }

@@ -699,7 +699,7 @@ pond_status pond_init(const pond_grid *grid, pond_velset velset, double gamma, d
     if (opts->limiter != POND_VANLEER && opts->limiter != POND_MINMOD) return fail(POND_ERR_INVALID_ARG, "bad limiter");
     if (!(opts->cfl > 0.0) || opts->max_iter < 1 || opts->fixed_iters < 0) return fail(POND_ERR_INVALID_ARG, "bad cfl/max_iter/fixed_iters");
     for (int k = 0; k < 4; ++k)
-        if (grid->bc[k] < 0 || grid->bc[k] > 2) return fail(POND_ERR_INVALID_ARG, "bad boundary condition on side %d", k);
+        if (grid->bc[k] < 0 || grid->bc[k] > 3) return fail(POND_ERR_INVALID_ARG, "bad boundary condition on side %d", k);
     if ((grid->bc[0] == POND_BC_PERIODIC) != (grid->bc[1] == POND_BC_PERIODIC) ||
         (D == 2 && (grid->bc[2] == POND_BC_PERIODIC) != (grid->bc[3] == POND_BC_PERIODIC)))
         return fail(POND_ERR_INVALID_ARG, "periodic sides must come in pairs");

@@ -59,6 +59,9 @@ __host__ __device__ __forceinline__ void fr_store(ffloat &w, double v)
     w.hi = float(v);
     w.lo = float(v - double(w.hi));
 }
+// -x
+__host__ __device__ __forceinline__ double fr_neg(double x) { return -x; }
+__host__ __device__ __forceinline__ ffloat fr_neg(ffloat x) { return ffloat{-x.hi, -x.lo}; }
 // a working-precision value as a word
 __device__ __forceinline__ double fr_word(double v) { return v; }
 __device__ __forceinline__ ffloat fr_word(float v) { return ffloat{v, 0.f}; }
@@ -86,7 +89,7 @@ __device__ __forceinline__ ffloat fr_add(ffloat x, float d)
 }
 
 
-enum { BC_TRANSMISSIVE = 0, BC_PERIODIC = 1, BC_INFLOW = 2 };
+enum { BC_TRANSMISSIVE = 0, BC_PERIODIC = 1, BC_INFLOW = 2, BC_REFLECTIVE = 3 };
 enum { FLAG_NONPHYSICAL = 1u, FLAG_NOT_CONVERGED = 2u, FLAG_TIMEOUT = 4u };
 
 // constants of the step about to run, set with dt (Eqs. FinalUpdateDUGKS, Fbarplus,
@@ -193,23 +196,56 @@ __device__ __forceinline__ long long clampll(long long v, long long lo, long lon
 __device__ __forceinline__ long long wrapll(long long v, long long n) { long long r = v % n; return r < 0 ? r + n : r; }
 
 // Ghost-cell rules (two layers; y sides first, then x sides).  Returns -1 and the linear
-// cell index, or the side (0..3) whose inflow state the cell holds.
+// cell index, or the side (0..3) whose inflow state the cell holds.  *flip receives the
+// axes (bit 0 x, bit 1 y) across which the cell is a mirror image (reflective walls: ghost
+// -k mirrors cell k-1, ghost n-1+k mirrors cell n-k); the holder of the cell reverses the
+// normal components of its velocity and of its odd-order coefficients along those axes.
 template <int D, typename R>
-__device__ __forceinline__ int resolve(const Params<D, R> &P, long long i, long long j, long long *idx)
+__device__ __forceinline__ int resolve(const Params<D, R> &P, long long i, long long j, long long *idx, int *flip)
 {
+    int fl = 0;
     if (D == 2 && (j < 0 || j >= P.ny)) {
         const int side = j < 0 ? 2 : 3;
         const long long ic = clampll(i, 0, P.nx - 1);
-        if (P.bc[side] == BC_INFLOW && ic >= P.lo[side] && ic < P.hi[side]) return side;
-        j = P.bc[side] == BC_PERIODIC ? wrapll(j, P.ny) : clampll(j, 0, P.ny - 1);
+        if (P.bc[side] == BC_INFLOW && ic >= P.lo[side] && ic < P.hi[side]) { *flip = fl; return side; }
+        if (P.bc[side] == BC_REFLECTIVE) {
+            j = j < 0 ? -1 - j : 2 * P.ny - 1 - j;
+            j = clampll(j, 0, P.ny - 1);  // grids thinner than the ghost layers
+            fl |= 2;
+        } else {
+            j = P.bc[side] == BC_PERIODIC ? wrapll(j, P.ny) : clampll(j, 0, P.ny - 1);
+        }
     }
     if (i < 0 || i >= P.nx) {
         const int side = i < 0 ? 0 : 1;
-        if (P.bc[side] == BC_INFLOW && j >= P.lo[side] && j < P.hi[side]) return side;
-        i = P.bc[side] == BC_PERIODIC ? wrapll(i, P.nx) : clampll(i, 0, P.nx - 1);
+        if (P.bc[side] == BC_INFLOW && j >= P.lo[side] && j < P.hi[side]) { *flip = fl; return side; }
+        if (P.bc[side] == BC_REFLECTIVE) {
+            i = i < 0 ? -1 - i : 2 * P.nx - 1 - i;
+            i = clampll(i, 0, P.nx - 1);
+            fl |= 1;
+        } else {
+            i = P.bc[side] == BC_PERIODIC ? wrapll(i, P.nx) : clampll(i, 0, P.nx - 1);
+        }
     }
     *idx = j * P.nx + i;
+    *flip = fl;
     return -1;
+}
+
+// sign of coefficient (r, s) (orders along x and y) of a cell mirrored across the axes in flip
+template <int D>
+__device__ __forceinline__ bool mirror_odd(int k, int flip)
+{
+    int r = 0, s = 0;
+    if (D == 1) {
+        r = k;
+    } else {
+        int n = 0;
+        while ((n + 1) * (n + 2) / 2 <= k) ++n;  // k = hidx(r, s) with r + s = n
+        s = k - n * (n + 1) / 2;
+        r = n - s;
+    }
+    return (((flip & 1) && (r & 1)) != 0) != (((flip & 2) && (s & 1)) != 0);
 }
 
 // Cell data as staged for the face corrector: phi-bar-plus coefficients (Eq. Fbarplus) in
@@ -229,7 +265,8 @@ __device__ __forceinline__ void cell_velocity(const Params<D, R> &P, long long i
                                               typename FrameWords<R>::word *u)
 {
     long long idx = 0;
-    const int side = resolve(P, i, j, &idx);
+    int flip = 0;
+    const int side = resolve(P, i, j, &idx, &flip);
     if (side >= 0) {
         fr_store(u[0], P.inflow[side][1]);
         if constexpr (D == 2) fr_store(u[1], P.inflow[side][2]);
@@ -237,6 +274,9 @@ __device__ __forceinline__ void cell_velocity(const Params<D, R> &P, long long i
 #pragma unroll
         for (int a = 0; a < D; ++a) u[a] = P.sfr[a * P.ncell() + idx];
     }
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+        if (flip & (1 << a)) u[a] = fr_neg(u[a]);
 }
 
 template <int D, typename R>
@@ -246,7 +286,8 @@ __device__ __forceinline__ void load_cell_bar_plus(const Params<D, R> &P, long l
     constexpr int NFC = NCoef<D, 3>::value, NGC = NCoef<D, 2>::value;
     using W = typename FrameWords<R>::word;
     long long idx = 0;
-    const int side = resolve(P, i, j, &idx);
+    int flip = 0;
+    const int side = resolve(P, i, j, &idx, &flip);
     W u[D];
     R T;
     if (side >= 0) {
@@ -272,6 +313,18 @@ __device__ __forceinline__ void load_cell_bar_plus(const Params<D, R> &P, long l
 #pragma unroll
         for (int a = 0; a < D; ++a) u[a] = P.sfr[a * n + idx];
         T = R(fr_lead(P.sfr[D * n + idx]));
+    }
+    if (flip) {
+        // mirror image: odd orders along a flipped axis and that velocity component reverse
+#pragma unroll
+        for (int k = 0; k < NFC; ++k)
+            if (mirror_odd<D>(k, flip)) c.A[k] = -c.A[k];
+#pragma unroll
+        for (int k = 0; k < NGC; ++k)
+            if (mirror_odd<D>(k, flip)) c.B[k] = -c.B[k];
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+            if (flip & (1 << a)) u[a] = fr_neg(u[a]);
     }
 #pragma unroll
     for (int a = 0; a < D; ++a) c.du[a] = R(fr_rel(u[a], utile[a]));
@@ -1110,7 +1163,8 @@ template <int D, typename R>
 __device__ __forceinline__ void cell_conserved(const Params<D, R> &P, long long i, long long j, double &r, double *m, double &E)
 {
     long long idx = 0;
-    const int side = resolve(P, i, j, &idx);
+    int flip = 0;
+    const int side = resolve(P, i, j, &idx, &flip);
     double u[2] = {0.0, 0.0}, T;
     if (side >= 0) {
         r = P.inflow[side][0];
@@ -1124,6 +1178,8 @@ __device__ __forceinline__ void cell_conserved(const Params<D, R> &P, long long 
         for (int a = 0; a < D; ++a) u[a] = fr_value(P.sfr[a * n + idx]);
         T = fr_value(P.sfr[D * n + idx]);
     }
+    if (flip & 1) u[0] = -u[0];
+    if (flip & 2) u[1] = -u[1];
     double k2 = 0.0;
 #pragma unroll
     for (int a = 0; a < D; ++a) { m[a] = r * u[a]; k2 += u[a] * u[a]; }
@@ -1216,7 +1272,8 @@ gauge_predict_kernel(const Params<2, R> P)
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 long long idx = 0;
-                const int side = resolve(P, ci[q], cj[q], &idx);
+                int flip = 0;
+                const int side = resolve(P, ci[q], cj[q], &idx, &flip);
                 W u[2];
                 float rho, T;
                 if (side >= 0) {
@@ -1230,6 +1287,8 @@ gauge_predict_kernel(const Params<2, R> P)
                     u[1] = P.sfr[n + idx];
                     T = float(fr_lead(P.sfr[2 * n + idx]));
                 }
+                if (flip & 1) u[0] = fr_neg(u[0]);
+                if (flip & 2) u[1] = fr_neg(u[1]);
                 sp[q] = {rho, float(fr_rel(u[na], uref[na])), float(fr_rel(u[ta], uref[ta])), T};
             }
             mlp::features(sp, float(Tp), dir ? K.kf.h_dy : K.kf.h_dx, f);

@@ -17,7 +17,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-TRANSMISSIVE, PERIODIC, INFLOW = 0, 1, 2
+TRANSMISSIVE, PERIODIC, INFLOW, REFLECTIVE = 0, 1, 2, 3
 
 
 @dataclass
@@ -250,3 +250,60 @@ def jet_2d(n, seed, gamma=5.0 / 3.0, mach=80.0, density_ratio=10.0):
     return Problem(2, n, n, 0.0, 1.0, -0.5, 0.5, gamma, np.full(N, rho_amb), np.zeros(N),
                    np.zeros(N), np.full(N, p_amb), bc=(INFLOW, TRANSMISSIVE, TRANSMISSIVE, TRANSMISSIVE),
                    inflow=inflow, inflow_range=rngs, name="jet_%d_seed%d" % (n, seed))
+
+
+# ------------------------------------------------------------------ reflective walls
+
+def two_blast_1d(n, gamma=1.4):
+    """Two interacting blast waves (Sec. IV, Woodward-Colella): rho = 1, u = 0 and p = 1000 on
+    [0, 0.1), 0.01 on [0.1, 0.9), 100 on [0.9, 1]; reflective walls at x = 0 and x = 1
+    (the paper runs 1600 cells to t = 0.038)."""
+    x = cell_centres(n, 0.0, 1.0)
+    p = np.where(x < 0.1, 1000.0, np.where(x < 0.9, 0.01, 100.0))
+    return Problem(1, n, 1, 0.0, 1.0, 0.0, 1.0, gamma, np.ones(n), np.zeros(n), np.zeros(n), p,
+                   bc=(REFLECTIVE, REFLECTIVE, TRANSMISSIVE, TRANSMISSIVE), name="two_blast_%d" % n)
+
+
+def explosion_box_2d(n, gamma=1.4):
+    """Explosion in a box (Sec. IV): the unit square with reflective walls; (rho, u, v, p) =
+    (5, 0, 0, 5) inside the circle of radius 0.3 about (0.4, 0.4), (1, 0, 0, 1) elsewhere,
+    sampled at cell centres (the paper runs 256 x 256 to t = 0.5)."""
+    x = cell_centres(n, 0.0, 1.0)
+    X, Y = np.meshgrid(x, x)
+    inside = ((X - 0.4) ** 2 + (Y - 0.4) ** 2 < 0.09).ravel()
+    rho = np.where(inside, 5.0, 1.0)
+    return Problem(2, n, n, 0.0, 1.0, 0.0, 1.0, gamma, rho, np.zeros(n * n), np.zeros(n * n), rho.copy(),
+                   bc=(REFLECTIVE,) * 4, name="explosion_box_%d" % n)
+
+
+def wall_reflection_1d(n, rho=1.0, u=-1.0, p=1.0, gamma=1.4):
+    """Uniform gas moving into a reflective wall at x = 0 (transmissive at x = 1).  By
+    symmetry it is the Riemann problem (rho, -u, p) | (rho, u, p) about x = 0, whose exact
+    solution on x > 0 is a reflected shock leaving the wall with the gas at rest behind it."""
+    return Problem(1, n, 1, 0.0, 1.0, 0.0, 1.0, gamma, np.full(n, rho), np.full(n, u), np.zeros(n), np.full(n, p),
+                   bc=(REFLECTIVE, TRANSMISSIVE, TRANSMISSIVE, TRANSMISSIVE), name="wall_reflection_%d" % n)
+
+
+def mirror_extend(pb: Problem) -> Problem:
+    """The reflective problem pb unfolded into a periodic one: every reflective axis is
+    doubled with the mirror image (the normal velocity reversed) placed across the wall.
+    Its copy of pb's cells evolves exactly as pb does (both sides of each wall see the
+    same ghost values)."""
+    nx, ny = pb.nx, pb.ny
+    rho, ux, uy, p = (a.reshape(ny, nx) for a in (pb.rho, pb.ux, pb.uy, pb.p))
+    x0, x1, y0, y1 = pb.x0, pb.x1, pb.y0, pb.y1
+    bc = list(pb.bc)
+    if pb.bc[0] == REFLECTIVE:
+        assert pb.bc[1] == REFLECTIVE
+        rho, ux, uy, p = (np.concatenate([a[:, ::-1] * s, a], axis=1) for a, s in ((rho, 1), (ux, -1), (uy, 1), (p, 1)))
+        x0 = x0 - (x1 - x0)
+        bc[0] = bc[1] = PERIODIC
+    if pb.dim == 2 and pb.bc[2] == REFLECTIVE:
+        assert pb.bc[3] == REFLECTIVE
+        rho, ux, uy, p = (np.concatenate([a[::-1, :] * s, a], axis=0) for a, s in ((rho, 1), (ux, 1), (uy, -1), (p, 1)))
+        y0 = y0 - (y1 - y0)
+        bc[2] = bc[3] = PERIODIC
+    NY, NX = rho.shape
+    return Problem(pb.dim, NX, NY if pb.dim == 2 else 1, x0, x1, y0, y1, pb.gamma, rho.ravel(), ux.ravel(),
+                   uy.ravel(), p.ravel(), bc=tuple(bc), name=pb.name + "_unfolded")
+
