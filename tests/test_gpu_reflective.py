@@ -3,6 +3,7 @@ FP64 parity with the oracle at 1e-12 in corrector parity mode, on walls alone, w
 corners, walls beside transmissive and inflow sides, and with nonzero wall-normal
 velocities; mass and energy conservation in a closed box; FP32 against the FP64 oracle."""
 import dataclasses
+import os
 
 import numpy as np
 import pytest
@@ -84,3 +85,54 @@ def test_fp32_explosion_box_against_fp64_oracle():
     assert rel_l1(r, ro) <= 1e-4 and rel_l1(p, po) <= 1e-4
     speed = np.sqrt(uxo ** 2 + uyo ** 2)
     assert np.abs(ux - uxo).sum() / speed.sum() <= 1e-4 and np.abs(uy - uyo).sum() / speed.sum() <= 1e-4
+
+
+def _golden(name):
+    vals = {}
+    path = os.path.join(os.path.dirname(__file__), "golden", name)
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            k, v = line.split()
+            vals[k] = float(v)
+    return vals
+
+
+def test_explosion_box_density_range_matches_paper():
+    """The paper's explosion-in-a-box figure spans rho in [0.52, 3.8] at t = 0.5 (256^2); the
+    FP32 run reaches t = 0.5 without a non-physical state and spans the same range to 3%."""
+    g = _golden("explosion_box_density_range.txt")
+    pb = I.explosion_box_2d(int(g["n"]))
+    s = gpu_for(pb, precision="fp32", tau=1e-5, cfl=0.2, t_end=g["t"], max_iter=16)
+    for _ in range(40):
+        s.step(128)
+        d = s.sync()
+        if d["t"] >= g["t"] or d["nonphysical"]:
+            break
+    assert d["nonphysical"] == 0 and d["t"] == pytest.approx(g["t"], rel=1e-12)
+    r = s.primitive()[0]
+    assert r.min() == pytest.approx(g["rho_min"], rel=0.03)
+    assert r.max() == pytest.approx(g["rho_max"], rel=0.03)
+
+
+def test_two_blast_fp32_matches_fp64_at_paper_size():
+    """Two interacting blast waves at the paper's 1600 cells to t = 0.038 (about 21 000
+    steps): both precisions finish without a non-physical state, and FP32 stays within 1e-4
+    relative L1 of FP64 (whose parity with the oracle the tests above establish)."""
+    pb = I.two_blast_1d(1600)
+    out = {}
+    for prec in ("fp64", "fp32"):
+        s = gpu_for(pb, precision=prec, tau=1e-5, cfl=0.2, t_end=0.038, max_iter=16)
+        for _ in range(200):
+            s.step(256)
+            d = s.sync()
+            if d["t"] >= 0.038 or d["nonphysical"]:
+                break
+        assert d["nonphysical"] == 0 and d["t"] == pytest.approx(0.038, rel=1e-12), prec
+        out[prec] = s.primitive()
+    for k in (0, 1, 3):
+        assert rel_l1(out["fp32"][k], out["fp64"][k]) <= 1e-4, k
+    r = out["fp64"][0]
+    x = (np.arange(1600) + 0.5) / 1600
+    # the collision of the two blast waves leaves its density peak (about 6) near x = 0.78
+    assert 5.5 < r.max() < 6.6 and abs(x[np.argmax(r)] - 0.78) < 0.02
+
