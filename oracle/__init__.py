@@ -57,6 +57,8 @@ def _load():
         lib.oracle_set_primitive.argtypes = [ctypes.c_void_p, dp, dp, dp, dp]
         lib.oracle_step.argtypes = [ctypes.c_void_p, ctypes.c_int]
         lib.oracle_step.restype = ctypes.c_int
+        lib.oracle_sl_step.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        lib.oracle_sl_step.restype = ctypes.c_int
         lib.oracle_conserved.argtypes = [ctypes.c_void_p, dp, dp, dp, dp]
         lib.oracle_regauged_state.argtypes = [ctypes.c_void_p, dp, dp, dp, dp]
         lib.oracle_raw_state.argtypes = [ctypes.c_void_p, dp, dp, dp, dp]
@@ -155,6 +157,10 @@ class Solver:
 
     def step(self, n: int) -> int:
         return int(self.lib.oracle_step(self.h, int(n)))
+
+    def sl_step(self, n: int) -> int:
+        """n steps of the semi-Lagrangian realization (Sec. III.A) instead of the FV step."""
+        return int(self.lib.oracle_sl_step(self.h, int(n)))
 
     def conserved(self):
         n = self.ncell

@@ -21,7 +21,10 @@
  *                   corrector with limited slopes and MUSCL reconstruction (Sec. III.B.3),
  *                   and Eq. (fluxEq);
  *   - step order:   the algorithm summary of Sec. III.B.4;
- *   - time step:    CFL = max|v_ia| dt/dx (Sec. IV).
+ *   - time step:    CFL = max|v_ia| dt/dx (Sec. IV);
+ *   - SL step:      the semi-Lagrangian realization of Sec. III.A (oracle_sl_step):
+ *                   Eqs. (advectionPond)-(advectionPondg), (correctorfieldsrho)-
+ *                   (correctorfieldT) and the BGK collision with beta.
  *
  * Readings where the paper is silent (each one is listed in the design notes):
  *   R = 1, p = rho T, Cv = 1/(gamma-1); D in g^eq is the lattice dimension; the
@@ -229,7 +232,8 @@ typedef struct oracle {
     int max_iter, fixed_iters;
     /* cell state (padded, AoS): populations in the cell frame (u, T) */
     double *f, *g, *u, *T;
-    double *fp, *gp;   /* phi-bar-plus, Eq. (Fbarplus) */
+    double *fp, *gp;   /* phi-bar-plus, Eq. (Fbarplus); the new populations in the SL step */
+    double *un, *Tn;   /* the new frames in the SL step */
     /* faces: x-faces (nx+1) x ny, y-faces nx x (ny+1); gauge and populations */
     double *xu, *xT, *yu, *yT;
     double *xf, *xg, *yf, *yg;
@@ -360,6 +364,8 @@ oracle *oracle_create(int D, int nx, int ny, double dx, double dy, double gamma,
     o->gp = calloc(nc * o->Q, sizeof(double));
     o->u = calloc(nc * MAXD, sizeof(double));
     o->T = calloc(nc, sizeof(double));
+    o->un = calloc(nc * MAXD, sizeof(double));
+    o->Tn = calloc(nc, sizeof(double));
     size_t nxf = (size_t)(nx + 1) * ny, nyf = (size_t)nx * (ny + 1);
     o->xu = calloc(nxf * MAXD, sizeof(double)); o->xT = calloc(nxf, sizeof(double));
     o->xf = calloc(nxf * o->Q, sizeof(double)); o->xg = calloc(nxf * o->Q, sizeof(double));
@@ -371,7 +377,7 @@ oracle *oracle_create(int D, int nx, int ny, double dx, double dy, double gamma,
 void oracle_free(oracle *o)
 {
     if (!o) return;
-    free(o->f); free(o->g); free(o->fp); free(o->gp); free(o->u); free(o->T);
+    free(o->f); free(o->g); free(o->fp); free(o->gp); free(o->u); free(o->T); free(o->un); free(o->Tn);
     free(o->xu); free(o->xT); free(o->xf); free(o->xg);
     free(o->yu); free(o->yT); free(o->yf); free(o->yg);
     free(o);
@@ -685,6 +691,187 @@ int oracle_step(oracle *o, int n)
                     *fq = ca * *fq + cb * feq[q] - dt * Ff[q];
                     *gq = ca * *gq + cb * geq[q] - dt * Fg[q];
                 }
+            }
+        o->t += dt;
+        o->last_dt = dt;
+        o->steps++;
+        taken++;
+    }
+    return taken;
+}
+
+/* ------------------------------------------------- semi-Lagrangian realization */
+
+/* Interpolation for the semi-Lagrangian step (Sec. III.A uses a 4-point stencil with a
+ * B-spline kernel and limiters whose details are in a thesis that is not available).
+ * Reading: the 4-point Lagrange interpolant (exact for cubics) at collocation offsets
+ * -1, 0, 1, 2, evaluated at th in [0, 1] (in 2D its tensor product on the 4 x 4 points);
+ * if it leaves the interval spanned by the bracketing values (the 2 nearest points, or the
+ * 2 x 2 nearest in 2D), the linear (bilinear) interpolant of those values is used. */
+static void lagrange4_weights(double th, double *w)
+{
+    w[0] = -th * (th - 1.0) * (th - 2.0) / 6.0;
+    w[1] = (th + 1.0) * (th - 1.0) * (th - 2.0) / 2.0;
+    w[2] = -(th + 1.0) * th * (th - 2.0) / 2.0;
+    w[3] = (th + 1.0) * th * (th - 1.0) / 6.0;
+}
+
+static double sl_interp(const double *v, double th)
+{
+    double w[4];
+    lagrange4_weights(th, w);
+    double p = w[0] * v[0] + w[1] * v[1] + w[2] * v[2] + w[3] * v[3];
+    const double lo = fmin(v[1], v[2]), hi = fmax(v[1], v[2]);
+    if (p < lo || p > hi) p = v[1] + th * (v[2] - v[1]);
+    return p;
+}
+
+/* v[r][m]: row r along y (offsets -1..2), column m along x */
+static double sl_interp2(double v[4][4], double thx, double thy)
+{
+    double wx[4], wy[4];
+    lagrange4_weights(thx, wx);
+    lagrange4_weights(thy, wy);
+    double p = 0.0;
+    for (int r = 0; r < 4; ++r)
+        for (int m = 0; m < 4; ++m) p += wy[r] * wx[m] * v[r][m];
+    const double lo = fmin(fmin(v[1][1], v[1][2]), fmin(v[2][1], v[2][2]));
+    const double hi = fmax(fmax(v[1][1], v[1][2]), fmax(v[2][1], v[2][2]));
+    if (p < lo || p > hi)
+        p = (1.0 - thy) * ((1.0 - thx) * v[1][1] + thx * v[1][2]) + thy * ((1.0 - thx) * v[2][1] + thx * v[2][2]);
+    return p;
+}
+
+/* Base collocation point and fraction of a departure point x_node - d along one axis, in
+ * units of the spacing: base = node - 1 when d > 0, else node (so |d| < h keeps th in [0, 1]). */
+static void sl_base(double d_over_h, int *base_off, double *th)
+{
+    if (d_over_h > 0.0) { *base_off = -1; *th = 1.0 - d_over_h; }
+    else                { *base_off = 0;  *th = -d_over_h; }
+}
+
+/* One node of the semi-Lagrangian step (Sec. III.A): predictor-corrector on the node's
+ * frame, each pass advecting every population from its departure point x - v_i dt with
+ * the stencil re-expressed in the pass's frame (regularized transformation, Sec. II.C),
+ * then the BGK collision with beta = dt / (2 tau + dt).  The corrector readings of the
+ * finite-volume faces apply unchanged (convergence rule, restart from the pooled moments
+ * of the stencil, the last valid pass's moments Grad-projected into the frame they define).
+ * Writes the new populations and frame of the node into fp/gp/un/Tn. */
+static void sl_node(oracle *o, int i, int j, double dt)
+{
+    const lattice *L = &o->L;
+    const int D = o->D, Q = o->Q;
+    const int R = 2, W = 2 * R + 1;              /* stencil i-2..i+2 (and j-2..j+2 in 2D) */
+    const int ny_s = D == 2 ? W : 1;
+    int cells[25];
+    int ns = 0;
+    for (int b = 0; b < ny_s; ++b)
+        for (int a = 0; a < W; ++a) cells[ns++] = cidx(o, i - R + a, D == 2 ? j - R + b : j);
+    const int c0 = cidx(o, i, j);
+    double pf[25][MAXQ], pg[25][MAXQ];
+    double lam_u[MAXD] = {0}, lam_T = o->T[c0];
+    for (int a = 0; a < D; ++a) lam_u[a] = o->u[(size_t)c0 * MAXD + a];
+    double fbar[MAXQ], gbar[MAXQ];
+    double keep_f[MAXQ], keep_g[MAXQ], keep_in_u[MAXD] = {0}, keep_in_T = 0.0;
+    double keep_u[MAXD] = {0}, keep_T = 0.0, keep_rho = 0.0;
+    int have = 0, iters = 0, done = 0, restarted = 0;
+    for (int k = 0; k < o->max_iter && !done; ++k) {
+        for (int s = 0; s < ns; ++s) {
+            int c = cells[s];
+            grad_transform(L, 3, o->f + (size_t)c * Q, o->u + (size_t)c * MAXD, o->T[c], lam_u, lam_T, pf[s]);
+            grad_transform(L, 2, o->g + (size_t)c * Q, o->u + (size_t)c * MAXD, o->T[c], lam_u, lam_T, pg[s]);
+        }
+        const double sq = sqrt(lam_T / L->TL);
+        for (int q = 0; q < Q; ++q) {
+            double v[MAXD];
+            for (int a = 0; a < D; ++a) v[a] = sq * L->c[q][a] + lam_u[a];
+            int bx, by = 0;
+            double thx, thy = 0.0;
+            sl_base(v[0] * dt / o->dx, &bx, &thx);
+            if (D == 2) sl_base(v[1] * dt / o->dy, &by, &thy);
+            for (int pop = 0; pop < 2; ++pop) {
+                double (*P)[MAXQ] = pop == 0 ? pf : pg;
+                double val;
+                if (D == 1) {
+                    double col[4];
+                    for (int m = 0; m < 4; ++m) col[m] = P[R + bx - 1 + m][q];
+                    val = sl_interp(col, thx);
+                } else {
+                    double box[4][4];
+                    for (int r = 0; r < 4; ++r)
+                        for (int m = 0; m < 4; ++m) box[r][m] = P[(R + by - 1 + r) * W + R + bx - 1 + m][q];
+                    val = sl_interp2(box, thx, thy);
+                }
+                if (pop == 0) fbar[q] = val; else gbar[q] = val;
+            }
+        }
+        /* Eqs. (correctorfieldsrho)-(correctorfieldT) */
+        double rho1, mom[MAXD] = {0}, rhoE, u1[MAXD] = {0};
+        conserved_moments(L, fbar, gbar, lam_u, lam_T, &rho1, mom, &rhoE);
+        for (int a = 0; a < D; ++a) u1[a] = mom[a] / rho1;
+        double T1 = temperature_from(rho1, mom, rhoE, D, o->Cv);
+        iters = k + 1;
+        if (!(T1 > 0.0) || bad(rho1) || bad(T1) || bad(u1[0]) || (D == 2 && bad(u1[1]))) {
+            o->fallbacks++;
+            if (!restarted) {
+                restarted = 1;
+                pooled_frame_n(o, cells, ns, lam_u, &lam_T);
+                continue;
+            }
+            break;
+        }
+        memcpy(keep_f, fbar, sizeof(keep_f));
+        memcpy(keep_g, gbar, sizeof(keep_g));
+        for (int a = 0; a < D; ++a) { keep_in_u[a] = lam_u[a]; keep_u[a] = u1[a]; }
+        keep_in_T = lam_T; keep_T = T1; keep_rho = rho1;
+        have = 1;
+        if (o->fixed_iters > 0) {
+            done = iters >= o->fixed_iters;
+        } else {
+            double du = 0.0;
+            for (int a = 0; a < D; ++a) du = fmax(du, fabs(u1[a] - lam_u[a]));
+            done = du <= o->tol * sqrt(lam_T) && fabs(T1 - lam_T) <= o->tol * lam_T;
+        }
+        for (int a = 0; a < D; ++a) lam_u[a] = u1[a];
+        lam_T = T1;
+    }
+    o->face_iters += iters;
+    o->face_count += 1;
+    if (!done) o->nonconv++;
+    if (!have) { o->nonphys++; keep_T = NAN; keep_in_T = NAN; }
+    /* the pre-collision populations in the frame of their own moments, then BGK */
+    double fl[MAXQ], gl[MAXQ], feq[MAXQ], geq[MAXQ];
+    grad_transform(L, 3, keep_f, keep_in_u, keep_in_T, keep_u, keep_T, fl);
+    grad_transform(L, 2, keep_g, keep_in_u, keep_in_T, keep_u, keep_T, gl);
+    equilibria(L, keep_rho, keep_T, o->Cv, feq, geq);
+    const double beta = dt / (2.0 * o->tau + dt);
+    for (int q = 0; q < Q; ++q) {
+        o->fp[(size_t)c0 * Q + q] = fl[q] + 2.0 * beta * (feq[q] - fl[q]);
+        o->gp[(size_t)c0 * Q + q] = gl[q] + 2.0 * beta * (geq[q] - gl[q]);
+    }
+    for (int a = 0; a < D; ++a) o->un[(size_t)c0 * MAXD + a] = keep_u[a];
+    o->Tn[c0] = keep_T;
+}
+
+/* n semi-Lagrangian steps (Sec. III.A); the time step follows the same CFL rule. */
+int oracle_sl_step(oracle *o, int n)
+{
+    const int Q = o->Q, D = o->D;
+    int taken = 0;
+    for (int s = 0; s < n; ++s) {
+        if (o->t_end > 0.0 && o->t >= o->t_end) break;
+        fill_ghosts(o);
+        double dt = o->forced_dt > 0.0 ? o->forced_dt : cfl_dt(o);
+        if (o->t_end > 0.0 && o->t + dt > o->t_end) dt = o->t_end - o->t;
+        for (int j = 0; j < o->ny; ++j)
+            for (int i = 0; i < o->nx; ++i) sl_node(o, i, j, dt);
+        for (int j = 0; j < o->ny; ++j)
+            for (int i = 0; i < o->nx; ++i) {
+                int c = cidx(o, i, j);
+                memcpy(o->f + (size_t)c * Q, o->fp + (size_t)c * Q, sizeof(double) * Q);
+                memcpy(o->g + (size_t)c * Q, o->gp + (size_t)c * Q, sizeof(double) * Q);
+                for (int a = 0; a < D; ++a) o->u[(size_t)c * MAXD + a] = o->un[(size_t)c * MAXD + a];
+                o->T[c] = o->Tn[c];
             }
         o->t += dt;
         o->last_dt = dt;
