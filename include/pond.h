@@ -75,6 +75,14 @@ typedef struct {
     int64_t inflow_hi[4];
 } pond_grid;
 
+/* Time-stepping realizations of Sec. III: the finite-volume scheme (Sec. III.B, the
+ * conservative default) or the semi-Lagrangian one (Sec. III.A: per-node predictor-
+ * corrector on the node's frame, populations advected from their departure points by a
+ * limited 4-point Lagrange interpolation, BGK collision; not conservative).  The
+ * semi-Lagrangian scheme runs on D1Q4 grids; D2Q16 and batches refuse it with
+ * POND_ERR_UNSUPPORTED. */
+typedef enum { POND_FV = 0, POND_SL = 1 } pond_scheme;
+
 typedef struct {
     int precision;              /* pond_precision */
     int limiter;                /* pond_limiter */
@@ -89,6 +97,7 @@ typedef struct {
     void *(*alloc)(size_t bytes, void *ctx);  /* device allocator, or NULL for cudaMalloc */
     void (*free)(void *ptr, void *ctx);
     void *alloc_ctx;
+    int scheme;                 /* pond_scheme (0: finite volume) */
 } pond_options;
 
 typedef struct pond_state pond_state;

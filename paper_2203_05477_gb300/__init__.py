@@ -27,6 +27,7 @@ POND_ERR_NONPHYSICAL, POND_ERR_NOT_CONVERGED, POND_ERR_TIMEOUT = 5, 6, 7
 POND_D1Q3, POND_D1Q4, POND_D2Q16, POND_D2Q9 = 0, 1, 2, 3
 POND_FP64, POND_FP32 = 0, 1
 POND_VANLEER, POND_MINMOD = 0, 1
+POND_FV, POND_SL = 0, 1
 MLP_PARAMS, MLP_FEATURES, MLP_PAIR_STRIDE = 8336, 48, 52
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -46,7 +47,7 @@ class pond_options(ctypes.Structure):
                 ("t_end", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("fixed_iters", ctypes.c_int), ("strict_convergence", ctypes.c_int),
                 ("learned", ctypes.c_int), ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN),
-                ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p)]
+                ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p), ("scheme", ctypes.c_int)]
 
 
 class pond_diag(ctypes.Structure):
@@ -178,7 +179,8 @@ class Solver:
     """One PonD problem on the current CUDA device (see ``inputs.Problem``)."""
 
     def __init__(self, problem, *, tau, cfl, precision="fp64", limiter=POND_VANLEER, t_end=0.0,
-                 tol=None, max_iter=16, fixed_iters=0, strict=False, stream=None, torch_alloc=True):
+                 tol=None, max_iter=16, fixed_iters=0, strict=False, stream=None, torch_alloc=True,
+                 scheme="fv"):
         import torch
         lib = _load()
         self.problem = problem
@@ -208,6 +210,7 @@ class Solver:
         o.max_iter = int(max_iter)
         o.fixed_iters = int(fixed_iters)
         o.strict_convergence = int(bool(strict))
+        o.scheme = POND_SL if scheme in ("sl", POND_SL) else POND_FV
         o.stream = self.stream.cuda_stream
         self._alloc = _TorchAllocator(self.device, self.stream) if torch_alloc else None
         if self._alloc:

@@ -13,12 +13,14 @@
 #include <cmath>
 #include <type_traits>
 #include <new>
+#include <utility>
 #include <vector>
 #include <mutex>
 #include <string>
 
 #include "../../include/pond.h"
 #include "pond_launch.cuh"
+#include "pond_sl.cuh"
 #include "pond_mlp_train.cuh"
 #include "pond_reduce.cuh"
 #include <cuda_bf16.h>
@@ -79,6 +81,10 @@ struct pond_state {
     int sms = 152;
     // kernel variants in use (indices into the lists of pond_launch.cuh), set by the autotuner
     int face_v = 0, cell_v = 0, tube_v = 0;
+    // semi-Lagrangian scheme: the state alternates between the cell planes and the face
+    // planes; sl_parity counts the swaps, graph_parity is the parity a captured graph starts at
+    int scheme = POND_FV;
+    int sl_parity = 0, graph_parity = 0;
     // batched tubes
     bool batch = false;
     int64_t n_tubes = 0, ncell = 0, nface = 0, steps_taken = 0;
@@ -272,10 +278,31 @@ pond_status mlp_setup(pond_state *s)
     return POND_OK;
 }
 
+// one semi-Lagrangian step: the kernel reads the cell planes and writes the face planes,
+// which then become the state (the swap is on the host copy of the parameters, so a
+// captured graph holds both orders alternately)
+constexpr int kSlThreads = 128;
+
+template <typename R>
+void launch_sl(pond_state *s, pond::Params<1, R> &P)
+{
+    pond::sl_kernel<R, kSlThreads><<<blocks_for(P.nx, kSlThreads), kSlThreads, 0, s->stream>>>(P);
+    std::swap(P.sf, P.xf);
+    std::swap(P.sg, P.xg);
+    std::swap(P.sfr, P.xfr);
+    s->sl_parity ^= 1;
+}
+
 template <int D, typename R>
 void launch_step(pond_state *s, bool collect = false)
 {
     auto &P = params_of<D, R>(s);
+    if constexpr (D == 1) {
+        if (s->scheme == POND_SL) {
+            launch_sl<R>(s, P);
+            return;
+        }
+    }
     if constexpr (D == 2) {
         if (s->learned) {
             pond::gauge_predict_kernel<R><<<predict_blocks(s), pond::mlp::kThreads, pond::mlp::kInferSmem, s->stream>>>(P);
@@ -290,8 +317,16 @@ template <int D, typename R>
 pond_status step_impl(pond_state *s, int64_t n_steps)
 {
     int64_t left = n_steps;
+    if (left >= kGraphSteps && s->graph_exec && s->scheme == POND_SL && s->graph_parity != s->sl_parity) {
+        // the graph was captured starting from the other buffer
+        cudaGraphExecDestroy(s->graph_exec);
+        cudaGraphDestroy(s->graph);
+        s->graph_exec = nullptr;
+        s->graph = nullptr;
+    }
     if (left >= kGraphSteps) {
         if (!s->graph_exec) {
+            s->graph_parity = s->sl_parity;
             CUDA_TRY(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
             const int64_t before = s->launches;
             for (int k = 0; k < kGraphSteps; ++k) launch_step<D, R>(s);
@@ -301,7 +336,7 @@ pond_status step_impl(pond_state *s, int64_t n_steps)
             s->graph = g;
             CUDA_TRY(cudaGraphInstantiate(&s->graph_exec, g, 0));
         }
-        const int per_step = 2 + ((D == 2 && s->learned) ? 1 : 0);
+        const int per_step = s->scheme == POND_SL ? 1 : 2 + ((D == 2 && s->learned) ? 1 : 0);
         while (left >= kGraphSteps) {
             CUDA_TRY(cudaGraphLaunch(s->graph_exec, s->stream));
             s->launches += per_step * kGraphSteps;
@@ -311,7 +346,7 @@ pond_status step_impl(pond_state *s, int64_t n_steps)
     for (; left > 0; --left) {
         const int64_t before = s->launches;
         launch_step<D, R>(s);
-        s->launches = before + 2 + ((D == 2 && s->learned) ? 1 : 0);
+        s->launches = before + (s->scheme == POND_SL ? 1 : 2 + ((D == 2 && s->learned) ? 1 : 0));
     }
     CUDA_TRY(cudaGetLastError());
     return POND_OK;
@@ -331,10 +366,20 @@ pond_status step_timed_impl(pond_state *s, int64_t n_steps, double *ms)
                 s->launches += 1;
             }
         }
-        pond::launch_face<D, R>(s->face_v, false, P, s->stream);
-        CUDA_TRY(cudaEventRecord(ev[2 * k + 1], s->stream));
-        pond::launch_cell<D, R>(s->cell_v, P, s->stream);
-        CUDA_TRY(cudaEventRecord(ev[2 * k + 2], s->stream));
+        bool sl = false;
+        if constexpr (D == 1) sl = s->scheme == POND_SL;
+        if (sl) {
+            // the whole semi-Lagrangian step is one kernel: it is timed as the first part
+            if constexpr (D == 1) launch_sl<R>(s, P);
+            CUDA_TRY(cudaEventRecord(ev[2 * k + 1], s->stream));
+            CUDA_TRY(cudaEventRecord(ev[2 * k + 2], s->stream));
+            s->launches -= 1;
+        } else {
+            pond::launch_face<D, R>(s->face_v, false, P, s->stream);
+            CUDA_TRY(cudaEventRecord(ev[2 * k + 1], s->stream));
+            pond::launch_cell<D, R>(s->cell_v, P, s->stream);
+            CUDA_TRY(cudaEventRecord(ev[2 * k + 2], s->stream));
+        }
     }
     s->launches += 2 * n_steps;
     CUDA_TRY(cudaGetLastError());
@@ -698,6 +743,11 @@ pond_status pond_init(const pond_grid *grid, pond_velset velset, double gamma, d
     if (opts->precision != POND_FP32 && opts->precision != POND_FP64) return fail(POND_ERR_INVALID_ARG, "bad precision");
     if (opts->limiter != POND_VANLEER && opts->limiter != POND_MINMOD) return fail(POND_ERR_INVALID_ARG, "bad limiter");
     if (!(opts->cfl > 0.0) || opts->max_iter < 1 || opts->fixed_iters < 0) return fail(POND_ERR_INVALID_ARG, "bad cfl/max_iter/fixed_iters");
+    if (opts->scheme != POND_FV && opts->scheme != POND_SL) return fail(POND_ERR_INVALID_ARG, "bad scheme %d", opts->scheme);
+    if (opts->scheme == POND_SL && D != 1)
+        return fail(POND_ERR_UNSUPPORTED, "the semi-Lagrangian scheme runs on D1Q4 grids only");
+    if (opts->scheme == POND_SL && !(opts->cfl < 1.0))
+        return fail(POND_ERR_INVALID_ARG, "the semi-Lagrangian stencil needs cfl < 1");
     for (int k = 0; k < 4; ++k)
         if (grid->bc[k] < 0 || grid->bc[k] > 3) return fail(POND_ERR_INVALID_ARG, "bad boundary condition on side %d", k);
     if ((grid->bc[0] == POND_BC_PERIODIC) != (grid->bc[1] == POND_BC_PERIODIC) ||
@@ -710,6 +760,7 @@ pond_status pond_init(const pond_grid *grid, pond_velset velset, double gamma, d
     s->grid = *grid;
     if (D == 1) s->grid.ny = 1;
     s->opts = *opts;
+    s->scheme = opts->scheme;
     s->gamma = gamma;
     s->tau = tau;
     cudaError_t e = cudaGetDevice(&s->device);
@@ -782,6 +833,7 @@ pond_status pond_get_face_gauges(pond_state *s, double *xg, double *yg)
 {
     if (pond_status st = check_state(s)) return st;
     if (!xg && !yg) return POND_OK;
+    if (s->scheme == POND_SL) return fail(POND_ERR_UNSUPPORTED, "the semi-Lagrangian scheme has no face frames");
     if (s->batch) return xg ? dispatch_batch(s, [&](auto r) { return batch_face_gauges<decltype(r)>(s, xg, nullptr); }) : POND_OK;
     return dispatch(s, [&](auto d, auto r) { return face_gauges_impl<decltype(d)::value, decltype(r)>(s, xg, yg, nullptr, nullptr); });
 }
@@ -790,6 +842,7 @@ pond_status pond_set_face_gauges(pond_state *s, const double *xg, const double *
 {
     if (pond_status st = check_state(s)) return st;
     if (!xg && !yg) return POND_OK;
+    if (s->scheme == POND_SL) return fail(POND_ERR_UNSUPPORTED, "the semi-Lagrangian scheme has no face frames");
     if (s->batch) return xg ? dispatch_batch(s, [&](auto r) { return batch_face_gauges<decltype(r)>(s, nullptr, xg); }) : POND_OK;
     return dispatch(s, [&](auto d, auto r) { return face_gauges_impl<decltype(d)::value, decltype(r)>(s, nullptr, nullptr, xg, yg); });
 }
@@ -843,6 +896,7 @@ pond_status pond_init_batch(int64_t n_tubes, const int64_t *lengths, const doubl
     if (opts->precision != POND_FP32 && opts->precision != POND_FP64) return fail(POND_ERR_INVALID_ARG, "bad precision");
     if (opts->limiter != POND_VANLEER && opts->limiter != POND_MINMOD) return fail(POND_ERR_INVALID_ARG, "bad limiter");
     if (!(opts->cfl > 0.0) || opts->max_iter < 1 || opts->fixed_iters < 0) return fail(POND_ERR_INVALID_ARG, "bad cfl/max_iter/fixed_iters");
+    if (opts->scheme != POND_FV) return fail(POND_ERR_UNSUPPORTED, "batches run the finite-volume scheme only");
     pond_state *s = new (std::nothrow) pond_state();
     if (!s) return fail(POND_ERR_OOM, "host allocation failed");
     s->batch = true;
@@ -1266,6 +1320,7 @@ void cache_store(const char *path, const std::string &key, const int v[3])
 
 int variant_total(const pond_state *s)
 {
+    if (s->scheme == POND_SL) return 0;
     if (s->batch) return s->prec == POND_FP32 ? pond::tube_variants<float>() : pond::tube_variants<double>();
     int nf = 0;
     if (s->D == 2) nf = s->prec == POND_FP32 ? pond::face_variants<2, float>() : pond::face_variants<2, double>();
@@ -1373,6 +1428,10 @@ pond_status pond_autotune(pond_state *s, int steps, const char *cache_path, pond
     if (pond_status st = check_state(s)) return st;
     if (steps < 1) return fail(POND_ERR_INVALID_ARG, "steps must be at least 1");
     pond_tune_result res{};
+    if (s->scheme == POND_SL) {  // one compiled variant: nothing to choose
+        if (out) *out = res;
+        return POND_OK;
+    }
     const std::string key = tune_key(s);
     int v[3] = {0, 0, 0};
     if (cache_lookup(cache_path, key, v) && pond_set_variants(s, v[0], v[1], v[2]) == POND_OK) {
