@@ -200,11 +200,16 @@ pond_status pond_gauge_collect(pond_state *s, int64_t n_steps, float *pairs, int
 pond_status pond_gauge_train(pond_state *s, const float *pairs, int64_t n, int epochs, int batch, float lr,
                              float *loss_out);
 
-/* Switches the learned predictor on (nonzero) or off for the following steps.  A face
- * keeps its previous frame unless the largest component of the predicted (normalized)
- * correction exceeds `gate` (default 0.01; 0: always use the prediction). */
+/* Switches the learned predictor on (nonzero) or off for the following steps.  The face
+ * corrector starts from the prediction where the largest component of the predicted
+ * (normalized) correction exceeds `gate` (default 0.01) and does not exceed `trust`
+ * (default 0.5: larger moves can lead the corrector to another fixed point).  It keeps the
+ * result only if it converges without a restart; otherwise it solves the face again from
+ * the previous half step's frame, as without the network, so the corrector stays the judge.
+ * Errors: INVALID_ARG for gate < 0 or trust <= 0. */
 pond_status pond_gauge_enable(pond_state *s, int on);
 pond_status pond_gauge_set_gate(pond_state *s, float gate);
+pond_status pond_gauge_set_trust(pond_state *s, float trust);
 
 /* The network as a self-describing byte blob (magic, version, count, parameters) for
  * checkpointing: pond_gauge_save writes it to buf (host) if *size is large enough and

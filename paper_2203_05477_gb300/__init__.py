@@ -106,6 +106,7 @@ def _load():
             "pond_gauge_train": (ctypes.c_int, [vp, vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_float, vp]),
             "pond_gauge_enable": (ctypes.c_int, [vp, ctypes.c_int]),
             "pond_gauge_set_gate": (ctypes.c_int, [vp, ctypes.c_float]),
+            "pond_gauge_set_trust": (ctypes.c_int, [vp, ctypes.c_float]),
             "pond_gauge_set_params": (ctypes.c_int, [vp, vp]),
             "pond_gauge_get_params": (ctypes.c_int, [vp, vp]),
             "pond_gauge_save": (ctypes.c_int, [vp, vp, ctypes.POINTER(ctypes.c_size_t)]),
@@ -340,9 +341,11 @@ class Solver:
                                          float(lr), _ptr(losses)))
         return losses
 
-    def gauge_enable(self, on=True, gate=None):
+    def gauge_enable(self, on=True, gate=None, trust=None):
         if gate is not None:
             _check(self.lib.pond_gauge_set_gate(self.h, float(gate)))
+        if trust is not None:
+            _check(self.lib.pond_gauge_set_trust(self.h, float(trust)))
         _check(self.lib.pond_gauge_enable(self.h, int(bool(on))))
 
     def gauge_params(self):

@@ -145,7 +145,11 @@ pond_status setup(pond_state *s)
     const size_t o_sf = take(sizeof(R) * NFS * n), o_sg = take(sizeof(R) * NGC * n), o_sfr = take(sizeof(W) * (D + 1) * n);
     const size_t o_xf = take(sizeof(R) * NFC * nxf), o_xg = take(sizeof(R) * NGC * nxf), o_xfr = take(sizeof(W) * (D + 1) * nxf);
     size_t o_yf = 0, o_yg = 0, o_yfr = 0;
-    if (D == 2) { o_yf = take(sizeof(R) * NFC * nyf); o_yg = take(sizeof(R) * NGC * nyf); o_yfr = take(sizeof(W) * (D + 1) * nyf); }
+    size_t o_xlr = 0, o_ylr = 0;
+    if (D == 2) {
+        o_yf = take(sizeof(R) * NFC * nyf); o_yg = take(sizeof(R) * NGC * nyf); o_yfr = take(sizeof(W) * (D + 1) * nyf);
+        o_xlr = take(sizeof(W) * (D + 1) * nxf); o_ylr = take(sizeof(W) * (D + 1) * nyf);  // learned predictions
+    }
     const size_t o_clock = take(sizeof(pond::Clock)), o_diag = take(sizeof(pond::Diag));
     size_t stage = 4 * size_t(n);
     stage = std::max<size_t>(stage, size_t(NFC + NGC + D + 1) * size_t(n));
@@ -165,6 +169,8 @@ pond_status setup(pond_state *s)
         P.yf = reinterpret_cast<R *>(s->base + o_yf);
         P.yg = reinterpret_cast<R *>(s->base + o_yg);
         P.yfr = reinterpret_cast<W *>(s->base + o_yfr);
+        P.xlr = reinterpret_cast<W *>(s->base + o_xlr);
+        P.ylr = reinterpret_cast<W *>(s->base + o_ylr);
     }
     P.clock = reinterpret_cast<pond::Clock *>(s->base + o_clock);
     P.diag = reinterpret_cast<pond::Diag *>(s->base + o_diag);
@@ -779,6 +785,7 @@ pond_status pond_init(const pond_grid *grid, pond_velset velset, double gamma, d
             auto wire = [&](auto &P) {
                 P.mlp = s->mlp; P.mlp_err = s->mlp_err; P.pair_count = s->pair_count; P.pair_every = 1;
                 P.gauge_gate = 0.01f;
+                P.gauge_trust = 0.5f;
             };
             if (s->prec == POND_FP32) wire(params_of<2, float>(s));
             else wire(params_of<2, double>(s));
@@ -787,6 +794,10 @@ pond_status pond_init(const pond_grid *grid, pond_velset velset, double gamma, d
     if (st == POND_OK) st = reset_clock(s);
     if (st != POND_OK) { pond_destroy(s); return st; }
     s->learned = D == 2 && opts->learned != 0;
+    if (s->learned) {
+        if (s->prec == POND_FP32) params_of<2, float>(s).use_learned = 1;
+        else params_of<2, double>(s).use_learned = 1;
+    }
     *out = s;
     return POND_OK;
 }
@@ -1076,6 +1087,8 @@ pond_status pond_gauge_enable(pond_state *s, int on)
         if (s->graph) { cudaGraphDestroy(s->graph); s->graph = nullptr; }
     }
     s->learned = on != 0;
+    if (s->prec == POND_FP32) params_of<2, float>(s).use_learned = s->learned;
+    else params_of<2, double>(s).use_learned = s->learned;
     return POND_OK;
 }
 
@@ -1085,6 +1098,17 @@ pond_status pond_gauge_set_gate(pond_state *s, float gate)
     if (!(gate >= 0.f)) return fail(POND_ERR_INVALID_ARG, "gate must be >= 0");
     if (s->prec == POND_FP32) params_of<2, float>(s).gauge_gate = gate;
     else params_of<2, double>(s).gauge_gate = gate;
+    if (s->graph_exec) { cudaGraphExecDestroy(s->graph_exec); s->graph_exec = nullptr; }
+    if (s->graph) { cudaGraphDestroy(s->graph); s->graph = nullptr; }
+    return POND_OK;
+}
+
+pond_status pond_gauge_set_trust(pond_state *s, float trust)
+{
+    if (pond_status st = check_gauge(s)) return st;
+    if (!(trust > 0.f)) return fail(POND_ERR_INVALID_ARG, "trust must be > 0");
+    if (s->prec == POND_FP32) params_of<2, float>(s).gauge_trust = trust;
+    else params_of<2, double>(s).gauge_trust = trust;
     if (s->graph_exec) { cudaGraphExecDestroy(s->graph_exec); s->graph_exec = nullptr; }
     if (s->graph) { cudaGraphDestroy(s->graph); s->graph = nullptr; }
     return POND_OK;

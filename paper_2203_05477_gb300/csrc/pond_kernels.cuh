@@ -170,6 +170,8 @@ struct Params {
     W *xfr;                           // [D+1][nxf]
     R *yf, *yg;
     W *yfr;
+    W *xlr, *ylr;                     // learned predictions per face [D+1][nf] (T not finite: none)
+    int use_learned;                  // the face corrector tries the learned prediction first
     Clock *clock;
     Diag *diag;
     // learned face-gauge predictor: parameters, and sampling of training pairs
@@ -179,6 +181,8 @@ struct Params {
     long long pair_cap;
     int pair_every;
     float gauge_gate;                 // the prediction is used where its largest component exceeds this
+    float gauge_trust;                // ... and does not exceed this (the corrector's basin of the
+                                      // previous frame; larger moves may reach another fixed point)
     unsigned int *mlp_err;
     __host__ __device__ long long ncell() const { return nx * ny; }
     __host__ __device__ long long nxf() const { return (nx + 1) * ny; }
@@ -793,8 +797,49 @@ face_kernel(const Params<D, R> P)
             dref[1] = R(fr_rel(uref[ta], utile[ta]));
             uabs[1] = R(fr_lead(uref[ta]));
         }
-        solve_face<D, R>(cells, swap, dref, uabs, Tp, cfg, o);
-        my_iters = o.iters; my_nonconv = o.done ? 0 : 1; my_fallbacks = o.fallbacks;
+        // With the learned predictor on, the corrector starts from the network's prediction
+        // and keeps that result only if it converges without a restart; otherwise the face
+        // is solved again from the previous half step's frame, exactly as without the
+        // network.  The corrector and its convergence test remain the judge.
+        W base[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) base[a] = uref[a];
+        bool learned_first = false;
+        W lrn[D + 1];
+        if constexpr (D == 2 && !COLLECT) {
+            if (P.use_learned) {
+                const W *Lrm = dir == 0 ? P.xlr : P.ylr;
+#pragma unroll
+                for (int a = 0; a <= D; ++a) lrn[a] = Lrm[a * nf + fidx];
+                const R Tl = R(fr_lead(lrn[D]));
+                learned_first = Tl > R(0) && isfinite(Tl);
+            }
+        }
+        int tot_iters = 0, tot_fallbacks = 0;
+        for (int attempt = learned_first ? 0 : 1; attempt < 2; ++attempt) {
+            const bool from_learned = attempt == 0;
+            R dw[D], uw[D], Tw = Tp;
+#pragma unroll
+            for (int a = 0; a < D; ++a) { dw[a] = dref[a]; uw[a] = uabs[a]; }
+            if (from_learned) {
+                dw[0] = R(fr_rel(lrn[na], utile[na]));
+                uw[0] = R(fr_lead(lrn[na]));
+                if constexpr (D == 2) {
+                    dw[1] = R(fr_rel(lrn[ta], utile[ta]));
+                    uw[1] = R(fr_lead(lrn[ta]));
+                }
+                Tw = R(fr_lead(lrn[D]));
+            }
+            solve_face<D, R>(cells, swap, dw, uw, Tw, cfg, o);
+            tot_iters += o.iters;
+            tot_fallbacks += o.fallbacks;
+            if (from_learned && o.have && o.done && o.fallbacks == 0) {
+#pragma unroll
+                for (int a = 0; a < D; ++a) base[a] = lrn[a];
+                break;
+            }
+        }
+        my_iters = tot_iters; my_nonconv = o.done ? 0 : 1; my_fallbacks = tot_fallbacks;
         if constexpr (COLLECT && D == 2) {
             const unsigned long long hsh = (unsigned long long)(fidx * 2 + dir + 1) * 0x9E3779B97F4A7C15ull ^
                                            (unsigned long long)(K.steps + 1) * 0xBF58476D1CE4E5B9ull;
@@ -826,7 +871,7 @@ face_kernel(const Params<D, R> P)
 #pragma unroll
             for (int k = 0; k < NGC; ++k) Gout[k * nf + fidx] = o.G[k];
 #pragma unroll
-            for (int a = 0; a < D; ++a) Frm[a * nf + fidx] = fr_add(uref[a], o.du[a]);
+            for (int a = 0; a < D; ++a) Frm[a * nf + fidx] = fr_add(base[a], o.du[a]);
             Frm[D * nf + fidx] = fr_word(o.T);
         } else {
             ++my_nonphys;
@@ -1300,18 +1345,24 @@ gauge_predict_kernel(const Params<2, R> P)
         for (int k0 = 0; k0 < mlp::kIn; k0 += 8) mlp::put_bf16x8(sm + mlp::iX, threadIdx.x, k0, mlp::kIn, f + k0);
         float out[mlp::kOutP];
         ok = mlp::forward_infer(sm, tmem, &mbar, phase, out);
-        if (ok && valid && Tp > R(0)) {
+        if (ok && valid) {
+            // the prediction for this step's corrector (T not finite: none, the gate or an
+            // undefined predictor frame); the previous half step's frame stays in place
             const int na = dir, ta = 1 - dir;
             const float y0 = fminf(fmaxf(out[0], -5.f), 5.f), y1 = fminf(fmaxf(out[1], -5.f), 5.f);
             const float y2 = fminf(fmaxf(out[2], -5.f), 5.f);
-            if (fmaxf(fabsf(y0), fmaxf(fabsf(y1), fabsf(y2))) <= P.gauge_gate) continue;
-            const R sq = sqrt(Tp);
-            W *Frm = dir ? P.yfr : P.xfr;
+            const float ymax = fmaxf(fabsf(y0), fmaxf(fabsf(y1), fabsf(y2)));
+            const bool use = Tp > R(0) && ymax > P.gauge_gate && ymax <= P.gauge_trust;
+            W *Lrm = dir ? P.ylr : P.xlr;
             const long long nfd = dir ? nyf : nxf;
-            const W un = fr_add(uref[na], sq * R(y0)), ut = fr_add(uref[ta], sq * R(y1));
-            Frm[na * nfd + fidx] = un;
-            Frm[ta * nfd + fidx] = ut;
-            Frm[2 * nfd + fidx] = fr_word(R(Tp * R(__expf(y2))));
+            if (use) {
+                const R sq = sqrt(Tp);
+                Lrm[na * nfd + fidx] = fr_add(uref[na], sq * R(y0));
+                Lrm[ta * nfd + fidx] = fr_add(uref[ta], sq * R(y1));
+                Lrm[2 * nfd + fidx] = fr_word(R(Tp * R(__expf(y2))));
+            } else {
+                Lrm[2 * nfd + fidx] = fr_word(R(__int_as_float(0x7fc00000)));
+            }
         }
     }
     if (!ok && threadIdx.x == 0) atomicOr(P.mlp_err, 1u);

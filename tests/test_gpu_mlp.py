@@ -124,6 +124,47 @@ def test_learned_predictor_in_the_solver():
         (rel_l1(r, ro), rel_l1(p, po), env_r, env_p)
 
 
+def _run_quadrants(params, steps, gate=None, trust=None, max_iter=16):
+    pb = I.quadrants_2d(48, seed=0)
+    g = pond.Solver(pb, precision="fp32", tau=1e-5, cfl=0.2, max_iter=max_iter)
+    g.set_primitive()
+    if params is not None:
+        g.set_gauge_params(params)
+        g.gauge_enable(True, gate=gate, trust=trust)
+    g.step(steps)
+    d = g.sync()
+    out = g.primitive(), d
+    g.close()
+    return out
+
+
+def test_a_biased_network_cannot_move_the_solution():
+    """A network that predicts the same wrong correction for every face (zero weights, output
+    bias (0.3, -0.2, 0.1) in units of sqrt(T) and log T, inside the trust radius) only moves
+    where the corrector starts.  Faces that converge end where the corrector's fixed point
+    is, and the others are solved again from the previous half step's frame.  On this draw
+    (1500 faces cycle without converging), a face next to a limit cycle can also settle
+    from another start, so the run is held to the method's own stopping-point envelope: how
+    far the plain run moves when max_iter changes by one (measured alongside)."""
+    p = np.zeros(G.NPARAMS, dtype=np.float32)
+    p[G.O_B3:G.O_B3 + 3] = (0.3, -0.2, 0.1)
+    (r0, u0, v0, p0), d0 = _run_quadrants(None, 30)
+    env_r = env_p = 0.0
+    for mi in (15, 17):
+        (re_, _, _, pe_), _ = _run_quadrants(None, 30, max_iter=mi)
+        env_r, env_p = max(env_r, rel_l1(re_, r0)), max(env_p, rel_l1(pe_, p0))
+    (r1, u1, v1, p1), d1 = _run_quadrants(p, 30, gate=0.0)
+    assert d1["status"] == pond.POND_OK and d1["nonphysical"] == 0
+    assert d1["face_iters"] > d0["face_iters"]   # the wrong start costs passes
+    dr, dp = rel_l1(r1, r0), rel_l1(p1, p0)
+    print("biased network: rho %.2e p %.2e; envelope rho %.2e p %.2e" % (dr, dp, env_r, env_p))
+    assert dr <= max(3e-5, 2 * env_r) and dp <= max(3e-5, 2 * env_p), (dr, dp, env_r, env_p)
+    # beyond the trust radius the prediction is not used at all: the run is the plain one
+    p[G.O_B3:G.O_B3 + 3] = (3.0, -2.0, 1.0)
+    (r2, u2, v2, p2), d2 = _run_quadrants(p, 30, gate=0.0)
+    assert np.array_equal(r2, r0) and np.array_equal(p2, p0) and d2["face_iters"] == d0["face_iters"]
+
+
 def test_gauge_blob_round_trip_and_learned_option():
     pb = I.quadrants_2d(32, seed=0)
     a = pond.Solver(pb, precision="fp32", tau=1e-5, cfl=0.2)
