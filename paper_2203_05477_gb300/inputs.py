@@ -307,3 +307,48 @@ def mirror_extend(pb: Problem) -> Problem:
     return Problem(pb.dim, NX, NY if pb.dim == 2 else 1, x0, x1, y0, y1, pb.gamma, rho.ravel(), ux.ravel(),
                    uy.ravel(), p.ravel(), bc=tuple(bc), name=pb.name + "_unfolded")
 
+
+def rankine_hugoniot(mach, rho1, p1, gamma):
+    """(rho2, u2, p2) behind a shock of Mach number `mach` running into gas at rest
+    (rho1, p1): the normal-shock relations of ideal-gas dynamics."""
+    m2 = mach * mach
+    rho2 = rho1 * (gamma + 1.0) * m2 / ((gamma - 1.0) * m2 + 2.0)
+    p2 = p1 * (1.0 + 2.0 * gamma / (gamma + 1.0) * (m2 - 1.0))
+    vs = mach * np.sqrt(gamma * p1 / rho1)
+    return rho2, vs * (1.0 - rho1 / rho2), p2
+
+
+def rmi_2d(kind, nx=600, ny=100):
+    """Richtmyer-Meshkov instability of Sec. IV on [0, 0.6] x [0, 0.1] (the paper runs
+    600 x 100).  kind 1: a Mach-1.2 shock from the light gas into the heavy one (post-shock,
+    light and heavy states split at x = 1/6 and x = 1/4); kind 2: a Mach-2.5 shock from the
+    heavy gas into the light one (split at 1/12 and 1/6).  The interface carries a
+    sinusoidal perturbation of amplitude 0.008; the paper gives no wavelength, and the
+    reading is one cosine period over the height, x_I(y) = x_I + 0.008 cos(2 pi y / 0.1),
+    symmetric about mid-height.  Inflow of the post-shock state on the left side,
+    transmissive elsewhere; gamma = 1.4."""
+    # the post-shock state is the Rankine-Hugoniot state of the shock running into
+    # (1, 0, 0, 1); it reproduces the printed (rho, u) of both types and the printed p of
+    # type 2, while type 1 prints p = 0.151332 for 1.51332 (see rankine_hugoniot)
+    if kind == 1:
+        post = rankine_hugoniot(1.2, 1.0, 1.0, 1.4)
+        states = ((post[0], post[1], 0.0, post[2]), (1.0, 0.0, 0.0, 1.0), (5.04, 0.0, 0.0, 1.0))
+        x_shock, x_int = 1.0 / 6.0, 0.25
+    else:
+        post = rankine_hugoniot(2.5, 1.0, 1.0, 1.4)
+        states = ((post[0], post[1], 0.0, post[2]), (1.0, 0.0, 0.0, 1.0), (0.138, 0.0, 0.0, 1.0))
+        x_shock, x_int = 1.0 / 12.0, 1.0 / 6.0
+    x = cell_centres(nx, 0.0, 0.6)
+    y = cell_centres(ny, 0.0, 0.1)
+    X, Y = np.meshgrid(x, y)
+    xi = x_int + 0.008 * np.cos(2.0 * np.pi * Y / 0.1)
+    region = np.where(X < x_shock, 0, np.where(X < xi, 1, 2)).ravel()
+    S = np.array(states)
+    inflow = np.zeros((4, 4))
+    inflow[0] = states[0]
+    rng = np.zeros((4, 2), dtype=np.int64)
+    rng[0] = (0, ny)
+    return Problem(2, nx, ny, 0.0, 0.6, 0.0, 0.1, 1.4, S[region, 0], S[region, 1], S[region, 2], S[region, 3],
+                   bc=(INFLOW, TRANSMISSIVE, TRANSMISSIVE, TRANSMISSIVE), inflow=inflow, inflow_range=rng,
+                   name="rmi%d_%dx%d" % (kind, nx, ny))
+
