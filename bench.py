@@ -417,7 +417,7 @@ def main():
         "fp64": {"value": fp64_value, "unit": "MLUPS", "steps": args.fp64_steps, "speedup_fp32": value / fp64_value},
         "fp32_learned": learned,
         "autotune": None if tune is None else {
-            "face": variant_names[fv], "cell": variant_names[len(variant_names) - 3 + cv],
+            "face": variant_names[fv], "cell": [n for n in variant_names if n.startswith("cell")][cv],
             "ms_per_launch": tune["ms"],
             "fp64": None if tune64 is None else {"face": tune64["face"], "cell": tune64["cell"]}},
         "corrector": {"passes_per_face": face_passes / max(faces, 1), "status_ok": status_ok},

@@ -1071,8 +1071,8 @@ __device__ __forceinline__ bool cell_finish(const R *H, const R *G, R invTc, R s
 // frame from the conserved moments) and the CFL reduction.  The frame (u, T) advances by
 // increments formed from the Hermite moments relative to the old frame (u' = u + du,
 // T' = T (1 + dT/T)), so no kinetic energy of the frame enters.
-template <int D, typename R, int THREADS>
-__global__ void __launch_bounds__(THREADS)
+template <int D, typename R, int THREADS, int MINB = 1>
+__global__ void __launch_bounds__(THREADS, MINB)
 cell_kernel(const Params<D, R> P)
 {
     constexpr int NFC = NCoef<D, 3>::value, NGC = NCoef<D, 2>::value;

@@ -66,15 +66,18 @@ void launch_face(int v, bool collect, const Params<D, R> &P, cudaStream_t st);
 
 // ---------------------------------------------------------------- cell kernel
 
-constexpr int kCellBlocks[3] = {256, 128, 512};
-constexpr int kCellVariants = 3;
+constexpr int kCellBlocks[5] = {256, 128, 512, 256, 256};
+constexpr int kCellMinBlocks[5] = {1, 1, 1, 3, 4};   // CTAs per SM asked of the register allocator
+constexpr int kCellVariants = 5;
 
 template <int D, typename R>
 void launch_cell(int v, const Params<D, R> &P, cudaStream_t st);
 
 inline void cell_name(int v, char *buf, size_t n)
 {
-    std::snprintf(buf, n, "cell %d threads", kCellBlocks[(v >= 0 && v < kCellVariants) ? v : 0]);
+    const int k = (v >= 0 && v < kCellVariants) ? v : 0;
+    if (kCellMinBlocks[k] > 1) std::snprintf(buf, n, "cell %d threads, %d CTA/SM", kCellBlocks[k], kCellMinBlocks[k]);
+    else std::snprintf(buf, n, "cell %d threads", kCellBlocks[k]);
 }
 
 // ---------------------------------------------------------------- tube kernel

@@ -52,6 +52,8 @@ void launch_cell(int v, const Params<D, R> &P, cudaStream_t st)
     switch (v) {
     case 1: cell_kernel<D, R, 128><<<blocks(128), 128, 0, st>>>(P); break;
     case 2: cell_kernel<D, R, 512><<<blocks(512), 512, 0, st>>>(P); break;
+    case 3: cell_kernel<D, R, 256, 3><<<blocks(256), 256, 0, st>>>(P); break;
+    case 4: cell_kernel<D, R, 256, 4><<<blocks(256), 256, 0, st>>>(P); break;
     default: cell_kernel<D, R, 256><<<blocks(256), 256, 0, st>>>(P); break;
     }
 }
