@@ -373,6 +373,63 @@ __device__ __forceinline__ void cell_maps(R Tc, const R *dc, R Tl, R invTl, R rs
     else Y = X;
 }
 
+// ---- FP32x2 helpers (packed FP32 arithmetic of sm_100 and later: one instruction, two lanes)
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+
+// limited slope of each lane (van Leer or minmod), the products and sums packed
+__device__ __forceinline__ float2 limit2(int kind, float2 a, float2 b)
+{
+    const float2 ab = __fmul2_rn(a, b);
+    if (kind == 1) return make_float2(minmod<float>(a.x, b.x), minmod<float>(a.y, b.y));
+    const float2 den = __fadd2_rn(a, b);
+    const float2 num = __fmul2_rn(bc2(2.f), ab);
+    return make_float2(ab.x > 0.f ? __fdividef(num.x, den.x) : 0.f, ab.y > 0.f ? __fdividef(num.y, den.y) : 0.f);
+}
+
+// The 16 populations of one normal node m at a 2D face (FP32): for each tangential node n,
+// the upwind (u), outer (l), downstream (h) and tangential (-, +) cells' values from their
+// column-collapsed coefficients (C: f, order <= 3; D: g, order <= 2), the limited MUSCL
+// reconstruction at the departure point, and the moments S (f) and SG (g) along the
+// tangent.  Lane x carries f and lane y carries g wherever both have the order.
+__device__ __forceinline__ void pair_populations(const float *Cu, const float *Cl, const float *Ch, const float *Cm,
+                                                 const float *Cp, const float *Du, const float *Dl, const float *Dh,
+                                                 const float *Dm, const float *Dp, float sqTl, float ut_abs, float h_dt,
+                                                 float offn, int limiter, float *S, float *SG)
+{
+    const float2 minus1 = bc2(-1.f);
+    float2 SS[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    float S3 = 0.f;
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+        const float vt = sqTl * float(node_c(n)) + ut_abs;
+        const float offt = -vt * h_dt;
+        float2 u2 = make_float2(0.f, 0.f), l2 = u2, h2 = u2, m2 = u2, p2 = u2;
+#pragma unroll
+        for (int b2 = 0; b2 <= 2; ++b2) {
+            const float2 hn = bc2(float(hen(b2, n)));
+            u2 = __ffma2_rn(make_float2(Cu[b2], Du[b2]), hn, u2);
+            l2 = __ffma2_rn(make_float2(Cl[b2], Dl[b2]), hn, l2);
+            h2 = __ffma2_rn(make_float2(Ch[b2], Dh[b2]), hn, h2);
+            m2 = __ffma2_rn(make_float2(Cm[b2], Dm[b2]), hn, m2);
+            p2 = __ffma2_rn(make_float2(Cp[b2], Dp[b2]), hn, p2);
+        }
+        const float h3 = float(hen(3, n));
+        u2.x += Cu[3] * h3; l2.x += Cl[3] * h3; h2.x += Ch[3] * h3; m2.x += Cm[3] * h3; p2.x += Cp[3] * h3;
+        const float2 ln = limit2(limiter, __ffma2_rn(l2, minus1, u2), __ffma2_rn(u2, minus1, h2));
+        const float2 lt = limit2(limiter, __ffma2_rn(m2, minus1, u2), __ffma2_rn(u2, minus1, p2));
+        const float2 b = __ffma2_rn(bc2(offt), lt, __ffma2_rn(bc2(offn), ln, u2));
+#pragma unroll
+        for (int b2 = 0; b2 <= 2; ++b2) SS[b2] = __ffma2_rn(bc2(float(node_w(n) * he(b2, n))), b, SS[b2]);
+        S3 += float(node_w(n) * he(3, n)) * b.x;
+    }
+#pragma unroll
+    for (int b2 = 0; b2 <= 2; ++b2) {
+        S[b2] = SS[b2].x;
+        SG[b2] = SS[b2].y;
+    }
+    S[3] = S3;
+}
+
 // One corrector pass at a face (Sec. III.B.3) in frame (dl, Tl) (velocity relative to the
 // face reference uref): every stencil cell's phi-bar-plus is re-expressed in that frame,
 // limited slopes are formed per population, each population is reconstructed by MUSCL
@@ -503,6 +560,12 @@ __device__ __forceinline__ void corrector_pass(const StagedCell<D, R> *const *ce
                 Dh[b2] = left ? DR[b2] : DS[0][b2];
             }
             R S[4] = {R(0), R(0), R(0), R(0)}, SG[3] = {R(0), R(0), R(0)};
+            if constexpr (sizeof(R) == 4) {
+                // FP32: the f and g populations run side by side as FP32x2 pairs (lane x: f,
+                // lane y: g), so the shared orders 0..2 take one packed FMA for both
+                pair_populations(Cu, Cl, Ch, CS[1], CS[2], Du, Dl, Dh, DS[1], DS[2], sqTl, ut_abs, h_dt, offn, limiter,
+                                 S, SG);
+            } else {
 #pragma unroll
             for (int n = 0; n < 4; ++n) {
                 const R vt = sqTl * R(node_c(n)) + ut_abs;
@@ -525,6 +588,7 @@ __device__ __forceinline__ void corrector_pass(const StagedCell<D, R> *const *ce
                 for (int b2 = 0; b2 <= 3; ++b2) S[b2] += R(node_w(n) * he(b2, n)) * fb;
 #pragma unroll
                 for (int b2 = 0; b2 <= 2; ++b2) SG[b2] += R(node_w(n) * he(b2, n)) * gb;
+            }
             }
 #pragma unroll
             for (int a2 = 0; a2 <= 3; ++a2)
