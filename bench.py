@@ -5,7 +5,8 @@ Workload: the 2D four-quadrant Riemann problem on the D2Q16 lattice, 1024 x 1024
 the unit square, quadrant states drawn from seed 0 (rho, p log-uniform in [0.1, 10], Mach
 up to 3), gamma 1.4, transmissive boundaries, CFL 0.2.  A step is one full time step of
 the grid (face corrector + cell update).  The headline runs the populations in FP32 (frames
-in FP64); the plain FP64 path is measured on the same GPU and reported beside it.
+as float-float pairs); the plain FP64 path is measured on the same GPU and reported beside
+it.  Before timing, the autotuner picks the face and cell kernel variants on the workload.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -164,7 +165,7 @@ def bench_tubes(args, n_tubes=4096, seed=0, rank=0):
     s.set_primitive(rho, ux, None, p)
     # tuned over the full step count: as tubes stop, the longest tubes set the launch's
     # length, so a short window from the initial state does not rank the variants right
-    tune = None if args.no_tune else s.autotune(steps=args.tube_steps)
+    tune = None if args.no_tune else s.autotune(steps=args.tube_steps, cache=args.tune_cache)
     s.step(max(1, args.warmup))
     d0 = s.sync()
     torch.cuda.synchronize()
@@ -255,6 +256,8 @@ def main():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--tube-steps", type=int, default=100)
     ap.add_argument("--no-tune", action="store_true", help="skip the kernel-variant autotuner (use the defaults)")
+    ap.add_argument("--tune-cache", default=None,
+                    help="autotuner cache file: choices found there are reused without timing (profiling runs)")
     ap.add_argument("--workload", default="quadrants", choices=["quadrants", "tubes"],
                     help="tubes: only the batched-tube measurement (profiling case)")
     ap.add_argument("--quick", action="store_true",
@@ -297,7 +300,7 @@ def main():
     s = pond.Solver(pb, precision="fp32", tau=1e-5, cfl=0.2, max_iter=16)
     s.set_primitive()
     # the autotuner times every compiled face/cell variant on this state and restores it
-    tune = None if args.no_tune else s.autotune(steps=3)
+    tune = None if args.no_tune else s.autotune(steps=3, cache=args.tune_cache)
     fv, cv = (tune["face"], tune["cell"]) if tune else (0, 0)
     variant_names = s.variants()
     s.step(args.warmup)
@@ -383,7 +386,7 @@ def main():
     # ---- plain FP64 on the same GPU
     s3 = pond.Solver(pb, precision="fp64", tau=1e-5, cfl=0.2, max_iter=16)
     s3.set_primitive()
-    tune64 = None if args.no_tune else s3.autotune(steps=2)
+    tune64 = None if args.no_tune else s3.autotune(steps=2, cache=args.tune_cache)
     s3.step(2)
     barrier()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

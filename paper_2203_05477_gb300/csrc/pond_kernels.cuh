@@ -774,12 +774,16 @@ struct FaceVariant {
     static constexpr int THREADS = D == 2 ? 2 * TX_ * TY_ : TX_;
 };
 
-// COLLECT: also write (features, converged frame) pairs of sampled converged faces for the
-// learned predictor (a separate instantiation, so the plain kernel carries none of it)
-template <int D, typename R, bool COLLECT, typename V>
+// Instantiations (MODE): FACE_PLAIN; FACE_COLLECT also writes (features, converged frame)
+// pairs of sampled converged faces for the learned predictor; FACE_LEARNED starts each face
+// from the learned prediction when there is one.  Separate instantiations, so the plain
+// kernel carries neither (and keeps its register budget).
+enum { FACE_PLAIN = 0, FACE_COLLECT = 1, FACE_LEARNED = 2 };
+template <int D, typename R, int MODE, typename V>
 __global__ void __launch_bounds__(V::THREADS, V::MINB)
 face_kernel(const Params<D, R> P)
 {
+    constexpr bool COLLECT = MODE == FACE_COLLECT, LEARNED = MODE == FACE_LEARNED;
     constexpr int TX = V::TX, TY = V::TY;
     constexpr int BX = TX + 3, BY = D == 2 ? TY + 3 : 1;
     constexpr int NFC = NCoef<D, 3>::value, NGC = NCoef<D, 2>::value;
@@ -870,7 +874,7 @@ face_kernel(const Params<D, R> P)
         for (int a = 0; a < D; ++a) base[a] = uref[a];
         bool learned_first = false;
         W lrn[D + 1];
-        if constexpr (D == 2 && !COLLECT) {
+        if constexpr (D == 2 && LEARNED) {
             if (P.use_learned) {
                 const W *Lrm = dir == 0 ? P.xlr : P.ylr;
 #pragma unroll

@@ -59,10 +59,23 @@ struct FaceNames<D, R, VList<Vs...>> {
 template <int D, typename R>
 constexpr int face_variants() { return FaceList<D, R>::type::size; }
 
-// the face kernel of variant v; with collect, the pair-collecting kernel of variant 0
-// (defined in pond_variants.cuh, instantiated in the pond_v*.cu translation units)
+// the face kernel of variant v in one mode (FACE_PLAIN, FACE_COLLECT: variant 0 only,
+// FACE_LEARNED: D2Q16 only), defined in pond_variants.cuh and instantiated in the pond_v*.cu
+// translation units
+template <int D, typename R, int MODE>
+void launch_face_m(int v, const Params<D, R> &P, cudaStream_t st);
+
+// the face kernel of variant v: pair-collecting with collect, else learned when the
+// parameters ask for the learned predictor, else plain
 template <int D, typename R>
-void launch_face(int v, bool collect, const Params<D, R> &P, cudaStream_t st);
+inline void launch_face(int v, bool collect, const Params<D, R> &P, cudaStream_t st)
+{
+    if constexpr (D == 2) {
+        if (collect) return launch_face_m<D, R, FACE_COLLECT>(0, P, st);
+        if (P.use_learned) return launch_face_m<D, R, FACE_LEARNED>(v, P, st);
+    }
+    launch_face_m<D, R, FACE_PLAIN>(v, P, st);
+}
 
 // ---------------------------------------------------------------- cell kernel
 

@@ -7,40 +7,40 @@
 
 namespace pond {
 
-template <int D, typename R, bool COLLECT, typename V>
+template <int D, typename R, int MODE, typename V>
 void launch_face_one(const Params<D, R> &P, cudaStream_t st)
 {
     const dim3 g(unsigned((P.nx + 1 + V::TX - 1) / V::TX), D == 2 ? unsigned((P.ny + 1 + V::TY - 1) / V::TY) : 1u);
-    face_kernel<D, R, COLLECT, V><<<g, V::THREADS, 0, st>>>(P);
+    face_kernel<D, R, MODE, V><<<g, V::THREADS, 0, st>>>(P);
 }
 
-template <int D, typename R, typename V, typename... Rest>
+template <int D, typename R, int MODE, typename V, typename... Rest>
 void launch_face_at(int v, const Params<D, R> &P, cudaStream_t st)
 {
     if constexpr (sizeof...(Rest) == 0) {
-        launch_face_one<D, R, false, V>(P, st);
+        launch_face_one<D, R, MODE, V>(P, st);
     } else {
-        if (v <= 0) launch_face_one<D, R, false, V>(P, st);
-        else launch_face_at<D, R, Rest...>(v - 1, P, st);
+        if (v <= 0) launch_face_one<D, R, MODE, V>(P, st);
+        else launch_face_at<D, R, MODE, Rest...>(v - 1, P, st);
     }
 }
 
-template <int D, typename R, typename L>
+template <int D, typename R, int MODE, typename L>
 struct FaceLaunch;
-template <int D, typename R, typename... Vs>
-struct FaceLaunch<D, R, VList<Vs...>> {
-    static void launch(int v, const Params<D, R> &P, cudaStream_t st) { launch_face_at<D, R, Vs...>(v, P, st); }
+template <int D, typename R, int MODE, typename... Vs>
+struct FaceLaunch<D, R, MODE, VList<Vs...>> {
+    static void launch(int v, const Params<D, R> &P, cudaStream_t st) { launch_face_at<D, R, MODE, Vs...>(v, P, st); }
 };
 
-// the face kernel of variant v; with collect, the pair-collecting kernel of variant 0
-template <int D, typename R>
-void launch_face(int v, bool collect, const Params<D, R> &P, cudaStream_t st)
+// the face kernel of variant v in one mode; the pair-collecting kernel exists for variant 0
+template <int D, typename R, int MODE>
+void launch_face_m(int v, const Params<D, R> &P, cudaStream_t st)
 {
-    if (collect) {
+    if constexpr (MODE == FACE_COLLECT) {
         using V0 = FaceVariant<D, D == 2 ? 32 : 128, 4, D == 2 && sizeof(R) == 4 ? 2 : 1>;
-        launch_face_one<D, R, true, V0>(P, st);
+        launch_face_one<D, R, FACE_COLLECT, V0>(P, st);
     } else {
-        FaceLaunch<D, R, typename FaceList<D, R>::type>::launch(v, P, st);
+        FaceLaunch<D, R, MODE, typename FaceList<D, R>::type>::launch(v, P, st);
     }
 }
 
