@@ -33,10 +33,13 @@ METRIC = "cell-updates/s (MLUPS) and % HBM roofline, FP32+learned vs plain FP64,
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 N_SMS, FP32_LANES = 152, 128
+# ncu dram read + write of one face-kernel launch at 1024^2, for the tile variants measured
+# on the current kernel (profiles/face_kernel_quadrants1024_fp32.md); other variants: null
+FACE_KERNEL_DRAM_BYTES = {1: 136.3e6 + 178.1e6}
 # FP32 operations (FMA = 2) of one corrector pass at one D2Q16 face (per-face overhead
-# included), from the ncu instruction counts of the face kernel; used for the ALU roofline
-# ncu dram read + write of one face-kernel launch at 1024^2, per tile variant measured
-FACE_KERNEL_DRAM_BYTES = {0: 137.0e6 + 176.1e6, 1: 136.4e6 + 179.6e6}
+# included), from the ncu instruction counts of the scalar face kernel; used for the ALU
+# roofline.  The packed FP32x2 form of the same algorithm executes ~4% more (differences
+# formed as fused multiply-adds by -1), which is not counted.
 FLOPS_PER_FACE_PASS = 4550.0
 # algorithmic bytes per cell-update of the FP32 D2Q16 layout: the face kernel reads the
 # cell state (8 + 6 FP32 coefficients + 3 float-float frame words = 80 B) and two face predictors
