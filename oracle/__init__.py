@@ -73,6 +73,9 @@ def _load():
         lib.oracle_limiter.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double]
         lib.oracle_limiter.restype = ctypes.c_double
         lib.oracle_force_dt.argtypes = [ctypes.c_void_p, ctypes.c_double]
+        lib.oracle_set_equilibration.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        lib.oracle_grad_transform_eq.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_double,
+                                                 dp, ctypes.c_double, dp]
         _lib = lib
         return lib
 
@@ -104,6 +107,20 @@ def grad_transform(D: int, order: int, f_in, u_in, T_in: float, u_out, T_out: fl
     ui = _f64(np.atleast_1d(u_in))
     uo = _f64(np.atleast_1d(u_out))
     lib.oracle_grad_transform(D, order, _dp(f_in), _dp(ui), float(T_in), _dp(uo), float(T_out), _dp(out))
+    return out
+
+
+def regularized_transform(D: int, order: int, f_in, u_in, T_in: float, u_out, T_out: float,
+                          equilibrate: bool) -> np.ndarray:
+    """The regularized transformation with Grad's projection (equilibrate False, as
+    grad_transform) or with the fast moments set to the equilibrium's (Sec. II.C)."""
+    lib = _load()
+    f_in = _f64(f_in)
+    out = np.zeros_like(f_in)
+    ui = _f64(np.atleast_1d(u_in))
+    uo = _f64(np.atleast_1d(u_out))
+    lib.oracle_grad_transform_eq(D, order, int(bool(equilibrate)), _dp(f_in), _dp(ui), float(T_in), _dp(uo),
+                                 float(T_out), _dp(out))
     return out
 
 
@@ -210,6 +227,10 @@ class Solver:
     def force_dt(self, dt: float):
         """Test hook: fixed time step instead of the CFL rule (dt <= 0 restores it)."""
         self.lib.oracle_force_dt(self.h, float(dt))
+
+    def set_equilibration(self, on: bool):
+        """Ablation: the equilibration alternative of Sec. II.C in every transformation."""
+        self.lib.oracle_set_equilibration(self.h, int(bool(on)))
 
     def stats(self):
         t = np.zeros(1); dt = np.zeros(1)

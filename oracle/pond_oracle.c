@@ -22,6 +22,7 @@
  *                   and Eq. (fluxEq);
  *   - step order:   the algorithm summary of Sec. III.B.4;
  *   - time step:    CFL = max|v_ia| dt/dx (Sec. IV);
+ *   - ablation:     the equilibration alternative of Sec. II.C (oracle_set_equilibration);
  *   - SL step:      the semi-Lagrangian realization of Sec. III.A (oracle_sl_step):
  *                   Eqs. (advectionPond)-(advectionPondg), (correctorfieldsrho)-
  *                   (correctorfieldT) and the BGK collision with beta.
@@ -60,6 +61,7 @@ typedef struct {
     double TL;
     double c[MAXQ][MAXD];
     double W[MAXQ];
+    int equilibrate;   /* 0: Grad's projection (the paper's choice); 1: the equilibration alternative */
 } lattice;
 
 /* Table I: D1Q4 nodes +-sqrt(3 -+ sqrt 6) with weights (3 +- sqrt 6)/12, T_L = 1.
@@ -143,6 +145,22 @@ static void grad_transform(const lattice *L, int order, const double *f_in,
                                    - M0 * up[a] * up[b] * up[c]) / (r * r * r);
                 }
     }
+    /* The equilibration alternative of Sec. II.C (an ablation; the paper uses Grad's
+     * projection): the slow moments (orders <= order) are kept as above, and the fast ones
+     * -- here the tensor Hermite components He_r(c_x) He_s(c_y) with r, s <= 3 and
+     * r + s > order, which D2Q16 carries beyond the slow set -- take the values of the
+     * equilibrium with the same zeroth and first moments in the new frame, M0 d_x^r d_y^s
+     * with d = (M1/M0 - u') / sqrt(T'/T_L) (the Hermite coefficients of a Maxwellian of
+     * temperature T' shifted by d).  D1Q4 carries no fast f moment; its g has the order-3 one. */
+    double fast[4][4];
+    memset(fast, 0, sizeof(fast));
+    if (L->equilibrate) {
+        double d[MAXD] = {0};
+        for (int a = 0; a < D; ++a) d[a] = (M1[a] / M0 - up[a]) / r;
+        for (int rr = 0; rr <= 3; ++rr)
+            for (int ss = 0; ss <= (D == 2 ? 3 : 0); ++ss)
+                if (rr + ss > order) fast[rr][ss] = M0 * pow(d[0], rr) * (D == 2 ? pow(d[1], ss) : 1.0);
+    }
     /* Eq. (f_transformed) */
     for (int i = 0; i < Q; ++i) {
         const double *c = L->c[i];
@@ -157,7 +175,18 @@ static void grad_transform(const lattice *L, int order, const double *f_in,
                                               - TL * (c[a] * kd(b, cc) + c[b] * kd(a, cc) + c[cc] * kd(a, b)));
             }
         }
-        f_out[i] = L->W[i] * (a0 + s1 / TL + s2 / (2.0 * TL * TL) + s3 / (6.0 * TL * TL * TL));
+        double sf = 0.0;
+        if (L->equilibrate) {
+            /* probabilists' Hermite polynomials He_0..He_3 over k! at the node (T_L = 1) */
+            const double hx[4] = {1.0, c[0], (c[0] * c[0] - 1.0) / 2.0, (c[0] * c[0] * c[0] - 3.0 * c[0]) / 6.0};
+            double hy[4] = {1.0, 0.0, 0.0, 0.0};
+            if (D == 2) {
+                hy[1] = c[1]; hy[2] = (c[1] * c[1] - 1.0) / 2.0; hy[3] = (c[1] * c[1] * c[1] - 3.0 * c[1]) / 6.0;
+            }
+            for (int rr = 0; rr <= 3; ++rr)
+                for (int ss = 0; ss <= 3; ++ss) sf += fast[rr][ss] * hx[rr] * hy[ss];
+        }
+        f_out[i] = L->W[i] * (a0 + s1 / TL + s2 / (2.0 * TL * TL) + s3 / (6.0 * TL * TL * TL) + sf);
     }
 }
 
@@ -1015,3 +1044,17 @@ double oracle_limiter(int kind, double a, double b) { return limiter(kind, a, b)
 /* Test hook: use this time step instead of the CFL one (dt <= 0 restores the CFL rule).
  * Lets a test run one step of a patch cut out of a larger grid with the larger grid's dt. */
 void oracle_force_dt(oracle *o, double dt) { o->forced_dt = dt; }
+
+/* Ablation switch: 1 replaces Grad's projection in every regularized transformation by
+ * the equilibration of the fast moments (Sec. II.C); 0 restores Grad's. */
+void oracle_set_equilibration(oracle *o, int on) { o->L.equilibrate = on != 0; }
+
+/* The regularized transformation alone (test hook), with the equilibration variant. */
+void oracle_grad_transform_eq(int D, int order, int equilibrate, const double *f_in, const double *u_in, double T_in,
+                              const double *u_out, double T_out, double *f_out)
+{
+    lattice L;
+    lattice_init(&L, D);
+    L.equilibrate = equilibrate;
+    grad_transform(&L, order, f_in, u_in, T_in, u_out, T_out, f_out);
+}
