@@ -3,7 +3,7 @@
 // Each CTA owns one tube for the whole run and loops over the time steps itself: the
 // tube's time step comes from its own CFL maximum (a CTA reduction), so tubes never wait
 // on one another and no inter-CTA synchronization exists.  Per step the tube is streamed
-// in chunks of THREADS - 1 cells: the chunk and a halo of two cells are staged in shared memory
+// in chunks of THREADS - 4 cells: the chunk and a halo of two cells are staged in shared memory
 // (phi-bar-plus, Eq. Fbarplus), the face corrector (Sec. III.B.3) writes the face
 // populations to shared memory, and the cell update (Eqs. fluxEq, FinalUpdateDUGKS, with
 // the re-expression in the new co-moving frame) writes the new state into the other of two
@@ -76,13 +76,14 @@ struct TubeStep {
     R cp, ce, wb, we, ca, cb, h_dx, dt_dx, inv_dx;
 };
 
-// THREADS threads per tube, chunks of THREADS - 1 cells (THREADS faces: one per thread),
+// THREADS threads per tube, chunks of THREADS - 4 cells (the chunk and its halo take one staging
+// load per thread; THREADS - 3 faces, one per thread),
 // MINB CTAs per SM for the register budget; the autotuner picks the variant
 template <typename R, int THREADS, int MINB>
 __global__ void __launch_bounds__(THREADS, MINB)
 tube_kernel(const TubeParams<R> P, int steps, int cur0)
 {
-    constexpr int kChunk = THREADS - 1;
+    constexpr int kChunk = THREADS - 4;  // the chunk and its 4 halo cells: one staging load per thread
     __shared__ StagedCell<1, R> tile[kChunk + 4];
     using CellW = typename FrameWords<R>::word;
     __shared__ R faceF[kChunk + 1][4];
