@@ -207,9 +207,9 @@ unsigned blocks_for(long long n, int threads) { return unsigned((n + threads - 1
 // persistent CTAs of the learned predictor: kInferCtasPerSm per SM, at most one per tile
 unsigned predict_blocks(const pond_state *s)
 {
-    const long long nf = (s->grid.nx + 1) * s->grid.ny + s->grid.nx * (s->grid.ny + 1);
-    const long long tiles = (nf + pond::mlp::kRows - 1) / pond::mlp::kRows;
-    return unsigned(std::min<long long>(tiles, (long long)pond::mlp::kInferCtasPerSm * s->sms));
+    const long long nbx = (s->grid.nx + 1 + pond::kPredTX - 1) / pond::kPredTX;
+    const long long nby = (s->grid.ny + 1 + pond::kPredTY - 1) / pond::kPredTY;
+    return unsigned(std::min<long long>(nbx * nby, (long long)pond::mlp::kInferCtasPerSm * s->sms));
 }
 
 template <int D, typename R>

@@ -1327,21 +1327,29 @@ __global__ void init_faces_kernel(const Params<D, R> P)
 
 // ------------------------------------------------------- learned gauge predictor
 
-// Before the face corrector of a step: every face's predictor frame is replaced by the
-// learned prediction of its converged frame (features as in mlp::features).  Persistent
-// CTAs (mlp::kInferCtasPerSm per SM) stage the network once and loop over tiles of 128
-// faces; the features are formed in FP32 from the frame words.
+// Before the face corrector of a step: the learned prediction of every face's converged
+// frame (features as in mlp::features), written beside the previous half step's frame.
+// Persistent CTAs (mlp::kInferCtasPerSm per SM) stage the network once and loop over tiles
+// of 16 x 4 cells: the 64 x-faces and 64 y-faces of a tile are the 128 rows of one MLP tile
+// (the face kernel's mapping), and the (16+3) x (4+3) cells they read are staged once in
+// shared memory as (rho, velocity relative to the tile's reference, T) in FP32.
+constexpr int kPredTX = 16, kPredTY = 4;
+static_assert(2 * kPredTX * kPredTY == mlp::kRows, "one face per MLP row");
+
 template <typename R>
 __global__ void __launch_bounds__(mlp::kThreads, mlp::kInferCtasPerSm)
 gauge_predict_kernel(const Params<2, R> P)
 {
     using W = typename FrameWords<R>::word;
+    constexpr int BX = kPredTX + 3, BY = kPredTY + 3;
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ uint64_t mbar;
     __shared__ uint32_t tmem_base;
+    __shared__ float4 box[BY * BX];   // rho, u - u_ref, v - v_ref, T
+    __shared__ W uref_tile[2];
     const Clock &K = *P.clock;
     if (!(K.dt > 0.0)) return;
-    const long long nxf = P.nxf(), nyf = P.nyf(), nf = nxf + nyf, n = P.ncell();
+    const long long nxf = P.nxf(), nyf = P.nyf(), n = P.ncell();
     if (threadIdx.x < 32) tc::tmem_alloc(&tmem_base, mlp::kInferTmemCols);
     if (threadIdx.x == 0) tc::mbar_init(&mbar, 1);
     mlp::stage_infer(P.mlp, sm);
@@ -1351,58 +1359,70 @@ gauge_predict_kernel(const Params<2, R> P)
     const uint32_t tmem = tmem_base;
     uint32_t phase = 0;
     bool ok = true;
-    const long long ntiles = (nf + mlp::kRows - 1) / mlp::kRows;
-    for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        const long long t = tile * mlp::kRows + threadIdx.x;
-        const bool valid = t < nf;
-        float f[mlp::kIn];
+    const int nbx = int((P.nx + 1 + kPredTX - 1) / kPredTX), nby = int((P.ny + 1 + kPredTY - 1) / kPredTY);
+    const int ntiles = nbx * nby;
+    // this thread's face within a tile
+    const int dir = threadIdx.x >= kPredTX * kPredTY ? 1 : 0;
+    const int tl = threadIdx.x - dir * kPredTX * kPredTY, tx = tl % kPredTX, ty = tl / kPredTX;
+    const int na = dir, ta = 1 - dir;
+    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const long long i0 = (long long)(tile % nbx) * kPredTX, j0 = (long long)(tile / nbx) * kPredTY;
+        if (threadIdx.x == 0) cell_velocity<2, R>(P, i0, j0, uref_tile);
+        __syncthreads();
+        for (int t = threadIdx.x; t < BX * BY; t += blockDim.x) {
+            const long long ci = i0 - 2 + t % BX, cj = j0 - 2 + t / BX;
+            long long idx = 0;
+            int flip = 0;
+            const int side = resolve(P, ci, cj, &idx, &flip);
+            W u[2];
+            float rho, T;
+            if (side >= 0) {
+                rho = float(P.inflow[side][0]);
+                fr_store(u[0], P.inflow[side][1]);
+                fr_store(u[1], P.inflow[side][2]);
+                T = float(P.inflow[side][3] / P.inflow[side][0]);
+            } else {
+                rho = float(P.sf[idx]);
+                u[0] = P.sfr[idx];
+                u[1] = P.sfr[n + idx];
+                T = float(fr_lead(P.sfr[2 * n + idx]));
+            }
+            if (flip & 1) u[0] = fr_neg(u[0]);
+            if (flip & 2) u[1] = fr_neg(u[1]);
+            box[t] = make_float4(rho, float(fr_rel(u[0], uref_tile[0])), float(fr_rel(u[1], uref_tile[1])), T);
+        }
+        __syncthreads();
+        const long long fi = i0 + tx, fj = j0 + ty;
+        const bool valid = dir == 0 ? (fi <= P.nx && fj < P.ny) : (fi < P.nx && fj <= P.ny);
+        const long long fidx = dir == 0 ? fj * (P.nx + 1) + fi : fj * P.nx + fi;
+        const long long nfd = dir ? nyf : nxf;
+        W *Frm = dir ? P.yfr : P.xfr;
         W uref[2];
         R Tp = R(0);
-        int dir = 0;
-        long long fidx = 0;
+        float f[mlp::kIn];
         if (valid) {
-            dir = t < nxf ? 0 : 1;
-            fidx = dir ? t - nxf : t;
-            long long ci[8], cj[8];
-            if (dir == 0) {
-                const long long i = fidx % (P.nx + 1), j = fidx / (P.nx + 1);
-                const int di[8] = {-2, -1, 0, 1, -1, -1, 0, 0}, dj[8] = {0, 0, 0, 0, -1, 1, -1, 1};
-#pragma unroll
-                for (int q = 0; q < 8; ++q) { ci[q] = i + di[q]; cj[q] = j + dj[q]; }
-            } else {
-                const long long i = fidx % P.nx, j = fidx / P.nx;
-                const int di[8] = {0, 0, 0, 0, -1, 1, -1, 1}, dj[8] = {-2, -1, 0, 1, -1, -1, 0, 0};
-#pragma unroll
-                for (int q = 0; q < 8; ++q) { ci[q] = i + di[q]; cj[q] = j + dj[q]; }
-            }
-            const W *Frm = dir ? P.yfr : P.xfr;
-            const long long nfd = dir ? nyf : nxf;
             uref[0] = Frm[fidx];
             uref[1] = Frm[nfd + fidx];
             Tp = R(fr_lead(Frm[2 * nfd + fidx]));
-            const int na = dir, ta = 1 - dir;
+            const float dref[2] = {float(fr_rel(uref[0], uref_tile[0])), float(fr_rel(uref[1], uref_tile[1]))};
+            // stencil slots LL, L, R, RR, L-t, L+t, R-t, R+t in box coordinates (x, y)
+            const int bx0 = tx + 2, by0 = ty + 2;
+            int sx[8], sy[8];
+            if (dir == 0) {
+                const int ox[8] = {-2, -1, 0, 1, -1, -1, 0, 0}, oy[8] = {0, 0, 0, 0, -1, 1, -1, 1};
+#pragma unroll
+                for (int q = 0; q < 8; ++q) { sx[q] = bx0 + ox[q]; sy[q] = by0 + oy[q]; }
+            } else {
+                const int ox[8] = {0, 0, 0, 0, -1, 1, -1, 1}, oy[8] = {-2, -1, 0, 1, -1, -1, 0, 0};
+#pragma unroll
+                for (int q = 0; q < 8; ++q) { sx[q] = bx0 + ox[q]; sy[q] = by0 + oy[q]; }
+            }
             mlp::SlotPrim sp[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-                long long idx = 0;
-                int flip = 0;
-                const int side = resolve(P, ci[q], cj[q], &idx, &flip);
-                W u[2];
-                float rho, T;
-                if (side >= 0) {
-                    rho = float(P.inflow[side][0]);
-                    fr_store(u[0], P.inflow[side][1]);
-                    fr_store(u[1], P.inflow[side][2]);
-                    T = float(P.inflow[side][3] / P.inflow[side][0]);
-                } else {
-                    rho = float(P.sf[idx]);
-                    u[0] = P.sfr[idx];
-                    u[1] = P.sfr[n + idx];
-                    T = float(fr_lead(P.sfr[2 * n + idx]));
-                }
-                if (flip & 1) u[0] = fr_neg(u[0]);
-                if (flip & 2) u[1] = fr_neg(u[1]);
-                sp[q] = {rho, float(fr_rel(u[na], uref[na])), float(fr_rel(u[ta], uref[ta])), T};
+                const float4 c = box[sy[q] * BX + sx[q]];
+                const float du[2] = {c.y - dref[0], c.z - dref[1]};
+                sp[q] = {c.x, du[na], du[ta], c.w};
             }
             mlp::features(sp, float(Tp), dir ? K.kf.h_dy : K.kf.h_dx, f);
         } else {
@@ -1416,13 +1436,11 @@ gauge_predict_kernel(const Params<2, R> P)
         if (ok && valid) {
             // the prediction for this step's corrector (T not finite: none, the gate or an
             // undefined predictor frame); the previous half step's frame stays in place
-            const int na = dir, ta = 1 - dir;
             const float y0 = fminf(fmaxf(out[0], -5.f), 5.f), y1 = fminf(fmaxf(out[1], -5.f), 5.f);
             const float y2 = fminf(fmaxf(out[2], -5.f), 5.f);
             const float ymax = fmaxf(fabsf(y0), fmaxf(fabsf(y1), fabsf(y2)));
             const bool use = Tp > R(0) && ymax > P.gauge_gate && ymax <= P.gauge_trust;
             W *Lrm = dir ? P.ylr : P.xlr;
-            const long long nfd = dir ? nyf : nxf;
             if (use) {
                 const R sq = sqrt(Tp);
                 Lrm[na * nfd + fidx] = fr_add(uref[na], sq * R(y0));
