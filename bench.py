@@ -191,28 +191,36 @@ def bench_tubes(args, n_tubes=4096, seed=0, rank=0):
     return out
 
 
-def bench_sl_vs_fv(args, n=1 << 22, steps=200, seed=0, rank=0):
-    """The paper's cost comparison of its two realizations (Sec. IV: the finite-volume step
-    costs about 20% more than the semi-Lagrangian one): the same D1Q4 problem (a smooth
-    periodic field of 4 M cells) advanced by each scheme in FP32, device time per step."""
-    import torch
+def time_schemes(pb, cfl, steps):
     import paper_2203_05477_gb300 as pond
-    from paper_2203_05477_gb300 import inputs as I
-    pb = I.smooth_periodic(1, n, 1, seed=replica_seed(seed, rank), amp=0.15)
-    out = {"workload": "smooth_periodic_1d_%d" % n, "steps": steps}
+    out = {}
     for scheme in ("fv", "sl"):
-        s = pond.Solver(pb, precision="fp32", tau=1e-5, cfl=0.3, max_iter=16, scheme=scheme)
+        s = pond.Solver(pb, precision="fp32", tau=1e-5, cfl=cfl, max_iter=16, scheme=scheme)
         s.set_primitive()
         s.step(5)
         d0 = s.sync()
         ms = s.step_timed(steps)
         d1 = s.sync()
         t = (ms[0] + ms[1]) / steps
-        out[scheme] = {"ms_per_step": t, "mlups": n / (t * 1e-3) / 1e6,
+        out[scheme] = {"ms_per_step": t, "mlups": pb.ncell / (t * 1e-3) / 1e6,
                        "passes": (d1["face_iters"] - d0["face_iters"]) / max(1, d1["face_solves"] - d0["face_solves"]),
                        "status_ok": d1["status"] == pond.POND_OK}
         s.close()
     out["fv_over_sl"] = out["fv"]["ms_per_step"] / out["sl"]["ms_per_step"]
+    return out
+
+
+def bench_sl_vs_fv(args, seed=0, rank=0):
+    """The paper's cost comparison of its two realizations (Sec. IV: the finite-volume step
+    costs about 20% more than the semi-Lagrangian one): the same smooth periodic field
+    advanced by each scheme in FP32, device time per step, on D1Q4 (4 M cells, 200 steps)
+    and on D2Q16 (1024 x 1024 cells, 50 steps)."""
+    from paper_2203_05477_gb300 import inputs as I
+    n1, n2 = 1 << 22, 1024
+    out = {"d1": {"workload": "smooth_periodic_1d_%d" % n1, "steps": 200},
+           "d2": {"workload": "smooth_periodic_2d_%dx%d" % (n2, n2), "steps": 50}}
+    out["d1"].update(time_schemes(I.smooth_periodic(1, n1, 1, seed=replica_seed(seed, rank), amp=0.15), 0.3, 200))
+    out["d2"].update(time_schemes(I.smooth_periodic(2, n2, n2, seed=replica_seed(seed, rank), amp=0.15), 0.2, 50))
     return out
 
 

@@ -14,7 +14,7 @@ LIB = os.path.join(HERE, "libpond.so")
 OBJ = os.path.join(HERE, "_build")
 SOURCES = ["pond_api.cu", "pond_v2f.cu", "pond_v2f_learned.cu", "pond_v2d.cu", "pond_v1.cu", "pond_vtube.cu"]
 HEADERS = ["pond_core.cuh", "pond_kernels.cuh", "pond_batch.cuh", "pond_launch.cuh", "pond_variants.cuh",
-           "pond_tc.cuh", "pond_mlp.cuh", "pond_mlp_train.cuh", "pond_reduce.cuh", "pond_sl.cuh"]
+           "pond_tc.cuh", "pond_mlp.cuh", "pond_mlp_train.cuh", "pond_reduce.cuh", "pond_sl.cuh", "pond_sl2.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC"]
 

@@ -20,7 +20,7 @@
 
 #include "../../include/pond.h"
 #include "pond_launch.cuh"
-#include "pond_sl.cuh"
+#include "pond_sl2.cuh"
 #include "pond_mlp_train.cuh"
 #include "pond_reduce.cuh"
 #include <cuda_bf16.h>
@@ -289,10 +289,24 @@ pond_status mlp_setup(pond_state *s)
 // captured graph holds both orders alternately)
 constexpr int kSlThreads = 128;
 
+// D2Q16: tiles of 8 x 8 nodes (FP32) or 8 x 4 (FP64), the per-thread scratch of 140
+// collapsed coefficients in dynamic shared memory
 template <typename R>
-void launch_sl(pond_state *s, pond::Params<1, R> &P)
+struct Sl2Tile {
+    static constexpr int TX = 8, TY = sizeof(R) == 4 ? 8 : 4;
+    static constexpr size_t scratch = size_t(TX) * TY * 140 * sizeof(R);
+};
+
+template <int D, typename R>
+void launch_sl(pond_state *s, pond::Params<D, R> &P)
 {
-    pond::sl_kernel<R, kSlThreads><<<blocks_for(P.nx, kSlThreads), kSlThreads, 0, s->stream>>>(P);
+    if constexpr (D == 1) {
+        pond::sl_kernel<R, kSlThreads><<<blocks_for(P.nx, kSlThreads), kSlThreads, 0, s->stream>>>(P);
+    } else {
+        using T = Sl2Tile<R>;
+        const dim3 g(unsigned((P.nx + T::TX - 1) / T::TX), unsigned((P.ny + T::TY - 1) / T::TY));
+        pond::sl2_kernel<R, T::TX, T::TY><<<g, T::TX * T::TY, T::scratch, s->stream>>>(P);
+    }
     std::swap(P.sf, P.xf);
     std::swap(P.sg, P.xg);
     std::swap(P.sfr, P.xfr);
@@ -303,11 +317,9 @@ template <int D, typename R>
 void launch_step(pond_state *s, bool collect = false)
 {
     auto &P = params_of<D, R>(s);
-    if constexpr (D == 1) {
-        if (s->scheme == POND_SL) {
-            launch_sl<R>(s, P);
-            return;
-        }
+    if (s->scheme == POND_SL) {
+        launch_sl<D, R>(s, P);
+        return;
     }
     if constexpr (D == 2) {
         if (s->learned) {
@@ -372,11 +384,9 @@ pond_status step_timed_impl(pond_state *s, int64_t n_steps, double *ms)
                 s->launches += 1;
             }
         }
-        bool sl = false;
-        if constexpr (D == 1) sl = s->scheme == POND_SL;
-        if (sl) {
+        if (s->scheme == POND_SL) {
             // the whole semi-Lagrangian step is one kernel: it is timed as the first part
-            if constexpr (D == 1) launch_sl<R>(s, P);
+            launch_sl<D, R>(s, P);
             CUDA_TRY(cudaEventRecord(ev[2 * k + 1], s->stream));
             CUDA_TRY(cudaEventRecord(ev[2 * k + 2], s->stream));
             s->launches -= 1;
@@ -750,8 +760,6 @@ pond_status pond_init(const pond_grid *grid, pond_velset velset, double gamma, d
     if (opts->limiter != POND_VANLEER && opts->limiter != POND_MINMOD) return fail(POND_ERR_INVALID_ARG, "bad limiter");
     if (!(opts->cfl > 0.0) || opts->max_iter < 1 || opts->fixed_iters < 0) return fail(POND_ERR_INVALID_ARG, "bad cfl/max_iter/fixed_iters");
     if (opts->scheme != POND_FV && opts->scheme != POND_SL) return fail(POND_ERR_INVALID_ARG, "bad scheme %d", opts->scheme);
-    if (opts->scheme == POND_SL && D != 1)
-        return fail(POND_ERR_UNSUPPORTED, "the semi-Lagrangian scheme runs on D1Q4 grids only");
     if (opts->scheme == POND_SL && !(opts->cfl < 1.0))
         return fail(POND_ERR_INVALID_ARG, "the semi-Lagrangian stencil needs cfl < 1");
     for (int k = 0; k < 4; ++k)
@@ -779,6 +787,15 @@ pond_status pond_init(const pond_grid *grid, pond_velset velset, double gamma, d
         s->own_stream = true;
     }
     pond_status st = dispatch(s, [&](auto d, auto r) { return setup<decltype(d)::value, decltype(r)>(s); });
+    if (st == POND_OK && D == 2 && s->scheme == POND_SL) {
+        // the 2D semi-Lagrangian kernel's scratch can exceed the default dynamic shared memory
+        const cudaError_t ea = s->prec == POND_FP32
+            ? cudaFuncSetAttribute(pond::sl2_kernel<float, Sl2Tile<float>::TX, Sl2Tile<float>::TY>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sl2Tile<float>::scratch))
+            : cudaFuncSetAttribute(pond::sl2_kernel<double, Sl2Tile<double>::TX, Sl2Tile<double>::TY>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sl2Tile<double>::scratch));
+        if (ea != cudaSuccess) st = fail(POND_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(ea));
+    }
     if (st == POND_OK && D == 2) {
         st = mlp_setup(s);
         if (st == POND_OK) {

@@ -1,4 +1,4 @@
-// pond_sl.cuh -- the semi-Lagrangian realization of Sec. III.A on D1Q4 grids.
+// pond_sl.cuh -- the semi-Lagrangian realization of Sec. III.A on D1Q4 grids (D2Q16: pond_sl2.cuh).
 //
 // One thread per node.  A CTA stages its TX nodes and a halo of two on each side (the raw
 // populations in each node's own frame, as Hermite coefficients).  Each thread then runs
@@ -29,6 +29,33 @@ __device__ __forceinline__ R sl_interp(R v0, R v1, R v2, R v3, R th)
     const R lo = min(v1, v2), hi = max(v1, v2);
     if (p < lo || p > hi) p = v1 + th * (v2 - v1);
     return p;
+}
+
+// warp-aggregated node diagnostics (passes, non-converged, restarts, non-physical), then
+// the CFL reduction that sets the next step; every thread of the block calls it
+template <typename R>
+__device__ __forceinline__ void sl_diag_and_advance(Diag *diag, Clock *clock, bool active, unsigned long long my_iters,
+                                                    unsigned long long my_nonconv, unsigned long long my_fallbacks,
+                                                    unsigned long long my_nonphys, double rate)
+{
+    const unsigned mask = 0xffffffffu;
+    unsigned long long n_act = active ? 1ull : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        my_iters += __shfl_down_sync(mask, my_iters, o);
+        my_nonconv += __shfl_down_sync(mask, my_nonconv, o);
+        my_fallbacks += __shfl_down_sync(mask, my_fallbacks, o);
+        my_nonphys += __shfl_down_sync(mask, my_nonphys, o);
+        n_act += __shfl_down_sync(mask, n_act, o);
+    }
+    if ((threadIdx.x & 31) == 0 && n_act) {
+        atomicAdd(&diag->face_iters, my_iters);
+        atomicAdd(&diag->face_solves, n_act);
+        if (my_nonconv) { atomicAdd(&diag->nonconv, my_nonconv); atomicOr(&diag->flags, FLAG_NOT_CONVERGED); }
+        if (my_fallbacks) atomicAdd(&diag->fallbacks, my_fallbacks);
+        if (my_nonphys) { atomicAdd(&diag->nonphys, my_nonphys); atomicOr(&diag->flags, FLAG_NONPHYSICAL); }
+    }
+    reduce_rate_and_advance(clock, rate, true);
 }
 
 template <typename R, int TX>
@@ -199,25 +226,7 @@ sl_kernel(const Params<1, R> P)
             rate = cell_rate<R>(&unr, out_T, KC.inv_dx, KC.inv_dx, 1);
         }
     }
-    // warp-aggregated diagnostics
-    const unsigned mask = 0xffffffffu;
-    unsigned long long n_act = active ? 1ull : 0ull;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        my_iters += __shfl_down_sync(mask, my_iters, o);
-        my_nonconv += __shfl_down_sync(mask, my_nonconv, o);
-        my_fallbacks += __shfl_down_sync(mask, my_fallbacks, o);
-        my_nonphys += __shfl_down_sync(mask, my_nonphys, o);
-        n_act += __shfl_down_sync(mask, n_act, o);
-    }
-    if ((threadIdx.x & 31) == 0 && n_act) {
-        atomicAdd(&P.diag->face_iters, my_iters);
-        atomicAdd(&P.diag->face_solves, n_act);
-        if (my_nonconv) { atomicAdd(&P.diag->nonconv, my_nonconv); atomicOr(&P.diag->flags, FLAG_NOT_CONVERGED); }
-        if (my_fallbacks) atomicAdd(&P.diag->fallbacks, my_fallbacks);
-        if (my_nonphys) { atomicAdd(&P.diag->nonphys, my_nonphys); atomicOr(&P.diag->flags, FLAG_NONPHYSICAL); }
-    }
-    reduce_rate_and_advance(P.clock, rate, true);
+    sl_diag_and_advance<R>(P.diag, P.clock, active, my_iters, my_nonconv, my_fallbacks, my_nonphys, rate);
 }
 
 }  // namespace pond

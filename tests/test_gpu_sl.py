@@ -1,7 +1,7 @@
-"""The semi-Lagrangian realization (Sec. III.A) on the GPU against the oracle's: FP64 at
-1e-12 in corrector parity mode (a fixed number of passes), through single launches and
-through captured graphs whose state buffers alternate; FP32 against the FP64 oracle at
-1e-4 relative L1; the ABI refuses the scheme where it is not built."""
+"""The semi-Lagrangian realization (Sec. III.A) on the GPU against the oracle's, on D1Q4 and
+D2Q16 grids: FP64 at 1e-12 in corrector parity mode (a fixed number of passes), through
+single launches and through captured graphs whose state buffers alternate; FP32 against the
+FP64 oracle; the scheme has no face frames to read back."""
 import numpy as np
 import pytest
 
@@ -10,6 +10,7 @@ torch = pytest.importorskip("torch")
 import paper_2203_05477_gb300 as pond  # noqa: E402
 from paper_2203_05477_gb300 import inputs as I  # noqa: E402
 from tests.common import hermite_of_pops, max_rel, oracle_for, rel_l1  # noqa: E402
+from tests.test_gpu_parity import compare_fp64  # noqa: E402
 from tests.test_oracle_reflective import perturbed, walled  # noqa: E402
 
 pytestmark = pytest.mark.gpu
@@ -101,10 +102,58 @@ def test_sl_fp32_against_fp64_oracle():
     assert np.abs(ux - uo)[off].sum() / np.abs(uo).sum() <= 1e-3
 
 
-def test_sl_refused_where_not_built():
-    with pytest.raises(pond.PondError) as e:
-        pond.Solver(I.quadrants_2d(8, seed=0), precision="fp32", cfl=0.2, tau=1e-5, scheme="sl")
-    assert e.value.status == pond.POND_ERR_UNSUPPORTED
+def test_sl_has_no_face_frames():
     gs, _ = sl_pair(I.sod_400(), 0.5, **KW64)
-    with pytest.raises(pond.PondError):
+    with pytest.raises(pond.PondError) as e:
         gs.face_gauges()
+    assert e.value.status == pond.POND_ERR_UNSUPPORTED
+
+
+def compare_sl_2d(gs, os_, tol=1e-12):
+    compare_fp64(gs, os_, tol=tol, faces=False)
+
+
+CASES_2D = [
+    ("periodic_13x11", lambda: I.smooth_periodic(2, 13, 11, seed=2, amp=0.15)),
+    ("lax_liu_16", lambda: I.lax_liu_2d(16)),
+    ("explosion_box_moving_12", lambda: perturbed(I.explosion_box_2d(12), 6)),
+    ("quadrants_19x19", lambda: I.quadrants_2d(19, seed=0)),
+]
+
+
+@pytest.mark.parametrize("name,make", CASES_2D, ids=[c[0] for c in CASES_2D])
+def test_sl_2d_fp64_parity(name, make):
+    gs, os_ = sl_pair(make(), 0.2, **KW64)
+    for chunk in (1, 4):
+        gs.step(chunk)
+        os_.sl_step(chunk)
+        d, st = gs.sync(), os_.stats()
+        assert d["steps"] == st["steps"] and d["face_iters"] == st["face_iters"]
+        assert d["fallbacks"] == st["fallbacks"] and d["nonphysical"] == st["nonphysical"] == 0
+        assert d["t"] == pytest.approx(st["t"], rel=1e-13)
+        compare_sl_2d(gs, os_)
+
+
+def test_sl_2d_fp32_against_fp64_oracle():
+    pb = I.smooth_periodic(2, 24, 20, seed=2, amp=0.15)
+    kw = dict(tau=1e-5, max_iter=16)
+    gs = pond.Solver(pb, precision="fp32", cfl=0.2, scheme="sl", tol=1e-6, **kw)
+    gs.set_primitive()
+    os_ = oracle_for(pb, cfl=0.2, tol=1e-6, **kw)
+    gs.step(20)
+    os_.sl_step(20)
+    assert gs.sync()["nonphysical"] == 0
+    r, ux, uy, p = gs.primitive()
+    ro, uxo, uyo, po = os_.primitive()
+    assert rel_l1(r, ro) <= 1e-4 and rel_l1(p, po) <= 1e-4
+    sp, spo = np.hypot(ux, uy), np.hypot(uxo, uyo)
+    assert np.abs(sp - spo).sum() / spo.sum() <= 1e-4
+
+
+def test_sl_2d_graph_replays():
+    gs, os_ = sl_pair(I.smooth_periodic(2, 13, 11, seed=2, amp=0.15), 0.2, **KW64)
+    for chunk in (32, 1, 33):
+        gs.step(chunk)
+        os_.sl_step(chunk)
+        assert gs.sync()["steps"] == os_.stats()["steps"]
+        compare_sl_2d(gs, os_)
