@@ -78,9 +78,10 @@ typedef struct {
 /* Time-stepping realizations of Sec. III: the finite-volume scheme (Sec. III.B, the
  * conservative default) or the semi-Lagrangian one (Sec. III.A: per-node predictor-
  * corrector on the node's frame, populations advected from their departure points by a
- * limited 4-point Lagrange interpolation, BGK collision; not conservative).  The
- * semi-Lagrangian scheme runs on D1Q4 grids; D2Q16 and batches refuse it with
- * POND_ERR_UNSUPPORTED. */
+ * limited 4-point Lagrange interpolation, in 2D its limited tensor product, BGK
+ * collision; not conservative).  The semi-Lagrangian scheme runs on D1Q4 and D2Q16 grids;
+ * batches refuse it with POND_ERR_UNSUPPORTED, and it keeps no face frames
+ * (pond_face_gauges returns POND_ERR_UNSUPPORTED). */
 typedef enum { POND_FV = 0, POND_SL = 1 } pond_scheme;
 
 typedef struct {
