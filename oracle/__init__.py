@@ -53,6 +53,14 @@ def _load():
                                       ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_double, ctypes.c_double, ip, dp, ip, ctypes.c_int,
                                       ctypes.c_double, ctypes.c_int, ctypes.c_int]
+        lib.oracle_create3.restype = ctypes.c_void_p
+        lib.oracle_create3.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_double, ip, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int]
+        lib.oracle_set_primitive3.argtypes = [ctypes.c_void_p, dp, dp, dp, dp, dp]
+        lib.oracle_conserved3.argtypes = [ctypes.c_void_p, dp, dp, dp, dp, dp]
+        lib.oracle_face_gauges3.argtypes = [ctypes.c_void_p, dp, dp, dp]
+        lib.oracle_set_face_gauges3.argtypes = [ctypes.c_void_p, dp, dp, dp]
         lib.oracle_free.argtypes = [ctypes.c_void_p]
         lib.oracle_set_primitive.argtypes = [ctypes.c_void_p, dp, dp, dp, dp]
         lib.oracle_step.argtypes = [ctypes.c_void_p, ctypes.c_int]
@@ -89,10 +97,11 @@ def _f64(a) -> np.ndarray:
 
 
 def lattice(D: int):
-    """Lattice speeds c [Q, D], weights W [Q] and T_L (Table I, Eq. wi)."""
+    """Lattice speeds c [Q, D], weights W [Q] and T_L (Table I, Eq. wi; D3Q64 as the
+    three-dimensional tensor product)."""
     lib = _load()
-    c = np.zeros((16, D))
-    w = np.zeros(16)
+    c = np.zeros((64, D))
+    w = np.zeros(64)
     tl = np.zeros(1)
     q = lib.oracle_lattice(D, _dp(c), _dp(w), _dp(tl))
     return c[:q].copy(), w[:q].copy(), float(tl[0])
@@ -131,18 +140,28 @@ def limiter(kind: int, a: float, b: float) -> float:
 class Solver:
     """The FP64 oracle solver: one instance per problem.
 
-    Grid of nx (x ny) cells, D = 1 (D1Q4) or D = 2 (D2Q16).  ``bc`` lists x-lo, x-hi,
-    y-lo, y-hi; ``inflow`` is a 4x4 array of (rho, ux, uy, p) per side and
-    ``inflow_range`` a 4x2 array of [lo, hi) cell ranges along that side.
+    Grid of nx (x ny (x nz)) cells, D = 1 (D1Q4), 2 (D2Q16) or 3 (D3Q64).  ``bc`` lists
+    x-lo, x-hi, y-lo, y-hi (and z-lo, z-hi in 3D); ``inflow`` is a 4x4 array of
+    (rho, ux, uy, p) per side and ``inflow_range`` a 4x2 array of [lo, hi) cell ranges
+    along that side (1D and 2D only).
     """
 
-    def __init__(self, D, nx, ny=1, *, dx, dy=None, gamma, tau, cfl, t_end=0.0,
+    def __init__(self, D, nx, ny=1, nz=1, *, dx, dy=None, dz=None, gamma, tau, cfl, t_end=0.0,
                  bc=(0, 0, 0, 0), inflow=None, inflow_range=None, limiter=VANLEER,
                  tol=1e-12, max_iter=50, fixed_iters=0):
         self.lib = _load()
-        self.D, self.nx, self.ny = D, nx, (ny if D == 2 else 1)
+        self.D, self.nx, self.ny, self.nz = D, nx, (ny if D >= 2 else 1), (nz if D == 3 else 1)
         _, w, _ = lattice(D)
         self.Q = len(w)
+        if D == 3:
+            bc6 = tuple(bc) + (0,) * (6 - len(bc))
+            self.h = self.lib.oracle_create3(nx, self.ny, self.nz, float(dx), float(dy if dy is not None else dx),
+                                             float(dz if dz is not None else dx), float(gamma), float(tau),
+                                             float(cfl), float(t_end), (ctypes.c_int * 6)(*[int(b) for b in bc6]),
+                                             int(limiter), float(tol), int(max_iter), int(fixed_iters))
+            if not self.h:
+                raise ValueError("oracle_create3 failed")
+            return
         bc_arr = (ctypes.c_int * 4)(*[int(b) for b in bc])
         infl = _f64(np.zeros((4, 4)) if inflow is None else inflow).reshape(16)
         rng = np.zeros((4, 2), dtype=np.int32) if inflow_range is None else np.asarray(inflow_range, dtype=np.int32)
@@ -163,7 +182,13 @@ class Solver:
 
     @property
     def ncell(self):
-        return self.nx * self.ny
+        return self.nx * self.ny * self.nz
+
+    def set_primitive3(self, rho, ux, uy, uz, p):
+        n = self.ncell
+        rho, ux, uy, uz, p = (_f64(np.ravel(a)) for a in (rho, ux, uy, uz, p))
+        assert all(a.size == n for a in (rho, ux, uy, uz, p))
+        self.lib.oracle_set_primitive3(self.h, _dp(rho), _dp(ux), _dp(uy), _dp(uz), _dp(p))
 
     def set_primitive(self, rho, ux, uy, p):
         n = self.ncell
@@ -180,15 +205,25 @@ class Solver:
         return int(self.lib.oracle_sl_step(self.h, int(n)))
 
     def conserved(self):
+        """rho, mx, my, E per cell (1D, 2D); rho, mx, my, mz, E in 3D."""
         n = self.ncell
+        if self.D == 3:
+            out = [np.zeros(n) for _ in range(5)]
+            self.lib.oracle_conserved3(self.h, *(_dp(a) for a in out))
+            return out
         out = [np.zeros(n) for _ in range(4)]
         self.lib.oracle_conserved(self.h, *(_dp(a) for a in out))
         return out  # rho, mx, my, E
 
     def primitive(self):
+        """rho, ux, uy, p (1D, 2D); rho, ux, uy, uz, p in 3D."""
+        cv = 1.0 / (self.gamma - 1.0)
+        if self.D == 3:
+            rho, mx, my, mz, E = self.conserved()
+            T = (E - 0.5 * (mx * mx + my * my + mz * mz) / rho) / (cv * rho)
+            return rho, mx / rho, my / rho, mz / rho, rho * T
         rho, mx, my, E = self.conserved()
         ux, uy = mx / rho, my / rho
-        cv = 1.0 / (self.gamma - 1.0)
         T = (E - 0.5 * (mx * mx + my * my) / rho) / (cv * rho)
         return rho, ux, uy, rho * T
 
@@ -214,12 +249,22 @@ class Solver:
 
     def face_gauges(self):
         D = self.D
+        if D == 3:
+            nx, ny, nz = self.nx, self.ny, self.nz
+            out = [np.zeros(((nx + 1) * ny * nz, 4)), np.zeros((nx * (ny + 1) * nz, 4)),
+                   np.zeros((nx * ny * (nz + 1), 4))]
+            self.lib.oracle_face_gauges3(self.h, *(_dp(a) for a in out))
+            return tuple(out)
         xg = np.zeros(((self.nx + 1) * self.ny, D + 1))
         yg = np.zeros((self.nx * (self.ny + 1), D + 1)) if D == 2 else np.zeros((1, D + 1))
         self.lib.oracle_face_gauges(self.h, _dp(xg), _dp(yg))
         return xg, (yg if D == 2 else None)
 
-    def set_face_gauges(self, xg, yg=None):
+    def set_face_gauges(self, xg, yg=None, zg=None):
+        if self.D == 3:
+            xg, yg, zg = (_f64(a) for a in (xg, yg, zg))
+            self.lib.oracle_set_face_gauges3(self.h, _dp(xg), _dp(yg), _dp(zg))
+            return
         xg = _f64(xg)
         yg = _f64(yg) if yg is not None else np.zeros(1)
         self.lib.oracle_set_face_gauges(self.h, _dp(xg), _dp(yg))
@@ -242,7 +287,7 @@ class Solver:
         return d
 
 
-def make_solver(D, nx, ny=1, *, gamma, **kw) -> Solver:
-    s = Solver(D, nx, ny, gamma=gamma, **kw)
+def make_solver(D, nx, ny=1, nz=1, *, gamma, **kw) -> Solver:
+    s = Solver(D, nx, ny, nz, gamma=gamma, **kw)
     s.gamma = gamma
     return s

@@ -10,7 +10,9 @@
  * paper states:
  *
  *   - lattice:      Table I (D1Q4 Gauss-Hermite roots and weights, T_L = 1) and
- *                   Eq. (wi) (D2Q16 as the tensor product W_i = w_ix w_iy);
+ *                   Eq. (wi) (D2Q16 as the tensor product W_i = w_ix w_iy; D3Q64, the
+ *                   three-dimensional extension named as future work in Sec. V, as
+ *                   W_i = w_ix w_iy w_iz);
  *   - velocities:   Eq. (vlambda)   v_i = sqrt(T/T_L) c_i + u;
  *   - moments:      Sec. II.B       rho, rho u, rho E;  Eq. (E) rho E = Cv rho T + rho u^2/2;
  *   - equilibria:   Eqs. (feqPond), (geqPond)   f^eq = rho W_i,  g^eq = (Cv - D/2) T rho W_i;
@@ -50,8 +52,8 @@
 #include <string.h>
 #include <stdint.h>
 
-#define MAXQ 16
-#define MAXD 2
+#define MAXQ 64
+#define MAXD 3
 #define NG 2
 
 /* ------------------------------------------------------------------ lattice */
@@ -65,7 +67,9 @@ typedef struct {
 } lattice;
 
 /* Table I: D1Q4 nodes +-sqrt(3 -+ sqrt 6) with weights (3 +- sqrt 6)/12, T_L = 1.
- * D2Q16 (Eq. wi): population i = m*4 + n has c_i = (c_m, c_n), W_i = w_m w_n. */
+ * D2Q16 (Eq. wi): population i = m*4 + n has c_i = (c_m, c_n), W_i = w_m w_n.
+ * D3Q64 (the same product in three dimensions): i = (m*4 + n)*4 + p, c_i = (c_m, c_n, c_p),
+ * W_i = w_m w_n w_p. */
 static void lattice_init(lattice *L, int D)
 {
     double s6 = sqrt(6.0);
@@ -77,7 +81,7 @@ static void lattice_init(lattice *L, int D)
     if (D == 1) {
         L->Q = 4;
         for (int m = 0; m < 4; ++m) { L->c[m][0] = c1[m]; L->W[m] = w1[m]; }
-    } else {
+    } else if (D == 2) {
         L->Q = 16;
         for (int m = 0; m < 4; ++m)
             for (int n = 0; n < 4; ++n) {
@@ -86,6 +90,17 @@ static void lattice_init(lattice *L, int D)
                 L->c[i][1] = c1[n];
                 L->W[i] = w1[m] * w1[n];
             }
+    } else {
+        L->Q = 64;
+        for (int m = 0; m < 4; ++m)
+            for (int n = 0; n < 4; ++n)
+                for (int p = 0; p < 4; ++p) {
+                    int i = (m * 4 + n) * 4 + p;
+                    L->c[i][0] = c1[m];
+                    L->c[i][1] = c1[n];
+                    L->c[i][2] = c1[p];
+                    L->W[i] = w1[m] * w1[n] * w1[p];
+                }
     }
 }
 
@@ -147,19 +162,22 @@ static void grad_transform(const lattice *L, int order, const double *f_in,
     }
     /* The equilibration alternative of Sec. II.C (an ablation; the paper uses Grad's
      * projection): the slow moments (orders <= order) are kept as above, and the fast ones
-     * -- here the tensor Hermite components He_r(c_x) He_s(c_y) with r, s <= 3 and
-     * r + s > order, which D2Q16 carries beyond the slow set -- take the values of the
-     * equilibrium with the same zeroth and first moments in the new frame, M0 d_x^r d_y^s
-     * with d = (M1/M0 - u') / sqrt(T'/T_L) (the Hermite coefficients of a Maxwellian of
-     * temperature T' shifted by d).  D1Q4 carries no fast f moment; its g has the order-3 one. */
-    double fast[4][4];
+     * -- here the tensor Hermite components He_r(c_x) He_s(c_y) He_t(c_z) with r, s, t <= 3
+     * and r + s + t > order, which the tensor-product lattices carry beyond the slow set --
+     * take the values of the equilibrium with the same zeroth and first moments in the new
+     * frame, M0 d_x^r d_y^s d_z^t with d = (M1/M0 - u') / sqrt(T'/T_L) (the Hermite
+     * coefficients of a Maxwellian of temperature T' shifted by d).  D1Q4 carries no fast f
+     * moment; its g has the order-3 one. */
+    double fast[4][4][4];
     memset(fast, 0, sizeof(fast));
     if (L->equilibrate) {
         double d[MAXD] = {0};
         for (int a = 0; a < D; ++a) d[a] = (M1[a] / M0 - up[a]) / r;
         for (int rr = 0; rr <= 3; ++rr)
-            for (int ss = 0; ss <= (D == 2 ? 3 : 0); ++ss)
-                if (rr + ss > order) fast[rr][ss] = M0 * pow(d[0], rr) * (D == 2 ? pow(d[1], ss) : 1.0);
+            for (int ss = 0; ss <= (D >= 2 ? 3 : 0); ++ss)
+                for (int tt = 0; tt <= (D == 3 ? 3 : 0); ++tt)
+                    if (rr + ss + tt > order)
+                        fast[rr][ss][tt] = M0 * pow(d[0], rr) * (D >= 2 ? pow(d[1], ss) : 1.0) * (D == 3 ? pow(d[2], tt) : 1.0);
     }
     /* Eq. (f_transformed) */
     for (int i = 0; i < Q; ++i) {
@@ -179,12 +197,16 @@ static void grad_transform(const lattice *L, int order, const double *f_in,
         if (L->equilibrate) {
             /* probabilists' Hermite polynomials He_0..He_3 over k! at the node (T_L = 1) */
             const double hx[4] = {1.0, c[0], (c[0] * c[0] - 1.0) / 2.0, (c[0] * c[0] * c[0] - 3.0 * c[0]) / 6.0};
-            double hy[4] = {1.0, 0.0, 0.0, 0.0};
-            if (D == 2) {
+            double hy[4] = {1.0, 0.0, 0.0, 0.0}, hz[4] = {1.0, 0.0, 0.0, 0.0};
+            if (D >= 2) {
                 hy[1] = c[1]; hy[2] = (c[1] * c[1] - 1.0) / 2.0; hy[3] = (c[1] * c[1] * c[1] - 3.0 * c[1]) / 6.0;
             }
+            if (D == 3) {
+                hz[1] = c[2]; hz[2] = (c[2] * c[2] - 1.0) / 2.0; hz[3] = (c[2] * c[2] * c[2] - 3.0 * c[2]) / 6.0;
+            }
             for (int rr = 0; rr <= 3; ++rr)
-                for (int ss = 0; ss <= 3; ++ss) sf += fast[rr][ss] * hx[rr] * hy[ss];
+                for (int ss = 0; ss <= 3; ++ss)
+                    for (int tt = 0; tt <= 3; ++tt) sf += fast[rr][ss][tt] * hx[rr] * hy[ss] * hz[tt];
         }
         f_out[i] = L->W[i] * (a0 + s1 / TL + s2 / (2.0 * TL * TL) + s3 / (6.0 * TL * TL * TL) + sf);
     }
@@ -249,11 +271,11 @@ enum { BC_TRANSMISSIVE = 0, BC_PERIODIC = 1, BC_INFLOW = 2, BC_REFLECTIVE = 3 };
 
 typedef struct oracle {
     lattice L;
-    int D, Q, nx, ny;
-    int gx, gy;        /* ghost layers in x and y (gy = 0 in 1D) */
-    int px, py;        /* padded extents */
-    double dx, dy, gamma, Cv, tau, cfl, t_end;
-    int bc[4];         /* x-lo, x-hi, y-lo, y-hi */
+    int D, Q, nx, ny, nz;
+    int gx, gy, gz;    /* ghost layers in x, y and z (0 along the axes a grid does not have) */
+    int px, py, pz;    /* padded extents */
+    double dx, dy, dz, gamma, Cv, tau, cfl, t_end;
+    int bc[6];         /* x-lo, x-hi, y-lo, y-hi, z-lo, z-hi */
     double inflow[4][4];
     int inflow_lo[4], inflow_hi[4];
     int limiter;
@@ -263,16 +285,24 @@ typedef struct oracle {
     double *f, *g, *u, *T;
     double *fp, *gp;   /* phi-bar-plus, Eq. (Fbarplus); the new populations in the SL step */
     double *un, *Tn;   /* the new frames in the SL step */
-    /* faces: x-faces (nx+1) x ny, y-faces nx x (ny+1); gauge and populations */
-    double *xu, *xT, *yu, *yT;
-    double *xf, *xg, *yf, *yg;
+    /* faces: x-faces (nx+1) x ny x nz, y-faces nx x (ny+1) x nz, z-faces nx x ny x (nz+1);
+     * gauge and populations */
+    double *xu, *xT, *yu, *yT, *zu, *zT;
+    double *xf, *xg, *yf, *yg, *zf, *zg;
     double t, dt, last_dt, forced_dt;
     long long steps, face_iters, face_count, nonconv, nonphys, fallbacks;
 } oracle;
 
-static int cidx(const oracle *o, int i, int j) { return (j + o->gy) * o->px + (i + o->gx); }
-static int xface(const oracle *o, int i, int j) { return j * (o->nx + 1) + i; }
-static int yface(const oracle *o, int i, int j) { return j * o->nx + i; }
+static int cidx3(const oracle *o, int i, int j, int k)
+{
+    return ((k + o->gz) * o->py + (j + o->gy)) * o->px + (i + o->gx);
+}
+static int cidx(const oracle *o, int i, int j) { return cidx3(o, i, j, 0); }
+static int xface3(const oracle *o, int i, int j, int k) { return (k * o->ny + j) * (o->nx + 1) + i; }
+static int yface3(const oracle *o, int i, int j, int k) { return (k * (o->ny + 1) + j) * o->nx + i; }
+static int zface3(const oracle *o, int i, int j, int k) { return (k * o->ny + j) * o->nx + i; }
+static int xface(const oracle *o, int i, int j) { return xface3(o, i, j, 0); }
+static int yface(const oracle *o, int i, int j) { return yface3(o, i, j, 0); }
 
 static void set_equilibrium_cell(oracle *o, int c, double rho, const double *u, double p)
 {
@@ -319,74 +349,96 @@ static void mirror_cell(oracle *o, int dst, int src, int axis)
 static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 static int wrapi(int v, int n) { return ((v % n) + n) % n; }
 
-/* Two ghost layers: x-sides first (interior rows), then y-sides for every padded column. */
+/* Two ghost layers: x-sides first (interior rows), then y-sides for every padded column,
+ * then (3D) z-sides for every padded x-y position. */
 static void fill_ghosts(oracle *o)
 {
-    for (int j = 0; j < o->ny; ++j)
-        for (int k = 1; k <= o->gx; ++k) {
-            for (int side = 0; side < 2; ++side) {
-                int i = side == 0 ? -k : o->nx - 1 + k;
-                int dst = cidx(o, i, j);
-                int b = o->bc[side];
-                if (b == BC_INFLOW && j >= o->inflow_lo[side] && j < o->inflow_hi[side]) {
-                    double uu[2] = {o->inflow[side][1], o->inflow[side][2]};
-                    set_equilibrium_cell(o, dst, o->inflow[side][0], uu, o->inflow[side][3]);
-                } else if (b == BC_PERIODIC) {
-                    copy_cell(o, dst, cidx(o, wrapi(i, o->nx), j));
-                } else if (b == BC_REFLECTIVE) {
-                    /* ghost -k mirrors cell k-1; ghost nx-1+k mirrors cell nx-k (clamped
-                     * into the grid when it is thinner than the ghost layers) */
-                    mirror_cell(o, dst, cidx(o, clampi(side == 0 ? k - 1 : o->nx - k, 0, o->nx - 1), j), 0);
-                } else {
-                    copy_cell(o, dst, cidx(o, clampi(i, 0, o->nx - 1), j));
+    for (int kz = 0; kz < o->nz; ++kz)
+        for (int j = 0; j < o->ny; ++j)
+            for (int k = 1; k <= o->gx; ++k) {
+                for (int side = 0; side < 2; ++side) {
+                    int i = side == 0 ? -k : o->nx - 1 + k;
+                    int dst = cidx3(o, i, j, kz);
+                    int b = o->bc[side];
+                    if (b == BC_INFLOW && j >= o->inflow_lo[side] && j < o->inflow_hi[side]) {
+                        double uu[3] = {o->inflow[side][1], o->inflow[side][2], 0.0};
+                        set_equilibrium_cell(o, dst, o->inflow[side][0], uu, o->inflow[side][3]);
+                    } else if (b == BC_PERIODIC) {
+                        copy_cell(o, dst, cidx3(o, wrapi(i, o->nx), j, kz));
+                    } else if (b == BC_REFLECTIVE) {
+                        /* ghost -k mirrors cell k-1; ghost nx-1+k mirrors cell nx-k (clamped
+                         * into the grid when it is thinner than the ghost layers) */
+                        mirror_cell(o, dst, cidx3(o, clampi(side == 0 ? k - 1 : o->nx - k, 0, o->nx - 1), j, kz), 0);
+                    } else {
+                        copy_cell(o, dst, cidx3(o, clampi(i, 0, o->nx - 1), j, kz));
+                    }
                 }
             }
-        }
     if (o->D < 2) return;
-    for (int i = -o->gx; i < o->nx + o->gx; ++i)
-        for (int k = 1; k <= o->gy; ++k) {
-            for (int side = 2; side < 4; ++side) {
-                int j = side == 2 ? -k : o->ny - 1 + k;
-                int dst = cidx(o, i, j);
-                int b = o->bc[side];
-                int ic = clampi(i, 0, o->nx - 1);
-                if (b == BC_INFLOW && ic >= o->inflow_lo[side] && ic < o->inflow_hi[side]) {
-                    double uu[2] = {o->inflow[side][1], o->inflow[side][2]};
-                    set_equilibrium_cell(o, dst, o->inflow[side][0], uu, o->inflow[side][3]);
-                } else if (b == BC_PERIODIC) {
-                    copy_cell(o, dst, cidx(o, i, wrapi(j, o->ny)));
-                } else if (b == BC_REFLECTIVE) {
-                    mirror_cell(o, dst, cidx(o, i, clampi(side == 2 ? k - 1 : o->ny - k, 0, o->ny - 1)), 1);
-                } else {
-                    copy_cell(o, dst, cidx(o, i, clampi(j, 0, o->ny - 1)));
+    for (int kz = 0; kz < o->nz; ++kz)
+        for (int i = -o->gx; i < o->nx + o->gx; ++i)
+            for (int k = 1; k <= o->gy; ++k) {
+                for (int side = 2; side < 4; ++side) {
+                    int j = side == 2 ? -k : o->ny - 1 + k;
+                    int dst = cidx3(o, i, j, kz);
+                    int b = o->bc[side];
+                    int ic = clampi(i, 0, o->nx - 1);
+                    if (b == BC_INFLOW && ic >= o->inflow_lo[side] && ic < o->inflow_hi[side]) {
+                        double uu[3] = {o->inflow[side][1], o->inflow[side][2], 0.0};
+                        set_equilibrium_cell(o, dst, o->inflow[side][0], uu, o->inflow[side][3]);
+                    } else if (b == BC_PERIODIC) {
+                        copy_cell(o, dst, cidx3(o, i, wrapi(j, o->ny), kz));
+                    } else if (b == BC_REFLECTIVE) {
+                        mirror_cell(o, dst, cidx3(o, i, clampi(side == 2 ? k - 1 : o->ny - k, 0, o->ny - 1), kz), 1);
+                    } else {
+                        copy_cell(o, dst, cidx3(o, i, clampi(j, 0, o->ny - 1), kz));
+                    }
                 }
             }
-        }
+    if (o->D < 3) return;
+    for (int j = -o->gy; j < o->ny + o->gy; ++j)
+        for (int i = -o->gx; i < o->nx + o->gx; ++i)
+            for (int k = 1; k <= o->gz; ++k) {
+                for (int side = 4; side < 6; ++side) {
+                    int kz = side == 4 ? -k : o->nz - 1 + k;
+                    int dst = cidx3(o, i, j, kz);
+                    int b = o->bc[side];
+                    if (b == BC_PERIODIC) {
+                        copy_cell(o, dst, cidx3(o, i, j, wrapi(kz, o->nz)));
+                    } else if (b == BC_REFLECTIVE) {
+                        mirror_cell(o, dst, cidx3(o, i, j, clampi(side == 4 ? k - 1 : o->nz - k, 0, o->nz - 1)), 2);
+                    } else {
+                        copy_cell(o, dst, cidx3(o, i, j, clampi(kz, 0, o->nz - 1)));
+                    }
+                }
+            }
 }
 
-oracle *oracle_create(int D, int nx, int ny, double dx, double dy, double gamma, double tau,
-                      double cfl, double t_end, const int *bc, const double *inflow,
-                      const int *inflow_range, int limiter_kind, double tol, int max_iter,
-                      int fixed_iters)
+static oracle *create_grid(int D, int nx, int ny, int nz, double dx, double dy, double dz, double gamma,
+                           double tau, double cfl, double t_end, const int *bc6, const double *inflow,
+                           const int *inflow_range, int limiter_kind, double tol, int max_iter,
+                           int fixed_iters)
 {
-    if (D != 1 && D != 2) return NULL;
-    if (D == 1) ny = 1;
+    if (D < 1 || D > 3 || nx < 1) return NULL;
+    if (D < 2) ny = 1;
+    if (D < 3) nz = 1;
+    if (ny < 1 || nz < 1) return NULL;
     oracle *o = (oracle *)calloc(1, sizeof(oracle));
     lattice_init(&o->L, D);
-    o->D = D; o->Q = o->L.Q; o->nx = nx; o->ny = ny;
-    o->gx = NG; o->gy = D == 2 ? NG : 0;
-    o->px = nx + 2 * o->gx; o->py = ny + 2 * o->gy;
-    o->dx = dx; o->dy = D == 2 ? dy : 1.0;
+    o->D = D; o->Q = o->L.Q; o->nx = nx; o->ny = ny; o->nz = nz;
+    o->gx = NG; o->gy = D >= 2 ? NG : 0; o->gz = D == 3 ? NG : 0;
+    o->px = nx + 2 * o->gx; o->py = ny + 2 * o->gy; o->pz = nz + 2 * o->gz;
+    o->dx = dx; o->dy = D >= 2 ? dy : 1.0; o->dz = D == 3 ? dz : 1.0;
     o->gamma = gamma; o->Cv = 1.0 / (gamma - 1.0);
     o->tau = tau; o->cfl = cfl; o->t_end = t_end;
+    for (int s = 0; s < 6; ++s) o->bc[s] = bc6 ? bc6[s] : BC_TRANSMISSIVE;
     for (int s = 0; s < 4; ++s) {
-        o->bc[s] = bc ? bc[s] : BC_TRANSMISSIVE;
         for (int q = 0; q < 4; ++q) o->inflow[s][q] = inflow ? inflow[s * 4 + q] : 0.0;
         o->inflow_lo[s] = inflow_range ? inflow_range[2 * s] : 0;
         o->inflow_hi[s] = inflow_range ? inflow_range[2 * s + 1] : 0;
     }
     o->limiter = limiter_kind; o->tol = tol; o->max_iter = max_iter; o->fixed_iters = fixed_iters;
-    size_t nc = (size_t)o->px * o->py;
+    size_t nc = (size_t)o->px * o->py * o->pz;
     o->f = calloc(nc * o->Q, sizeof(double));
     o->g = calloc(nc * o->Q, sizeof(double));
     o->fp = calloc(nc * o->Q, sizeof(double));
@@ -395,12 +447,38 @@ oracle *oracle_create(int D, int nx, int ny, double dx, double dy, double gamma,
     o->T = calloc(nc, sizeof(double));
     o->un = calloc(nc * MAXD, sizeof(double));
     o->Tn = calloc(nc, sizeof(double));
-    size_t nxf = (size_t)(nx + 1) * ny, nyf = (size_t)nx * (ny + 1);
+    size_t nxf = (size_t)(nx + 1) * ny * nz, nyf = (size_t)nx * (ny + 1) * nz, nzf = (size_t)nx * ny * (nz + 1);
     o->xu = calloc(nxf * MAXD, sizeof(double)); o->xT = calloc(nxf, sizeof(double));
     o->xf = calloc(nxf * o->Q, sizeof(double)); o->xg = calloc(nxf * o->Q, sizeof(double));
     o->yu = calloc(nyf * MAXD, sizeof(double)); o->yT = calloc(nyf, sizeof(double));
     o->yf = calloc(nyf * o->Q, sizeof(double)); o->yg = calloc(nyf * o->Q, sizeof(double));
+    o->zu = calloc(nzf * MAXD, sizeof(double)); o->zT = calloc(nzf, sizeof(double));
+    o->zf = calloc(nzf * o->Q, sizeof(double)); o->zg = calloc(nzf * o->Q, sizeof(double));
     return o;
+}
+
+oracle *oracle_create(int D, int nx, int ny, double dx, double dy, double gamma, double tau,
+                      double cfl, double t_end, const int *bc, const double *inflow,
+                      const int *inflow_range, int limiter_kind, double tol, int max_iter,
+                      int fixed_iters)
+{
+    if (D != 1 && D != 2) return NULL;
+    int bc6[6] = {BC_TRANSMISSIVE, BC_TRANSMISSIVE, BC_TRANSMISSIVE, BC_TRANSMISSIVE, BC_TRANSMISSIVE, BC_TRANSMISSIVE};
+    for (int s = 0; s < 4; ++s) bc6[s] = bc ? bc[s] : BC_TRANSMISSIVE;
+    return create_grid(D, nx, ny, 1, dx, dy, 1.0, gamma, tau, cfl, t_end, bc6, inflow, inflow_range,
+                       limiter_kind, tol, max_iter, fixed_iters);
+}
+
+/* A D3Q64 grid of nx x ny x nz cells; bc lists x-lo, x-hi, y-lo, y-hi, z-lo, z-hi
+ * (transmissive, periodic or reflective; no inflow sides in 3D). */
+oracle *oracle_create3(int nx, int ny, int nz, double dx, double dy, double dz, double gamma, double tau,
+                       double cfl, double t_end, const int *bc6, int limiter_kind, double tol, int max_iter,
+                       int fixed_iters)
+{
+    for (int s = 0; s < 6; ++s)
+        if (bc6 && bc6[s] == BC_INFLOW) return NULL;
+    return create_grid(3, nx, ny, nz, dx, dy, dz, gamma, tau, cfl, t_end, bc6, NULL, NULL, limiter_kind,
+                       tol, max_iter, fixed_iters);
 }
 
 void oracle_free(oracle *o)
@@ -409,6 +487,7 @@ void oracle_free(oracle *o)
     free(o->f); free(o->g); free(o->fp); free(o->gp); free(o->u); free(o->T); free(o->un); free(o->Tn);
     free(o->xu); free(o->xT); free(o->xf); free(o->xg);
     free(o->yu); free(o->yT); free(o->yf); free(o->yg);
+    free(o->zu); free(o->zT); free(o->zf); free(o->zg);
     free(o);
 }
 
@@ -441,34 +520,51 @@ static void pooled_frame_n(const oracle *o, const int *cells, int n, double *u, 
 
 static void init_face_gauges(oracle *o)
 {
-    for (int j = 0; j < o->ny; ++j)
-        for (int i = 0; i <= o->nx; ++i) {
-            int fidx = xface(o, i, j);
-            pooled_frame(o, cidx(o, i - 1, j), cidx(o, i, j), o->xu + (size_t)fidx * MAXD, o->xT + fidx);
-        }
+    for (int k = 0; k < o->nz; ++k)
+        for (int j = 0; j < o->ny; ++j)
+            for (int i = 0; i <= o->nx; ++i) {
+                int fidx = xface3(o, i, j, k);
+                pooled_frame(o, cidx3(o, i - 1, j, k), cidx3(o, i, j, k), o->xu + (size_t)fidx * MAXD, o->xT + fidx);
+            }
     if (o->D < 2) return;
-    for (int j = 0; j <= o->ny; ++j)
-        for (int i = 0; i < o->nx; ++i) {
-            int fidx = yface(o, i, j);
-            pooled_frame(o, cidx(o, i, j - 1), cidx(o, i, j), o->yu + (size_t)fidx * MAXD, o->yT + fidx);
-        }
+    for (int k = 0; k < o->nz; ++k)
+        for (int j = 0; j <= o->ny; ++j)
+            for (int i = 0; i < o->nx; ++i) {
+                int fidx = yface3(o, i, j, k);
+                pooled_frame(o, cidx3(o, i, j - 1, k), cidx3(o, i, j, k), o->yu + (size_t)fidx * MAXD, o->yT + fidx);
+            }
+    if (o->D < 3) return;
+    for (int k = 0; k <= o->nz; ++k)
+        for (int j = 0; j < o->ny; ++j)
+            for (int i = 0; i < o->nx; ++i) {
+                int fidx = zface3(o, i, j, k);
+                pooled_frame(o, cidx3(o, i, j, k - 1), cidx3(o, i, j, k), o->zu + (size_t)fidx * MAXD, o->zT + fidx);
+            }
 }
 
 /* Initial condition: equilibrium populations in each cell's co-moving frame, from
- * primitive fields (rho, ux, uy, p) of size nx*ny (x fastest).  uy may be NULL in 1D. */
-void oracle_set_primitive(oracle *o, const double *rho, const double *ux, const double *uy,
-                          const double *p)
+ * primitive fields (rho, ux, uy, uz, p) of size nx*ny*nz (x fastest, then y).  uy may be
+ * NULL in 1D, uz outside 3D. */
+void oracle_set_primitive3(oracle *o, const double *rho, const double *ux, const double *uy,
+                           const double *uz, const double *p)
 {
-    for (int j = 0; j < o->ny; ++j)
-        for (int i = 0; i < o->nx; ++i) {
-            int k = j * o->nx + i;
-            double uu[2] = {ux[k], (o->D == 2 && uy) ? uy[k] : 0.0};
-            set_equilibrium_cell(o, cidx(o, i, j), rho[k], uu, p[k]);
-        }
+    for (int kz = 0; kz < o->nz; ++kz)
+        for (int j = 0; j < o->ny; ++j)
+            for (int i = 0; i < o->nx; ++i) {
+                int k = (kz * o->ny + j) * o->nx + i;
+                double uu[3] = {ux[k], (o->D >= 2 && uy) ? uy[k] : 0.0, (o->D == 3 && uz) ? uz[k] : 0.0};
+                set_equilibrium_cell(o, cidx3(o, i, j, kz), rho[k], uu, p[k]);
+            }
     fill_ghosts(o);
     init_face_gauges(o);
     o->t = 0.0; o->dt = 0.0; o->steps = 0;
     o->face_iters = o->face_count = o->nonconv = o->nonphys = o->fallbacks = 0;
+}
+
+void oracle_set_primitive(oracle *o, const double *rho, const double *ux, const double *uy,
+                          const double *p)
+{
+    oracle_set_primitive3(o, rho, ux, uy, NULL, p);
 }
 
 static int bad(double x) { return !(x == x) || isinf(x); }
@@ -501,29 +597,35 @@ static double cfl_dt(const oracle *o)
     for (int i = 0; i < o->Q; ++i)
         for (int a = 0; a < o->D; ++a) cmax = fmax(cmax, fabs(o->L.c[i][a]));
     double rate = 0.0;
-    for (int j = 0; j < o->ny; ++j)
-        for (int i = 0; i < o->nx; ++i) {
-            int c = cidx(o, i, j);
-            double s = sqrt(o->T[c] / o->L.TL) * cmax;
-            rate = fmax(rate, (fabs(o->u[(size_t)c * MAXD + 0]) + s) / o->dx);
-            if (o->D == 2) rate = fmax(rate, (fabs(o->u[(size_t)c * MAXD + 1]) + s) / o->dy);
-        }
+    for (int k = 0; k < o->nz; ++k)
+        for (int j = 0; j < o->ny; ++j)
+            for (int i = 0; i < o->nx; ++i) {
+                int c = cidx3(o, i, j, k);
+                double s = sqrt(o->T[c] / o->L.TL) * cmax;
+                rate = fmax(rate, (fabs(o->u[(size_t)c * MAXD + 0]) + s) / o->dx);
+                if (o->D >= 2) rate = fmax(rate, (fabs(o->u[(size_t)c * MAXD + 1]) + s) / o->dy);
+                if (o->D == 3) rate = fmax(rate, (fabs(o->u[(size_t)c * MAXD + 2]) + s) / o->dz);
+            }
     return o->cfl / rate;
 }
 
-/* One face (Sec. III.B.3).  dir = 0: x-face, dir = 1: y-face.  Cells along the normal:
- * LL, L, R, RR; tangential neighbours of L and R: Lm, Lp, Rm, Rp (2D only).
- * Writes the face gauge (in/out) and the face populations phi (in the face frame). */
-static void solve_face(oracle *o, int dir, const int cells[8], double *gu, double *gT,
+/* One face (Sec. III.B.3).  dir = 0: x-face, 1: y-face, 2: z-face.  Cells along the
+ * normal: LL, L, R, RR; neighbours of L and R along the first tangential axis (the other
+ * axes in increasing order): Lm, Lp, Rm, Rp (2D and 3D); along the second (3D): Lm2, Lp2,
+ * Rm2, Rp2.  Writes the face gauge (in/out) and the face populations phi (in the face
+ * frame). */
+static void solve_face(oracle *o, int dir, const int *cells, double *gu, double *gT,
                        double *face_f, double *face_g, double h)
 {
     const lattice *L = &o->L;
     const int D = o->D, Q = o->Q;
-    const double dn = dir == 0 ? o->dx : o->dy;   /* spacing along the normal */
-    const double dtg = dir == 0 ? o->dy : o->dx;  /* spacing along the tangent */
-    const int tdir = 1 - dir;
-    const int ncell = D == 2 ? 8 : 4;
-    double pf[8][MAXQ], pg[8][MAXQ];
+    const double sp[3] = {o->dx, o->dy, o->dz};
+    const double dn = sp[dir];                    /* spacing along the normal */
+    const int tdir = dir == 0 ? 1 : 0;            /* first tangential axis */
+    const int tdir2 = dir == 2 ? 1 : 2;           /* second tangential axis (3D) */
+    const double dtg = sp[tdir], dtg2 = sp[tdir2];
+    const int ncell = D == 3 ? 12 : (D == 2 ? 8 : 4);
+    double pf[12][MAXQ], pg[12][MAXQ];
     double lam_u[MAXD] = {0}, lam_T = *gT;
     for (int a = 0; a < D; ++a) lam_u[a] = gu[a];
     double fbar[MAXQ], gbar[MAXQ];
@@ -549,14 +651,20 @@ static void solve_face(oracle *o, int dir, const int cells[8], double *gu, doubl
             else              { up = 2; lo = 1; hi = 3; tm = 6; tp = 7; off_n = -0.5 * dn; }
             /* departure point x' = x_b - v h, measured from the upwind cell centre */
             double dxn = off_n - v[dir] * h;
-            double dxt = D == 2 ? -v[tdir] * h : 0.0;
+            double dxt = D >= 2 ? -v[tdir] * h : 0.0;
+            double dxt2 = D == 3 ? -v[tdir2] * h : 0.0;
             for (int pop = 0; pop < 2; ++pop) {
                 double (*P)[MAXQ] = pop == 0 ? pf : pg;
                 double sn = limiter(o->limiter, (P[up][i] - P[lo][i]) / dn, (P[hi][i] - P[up][i]) / dn);
                 double st = 0.0;
-                if (D == 2)
+                if (D >= 2)
                     st = limiter(o->limiter, (P[up][i] - P[tm][i]) / dtg, (P[tp][i] - P[up][i]) / dtg);
                 double val = P[up][i] + dxn * sn + dxt * st;
+                if (D == 3) {
+                    /* the second tangential neighbours sit 4 slots after the first */
+                    double st2 = limiter(o->limiter, (P[up][i] - P[tm + 4][i]) / dtg2, (P[tp + 4][i] - P[up][i]) / dtg2);
+                    val += dxt2 * st2;
+                }
                 if (pop == 0) fbar[i] = val; else gbar[i] = val;
             }
         }
@@ -566,9 +674,9 @@ static void solve_face(oracle *o, int dir, const int cells[8], double *gu, doubl
         for (int a = 0; a < D; ++a) u1[a] = mom[a] / rho1;
         double T1 = temperature_from(rho1, mom, rhoE, D, o->Cv);
         iters = k + 1;
-        if (!(T1 > 0.0) || bad(rho1) || bad(T1) || bad(u1[0]) || (D == 2 && bad(u1[1]))) {
-            /* this pass defines no frame: restart once from the pooled frame of the two
-             * cells next to the face, otherwise stop at the last pass that did */
+        if (!(T1 > 0.0) || bad(rho1) || bad(T1) || bad(u1[0]) || (D >= 2 && bad(u1[1])) || (D == 3 && bad(u1[2]))) {
+            /* this pass defines no frame: restart once from the pooled frame of the whole
+             * face stencil, otherwise stop at the last pass that did */
             o->fallbacks++;
             if (!restarted) {
                 restarted = 1;
@@ -649,6 +757,26 @@ static void stencil_y(const oracle *o, int i, int j, int cells[8])
     cells[6] = cidx(o, i - 1, j);     cells[7] = cidx(o, i + 1, j);
 }
 
+/* 3D stencil of the face of axis dir whose high-side cell is (i, j, k): along the normal
+ * two cells on each side, then the neighbours of L and R along the first and the second
+ * tangential axis (the same slots as the 2D stencils). */
+static void stencil3(const oracle *o, int dir, int i, int j, int k, int cells[12])
+{
+    int e[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    const int *n = e[dir], *t1 = e[dir == 0 ? 1 : 0], *t2 = e[dir == 2 ? 1 : 2];
+    for (int s = 0; s < 4; ++s)
+        cells[s] = cidx3(o, i + (s - 2) * n[0], j + (s - 2) * n[1], k + (s - 2) * n[2]);
+    for (int side = 0; side < 2; ++side) {          /* L (side 0) and R (side 1) */
+        int bi = i + (side - 1) * n[0], bj = j + (side - 1) * n[1], bk = k + (side - 1) * n[2];
+        cells[4 + 2 * side] = cidx3(o, bi - t1[0], bj - t1[1], bk - t1[2]);
+        cells[5 + 2 * side] = cidx3(o, bi + t1[0], bj + t1[1], bk + t1[2]);
+        cells[8 + 2 * side] = cidx3(o, bi - t2[0], bj - t2[1], bk - t2[2]);
+        cells[9 + 2 * side] = cidx3(o, bi + t2[0], bj + t2[1], bk + t2[2]);
+    }
+}
+
+static void step3(oracle *o, double dt);
+
 /* Advances n time steps (fewer when t_end > 0 is reached).  Returns the number taken. */
 int oracle_step(oracle *o, int n)
 {
@@ -658,11 +786,20 @@ int oracle_step(oracle *o, int n)
     for (int s = 0; s < n; ++s) {
         if (o->t_end > 0.0 && o->t >= o->t_end) break;
         /* 1. every cell in its local frame */
-        for (int j = 0; j < o->ny; ++j)
-            for (int i = 0; i < o->nx; ++i) regauge_cell(o, cidx(o, i, j));
+        for (int k = 0; k < o->nz; ++k)
+            for (int j = 0; j < o->ny; ++j)
+                for (int i = 0; i < o->nx; ++i) regauge_cell(o, cidx3(o, i, j, k));
         fill_ghosts(o);
         double dt = o->forced_dt > 0.0 ? o->forced_dt : cfl_dt(o);
         if (o->t_end > 0.0 && o->t + dt > o->t_end) dt = o->t_end - o->t;
+        if (D == 3) {
+            step3(o, dt);
+            o->t += dt;
+            o->last_dt = dt;
+            o->steps++;
+            taken++;
+            continue;
+        }
         const double h = 0.5 * dt, tau = o->tau;
         /* 2a. phi-bar-plus at every cell (ghosts included), Eq. (Fbarplus) with Eq. (variableTransform) */
         const double cp = (2.0 * tau - h) / (2.0 * tau + dt), ce = 3.0 * h / (2.0 * tau + dt);
@@ -727,6 +864,74 @@ int oracle_step(oracle *o, int n)
         taken++;
     }
     return taken;
+}
+
+/* Steps 2 and 3 of the algorithm on a D3Q64 grid (the 1D/2D loops above with a third
+ * axis): phi-bar-plus everywhere, the faces of the three axes, then the flux of the six
+ * faces of every cell and the update. */
+static void step3(oracle *o, double dt)
+{
+    const lattice *L = &o->L;
+    const int Q = o->Q;
+    const double h = 0.5 * dt, tau = o->tau;
+    const double cp = (2.0 * tau - h) / (2.0 * tau + dt), ce = 3.0 * h / (2.0 * tau + dt);
+    for (int c = 0; c < o->px * o->py * o->pz; ++c) {
+        double rho = 0.0;
+        for (int i = 0; i < Q; ++i) rho += o->f[(size_t)c * Q + i];
+        double feq[MAXQ], geq[MAXQ];
+        equilibria(L, rho, o->T[c], o->Cv, feq, geq);
+        for (int i = 0; i < Q; ++i) {
+            o->fp[(size_t)c * Q + i] = cp * o->f[(size_t)c * Q + i] + ce * feq[i];
+            o->gp[(size_t)c * Q + i] = cp * o->g[(size_t)c * Q + i] + ce * geq[i];
+        }
+    }
+    int cells[12];
+    for (int k = 0; k < o->nz; ++k)
+        for (int j = 0; j < o->ny; ++j)
+            for (int i = 0; i <= o->nx; ++i) {
+                int fi = xface3(o, i, j, k);
+                stencil3(o, 0, i, j, k, cells);
+                solve_face(o, 0, cells, o->xu + (size_t)fi * MAXD, o->xT + fi, o->xf + (size_t)fi * Q, o->xg + (size_t)fi * Q, h);
+            }
+    for (int k = 0; k < o->nz; ++k)
+        for (int j = 0; j <= o->ny; ++j)
+            for (int i = 0; i < o->nx; ++i) {
+                int fi = yface3(o, i, j, k);
+                stencil3(o, 1, i, j, k, cells);
+                solve_face(o, 1, cells, o->yu + (size_t)fi * MAXD, o->yT + fi, o->yf + (size_t)fi * Q, o->yg + (size_t)fi * Q, h);
+            }
+    for (int k = 0; k <= o->nz; ++k)
+        for (int j = 0; j < o->ny; ++j)
+            for (int i = 0; i < o->nx; ++i) {
+                int fi = zface3(o, i, j, k);
+                stencil3(o, 2, i, j, k, cells);
+                solve_face(o, 2, cells, o->zu + (size_t)fi * MAXD, o->zT + fi, o->zf + (size_t)fi * Q, o->zg + (size_t)fi * Q, h);
+            }
+    const double ca = (2.0 * tau - dt) / (2.0 * tau + dt), cb = 2.0 * dt / (2.0 * tau + dt);
+    for (int k = 0; k < o->nz; ++k)
+        for (int j = 0; j < o->ny; ++j)
+            for (int i = 0; i < o->nx; ++i) {
+                int c = cidx3(o, i, j, k);
+                double Ff[MAXQ] = {0}, Fg[MAXQ] = {0};
+                int fl = xface3(o, i, j, k), fr = xface3(o, i + 1, j, k);
+                int fb = yface3(o, i, j, k), ft = yface3(o, i, j + 1, k);
+                int fd = zface3(o, i, j, k), fu = zface3(o, i, j, k + 1);
+                add_face_flux(o, c, o->xu + (size_t)fl * MAXD, o->xT[fl], o->xf + (size_t)fl * Q, o->xg + (size_t)fl * Q, 0, -1.0, 1.0 / o->dx, Ff, Fg);
+                add_face_flux(o, c, o->xu + (size_t)fr * MAXD, o->xT[fr], o->xf + (size_t)fr * Q, o->xg + (size_t)fr * Q, 0, +1.0, 1.0 / o->dx, Ff, Fg);
+                add_face_flux(o, c, o->yu + (size_t)fb * MAXD, o->yT[fb], o->yf + (size_t)fb * Q, o->yg + (size_t)fb * Q, 1, -1.0, 1.0 / o->dy, Ff, Fg);
+                add_face_flux(o, c, o->yu + (size_t)ft * MAXD, o->yT[ft], o->yf + (size_t)ft * Q, o->yg + (size_t)ft * Q, 1, +1.0, 1.0 / o->dy, Ff, Fg);
+                add_face_flux(o, c, o->zu + (size_t)fd * MAXD, o->zT[fd], o->zf + (size_t)fd * Q, o->zg + (size_t)fd * Q, 2, -1.0, 1.0 / o->dz, Ff, Fg);
+                add_face_flux(o, c, o->zu + (size_t)fu * MAXD, o->zT[fu], o->zf + (size_t)fu * Q, o->zg + (size_t)fu * Q, 2, +1.0, 1.0 / o->dz, Ff, Fg);
+                double rho = 0.0;
+                for (int q = 0; q < Q; ++q) rho += o->f[(size_t)c * Q + q];
+                double feq[MAXQ], geq[MAXQ];
+                equilibria(L, rho, o->T[c], o->Cv, feq, geq);
+                for (int q = 0; q < Q; ++q) {
+                    double *fq = o->f + (size_t)c * Q + q, *gq = o->g + (size_t)c * Q + q;
+                    *fq = ca * *fq + cb * feq[q] - dt * Ff[q];
+                    *gq = ca * *gq + cb * geq[q] - dt * Fg[q];
+                }
+            }
 }
 
 /* ------------------------------------------------- semi-Lagrangian realization */
@@ -887,6 +1092,7 @@ int oracle_sl_step(oracle *o, int n)
 {
     const int Q = o->Q, D = o->D;
     int taken = 0;
+    if (D == 3) return -1;   /* the semi-Lagrangian step is written for D1Q4 and D2Q16 */
     for (int s = 0; s < n; ++s) {
         if (o->t_end > 0.0 && o->t >= o->t_end) break;
         fill_ghosts(o);
@@ -912,19 +1118,27 @@ int oracle_sl_step(oracle *o, int n)
 
 /* --------------------------------------------------------------- read-back */
 
-/* Conserved fields per interior cell (x fastest); my may be NULL in 1D. */
+/* Conserved fields per interior cell (x fastest, then y, then z); my may be NULL in 1D,
+ * mz outside 3D. */
+void oracle_conserved3(const oracle *o, double *rho, double *mx, double *my, double *mz, double *E)
+{
+    for (int kz = 0; kz < o->nz; ++kz)
+        for (int j = 0; j < o->ny; ++j)
+            for (int i = 0; i < o->nx; ++i) {
+                int c = cidx3(o, i, j, kz), k = (kz * o->ny + j) * o->nx + i;
+                double r, m[MAXD] = {0}, e;
+                conserved_moments(&o->L, o->f + (size_t)c * o->Q, o->g + (size_t)c * o->Q,
+                                  o->u + (size_t)c * MAXD, o->T[c], &r, m, &e);
+                rho[k] = r; mx[k] = m[0];
+                if (my) my[k] = o->D >= 2 ? m[1] : 0.0;
+                if (mz) mz[k] = o->D == 3 ? m[2] : 0.0;
+                E[k] = e;
+            }
+}
+
 void oracle_conserved(const oracle *o, double *rho, double *mx, double *my, double *E)
 {
-    for (int j = 0; j < o->ny; ++j)
-        for (int i = 0; i < o->nx; ++i) {
-            int c = cidx(o, i, j), k = j * o->nx + i;
-            double r, m[MAXD] = {0}, e;
-            conserved_moments(&o->L, o->f + (size_t)c * o->Q, o->g + (size_t)c * o->Q,
-                              o->u + (size_t)c * MAXD, o->T[c], &r, m, &e);
-            rho[k] = r; mx[k] = m[0];
-            if (my) my[k] = o->D == 2 ? m[1] : 0.0;
-            E[k] = e;
-        }
+    oracle_conserved3(o, rho, mx, my, NULL, E);
 }
 
 /* Populations and frames of the interior cells, each first re-expressed in its own
@@ -933,78 +1147,96 @@ void oracle_conserved(const oracle *o, double *rho, double *mx, double *my, doub
 void oracle_regauged_state(const oracle *o, double *f, double *g, double *u, double *T)
 {
     const lattice *L = &o->L;
-    for (int j = 0; j < o->ny; ++j)
-        for (int i = 0; i < o->nx; ++i) {
-            int c = cidx(o, i, j), k = j * o->nx + i;
-            const double *fc = o->f + (size_t)c * o->Q, *gc = o->g + (size_t)c * o->Q;
-            const double *uc = o->u + (size_t)c * MAXD;
-            double rho, mom[MAXD] = {0}, rhoE, un[MAXD] = {0};
-            conserved_moments(L, fc, gc, uc, o->T[c], &rho, mom, &rhoE);
-            for (int a = 0; a < o->D; ++a) un[a] = mom[a] / rho;
-            double Tn = temperature_from(rho, mom, rhoE, o->D, o->Cv);
-            grad_transform(L, 3, fc, uc, o->T[c], un, Tn, f + (size_t)k * o->Q);
-            grad_transform(L, 2, gc, uc, o->T[c], un, Tn, g + (size_t)k * o->Q);
-            for (int a = 0; a < o->D; ++a) u[(size_t)k * o->D + a] = un[a];
-            T[k] = Tn;
-        }
+    for (int kz = 0; kz < o->nz; ++kz)
+        for (int j = 0; j < o->ny; ++j)
+            for (int i = 0; i < o->nx; ++i) {
+                int c = cidx3(o, i, j, kz), k = (kz * o->ny + j) * o->nx + i;
+                const double *fc = o->f + (size_t)c * o->Q, *gc = o->g + (size_t)c * o->Q;
+                const double *uc = o->u + (size_t)c * MAXD;
+                double rho, mom[MAXD] = {0}, rhoE, un[MAXD] = {0};
+                conserved_moments(L, fc, gc, uc, o->T[c], &rho, mom, &rhoE);
+                for (int a = 0; a < o->D; ++a) un[a] = mom[a] / rho;
+                double Tn = temperature_from(rho, mom, rhoE, o->D, o->Cv);
+                grad_transform(L, 3, fc, uc, o->T[c], un, Tn, f + (size_t)k * o->Q);
+                grad_transform(L, 2, gc, uc, o->T[c], un, Tn, g + (size_t)k * o->Q);
+                for (int a = 0; a < o->D; ++a) u[(size_t)k * o->D + a] = un[a];
+                T[k] = Tn;
+            }
 }
 
 /* Raw state (populations as stored, in the frame of the previous step). */
 void oracle_raw_state(const oracle *o, double *f, double *g, double *u, double *T)
 {
-    for (int j = 0; j < o->ny; ++j)
-        for (int i = 0; i < o->nx; ++i) {
-            int c = cidx(o, i, j), k = j * o->nx + i;
-            memcpy(f + (size_t)k * o->Q, o->f + (size_t)c * o->Q, sizeof(double) * o->Q);
-            memcpy(g + (size_t)k * o->Q, o->g + (size_t)c * o->Q, sizeof(double) * o->Q);
-            for (int a = 0; a < o->D; ++a) u[(size_t)k * o->D + a] = o->u[(size_t)c * MAXD + a];
-            T[k] = o->T[c];
-        }
+    for (int kz = 0; kz < o->nz; ++kz)
+        for (int j = 0; j < o->ny; ++j)
+            for (int i = 0; i < o->nx; ++i) {
+                int c = cidx3(o, i, j, kz), k = (kz * o->ny + j) * o->nx + i;
+                memcpy(f + (size_t)k * o->Q, o->f + (size_t)c * o->Q, sizeof(double) * o->Q);
+                memcpy(g + (size_t)k * o->Q, o->g + (size_t)c * o->Q, sizeof(double) * o->Q);
+                for (int a = 0; a < o->D; ++a) u[(size_t)k * o->D + a] = o->u[(size_t)c * MAXD + a];
+                T[k] = o->T[c];
+            }
 }
 
 /* Overwrites the interior state with populations (f, g) given in frames (u, T). */
 void oracle_set_state(oracle *o, const double *f, const double *g, const double *u, const double *T)
 {
-    for (int j = 0; j < o->ny; ++j)
-        for (int i = 0; i < o->nx; ++i) {
-            int c = cidx(o, i, j), k = j * o->nx + i;
-            memcpy(o->f + (size_t)c * o->Q, f + (size_t)k * o->Q, sizeof(double) * o->Q);
-            memcpy(o->g + (size_t)c * o->Q, g + (size_t)k * o->Q, sizeof(double) * o->Q);
-            for (int a = 0; a < o->D; ++a) o->u[(size_t)c * MAXD + a] = u[(size_t)k * o->D + a];
-            o->T[c] = T[k];
-        }
+    for (int kz = 0; kz < o->nz; ++kz)
+        for (int j = 0; j < o->ny; ++j)
+            for (int i = 0; i < o->nx; ++i) {
+                int c = cidx3(o, i, j, kz), k = (kz * o->ny + j) * o->nx + i;
+                memcpy(o->f + (size_t)c * o->Q, f + (size_t)k * o->Q, sizeof(double) * o->Q);
+                memcpy(o->g + (size_t)c * o->Q, g + (size_t)k * o->Q, sizeof(double) * o->Q);
+                for (int a = 0; a < o->D; ++a) o->u[(size_t)c * MAXD + a] = u[(size_t)k * o->D + a];
+                o->T[c] = T[k];
+            }
     fill_ghosts(o);
     init_face_gauges(o);
 }
 
-/* Face gauges: x-faces [(nx+1)*ny][D+1] then (2D) y-faces [nx*(ny+1)][D+1], as (u..., T). */
-void oracle_face_gauges(const oracle *o, double *xg, double *yg)
+/* Face gauges as (u..., T) rows: x-faces [(nx+1)*ny*nz][D+1], then y-faces
+ * [nx*(ny+1)*nz][D+1] (2D, 3D), then z-faces [nx*ny*(nz+1)][D+1] (3D), each x fastest. */
+void oracle_face_gauges3(const oracle *o, double *xg, double *yg, double *zg)
 {
     int D = o->D;
-    for (int k = 0; k < (o->nx + 1) * o->ny; ++k) {
-        for (int a = 0; a < D; ++a) xg[(size_t)k * (D + 1) + a] = o->xu[(size_t)k * MAXD + a];
-        xg[(size_t)k * (D + 1) + D] = o->xT[k];
-    }
-    if (D == 2 && yg)
-        for (int k = 0; k < o->nx * (o->ny + 1); ++k) {
-            for (int a = 0; a < D; ++a) yg[(size_t)k * (D + 1) + a] = o->yu[(size_t)k * MAXD + a];
-            yg[(size_t)k * (D + 1) + D] = o->yT[k];
+    const double *us[3] = {o->xu, o->yu, o->zu}, *Ts[3] = {o->xT, o->yT, o->zT};
+    double *out[3] = {xg, yg, zg};
+    long long nf[3] = {(long long)(o->nx + 1) * o->ny * o->nz, (long long)o->nx * (o->ny + 1) * o->nz,
+                       (long long)o->nx * o->ny * (o->nz + 1)};
+    for (int d = 0; d < D; ++d) {
+        if (!out[d]) continue;
+        for (long long k = 0; k < nf[d]; ++k) {
+            for (int a = 0; a < D; ++a) out[d][k * (D + 1) + a] = us[d][k * MAXD + a];
+            out[d][k * (D + 1) + D] = Ts[d][k];
         }
+    }
 }
 
-/* Overwrites the face gauges (same layout as oracle_face_gauges). */
-void oracle_set_face_gauges(oracle *o, const double *xg, const double *yg)
+void oracle_face_gauges(const oracle *o, double *xg, double *yg)
+{
+    oracle_face_gauges3(o, xg, o->D == 2 ? yg : NULL, NULL);
+}
+
+/* Overwrites the face gauges (same layout as oracle_face_gauges3). */
+void oracle_set_face_gauges3(oracle *o, const double *xg, const double *yg, const double *zg)
 {
     int D = o->D;
-    for (int k = 0; k < (o->nx + 1) * o->ny; ++k) {
-        for (int a = 0; a < D; ++a) o->xu[(size_t)k * MAXD + a] = xg[(size_t)k * (D + 1) + a];
-        o->xT[k] = xg[(size_t)k * (D + 1) + D];
-    }
-    if (D == 2 && yg)
-        for (int k = 0; k < o->nx * (o->ny + 1); ++k) {
-            for (int a = 0; a < D; ++a) o->yu[(size_t)k * MAXD + a] = yg[(size_t)k * (D + 1) + a];
-            o->yT[k] = yg[(size_t)k * (D + 1) + D];
+    double *us[3] = {o->xu, o->yu, o->zu}, *Ts[3] = {o->xT, o->yT, o->zT};
+    const double *in[3] = {xg, yg, zg};
+    long long nf[3] = {(long long)(o->nx + 1) * o->ny * o->nz, (long long)o->nx * (o->ny + 1) * o->nz,
+                       (long long)o->nx * o->ny * (o->nz + 1)};
+    for (int d = 0; d < D; ++d) {
+        if (!in[d]) continue;
+        for (long long k = 0; k < nf[d]; ++k) {
+            for (int a = 0; a < D; ++a) us[d][k * MAXD + a] = in[d][k * (D + 1) + a];
+            Ts[d][k] = in[d][k * (D + 1) + D];
         }
+    }
+}
+
+void oracle_set_face_gauges(oracle *o, const double *xg, const double *yg)
+{
+    oracle_set_face_gauges3(o, xg, o->D == 2 ? yg : NULL, NULL);
 }
 
 /* time, last dt, steps, face iterations, faces solved, non-converged faces, non-physical
@@ -1021,7 +1253,7 @@ void oracle_stats(const oracle *o, double *t, double *dt, long long *counts)
 int oracle_lattice(int D, double *c, double *w, double *TL)
 {
     lattice L;
-    if (D != 1 && D != 2) return 0;
+    if (D < 1 || D > 3) return 0;
     lattice_init(&L, D);
     for (int i = 0; i < L.Q; ++i) {
         for (int a = 0; a < D; ++a) c[i * D + a] = L.c[i][a];

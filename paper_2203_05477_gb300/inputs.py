@@ -352,3 +352,171 @@ def rmi_2d(kind, nx=600, ny=100):
                    bc=(INFLOW, TRANSMISSIVE, TRANSMISSIVE, TRANSMISSIVE), inflow=inflow, inflow_range=rng,
                    name="rmi%d_%dx%d" % (kind, nx, ny))
 
+
+
+# ------------------------------------------------------------------ 3D (D3Q64) problems
+
+@dataclass
+class Problem3:
+    """A D3Q64 problem on a box of nx x ny x nz cells; fields are flat, x fastest, then y."""
+    nx: int
+    ny: int
+    nz: int
+    x0: float
+    x1: float
+    y0: float
+    y1: float
+    z0: float
+    z1: float
+    gamma: float
+    rho: np.ndarray
+    ux: np.ndarray
+    uy: np.ndarray
+    uz: np.ndarray
+    p: np.ndarray
+    bc: tuple = (TRANSMISSIVE,) * 6   # x-lo, x-hi, y-lo, y-hi, z-lo, z-hi
+    name: str = ""
+    dim: int = 3
+
+    @property
+    def dx(self):
+        return (self.x1 - self.x0) / self.nx
+
+    @property
+    def dy(self):
+        return (self.y1 - self.y0) / self.ny
+
+    @property
+    def dz(self):
+        return (self.z1 - self.z0) / self.nz
+
+    @property
+    def ncell(self):
+        return self.nx * self.ny * self.nz
+
+
+def _grid3(nx, ny, nz, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0)):
+    x = cell_centres(nx, lo[0], hi[0])
+    y = cell_centres(ny, lo[1], hi[1])
+    z = cell_centres(nz, lo[2], hi[2])
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")   # [z][y][x]: x fastest when flattened
+    return X, Y, Z
+
+
+def smooth_periodic_3d(nx, ny, nz, seed, amp=0.1, gamma=1.4, modes=3):
+    """Smooth random periodic fields on the unit cube (a few Fourier modes of relative
+    amplitude amp; a random mean velocity)."""
+    rng = np.random.default_rng(seed)
+    X, Y, Z = _grid3(nx, ny, nz)
+
+    def field_(scale):
+        f = np.zeros_like(X)
+        for _ in range(modes):
+            k = rng.integers(0, 3, 3)
+            k[0] = max(k[0], 1)
+            ph = rng.uniform(0, 2 * np.pi)
+            f += rng.uniform(-1, 1) * np.sin(2 * np.pi * (k[0] * X + k[1] * Y + k[2] * Z) + ph)
+        return scale * f / modes
+
+    rho = np.exp(field_(amp)).ravel()
+    p = np.exp(field_(amp)).ravel()
+    u = [(rng.uniform(-1, 1) + field_(amp)).ravel() for _ in range(3)]
+    return Problem3(nx, ny, nz, 0, 1, 0, 1, 0, 1, gamma, rho, u[0], u[1], u[2], p, bc=(PERIODIC,) * 6,
+                    name="smooth_periodic_3d_%dx%dx%d" % (nx, ny, nz))
+
+
+def shock_tube_3d(left, right, gamma, n, axis, nt=1, x_split=0.5):
+    """A two-state Riemann problem along one axis of the unit box (n cells along it, nt
+    along the others, periodic across it, transmissive along it); left = (rho, u_n, p)."""
+    shape = [nt, nt, nt]
+    shape[axis] = n
+    X, Y, Z = _grid3(*shape)
+    s = (X, Y, Z)[axis].ravel()
+    L = s < x_split
+    rho = np.where(L, left[0], right[0]).astype(np.float64)
+    un = np.where(L, left[1], right[1]).astype(np.float64)
+    p = np.where(L, left[2], right[2]).astype(np.float64)
+    u = [np.zeros_like(rho) for _ in range(3)]
+    u[axis] = un
+    bc = [PERIODIC] * 6
+    bc[2 * axis] = bc[2 * axis + 1] = TRANSMISSIVE
+    return Problem3(shape[0], shape[1], shape[2], 0, 1, 0, 1, 0, 1, float(gamma), rho, u[0], u[1], u[2], p,
+                    bc=tuple(bc), name="tube3d_axis%d_%d" % (axis, n))
+
+
+def spherical_blast_3d(n, r0=0.4, inner=(1.0, 1.0), outer=(0.125, 0.1), gamma=1.4):
+    """The spherical explosion in a box: gas at rest, (rho, p) = inner inside a sphere of
+    radius r0 about the centre of [-1, 1]^3 and outer outside; transmissive sides."""
+    X, Y, Z = _grid3(n, n, n, (-1.0, -1.0, -1.0), (1.0, 1.0, 1.0))
+    inside = (X * X + Y * Y + Z * Z < r0 * r0).ravel()
+    rho = np.where(inside, inner[0], outer[0]).astype(np.float64)
+    p = np.where(inside, inner[1], outer[1]).astype(np.float64)
+    z = np.zeros_like(rho)
+    return Problem3(n, n, n, -1, 1, -1, 1, -1, 1, gamma, rho, z, z.copy(), z.copy(), p,
+                    name="spherical_blast_%d" % n)
+
+
+def octants_3d(n, seed, gamma=1.4, mach_max=2.0):
+    """Eight-octant Riemann problem on the unit cube: each octant draws rho and p
+    log-uniform in [0.1, 10] and a velocity of Mach number uniform in [0, mach_max] pointing
+    towards the centre within a cone of half-angle 45 degrees; transmissive sides."""
+    rng = np.random.default_rng(seed)
+    r8 = np.exp(rng.uniform(np.log(0.1), np.log(10.0), 8))
+    p8 = np.exp(rng.uniform(np.log(0.1), np.log(10.0), 8))
+    M = rng.uniform(0.0, mach_max, 8)
+    u8 = np.zeros((8, 3))
+    for q in range(8):
+        centre = np.array([0.25 + 0.5 * (q & 1), 0.25 + 0.5 * ((q >> 1) & 1), 0.25 + 0.5 * ((q >> 2) & 1)])
+        d = 0.5 - centre
+        d = d / np.linalg.norm(d)
+        w = rng.normal(size=3)
+        w -= (w @ d) * d
+        w /= np.linalg.norm(w)
+        th = rng.uniform(0.0, np.pi / 4)
+        u8[q] = M[q] * np.sqrt(gamma * p8[q] / r8[q]) * (np.cos(th) * d + np.sin(th) * w)
+    X, Y, Z = _grid3(n, n, n)
+    q = ((X > 0.5).astype(np.int64) + 2 * (Y > 0.5).astype(np.int64) + 4 * (Z > 0.5).astype(np.int64)).ravel()
+    return Problem3(n, n, n, 0, 1, 0, 1, 0, 1, gamma, r8[q], u8[q, 0], u8[q, 1], u8[q, 2], p8[q],
+                    name="octants_%d_seed%d" % (n, seed))
+
+
+def permute_3d(pb, perm):
+    """The same problem with the axes relabelled: new axis a is old axis perm[a]."""
+    shape = (pb.nz, pb.ny, pb.nx)                     # array axes [z][y][x]
+    arr = lambda a: np.asarray(a).reshape(shape)
+    # array axis of old spatial axis k is 2 - k; new array axis 2 - a holds old 2 - perm[a]
+    order = [2 - perm[2 - ax] for ax in range(3)]
+    rho, p = (np.transpose(arr(a), order).ravel() for a in (pb.rho, pb.p))
+    uo = [pb.ux, pb.uy, pb.uz]
+    u = [np.transpose(arr(uo[perm[a]]), order).ravel() for a in range(3)]
+    n = (pb.nx, pb.ny, pb.nz)
+    lo, hi = (pb.x0, pb.y0, pb.z0), (pb.x1, pb.y1, pb.z1)
+    bc = []
+    for a in range(3):
+        bc += [pb.bc[2 * perm[a]], pb.bc[2 * perm[a] + 1]]
+    return Problem3(n[perm[0]], n[perm[1]], n[perm[2]], lo[perm[0]], hi[perm[0]], lo[perm[1]], hi[perm[1]],
+                    lo[perm[2]], hi[perm[2]], pb.gamma, rho, u[0], u[1], u[2], p, bc=tuple(bc),
+                    name=pb.name + "_perm%d%d%d" % tuple(perm))
+
+
+def mirror_extend_3d(pb):
+    """A box with reflective walls on both sides of an axis unfolded into the periodic box
+    of twice the length along that axis (the mirror image, normal velocity reversed)."""
+    shape = (pb.nz, pb.ny, pb.nx)
+    f = {k: np.asarray(getattr(pb, k)).reshape(shape) for k in ("rho", "ux", "uy", "uz", "p")}
+    n = [pb.nx, pb.ny, pb.nz]
+    lo, hi = [pb.x0, pb.y0, pb.z0], [pb.x1, pb.y1, pb.z1]
+    bc = list(pb.bc)
+    for axis in range(3):
+        if pb.bc[2 * axis] != REFLECTIVE:
+            continue
+        assert pb.bc[2 * axis + 1] == REFLECTIVE
+        ax = 2 - axis
+        for k in f:
+            s = -1.0 if k == "u" + "xyz"[axis] else 1.0
+            f[k] = np.concatenate([np.flip(f[k], ax) * s, f[k]], axis=ax)
+        lo[axis] -= hi[axis] - lo[axis]
+        n[axis] *= 2
+        bc[2 * axis] = bc[2 * axis + 1] = PERIODIC
+    return Problem3(n[0], n[1], n[2], lo[0], hi[0], lo[1], hi[1], lo[2], hi[2], pb.gamma,
+                    *(f[k].ravel() for k in ("rho", "ux", "uy", "uz", "p")), bc=tuple(bc), name=pb.name + "_unfolded")

@@ -5,6 +5,12 @@ import oracle as O
 
 
 def oracle_for(problem, *, tau, cfl, t_end=0.0, tol=1e-10, max_iter=16, fixed_iters=0, limiter=0):
+    if problem.dim == 3:
+        s = O.make_solver(3, problem.nx, problem.ny, problem.nz, dx=problem.dx, dy=problem.dy, dz=problem.dz,
+                          gamma=problem.gamma, tau=tau, cfl=cfl, t_end=t_end, bc=problem.bc, limiter=limiter,
+                          tol=tol, max_iter=max_iter, fixed_iters=fixed_iters)
+        s.set_primitive3(problem.rho, problem.ux, problem.uy, problem.uz, problem.p)
+        return s
     s = O.make_solver(problem.dim, problem.nx, problem.ny, dx=problem.dx, dy=problem.dy,
                       gamma=problem.gamma, tau=tau, cfl=cfl, t_end=t_end, bc=problem.bc,
                       inflow=problem.inflow, inflow_range=problem.inflow_range, limiter=limiter,
