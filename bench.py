@@ -224,6 +224,42 @@ def bench_sl_vs_fv(args, seed=0, rank=0):
     return out
 
 
+# algorithmic bytes per cell and step of the D3Q64 kernels with FP32 populations and
+# float-float frames: cell state 27 coefficients + 4 frame words (140 B), the faces of a
+# cell 3 x (30 coefficients + 4 frame words) (456 B).  The face kernel reads the state and
+# the face predictors and writes the faces; the cell kernel reads state and faces and
+# writes the state.
+D3_FACE_BYTES_PER_CELL = 140 + 3 * 32 + 456
+D3_CELL_BYTES_PER_CELL = 140 + 456 + 140
+
+
+def bench_d3q64(args, n=128, steps=20, fp64_steps=3, rank=0):
+    """The D3Q64 finite-volume step (Sec. V's three-dimensional extension) on the spherical
+    explosion in a box, n^3 cells, FP32 (and FP64): device time per step through
+    pond_step_timed, face and cell kernels apart."""
+    import paper_2203_05477_gb300 as pond
+    from paper_2203_05477_gb300 import inputs as I
+    pb = I.spherical_blast_3d(n)
+    out = {"workload": "spherical_blast_3d_%d" % n, "cells": pb.ncell, "steps": steps}
+    for prec, k in (("fp32", steps), ("fp64", fp64_steps)):
+        s = pond.Solver3(pb, precision=prec, tau=1e-5, cfl=0.3, max_iter=16)
+        s.set_primitive()
+        s.step(2)
+        d0 = s.sync()
+        ms_face, ms_cell = s.step_timed(k)
+        d1 = s.sync()
+        t = (ms_face + ms_cell) / k
+        out[prec] = {"mlups": pb.ncell / (t * 1e-3) / 1e6, "ms_per_step": t, "face_ms": ms_face / k,
+                     "cell_ms": ms_cell / k, "steps": k,
+                     "passes_per_face": (d1["face_iters"] - d0["face_iters"]) / max(1, d1["face_solves"] - d0["face_solves"]),
+                     "status_ok": d1["status"] == pond.POND_OK}
+        s.close()
+    f32 = out["fp32"]
+    f32["face_gbs"] = D3_FACE_BYTES_PER_CELL * pb.ncell / (f32["face_ms"] * 1e-3) / 1e9
+    f32["cell_gbs"] = D3_CELL_BYTES_PER_CELL * pb.ncell / (f32["cell_ms"] * 1e-3) / 1e9
+    return out
+
+
 def run_reference(args, rank, world):
     """Reference arm: the FP64 CPU oracle (the paper ships no code) on host cores."""
     if rank != 0:
@@ -269,8 +305,9 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="skip the kernel-variant autotuner (use the defaults)")
     ap.add_argument("--tune-cache", default=None,
                     help="autotuner cache file: choices found there are reused without timing (profiling runs)")
-    ap.add_argument("--workload", default="quadrants", choices=["quadrants", "tubes"],
-                    help="tubes: only the batched-tube measurement (profiling case)")
+    ap.add_argument("--workload", default="quadrants", choices=["quadrants", "tubes", "d3q64"],
+                    help="tubes / d3q64: only that measurement (profiling cases)")
+    ap.add_argument("--d3-n", type=int, default=128, help="cells per side of the D3Q64 measurement")
     ap.add_argument("--quick", action="store_true",
                     help="FP32 timed steps only (no e2e, FP64 or CPU legs): the profiling case")
     args = ap.parse_args()
@@ -294,6 +331,10 @@ def main():
     if args.workload == "tubes":
         if rank == 0:
             print(json.dumps(bench_tubes(args)), flush=True)
+        return
+    if args.workload == "d3q64":
+        if rank == 0:
+            print(json.dumps(bench_d3q64(args, n=args.d3_n)), flush=True)
         return
     n = args.n
     pb = I.quadrants_2d(n, seed=replica_seed(args.seed, rank))
@@ -450,6 +491,9 @@ def main():
     tubes["hbm_frac"] = tubes["hbm_gbs"] / hbm_peak
     line["tubes"] = tubes
     line["sl_vs_fv"] = bench_sl_vs_fv(args, rank=rank)
+    d3 = bench_d3q64(args, n=args.d3_n, rank=rank)
+    d3["fp32"]["cell_hbm_frac"] = d3["fp32"]["cell_gbs"] / hbm_peak
+    line["d3q64"] = d3
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(pb, steps=20)
     print(json.dumps(line), flush=True)

@@ -47,8 +47,9 @@ typedef enum {
 
 /* Velocity sets of Table I: D1Q4 (Gauss-Hermite roots of He_4, T_L = 1) and its tensor
  * product D2Q16 (Eq. wi).  D1Q3/D2Q9 cannot carry the third-order Grad projection the
- * paper requires (Sec. II.C) and are refused with POND_ERR_UNSUPPORTED. */
-typedef enum { POND_D1Q3 = 0, POND_D1Q4 = 1, POND_D2Q16 = 2, POND_D2Q9 = 3 } pond_velset;
+ * paper requires (Sec. II.C) and are refused with POND_ERR_UNSUPPORTED.  D3Q64, the tensor
+ * product in three dimensions, is created by pond_init3 (pond_init refuses it). */
+typedef enum { POND_D1Q3 = 0, POND_D1Q4 = 1, POND_D2Q16 = 2, POND_D2Q9 = 3, POND_D3Q64 = 4 } pond_velset;
 
 /* Ghost-cell rules (two layers): copy of the nearest cell (zero gradient), wrap-around,
  * the equilibrium at a prescribed state on part of a side (transmissive on the rest), or a
@@ -123,6 +124,37 @@ typedef struct {
  * Cv >= D/2 (Eq. geqPond), i.e. gamma <= 1 + 2/D.  Allocates all device memory once. */
 pond_status pond_init(const pond_grid *grid, pond_velset velset, double gamma, double tau,
                       const pond_options *opts, pond_state **out);
+
+/* Three-dimensional grids (D3Q64: W_i = w_ix w_iy w_iz of the D1Q4 rule; the extension the
+ * paper names as future work in Sec. V, with the 20 slow f moments of Sec. II.C for D = 3).
+ * Box [x0,x1] x [y0,y1] x [z0,z1] of nx x ny x nz cells; fields are nx*ny*nz values, x
+ * fastest, then y.  Sides are transmissive, periodic (in pairs) or reflective; no inflow. */
+typedef struct {
+    int64_t nx, ny, nz;
+    double x0, x1, y0, y1, z0, z1;
+    int bc[6];                  /* pond_bc for sides x-lo, x-hi, y-lo, y-hi, z-lo, z-hi */
+} pond_grid3;
+
+/* pond_init for a D3Q64 grid: the finite-volume scheme (Sec. III.B) with the face
+ * corrector of Sec. III.B.3 on the faces of all three axes (two tangential limited slopes
+ * per face).  gamma <= 5/3 (Cv >= 3/2, Eq. geqPond).  The learned predictor and the
+ * semi-Lagrangian scheme are D1Q4/D2Q16 features: options asking for them are refused
+ * with POND_ERR_UNSUPPORTED.  On the returned state pond_step, pond_step_timed,
+ * pond_sync, pond_get_state (coef_f [cells][20], coef_g [cells][10], frame [cells][4]:
+ * ux, uy, uz, T; coefficient (r, s, t) at position (r+s+t)(r+s+t+1)(r+s+t+2)/6 +
+ * (s+t)(s+t+1)/2 + t) and pond_destroy work as for the other grids; initial conditions,
+ * moments and face frames go through the three calls below. */
+pond_status pond_init3(const pond_grid3 *grid, double gamma, double tau, const pond_options *opts, pond_state **out);
+/* pond_set_primitive with the third velocity component uz (all five fields required). */
+pond_status pond_set_primitive3(pond_state *s, const double *rho, const double *ux, const double *uy,
+                                const double *uz, const double *p, int on_device);
+/* pond_moments with the third momentum component; totals[5] (rho, mx, my, mz, E). */
+pond_status pond_moments3(pond_state *s, double *rho, double *mx, double *my, double *mz, double *E,
+                          double totals[5], int on_device);
+/* Face frames of the three axes, [nf][4] (ux, uy, uz, T) each: x-faces (nx+1)*ny*nz,
+ * y-faces nx*(ny+1)*nz, z-faces nx*ny*(nz+1), x fastest.  NULL arrays are skipped. */
+pond_status pond_get_face_gauges3(pond_state *s, double *xg, double *yg, double *zg);
+pond_status pond_set_face_gauges3(pond_state *s, const double *xg, const double *yg, const double *zg);
 
 /* Initial condition: the co-moving equilibria Eqs. (feqPond), (geqPond) of primitive
  * fields rho, ux, uy, p (uy may be NULL in 1D).  on_device: the arrays are device

@@ -24,7 +24,7 @@ _lib = None
 
 POND_OK, POND_ERR_INVALID_ARG, POND_ERR_UNSUPPORTED, POND_ERR_OOM, POND_ERR_CUDA = 0, 1, 2, 3, 4
 POND_ERR_NONPHYSICAL, POND_ERR_NOT_CONVERGED, POND_ERR_TIMEOUT = 5, 6, 7
-POND_D1Q3, POND_D1Q4, POND_D2Q16, POND_D2Q9 = 0, 1, 2, 3
+POND_D1Q3, POND_D1Q4, POND_D2Q16, POND_D2Q9, POND_D3Q64 = 0, 1, 2, 3, 4
 POND_FP64, POND_FP32 = 0, 1
 POND_VANLEER, POND_MINMOD = 0, 1
 POND_FV, POND_SL = 0, 1
@@ -40,6 +40,12 @@ class pond_grid(ctypes.Structure):
                 ("y1", ctypes.c_double), ("bc", ctypes.c_int * 4),
                 ("inflow", (ctypes.c_double * 4) * 4), ("inflow_lo", ctypes.c_int64 * 4),
                 ("inflow_hi", ctypes.c_int64 * 4)]
+
+
+class pond_grid3(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("nz", ctypes.c_int64),
+                ("x0", ctypes.c_double), ("x1", ctypes.c_double), ("y0", ctypes.c_double), ("y1", ctypes.c_double),
+                ("z0", ctypes.c_double), ("z1", ctypes.c_double), ("bc", ctypes.c_int * 6)]
 
 
 class pond_options(ctypes.Structure):
@@ -90,6 +96,12 @@ def _load():
             "pond_init": (ctypes.c_int, [ctypes.POINTER(pond_grid), ctypes.c_int, ctypes.c_double,
                                          ctypes.c_double, ctypes.POINTER(pond_options), ctypes.POINTER(vp)]),
             "pond_set_primitive": (ctypes.c_int, [vp, vp, vp, vp, vp, ctypes.c_int]),
+            "pond_init3": (ctypes.c_int, [ctypes.POINTER(pond_grid3), ctypes.c_double, ctypes.c_double,
+                                          ctypes.POINTER(pond_options), ctypes.POINTER(vp)]),
+            "pond_set_primitive3": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, ctypes.c_int]),
+            "pond_moments3": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, ctypes.c_int]),
+            "pond_get_face_gauges3": (ctypes.c_int, [vp, vp, vp, vp]),
+            "pond_set_face_gauges3": (ctypes.c_int, [vp, vp, vp, vp]),
             "pond_step": (ctypes.c_int, [vp, ctypes.c_int64]),
             "pond_step_timed": (ctypes.c_int, [vp, ctypes.c_int64, vp]),
             "pond_moments": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, ctypes.c_int]),
@@ -368,6 +380,83 @@ class Solver:
         p = np.ascontiguousarray(p, dtype=np.float32)
         assert p.size == MLP_PARAMS
         _check(self.lib.pond_gauge_set_params(self.h, _ptr(p)))
+
+
+class Solver3(Solver):
+    """One PonD problem on a D3Q64 grid (see ``inputs.Problem3``): the finite-volume scheme."""
+
+    def __init__(self, problem, *, tau, cfl, precision="fp64", limiter=POND_VANLEER, t_end=0.0,
+                 tol=None, max_iter=16, fixed_iters=0, strict=False, stream=None, torch_alloc=True):
+        import torch
+        lib = _load()
+        self.problem = problem
+        self.D = 3
+        self.nx, self.ny, self.nz = problem.nx, problem.ny, problem.nz
+        self.prec = POND_FP32 if precision in ("fp32", POND_FP32) else POND_FP64
+        g = pond_grid3()
+        g.nx, g.ny, g.nz = problem.nx, problem.ny, problem.nz
+        g.x0, g.x1, g.y0, g.y1, g.z0, g.z1 = problem.x0, problem.x1, problem.y0, problem.y1, problem.z0, problem.z1
+        for k in range(6):
+            g.bc[k] = int(problem.bc[k])
+        self.device = torch.cuda.current_device()
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        o = pond_options()
+        o.precision = self.prec
+        o.limiter = int(limiter)
+        o.cfl = float(cfl)
+        o.t_end = float(t_end)
+        o.tol = float(tol if tol is not None else (1e-10 if self.prec == POND_FP64 else 1e-6))
+        o.max_iter = int(max_iter)
+        o.fixed_iters = int(fixed_iters)
+        o.strict_convergence = int(bool(strict))
+        o.scheme = POND_FV
+        o.stream = self.stream.cuda_stream
+        self._alloc = _TorchAllocator(self.device, self.stream) if torch_alloc else None
+        if self._alloc:
+            o.alloc = self._alloc.alloc_fn
+            o.free = self._alloc.free_fn
+        self._grid, self._opts = g, o
+        self.h = ctypes.c_void_p()
+        _check(lib.pond_init3(ctypes.byref(g), float(problem.gamma), float(tau), ctypes.byref(o), ctypes.byref(self.h)))
+        self.lib = lib
+        self.ncell = self.nx * self.ny * self.nz
+        self.nfc, self.ngc = 20, 10
+
+    def set_primitive(self, rho=None, ux=None, uy=None, uz=None, p=None):
+        pb = self.problem
+        vals = [pb.rho if rho is None else rho, pb.ux if ux is None else ux, pb.uy if uy is None else uy,
+                pb.uz if uz is None else uz, pb.p if p is None else p]
+        on_dev = not isinstance(vals[0], np.ndarray)
+        if not on_dev:
+            vals = [np.ascontiguousarray(v, dtype=np.float64) for v in vals]
+        self._keep = vals
+        _check(self.lib.pond_set_primitive3(self.h, *[_ptr(v) for v in vals], int(on_dev)))
+
+    def moments(self, totals=True):
+        """(rho, mx, my, mz, E) per cell and their compensated totals over the box."""
+        out = [np.zeros(self.ncell) for _ in range(5)]
+        tot = np.zeros(5)
+        _check(self.lib.pond_moments3(self.h, *[_ptr(a) for a in out], _ptr(tot) if totals else None, 0))
+        return out, tot
+
+    def moments_device(self, outs, totals=None):
+        _check(self.lib.pond_moments3(self.h, *[_ptr(a) for a in outs], _ptr(totals), 1))
+
+    def primitive(self):
+        (rho, mx, my, mz, E), _ = self.moments(totals=False)
+        cv = 1.0 / (self.problem.gamma - 1.0)
+        T = (E - 0.5 * (mx * mx + my * my + mz * mz) / rho) / (cv * rho)
+        return rho, mx / rho, my / rho, mz / rho, rho * T
+
+    def face_gauges(self):
+        nx, ny, nz = self.nx, self.ny, self.nz
+        out = (np.zeros(((nx + 1) * ny * nz, 4)), np.zeros((nx * (ny + 1) * nz, 4)), np.zeros((nx * ny * (nz + 1), 4)))
+        _check(self.lib.pond_get_face_gauges3(self.h, *[_ptr(a) for a in out]))
+        return out
+
+    def set_face_gauges(self, xg, yg=None, zg=None):
+        arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.float64) for a in (xg, yg, zg)]
+        _check(self.lib.pond_set_face_gauges3(self.h, *[_ptr(a) for a in arrs]))
 
 
 class BatchSolver(Solver):

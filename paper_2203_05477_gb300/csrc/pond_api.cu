@@ -21,6 +21,7 @@
 #include "../../include/pond.h"
 #include "pond_launch.cuh"
 #include "pond_sl2.cuh"
+#include "pond3_launch.cuh"
 #include "pond_mlp_train.cuh"
 #include "pond_reduce.cuh"
 #include <cuda_bf16.h>
@@ -66,6 +67,9 @@ struct pond_state {
     double *stage = nullptr;      // staging for host transfers and reductions
     size_t stage_doubles = 0;
     alignas(16) unsigned char params[sizeof(pond::Params<2, double>)];
+    // D3Q64 grids
+    pond_grid3 grid3{};
+    alignas(16) unsigned char params3[sizeof(pond::Params3<double>)];
     int64_t launches = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
@@ -193,6 +197,12 @@ pond_status reset_clock(pond_state *s)
     c.tau = s->tau;
     c.dx = (s->grid.x1 - s->grid.x0) / double(s->grid.nx);
     c.dy = s->D == 2 ? (s->grid.y1 - s->grid.y0) / double(s->grid.ny) : 1.0;
+    c.dz = 1.0;
+    if (s->D == 3) {
+        c.dy = (s->grid3.y1 - s->grid3.y0) / double(s->grid3.ny);
+        c.dz = (s->grid3.z1 - s->grid3.z0) / double(s->grid3.nz);
+        c.dx = (s->grid3.x1 - s->grid3.x0) / double(s->grid3.nx);
+    }
     pond::Diag d{};
     d.first_bad = -1;
     CUDA_TRY(cudaMemcpyAsync(s->clock, &c, sizeof(c), cudaMemcpyHostToDevice, s->stream));
@@ -718,6 +728,237 @@ pond_status batch_face_gauges(pond_state *s, double *out, const double *in)
     return POND_OK;
 }
 
+// ------------------------------------------------------------------ D3Q64 grids
+
+template <typename R>
+pond::Params3<R> &params3_of(pond_state *s) { return *reinterpret_cast<pond::Params3<R> *>(s->params3); }
+
+template <typename R>
+pond_status setup3(pond_state *s)
+{
+    using P_t = pond::Params3<R>;
+    using W = typename P_t::W;
+    P_t P{};
+    const pond_grid3 &g = s->grid3;
+    P.nx = g.nx;
+    P.ny = g.ny;
+    P.nz = g.nz;
+    P.dx = (g.x1 - g.x0) / double(g.nx);
+    P.dy = (g.y1 - g.y0) / double(g.ny);
+    P.dz = (g.z1 - g.z0) / double(g.nz);
+    for (int k = 0; k < 6; ++k) P.bc[k] = g.bc[k];
+    P.gamma = s->gamma;
+    P.Cv = 1.0 / (s->gamma - 1.0);
+    P.tau = s->tau;
+    P.limiter = s->opts.limiter;
+    P.Cv_r = R(P.Cv);
+    P.Cvh_r = R(P.Cv - 1.5);
+    P.tol_r = R(s->opts.tol);
+    P.max_iter = s->opts.max_iter;
+    P.fixed_iters = s->opts.fixed_iters;
+    const long long n = P.ncell();
+    size_t off = 0;
+    auto take = [&](size_t b) { size_t o = off; off = align_up(off + b, 256); return o; };
+    const size_t o_sf = take(sizeof(R) * pond::kNFS3 * n), o_sg = take(sizeof(R) * pond::kNG3 * n);
+    const size_t o_sfr = take(sizeof(W) * 4 * n);
+    size_t o_ff[3], o_fg[3], o_ffr[3];
+    long long nf_all = 0;
+    for (int a = 0; a < 3; ++a) {
+        const long long nf = P.nf(a);
+        nf_all += nf;
+        o_ff[a] = take(sizeof(R) * pond::kNF3 * nf);
+        o_fg[a] = take(sizeof(R) * pond::kNG3 * nf);
+        o_ffr[a] = take(sizeof(W) * 4 * nf);
+    }
+    const size_t o_clock = take(sizeof(pond::Clock)), o_diag = take(sizeof(pond::Diag));
+    size_t stage = std::max<size_t>(5 * size_t(n), size_t(pond::kNF3 + pond::kNG3 + 4) * size_t(n));
+    stage = std::max<size_t>(stage, 4 * size_t(nf_all));
+    stage += 2 * (size_t(kReduceBlocks) * 8 + 8);
+    const size_t o_stage = take(8 * stage);
+    s->bytes = off;
+    s->base = static_cast<char *>(dev_alloc(s, off));
+    if (!s->base) return fail(POND_ERR_OOM, "device allocation of %zu bytes failed", off);
+    P.sf = reinterpret_cast<R *>(s->base + o_sf);
+    P.sg = reinterpret_cast<R *>(s->base + o_sg);
+    P.sfr = reinterpret_cast<W *>(s->base + o_sfr);
+    for (int a = 0; a < 3; ++a) {
+        P.ff[a] = reinterpret_cast<R *>(s->base + o_ff[a]);
+        P.fg[a] = reinterpret_cast<R *>(s->base + o_fg[a]);
+        P.ffr[a] = reinterpret_cast<W *>(s->base + o_ffr[a]);
+    }
+    P.clock = reinterpret_cast<pond::Clock *>(s->base + o_clock);
+    P.diag = reinterpret_cast<pond::Diag *>(s->base + o_diag);
+    s->clock = P.clock;
+    s->diag = P.diag;
+    s->stage = reinterpret_cast<double *>(s->base + o_stage);
+    s->stage_doubles = stage;
+    CUDA_TRY(cudaMemsetAsync(s->base, 0, off, s->stream));
+    CUDA_TRY(pond::prepare3<R>());
+    new (s->params3) P_t(P);
+    return POND_OK;
+}
+
+template <typename R>
+pond_status set_primitive3_impl(pond_state *s, const double *rho, const double *ux, const double *uy, const double *uz,
+                                const double *p, int on_device)
+{
+    auto &P = params3_of<R>(s);
+    const long long n = P.ncell();
+    const double *src[5] = {rho, ux, uy, uz, p};
+    const double *d[5];
+    for (int k = 0; k < 5; ++k) {
+        if (on_device) {
+            d[k] = src[k];
+        } else {
+            CUDA_TRY(cudaMemcpyAsync(s->stage + k * n, src[k], 8 * n, cudaMemcpyHostToDevice, s->stream));
+            d[k] = s->stage + k * n;
+        }
+    }
+    pond_status r = reset_clock(s);
+    if (r != POND_OK) return r;
+    pond::launch_init3<R>(P, d[0], d[1], d[2], d[3], d[4], s->stream);
+    s->launches += 2;
+    CUDA_TRY(cudaGetLastError());
+    if (!on_device) CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return POND_OK;
+}
+
+template <typename R>
+void launch_step3(pond_state *s)
+{
+    auto &P = params3_of<R>(s);
+    pond::launch_face3<R>(P, s->stream);
+    pond::launch_cell3<R>(P, s->stream);
+}
+
+template <typename R>
+pond_status step3_impl(pond_state *s, int64_t n_steps)
+{
+    int64_t left = n_steps;
+    if (left >= kGraphSteps) {
+        if (!s->graph_exec) {
+            CUDA_TRY(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+            for (int k = 0; k < kGraphSteps; ++k) launch_step3<R>(s);
+            cudaGraph_t g = nullptr;
+            CUDA_TRY(cudaStreamEndCapture(s->stream, &g));
+            s->graph = g;
+            CUDA_TRY(cudaGraphInstantiate(&s->graph_exec, g, 0));
+        }
+        while (left >= kGraphSteps) {
+            CUDA_TRY(cudaGraphLaunch(s->graph_exec, s->stream));
+            s->launches += 2 * kGraphSteps;
+            left -= kGraphSteps;
+        }
+    }
+    for (; left > 0; --left) {
+        launch_step3<R>(s);
+        s->launches += 2;
+    }
+    CUDA_TRY(cudaGetLastError());
+    return POND_OK;
+}
+
+template <typename R>
+pond_status step3_timed_impl(pond_state *s, int64_t n_steps, double *ms)
+{
+    auto &P = params3_of<R>(s);
+    std::vector<cudaEvent_t> ev(size_t(2 * n_steps + 1));
+    for (auto &e : ev) CUDA_TRY(cudaEventCreate(&e));
+    CUDA_TRY(cudaEventRecord(ev[0], s->stream));
+    for (int64_t k = 0; k < n_steps; ++k) {
+        pond::launch_face3<R>(P, s->stream);
+        CUDA_TRY(cudaEventRecord(ev[2 * k + 1], s->stream));
+        pond::launch_cell3<R>(P, s->stream);
+        CUDA_TRY(cudaEventRecord(ev[2 * k + 2], s->stream));
+    }
+    s->launches += 2 * n_steps;
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaEventSynchronize(ev.back()));
+    for (int64_t k = 0; k < n_steps; ++k) {
+        float a = 0.f, b = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&a, ev[2 * k], ev[2 * k + 1]));
+        CUDA_TRY(cudaEventElapsedTime(&b, ev[2 * k + 1], ev[2 * k + 2]));
+        ms[0] += a;
+        ms[1] += b;
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    return POND_OK;
+}
+
+template <typename R>
+pond_status moments3_impl(pond_state *s, double *rho, double *mx, double *my, double *mz, double *E, double *totals,
+                          int on_device)
+{
+    auto &P = params3_of<R>(s);
+    const long long n = P.ncell();
+    double *o[5] = {rho, mx, my, mz, E};
+    double *d[5];
+    for (int k = 0; k < 5; ++k) d[k] = (on_device && o[k]) ? o[k] : s->stage + k * n;
+    pond::launch_conserved3<R>(P, d[0], d[1], d[2], d[3], d[4], s->stream);
+    s->launches += 1;
+    if (totals) {
+        double *part = s->stage + 5 * n;
+        double *part2 = part + kReduceBlocks * 8 + 8;
+        const int nb = int(std::min<long long>(kReduceBlocks, (n + 255) / 256));
+        const double vol = P.dx * P.dy * P.dz;
+        pond::dd_partial_kernel<<<nb, 256, 0, s->stream>>>(d[0], d[1], d[2], d[3], n, part);
+        pond::dd_final_kernel<<<1, 32, 0, s->stream>>>(part, nb, vol, part + kReduceBlocks * 8);
+        pond::dd_partial_kernel<<<nb, 256, 0, s->stream>>>(d[4], nullptr, nullptr, nullptr, n, part2);
+        pond::dd_final_kernel<<<1, 32, 0, s->stream>>>(part2, nb, vol, part2 + kReduceBlocks * 8);
+        s->launches += 4;
+        CUDA_TRY(cudaMemcpyAsync(totals, part + kReduceBlocks * 8, 4 * 8, cudaMemcpyDeviceToHost, s->stream));
+        CUDA_TRY(cudaMemcpyAsync(totals + 4, part2 + kReduceBlocks * 8, 8, cudaMemcpyDeviceToHost, s->stream));
+    }
+    if (!on_device)
+        for (int k = 0; k < 5; ++k)
+            if (o[k]) CUDA_TRY(cudaMemcpyAsync(o[k], d[k], 8 * n, cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return POND_OK;
+}
+
+template <typename R>
+pond_status get_state3_impl(pond_state *s, double *cf, double *cg, double *fr)
+{
+    auto &P = params3_of<R>(s);
+    const long long n = P.ncell();
+    double *dcf = s->stage, *dcg = dcf + pond::kNF3 * n, *dfr = dcg + pond::kNG3 * n;
+    pond::launch_export3<R>(P, dcf, dcg, dfr, s->stream);
+    s->launches += 1;
+    CUDA_TRY(cudaGetLastError());
+    if (cf) CUDA_TRY(cudaMemcpyAsync(cf, dcf, 8 * pond::kNF3 * n, cudaMemcpyDeviceToHost, s->stream));
+    if (cg) CUDA_TRY(cudaMemcpyAsync(cg, dcg, 8 * pond::kNG3 * n, cudaMemcpyDeviceToHost, s->stream));
+    if (fr) CUDA_TRY(cudaMemcpyAsync(fr, dfr, 8 * 4 * n, cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return POND_OK;
+}
+
+// face frames are stored plane-major [4][nf]; the ABI exchanges [nf][4]
+template <typename R>
+pond_status face_gauges3_impl(pond_state *s, double *const *out, const double *const *in)
+{
+    auto &P = params3_of<R>(s);
+    using W = typename pond::Params3<R>::W;
+    for (int a = 0; a < 3; ++a) {
+        const long long nf = P.nf(a);
+        std::vector<W> h(size_t(4) * nf);
+        if (in) {
+            if (!in[a]) continue;
+            for (long long f = 0; f < nf; ++f)
+                for (int q = 0; q < 4; ++q) pond::fr_store(h[size_t(q) * nf + f], in[a][f * 4 + q]);
+            CUDA_TRY(cudaMemcpyAsync(P.ffr[a], h.data(), sizeof(W) * 4 * nf, cudaMemcpyHostToDevice, s->stream));
+            CUDA_TRY(cudaStreamSynchronize(s->stream));
+        } else {
+            if (!out[a]) continue;
+            CUDA_TRY(cudaMemcpyAsync(h.data(), P.ffr[a], sizeof(W) * 4 * nf, cudaMemcpyDeviceToHost, s->stream));
+            CUDA_TRY(cudaStreamSynchronize(s->stream));
+            for (long long f = 0; f < nf; ++f)
+                for (int q = 0; q < 4; ++q) out[a][f * 4 + q] = pond::fr_value(h[size_t(q) * nf + f]);
+        }
+    }
+    return POND_OK;
+}
+
 template <typename Fn>
 pond_status dispatch_batch(pond_state *s, Fn &&fn)
 {
@@ -748,6 +989,7 @@ pond_status pond_init(const pond_grid *grid, pond_velset velset, double gamma, d
     *out = nullptr;
     if (velset == POND_D1Q3 || velset == POND_D2Q9)
         return fail(POND_ERR_UNSUPPORTED, "D1Q3/D2Q9 cannot carry the third-order Grad projection");
+    if (velset == POND_D3Q64) return fail(POND_ERR_UNSUPPORTED, "D3Q64 grids are created by pond_init3");
     if (velset != POND_D1Q4 && velset != POND_D2Q16) return fail(POND_ERR_INVALID_ARG, "unknown velocity set %d", int(velset));
     const int D = velset == POND_D1Q4 ? 1 : 2;
     if (grid->dim != D) return fail(POND_ERR_INVALID_ARG, "grid dim %d does not match the velocity set", grid->dim);
@@ -819,9 +1061,93 @@ pond_status pond_init(const pond_grid *grid, pond_velset velset, double gamma, d
     return POND_OK;
 }
 
+pond_status pond_init3(const pond_grid3 *grid, double gamma, double tau, const pond_options *opts, pond_state **out)
+{
+    if (!grid || !opts || !out) return fail(POND_ERR_INVALID_ARG, "grid, opts and out must not be NULL");
+    *out = nullptr;
+    if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return fail(POND_ERR_INVALID_ARG, "grid must have at least one cell");
+    if (!(grid->x1 > grid->x0) || !(grid->y1 > grid->y0) || !(grid->z1 > grid->z0)) return fail(POND_ERR_INVALID_ARG, "empty domain");
+    if (!(gamma > 1.0)) return fail(POND_ERR_INVALID_ARG, "gamma must exceed 1");
+    if (1.0 / (gamma - 1.0) < 1.5) return fail(POND_ERR_UNSUPPORTED, "gamma > 5/3 makes Cv - 3/2 negative");
+    if (!(tau > 0.0)) return fail(POND_ERR_INVALID_ARG, "tau must be positive");
+    if (opts->precision != POND_FP32 && opts->precision != POND_FP64) return fail(POND_ERR_INVALID_ARG, "bad precision");
+    if (opts->limiter != POND_VANLEER && opts->limiter != POND_MINMOD) return fail(POND_ERR_INVALID_ARG, "bad limiter");
+    if (!(opts->cfl > 0.0) || opts->max_iter < 1 || opts->fixed_iters < 0) return fail(POND_ERR_INVALID_ARG, "bad cfl/max_iter/fixed_iters");
+    if (opts->scheme != POND_FV) return fail(POND_ERR_UNSUPPORTED, "D3Q64 grids run the finite-volume scheme");
+    if (opts->learned) return fail(POND_ERR_UNSUPPORTED, "the learned predictor is a D2Q16 feature");
+    for (int k = 0; k < 6; ++k)
+        if (grid->bc[k] != POND_BC_TRANSMISSIVE && grid->bc[k] != POND_BC_PERIODIC && grid->bc[k] != POND_BC_REFLECTIVE)
+            return fail(POND_ERR_INVALID_ARG, "side %d: D3Q64 sides are transmissive, periodic or reflective", k);
+    for (int a = 0; a < 3; ++a)
+        if ((grid->bc[2 * a] == POND_BC_PERIODIC) != (grid->bc[2 * a + 1] == POND_BC_PERIODIC))
+            return fail(POND_ERR_INVALID_ARG, "periodic sides must come in pairs");
+    pond_state *s = new (std::nothrow) pond_state();
+    if (!s) return fail(POND_ERR_OOM, "host allocation failed");
+    s->D = 3;
+    s->prec = opts->precision;
+    s->grid3 = *grid;
+    s->grid.dim = 3;
+    s->grid.nx = grid->nx;
+    s->grid.ny = grid->ny;
+    s->opts = *opts;
+    s->scheme = POND_FV;
+    s->gamma = gamma;
+    s->tau = tau;
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e != cudaSuccess) { delete s; return fail(POND_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e)); }
+    if (opts->stream) {
+        s->stream = static_cast<cudaStream_t>(opts->stream);
+    } else {
+        e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { delete s; return fail(POND_ERR_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e)); }
+        s->own_stream = true;
+    }
+    pond_status st = s->prec == POND_FP32 ? setup3<float>(s) : setup3<double>(s);
+    if (st == POND_OK) st = reset_clock(s);
+    if (st != POND_OK) { pond_destroy(s); return st; }
+    *out = s;
+    return POND_OK;
+}
+
+pond_status pond_set_primitive3(pond_state *s, const double *rho, const double *ux, const double *uy, const double *uz,
+                                const double *p, int on_device)
+{
+    if (pond_status st = check_state(s)) return st;
+    if (s->D != 3) return fail(POND_ERR_INVALID_ARG, "pond_set_primitive3 needs a D3Q64 state");
+    if (!rho || !ux || !uy || !uz || !p) return fail(POND_ERR_INVALID_ARG, "rho, ux, uy, uz, p must not be NULL");
+    return s->prec == POND_FP32 ? set_primitive3_impl<float>(s, rho, ux, uy, uz, p, on_device)
+                                : set_primitive3_impl<double>(s, rho, ux, uy, uz, p, on_device);
+}
+
+pond_status pond_moments3(pond_state *s, double *rho, double *mx, double *my, double *mz, double *E, double totals[5],
+                          int on_device)
+{
+    if (pond_status st = check_state(s)) return st;
+    if (s->D != 3) return fail(POND_ERR_INVALID_ARG, "pond_moments3 needs a D3Q64 state");
+    return s->prec == POND_FP32 ? moments3_impl<float>(s, rho, mx, my, mz, E, totals, on_device)
+                                : moments3_impl<double>(s, rho, mx, my, mz, E, totals, on_device);
+}
+
+pond_status pond_get_face_gauges3(pond_state *s, double *xg, double *yg, double *zg)
+{
+    if (pond_status st = check_state(s)) return st;
+    if (s->D != 3) return fail(POND_ERR_INVALID_ARG, "pond_get_face_gauges3 needs a D3Q64 state");
+    double *out[3] = {xg, yg, zg};
+    return s->prec == POND_FP32 ? face_gauges3_impl<float>(s, out, nullptr) : face_gauges3_impl<double>(s, out, nullptr);
+}
+
+pond_status pond_set_face_gauges3(pond_state *s, const double *xg, const double *yg, const double *zg)
+{
+    if (pond_status st = check_state(s)) return st;
+    if (s->D != 3) return fail(POND_ERR_INVALID_ARG, "pond_set_face_gauges3 needs a D3Q64 state");
+    const double *in[3] = {xg, yg, zg};
+    return s->prec == POND_FP32 ? face_gauges3_impl<float>(s, nullptr, in) : face_gauges3_impl<double>(s, nullptr, in);
+}
+
 pond_status pond_set_primitive(pond_state *s, const double *rho, const double *ux, const double *uy, const double *p, int on_device)
 {
     if (pond_status st = check_state(s)) return st;
+    if (s->D == 3) return fail(POND_ERR_INVALID_ARG, "D3Q64 states take pond_set_primitive3");
     if (!rho || !ux || !p || (s->D == 2 && !uy)) return fail(POND_ERR_INVALID_ARG, "rho, ux, p (and uy in 2D) must not be NULL");
     if (s->batch) return dispatch_batch(s, [&](auto r) { return batch_set_primitive<decltype(r)>(s, rho, ux, p, on_device); });
     return dispatch(s, [&](auto d, auto r) { return set_primitive_impl<decltype(d)::value, decltype(r)>(s, rho, ux, uy, p, on_device); });
@@ -832,6 +1158,7 @@ pond_status pond_step(pond_state *s, int64_t n_steps)
     if (pond_status st = check_state(s)) return st;
     if (n_steps < 0) return fail(POND_ERR_INVALID_ARG, "n_steps must be >= 0");
     if (s->batch) return dispatch_batch(s, [&](auto r) { return batch_step<decltype(r)>(s, n_steps, nullptr); });
+    if (s->D == 3) return s->prec == POND_FP32 ? step3_impl<float>(s, n_steps) : step3_impl<double>(s, n_steps);
     return dispatch(s, [&](auto d, auto r) { return step_impl<decltype(d)::value, decltype(r)>(s, n_steps); });
 }
 
@@ -840,6 +1167,7 @@ pond_status pond_step_timed(pond_state *s, int64_t n_steps, double ms[2])
     if (pond_status st = check_state(s)) return st;
     if (n_steps < 0 || !ms) return fail(POND_ERR_INVALID_ARG, "n_steps must be >= 0 and ms not NULL");
     if (s->batch) return dispatch_batch(s, [&](auto r) { return batch_step<decltype(r)>(s, n_steps, ms); });
+    if (s->D == 3) return s->prec == POND_FP32 ? step3_timed_impl<float>(s, n_steps, ms) : step3_timed_impl<double>(s, n_steps, ms);
     return dispatch(s, [&](auto d, auto r) { return step_timed_impl<decltype(d)::value, decltype(r)>(s, n_steps, ms); });
 }
 
@@ -847,6 +1175,7 @@ pond_status pond_moments(pond_state *s, double *rho, double *mx, double *my, dou
 {
     if (pond_status st = check_state(s)) return st;
     if (s->batch) return dispatch_batch(s, [&](auto r) { return batch_moments<decltype(r)>(s, rho, mx, my, E, totals, on_device); });
+    if (s->D == 3) return fail(POND_ERR_INVALID_ARG, "D3Q64 states take pond_moments3");
     return dispatch(s, [&](auto d, auto r) { return moments_impl<decltype(d)::value, decltype(r)>(s, rho, mx, my, E, totals, on_device); });
 }
 
@@ -854,6 +1183,8 @@ pond_status pond_get_state(pond_state *s, double *coef_f, double *coef_g, double
 {
     if (pond_status st = check_state(s)) return st;
     if (s->batch) return dispatch_batch(s, [&](auto r) { return batch_get_state<decltype(r)>(s, coef_f, coef_g, frame); });
+    if (s->D == 3) return s->prec == POND_FP32 ? get_state3_impl<float>(s, coef_f, coef_g, frame)
+                                               : get_state3_impl<double>(s, coef_f, coef_g, frame);
     return dispatch(s, [&](auto d, auto r) { return get_state_impl<decltype(d)::value, decltype(r)>(s, coef_f, coef_g, frame); });
 }
 
@@ -861,6 +1192,7 @@ pond_status pond_get_face_gauges(pond_state *s, double *xg, double *yg)
 {
     if (pond_status st = check_state(s)) return st;
     if (!xg && !yg) return POND_OK;
+    if (s->D == 3) return fail(POND_ERR_INVALID_ARG, "D3Q64 states take pond_get_face_gauges3");
     if (s->scheme == POND_SL) return fail(POND_ERR_UNSUPPORTED, "the semi-Lagrangian scheme has no face frames");
     if (s->batch) return xg ? dispatch_batch(s, [&](auto r) { return batch_face_gauges<decltype(r)>(s, xg, nullptr); }) : POND_OK;
     return dispatch(s, [&](auto d, auto r) { return face_gauges_impl<decltype(d)::value, decltype(r)>(s, xg, yg, nullptr, nullptr); });
@@ -870,6 +1202,7 @@ pond_status pond_set_face_gauges(pond_state *s, const double *xg, const double *
 {
     if (pond_status st = check_state(s)) return st;
     if (!xg && !yg) return POND_OK;
+    if (s->D == 3) return fail(POND_ERR_INVALID_ARG, "D3Q64 states take pond_set_face_gauges3");
     if (s->scheme == POND_SL) return fail(POND_ERR_UNSUPPORTED, "the semi-Lagrangian scheme has no face frames");
     if (s->batch) return xg ? dispatch_batch(s, [&](auto r) { return batch_face_gauges<decltype(r)>(s, nullptr, xg); }) : POND_OK;
     return dispatch(s, [&](auto d, auto r) { return face_gauges_impl<decltype(d)::value, decltype(r)>(s, nullptr, nullptr, xg, yg); });
@@ -1361,7 +1694,7 @@ void cache_store(const char *path, const std::string &key, const int v[3])
 
 int variant_total(const pond_state *s)
 {
-    if (s->scheme == POND_SL) return 0;
+    if (s->scheme == POND_SL || s->D == 3) return 0;
     if (s->batch) return s->prec == POND_FP32 ? pond::tube_variants<float>() : pond::tube_variants<double>();
     int nf = 0;
     if (s->D == 2) nf = s->prec == POND_FP32 ? pond::face_variants<2, float>() : pond::face_variants<2, double>();
@@ -1469,7 +1802,7 @@ pond_status pond_autotune(pond_state *s, int steps, const char *cache_path, pond
     if (pond_status st = check_state(s)) return st;
     if (steps < 1) return fail(POND_ERR_INVALID_ARG, "steps must be at least 1");
     pond_tune_result res{};
-    if (s->scheme == POND_SL) {  // one compiled variant: nothing to choose
+    if (s->scheme == POND_SL || s->D == 3) {  // one compiled variant: nothing to choose
         if (out) *out = res;
         return POND_OK;
     }

@@ -95,15 +95,16 @@ enum { FLAG_NONPHYSICAL = 1u, FLAG_NOT_CONVERGED = 2u, FLAG_TIMEOUT = 4u };
 // constants of the step about to run, set with dt (Eqs. FinalUpdateDUGKS, Fbarplus,
 // FluxTransf): update ca = (2tau-dt)/(2tau+dt), cb = 2dt/(2tau+dt); phi-bar-plus
 // cp = (2tau-h)/(2tau+dt), ce = 3h/(2tau+dt); face populations wb = 2tau/(2tau+h),
-// we = h/(2tau+h); departure offsets h/dx, h/dy; h = dt/2
+// we = h/(2tau+h); departure offsets h/dx, h/dy (h/dz on D3Q64 grids); h = dt/2
 template <typename T>
 struct StepC {
     T ca, cb, cp, ce, wb, we, h_dx, h_dy, dt_dx, dt_dy, inv_dx, inv_dy;
+    T h_dz, dt_dz, inv_dz;
 };
 
 struct Clock {
     double t, dt, t_end, cfl;
-    double tau, dx, dy;
+    double tau, dx, dy, dz;
     StepC<double> kd;               // formed in FP64
     StepC<float> kf;                // the same rounded to FP32
     long long steps;
@@ -136,8 +137,12 @@ __host__ __device__ inline void set_step_constants(Clock &c, double dt)
     k.dt_dy = dt / c.dy;
     k.inv_dx = 1.0 / c.dx;
     k.inv_dy = 1.0 / c.dy;
+    k.h_dz = h / c.dz;
+    k.dt_dz = dt / c.dz;
+    k.inv_dz = 1.0 / c.dz;
     c.kf = StepC<float>{float(k.ca),   float(k.cb),   float(k.cp),    float(k.ce),    float(k.wb),     float(k.we),
-                        float(k.h_dx), float(k.h_dy), float(k.dt_dx), float(k.dt_dy), float(k.inv_dx), float(k.inv_dy)};
+                        float(k.h_dx), float(k.h_dy), float(k.dt_dx), float(k.dt_dy), float(k.inv_dx), float(k.inv_dy),
+                        float(k.h_dz), float(k.dt_dz), float(k.inv_dz)};
 }
 
 struct Diag {

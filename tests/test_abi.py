@@ -70,3 +70,41 @@ def test_null_arguments(lib):
     assert L.pond_init(None, pond.POND_D1Q4, 1.4, 1e-5, None, ctypes.byref(h)) == pond.POND_ERR_INVALID_ARG
     assert L.pond_step(None, 1) == pond.POND_ERR_INVALID_ARG
     assert L.pond_sync(None, None) == pond.POND_ERR_INVALID_ARG
+
+
+def _grid3(n=4, bc=(0,) * 6):
+    g = pond.pond_grid3()
+    g.nx, g.ny, g.nz = n, n, n
+    g.x0, g.x1, g.y0, g.y1, g.z0, g.z1 = 0.0, 1.0, 0.0, 1.0, 0.0, 1.0
+    for k in range(6):
+        g.bc[k] = bc[k]
+    return g
+
+
+@pytest.mark.parametrize("change,want", [
+    (lambda g, o: None, "gamma"),                                               # gamma 1.7 > 5/3
+    (lambda g, o: setattr(g, "nz", 0), pond.POND_ERR_INVALID_ARG),
+    (lambda g, o: g.bc.__setitem__(4, 2), pond.POND_ERR_INVALID_ARG),          # no inflow sides in 3D
+    (lambda g, o: g.bc.__setitem__(0, 1), pond.POND_ERR_INVALID_ARG),          # unpaired periodic side
+    (lambda g, o: setattr(o, "scheme", pond.POND_SL), pond.POND_ERR_UNSUPPORTED),
+    (lambda g, o: setattr(o, "learned", 1), pond.POND_ERR_UNSUPPORTED),
+], ids=["gamma", "empty", "inflow", "periodic_pair", "sl", "learned"])
+def test_init3_rejects_bad_arguments(lib, change, want):
+    L = pond._load()
+    g, o = _grid3(), _opts()
+    change(g, o)
+    gamma = 1.7 if want == "gamma" else 1.4
+    h = ctypes.c_void_p()
+    st = L.pond_init3(ctypes.byref(g), gamma, 1e-5, ctypes.byref(o), ctypes.byref(h))
+    assert st == (pond.POND_ERR_UNSUPPORTED if want == "gamma" else want)
+    assert not h.value and L.pond_last_error()
+
+
+def test_d3q64_goes_through_init3(lib):
+    L = pond._load()
+    g, o = _grid(2), _opts()
+    h = ctypes.c_void_p()
+    assert L.pond_init(ctypes.byref(g), pond.POND_D3Q64, 1.4, 1e-5, ctypes.byref(o), ctypes.byref(h)) == pond.POND_ERR_UNSUPPORTED
+    assert L.pond_init3(None, 1.4, 1e-5, None, ctypes.byref(h)) == pond.POND_ERR_INVALID_ARG
+    assert L.pond_set_primitive3(None, None, None, None, None, None, 0) == pond.POND_ERR_INVALID_ARG
+    assert L.pond_moments3(None, None, None, None, None, None, None, 0) == pond.POND_ERR_INVALID_ARG
