@@ -118,15 +118,29 @@ __host__ __device__ __forceinline__ int lab_of_face(int dir, int r, int s, int t
 {
     return dir == 0 ? h3idx(r, s, t) : (dir == 1 ? h3idx(s, r, t) : h3idx(s, t, r));
 }
+// lab index of face-axis coefficient k, per face axis (a warp-uniform constant-bank read)
+struct FacePerm {
+    signed char k[3][kNF3];
+};
+__host__ __device__ constexpr FacePerm make_face_perm()
+{
+    FacePerm P{};
+    for (int d = 0; d < 3; ++d)
+        for (int r = 0; r <= 3; ++r)
+            for (int s = 0; r + s <= 3; ++s)
+                for (int t = 0; r + s + t <= 3; ++t)
+                    P.k[d][h3idx(r, s, t)] = (signed char)(d == 0 ? h3idx(r, s, t) : (d == 1 ? h3idx(s, r, t) : h3idx(s, t, r)));
+    return P;
+}
+static __constant__ FacePerm kFacePerm = make_face_perm();
+
+// the first NC3<N> coefficients of a staged cell in face axes (total orders are kept, so the
+// g set (N = 2) is the head of the same permutation)
 template <int N, typename R>
 __device__ __forceinline__ void to_face(const R *lab, R *face, int dir)
 {
 #pragma unroll
-    for (int r = 0; r <= N; ++r)
-#pragma unroll
-        for (int s = 0; r + s <= N; ++s)
-#pragma unroll
-            for (int t = 0; r + s + t <= N; ++t) face[h3idx(r, s, t)] = lab[lab_of_face(dir, r, s, t)];
+    for (int k = 0; k < NC3<N>::value; ++k) face[k] = lab[kFacePerm.k[dir][k]];
 }
 // face-axis coefficients back to lab axes, by selects (the destination is a register array)
 template <int N, typename R>
@@ -207,6 +221,7 @@ struct StagedCell3 {
     R B[kNG3];
     R du[3];   // frame velocity relative to the tile reference (lab axes)
     R T;
+    R pad;     // odd size in words: neighbouring threads' cells fall in distinct banks
 };
 
 template <typename R>
@@ -315,13 +330,47 @@ __device__ __forceinline__ void cell_maps3(const StagedCell3<R> *c, int dir, con
 }
 
 // One corrector pass at a face (Sec. III.B.3) in frame (dl, Tl) (velocity relative to the
-// face reference dref, face axes).  For each normal node m the seven cells a population
-// (m, n, p) can use -- the upwind cell, its outer and inner normal neighbours and its four
-// tangential neighbours -- are re-expressed in the pass frame, collapsed along the normal
-// at c_m and kept in a per-thread shared-memory scratch (slot-major, thread-minor, NT
-// threads); each population is then evaluated, reconstructed by MUSCL with limited slopes
-// at its departure point, and its Hermite moments accumulated (Phi: f, order 3; Psi: g,
-// order 2, face axes).
+// face reference dref, face axes).  A population (m, n, p) is reconstructed as
+// u + off_n lim(u - l, h - u) + off_1 lim(u - t1-, t1+ - u) + off_2 lim(u - t2-, t2+ - u)
+// from its upwind cell u, that cell's normal neighbours l, h and its tangential neighbours,
+// and only the moments of the reconstructions are kept; they are linear in the three terms,
+// so each normal node m runs three sweeps (normal, first and second tangential slope), each
+// needing the upwind cell and two neighbours.  The cells are re-expressed in the pass frame,
+// collapsed along the normal at c_m and kept in a per-thread shared-memory scratch (3 slots
+// of 16 values, slot-major, thread-minor over NT threads).  Phi: moments of f (order 3),
+// Psi: of g (order 2), face axes.
+template <typename R>
+__device__ __forceinline__ void collapse_normal(const StagedCell3<R> *c, int dir, const R *dref, const R *dl, R Tl,
+                                                R invTl, R rsqTl, const R *hn, R *slot, int NT)
+{
+    Map1<R> X(R(1), R(0), R(0)), Y = X, Z = X;
+    cell_maps3<R>(c, dir, dref, dl, Tl, invTl, rsqTl, X, Y, Z);
+    R tmp[kNF3], F[kNF3];
+    to_face<3, R>(c->A, tmp, dir);
+    shift_scale_3d<3, R>(tmp, X, Y, Z, F);
+#pragma unroll
+    for (int s2 = 0; s2 <= 3; ++s2)
+#pragma unroll
+        for (int t2 = 0; s2 + t2 <= 3; ++t2) {
+            R acc = R(0);
+#pragma unroll
+            for (int r = 0; r + s2 + t2 <= 3; ++r) acc += F[h3idx(r, s2, t2)] * hn[r];
+            slot[h2st(s2, t2) * NT] = acc;
+        }
+    R tg[kNG3], G[kNG3];
+    to_face<2, R>(c->B, tg, dir);
+    shift_scale_3d<2, R>(tg, X, Y, Z, G);
+#pragma unroll
+    for (int s2 = 0; s2 <= 2; ++s2)
+#pragma unroll
+        for (int t2 = 0; s2 + t2 <= 2; ++t2) {
+            R acc = R(0);
+#pragma unroll
+            for (int r = 0; r + s2 + t2 <= 2; ++r) acc += G[h3idx(r, s2, t2)] * hn[r];
+            slot[(10 + h2st(s2, t2)) * NT] = acc;
+        }
+}
+
 template <typename R, int NT>
 __device__ __forceinline__ void corrector_pass3(const FaceBox<R> &box, const R *dref, const R *uabs, const R *dl, R Tl,
                                                 R h_dn, R h_d1, R h_d2, int limiter, R *scr, R *Phi, R *Psi)
@@ -340,42 +389,9 @@ __device__ __forceinline__ void corrector_pass3(const FaceBox<R> &box, const R *
         const R vn = sqTl * tab.c[m] + un;
         const bool left = vn > R(0);
         const R offn = (left ? R(0.5) : R(-0.5)) - vn * h_dn;
-        // scratch slots: 0 upwind, 1 outer (l), 2 inner (h), 3 t1-, 4 t1+, 5 t2-, 6 t2+
-#pragma unroll 1
-        for (int q = 0; q < 7; ++q) {
-            int s;
-            if (q == 0) s = left ? 1 : 2;
-            else if (q == 1) s = left ? 0 : 1;
-            else if (q == 2) s = left ? 2 : 3;
-            else s = (left ? 4 : 6) + ((q - 3) & 1) + ((q - 3) >> 1) * 4;
-            const StagedCell3<R> *c = box.slot(s);
-            Map1<R> X(R(1), R(0), R(0)), Y = X, Z = X;
-            cell_maps3<R>(c, box.dir, dref, dl, Tl, invTl, rsqTl, X, Y, Z);
-            R tmp[kNF3], F[kNF3];
-            to_face<3, R>(c->A, tmp, box.dir);
-            shift_scale_3d<3, R>(tmp, X, Y, Z, F);
-#pragma unroll
-            for (int s2 = 0; s2 <= 3; ++s2)
-#pragma unroll
-                for (int t2 = 0; s2 + t2 <= 3; ++t2) {
-                    R acc = R(0);
-#pragma unroll
-                    for (int r = 0; r + s2 + t2 <= 3; ++r) acc += F[h3idx(r, s2, t2)] * tab.hen[m][r];
-                    scr[(q * 16 + h2st(s2, t2)) * NT] = acc;
-                }
-            R tg[kNG3], G[kNG3];
-            to_face<2, R>(c->B, tg, box.dir);
-            shift_scale_3d<2, R>(tg, X, Y, Z, G);
-#pragma unroll
-            for (int s2 = 0; s2 <= 2; ++s2)
-#pragma unroll
-                for (int t2 = 0; s2 + t2 <= 2; ++t2) {
-                    R acc = R(0);
-#pragma unroll
-                    for (int r = 0; r + s2 + t2 <= 2; ++r) acc += G[h3idx(r, s2, t2)] * tab.hen[m][r];
-                    scr[(q * 16 + 10 + h2st(s2, t2)) * NT] = acc;
-                }
-        }
+        const R hn[4] = {tab.hen[m][0], tab.hen[m][1], tab.hen[m][2], tab.hen[m][3]};
+        // scratch slot 0: the upwind cell
+        collapse_normal<R>(box.slot(left ? 1 : 2), box.dir, dref, dl, Tl, invTl, rsqTl, hn, scr, NT);
         // moments over the tangential nodes of this normal node, in (s, t)
         R S2f[10], S2g[6];
 #pragma unroll
@@ -383,61 +399,66 @@ __device__ __forceinline__ void corrector_pass3(const FaceBox<R> &box, const R *
 #pragma unroll
         for (int q = 0; q < 6; ++q) S2g[q] = R(0);
 #pragma unroll 1
-        for (int n = 0; n < 4; ++n) {
-            const R off1 = -(sqTl * tab.c[n] + u1) * h_d1;
-            // collapse the seven slots along the first tangential axis at c_n
-            R cf[7][4], cg[7][3];
+        for (int sw = 0; sw < 3; ++sw) {
+            // the two neighbours of the sweep: normal (l, h), then first and second tangential (-, +)
+            const int sa = sw == 0 ? (left ? 0 : 1) : (left ? 4 : 6) + 4 * (sw - 1);
+            const int sb = sw == 0 ? (left ? 2 : 3) : sa + 1;
+            collapse_normal<R>(box.slot(sa), box.dir, dref, dl, Tl, invTl, rsqTl, hn, scr + 16 * NT, NT);
+            collapse_normal<R>(box.slot(sb), box.dir, dref, dl, Tl, invTl, rsqTl, hn, scr + 32 * NT, NT);
+            const R plain = sw == 0 ? R(1) : R(0);
+#pragma unroll 1
+            for (int n = 0; n < 4; ++n) {
+                const R off1 = sw == 0 ? offn : -(sqTl * tab.c[n] + u1) * h_d1;
+                // collapse the three slots along the first tangential axis at c_n
+                R cf[3][4], cg[3][3];
 #pragma unroll
-            for (int q = 0; q < 7; ++q) {
+                for (int q = 0; q < 3; ++q) {
 #pragma unroll
-                for (int t2 = 0; t2 <= 3; ++t2) {
-                    R acc = R(0);
+                    for (int t2 = 0; t2 <= 3; ++t2) {
+                        R acc = R(0);
 #pragma unroll
-                    for (int s2 = 0; s2 + t2 <= 3; ++s2) acc += scr[(q * 16 + h2st(s2, t2)) * NT] * tab.hen[n][s2];
-                    cf[q][t2] = acc;
+                        for (int s2 = 0; s2 + t2 <= 3; ++s2) acc += scr[(q * 16 + h2st(s2, t2)) * NT] * tab.hen[n][s2];
+                        cf[q][t2] = acc;
+                    }
+#pragma unroll
+                    for (int t2 = 0; t2 <= 2; ++t2) {
+                        R acc = R(0);
+#pragma unroll
+                        for (int s2 = 0; s2 + t2 <= 2; ++s2) acc += scr[(q * 16 + 10 + h2st(s2, t2)) * NT] * tab.hen[n][s2];
+                        cg[q][t2] = acc;
+                    }
+                }
+                R S1f[4] = {R(0), R(0), R(0), R(0)}, S1g[3] = {R(0), R(0), R(0)};
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    const R off = sw == 2 ? -(sqTl * R(node_c(p)) + u2) * h_d2 : off1;
+                    R fv[3], gv[3];
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        R a = R(0), b = R(0);
+#pragma unroll
+                        for (int t2 = 0; t2 <= 3; ++t2) a += cf[q][t2] * R(hen(t2, p));
+#pragma unroll
+                        for (int t2 = 0; t2 <= 2; ++t2) b += cg[q][t2] * R(hen(t2, p));
+                        fv[q] = a;
+                        gv[q] = b;
+                    }
+                    const R fb = plain * fv[0] + off * limit<R>(limiter, fv[0] - fv[1], fv[2] - fv[0]);
+                    const R gb = plain * gv[0] + off * limit<R>(limiter, gv[0] - gv[1], gv[2] - gv[0]);
+#pragma unroll
+                    for (int t2 = 0; t2 <= 3; ++t2) S1f[t2] += R(node_w(p) * he(t2, p)) * fb;
+#pragma unroll
+                    for (int t2 = 0; t2 <= 2; ++t2) S1g[t2] += R(node_w(p) * he(t2, p)) * gb;
                 }
 #pragma unroll
-                for (int t2 = 0; t2 <= 2; ++t2) {
-                    R acc = R(0);
+                for (int s2 = 0; s2 <= 3; ++s2)
 #pragma unroll
-                    for (int s2 = 0; s2 + t2 <= 2; ++s2) acc += scr[(q * 16 + 10 + h2st(s2, t2)) * NT] * tab.hen[n][s2];
-                    cg[q][t2] = acc;
-                }
+                    for (int t2 = 0; s2 + t2 <= 3; ++t2) S2f[h2st(s2, t2)] += tab.whe[n][s2] * S1f[t2];
+#pragma unroll
+                for (int s2 = 0; s2 <= 2; ++s2)
+#pragma unroll
+                    for (int t2 = 0; s2 + t2 <= 2; ++t2) S2g[h2st(s2, t2)] += tab.whe[n][s2] * S1g[t2];
             }
-            R S1f[4] = {R(0), R(0), R(0), R(0)}, S1g[3] = {R(0), R(0), R(0)};
-#pragma unroll
-            for (int p = 0; p < 4; ++p) {
-                const R off2 = -(sqTl * R(node_c(p)) + u2) * h_d2;
-                R fv[7], gv[7];
-#pragma unroll
-                for (int q = 0; q < 7; ++q) {
-                    R a = R(0), b = R(0);
-#pragma unroll
-                    for (int t2 = 0; t2 <= 3; ++t2) a += cf[q][t2] * R(hen(t2, p));
-#pragma unroll
-                    for (int t2 = 0; t2 <= 2; ++t2) b += cg[q][t2] * R(hen(t2, p));
-                    fv[q] = a;
-                    gv[q] = b;
-                }
-                const R fb = fv[0] + offn * limit<R>(limiter, fv[0] - fv[1], fv[2] - fv[0]) +
-                             off1 * limit<R>(limiter, fv[0] - fv[3], fv[4] - fv[0]) +
-                             off2 * limit<R>(limiter, fv[0] - fv[5], fv[6] - fv[0]);
-                const R gb = gv[0] + offn * limit<R>(limiter, gv[0] - gv[1], gv[2] - gv[0]) +
-                             off1 * limit<R>(limiter, gv[0] - gv[3], gv[4] - gv[0]) +
-                             off2 * limit<R>(limiter, gv[0] - gv[5], gv[6] - gv[0]);
-#pragma unroll
-                for (int t2 = 0; t2 <= 3; ++t2) S1f[t2] += R(node_w(p) * he(t2, p)) * fb;
-#pragma unroll
-                for (int t2 = 0; t2 <= 2; ++t2) S1g[t2] += R(node_w(p) * he(t2, p)) * gb;
-            }
-#pragma unroll
-            for (int s2 = 0; s2 <= 3; ++s2)
-#pragma unroll
-                for (int t2 = 0; s2 + t2 <= 3; ++t2) S2f[h2st(s2, t2)] += tab.whe[n][s2] * S1f[t2];
-#pragma unroll
-            for (int s2 = 0; s2 <= 2; ++s2)
-#pragma unroll
-                for (int t2 = 0; s2 + t2 <= 2; ++t2) S2g[h2st(s2, t2)] += tab.whe[n][s2] * S1g[t2];
         }
 #pragma unroll
         for (int r = 0; r <= 3; ++r)
@@ -596,19 +617,21 @@ __device__ __forceinline__ void solve_face3(const FaceBox<R> &box, const R *dref
 
 // Tiles of the 3D face kernel: TX x TY x TZ cells per CTA, one thread per face of each axis
 // (3 TX TY TZ threads), the box [i0-2, i0+TX] x [j0-2, j0+TY] x [k0-2, k0+TZ] staged in
-// dynamic shared memory, followed by the per-thread corrector scratch (7 x 16 values).
+// dynamic shared memory, followed by the per-thread corrector scratch (3 x 16 values); two
+// CTAs per SM.
 template <typename R>
 struct Face3Tile {
     static constexpr int TX = 4, TY = 4, TZ = sizeof(R) == 4 ? 4 : 2;
     static constexpr int THREADS = 3 * TX * TY * TZ;
+    static constexpr int MINB = 2;
     static constexpr int BX = TX + 3, BY = TY + 3, BZ = TZ + 3;
     static constexpr size_t tile_bytes = sizeof(StagedCell3<R>) * BX * BY * BZ;
-    static constexpr size_t scratch_bytes = sizeof(R) * 7 * 16 * THREADS;
+    static constexpr size_t scratch_bytes = sizeof(R) * 3 * 16 * THREADS;
     static constexpr size_t smem = tile_bytes + scratch_bytes;
 };
 
 template <typename R>
-__global__ void __launch_bounds__(Face3Tile<R>::THREADS, 1)
+__global__ void __launch_bounds__(Face3Tile<R>::THREADS, Face3Tile<R>::MINB)
 face3_kernel(const Params3<R> P)
 {
     using Tl_ = Face3Tile<R>;
