@@ -231,6 +231,9 @@ def bench_sl_vs_fv(args, seed=0, rank=0):
 # writes the state.
 D3_FACE_BYTES_PER_CELL = 140 + 3 * 32 + 456
 D3_CELL_BYTES_PER_CELL = 140 + 456 + 140
+# executed FP32 FLOP per face-pass of face3_kernel<float> (FFMA x 2 + FADD + FMUL), counted by
+# ncu on the 64^3 spherical explosion (profiles/face3_kernel_blast64_fp32.md)
+D3_FLOPS_PER_FACE_PASS = 33.6e3
 
 
 def bench_d3q64(args, n=128, steps=20, fp64_steps=3, rank=0):
@@ -254,9 +257,12 @@ def bench_d3q64(args, n=128, steps=20, fp64_steps=3, rank=0):
                      "passes_per_face": (d1["face_iters"] - d0["face_iters"]) / max(1, d1["face_solves"] - d0["face_solves"]),
                      "status_ok": d1["status"] == pond.POND_OK}
         s.close()
+        if prec == "fp32":
+            out[prec]["face_passes_per_step"] = (d1["face_iters"] - d0["face_iters"]) / k
     f32 = out["fp32"]
     f32["face_gbs"] = D3_FACE_BYTES_PER_CELL * pb.ncell / (f32["face_ms"] * 1e-3) / 1e9
     f32["cell_gbs"] = D3_CELL_BYTES_PER_CELL * pb.ncell / (f32["cell_ms"] * 1e-3) / 1e9
+    f32["face_tflops"] = D3_FLOPS_PER_FACE_PASS * f32["face_passes_per_step"] / (f32["face_ms"] * 1e-3) / 1e12
     return out
 
 
@@ -493,6 +499,7 @@ def main():
     line["sl_vs_fv"] = bench_sl_vs_fv(args, rank=rank)
     d3 = bench_d3q64(args, n=args.d3_n, rank=rank)
     d3["fp32"]["cell_hbm_frac"] = d3["fp32"]["cell_gbs"] / hbm_peak
+    d3["fp32"]["face_alu_frac"] = d3["fp32"]["face_tflops"] / fp32_peak
     line["d3q64"] = d3
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(pb, steps=20)
