@@ -263,7 +263,31 @@ def bench_d3q64(args, n=128, steps=20, fp64_steps=3, rank=0):
     f32["face_gbs"] = D3_FACE_BYTES_PER_CELL * pb.ncell / (f32["face_ms"] * 1e-3) / 1e9
     f32["cell_gbs"] = D3_CELL_BYTES_PER_CELL * pb.ncell / (f32["cell_ms"] * 1e-3) / 1e9
     f32["face_tflops"] = D3_FLOPS_PER_FACE_PASS * f32["face_passes_per_step"] / (f32["face_ms"] * 1e-3) / 1e12
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_3d(pb)
     return out
+
+
+def cpu_baseline_3d(pb, side=12, steps=3, target_s=10.0):
+    """The FP64 oracle, single thread, on a side^3 patch of the 3D workload that crosses the
+    explosion's spherical front."""
+    import oracle as O
+    from paper_2203_05477_gb300 import inputs as I
+    n = pb.nx
+    c0 = n // 2 + int(0.4 * n / 2) - side // 2, n // 2 - side // 2, n // 2 - side // 2
+    sub = lambda a: np.asarray(a).reshape(n, n, n)[c0[2]:c0[2] + side, c0[1]:c0[1] + side, c0[0]:c0[0] + side].ravel()
+    patch = I.Problem3(side, side, side, 0, side * pb.dx, 0, side * pb.dy, 0, side * pb.dz, pb.gamma,
+                       sub(pb.rho), sub(pb.ux), sub(pb.uy), sub(pb.uz), sub(pb.p))
+    s = O.make_solver(3, side, side, side, dx=patch.dx, dy=patch.dy, dz=patch.dz, gamma=patch.gamma, tau=1e-5,
+                      cfl=0.3, tol=1e-10, max_iter=16)
+    s.set_primitive3(patch.rho, patch.ux, patch.uy, patch.uz, patch.p)
+    done, t0 = 0, time.perf_counter()
+    while done < steps and (time.perf_counter() - t0) < target_s:
+        s.step(1)
+        done += 1
+    el = time.perf_counter() - t0
+    return {"value": side ** 3 * done / el / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": "%d^3 patch across the spherical front, %d steps, FP64, single thread, %.1f s" % (side, done, el)}
 
 
 def run_reference(args, rank, world):
