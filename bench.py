@@ -408,6 +408,7 @@ def main():
     if args.quick:
         if rank == 0:
             print(json.dumps({"quick": True, "value": value, "unit": "MLUPS", "ms_per_step": el_ms / args.steps,
+                              "face_variant": variant_names[fv], "tune_ms": None if tune is None else tune["ms"],
                               "face_ms": ms_face / args.steps, "cell_ms": ms_cell / args.steps,
                               "passes_per_face": face_passes / max(faces, 1), "status_ok": status_ok}), flush=True)
         return
