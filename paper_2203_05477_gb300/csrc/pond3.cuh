@@ -197,7 +197,7 @@ __device__ __forceinline__ long long resolve3(const Params3<R> &P, long long i, 
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (c[a] >= 0 && c[a] < n[a]) continue;
-        const int b = P.bc[2 * a + (c[a] < 0 ? 0 : 1)];
+        const int b = c[a] < 0 ? P.bc[2 * a] : P.bc[2 * a + 1];   // selects: no run-time indexed parameter
         if (b == BC_REFLECTIVE) {
             c[a] = c[a] < 0 ? -1 - c[a] : 2 * n[a] - 1 - c[a];
             c[a] = clampll(c[a], 0, n[a] - 1);
@@ -371,6 +371,71 @@ __device__ __forceinline__ void collapse_normal(const StagedCell3<R> *c, int dir
         }
 }
 
+// The populations (n, p = 0..3) of one sweep at normal node m, FP32: the three scratch slots
+// (upwind cell, two neighbours; normal-collapsed) collapsed along the first tangential axis
+// at c_n, evaluated at c_p, reconstructed (plain * upwind + off * limited slope) and their
+// moments along the second tangential axis accumulated into S1f (f, orders 0..3) and S1g
+// (g, 0..2).  f rides in lane x and g in lane y of FP32x2 pairs for the orders 0..2.
+__device__ __forceinline__ void sweep_node_f32(const float *scr, int NT, int n, float off1, bool off_by_p, float plain,
+                                               float sqTl, float u2, float h_d2, int limiter, float *S1f, float *S1g)
+{
+    const NodeTab<float> &tab = node_tab<float>();
+    const float h0 = tab.hen[n][0], h1 = tab.hen[n][1], h2 = tab.hen[n][2], h3 = tab.hen[n][3];
+    const float2 H0 = bc2(h0), H1 = bc2(h1), H2 = bc2(h2);
+    // c[q][t2]: lane x f, lane y g (t2 = 0..2); cf3[q]: f at t2 = 3
+    float2 c[3][3];
+    float cf3[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const float *b = scr + q * 16 * NT;
+        auto F = [&](int s2, int t2) { return b[h2st(s2, t2) * NT]; };
+        auto G = [&](int s2, int t2) { return b[(10 + h2st(s2, t2)) * NT]; };
+        // t2 = 0: f sums s2 = 0..3, g s2 = 0..2
+        float2 a0 = __fmul2_rn(make_float2(F(0, 0), G(0, 0)), H0);
+        a0 = __ffma2_rn(make_float2(F(1, 0), G(1, 0)), H1, a0);
+        a0 = __ffma2_rn(make_float2(F(2, 0), G(2, 0)), H2, a0);
+        a0.x += F(3, 0) * h3;
+        // t2 = 1: f s2 = 0..2, g s2 = 0..1
+        float2 a1 = __fmul2_rn(make_float2(F(0, 1), G(0, 1)), H0);
+        a1 = __ffma2_rn(make_float2(F(1, 1), G(1, 1)), H1, a1);
+        a1.x += F(2, 1) * h2;
+        // t2 = 2: f s2 = 0..1, g s2 = 0
+        float2 a2 = __fmul2_rn(make_float2(F(0, 2), G(0, 2)), H0);
+        a2.x += F(1, 2) * h1;
+        c[q][0] = a0;
+        c[q][1] = a1;
+        c[q][2] = a2;
+        cf3[q] = F(0, 3) * h0;
+    }
+    float2 S[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    float S3 = 0.f;
+    const float2 minus1 = bc2(-1.f);
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const float off = off_by_p ? -(sqTl * float(node_c(p)) + u2) * h_d2 : off1;
+        float2 v[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            float2 a = __fmul2_rn(c[q][0], bc2(float(hen(0, p))));
+            a = __ffma2_rn(c[q][1], bc2(float(hen(1, p))), a);
+            a = __ffma2_rn(c[q][2], bc2(float(hen(2, p))), a);
+            a.x += cf3[q] * float(hen(3, p));
+            v[q] = a;
+        }
+        const float2 lim = limit2(limiter, __ffma2_rn(v[1], minus1, v[0]), __ffma2_rn(v[0], minus1, v[2]));
+        const float2 b = __ffma2_rn(bc2(off), lim, __fmul2_rn(bc2(plain), v[0]));
+#pragma unroll
+        for (int t2 = 0; t2 <= 2; ++t2) S[t2] = __ffma2_rn(bc2(float(node_w(p) * he(t2, p))), b, S[t2]);
+        S3 += float(node_w(p) * he(3, p)) * b.x;
+    }
+#pragma unroll
+    for (int t2 = 0; t2 <= 2; ++t2) {
+        S1f[t2] = S[t2].x;
+        S1g[t2] = S[t2].y;
+    }
+    S1f[3] = S3;
+}
+
 template <typename R, int NT>
 __device__ __forceinline__ void corrector_pass3(const FaceBox<R> &box, const R *dref, const R *uabs, const R *dl, R Tl,
                                                 R h_dn, R h_d1, R h_d2, int limiter, R *scr, R *Phi, R *Psi)
@@ -409,6 +474,12 @@ __device__ __forceinline__ void corrector_pass3(const FaceBox<R> &box, const R *
 #pragma unroll 1
             for (int n = 0; n < 4; ++n) {
                 const R off1 = sw == 0 ? offn : -(sqTl * tab.c[n] + u1) * h_d1;
+                R S1f[4] = {R(0), R(0), R(0), R(0)}, S1g[3] = {R(0), R(0), R(0)};
+                if constexpr (sizeof(R) == 4) {
+                    // FP32: f in lane x and g in lane y of FP32x2 pairs for the orders both carry
+                    // (0..2), f's third order alone
+                    sweep_node_f32(scr, NT, n, off1, sw == 2, plain, sqTl, u2, h_d2, limiter, S1f, S1g);
+                } else {
                 // collapse the three slots along the first tangential axis at c_n
                 R cf[3][4], cg[3][3];
 #pragma unroll
@@ -428,7 +499,6 @@ __device__ __forceinline__ void corrector_pass3(const FaceBox<R> &box, const R *
                         cg[q][t2] = acc;
                     }
                 }
-                R S1f[4] = {R(0), R(0), R(0), R(0)}, S1g[3] = {R(0), R(0), R(0)};
 #pragma unroll
                 for (int p = 0; p < 4; ++p) {
                     const R off = sw == 2 ? -(sqTl * R(node_c(p)) + u2) * h_d2 : off1;
@@ -449,6 +519,7 @@ __device__ __forceinline__ void corrector_pass3(const FaceBox<R> &box, const R *
                     for (int t2 = 0; t2 <= 3; ++t2) S1f[t2] += R(node_w(p) * he(t2, p)) * fb;
 #pragma unroll
                     for (int t2 = 0; t2 <= 2; ++t2) S1g[t2] += R(node_w(p) * he(t2, p)) * gb;
+                }
                 }
 #pragma unroll
                 for (int s2 = 0; s2 <= 3; ++s2)
@@ -670,9 +741,10 @@ face3_kernel(const Params3<R> P)
         box.bz = tz + 2;
         box.dir = dir;
         const long long nf = P.nf(dir), f = P.fidx(dir, fi, fj, fk);
-        R *Fout = P.ff[dir];
-        R *Gout = P.fg[dir];
-        W *Frm = P.ffr[dir];
+        // selects: a run-time index into the parameter arrays would copy them to local memory
+        R *Fout = dir == 0 ? P.ff[0] : (dir == 1 ? P.ff[1] : P.ff[2]);
+        R *Gout = dir == 0 ? P.fg[0] : (dir == 1 ? P.fg[1] : P.fg[2]);
+        W *Frm = dir == 0 ? P.ffr[0] : (dir == 1 ? P.ffr[1] : P.ffr[2]);
         W uref[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) uref[a] = Frm[a * nf + f];
