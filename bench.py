@@ -191,6 +191,12 @@ def bench_tubes(args, n_tubes=4096, seed=0, rank=0):
     return out
 
 
+# executed FP32 FLOP per node-pass of the semi-Lagrangian kernels (FFMA x 2 + FADD + FMUL, packed
+# forms x 2), counted by ncu on the sl_vs_fv workloads: sl_kernel<float> (D1Q4) 4.124 GFLOP per
+# launch over 4.19 M node-passes, sl2_kernel<float> (D2Q16) 41.17 GFLOP over 2.10 M
+SL_FLOPS_PER_NODE_PASS = {1: 983.0, 2: 19.6e3}
+
+
 def time_schemes(pb, cfl, steps):
     import paper_2203_05477_gb300 as pond
     out = {}
@@ -205,6 +211,10 @@ def time_schemes(pb, cfl, steps):
         out[scheme] = {"ms_per_step": t, "mlups": pb.ncell / (t * 1e-3) / 1e6,
                        "passes": (d1["face_iters"] - d0["face_iters"]) / max(1, d1["face_solves"] - d0["face_solves"]),
                        "status_ok": d1["status"] == pond.POND_OK}
+        if scheme == "sl":
+            # the whole step is one kernel: its executed FLOP rate (ALU roofline)
+            node_passes = (d1["face_iters"] - d0["face_iters"]) / steps
+            out[scheme]["tflops"] = SL_FLOPS_PER_NODE_PASS[pb.dim] * node_passes / (t * 1e-3) / 1e12
         s.close()
     out["fv_over_sl"] = out["fv"]["ms_per_step"] / out["sl"]["ms_per_step"]
     return out
@@ -335,8 +345,8 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="skip the kernel-variant autotuner (use the defaults)")
     ap.add_argument("--tune-cache", default=None,
                     help="autotuner cache file: choices found there are reused without timing (profiling runs)")
-    ap.add_argument("--workload", default="quadrants", choices=["quadrants", "tubes", "d3q64"],
-                    help="tubes / d3q64: only that measurement (profiling cases)")
+    ap.add_argument("--workload", default="quadrants", choices=["quadrants", "tubes", "d3q64", "sl"],
+                    help="tubes / d3q64 / sl: only that measurement (profiling cases)")
     ap.add_argument("--d3-n", type=int, default=128, help="cells per side of the D3Q64 measurement")
     ap.add_argument("--quick", action="store_true",
                     help="FP32 timed steps only (no e2e, FP64 or CPU legs): the profiling case")
@@ -365,6 +375,10 @@ def main():
     if args.workload == "d3q64":
         if rank == 0:
             print(json.dumps(bench_d3q64(args, n=args.d3_n)), flush=True)
+        return
+    if args.workload == "sl":
+        if rank == 0:
+            print(json.dumps(bench_sl_vs_fv(args)), flush=True)
         return
     n = args.n
     pb = I.quadrants_2d(n, seed=replica_seed(args.seed, rank))
@@ -525,6 +539,8 @@ def main():
     d3 = bench_d3q64(args, n=args.d3_n, rank=rank)
     d3["fp32"]["cell_hbm_frac"] = d3["fp32"]["cell_gbs"] / hbm_peak
     d3["fp32"]["face_alu_frac"] = d3["fp32"]["face_tflops"] / fp32_peak
+    for leg in ("d1", "d2"):
+        line["sl_vs_fv"][leg]["sl"]["alu_frac"] = line["sl_vs_fv"][leg]["sl"]["tflops"] / fp32_peak
     line["d3q64"] = d3
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(pb, steps=20)
