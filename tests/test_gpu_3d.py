@@ -89,9 +89,10 @@ def _mixed():
     return pb
 
 
+@pytest.mark.parametrize("limiter", [0, 1], ids=["vanleer", "minmod"])
 @pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
-def test_fp64_parity(name, make):
-    gs, os_ = pair(make(), **KW64)
+def test_fp64_parity(name, make, limiter):
+    gs, os_ = pair(make(), limiter=limiter, **KW64)
     for chunk in (1, 3):
         gs.step(chunk)
         os_.step(chunk)

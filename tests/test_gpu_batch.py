@@ -98,3 +98,16 @@ def test_single_tube_batch_matches_grid_solver():
     (rb, mb, _, Eb), _ = b.moments(totals=False)
     (rg, mg, _, Eg), _ = g.moments(totals=False)
     assert max_rel(rb, rg) <= 1e-13 and max_rel(Eb, Eg) <= 1e-13
+
+
+def test_batch_fp64_parity_minmod():
+    bt = small_batch()
+    kw = dict(tau=1e-5, cfl=0.2, fixed_iters=3, max_iter=8, limiter=1)
+    gs, oracles = run_pair(bt, "fp64", 5, **kw)
+    assert gs.sync()["status"] == pond.POND_OK
+    (rho, mx, _, E), _ = gs.moments()
+    for k, os_ in enumerate(oracles):
+        a, b = gs.offsets[k], gs.offsets[k + 1]
+        ro, mo, _, Eo = os_.conserved()
+        assert max_rel(rho[a:b], ro) <= 1e-12 and max_rel(E[a:b], Eo) <= 1e-12
+        assert np.abs(mx[a:b] - mo).max() <= 1e-12 * max(np.abs(mo).max(), np.sqrt(np.abs(Eo * ro).max()))

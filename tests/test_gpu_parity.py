@@ -266,3 +266,35 @@ def test_full_size_sampled_first_step():
             scale = max(abs(ref), abs(ro[0][k_patch]), abs(ro[3][k_patch]))
             assert abs(results["fp64"][fld][k] - ref) <= FP64_TOL * scale, ("fp64", i, j, fld)
             assert abs(results["fp32"][fld][k] - ref) <= 1e-5 * scale, ("fp32", i, j, fld)
+
+
+@pytest.mark.parametrize("name,pb,cfl", [
+    ("sod_400", I.sod_400(), 0.5),
+    ("quadrants_29x29", I.quadrants_2d(29, seed=0), 0.2),
+    ("lax_liu_24", I.lax_liu_2d(24), 0.2),
+], ids=["sod_400", "quadrants_29x29", "lax_liu_24"])
+def test_fp64_parity_minmod(name, pb, cfl):
+    """The second limiter the paper names (Sec. III.B.3), minmod, in every slope."""
+    kw = dict(tau=1e-5, cfl=cfl, fixed_iters=3, max_iter=8, limiter=1)
+    gs = gpu_for(pb, precision="fp64", **kw)
+    os_ = oracle_for(pb, **kw)
+    for chunk in (1, 5):
+        gs.step(chunk)
+        os_.step(chunk)
+        d, st = gs.sync(), os_.stats()
+        assert d["steps"] == st["steps"] and d["face_iters"] == st["face_iters"]
+        assert d["nonphysical"] == st["nonphysical"] == 0
+        compare_fp64(gs, os_)
+
+
+def test_fp32_minmod_against_fp64_oracle():
+    pb = I.quadrants_2d(48, seed=0)
+    kw = dict(tau=1e-5, cfl=0.2, max_iter=16, limiter=1)
+    gs = gpu_for(pb, precision="fp32", tol=1e-6, **kw)
+    os_ = oracle_for(pb, tol=1e-6, **kw)
+    gs.step(10)
+    os_.step(10)
+    assert gs.sync()["nonphysical"] == 0
+    r, _, _, p = gs.primitive()
+    ro, _, _, po = os_.primitive()
+    assert rel_l1(r, ro) <= 1e-4 and rel_l1(p, po) <= 1e-4
