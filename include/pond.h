@@ -63,7 +63,7 @@ typedef enum { POND_BC_TRANSMISSIVE = 0, POND_BC_PERIODIC = 1, POND_BC_INFLOW = 
  * (about 48 significant bits) in FP32 mode. */
 typedef enum { POND_FP64 = 0, POND_FP32 = 1 } pond_precision;
 
-/* Slope limiters of Sec. III.B.3 ("Van Leer and minmod"). */
+/* Slope limiters named in Sec. III.B.3: van Leer and minmod. */
 typedef enum { POND_VANLEER = 0, POND_MINMOD = 1 } pond_limiter;
 
 typedef struct {
