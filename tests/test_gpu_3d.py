@@ -186,3 +186,38 @@ def test_full_size_sampled_first_step():
             scale = max(abs(ref), abs(ro[0][kp]), abs(ro[4][kp]))
             assert abs(results["fp64"][fld][kg] - ref) <= 1e-12 * scale, ("fp64", i, j, k, fld)
             assert abs(results["fp32"][fld][kg] - ref) <= 1e-5 * scale, ("fp32", i, j, k, fld)
+
+
+def test_abi_round_trips():
+    """Face frames written and read back, device-side moments equal to host-side ones, and
+    the compensated totals equal to the volume-weighted sums of the fields."""
+    pb = I.octants_3d(5, seed=2)
+    gs = pond.Solver3(pb, precision="fp64", tau=1e-5, cfl=0.3, max_iter=16)
+    gs.set_primitive()
+    gs.step(2)
+    xg, yg, zg = gs.face_gauges()
+    rng = np.random.default_rng(0)
+    new = [g * (1.0 + 0.01 * rng.uniform(-1, 1, g.shape)) for g in (xg, yg, zg)]
+    gs.set_face_gauges(*new)
+    for a, b in zip(gs.face_gauges(), new):
+        np.testing.assert_array_equal(a, b)
+    gs.set_face_gauges(None, None, zg)       # NULL arrays are skipped
+    got = gs.face_gauges()
+    np.testing.assert_array_equal(got[0], new[0])
+    np.testing.assert_array_equal(got[2], zg)
+    fields, tot = gs.moments()
+    dev = [torch.empty(gs.ncell, dtype=torch.float64, device="cuda") for _ in range(5)]
+    tot_d = np.zeros(5)
+    gs.moments_device(dev, tot_d)
+    torch.cuda.synchronize()
+    for f, d in zip(fields, dev):
+        np.testing.assert_array_equal(f, d.cpu().numpy())
+    vol = pb.dx * pb.dy * pb.dz
+    for t_, f in zip(tot, fields):
+        assert abs(t_ - f.sum() * vol) <= 1e-13 * np.abs(f).sum() * vol
+    np.testing.assert_array_equal(tot, tot_d)
+    # the calls of the other grids refuse a 3D state
+    assert gs.lib.pond_moments(gs.h, None, None, None, None, None, 0) == pond.POND_ERR_INVALID_ARG
+    assert gs.lib.pond_set_primitive(gs.h, None, None, None, None, 0) == pond.POND_ERR_INVALID_ARG
+    buf = np.zeros(4 * xg.shape[0])
+    assert gs.lib.pond_get_face_gauges(gs.h, buf.ctypes.data, None) == pond.POND_ERR_INVALID_ARG
