@@ -59,7 +59,7 @@ __device__ __forceinline__ void sl_diag_and_advance(Diag *diag, Clock *clock, bo
 }
 
 template <typename R, int TX>
-__global__ void __launch_bounds__(TX)
+__global__ void __launch_bounds__(TX, sizeof(R) == 4 ? 8 : 1)   // FP32: 64 registers, 8 CTAs per SM
 sl_kernel(const Params<1, R> P)
 {
     using W = typename FrameWords<R>::word;
