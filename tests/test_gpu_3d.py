@@ -80,7 +80,15 @@ CASES = [
     ("walled_3", lambda: walled_box(3, 6)),
     ("tube_z_12", lambda: I.shock_tube_3d((1.0, 0.3, 1.0), (0.4, -0.5, 0.3), 1.4, 12, axis=2, nt=2)),
     ("mixed_bc_6x5x4", lambda: _mixed()),
+    ("anisotropic_5x4x3", lambda: _anisotropic()),
 ]
+
+
+def _anisotropic():
+    """Cells of three different sizes (dx = 0.2, dy = 0.125, dz = 0.4)."""
+    pb = I.smooth_periodic_3d(5, 4, 3, seed=9, amp=0.2)
+    pb.y1, pb.z1 = 0.5, 1.2
+    return pb
 
 
 def _mixed():
