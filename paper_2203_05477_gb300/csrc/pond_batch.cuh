@@ -146,8 +146,10 @@ tube_kernel(const TubeParams<R> P, int steps, int cur0)
             // faces c0 .. c0+nc: face k lies between cells k-1 and k
             for (int f = threadIdx.x; f <= nc; f += blockDim.x) {
                 const long long k = c0 + f;
-                const StagedCell<1, R> *cells[8] = {&tile[f], &tile[f + 1], &tile[f + 2], &tile[f + 3],
-                                                    nullptr, nullptr, nullptr, nullptr};
+                Stencil<1, R> cells;   // LL, L, R, RR at tile[f .. f+3]
+                cells.base = &tile[f + 2];
+                cells.sn = 1;
+                cells.st = 0;
                 const R dref[1] = {R(fr_rel(P.fu[f_off + k], utile))};
                 const R uabs[1] = {R(fr_lead(P.fu[f_off + k]))};
                 FaceOut<1, R> o;

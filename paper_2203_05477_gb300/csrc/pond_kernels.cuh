@@ -378,6 +378,34 @@ __device__ __forceinline__ void cell_maps(R Tc, const R *dc, R Tl, R invTl, R rs
     else Y = X;
 }
 
+// The stencil of one face in the staged tile: slot s at offsets (normal, tangential) from
+// cell R -- 0 (-2, 0), 1 (-1, 0), 2 (0, 0), 3 (1, 0), 4 (-1, -1), 5 (-1, 1), 6 (0, -1),
+// 7 (0, 1) -- with the strides (in cells) of the face's normal and tangential axes.  A base
+// pointer and two strides instead of an array of eight pointers keeps registers free.
+template <int D, typename R>
+struct Stencil {
+    const StagedCell<D, R> *base;
+    int sn, st;
+    __device__ __forceinline__ const StagedCell<D, R> *operator[](int s) const
+    {
+        const int on = s < 4 ? s - 2 : (s < 6 ? -1 : 0);
+        const int ot = s < 4 ? 0 : ((s & 1) ? 1 : -1);
+        return base + on * sn + ot * st;
+    }
+};
+
+// frame velocity of a staged cell in face axes (normal, tangential) minus the face reference
+template <int D, typename R>
+__device__ __forceinline__ void rel_velocity(const StagedCell<D, R> *c, const R *dref, bool swap, R *out)
+{
+    if constexpr (D == 1) {
+        out[0] = c->du[0] - dref[0];
+    } else {
+        out[0] = c->du[swap ? 1 : 0] - dref[0];
+        out[1] = c->du[swap ? 0 : 1] - dref[1];
+    }
+}
+
 // ---- FP32x2 helpers (packed FP32 arithmetic of sm_100 and later: one instruction, two lanes)
 __device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
 
@@ -442,7 +470,7 @@ __device__ __forceinline__ void pair_populations(const float *Cu, const float *C
 // the reconstructed f-bar and g-bar are returned (Phi: f, order 3; Psi: g, order 2).
 // Stencil slots: 0 LL, 1 L, 2 R, 3 RR, 4 L-t, 5 L+t, 6 R-t, 7 R+t (t: tangential).
 template <int D, typename R>
-__device__ __forceinline__ void corrector_pass(const StagedCell<D, R> *const *cells, const R (*dc)[D],
+__device__ __forceinline__ void corrector_pass(const Stencil<D, R> &cells, const R *dref,
                                                const R *dl, R Tl, R un_abs, R ut_abs, R h_dn, R h_dt,
                                                bool swap, int limiter, R *Phi, R *Psi)
 {
@@ -455,12 +483,15 @@ __device__ __forceinline__ void corrector_pass(const StagedCell<D, R> *const *ce
     {
         Map1<R> X(R(1), R(0), R(0)), Y(R(1), R(0), R(0));
         R tmp[NFC], tmpg[NGC];
-        cell_maps<D, R>(cells[1]->T, dc[1], Tl, invTl, rsqTl, dl, X, Y);
+        R dcs[D];
+        rel_velocity<D, R>(cells[1], dref, swap, dcs);
+        cell_maps<D, R>(cells[1]->T, dcs, Tl, invTl, rsqTl, dl, X, Y);
         orient<D, 3, R>(cells[1]->A, tmp, swap);
         orient<D, 2, R>(cells[1]->B, tmpg, swap);
         shift_scale<D, 3, R>(tmp, X, Y, FL);
         shift_scale<D, 2, R>(tmpg, X, Y, GL);
-        cell_maps<D, R>(cells[2]->T, dc[2], Tl, invTl, rsqTl, dl, X, Y);
+        rel_velocity<D, R>(cells[2], dref, swap, dcs);
+        cell_maps<D, R>(cells[2]->T, dcs, Tl, invTl, rsqTl, dl, X, Y);
         orient<D, 3, R>(cells[2]->A, tmp, swap);
         orient<D, 2, R>(cells[2]->B, tmpg, swap);
         shift_scale<D, 3, R>(tmp, X, Y, FR);
@@ -484,7 +515,8 @@ __device__ __forceinline__ void corrector_pass(const StagedCell<D, R> *const *ce
             {
                 // slot 0 or 3, chosen by selects so that no array is indexed at run time
                 const StagedCell<D, R> *sc = left ? cells[0] : cells[3];
-                const R dcs[1] = {left ? dc[0][0] : dc[3][0]};
+                R dcs[1];
+                rel_velocity<D, R>(sc, dref, swap, dcs);
                 Map1<R> X(R(1), R(0), R(0)), Y(R(1), R(0), R(0));
                 cell_maps<D, R>(sc->T, dcs, Tl, invTl, rsqTl, dl, X, Y);
                 shift_scale<D, 3, R>(sc->A, X, Y, FS);
@@ -539,8 +571,7 @@ __device__ __forceinline__ void corrector_pass(const StagedCell<D, R> *const *ce
                 constexpr int sa[3] = {0, 4, 5}, sb[3] = {3, 6, 7};
                 const StagedCell<D, R> *sc = left ? cells[sa[q]] : cells[sb[q]];
                 R dcs[D];
-#pragma unroll
-                for (int a = 0; a < D; ++a) dcs[a] = left ? dc[sa[q]][a] : dc[sb[q]][a];
+                rel_velocity<D, R>(sc, dref, swap, dcs);
                 Map1<R> X(R(1), R(0), R(0)), Y(R(1), R(0), R(0));
                 R tmp[NFC], tmpg[NGC], tr[NFC], trg[NGC];
                 cell_maps<D, R>(sc->T, dcs, Tl, invTl, rsqTl, dl, X, Y);
@@ -660,7 +691,7 @@ struct FaceOut {
 // stencil, else the corrector stops at the last pass that did.  The face populations are
 // Eq. (FluxTransf) at the frame of the last valid pass's moments.
 template <int D, typename R>
-__device__ __forceinline__ void solve_face(const StagedCell<D, R> *const *cells, bool swap, const R *dref, const R *uabs,
+__device__ __forceinline__ void solve_face(const Stencil<D, R> &cells, bool swap, const R *dref, const R *uabs,
                                            R Tpred, const FaceCfg<R> &cfg, FaceOut<D, R> &o)
 {
     o.fallbacks = 0;
@@ -668,12 +699,6 @@ __device__ __forceinline__ void solve_face(const StagedCell<D, R> *const *cells,
     constexpr int NFC = NCoef<D, 3>::value, NGC = NCoef<D, 2>::value;
     const int na = swap ? 1 : 0, ta = swap ? 0 : 1;  // normal / tangential axes
     const R h_dn = cfg.h_dn, h_dt = cfg.h_dt;
-    R dc[NCELL][D];
-#pragma unroll
-    for (int s = 0; s < NCELL; ++s) {
-        dc[s][0] = cells[s]->du[na] - dref[0];
-        if constexpr (D == 2) dc[s][1] = cells[s]->du[ta] - dref[1];
-    }
     R uref_t = R(0);
     if constexpr (D == 2) uref_t = uabs[1];
     const R uref_n = uabs[0];
@@ -687,7 +712,7 @@ __device__ __forceinline__ void solve_face(const StagedCell<D, R> *const *cells,
     int iters = 0;
     R Phi[NFC], Psi[NGC];
     for (int k = 0; k < cfg.max_iter && !done; ++k) {
-        corrector_pass<D, R>(cells, dc, dl, Tl, uref_n + dl[0], D == 2 ? uref_t + dl[D - 1] : R(0),
+        corrector_pass<D, R>(cells, dref, dl, Tl, uref_n + dl[0], D == 2 ? uref_t + dl[D - 1] : R(0),
                              h_dn, h_dt, swap, cfg.limiter, Phi, Psi);
         R rho1, du[D], T1;
         const bool ok = pass_frame<D, R>(Phi, Psi, Tl, Cv, rho1, du, T1);
@@ -704,9 +729,10 @@ __device__ __forceinline__ void solve_face(const StagedCell<D, R> *const *cells,
 #pragma unroll
                 for (int s = 0; s < NCELL; ++s) {
                     const R rc = cells[s]->A[0];
-                    R v2 = R(0);
+                    R v2 = R(0), dcs[D];
+                    rel_velocity<D, R>(cells[s], dref, swap, dcs);
 #pragma unroll
-                    for (int a = 0; a < D; ++a) { m[a] += rc * dc[s][a]; v2 += dc[s][a] * dc[s][a]; }
+                    for (int a = 0; a < D; ++a) { m[a] += rc * dcs[a]; v2 += dcs[a] * dcs[a]; }
                     r += rc;
                     e += rc * (Cv * cells[s]->T + R(0.5) * v2);
                 }
@@ -743,7 +769,7 @@ __device__ __forceinline__ void solve_face(const StagedCell<D, R> *const *cells,
     if (have) {
         if (!last_valid) {
             // the last pass defined no frame: recompute the last valid one
-            corrector_pass<D, R>(cells, dc, keep_dl, keep_T, uref_n + keep_dl[0],
+            corrector_pass<D, R>(cells, dref, keep_dl, keep_T, uref_n + keep_dl[0],
                                  D == 2 ? uref_t + keep_dl[D - 1] : R(0), h_dn, h_dt, swap, cfg.limiter, Phi, Psi);
         }
         // Eq. (FluxTransf) in the frame of the last valid pass's moments, with the exact
@@ -830,23 +856,12 @@ face_kernel(const Params<D, R> P)
     unsigned long long my_iters = 0, my_nonconv = 0, my_fallbacks = 0, my_nonphys = 0;
     if (active) {
         // stencil slots in the staged box (box coords of cell (i, j) = (i - i0 + 2, j - j0 + 2))
-        const StagedCell<D, R> *cells[8];
-        auto at = [&](long long ci, long long cj) -> const StagedCell<D, R> * {
-            const int bx = int(ci - i0 + 2), by = D == 2 ? int(cj - j0 + 2) : 0;
-            return &tile[by * BX + bx];
-        };
-        if (dir == 0) {
-            cells[0] = at(fi - 2, fj); cells[1] = at(fi - 1, fj); cells[2] = at(fi, fj); cells[3] = at(fi + 1, fj);
-            if (D == 2) {
-                cells[4] = at(fi - 1, fj - 1); cells[5] = at(fi - 1, fj + 1);
-                cells[6] = at(fi, fj - 1); cells[7] = at(fi, fj + 1);
-            }
-        } else {
-            cells[0] = at(fi, fj - 2); cells[1] = at(fi, fj - 1); cells[2] = at(fi, fj); cells[3] = at(fi, fj + 1);
-            cells[4] = at(fi - 1, fj - 1); cells[5] = at(fi + 1, fj - 1);
-            cells[6] = at(fi - 1, fj); cells[7] = at(fi + 1, fj);
-        }
         const bool swap = dir == 1;
+        // the face's stencil in the staged box (box coords of cell (i, j) = (i - i0 + 2, j - j0 + 2))
+        Stencil<D, R> cells;
+        cells.base = &tile[(D == 2 ? int(fj - j0 + 2) * BX : 0) + int(fi - i0 + 2)];
+        cells.sn = swap ? BX : 1;
+        cells.st = D == 2 ? (swap ? 1 : BX) : 0;
         R *Fout = dir == 0 ? P.xf : P.yf;
         R *Gout = dir == 0 ? P.xg : P.yg;
         W *Frm = dir == 0 ? P.xfr : P.yfr;
