@@ -105,21 +105,24 @@ struct Map1 {
     }
 };
 
-// 1D: out_r = sum_{p<=r} X(r,p) in_p, r <= N
-template <int N, typename R>
+// 1D: out_r = sum_{p<=r} X(r,p) in_p, r <= N.  Z1: in_1 is known to be zero (coefficients in
+// the frame of their own first moment) and its terms are skipped.
+template <int N, typename R, bool Z1 = false>
 __device__ __forceinline__ void shift_scale_1d(const R *in, const Map1<R> &X, R *out)
 {
 #pragma unroll
     for (int r = 0; r <= N; ++r) {
         R acc = R(0);
 #pragma unroll
-        for (int p = 0; p <= r; ++p) acc += X.get(r, p) * in[p];
+        for (int p = 0; p <= r; ++p)
+            if (!(Z1 && p == 1)) acc += X.get(r, p) * in[p];
         out[r] = acc;
     }
 }
 
-// 2D: out_rs = sum_{p<=r} X(r,p) sum_{q<=s} Y(s,q) in_pq, r + s <= N
-template <int N, typename R>
+// 2D: out_rs = sum_{p<=r} X(r,p) sum_{q<=s} Y(s,q) in_pq, r + s <= N.  Z1: in_10 = in_01 = 0;
+// their terms are skipped, and so is the intermediate B_10 (= Y(0,0) in_10 = 0).
+template <int N, typename R, bool Z1 = false>
 __device__ __forceinline__ void shift_scale_2d(const R *in, const Map1<R> &X, const Map1<R> &Y, R *out)
 {
     R B[NCoef<2, N>::value];
@@ -129,7 +132,8 @@ __device__ __forceinline__ void shift_scale_2d(const R *in, const Map1<R> &X, co
         for (int s = 0; s + p <= N; ++s) {
             R acc = R(0);
 #pragma unroll
-            for (int q = 0; q <= s; ++q) acc += Y.get(s, q) * in[hidx(p, q)];
+            for (int q = 0; q <= s; ++q)
+                if (!(Z1 && p + q == 1)) acc += Y.get(s, q) * in[hidx(p, q)];
             B[hidx(p, s)] = acc;
         }
 #pragma unroll
@@ -138,16 +142,17 @@ __device__ __forceinline__ void shift_scale_2d(const R *in, const Map1<R> &X, co
         for (int s = 0; s + r <= N; ++s) {
             R acc = R(0);
 #pragma unroll
-            for (int p = 0; p <= r; ++p) acc += X.get(r, p) * B[hidx(p, s)];
+            for (int p = 0; p <= r; ++p)
+                if (!(Z1 && p == 1 && s == 0)) acc += X.get(r, p) * B[hidx(p, s)];
             out[hidx(r, s)] = acc;
         }
 }
 
-template <int D, int N, typename R>
+template <int D, int N, typename R, bool Z1 = false>
 __device__ __forceinline__ void shift_scale(const R *in, const Map1<R> &X, const Map1<R> &Y, R *out)
 {
-    if constexpr (D == 1) shift_scale_1d<N, R>(in, X, out);
-    else shift_scale_2d<N, R>(in, X, Y, out);
+    if constexpr (D == 1) shift_scale_1d<N, R, Z1>(in, X, out);
+    else shift_scale_2d<N, R, Z1>(in, X, Y, out);
 }
 
 // --------------------------------------------------------------------- limiters

@@ -488,13 +488,13 @@ __device__ __forceinline__ void corrector_pass(const Stencil<D, R> &cells, const
         cell_maps<D, R>(cells[1]->T, dcs, Tl, invTl, rsqTl, dl, X, Y);
         orient<D, 3, R>(cells[1]->A, tmp, swap);
         orient<D, 2, R>(cells[1]->B, tmpg, swap);
-        shift_scale<D, 3, R>(tmp, X, Y, FL);
+        shift_scale<D, 3, R, true>(tmp, X, Y, FL);   // staged f: zero first order
         shift_scale<D, 2, R>(tmpg, X, Y, GL);
         rel_velocity<D, R>(cells[2], dref, swap, dcs);
         cell_maps<D, R>(cells[2]->T, dcs, Tl, invTl, rsqTl, dl, X, Y);
         orient<D, 3, R>(cells[2]->A, tmp, swap);
         orient<D, 2, R>(cells[2]->B, tmpg, swap);
-        shift_scale<D, 3, R>(tmp, X, Y, FR);
+        shift_scale<D, 3, R, true>(tmp, X, Y, FR);
         shift_scale<D, 2, R>(tmpg, X, Y, GR);
     }
 #pragma unroll
@@ -519,7 +519,7 @@ __device__ __forceinline__ void corrector_pass(const Stencil<D, R> &cells, const
                 rel_velocity<D, R>(sc, dref, swap, dcs);
                 Map1<R> X(R(1), R(0), R(0)), Y(R(1), R(0), R(0));
                 cell_maps<D, R>(sc->T, dcs, Tl, invTl, rsqTl, dl, X, Y);
-                shift_scale<D, 3, R>(sc->A, X, Y, FS);
+                shift_scale<D, 3, R, true>(sc->A, X, Y, FS);
                 shift_scale<D, 2, R>(sc->B, X, Y, GS);
             }
             // populations at node m (unweighted: the limiter is homogeneous of degree one,
@@ -577,7 +577,7 @@ __device__ __forceinline__ void corrector_pass(const Stencil<D, R> &cells, const
                 cell_maps<D, R>(sc->T, dcs, Tl, invTl, rsqTl, dl, X, Y);
                 orient<D, 3, R>(sc->A, tmp, swap);
                 orient<D, 2, R>(sc->B, tmpg, swap);
-                shift_scale<D, 3, R>(tmp, X, Y, tr);
+                shift_scale<D, 3, R, true>(tmp, X, Y, tr);
                 shift_scale<D, 2, R>(tmpg, X, Y, trg);
                 collapse_f(tr, CS[q]);
                 collapse_g(trg, DS[q]);
