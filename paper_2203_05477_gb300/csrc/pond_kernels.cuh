@@ -472,7 +472,7 @@ __device__ __forceinline__ void pair_populations(const float *Cu, const float *C
 template <int D, typename R>
 __device__ __forceinline__ void corrector_pass(const Stencil<D, R> &cells, const R *dref,
                                                const R *dl, R Tl, R un_abs, R ut_abs, R h_dn, R h_dt,
-                                               bool swap, int limiter, R *Phi, R *Psi)
+                                               int limiter, R *Phi, R *Psi)
 {
     constexpr int NFC = NCoef<D, 3>::value, NGC = NCoef<D, 2>::value;
     const R invTl = R(1) / Tl;
@@ -484,16 +484,16 @@ __device__ __forceinline__ void corrector_pass(const Stencil<D, R> &cells, const
         Map1<R> X(R(1), R(0), R(0)), Y(R(1), R(0), R(0));
         R tmp[NFC], tmpg[NGC];
         R dcs[D];
-        rel_velocity<D, R>(cells[1], dref, swap, dcs);
+        rel_velocity<D, R>(cells[1], dref, false, dcs);
         cell_maps<D, R>(cells[1]->T, dcs, Tl, invTl, rsqTl, dl, X, Y);
-        orient<D, 3, R>(cells[1]->A, tmp, swap);
-        orient<D, 2, R>(cells[1]->B, tmpg, swap);
+        orient<D, 3, R>(cells[1]->A, tmp, false);
+        orient<D, 2, R>(cells[1]->B, tmpg, false);
         shift_scale<D, 3, R, true>(tmp, X, Y, FL);   // staged f: zero first order
         shift_scale<D, 2, R>(tmpg, X, Y, GL);
-        rel_velocity<D, R>(cells[2], dref, swap, dcs);
+        rel_velocity<D, R>(cells[2], dref, false, dcs);
         cell_maps<D, R>(cells[2]->T, dcs, Tl, invTl, rsqTl, dl, X, Y);
-        orient<D, 3, R>(cells[2]->A, tmp, swap);
-        orient<D, 2, R>(cells[2]->B, tmpg, swap);
+        orient<D, 3, R>(cells[2]->A, tmp, false);
+        orient<D, 2, R>(cells[2]->B, tmpg, false);
         shift_scale<D, 3, R, true>(tmp, X, Y, FR);
         shift_scale<D, 2, R>(tmpg, X, Y, GR);
     }
@@ -516,7 +516,7 @@ __device__ __forceinline__ void corrector_pass(const Stencil<D, R> &cells, const
                 // slot 0 or 3, chosen by selects so that no array is indexed at run time
                 const StagedCell<D, R> *sc = left ? cells[0] : cells[3];
                 R dcs[1];
-                rel_velocity<D, R>(sc, dref, swap, dcs);
+                rel_velocity<D, R>(sc, dref, false, dcs);
                 Map1<R> X(R(1), R(0), R(0)), Y(R(1), R(0), R(0));
                 cell_maps<D, R>(sc->T, dcs, Tl, invTl, rsqTl, dl, X, Y);
                 shift_scale<D, 3, R, true>(sc->A, X, Y, FS);
@@ -571,12 +571,12 @@ __device__ __forceinline__ void corrector_pass(const Stencil<D, R> &cells, const
                 constexpr int sa[3] = {0, 4, 5}, sb[3] = {3, 6, 7};
                 const StagedCell<D, R> *sc = left ? cells[sa[q]] : cells[sb[q]];
                 R dcs[D];
-                rel_velocity<D, R>(sc, dref, swap, dcs);
+                rel_velocity<D, R>(sc, dref, false, dcs);
                 Map1<R> X(R(1), R(0), R(0)), Y(R(1), R(0), R(0));
                 R tmp[NFC], tmpg[NGC], tr[NFC], trg[NGC];
                 cell_maps<D, R>(sc->T, dcs, Tl, invTl, rsqTl, dl, X, Y);
-                orient<D, 3, R>(sc->A, tmp, swap);
-                orient<D, 2, R>(sc->B, tmpg, swap);
+                orient<D, 3, R>(sc->A, tmp, false);
+                orient<D, 2, R>(sc->B, tmpg, false);
                 shift_scale<D, 3, R, true>(tmp, X, Y, tr);
                 shift_scale<D, 2, R>(tmpg, X, Y, trg);
                 collapse_f(tr, CS[q]);
@@ -682,8 +682,9 @@ struct FaceOut {
 };
 
 // The face predictor-corrector of Sec. III.B.3 at one face.  cells: stencil slots 0 LL,
-// 1 L, 2 R, 3 RR, 4 L-t, 5 L+t, 6 R-t, 7 R+t (staged phi-bar-plus, velocities relative to
-// the tile reference); swap: the face normal is y; the predictor lambda_0 is given by its
+// 1 L, 2 R, 3 RR, 4 L-t, 5 L+t, 6 R-t, 7 R+t (staged phi-bar-plus in face axes -- coefficient
+// orders and velocities with the normal first --, velocities relative to the tile
+// reference); swap: the face normal is y (the outputs go back to x, y order); the predictor lambda_0 is given by its
 // velocity minus the tile reference (dref) and its absolute velocity (uabs, used only for
 // upwinding and departure points), both in face axes (normal, tangential), and Tpred.
 // Passes run until the frame converges (or fixed_iters passes); a pass whose moments define
@@ -713,7 +714,7 @@ __device__ __forceinline__ void solve_face(const Stencil<D, R> &cells, bool swap
     R Phi[NFC], Psi[NGC];
     for (int k = 0; k < cfg.max_iter && !done; ++k) {
         corrector_pass<D, R>(cells, dref, dl, Tl, uref_n + dl[0], D == 2 ? uref_t + dl[D - 1] : R(0),
-                             h_dn, h_dt, swap, cfg.limiter, Phi, Psi);
+                             h_dn, h_dt, cfg.limiter, Phi, Psi);
         R rho1, du[D], T1;
         const bool ok = pass_frame<D, R>(Phi, Psi, Tl, Cv, rho1, du, T1);
         iters = k + 1;
@@ -730,7 +731,7 @@ __device__ __forceinline__ void solve_face(const Stencil<D, R> &cells, bool swap
                 for (int s = 0; s < NCELL; ++s) {
                     const R rc = cells[s]->A[0];
                     R v2 = R(0), dcs[D];
-                    rel_velocity<D, R>(cells[s], dref, swap, dcs);
+                    rel_velocity<D, R>(cells[s], dref, false, dcs);
 #pragma unroll
                     for (int a = 0; a < D; ++a) { m[a] += rc * dcs[a]; v2 += dcs[a] * dcs[a]; }
                     r += rc;
@@ -770,7 +771,7 @@ __device__ __forceinline__ void solve_face(const Stencil<D, R> &cells, bool swap
         if (!last_valid) {
             // the last pass defined no frame: recompute the last valid one
             corrector_pass<D, R>(cells, dref, keep_dl, keep_T, uref_n + keep_dl[0],
-                                 D == 2 ? uref_t + keep_dl[D - 1] : R(0), h_dn, h_dt, swap, cfg.limiter, Phi, Psi);
+                                 D == 2 ? uref_t + keep_dl[D - 1] : R(0), h_dn, h_dt, cfg.limiter, Phi, Psi);
         }
         // Eq. (FluxTransf) in the frame of the last valid pass's moments, with the exact
         // co-moving equilibria there: phi = (2 tau phibar + h phi^eq)/(2 tau + h)
@@ -819,7 +820,11 @@ face_kernel(const Params<D, R> P)
     constexpr int BX = TX + 3, BY = D == 2 ? TY + 3 : 1;
     constexpr int NFC = NCoef<D, 3>::value, NGC = NCoef<D, 2>::value;
     using W = typename FrameWords<R>::word;
+    // the staged box, and (2D) its transpose for the y-face threads: there a cell sits at
+    // [x][y] with its coefficient orders and velocity components swapped, so every face
+    // reads its stencil in face axes (normal first) and no transformation reorders anything
     __shared__ StagedCell<D, R> tile[BY * BX];
+    __shared__ StagedCell<D, R> tileT[D == 2 ? BY * BX : 1];
     __shared__ W utile[D];
 
     const Clock &K = *P.clock;
@@ -835,7 +840,20 @@ face_kernel(const Params<D, R> P)
     for (int t = threadIdx.x; t < BX * BY; t += blockDim.x) {
         const int bx = t % BX, by = t / BX;
         const long long ci = i0 - 2 + bx, cj = D == 2 ? j0 - 2 + by : 0;
-        load_cell_bar_plus<D, R>(P, ci, cj, cp, ce, utile, tile[t]);
+        if constexpr (D == 2) {
+            StagedCell<D, R> c;
+            load_cell_bar_plus<D, R>(P, ci, cj, cp, ce, utile, c);
+            tile[t] = c;
+            StagedCell<D, R> ct;
+            orient<D, 3, R>(c.A, ct.A, true);
+            orient<D, 2, R>(c.B, ct.B, true);
+            ct.du[0] = c.du[1];
+            ct.du[1] = c.du[0];
+            ct.T = c.T;
+            tileT[bx * BY + by] = ct;
+        } else {
+            load_cell_bar_plus<D, R>(P, ci, cj, cp, ce, utile, tile[t]);
+        }
     }
     __syncthreads();
 
@@ -859,9 +877,15 @@ face_kernel(const Params<D, R> P)
         const bool swap = dir == 1;
         // the face's stencil in the staged box (box coords of cell (i, j) = (i - i0 + 2, j - j0 + 2))
         Stencil<D, R> cells;
-        cells.base = &tile[(D == 2 ? int(fj - j0 + 2) * BX : 0) + int(fi - i0 + 2)];
-        cells.sn = swap ? BX : 1;
-        cells.st = D == 2 ? (swap ? 1 : BX) : 0;
+        if (swap) {   // transposed copy: the normal (y) runs along its rows
+            cells.base = &tileT[int(fi - i0 + 2) * BY + int(fj - j0 + 2)];
+            cells.sn = 1;
+            cells.st = BY;
+        } else {
+            cells.base = &tile[(D == 2 ? int(fj - j0 + 2) * BX : 0) + int(fi - i0 + 2)];
+            cells.sn = 1;
+            cells.st = D == 2 ? BX : 0;
+        }
         R *Fout = dir == 0 ? P.xf : P.yf;
         R *Gout = dir == 0 ? P.xg : P.yg;
         W *Frm = dir == 0 ? P.xfr : P.yfr;
@@ -936,8 +960,8 @@ face_kernel(const Params<D, R> P)
                 mlp::SlotPrim sp[8];
 #pragma unroll
                 for (int q = 0; q < 8; ++q)
-                    sp[q] = {float(cells[q]->A[0]), float(cells[q]->du[na]) - dn, float(cells[q]->du[ta]) - dt_,
-                             float(cells[q]->T)};
+                    sp[q] = {float(cells[q]->A[0]), float(cells[q]->du[0]) - dn, float(cells[q]->du[1]) - dt_,
+                             float(cells[q]->T)};   // stencil cells are in face axes
                 float f[mlp::kIn];
                 mlp::features(sp, float(Tp), float(cfg.h_dn), f);
                 const unsigned long long slot = atomicAdd(P.pair_count, 1ull);
