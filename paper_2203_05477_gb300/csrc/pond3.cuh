@@ -69,8 +69,11 @@ __host__ __device__ constexpr int h3t(int k)
 // stored f plane of coefficient k (-1: a first-order one, zero in the cell's own frame)
 __host__ __device__ constexpr int fplane3(int k) { return k == 0 ? 0 : (k <= 3 ? -1 : k - 3); }
 
-// out_rst = sum_{p<=r} X(r,p) sum_{q<=s} Y(s,q) sum_{w<=t} Z(t,w) in_pqw, r + s + t <= N
-template <int N, typename R>
+// out_rst = sum_{p<=r} X(r,p) sum_{q<=s} Y(s,q) sum_{w<=t} Z(t,w) in_pqw, r + s + t <= N.
+// Z1: the first-order inputs are known to be zero (coefficients in the frame of their own
+// first moment); their terms are skipped, and so are the intermediates they alone feed
+// (B_100 = B_010 = 0 after the z stage, C_100 = 0 after the y stage).
+template <int N, typename R, bool Z1 = false>
 __device__ __forceinline__ void shift_scale_3d(const R *in, const Map1<R> &X, const Map1<R> &Y, const Map1<R> &Z, R *out)
 {
     R B[NC3<N>::value], C[NC3<N>::value];
@@ -82,7 +85,8 @@ __device__ __forceinline__ void shift_scale_3d(const R *in, const Map1<R> &X, co
             for (int t = 0; p + q + t <= N; ++t) {
                 R acc = R(0);
 #pragma unroll
-                for (int w = 0; w <= t; ++w) acc += Z.get(t, w) * in[h3idx(p, q, w)];
+                for (int w = 0; w <= t; ++w)
+                    if (!(Z1 && p + q + w == 1)) acc += Z.get(t, w) * in[h3idx(p, q, w)];
                 B[h3idx(p, q, t)] = acc;
             }
 #pragma unroll
@@ -93,7 +97,8 @@ __device__ __forceinline__ void shift_scale_3d(const R *in, const Map1<R> &X, co
             for (int t = 0; p + s + t <= N; ++t) {
                 R acc = R(0);
 #pragma unroll
-                for (int q = 0; q <= s; ++q) acc += Y.get(s, q) * B[h3idx(p, q, t)];
+                for (int q = 0; q <= s; ++q)
+                    if (!(Z1 && t == 0 && p + q == 1)) acc += Y.get(s, q) * B[h3idx(p, q, t)];
                 C[h3idx(p, s, t)] = acc;
             }
 #pragma unroll
@@ -104,7 +109,8 @@ __device__ __forceinline__ void shift_scale_3d(const R *in, const Map1<R> &X, co
             for (int t = 0; r + s + t <= N; ++t) {
                 R acc = R(0);
 #pragma unroll
-                for (int p = 0; p <= r; ++p) acc += X.get(r, p) * C[h3idx(p, s, t)];
+                for (int p = 0; p <= r; ++p)
+                    if (!(Z1 && p == 1 && s == 0 && t == 0)) acc += X.get(r, p) * C[h3idx(p, s, t)];
                 out[h3idx(r, s, t)] = acc;
             }
 }
@@ -347,7 +353,7 @@ __device__ __forceinline__ void collapse_normal(const StagedCell3<R> *c, int dir
     cell_maps3<R>(c, dir, dref, dl, Tl, invTl, rsqTl, X, Y, Z);
     R tmp[kNF3], F[kNF3];
     to_face<3, R>(c->A, tmp, dir);
-    shift_scale_3d<3, R>(tmp, X, Y, Z, F);
+    shift_scale_3d<3, R, true>(tmp, X, Y, Z, F);   // staged f: zero first order
 #pragma unroll
     for (int s2 = 0; s2 <= 3; ++s2)
 #pragma unroll
