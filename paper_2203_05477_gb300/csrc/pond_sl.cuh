@@ -100,7 +100,7 @@ sl_kernel(const Params<1, R> P)
             for (int s = 0; s < 5; ++s) {
                 const R sc = sqrt(cells[s]->T * invTl), e = (cells[s]->T - Tlp) * invTl;
                 Map1<R> X(sc, e, (cells[s]->du[0] - dlp) * rsqTl);
-                shift_scale_1d<3, R>(cells[s]->A, X, F[s]);
+                shift_scale_1d<3, R, true>(cells[s]->A, X, F[s]);   // staged f: zero first order
                 shift_scale_1d<2, R>(cells[s]->B, X, G[s]);
             }
             // The node's own coefficients enter the moments directly and only the differences

@@ -51,7 +51,7 @@ __device__ __forceinline__ void sl2_transform(const StagedCell<2, R> *c, const R
 {
     Map1<R> X(R(1), R(0), R(0)), Y(R(1), R(0), R(0));
     cell_maps<2, R>(c->T, c->du, Tl, invTl, rsqTl, dl, X, Y);
-    shift_scale<2, 3, R>(c->A, X, Y, F);
+    shift_scale<2, 3, R, true>(c->A, X, Y, F);   // staged f: zero first order
     shift_scale<2, 2, R>(c->B, X, Y, G);
 }
 
