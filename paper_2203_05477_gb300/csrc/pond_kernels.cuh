@@ -259,13 +259,39 @@ __device__ __forceinline__ bool mirror_odd(int k, int flip)
 
 // Cell data as staged for the face corrector: phi-bar-plus coefficients (Eq. Fbarplus) in
 // the cell frame, the frame, and the density.
+// Records are padded to a multiple of 16 bytes and read with 16-byte loads (fetch): 5 loads
+// instead of 19 for a D2Q16 FP32 record, and neighbouring threads' records (80 B apart)
+// fall in distinct bank groups.
 template <int D, typename R>
-struct StagedCell {
+constexpr int staged_pad()
+{
+    constexpr int bytes = (NCoef<D, 3>::value + NCoef<D, 2>::value + D + 1) * int(sizeof(R));
+    return ((16 - bytes % 16) % 16) / int(sizeof(R));
+}
+template <int D, typename R>
+struct __align__(16) StagedCell {
     R A[NCoef<D, 3>::value];
     R B[NCoef<D, 2>::value];
     R du[D];    // frame velocity relative to the tile reference velocity
     R T;
+    R pad[staged_pad<D, R>() > 0 ? staged_pad<D, R>() : 1];
 };
+
+// a staged record into registers with 16-byte shared-memory loads
+template <int D, typename R>
+__device__ __forceinline__ StagedCell<D, R> fetch(const StagedCell<D, R> *p)
+{
+    static_assert(sizeof(StagedCell<D, R>) % 16 == 0, "16-byte records");
+    constexpr int N = int(sizeof(StagedCell<D, R>) / 16);
+    union {
+        StagedCell<D, R> c;
+        float4 v[N];
+    } u;
+    const float4 *src = reinterpret_cast<const float4 *>(p);
+#pragma unroll
+    for (int k = 0; k < N; ++k) u.v[k] = src[k];
+    return u.c;
+}
 
 // Loads cell (i, j) (ghosts resolved) and forms phi-bar-plus = cp phi~ + ce phi^eq with
 // phi^eq the co-moving equilibria (rho, 0, ...) and ((Cv - D/2) rho T, 0, ...).
@@ -484,16 +510,18 @@ __device__ __forceinline__ void corrector_pass(const Stencil<D, R> &cells, const
         Map1<R> X(R(1), R(0), R(0)), Y(R(1), R(0), R(0));
         R tmp[NFC], tmpg[NGC];
         R dcs[D];
-        rel_velocity<D, R>(cells[1], dref, false, dcs);
-        cell_maps<D, R>(cells[1]->T, dcs, Tl, invTl, rsqTl, dl, X, Y);
-        orient<D, 3, R>(cells[1]->A, tmp, false);
-        orient<D, 2, R>(cells[1]->B, tmpg, false);
+        const StagedCell<D, R> cl = fetch<D, R>(cells[1]);
+        rel_velocity<D, R>(&cl, dref, false, dcs);
+        cell_maps<D, R>(cl.T, dcs, Tl, invTl, rsqTl, dl, X, Y);
+        orient<D, 3, R>(cl.A, tmp, false);
+        orient<D, 2, R>(cl.B, tmpg, false);
         shift_scale<D, 3, R, true>(tmp, X, Y, FL);   // staged f: zero first order
         shift_scale<D, 2, R>(tmpg, X, Y, GL);
-        rel_velocity<D, R>(cells[2], dref, false, dcs);
-        cell_maps<D, R>(cells[2]->T, dcs, Tl, invTl, rsqTl, dl, X, Y);
-        orient<D, 3, R>(cells[2]->A, tmp, false);
-        orient<D, 2, R>(cells[2]->B, tmpg, false);
+        const StagedCell<D, R> cr = fetch<D, R>(cells[2]);
+        rel_velocity<D, R>(&cr, dref, false, dcs);
+        cell_maps<D, R>(cr.T, dcs, Tl, invTl, rsqTl, dl, X, Y);
+        orient<D, 3, R>(cr.A, tmp, false);
+        orient<D, 2, R>(cr.B, tmpg, false);
         shift_scale<D, 3, R, true>(tmp, X, Y, FR);
         shift_scale<D, 2, R>(tmpg, X, Y, GR);
     }
@@ -514,13 +542,13 @@ __device__ __forceinline__ void corrector_pass(const Stencil<D, R> &cells, const
             R FS[NFC], GS[NGC];
             {
                 // slot 0 or 3, chosen by selects so that no array is indexed at run time
-                const StagedCell<D, R> *sc = left ? cells[0] : cells[3];
+                const StagedCell<D, R> sc = fetch<D, R>(left ? cells[0] : cells[3]);
                 R dcs[1];
-                rel_velocity<D, R>(sc, dref, false, dcs);
+                rel_velocity<D, R>(&sc, dref, false, dcs);
                 Map1<R> X(R(1), R(0), R(0)), Y(R(1), R(0), R(0));
-                cell_maps<D, R>(sc->T, dcs, Tl, invTl, rsqTl, dl, X, Y);
-                shift_scale<D, 3, R, true>(sc->A, X, Y, FS);
-                shift_scale<D, 2, R>(sc->B, X, Y, GS);
+                cell_maps<D, R>(sc.T, dcs, Tl, invTl, rsqTl, dl, X, Y);
+                shift_scale<D, 3, R, true>(sc.A, X, Y, FS);
+                shift_scale<D, 2, R>(sc.B, X, Y, GS);
             }
             // populations at node m (unweighted: the limiter is homogeneous of degree one,
             // so the weight w_m factors out) of L, R and the outer neighbour
@@ -569,14 +597,14 @@ __device__ __forceinline__ void corrector_pass(const Stencil<D, R> &cells, const
                 // slot (left, right upwind): q = 0 (0, 3), q = 1 (4, 6), q = 2 (5, 7); chosen by
                 // selects so that no array is indexed at run time
                 constexpr int sa[3] = {0, 4, 5}, sb[3] = {3, 6, 7};
-                const StagedCell<D, R> *sc = left ? cells[sa[q]] : cells[sb[q]];
+                const StagedCell<D, R> sc = fetch<D, R>(left ? cells[sa[q]] : cells[sb[q]]);
                 R dcs[D];
-                rel_velocity<D, R>(sc, dref, false, dcs);
+                rel_velocity<D, R>(&sc, dref, false, dcs);
                 Map1<R> X(R(1), R(0), R(0)), Y(R(1), R(0), R(0));
                 R tmp[NFC], tmpg[NGC], tr[NFC], trg[NGC];
-                cell_maps<D, R>(sc->T, dcs, Tl, invTl, rsqTl, dl, X, Y);
-                orient<D, 3, R>(sc->A, tmp, false);
-                orient<D, 2, R>(sc->B, tmpg, false);
+                cell_maps<D, R>(sc.T, dcs, Tl, invTl, rsqTl, dl, X, Y);
+                orient<D, 3, R>(sc.A, tmp, false);
+                orient<D, 2, R>(sc.B, tmpg, false);
                 shift_scale<D, 3, R, true>(tmp, X, Y, tr);
                 shift_scale<D, 2, R>(tmpg, X, Y, trg);
                 collapse_f(tr, CS[q]);
