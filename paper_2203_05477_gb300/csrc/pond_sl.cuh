@@ -58,13 +58,23 @@ __device__ __forceinline__ void sl_diag_and_advance(Diag *diag, Clock *clock, bo
     reduce_rate_and_advance(clock, rate, true);
 }
 
+// a staged D1Q4 node without padding: nine words, so that neighbouring threads' scalar
+// loads (this kernel reads fields one at a time) fall in distinct banks
+template <typename R>
+struct SlCell1 {
+    R A[4];
+    R B[3];
+    R du[1];
+    R T;
+};
+
 template <typename R, int TX>
 __global__ void __launch_bounds__(TX, sizeof(R) == 4 ? 8 : 1)   // FP32: 64 registers, 8 CTAs per SM
 sl_kernel(const Params<1, R> P)
 {
     using W = typename FrameWords<R>::word;
     constexpr int BX = TX + 4;
-    __shared__ StagedCell<1, R> tile[BX];
+    __shared__ SlCell1<R> tile[BX];
     __shared__ W utile[1];
     const Clock &K = *P.clock;
     if (!(K.dt > 0.0)) return;
@@ -73,7 +83,17 @@ sl_kernel(const Params<1, R> P)
     const long long i0 = (long long)blockIdx.x * TX;
     if (threadIdx.x == 0) cell_velocity<1, R>(P, i0, 0, utile);
     __syncthreads();
-    for (int t = threadIdx.x; t < BX; t += blockDim.x) load_cell_bar_plus<1, R>(P, i0 - 2 + t, 0, R(1), R(0), utile, tile[t]);
+    for (int t = threadIdx.x; t < BX; t += blockDim.x) {
+        StagedCell<1, R> c;
+        load_cell_bar_plus<1, R>(P, i0 - 2 + t, 0, R(1), R(0), utile, c);
+        SlCell1<R> &o = tile[t];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) o.A[k] = c.A[k];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) o.B[k] = c.B[k];
+        o.du[0] = c.du[0];
+        o.T = c.T;
+    }
     __syncthreads();
 
     const long long i = i0 + threadIdx.x;
@@ -81,7 +101,7 @@ sl_kernel(const Params<1, R> P)
     unsigned long long my_iters = 0, my_nonconv = 0, my_fallbacks = 0, my_nonphys = 0;
     const bool active = i < P.nx;
     if (active) {
-        const StagedCell<1, R> *cells[5];
+        const SlCell1<R> *cells[5];
 #pragma unroll
         for (int s = 0; s < 5; ++s) cells[s] = &tile[threadIdx.x + s];
         const R dt_dx = KC.dt_dx;

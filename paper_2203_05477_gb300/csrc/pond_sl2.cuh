@@ -47,12 +47,13 @@ __device__ __forceinline__ R sl_interp2(const R (&v)[4][4], R thx, R thy)
 }
 
 template <typename R>
-__device__ __forceinline__ void sl2_transform(const StagedCell<2, R> *c, const R *dl, R Tl, R invTl, R rsqTl, R *F, R *G)
+__device__ __forceinline__ void sl2_transform(const StagedCell<2, R> *cp, const R *dl, R Tl, R invTl, R rsqTl, R *F, R *G)
 {
+    const StagedCell<2, R> c = fetch<2, R>(cp);   // 16-byte loads of the staged record
     Map1<R> X(R(1), R(0), R(0)), Y(R(1), R(0), R(0));
-    cell_maps<2, R>(c->T, c->du, Tl, invTl, rsqTl, dl, X, Y);
-    shift_scale<2, 3, R, true>(c->A, X, Y, F);   // staged f: zero first order
-    shift_scale<2, 2, R>(c->B, X, Y, G);
+    cell_maps<2, R>(c.T, c.du, Tl, invTl, rsqTl, dl, X, Y);
+    shift_scale<2, 3, R, true>(c.A, X, Y, F);   // staged f: zero first order
+    shift_scale<2, 2, R>(c.B, X, Y, G);
 }
 
 // per-thread scratch: [row 0..4][column 0..3][7 collapsed coefficients], thread-minor
