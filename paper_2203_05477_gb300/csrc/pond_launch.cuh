@@ -79,9 +79,9 @@ inline void launch_face(int v, bool collect, const Params<D, R> &P, cudaStream_t
 
 // ---------------------------------------------------------------- cell kernel
 
-constexpr int kCellBlocks[5] = {256, 128, 512, 256, 256};
-constexpr int kCellMinBlocks[5] = {1, 1, 1, 3, 4};   // CTAs per SM asked of the register allocator
-constexpr int kCellVariants = 5;
+constexpr int kCellBlocks[6] = {256, 128, 512, 256, 256, 128};
+constexpr int kCellMinBlocks[6] = {1, 1, 1, 3, 4, 6};   // CTAs per SM asked of the register allocator
+constexpr int kCellVariants = 6;
 
 template <int D, typename R>
 void launch_cell(int v, const Params<D, R> &P, cudaStream_t st);

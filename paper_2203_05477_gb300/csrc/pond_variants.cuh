@@ -54,6 +54,7 @@ void launch_cell(int v, const Params<D, R> &P, cudaStream_t st)
     case 2: cell_kernel<D, R, 512><<<blocks(512), 512, 0, st>>>(P); break;
     case 3: cell_kernel<D, R, 256, 3><<<blocks(256), 256, 0, st>>>(P); break;
     case 4: cell_kernel<D, R, 256, 4><<<blocks(256), 256, 0, st>>>(P); break;
+    case 5: cell_kernel<D, R, 128, 6><<<blocks(128), 128, 0, st>>>(P); break;
     default: cell_kernel<D, R, 256><<<blocks(256), 256, 0, st>>>(P); break;
     }
 }

@@ -33,7 +33,7 @@ def test_every_grid_variant_matches_oracle_fp64(name, pb):
     os_.step(4)
     gs = gpu_for(pb, precision="fp64", **KW64)
     nf, nc = split(gs.variants())
-    assert nf >= 3 and nc == 5
+    assert nf >= 3 and nc == 6
     for f in range(nf):
         for c in range(nc):
             if f and c != f % nc:
