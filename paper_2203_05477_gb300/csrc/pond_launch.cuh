@@ -31,7 +31,7 @@ struct FaceList<2, float> {
 };
 template <>
 struct FaceList<2, double> {
-    using type = VList<FaceVariant<2, 32, 4, 1>, FaceVariant<2, 16, 8, 1>, FaceVariant<2, 16, 4, 2>>;
+    using type = VList<FaceVariant<2, 32, 4, 1>, FaceVariant<2, 16, 8, 1>, FaceVariant<2, 16, 4, 2>, FaceVariant<2, 8, 8, 2>>;
 };
 template <typename R>
 struct FaceList<1, R> {
