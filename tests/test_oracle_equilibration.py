@@ -18,7 +18,7 @@ def he(k, x):
     return [np.ones_like(x), x, x * x - 1.0, x ** 3 - 3.0 * x][k]
 
 
-@pytest.mark.parametrize("D", [1, 2])
+@pytest.mark.parametrize("D", [1, 2, 3])
 @pytest.mark.parametrize("order", [2, 3])
 def test_slow_moments_are_kept(D, order):
     rng = np.random.default_rng(7 * D + order)
@@ -67,3 +67,22 @@ def test_solver_with_equilibration_conserves():
     r1, mx1, my1, E1 = (a.sum() for a in s.conserved())
     assert abs(r1 - r0) <= 1e-13 * r0 and abs(E1 - E0) <= 1e-13 * E0
     assert abs(mx1 - mx0) <= 1e-13 * r0 and abs(my1 - my0) <= 1e-13 * r0
+
+
+@pytest.mark.parametrize("order", [2, 3])
+def test_fast_components_are_the_equilibrium_3d(order):
+    """D3Q64: every tensor component He_r He_s He_t with r, s, t <= 3 and r + s + t > order is
+    the equilibrium's M0 d_x^r d_y^s d_z^t."""
+    from tests.test_oracle_3d import random_case_3d
+    rng = np.random.default_rng(40 + order)
+    for _ in range(6):
+        c, W, f, u, T, up, Tp = random_case_3d(rng)
+        fo = O.regularized_transform(3, order, f, u, T, up, Tp, equilibrate=True)
+        M = lab_moments(f, c, u, T, 1)
+        d = (M[1] / M[0] - up) / np.sqrt(Tp)
+        for r in range(4):
+            for s_ in range(4):
+                for t in range(4):
+                    if r + s_ + t > order:
+                        a = np.sum(fo * he(r, c[:, 0]) * he(s_, c[:, 1]) * he(t, c[:, 2]))
+                        assert a == pytest.approx(M[0] * d[0] ** r * d[1] ** s_ * d[2] ** t, rel=1e-9, abs=1e-11)
