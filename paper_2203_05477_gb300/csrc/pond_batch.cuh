@@ -148,6 +148,7 @@ tube_kernel(const TubeParams<R> P, int steps, int cur0)
                 const long long k = c0 + f;
                 Stencil<1, R> cells;   // LL, L, R, RR at tile[f .. f+3]
                 cells.base = &tile[f + 2];
+                cells.sn = 1;
                 cells.st = 0;
                 const R dref[1] = {R(fr_rel(P.fu[f_off + k], utile))};
                 const R uabs[1] = {R(fr_lead(P.fu[f_off + k]))};

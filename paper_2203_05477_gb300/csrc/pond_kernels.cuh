@@ -406,18 +406,17 @@ __device__ __forceinline__ void cell_maps(R Tc, const R *dc, R Tl, R invTl, R rs
 
 // The stencil of one face in the staged tile: slot s at offsets (normal, tangential) from
 // cell R -- 0 (-2, 0), 1 (-1, 0), 2 (0, 0), 3 (1, 0), 4 (-1, -1), 5 (-1, 1), 6 (0, -1),
-// 7 (0, 1).  The tiles keep the face normal along their rows (an x-face reads the staged
-// box, a y-face its transpose), so the normal stride is one cell and st is the row length.
-// A base pointer and a stride instead of an array of eight pointers keeps registers free.
+// 7 (0, 1) -- with the strides (in cells) of the face's normal and tangential axes.  A base
+// pointer and two strides instead of an array of eight pointers keeps registers free.
 template <int D, typename R>
 struct Stencil {
     const StagedCell<D, R> *base;
-    int st;
+    int sn, st;
     __device__ __forceinline__ const StagedCell<D, R> *operator[](int s) const
     {
         const int on = s < 4 ? s - 2 : (s < 6 ? -1 : 0);
         const int ot = s < 4 ? 0 : ((s & 1) ? 1 : -1);
-        return base + on + ot * st;
+        return base + on * sn + ot * st;
     }
 };
 
@@ -908,9 +907,11 @@ face_kernel(const Params<D, R> P)
         Stencil<D, R> cells;
         if (swap) {   // transposed copy: the normal (y) runs along its rows
             cells.base = &tileT[int(fi - i0 + 2) * BY + int(fj - j0 + 2)];
+            cells.sn = 1;
             cells.st = BY;
         } else {
             cells.base = &tile[(D == 2 ? int(fj - j0 + 2) * BX : 0) + int(fi - i0 + 2)];
+            cells.sn = 1;
             cells.st = D == 2 ? BX : 0;
         }
         R *Fout = dir == 0 ? P.xf : P.yf;
