@@ -138,6 +138,25 @@ def test_sod_400_against_exact_solution():
     assert abs(k_num - k_ex) <= 2, (x[k_num], x[k_ex])
 
 
+def test_sod_error_is_flat_in_tau_near_the_default():
+    """The relaxation time is a free parameter of the FV runs (Sec. IV asks only that it be
+    low enough not to change the results).  On Sod at 400 cells the error against the exact
+    solution has its minimum at tau ~ 1e-5..2e-5 (delta t ~ 5e-4): doubling tau from the
+    default changes it by about 1%.  Larger tau adds BGK viscosity (tau T); smaller tau
+    drives the collision factor (2 tau - dt) / (2 tau + dt) towards -1, which damps the
+    oscillations behind the shock less."""
+    re, ue, pe = cell_averaged_profile((1, 0, 1), (0.125, 0, 0.1), 1.4, np.linspace(0, 1, 401), 0.5, 0.2)
+    err = {}
+    for tau in (5e-6, 1e-5, 2e-5, 5e-5):
+        s = oracle_for(I.sod_400(), tau=tau, cfl=0.5, t_end=0.2)
+        s.step(10 ** 6)
+        r, _, _, p = s.primitive()
+        err[tau] = (rel_l1(r, re), rel_l1(p, pe))
+    for k in (0, 1):
+        assert abs(err[2e-5][k] - err[1e-5][k]) <= 0.03 * err[1e-5][k], err
+        assert err[5e-6][k] > err[1e-5][k] and err[5e-5][k] > err[2e-5][k], err
+
+
 def test_sod_converges_under_refinement():
     errs = []
     for n in (100, 200, 400):
