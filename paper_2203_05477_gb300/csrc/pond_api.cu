@@ -50,6 +50,29 @@ constexpr int kReduceBlocks = 1024;
 
 constexpr size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// The CUDA events of one timed run, destroyed on every return path.
+struct Events {
+    std::vector<cudaEvent_t> ev;
+    explicit Events(size_t n) : ev(n, nullptr) {}
+    Events(const Events &) = delete;
+    Events &operator=(const Events &) = delete;
+    ~Events()
+    {
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+    cudaError_t create()
+    {
+        for (cudaEvent_t &e : ev) {
+            const cudaError_t r = cudaEventCreate(&e);
+            if (r != cudaSuccess) return r;
+        }
+        return cudaSuccess;
+    }
+    cudaEvent_t &operator[](size_t i) { return ev[i]; }
+    cudaEvent_t back() const { return ev.back(); }
+};
+
 }  // namespace
 
 struct pond_state {
@@ -384,8 +407,8 @@ template <int D, typename R>
 pond_status step_timed_impl(pond_state *s, int64_t n_steps, double *ms)
 {
     auto &P = params_of<D, R>(s);
-    std::vector<cudaEvent_t> ev(size_t(2 * n_steps + 1));
-    for (auto &e : ev) CUDA_TRY(cudaEventCreate(&e));
+    Events ev(size_t(2 * n_steps + 1));
+    CUDA_TRY(ev.create());
     CUDA_TRY(cudaEventRecord(ev[0], s->stream));
     for (int64_t k = 0; k < n_steps; ++k) {
         if constexpr (D == 2) {
@@ -417,7 +440,6 @@ pond_status step_timed_impl(pond_state *s, int64_t n_steps, double *ms)
         ms[0] += a;
         ms[1] += b;
     }
-    for (auto &e : ev) cudaEventDestroy(e);
     return POND_OK;
 }
 
@@ -631,11 +653,10 @@ pond_status batch_step(pond_state *s, int64_t n_steps, double *ms)
 {
     if (n_steps <= 0) return POND_OK;
     auto &P = tparams_of<R>(s);
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    Events ev(ms ? 2 : 0);
     if (ms) {
-        CUDA_TRY(cudaEventCreate(&e0));
-        CUDA_TRY(cudaEventCreate(&e1));
-        CUDA_TRY(cudaEventRecord(e0, s->stream));
+        CUDA_TRY(ev.create());
+        CUDA_TRY(cudaEventRecord(ev[0], s->stream));
     }
     pond::launch_tube<R>(s->tube_v, unsigned(s->n_tubes), P, int(n_steps), s->cur, s->stream);
     s->launches += 1;
@@ -643,13 +664,11 @@ pond_status batch_step(pond_state *s, int64_t n_steps, double *ms)
     s->cur ^= int(n_steps & 1);
     s->steps_taken += n_steps;
     if (ms) {
-        CUDA_TRY(cudaEventRecord(e1, s->stream));
-        CUDA_TRY(cudaEventSynchronize(e1));
+        CUDA_TRY(cudaEventRecord(ev[1], s->stream));
+        CUDA_TRY(cudaEventSynchronize(ev[1]));
         float a = 0.f;
-        CUDA_TRY(cudaEventElapsedTime(&a, e0, e1));
+        CUDA_TRY(cudaEventElapsedTime(&a, ev[0], ev[1]));
         ms[0] += a;
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
     }
     return POND_OK;
 }
@@ -862,8 +881,8 @@ template <typename R>
 pond_status step3_timed_impl(pond_state *s, int64_t n_steps, double *ms)
 {
     auto &P = params3_of<R>(s);
-    std::vector<cudaEvent_t> ev(size_t(2 * n_steps + 1));
-    for (auto &e : ev) CUDA_TRY(cudaEventCreate(&e));
+    Events ev(size_t(2 * n_steps + 1));
+    CUDA_TRY(ev.create());
     CUDA_TRY(cudaEventRecord(ev[0], s->stream));
     for (int64_t k = 0; k < n_steps; ++k) {
         pond::launch_face3<R>(P, s->stream);
@@ -881,7 +900,6 @@ pond_status step3_timed_impl(pond_state *s, int64_t n_steps, double *ms)
         ms[0] += a;
         ms[1] += b;
     }
-    for (auto &e : ev) cudaEventDestroy(e);
     return POND_OK;
 }
 
@@ -1710,8 +1728,8 @@ pond_status time_grid_variant(pond_state *s, const char *saved, int steps, int w
     auto &P = params_of<D, R>(s);
     CUDA_TRY(cudaMemcpyAsync(s->base, saved, s->bytes, cudaMemcpyDeviceToDevice, s->stream));
     launch_step<D, R>(s);
-    std::vector<cudaEvent_t> ev(size_t(2 * steps));
-    for (auto &e : ev) CUDA_TRY(cudaEventCreate(&e));
+    Events ev(size_t(2 * steps));
+    CUDA_TRY(ev.create());
     for (int k = 0; k < steps; ++k) {
         if constexpr (D == 2) {
             if (s->learned)
@@ -1733,7 +1751,6 @@ pond_status time_grid_variant(pond_state *s, const char *saved, int steps, int w
         CUDA_TRY(cudaEventElapsedTime(&a, ev[2 * k], ev[2 * k + 1]));
         sum += a;
     }
-    for (auto &e : ev) cudaEventDestroy(e);
     *ms = sum / steps;
     return POND_OK;
 }
@@ -1771,9 +1788,9 @@ pond_status tune_batch(pond_state *s, const char *saved, int steps, pond_tune_re
     const int nv = pond::tube_variants<R>();
     double best = 0.0;
     int bv = 0;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    CUDA_TRY(cudaEventCreate(&e0));
-    CUDA_TRY(cudaEventCreate(&e1));
+    Events ev(2);
+    CUDA_TRY(ev.create());
+    cudaEvent_t e0 = ev[0], e1 = ev[1];
     for (int v = 0; v < nv; ++v) {
         CUDA_TRY(cudaMemcpyAsync(s->base, saved, s->bytes, cudaMemcpyDeviceToDevice, s->stream));
         CUDA_TRY(cudaEventRecord(e0, s->stream));
@@ -1787,8 +1804,6 @@ pond_status tune_batch(pond_state *s, const char *saved, int steps, pond_tune_re
         if (res && res->n < POND_TUNE_MAX) res->ms[res->n++] = a / steps;
         if (v == 0 || a < best) { best = a; bv = v; }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     s->tube_v = bv;
     return POND_OK;
 }
