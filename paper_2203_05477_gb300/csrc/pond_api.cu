@@ -364,16 +364,35 @@ void launch_step(pond_state *s, bool collect = false)
     pond::launch_cell<D, R>(s->cell_v, P, s->stream);
 }
 
+// Releases the captured step graph (it is captured again on the next long step).
+void drop_graph(pond_state *s)
+{
+    if (s->graph_exec) cudaGraphExecDestroy(s->graph_exec);
+    if (s->graph) cudaGraphDestroy(s->graph);
+    s->graph_exec = nullptr;
+    s->graph = nullptr;
+}
+
+// Instantiates a captured graph and keeps both on the state; on failure neither is kept.
+pond_status keep_graph(pond_state *s, cudaGraph_t g)
+{
+    const cudaError_t e = cudaGraphInstantiate(&s->graph_exec, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        s->graph_exec = nullptr;
+        return fail(POND_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+    }
+    s->graph = g;
+    return POND_OK;
+}
+
 template <int D, typename R>
 pond_status step_impl(pond_state *s, int64_t n_steps)
 {
     int64_t left = n_steps;
     if (left >= kGraphSteps && s->graph_exec && s->scheme == POND_SL && s->graph_parity != s->sl_parity) {
         // the graph was captured starting from the other buffer
-        cudaGraphExecDestroy(s->graph_exec);
-        cudaGraphDestroy(s->graph);
-        s->graph_exec = nullptr;
-        s->graph = nullptr;
+        drop_graph(s);
     }
     if (left >= kGraphSteps) {
         if (!s->graph_exec) {
@@ -384,8 +403,7 @@ pond_status step_impl(pond_state *s, int64_t n_steps)
             s->launches = before;
             cudaGraph_t g = nullptr;
             CUDA_TRY(cudaStreamEndCapture(s->stream, &g));
-            s->graph = g;
-            CUDA_TRY(cudaGraphInstantiate(&s->graph_exec, g, 0));
+            if (pond_status st = keep_graph(s, g)) return st;
         }
         const int per_step = s->scheme == POND_SL ? 1 : 2 + ((D == 2 && s->learned) ? 1 : 0);
         while (left >= kGraphSteps) {
@@ -860,8 +878,7 @@ pond_status step3_impl(pond_state *s, int64_t n_steps)
             for (int k = 0; k < kGraphSteps; ++k) launch_step3<R>(s);
             cudaGraph_t g = nullptr;
             CUDA_TRY(cudaStreamEndCapture(s->stream, &g));
-            s->graph = g;
-            CUDA_TRY(cudaGraphInstantiate(&s->graph_exec, g, 0));
+            if (pond_status st = keep_graph(s, g)) return st;
         }
         while (left >= kGraphSteps) {
             CUDA_TRY(cudaGraphLaunch(s->graph_exec, s->stream));
@@ -1451,8 +1468,7 @@ pond_status pond_gauge_enable(pond_state *s, int on)
     if (pond_status st = check_gauge(s)) return st;
     if (bool(on) != s->learned) {
         // the captured step graph depends on the set of kernels
-        if (s->graph_exec) { cudaGraphExecDestroy(s->graph_exec); s->graph_exec = nullptr; }
-        if (s->graph) { cudaGraphDestroy(s->graph); s->graph = nullptr; }
+        drop_graph(s);
     }
     s->learned = on != 0;
     if (s->prec == POND_FP32) params_of<2, float>(s).use_learned = s->learned;
@@ -1466,8 +1482,7 @@ pond_status pond_gauge_set_gate(pond_state *s, float gate)
     if (!(gate >= 0.f)) return fail(POND_ERR_INVALID_ARG, "gate must be >= 0");
     if (s->prec == POND_FP32) params_of<2, float>(s).gauge_gate = gate;
     else params_of<2, double>(s).gauge_gate = gate;
-    if (s->graph_exec) { cudaGraphExecDestroy(s->graph_exec); s->graph_exec = nullptr; }
-    if (s->graph) { cudaGraphDestroy(s->graph); s->graph = nullptr; }
+    drop_graph(s);
     return POND_OK;
 }
 
@@ -1477,8 +1492,7 @@ pond_status pond_gauge_set_trust(pond_state *s, float trust)
     if (!(trust > 0.f)) return fail(POND_ERR_INVALID_ARG, "trust must be > 0");
     if (s->prec == POND_FP32) params_of<2, float>(s).gauge_trust = trust;
     else params_of<2, double>(s).gauge_trust = trust;
-    if (s->graph_exec) { cudaGraphExecDestroy(s->graph_exec); s->graph_exec = nullptr; }
-    if (s->graph) { cudaGraphDestroy(s->graph); s->graph = nullptr; }
+    drop_graph(s);
     return POND_OK;
 }
 
@@ -1655,14 +1669,6 @@ pond_status pond_mlp_gradient_noalloc(const float *params, const float *x, int l
 // the problem kind and its size.
 
 namespace {
-
-void drop_graph(pond_state *s)
-{
-    if (s->graph_exec) cudaGraphExecDestroy(s->graph_exec);
-    if (s->graph) cudaGraphDestroy(s->graph);
-    s->graph_exec = nullptr;
-    s->graph = nullptr;
-}
 
 std::string tune_key(const pond_state *s)
 {
@@ -1903,8 +1909,7 @@ void pond_destroy(pond_state *s)
 {
     if (!s) return;
     if (s->stream) cudaStreamSynchronize(s->stream);
-    if (s->graph_exec) cudaGraphExecDestroy(s->graph_exec);
-    if (s->graph) cudaGraphDestroy(s->graph);
+    drop_graph(s);
     dev_free(s, s->base);
     dev_free(s, s->mlp_block);
     dev_free(s, s->train_scratch);
