@@ -442,7 +442,10 @@ def main():
     s2.close()
     e2e = {"value": world * ncell * args.steps / e2e_s / 1e6, "unit": "MLUPS",
            "h2d_bytes_per_step": 4 * 8 * ncell / args.steps, "d2h_bytes_per_step": 4 * 8 * ncell / args.steps,
-           "note": "pond_set_primitive from pinned host arrays, %d steps, pond_moments to pinned host" % args.steps}
+           "note": ("pond_set_primitive from pinned host arrays, %d steps, pond_moments to pinned host; "
+                    "the steps replay the captured step graph (pond_step), while the device-timed value "
+                    "records an event after every kernel (pond_step_timed) to time face and cell kernels "
+                    "apart, so e2e can come out slightly above it" % args.steps)}
 
     # ---- FP32 with the learned face-gauge predictor (trained here on another seed)
     learned = None
