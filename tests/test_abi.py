@@ -3,6 +3,7 @@ that include/pond.h declares, and validates its arguments before touching the de
 import ctypes
 import os
 import re
+import subprocess
 
 import pytest
 
@@ -108,3 +109,40 @@ def test_d3q64_goes_through_init3(lib):
     assert L.pond_init3(None, 1.4, 1e-5, None, ctypes.byref(h)) == pond.POND_ERR_INVALID_ARG
     assert L.pond_set_primitive3(None, None, None, None, None, None, 0) == pond.POND_ERR_INVALID_ARG
     assert L.pond_moments3(None, None, None, None, None, None, None, 0) == pond.POND_ERR_INVALID_ARG
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """The ctypes structures and constants of the binding have the sizes, field offsets and
+    values that a C compiler gives the declarations of include/pond.h."""
+    structs = {"pond_grid": pond.pond_grid, "pond_grid3": pond.pond_grid3, "pond_options": pond.pond_options,
+               "pond_diag": pond.pond_diag, "pond_tune_result": pond.pond_tune_result}
+    consts = ["POND_OK", "POND_ERR_INVALID_ARG", "POND_ERR_UNSUPPORTED", "POND_ERR_OOM", "POND_ERR_CUDA",
+              "POND_ERR_NONPHYSICAL", "POND_ERR_NOT_CONVERGED", "POND_ERR_TIMEOUT", "POND_D1Q3", "POND_D1Q4",
+              "POND_D2Q16", "POND_D2Q9", "POND_D3Q64", "POND_FP64", "POND_FP32", "POND_VANLEER", "POND_MINMOD",
+              "POND_FV", "POND_SL", "POND_TUNE_MAX"]
+    lines = ['#include <stdio.h>', '#include "pond.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (name, name))
+        for field, _ in cls._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (name, field, name, field))
+    for c in consts:
+        lines.append('printf("%s %%ld\\n", (long)%s);' % (c, c))
+    for c in ("POND_MLP_PARAMS", "POND_MLP_FEATURES", "POND_MLP_PAIR_STRIDE"):
+        lines.append('printf("%s %%ld\\n", (long)%s);' % (c, c))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = dict(line.rsplit(" ", 1) for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                              text=True).stdout.splitlines())
+    for name, cls in structs.items():
+        assert int(got["%s size" % name]) == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert int(got["%s.%s" % (name, field)]) == getattr(cls, field).offset, (name, field)
+    for c in consts:
+        assert int(got[c]) == getattr(pond, c), c
+    assert int(got["POND_MLP_PARAMS"]) == pond.MLP_PARAMS
+    assert int(got["POND_MLP_FEATURES"]) == pond.MLP_FEATURES
+    assert int(got["POND_MLP_PAIR_STRIDE"]) == pond.MLP_PAIR_STRIDE
