@@ -79,10 +79,12 @@ def peaks():
 class ClockSampler:
     """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
 
-    def __init__(self, index):
+    def __init__(self, index, interval_ms=100):
         self.index = index
+        self.interval_ms = interval_ms
         self.proc = None
         self.lines = []
+        self.skip = 0
 
     def __enter__(self):
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -90,10 +92,16 @@ class ClockSampler:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.interval_ms)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            # nvidia-smi takes a moment to start: let its first sample arrive, so that the
+            # samples after this point fall inside the timed region that follows
+            t0 = time.perf_counter()
+            while not self.lines and self.proc.poll() is None and time.perf_counter() - t0 < 5.0:
+                time.sleep(0.01)
+            self.skip = len(self.lines)
         except Exception:
             self.proc = None
         return self
@@ -111,9 +119,12 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self, sm_max_default):
+        """Median SM clock and the throttle reasons seen in the samples taken during the timed
+        region (the samples before it when the region was shorter than one interval)."""
         sms, maxs, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        in_region = self.lines[self.skip:]
+        for ln in in_region or self.lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -128,7 +139,7 @@ class ClockSampler:
         if not sms:
             return {"sm_mhz": None, "sm_max_mhz": sm_max_default, "reasons": ["unsampled"]}
         return {"sm_mhz": statistics.median(sms), "sm_max_mhz": max(maxs), "reasons": sorted(reasons),
-                "samples": len(sms)}
+                "samples": len(sms), "samples_in_region": len(in_region)}
 
 
 def cpu_baseline(pb_full, steps, target_s=12.0):

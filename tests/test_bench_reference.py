@@ -1,6 +1,6 @@
-"""bench.py's reference arm (the FP64 oracle on host cores) on CPU: one JSON line with the
+"""bench.py on CPU.  The reference arm (the FP64 oracle on host cores): one JSON line with the
 headline's metric and unit, a cpu_baseline and an e2e object; under a launcher only rank 0
-runs it and the other ranks exit without work."""
+runs it and the other ranks exit without work.  The clock summary of the timed region."""
 import json
 import os
 import subprocess
@@ -33,3 +33,20 @@ def test_reference_arm_prints_one_line():
 def test_reference_arm_other_ranks_do_nothing():
     res = _run({"RANK": "1", "WORLD_SIZE": "2"})
     assert res.stdout.strip() == ""
+
+
+def test_clock_summary_reads_the_samples_of_the_timed_region():
+    c = bench.ClockSampler(0)
+    c.lines = ["0, 1980, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",   # before the region
+               "0, 2070, 2070, 1200.5, 0x4, Not Active, Not Active, Not Active, Active",
+               "0, 2055, 2070, 1300.0, 0x4, Not Active, Not Active, Not Active, Active",
+               "garbage"]
+    c.skip = 1
+    d = c.summary(2070.0)
+    assert d["sm_mhz"] == 2062.5 and d["sm_max_mhz"] == 2070.0
+    assert d["reasons"] == ["sw_power_cap"] and d["samples"] == 2 and d["samples_in_region"] == 3
+    c.lines = c.lines[:1]                       # region shorter than one interval
+    d = c.summary(2070.0)
+    assert d["sm_mhz"] == 1980.0 and d["samples_in_region"] == 0
+    c.lines = []
+    assert bench.ClockSampler(0).summary(2070.0)["reasons"] == ["unsampled"]
