@@ -238,7 +238,8 @@ pond_status pond_gauge_train(pond_state *s, const float *pairs, int64_t n, int e
  * (normalized) correction exceeds `gate` (default 0.01) and does not exceed `trust`
  * (default 0.5: larger moves can lead the corrector to another fixed point).  It keeps the
  * result only if it converges without a restart; otherwise it solves the face again from
- * the previous half step's frame, as without the network, so the corrector stays the judge.
+ * the previous half step's frame, as without the network, so the corrector alone decides
+ * the result.
  * Errors: INVALID_ARG for gate < 0 or trust <= 0. */
 pond_status pond_gauge_enable(pond_state *s, int on);
 pond_status pond_gauge_set_gate(pond_state *s, float gate);

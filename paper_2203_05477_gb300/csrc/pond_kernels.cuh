@@ -940,7 +940,7 @@ face_kernel(const Params<D, R> P)
         // With the learned predictor on, the corrector starts from the network's prediction
         // and keeps that result only if it converges without a restart; otherwise the face
         // is solved again from the previous half step's frame, exactly as without the
-        // network.  The corrector and its convergence test remain the judge.
+        // network.  The corrector and its convergence test alone decide the result.
         W base[D];
 #pragma unroll
         for (int a = 0; a < D; ++a) base[a] = uref[a];

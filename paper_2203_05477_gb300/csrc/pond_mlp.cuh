@@ -2,8 +2,8 @@
 //
 // The corrector of Sec. III.B.3 starts each face from the previous half step's frame.
 // This network predicts the converged frame from the face stencil, so the corrector starts
-// nearer its fixed point; the corrector and its convergence test are unchanged and remain
-// the judge of the result.
+// nearer its fixed point; the corrector and its convergence test are unchanged and alone
+// decide the result.
 //
 // Network: 48 (34 used) features -> 64 -> 64 -> 16 (3 used), ReLU, BF16 operands on the
 // tensor cores (tcgen05.mma kind::f16) with FP32 accumulation in tensor memory; biases and

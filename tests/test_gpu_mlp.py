@@ -62,7 +62,7 @@ def test_training_fits_a_smooth_target():
 
 def test_learned_predictor_in_the_solver():
     """Collect pairs from the plain FP32 solver on one seed, train on the GPU, then run
-    another seed with and without the learned predictor.  The corrector still judges
+    another seed with and without the learned predictor.  The corrector still decides
     convergence: the learned run stays within 1e-4 relative L1 of the FP64 oracle (as the
     plain FP32 run does), and the passes per face of both runs are reported."""
     from tests.common import oracle_for
