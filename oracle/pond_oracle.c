@@ -29,7 +29,7 @@
  *                   Eqs. (advectionPond)-(advectionPondg), (correctorfieldsrho)-
  *                   (correctorfieldT) and the BGK collision with beta.
  *
- * Readings where the paper is silent (each one is listed in the design notes):
+ * Readings where the paper is silent:
  *   R = 1, p = rho T, Cv = 1/(gamma-1); D in g^eq is the lattice dimension; the
  *   overline (symmetrization) is the sum over distinct index permutations; the face
  *   predictor before the first step is the frame of the pooled conserved moments of the two
