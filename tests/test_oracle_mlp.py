@@ -1,7 +1,9 @@
 """Pin of the reference network: its back-propagated gradient equals central finite
 differences of its loss (FP64, no quantization), and the quantized forward pass differs
-from the exact one only at the bfloat16 level."""
+from the exact one only at the bfloat16 level; the network, its loss and gradient equal
+torch's layers and autograd, and the bfloat16 rounding equals torch's conversion."""
 import numpy as np
+import pytest
 
 from oracle import gauge_mlp as G
 
@@ -38,3 +40,33 @@ def test_bf16_rounding():
     oq, _ = G.forward(p, X, quantize=True)
     oe, _ = G.forward(p, X, quantize=False)
     assert np.abs(oq - oe).max() <= 0.05 * np.abs(oe).max()
+
+
+def test_forward_loss_and_gradient_match_torch():
+    """The plain network and its loss, written out in numpy, against torch's Linear/ReLU
+    layers (y = x W^T + b, W stored [out][in]) and autograd, on the same FP64 parameters."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(5)
+    p = G.init_params(6)
+    X = rng.standard_normal((29, G.IN))
+    Y = rng.standard_normal((29, G.OUT))
+    W1, b1, W2, b2, W3, b3 = (torch.tensor(a, dtype=torch.float64, requires_grad=True) for a in G.unpack(p))
+    x = torch.tensor(X, dtype=torch.float64)
+    F = torch.nn.functional
+    out = F.linear(F.relu(F.linear(F.relu(F.linear(x, W1, b1)), W2, b2)), W3, b3)
+    loss = F.mse_loss(out[:, :G.OUT], torch.tensor(Y, dtype=torch.float64))
+    loss.backward()
+    ref_out, _ = G.forward(p, X, quantize=False)
+    ref_loss, ref_g = G.loss_and_grad(p, X, Y, quantize=False)
+    np.testing.assert_allclose(ref_out, out.detach().numpy(), rtol=1e-13, atol=1e-13)
+    assert ref_loss == pytest.approx(float(loss.detach()), rel=1e-13)
+    tg = np.concatenate([t.grad.numpy().ravel() for t in (W1, b1, W2, b2, W3, b3)])
+    np.testing.assert_allclose(ref_g, tg, rtol=1e-12, atol=1e-15)
+
+
+def test_bf16_matches_torch_rounding():
+    torch = pytest.importorskip("torch")
+    a = np.random.default_rng(7).standard_normal(4096) * np.exp(np.random.default_rng(8).uniform(-20, 20, 4096))
+    a = np.concatenate([a, [1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, -(1.0 + 2 ** -8), 0.0, 65504.0]]).astype(np.float32)
+    want = torch.from_numpy(a).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(G.bf16(a), want)
