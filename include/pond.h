@@ -281,6 +281,18 @@ pond_status pond_mlp_gradient(const float *params, const float *x, int ldx, cons
 pond_status pond_mlp_gradient_noalloc(const float *params, const float *x, int ldx, const float *y, int ldy, int64_t n,
                                       float *grad, float *loss, void *stream);
 
+/* Failure-detection check (not part of the paper).  Every wait inside the library's kernels
+ * is bounded: the tensor-core kernels poll the mbarrier that tcgen05.commit signals at most
+ * a fixed number of times and, when the bound expires, skip the rest of their tile, wait
+ * once more (bounded) for the work in flight, release their tensor memory and set an error
+ * word that the host reports as POND_ERR_TIMEOUT (pond_sync for the learned predictor, the
+ * call itself for training and the stand-alone network calls).  This call exercises that
+ * path without a fault: one CTA waits on an mbarrier that nothing arrives on, with `polls`
+ * polls (1 .. 2^24) of the same bounded wait, enqueued on `stream` (NULL: the legacy
+ * default stream) and waited for.  It returns POND_ERR_TIMEOUT, and the CUDA context stays
+ * usable; INVALID_ARG for polls out of range. */
+pond_status pond_wait_timeout_check(int64_t polls, void *stream);
+
 /* ---- Kernel-variant autotuning.  Not part of the paper.  Each step kernel is compiled in
    several variants: tile shapes and CTAs per SM of the face corrector, block sizes of the
    cell update, thread counts of the persistent tube kernel.  pond_autotune times every

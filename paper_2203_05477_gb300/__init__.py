@@ -117,6 +117,7 @@ def _load():
             "pond_gauge_collect": (ctypes.c_int, [vp, ctypes.c_int64, vp, ctypes.c_int64, ctypes.c_int, vp]),
             "pond_gauge_train": (ctypes.c_int, [vp, vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_float, vp]),
             "pond_gauge_enable": (ctypes.c_int, [vp, ctypes.c_int]),
+            "pond_wait_timeout_check": (ctypes.c_int, [ctypes.c_int64, vp]),
             "pond_gauge_set_gate": (ctypes.c_int, [vp, ctypes.c_float]),
             "pond_gauge_set_trust": (ctypes.c_int, [vp, ctypes.c_float]),
             "pond_gauge_set_params": (ctypes.c_int, [vp, vp]),

@@ -1250,8 +1250,11 @@ pond_status pond_sync(pond_state *s, pond_diag *diag)
     pond::Diag d{};
     CUDA_TRY(cudaMemcpyAsync(&c, s->clock, sizeof(c), cudaMemcpyDeviceToHost, s->stream));
     CUDA_TRY(cudaMemcpyAsync(&d, s->diag, sizeof(d), cudaMemcpyDeviceToHost, s->stream));
+    unsigned int mlp_e = 0;   // set by a tensor-core wait of the learned predictor that expired
+    if (s->mlp_err) CUDA_TRY(cudaMemcpyAsync(&mlp_e, s->mlp_err, sizeof(mlp_e), cudaMemcpyDeviceToHost, s->stream));
     CUDA_TRY(cudaStreamSynchronize(s->stream));
     CUDA_TRY(cudaGetLastError());
+    if (mlp_e) d.flags |= pond::FLAG_TIMEOUT;
     if (s->batch) {
         c.t = 0.0;
         c.dt = 0.0;
@@ -1271,6 +1274,9 @@ pond_status pond_sync(pond_state *s, pond_diag *diag)
     }
     if (d.flags & pond::FLAG_NONPHYSICAL) return fail(POND_ERR_NONPHYSICAL, "non-physical state: %llu cells/faces, first cell %lld",
                                                       (unsigned long long)d.nonphys, (long long)d.first_bad);
+    if (d.flags & pond::FLAG_TIMEOUT)
+        return fail(POND_ERR_TIMEOUT, "a tensor-core wait of the learned predictor expired; its faces started from the "
+                                      "previous half step's frame");
     if (s->opts.strict_convergence && (d.flags & pond::FLAG_NOT_CONVERGED))
         return fail(POND_ERR_NOT_CONVERGED, "%llu faces stopped at max_iter", (unsigned long long)d.nonconv);
     return POND_OK;
@@ -1408,6 +1414,18 @@ pond_status mlp_grad_launch(const float *prm, const float *x, int ldx, const flo
 }
 
 __device__ unsigned int g_standalone_err;
+__device__ unsigned int g_wait_check_err;
+
+// One CTA waits on an mbarrier that nothing arrives on, through the same bounded poll as the
+// tensor-core kernels, and records that the bound expired.
+__global__ void wait_timeout_check_kernel(long long polls, unsigned int *err)
+{
+    __shared__ __align__(8) uint64_t mbar;
+    if (threadIdx.x == 0) pond::tc::mbar_init(&mbar, 1);
+    __syncthreads();
+    const bool ok = pond::tc::mbar_wait(&mbar, 0u, polls);
+    if (!ok && threadIdx.x == 0) atomicOr(err, 1u);
+}
 
 }  // namespace
 
@@ -1541,6 +1559,22 @@ pond_status pond_gauge_get_params(pond_state *s, float *params)
     if (!params) return fail(POND_ERR_INVALID_ARG, "params is NULL");
     CUDA_TRY(cudaMemcpyAsync(params, s->mlp, 4 * pond::mlp::kParams, cudaMemcpyDeviceToHost, s->stream));
     CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return POND_OK;
+}
+
+pond_status pond_wait_timeout_check(int64_t polls, void *stream)
+{
+    if (polls < 1 || polls > (int64_t(1) << 24)) return fail(POND_ERR_INVALID_ARG, "polls must be in [1, 2^24]");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned int *err = nullptr;
+    CUDA_TRY(cudaGetSymbolAddress(reinterpret_cast<void **>(&err), g_wait_check_err));
+    CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(unsigned int), st));
+    wait_timeout_check_kernel<<<1, 32, 0, st>>>(polls, err);
+    CUDA_TRY(cudaGetLastError());
+    unsigned int e = 0;
+    CUDA_TRY(cudaMemcpyAsync(&e, err, sizeof(e), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (e) return fail(POND_ERR_TIMEOUT, "the bounded wait expired after %lld polls", (long long)polls);
     return POND_OK;
 }
 
