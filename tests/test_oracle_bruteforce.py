@@ -226,9 +226,9 @@ def random_state(D, shape, seed):
 @pytest.mark.parametrize("D,shape,seed,steps,minmod", [(1, (3,), 1, 2, False), (1, (5,), 2, 2, False),
                                                        (1, (8,), 3, 2, False), (2, (3, 3), 4, 2, False),
                                                        (1, (5,), 10, 2, True), (2, (3, 3), 11, 2, True),
-                                                       (2, (3, 4), 12, 2, False), (3, (3, 3, 3), 5, 1, False)],
+                                                       (2, (3, 4), 12, 2, False), (3, (3, 3, 4), 5, 1, False)],
                          ids=["1d_3", "1d_5", "1d_8", "2d_3x3", "1d_5_minmod", "2d_3x3_minmod", "2d_3x4_nonsquare",
-                              "3d_3x3x3"])
+                              "3d_3x3x4"])
 def test_oracle_step_equals_brute_force(D, shape, seed, steps, minmod):
     """The D3Q64 case (one step, about 40 s) pins the three-dimensional stencil: the normal
     and both tangential slopes of every face, and the fluxes of the three axes.  The 3 x 4
