@@ -148,6 +148,6 @@ def test_binding_structs_match_the_header(tmp_path):
     assert int(got["POND_MLP_PAIR_STRIDE"]) == pond.MLP_PAIR_STRIDE
 
 
-def test_wait_timeout_check_validates_before_touching_the_device():
+def test_wait_timeout_check_validates_before_touching_the_device(lib):
     assert pond.pond_wait_timeout_check(0, None) == pond.POND_ERR_INVALID_ARG
     assert pond.pond_wait_timeout_check(1 << 25, None) == pond.POND_ERR_INVALID_ARG
