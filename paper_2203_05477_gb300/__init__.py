@@ -280,13 +280,6 @@ class Solver:
         """Conserved fields into device tensors (each may be None); totals into a host array."""
         _check(self.lib.pond_moments(self.h, *[_ptr(a) for a in outs], _ptr(totals), 1))
 
-    def primitive(self):
-        (rho, mx, my, E), _ = self.moments(totals=False)
-        cv = 1.0 / (self.problem.gamma - 1.0)
-        ux, uy = mx / rho, my / rho
-        T = (E - 0.5 * (mx * mx + my * my) / rho) / (cv * rho)
-        return rho, ux, uy, rho * T
-
     def state(self):
         cf = np.zeros((self.ncell, self.nfc))
         cg = np.zeros((self.ncell, self.ngc))
@@ -443,12 +436,6 @@ class Solver3(Solver):
     def moments_device(self, outs, totals=None):
         _check(self.lib.pond_moments3(self.h, *[_ptr(a) for a in outs], _ptr(totals), 1))
 
-    def primitive(self):
-        (rho, mx, my, mz, E), _ = self.moments(totals=False)
-        cv = 1.0 / (self.problem.gamma - 1.0)
-        T = (E - 0.5 * (mx * mx + my * my + mz * mz) / rho) / (cv * rho)
-        return rho, mx / rho, my / rho, mz / rho, rho * T
-
     def face_gauges(self):
         nx, ny, nz = self.nx, self.ny, self.nz
         out = (np.zeros(((nx + 1) * ny * nz, 4)), np.zeros((nx * (ny + 1) * nz, 4)), np.zeros((nx * ny * (nz + 1), 4)))
@@ -521,15 +508,6 @@ class BatchSolver(Solver):
         g = np.zeros((int((self.lengths + 1).sum()), 2))
         _check(self.lib.pond_get_face_gauges(self.h, _ptr(g), None))
         return g, None
-
-    def primitive_tube(self, k, gamma):
-        (rho, mx, _, E), _ = self.moments(totals=False)
-        a, b = self.offsets[k], self.offsets[k + 1]
-        r, m, e = rho[a:b], mx[a:b], E[a:b]
-        cv = 1.0 / (gamma - 1.0)
-        u = m / r
-        T = (e - 0.5 * m * m / r) / (cv * r)
-        return r, u, r * T
 
 
 def mlp_forward(params, x):

@@ -1,4 +1,4 @@
-// pond3_launch.cuh -- launches of the D3Q64 kernels (instantiated in pond_v3.cu).
+// pond3_launch.cuh -- launches of the D3Q64 kernels (instantiated in pond_v3f.cu and pond_v3d.cu through pond_v3_impl.cuh).
 #pragma once
 
 #include "pond3.cuh"

@@ -48,3 +48,25 @@ def max_rel(a, b):
     """max |a - b| / max |b| (field-wise relative error)."""
     a, b = np.asarray(a), np.asarray(b)
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def gpu_primitive(s):
+    """Primitive fields of a GPU solver's grid from the conserved fields it returns (test
+    helper; the library itself never converts): rho, ux, uy, p on 1D/2D grids and rho, ux,
+    uy, uz, p on D3Q64 grids, with p = rho T and E = rho (Cv T + |u|^2 / 2), Cv = 1/(gamma - 1)."""
+    out, _ = s.moments(totals=False)
+    cv = 1.0 / (s.problem.gamma - 1.0)
+    rho, E = out[0], out[-1]
+    mom = out[1:-1]
+    T = (E - 0.5 * sum(m * m for m in mom) / rho) / (cv * rho)
+    return (rho, *[m / rho for m in mom], rho * T)
+
+
+def gpu_primitive_tube(s, k, gamma):
+    """rho, u, p of tube k of a batched GPU solver (test helper, as gpu_primitive)."""
+    (rho, mx, _, E), _ = s.moments(totals=False)
+    a, b = s.offsets[k], s.offsets[k + 1]
+    r, m, e = rho[a:b], mx[a:b], E[a:b]
+    cv = 1.0 / (gamma - 1.0)
+    T = (e - 0.5 * m * m / r) / (cv * r)
+    return r, m / r, r * T

@@ -12,7 +12,7 @@ pytestmark = pytest.mark.gpu
 import oracle as O  # noqa: E402
 import paper_2203_05477_gb300 as pond  # noqa: E402
 from paper_2203_05477_gb300 import inputs as I  # noqa: E402
-from tests.common import max_rel, oracle_for, rel_l1  # noqa: E402
+from tests.common import gpu_primitive, max_rel, oracle_for, rel_l1  # noqa: E402
 
 KW64 = dict(tau=1e-5, fixed_iters=3, max_iter=8)
 
@@ -131,7 +131,7 @@ def test_fp32_against_fp64_oracle():
     gs.step(6)
     os_.step(6)
     assert gs.sync()["nonphysical"] == 0
-    r, ux, uy, uz, p = gs.primitive()
+    r, ux, uy, uz, p = gpu_primitive(gs)
     ro, uxo, uyo, uzo, po = os_.primitive()
     assert rel_l1(r, ro) <= 1e-4 and rel_l1(p, po) <= 1e-4
     sp, spo = np.sqrt(ux ** 2 + uy ** 2 + uz ** 2), np.sqrt(uxo ** 2 + uyo ** 2 + uzo ** 2)

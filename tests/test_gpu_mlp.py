@@ -9,7 +9,7 @@ torch = pytest.importorskip("torch")
 import paper_2203_05477_gb300 as pond  # noqa: E402
 from oracle import gauge_mlp as G  # noqa: E402
 from paper_2203_05477_gb300 import inputs as I  # noqa: E402
-from tests.common import rel_l1  # noqa: E402
+from tests.common import gpu_primitive, rel_l1  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -86,7 +86,7 @@ def test_learned_predictor_in_the_solver():
         g.step(steps)
         d = g.sync()
         assert d["status"] == pond.POND_OK, d
-        out = (g.primitive(), d["face_iters"] / d["face_solves"], d["nonconverged"])
+        out = (gpu_primitive(g), d["face_iters"] / d["face_solves"], d["nonconverged"])
         g.close()
         return out
 
@@ -133,7 +133,7 @@ def _run_quadrants(params, steps, gate=None, trust=None, max_iter=16):
         g.gauge_enable(True, gate=gate, trust=trust)
     g.step(steps)
     d = g.sync()
-    out = g.primitive(), d
+    out = gpu_primitive(g), d
     g.close()
     return out
 

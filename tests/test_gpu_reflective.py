@@ -12,7 +12,7 @@ torch = pytest.importorskip("torch")
 
 import paper_2203_05477_gb300 as pond  # noqa: E402
 from paper_2203_05477_gb300 import inputs as I  # noqa: E402
-from tests.common import oracle_for, rel_l1  # noqa: E402
+from tests.common import gpu_primitive, oracle_for, rel_l1  # noqa: E402
 from tests.test_gpu_parity import compare_fp64, gpu_for  # noqa: E402
 from tests.test_oracle_reflective import perturbed  # noqa: E402
 
@@ -80,7 +80,7 @@ def test_fp32_explosion_box_against_fp64_oracle():
     gs.step(40)
     os_.step(40)
     assert gs.sync()["nonphysical"] == 0 and os_.stats()["nonphysical"] == 0
-    r, ux, uy, p = gs.primitive()
+    r, ux, uy, p = gpu_primitive(gs)
     ro, uxo, uyo, po = os_.primitive()
     assert rel_l1(r, ro) <= 1e-4 and rel_l1(p, po) <= 1e-4
     speed = np.sqrt(uxo ** 2 + uyo ** 2)
@@ -109,7 +109,7 @@ def test_explosion_box_density_range_matches_paper():
         if d["t"] >= g["t"] or d["nonphysical"]:
             break
     assert d["nonphysical"] == 0 and d["t"] == pytest.approx(g["t"], rel=1e-12)
-    r = s.primitive()[0]
+    r = gpu_primitive(s)[0]
     assert r.min() == pytest.approx(g["rho_min"], rel=0.03)
     assert r.max() == pytest.approx(g["rho_max"], rel=0.03)
 
@@ -128,7 +128,7 @@ def test_two_blast_fp32_matches_fp64_at_paper_size():
             if d["t"] >= 0.038 or d["nonphysical"]:
                 break
         assert d["nonphysical"] == 0 and d["t"] == pytest.approx(0.038, rel=1e-12), prec
-        out[prec] = s.primitive()
+        out[prec] = gpu_primitive(s)
     for k in (0, 1, 3):
         assert rel_l1(out["fp32"][k], out["fp64"][k]) <= 1e-4, k
     r = out["fp64"][0]

@@ -13,7 +13,7 @@ import pytest
 torch = pytest.importorskip("torch")
 
 from paper_2203_05477_gb300 import inputs as I  # noqa: E402
-from tests.common import oracle_for  # noqa: E402
+from tests.common import gpu_primitive, oracle_for  # noqa: E402
 from tests.test_gpu_parity import compare_fp64, gpu_for  # noqa: E402
 
 pytestmark = pytest.mark.gpu
@@ -50,7 +50,7 @@ def interface_amplitude(r, thr, nx=600, ny=100):
 def test_rmi_paper_size(kind, t_end, thr):
     pb = I.rmi_2d(kind)
     s = gpu_for(pb, precision="fp32", tau=1e-5, cfl=0.2, t_end=t_end, max_iter=16)
-    a0 = interface_amplitude(s.primitive()[0], thr)
+    a0 = interface_amplitude(gpu_primitive(s)[0], thr)
     assert a0 == pytest.approx(0.008, abs=0.001)
     for _ in range(200):
         s.step(128)
@@ -58,7 +58,7 @@ def test_rmi_paper_size(kind, t_end, thr):
         if d["t"] >= t_end or d["nonphysical"]:
             break
     assert d["nonphysical"] == 0 and d["t"] == pytest.approx(t_end, rel=1e-9)
-    r = s.primitive()[0]
+    r = gpu_primitive(s)[0]
     R = r.reshape(100, 600)
     assert np.abs(R - R[::-1]).max() <= 1e-3 * R.max()
     a = interface_amplitude(r, thr)

@@ -9,7 +9,7 @@ torch = pytest.importorskip("torch")
 
 import paper_2203_05477_gb300 as pond  # noqa: E402
 from paper_2203_05477_gb300 import inputs as I  # noqa: E402
-from tests.common import hermite_of_pops, max_rel, oracle_for, rel_l1  # noqa: E402
+from tests.common import gpu_primitive, hermite_of_pops, max_rel, oracle_for, rel_l1  # noqa: E402
 from tests.test_gpu_parity import compare_fp64  # noqa: E402
 from tests.test_oracle_reflective import perturbed, walled  # noqa: E402
 
@@ -89,7 +89,7 @@ def test_sl_fp32_against_fp64_oracle():
     os_.sl_step(2000)
     d = gs.sync()
     assert d["t"] == pytest.approx(0.2, rel=1e-9) and d["nonphysical"] == 0
-    r, ux, _, p = gs.primitive()
+    r, ux, _, p = gpu_primitive(gs)
     ro, uo, _, po = os_.primitive()
     x = (np.arange(400) + 0.5) / 400
     window = x > 0.75
@@ -143,7 +143,7 @@ def test_sl_2d_fp32_against_fp64_oracle():
     gs.step(20)
     os_.sl_step(20)
     assert gs.sync()["nonphysical"] == 0
-    r, ux, uy, p = gs.primitive()
+    r, ux, uy, p = gpu_primitive(gs)
     ro, uxo, uyo, po = os_.primitive()
     assert rel_l1(r, ro) <= 1e-4 and rel_l1(p, po) <= 1e-4
     sp, spo = np.hypot(ux, uy), np.hypot(uxo, uyo)

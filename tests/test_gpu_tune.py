@@ -9,7 +9,7 @@ torch = pytest.importorskip("torch")
 
 import paper_2203_05477_gb300 as pond  # noqa: E402
 from paper_2203_05477_gb300 import inputs as I  # noqa: E402
-from tests.common import max_rel, oracle_for, rel_l1  # noqa: E402
+from tests.common import gpu_primitive, max_rel, oracle_for, rel_l1  # noqa: E402
 from tests.test_gpu_batch import run_pair, small_batch  # noqa: E402
 from tests.test_gpu_parity import compare_fp64, gpu_for  # noqa: E402
 
@@ -47,7 +47,7 @@ def test_every_grid_variant_matches_oracle_fp64(name, pb):
 
 
 def _prims(s):
-    return [np.asarray(a) for a in s.primitive()]  # rho, ux, uy, p
+    return [np.asarray(a) for a in gpu_primitive(s)]  # rho, ux, uy, p
 
 
 def test_fp32_grid_variants_agree():
