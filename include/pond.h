@@ -272,11 +272,14 @@ pond_status pond_mlp_gradient(const float *params, const float *x, int ldx, cons
  * arrays owned by the caller).  The activation scratch lives in a fixed device array of
  * the library sized for POND_MLP_NOALLOC_MAX_ROWS rows (about 5 MB, held by every GPU that
  * loads the library until the process exits); n above that limit returns
- * POND_ERR_INVALID_ARG.  The first call on a device looks up that array's device address
- * and sets the kernels' shared-memory limit for that device, so make the first call before
- * any stream capture.  All calls share the one array: calls whose work overlaps on the GPU
+ * POND_ERR_INVALID_ARG.  Every call looks up that array's device address in the current
+ * context (no allocation); the first call on a device also sets the kernels' shared-memory
+ * limit for that device and loads the array's module, so make the first call before any
+ * stream capture.  All calls share the one array: calls whose work overlaps on the GPU
  * (different streams, or threads calling concurrently) race on it; serialize them.  The
- * call clears *loss and its error word itself, enqueues on `stream`, and waits for it. */
+ * call clears *loss and its error word itself, enqueues on `stream`, and waits for it.
+ * On POND_ERR_TIMEOUT grad is left as it was (the weight-gradient kernel does not run on
+ * incomplete activations) and *loss is undefined. */
 #define POND_MLP_NOALLOC_MAX_ROWS 8192
 pond_status pond_mlp_gradient_noalloc(const float *params, const float *x, int ldx, const float *y, int ldy, int64_t n,
                                       float *grad, float *loss, void *stream);

@@ -1640,23 +1640,24 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratch
 
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mutex;
-unsigned char *g_noalloc_ptr[kMaxDevices] = {};
+bool g_noalloc_ready[kMaxDevices] = {};
 
-// once per device, with that device current: the array's device address and the
-// shared-memory limit of the tile kernel
+// With the caller's device current: the array's device address in the current context
+// (looked up on every call, which allocates nothing, so a context created after a device
+// reset gets its own address) and, once per device, the tile kernel's shared-memory limit.
 pond_status noalloc_setup(unsigned char **out)
 {
     int dev = 0;
     CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return fail(POND_ERR_UNSUPPORTED, "device ordinal %d out of range", dev);
+    void *p = nullptr;
+    CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
-        CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    if (!g_noalloc_ready[dev]) {
         CUDA_TRY(cudaFuncSetAttribute(pond::mlp::tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, pond::mlp::kTileSmem));
-        g_noalloc_ptr[dev] = static_cast<unsigned char *>(p);
+        g_noalloc_ready[dev] = true;
     }
-    *out = g_noalloc_ptr[dev];
+    *out = static_cast<unsigned char *>(p);
     return POND_OK;
 }
 

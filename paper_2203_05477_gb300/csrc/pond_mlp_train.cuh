@@ -95,6 +95,9 @@ wgrad_kernel(const float *x, int ldx, const __nv_bfloat16 *H1, const __nv_bfloat
     __shared__ __align__(1024) unsigned char sB[kHid * KC * 2];
     __shared__ uint64_t mbar;
     __shared__ uint32_t tmem_base;
+    // the tile kernel's activations are incomplete when one of its waits expired: leave grad
+    // untouched (the call reports POND_ERR_TIMEOUT)
+    if (*(volatile unsigned int *)err) return;
     const int which = blockIdx.x;  // 0: W1, 1: W2, 2: W3
     const int Mr = which == 2 ? kOutP : kHid;
     const int N = which == 0 ? kIn : kHid;

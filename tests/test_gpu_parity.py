@@ -9,7 +9,7 @@ torch = pytest.importorskip("torch")
 
 import paper_2203_05477_gb300 as pond  # noqa: E402
 from paper_2203_05477_gb300 import inputs as I  # noqa: E402
-from tests.common import hermite_of_pops, max_rel, oracle_for, rel_l1  # noqa: E402
+from tests.common import gpu_primitive, hermite_of_pops, max_rel, oracle_for, rel_l1  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -142,7 +142,7 @@ def test_fp32_against_fp64_oracle_sod():
     os_.step(700)
     d = gs.sync()
     assert d["status"] == pond.POND_OK, d
-    r, u, _, p = gs.primitive()
+    r, u, _, p = gpu_primitive(gs)
     ro, uo, _, po = os_.primitive()
     assert rel_l1(r, ro) < 1e-4 and rel_l1(p, po) < 1e-4
     assert np.abs(u - uo).sum() / np.abs(uo).sum() < 1e-4
@@ -158,7 +158,7 @@ def test_fp32_against_fp64_oracle_quadrants(seed):
     os_.step(40)
     d = gs.sync()
     assert d["status"] == pond.POND_OK, d
-    r, ux, uy, p = gs.primitive()
+    r, ux, uy, p = gpu_primitive(gs)
     ro, uxo, uyo, po = os_.primitive()
     assert rel_l1(r, ro) < 1e-4 and rel_l1(p, po) < 1e-4
     sp, spo = np.hypot(ux, uy), np.hypot(uxo, uyo)
@@ -196,7 +196,7 @@ def test_uniform_mach80_any_gauge(precision):
     gs.step(20)
     d = gs.sync()
     assert d["status"] == pond.POND_OK, d
-    r, ux, uy, p = gs.primitive()
+    r, ux, uy, p = gpu_primitive(gs)
     tol = 1e-9 if precision == "fp64" else 2e-5
     assert max_rel(r, np.full(N, 2.0)) < tol and max_rel(p, np.full(N, 2.0 * T)) < 10 * tol
     assert np.abs(ux - u).max() < tol * u and np.abs(uy + 0.4 * u).max() < tol * u
@@ -229,47 +229,99 @@ def test_nonphysical_input_is_reported():
     assert ok.sync()["status"] == pond.POND_OK
 
 
-def test_full_size_sampled_first_step():
-    """The bench workload (1024^2 quadrants, FP32 and FP64, in the autotuned launch
-    configuration the bench uses) checked on sampled cells: one step depends only on a
-    radius-3 neighbourhood, so the oracle runs that step on patches cut from the same
-    initial condition with the full grid's first time step."""
-    n, cfl = 1024, 0.2
-    pb = I.quadrants_2d(n, seed=0)
-    g = pb.gamma
+C_MAX = 2.3344142183389773  # the largest D1Q4 node, sqrt(3 + sqrt(6))
+
+
+def sampled_first_step(pb, samples, cfl, m=4):
+    """A bench-size workload (FP32 and FP64, in the autotuned launch configuration the bench
+    uses) checked on sampled cells: one step depends only on a radius-3 neighbourhood, so
+    the oracle runs that step on (2m+1)^2 patches cut from the same initial condition, with
+    the full grid's first time step and the grid's own sides where a patch touches them
+    (periodic axes are cut with wrap-around)."""
+    nx, ny = pb.nx, pb.ny
     T = pb.p / pb.rho
-    rate = ((np.maximum(np.abs(pb.ux), np.abs(pb.uy)) + np.sqrt(T) * 2.3344142183389773) / pb.dx).max()
+    rate = max(((np.abs(pb.ux) + np.sqrt(T) * C_MAX) / pb.dx).max(), ((np.abs(pb.uy) + np.sqrt(T) * C_MAX) / pb.dy).max())
     dt = cfl / rate
-    rng = np.random.default_rng(0)
-    samples = [(int(i), int(j)) for i, j in rng.integers(0, n, (6, 2))] + [(511, 511), (512, 512), (0, 0), (n - 1, 700)]
     results = {}
     for prec in ("fp64", "fp32"):
         gs = gpu_for(pb, precision=prec, tau=1e-5, cfl=cfl, fixed_iters=3, max_iter=8)
-        # the kernel variants the bench runs: the autotuner's choice on this state (restored)
         tuned = gs.autotune(steps=1)
         assert not tuned["from_cache"]
         gs.step(1)
-        assert gs.sync()["dt"] > 0
+        d = gs.sync()
+        assert d["dt"] > 0 and d["nonphysical"] == 0, d
         results[prec] = gs.moments(totals=False)[0]
         gs.close()
-    m = 4
+    per_y = pb.bc[2] == I.PERIODIC
     for (i, j) in samples:
-        i0, i1 = max(0, i - m), min(n, i + m + 1)
-        j0, j1 = max(0, j - m), min(n, j + m + 1)
-        sub = lambda a: a.reshape(n, n)[j0:j1, i0:i1].ravel()
-        patch = I.Problem(2, i1 - i0, j1 - j0, 0, (i1 - i0) * pb.dx, 0, (j1 - j0) * pb.dy, g,
-                          sub(pb.rho), sub(pb.ux), sub(pb.uy), sub(pb.p))
+        i0, i1 = max(0, i - m), min(nx, i + m + 1)
+        js = np.arange(j - m, j + m + 1) % ny if per_y else np.arange(max(0, j - m), min(ny, j + m + 1))
+        grid = lambda a: a.reshape(ny, nx)[js][:, i0:i1].ravel()
+        bc = [pb.bc[0] if i0 == 0 else I.TRANSMISSIVE, pb.bc[1] if i1 == nx else I.TRANSMISSIVE,
+              I.TRANSMISSIVE if per_y or js[0] != 0 else pb.bc[2], I.TRANSMISSIVE if per_y or js[-1] != ny - 1 else pb.bc[3]]
+        inflow = np.zeros((4, 4))
+        rng = np.zeros((4, 2), dtype=np.int64)
+        if bc[0] == I.INFLOW:
+            inflow[0] = pb.inflow[0]
+            rows = np.nonzero((js >= pb.inflow_range[0][0]) & (js < pb.inflow_range[0][1]))[0]
+            if rows.size:
+                assert rows.size == rows[-1] - rows[0] + 1
+                rng[0] = (rows[0], rows[-1] + 1)
+        assert bc[1] != I.INFLOW and bc[2] != I.INFLOW and bc[3] != I.INFLOW
+        pw, ph = i1 - i0, len(js)
+        patch = I.Problem(2, pw, ph, 0, pw * pb.dx, 0, ph * pb.dy, pb.gamma, grid(pb.rho), grid(pb.ux), grid(pb.uy),
+                          grid(pb.p), bc=tuple(bc), inflow=inflow, inflow_range=rng)
         os_ = oracle_for(patch, tau=1e-5, cfl=cfl, fixed_iters=3, max_iter=8)
         os_.force_dt(dt)
         os_.step(1)
+        assert os_.stats()["nonphysical"] == 0
         ro = os_.conserved()
-        k_patch = (j - j0) * (i1 - i0) + (i - i0)
-        k = j * n + i
+        k_patch = int(np.nonzero(js == j)[0][0]) * pw + (i - i0)
+        k = j * nx + i
         for fld in range(4):
             ref = ro[fld][k_patch]
             scale = max(abs(ref), abs(ro[0][k_patch]), abs(ro[3][k_patch]))
             assert abs(results["fp64"][fld][k] - ref) <= FP64_TOL * scale, ("fp64", i, j, fld)
             assert abs(results["fp32"][fld][k] - ref) <= 1e-5 * scale, ("fp32", i, j, fld)
+
+
+def test_full_size_sampled_first_step():
+    """Configuration 2 at the bench's size: 1024^2 quadrants, seed 0."""
+    n = 1024
+    pb = I.quadrants_2d(n, seed=0)
+    rng = np.random.default_rng(0)
+    samples = [(int(i), int(j)) for i, j in rng.integers(0, n, (6, 2))] + [(511, 511), (512, 512), (0, 0), (n - 1, 700)]
+    sampled_first_step(pb, samples, 0.2)
+
+
+def test_full_size_sampled_first_step_shocked_interface():
+    """Configuration 4 at its stated size: the shocked perturbed interface on 4096 x 1024
+    cells (left inflow at the post-shock state, periodic in y), sampled at the inflow side,
+    across the shock (x = 0.5) and the interface (x ~ 1), at the periodic seam and at
+    random cells."""
+    pb = I.shocked_interface_2d(4096, 1024, seed=0)
+    rng = np.random.default_rng(1)
+    samples = [(int(i), int(j)) for i, j in zip(rng.integers(0, 4096, 6), rng.integers(0, 1024, 6))]
+    samples += [(0, 0), (0, 1023), (1, 500), (511, 3), (512, 1020), (4095, 0), (4095, 777)]
+    r = pb.rho.reshape(1024, 4096)
+    for j in (0, 100, 255, 600):
+        i_if = int(np.argmax(r[j, 600:] > 1.5)) + 600   # first heavy-gas cell of row j
+        samples += [(i_if - 1, j), (i_if, j)]
+    sampled_first_step(pb, samples, 0.2)
+
+
+def test_full_size_sampled_first_step_jet():
+    """Configuration 5 at its stated size: the Mach-80 jet on 4096^2 cells, sampled at the
+    edges of the inflow band, next to it on the inflow side, in the corners and at random
+    cells."""
+    n = 4096
+    pb = I.jet_2d(n, seed=0)
+    lo, hi = int(pb.inflow_range[0][0]), int(pb.inflow_range[0][1])
+    rng = np.random.default_rng(2)
+    samples = [(int(i), int(j)) for i, j in rng.integers(0, n, (4, 2))]
+    samples += [(0, lo - 1), (0, lo), (0, (lo + hi) // 2), (0, hi - 1), (0, hi), (1, lo), (2, hi - 1), (0, 0),
+                (n - 1, n - 1), (0, n - 1)]
+    sampled_first_step(pb, samples, 0.2)
 
 
 @pytest.mark.parametrize("name,pb,cfl", [
@@ -299,6 +351,35 @@ def test_fp32_minmod_against_fp64_oracle():
     gs.step(10)
     os_.step(10)
     assert gs.sync()["nonphysical"] == 0
-    r, _, _, p = gs.primitive()
+    r, _, _, p = gpu_primitive(gs)
     ro, _, _, po = os_.primitive()
     assert rel_l1(r, ro) <= 1e-4 and rel_l1(p, po) <= 1e-4
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_compensated_totals_against_exact_sum(precision):
+    """The double-double totals of pond_moments (the conserved moments of Sec. II.B summed
+    over the grid, times the cell area) against the exactly rounded sum (math.fsum) of the
+    per-cell fields the same call returns, on ill-conditioned fields: densities alternating
+    1e16 and O(1), with momenta of the heavy cells cancelling in pairs, so that a plain
+    double sum loses every light cell's contribution.  Bound: one rounding of the result."""
+    import math
+    nx, ny = 129, 67
+    N = nx * ny
+    k = np.arange(N)
+    heavy = k % 2 == 0
+    sign = np.where((k // 2) % 2 == 0, 1.0, -1.0)
+    rho = np.where(heavy, 1e16, 1.0 + 0.37 * (k % 7))
+    ux = np.where(heavy, sign, 0.3 + 0.011 * (k % 5))
+    uy = np.where(heavy, -sign * 0.5, -0.2 + 0.013 * (k % 3))
+    p = 0.5 * rho
+    pb = I.Problem(2, nx, ny, 0, 1.0, 0, 0.75, 1.4, rho, ux, uy, p, bc=(I.PERIODIC,) * 4)
+    gs = gpu_for(pb, precision=precision, tau=1e-5, cfl=0.2)
+    fields, tot = gs.moments(totals=True)
+    vol = pb.dx * pb.dy
+    naive_lost = 0
+    for q in range(4):
+        exact = math.fsum(fields[q].tolist()) * vol
+        assert abs(tot[q] - exact) <= np.spacing(abs(exact)), (q, tot[q], exact)
+        naive_lost += int(float(np.cumsum(fields[q])[-1]) * vol != exact)
+    assert naive_lost >= 2   # the fields defeat a plain left-to-right double sum
