@@ -590,7 +590,11 @@ pond_status batch_setup(pond_state *s, const int64_t *lengths, const double *gam
         o_sg[b] = take(sizeof(R) * 3 * nc);
         o_sfr[b] = take(sizeof(typename TP::CellW) * 2 * nc);
     }
-    const size_t o_fu = take(sizeof(typename TP::FaceW) * nf), o_fT = take(sizeof(typename TP::FaceW) * nf);
+    size_t o_fu[2], o_fT[2];
+    for (int b = 0; b < 2; ++b) {
+        o_fu[b] = take(sizeof(typename TP::FaceW) * nf);
+        o_fT[b] = take(sizeof(typename TP::FaceW) * nf);
+    }
     const size_t o_diag = take(sizeof(pond::Diag)), o_clock = take(sizeof(pond::Clock));
     const size_t stage = std::max<size_t>(4 * size_t(nc), 7 * size_t(nc)) + 2 * size_t(nf) + 8;
     const size_t o_stage = take(8 * stage);
@@ -623,8 +627,10 @@ pond_status batch_setup(pond_state *s, const int64_t *lengths, const double *gam
         P.sg[b] = reinterpret_cast<R *>(B + o_sg[b]);
         P.sfr[b] = reinterpret_cast<typename TP::CellW *>(B + o_sfr[b]);
     }
-    P.fu = reinterpret_cast<typename TP::FaceW *>(B + o_fu);
-    P.fT = reinterpret_cast<typename TP::FaceW *>(B + o_fT);
+    for (int b = 0; b < 2; ++b) {
+        P.fu[b] = reinterpret_cast<typename TP::FaceW *>(B + o_fu[b]);
+        P.fT[b] = reinterpret_cast<typename TP::FaceW *>(B + o_fT[b]);
+    }
     P.diag = reinterpret_cast<pond::Diag *>(B + o_diag);
     P.tau = s->tau;
     P.cfl = s->opts.cfl;
@@ -753,12 +759,12 @@ pond_status batch_face_gauges(pond_state *s, double *out, const double *in)
     std::vector<W> u(nf), T(nf);
     if (in) {
         for (long long f = 0; f < nf; ++f) { u[f] = W(in[2 * f]); T[f] = W(in[2 * f + 1]); }
-        CUDA_TRY(cudaMemcpyAsync(P.fu, u.data(), sizeof(W) * nf, cudaMemcpyHostToDevice, s->stream));
-        CUDA_TRY(cudaMemcpyAsync(P.fT, T.data(), sizeof(W) * nf, cudaMemcpyHostToDevice, s->stream));
+        CUDA_TRY(cudaMemcpyAsync(P.fu[s->cur], u.data(), sizeof(W) * nf, cudaMemcpyHostToDevice, s->stream));
+        CUDA_TRY(cudaMemcpyAsync(P.fT[s->cur], T.data(), sizeof(W) * nf, cudaMemcpyHostToDevice, s->stream));
         CUDA_TRY(cudaStreamSynchronize(s->stream));
     } else {
-        CUDA_TRY(cudaMemcpyAsync(u.data(), P.fu, sizeof(W) * nf, cudaMemcpyDeviceToHost, s->stream));
-        CUDA_TRY(cudaMemcpyAsync(T.data(), P.fT, sizeof(W) * nf, cudaMemcpyDeviceToHost, s->stream));
+        CUDA_TRY(cudaMemcpyAsync(u.data(), P.fu[s->cur], sizeof(W) * nf, cudaMemcpyDeviceToHost, s->stream));
+        CUDA_TRY(cudaMemcpyAsync(T.data(), P.fT[s->cur], sizeof(W) * nf, cudaMemcpyDeviceToHost, s->stream));
         CUDA_TRY(cudaStreamSynchronize(s->stream));
         for (long long f = 0; f < nf; ++f) { out[2 * f] = double(u[f]); out[2 * f + 1] = double(T[f]); }
     }

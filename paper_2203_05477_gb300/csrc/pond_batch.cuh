@@ -2,14 +2,17 @@
 //
 // Each CTA owns one tube for the whole run and loops over the time steps itself: the
 // tube's time step comes from its own CFL maximum (a CTA reduction), so tubes never wait
-// on one another and no inter-CTA synchronization exists.  Per step the tube is streamed
-// in chunks of THREADS - 4 cells: the chunk and a halo of two cells are staged in shared memory
-// (phi-bar-plus, Eq. Fbarplus), the face corrector (Sec. III.B.3) writes the face
-// populations to shared memory, and the cell update (Eqs. fluxEq, FinalUpdateDUGKS, with
-// the re-expression in the new co-moving frame) writes the new state into the other of two
-// state buffers, so later chunks still read the old state.  Face populations never reach
-// global memory; per cell and step the traffic is the state read and written once and the
-// face predictor read and written once.
+// on one another and no inter-CTA synchronization exists.  Per step every warp streams its
+// own chunks of 30 cells (chunk w, w + warps, ...): the chunk and a halo of two cells on
+// each side are staged in the warp's part of shared memory (phi-bar-plus, Eq. Fbarplus),
+// each lane solves one of the chunk's 31 faces (Sec. III.B.3) into shared memory, and the
+// lane that staged a cell of the chunk then updates it from the state it still holds
+// (Eqs. fluxEq, FinalUpdateDUGKS, with the re-expression in the new co-moving frame).  Warps meet only at the end of a step (the CFL reduction), so a
+// warp whose faces need more corrector passes holds up no other.  The state and the face
+// predictors are read from one of two buffers and written to the other, so a chunk never
+// sees a neighbouring chunk's new values.  Face populations never reach global memory; per
+// cell and step the traffic is the state read and written once and the face predictor
+// read and written once.
 //
 // Frames.  The FP64 kernel holds each frame as doubles.  The FP32 kernel holds a cell frame
 // (u, T) as a float-float pair and the face predictor as plain floats, so its inner loops
@@ -42,7 +45,7 @@ struct TubeParams {
     R *sf[2];                     // [3][ncell] rho, a2, a3  (two buffers)
     R *sg[2];                     // [3][ncell] b0, b1, b2
     CellW *sfr[2];                // [2][ncell] u, T
-    FaceW *fu, *fT;               // face predictors [nface]
+    FaceW *fu[2], *fT[2];         // face predictors [nface] (two buffers, paired with the state's)
     double *t, *dt;               // per tube
     double *totals;               // per tube [4]: rho, rho u, 0, rho E summed times dx
     int *status;                  // per tube: 0 running, 1 stopped after a non-physical state
@@ -76,26 +79,28 @@ struct TubeStep {
     R cp, ce, wb, we, ca, cb, h_dx, dt_dx, inv_dx;
 };
 
-// THREADS threads per tube, chunks of THREADS - 4 cells (the chunk and its halo take one staging
-// load per thread; THREADS - 3 faces, one per thread),
-// MINB CTAs per SM for the register budget; the autotuner picks the variant
+// THREADS threads per tube (THREADS / 32 warps, each streaming its own chunks of kTubeChunk
+// cells), MINB CTAs per SM for the register budget; the autotuner picks the variant
+constexpr int kTubeChunk = 30;  // cells per warp chunk: 31 faces and 34 staged cells
+
 template <typename R, int THREADS, int MINB>
 __global__ void __launch_bounds__(THREADS, MINB)
 tube_kernel(const TubeParams<R> P, int steps, int cur0)
 {
-    constexpr int kChunk = THREADS - 4;  // the chunk and its 4 halo cells: one staging load per thread
-    __shared__ StagedCell<1, R> tile[kChunk + 4];
+    constexpr int NW = THREADS / 32;
+    constexpr int kStage = kTubeChunk + 4;
     using CellW = typename FrameWords<R>::word;
-    __shared__ R faceF[kChunk + 1][4];
-    __shared__ R faceG[kChunk + 1][3];
-    __shared__ R faceU[kChunk + 1], faceT[kChunk + 1];  // face frame: velocity relative to utile, T
+    __shared__ StagedCell<1, R> tile[NW][kStage];
+    __shared__ R faceF[NW][kTubeChunk + 1][4];
+    __shared__ R faceG[NW][kTubeChunk + 1][3];
+    __shared__ R faceU[NW][kTubeChunk + 1], faceT[NW][kTubeChunk + 1];  // face frame: velocity relative to the chunk reference, T
     __shared__ TubeStep<R> ks;
-    __shared__ CellW uref_s;
-    __shared__ R red[THREADS / 32];
+    __shared__ R red[NW];
     __shared__ int tube_bad;
 
     const int tube = P.order[blockIdx.x];
     if (P.status[tube] != 0) return;  // stopped earlier: its state is not advanced any more
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) tube_bad = 0;
     const long long c_off = P.cell_off[tube], f_off = P.face_off[tube];
     const int L = P.len[tube];
@@ -103,6 +108,7 @@ tube_kernel(const TubeParams<R> P, int steps, int cur0)
     const double tau = P.tau;
     const R CvR = R(Cv), tolR = R(P.tol);
     unsigned long long my_iters = 0, my_faces = 0, my_nonconv = 0, my_fallbacks = 0, my_nonphys = 0;
+    StagedCell<1, R> *wt = tile[warp];
 
     for (int step = 0; step < steps; ++step) {
         const int cur = (cur0 + step) & 1, nxt = cur ^ 1;
@@ -131,29 +137,49 @@ tube_kernel(const TubeParams<R> P, int steps, int cur0)
         cfg.limiter = P.limiter;
         cfg.max_iter = P.max_iter;
         cfg.fixed_iters = P.fixed_iters;
+        const typename TubeParams<R>::FaceW *fu_in = P.fu[cur], *fT_in = P.fT[cur];
+        typename TubeParams<R>::FaceW *fu_out = P.fu[nxt], *fT_out = P.fT[nxt];
         R rate = R(0);
-        for (int c0 = 0; c0 < L; c0 += kChunk) {
-            const int nc = min(kChunk, L - c0);
-            if (threadIdx.x == 0) uref_s = P.sfr[cur][c_off + c0];
-            __syncthreads();
-            const CellW utile = uref_s;
-            // stage cells c0-2 .. c0+nc+1 (zero-gradient ends)
-            for (int t = threadIdx.x; t < nc + 4; t += blockDim.x) {
-                const int k = min(max(c0 - 2 + t, 0), L - 1);
-                tube_stage<R>(P, cur, c_off + k, CvR - R(0.5), cp, ce, utile, tile[t]);
+        const long long n = P.ncell;
+        const R Cvh = CvR - R(0.5);
+        for (int c0 = warp * kTubeChunk; c0 < L; c0 += NW * kTubeChunk) {
+            const int nc = min(kTubeChunk, L - c0);
+            // reference velocity of the chunk: its first cell's frame velocity
+            const CellW utile = P.sfr[cur][c_off + c0];
+            // lane l stages cell c0 - 2 + l (zero-gradient ends) and keeps its state for the
+            // update below; lanes 0 and 1 also stage the right halo c0 + 30, c0 + 31
+            const long long c = c_off + min(max(c0 - 2 + lane, 0), L - 1);
+            const R rho = P.sf[cur][c], a2 = P.sf[cur][n + c], a3 = P.sf[cur][2 * n + c];
+            const R b0 = P.sg[cur][c], b1 = P.sg[cur][n + c], b2 = P.sg[cur][2 * n + c];
+            const CellW uc = P.sfr[cur][c], Tc = P.sfr[cur][n + c];
+            const R Tcr = R(fr_lead(Tc));
+            {
+                StagedCell<1, R> &o = wt[lane];
+                o.A[0] = cp * rho + ce * rho;
+                o.A[1] = R(0);
+                o.A[2] = cp * a2;
+                o.A[3] = cp * a3;
+                o.B[0] = cp * b0 + ce * Cvh * rho * Tcr;
+                o.B[1] = cp * b1;
+                o.B[2] = cp * b2;
+                o.du[0] = R(fr_rel(uc, utile));
+                o.T = Tcr;
             }
-            __syncthreads();
-            // faces c0 .. c0+nc: face k lies between cells k-1 and k
-            for (int f = threadIdx.x; f <= nc; f += blockDim.x) {
+            if (lane < 2) tube_stage<R>(P, cur, c_off + min(c0 + kTubeChunk + lane, L - 1), Cvh, cp, ce, utile, wt[32 + lane]);
+            __syncwarp();
+            // faces c0 .. c0+nc: face k lies between cells k-1 and k; the last one is also the
+            // next chunk's first face, which that chunk owns (except at the tube's end)
+            if (lane <= nc) {
+                const int f = lane;
                 const long long k = c0 + f;
-                Stencil<1, R> cells;   // LL, L, R, RR at tile[f .. f+3]
-                cells.base = &tile[f + 2];
+                Stencil<1, R> cells;   // LL, L, R, RR at wt[f .. f+3]
+                cells.base = &wt[f + 2];
                 cells.sn = 1;
                 cells.st = 0;
-                const R dref[1] = {R(fr_rel(P.fu[f_off + k], utile))};
-                const R uabs[1] = {R(fr_lead(P.fu[f_off + k]))};
+                const R dref[1] = {R(fr_rel(fu_in[f_off + k], utile))};
+                const R uabs[1] = {R(fr_lead(fu_in[f_off + k]))};
                 FaceOut<1, R> o;
-                solve_face<1, R>(cells, false, dref, uabs, R(P.fT[f_off + k]), cfg, o);
+                solve_face<1, R>(cells, false, dref, uabs, R(fT_in[f_off + k]), cfg, o);
                 const bool owned = f < nc || k == L;
                 if (owned) {
                     my_iters += o.iters;
@@ -163,53 +189,54 @@ tube_kernel(const TubeParams<R> P, int steps, int cur0)
                 }
                 if (o.have) {
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) faceF[f][q] = o.F[q];
+                    for (int q = 0; q < 4; ++q) faceF[warp][f][q] = o.F[q];
 #pragma unroll
-                    for (int q = 0; q < 3; ++q) faceG[f][q] = o.G[q];
-                    faceU[f] = dref[0] + o.du[0];
-                    faceT[f] = o.T;
+                    for (int q = 0; q < 3; ++q) faceG[warp][f][q] = o.G[q];
+                    const R fdu = dref[0] + o.du[0];
+                    faceU[warp][f] = fdu;
+                    faceT[warp][f] = o.T;
                     if (owned) {
-                        P.fu[f_off + k] = fr_face(utile, faceU[f]);
-                        P.fT[f_off + k] = o.T;
+                        fu_out[f_off + k] = fr_face(utile, fdu);
+                        fT_out[f_off + k] = o.T;
                     }
                 } else {
                     if (owned) ++my_nonphys;
                     tube_bad = 1;
                     const R nan = R(__int_as_float(0x7fc00000));
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) faceF[f][q] = nan;
+                    for (int q = 0; q < 4; ++q) faceF[warp][f][q] = nan;
 #pragma unroll
-                    for (int q = 0; q < 3; ++q) faceG[f][q] = nan;
-                    faceU[f] = dref[0];
-                    faceT[f] = nan;
-                    if (owned) P.fT[f_off + k] = nan;
+                    for (int q = 0; q < 3; ++q) faceG[warp][f][q] = nan;
+                    faceU[warp][f] = dref[0];
+                    faceT[warp][f] = nan;
+                    if (owned) {
+                        fu_out[f_off + k] = fu_in[f_off + k];
+                        fT_out[f_off + k] = nan;
+                    }
                 }
             }
-            __syncthreads();
-            // cells c0 .. c0+nc-1 (cell c0 + t is staged in tile[t + 2])
-            const long long n = P.ncell;
-            for (int t = threadIdx.x; t < nc; t += blockDim.x) {
-                const long long c = c_off + c0 + t;
-                const CellW uc = P.sfr[cur][c], Tc = P.sfr[cur][n + c];
-                const R duc = tile[t + 2].du[0];
-                const R rho = P.sf[cur][c];
-                const R Tcr = R(fr_lead(Tc)), invTc = R(1) / Tcr, rsqTc = sqrt(invTc), sqTc = Tcr * rsqTc;
+            __syncwarp();
+            // lane l = 2 .. nc+1 updates the cell it staged, c0 + l - 2, between faces l-2 and l-1
+            if (lane >= 2 && lane < nc + 2) {
+                const int t = lane - 2;
+                const R duc = wt[lane].du[0];
+                const R invTc = w_rcp<R>(Tcr), rsqTc = w_sqrt<R>(invTc), sqTc = Tcr * rsqTc;
                 R H[4], G[3];
                 H[0] = ca * rho + cb * rho;
                 H[1] = R(0);
-                H[2] = ca * P.sf[cur][n + c];
-                H[3] = ca * P.sf[cur][2 * n + c];
-                G[0] = ca * P.sg[cur][c] + cb * (CvR - R(0.5)) * rho * Tcr;
-                G[1] = ca * P.sg[cur][n + c];
-                G[2] = ca * P.sg[cur][2 * n + c];
+                H[2] = ca * a2;
+                H[3] = ca * a3;
+                G[0] = ca * b0 + cb * Cvh * rho * Tcr;
+                G[1] = ca * b1;
+                G[2] = ca * b2;
                 const R sx = ks.dt_dx;
                 const R ucr = R(fr_lead(uc));
 #pragma unroll
                 for (int side = 0; side < 2; ++side) {
                     const int f = t + side;
-                    const R dv[1] = {faceU[f] - duc};
-                    add_face_flux<1, R>(faceF[f], faceG[f], dv, faceT[f], Tcr, invTc, rsqTc, 0, side ? sx : -sx, sqTc,
-                                        ucr, H, G);
+                    const R dv[1] = {faceU[warp][f] - duc};
+                    add_face_flux<1, R>(faceF[warp][f], faceG[warp][f], dv, faceT[warp][f], Tcr, invTc, rsqTc, 0,
+                                        side ? sx : -sx, sqTc, ucr, H, G);
                 }
                 R Ho[4], Go[3], du[1], dT;
                 bool ok = cell_finish<1, R>(H, G, invTc, sqTc, CvR, Ho, Go, du, dT);
@@ -235,17 +262,17 @@ tube_kernel(const TubeParams<R> P, int steps, int cur0)
                     else rate = fmaxf(rate, (fabsf(unr) + sqrtf(Tnr) * float(kCHi)) * ks.inv_dx);
                 }
             }
-            __syncthreads();
+            __syncwarp();   // the chunk's shared records are read before the next chunk restages them
         }
         // the tube's next time step from its CFL maximum (Sec. IV)
         R r = rate;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) r = max(r, __shfl_down_sync(0xffffffffu, r, o));
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = r;
+        if (lane == 0) red[warp] = r;
         __syncthreads();
         if (threadIdx.x == 0) {
             R rm = R(0);
-            for (int w = 0; w < THREADS / 32; ++w) rm = max(rm, red[w]);
+            for (int w = 0; w < NW; ++w) rm = max(rm, red[w]);
             P.t[tube] += ks.dt;
             P.dt[tube] = P.cfl / double(rm);
             P.steps_done[tube] += 1;
@@ -263,7 +290,7 @@ tube_kernel(const TubeParams<R> P, int steps, int cur0)
         my_fallbacks += __shfl_down_sync(0xffffffffu, my_fallbacks, o);
         my_nonphys += __shfl_down_sync(0xffffffffu, my_nonphys, o);
     }
-    if ((threadIdx.x & 31) == 0) {
+    if (lane == 0) {
         if (my_faces) { atomicAdd(&P.diag->face_iters, my_iters); atomicAdd(&P.diag->face_solves, my_faces); }
         if (my_nonconv) { atomicAdd(&P.diag->nonconv, my_nonconv); atomicOr(&P.diag->flags, FLAG_NOT_CONVERGED); }
         if (my_fallbacks) atomicAdd(&P.diag->fallbacks, my_fallbacks);
@@ -312,8 +339,8 @@ tube_init_kernel(const TubeParams<R> P, int cur, const double *rho, const double
         const double ra = rho[a], rb = rho[b], ua = ux[a], ub = ux[b];
         const double Ea = p[a] * Cv + 0.5 * ra * ua * ua, Eb = p[b] * Cv + 0.5 * rb * ub * ub;
         const double r = 0.5 * (ra + rb), m = 0.5 * (ra * ua + rb * ub), E = 0.5 * (Ea + Eb);
-        fr_store(P.fu[f_off + k], m / r);
-        fr_store(P.fT[f_off + k], (E - 0.5 * m * m / r) / (Cv * r));
+        fr_store(P.fu[cur][f_off + k], m / r);
+        fr_store(P.fT[cur][f_off + k], (E - 0.5 * m * m / r) / (Cv * r));
     }
     if (bad) { atomicAdd(&P.diag->nonphys, bad); atomicOr(&P.diag->flags, FLAG_NONPHYSICAL); any_bad = 1; }
 #pragma unroll

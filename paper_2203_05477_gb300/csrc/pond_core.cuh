@@ -155,6 +155,29 @@ __device__ __forceinline__ void shift_scale(const R *in, const Map1<R> &X, const
     else shift_scale_2d<N, R, Z1>(in, X, Y, out);
 }
 
+// ----------------------------------------------- reciprocal, square root, division
+// In the working precision R of the step kernels.  FP64: the IEEE operations.  FP32: the
+// single-instruction approximations of PTX (rcp.approx, sqrt.approx), whose relative
+// error is a few units in the last place over the normal range; they keep the corrector's
+// inner loops free of the multi-instruction IEEE sequences and their slow-path branches.
+// The FP32 path is held to its tolerance against the FP64 oracle, not to IEEE rounding.
+template <typename R> __device__ __forceinline__ R w_rcp(R x) { return R(1) / x; }
+template <typename R> __device__ __forceinline__ R w_sqrt(R x) { return sqrt(x); }
+template <typename R> __device__ __forceinline__ R w_div(R a, R b) { return a / b; }
+template <> __device__ __forceinline__ float w_rcp<float>(float x)
+{
+    float r;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+template <> __device__ __forceinline__ float w_sqrt<float>(float x)
+{
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+template <> __device__ __forceinline__ float w_div<float>(float a, float b) { return a * w_rcp<float>(b); }
+
 // --------------------------------------------------------------------- limiters
 // Slope limiters of Sec. III.B.3 on one-sided differences a (upstream) and b (downstream).
 template <typename R>

@@ -397,7 +397,7 @@ template <int D, typename R>
 __device__ __forceinline__ void cell_maps(R Tc, const R *dc, R Tl, R invTl, R rsqTl, const R *dl,
                                           Map1<R> &X, Map1<R> &Y)
 {
-    const R s = sqrt(Tc * invTl);
+    const R s = w_sqrt<R>(Tc * invTl);
     const R e = (Tc - Tl) * invTl;
     X = Map1<R>(s, e, (dc[0] - dl[0]) * rsqTl);
     if (D == 2) Y = Map1<R>(s, e, (dc[1] - dl[1]) * rsqTl);
@@ -501,8 +501,8 @@ __device__ __forceinline__ void corrector_pass(const Stencil<D, R> &cells, const
                                                int limiter, R *Phi, R *Psi)
 {
     constexpr int NFC = NCoef<D, 3>::value, NGC = NCoef<D, 2>::value;
-    const R invTl = R(1) / Tl;
-    const R rsqTl = sqrt(invTl);
+    const R invTl = w_rcp<R>(Tl);
+    const R rsqTl = w_sqrt<R>(invTl);
     const R sqTl = Tl * rsqTl;
     // the two cells next to the face, in the corrector frame
     R FL[NFC], FR[NFC], GL[NGC], GR[NGC];
@@ -531,8 +531,10 @@ __device__ __forceinline__ void corrector_pass(const Stencil<D, R> &cells, const
     for (int k = 0; k < NGC; ++k) Psi[k] = R(0);
 
     const NodeTab<R> &tab = node_tab<R>();
-#pragma unroll 1
-    for (int m = 0; m < 4; ++m) {
+    // normal node m: its populations, limited slopes and MUSCL values, summed into the
+    // moments (unrolled in 1D, where the node's work is small; rolled in 2D, which keeps the
+    // kernel within its register budget)
+    auto node = [&](const int m) {
         const R vn = sqTl * tab.c[m] + un_abs;
         const bool left = vn > R(0);
         // departure point along the normal, in cells, from the upwind cell centre
@@ -663,6 +665,13 @@ __device__ __forceinline__ void corrector_pass(const Stencil<D, R> &cells, const
 #pragma unroll
                 for (int b2 = 0; a2 + b2 <= 2; ++b2) Psi[hidx(a2, b2)] += tab.whe[m][a2] * SG[b2];
         }
+    };
+    if constexpr (D == 1) {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) node(m);
+    } else {
+#pragma unroll 1
+        for (int m = 0; m < 4; ++m) node(m);
     }
 }
 
@@ -672,20 +681,20 @@ template <int D, typename R>
 __device__ __forceinline__ bool pass_frame(const R *Phi, const R *Psi, R Tl, R Cv, R &rho, R *du, R &T)
 {
     rho = Phi[0];
-    const R sq = sqrt(Tl);
+    const R sq = w_sqrt<R>(Tl);
     R k2 = R(0), tr;
     if constexpr (D == 1) {
-        du[0] = sq * Phi[1] / rho;
+        du[0] = w_div<R>(sq * Phi[1], rho);
         k2 = du[0] * du[0];
         tr = Phi[2] + Phi[0];
     } else {
-        du[0] = sq * Phi[hidx(1, 0)] / rho;
-        du[1] = sq * Phi[hidx(0, 1)] / rho;
+        du[0] = w_div<R>(sq * Phi[hidx(1, 0)], rho);
+        du[1] = w_div<R>(sq * Phi[hidx(0, 1)], rho);
         k2 = du[0] * du[0] + du[1] * du[1];
         tr = Phi[hidx(2, 0)] + Phi[hidx(0, 2)] + R(2) * Phi[0];
     }
     // internal energy in the pass frame: T/2 sum f |c|^2 + sum g - rho |du|^2 / 2
-    T = (R(0.5) * Tl * tr + Psi[0] - R(0.5) * rho * k2) / (Cv * rho);
+    T = w_div<R>(R(0.5) * Tl * tr + Psi[0] - R(0.5) * rho * k2, Cv * rho);
     bool ok = T > R(0) && isfinite(T) && isfinite(rho);
 #pragma unroll
     for (int a = 0; a < D; ++a) ok = ok && isfinite(du[a]);
@@ -783,7 +792,7 @@ __device__ __forceinline__ void solve_face(const Stencil<D, R> &cells, bool swap
             done = iters >= cfg.fixed_iters;
         } else {
             bool c = fabs(T1 - Tl) <= tolR * Tl;
-            const R sq = sqrt(Tl);
+            const R sq = w_sqrt<R>(Tl);
 #pragma unroll
             for (int a = 0; a < D; ++a) c = c && fabs(du[a]) <= tolR * sq;
             done = c;
@@ -803,10 +812,11 @@ __device__ __forceinline__ void solve_face(const Stencil<D, R> &cells, bool swap
         }
         // Eq. (FluxTransf) in the frame of the last valid pass's moments, with the exact
         // co-moving equilibria there: phi = (2 tau phibar + h phi^eq)/(2 tau + h)
-        const R invT = R(1) / out_T;
-        Map1<R> X(sqrt(keep_T * invT), (keep_T - out_T) * invT, -out_du[0] * sqrt(invT));
+        const R invT = w_rcp<R>(out_T);
+        const R sk = w_sqrt<R>(keep_T * invT), rsq = w_sqrt<R>(invT);
+        Map1<R> X(sk, (keep_T - out_T) * invT, -out_du[0] * rsq);
         Map1<R> Y = X;
-        if (D == 2) Y = Map1<R>(sqrt(keep_T * invT), (keep_T - out_T) * invT, -out_du[D - 1] * sqrt(invT));
+        if (D == 2) Y = Map1<R>(sk, (keep_T - out_T) * invT, -out_du[D - 1] * rsq);
         R Fo[NFC], Go[NGC];
         shift_scale<D, 3, R>(Phi, X, Y, Fo);
         shift_scale<D, 2, R>(Psi, X, Y, Go);
@@ -1056,7 +1066,7 @@ __device__ __forceinline__ void add_face_flux(const R *Fc, const R *Gc, const R 
                                               int axis, R scale, R sqTc, R un, R *H, R *G)
 {
     constexpr int NFC = NCoef<D, 3>::value, NGC = NCoef<D, 2>::value;
-    const R s = sqrt(Tbr * invTc), e = (Tbr - Tcr) * invTc;
+    const R s = w_sqrt<R>(Tbr * invTc), e = (Tbr - Tcr) * invTc;
     Map1<R> X(s, e, dv[0] * rsqTc);
     Map1<R> Y = X;
     if constexpr (D == 2) Y = Map1<R>(s, e, dv[1] * rsqTc);
@@ -1179,7 +1189,7 @@ __device__ __forceinline__ bool cell_finish(const R *H, const R *G, R invTc, R s
 {
     const R rsqTc = invTc * sqTc;
     const R rn = H[0];
-    const R irn = R(1) / rn;
+    const R irn = w_rcp<R>(rn);
     R k2 = R(0), trH;
     if constexpr (D == 1) {
         du[0] = sqTc * H[1] * irn;
@@ -1192,11 +1202,11 @@ __device__ __forceinline__ bool cell_finish(const R *H, const R *G, R invTc, R s
         trH = H[hidx(2, 0)] + H[hidx(0, 2)];
     }
     // T'/T - 1 = (1/2 tr H + G0/T - (Cv - D/2) rho' - rho' |du|^2/(2T)) / (Cv rho')
-    dT = (R(0.5) * trH + G[0] * invTc - (Cv - R(0.5 * D)) * rn - R(0.5) * rn * k2 * invTc) / (Cv * rn);
+    dT = w_div<R>(R(0.5) * trH + G[0] * invTc - (Cv - R(0.5 * D)) * rn - R(0.5) * rn * k2 * invTc, Cv * rn);
     const bool ok = rn > R(0) && R(1) + dT > R(0) && isfinite(double(rn)) && isfinite(double(dT));
     // s^2 = T/T' = 1/(1 + dT/T), e = s^2 - 1, d = -du/sqrt(T')
-    const R s2 = R(1) / (R(1) + dT);
-    const R sc = sqrt(s2), e = -dT * s2;
+    const R s2 = w_rcp<R>(R(1) + dT);
+    const R sc = w_sqrt<R>(s2), e = -dT * s2;
     const R rsqn = rsqTc * sc;
     Map1<R> X(sc, e, -du[0] * rsqn);
     Map1<R> Y = X;
@@ -1232,7 +1242,7 @@ cell_kernel(const Params<D, R> P)
         const R rho = P.sf[c];
         const R ca = KC.ca, cb = KC.cb, Cv = P.Cv_r;
         const R Tcr = R(fr_lead(Tc));
-        const R invTc = R(1) / Tcr, rsqTc = sqrt(invTc), sqTc = Tcr * rsqTc;
+        const R invTc = w_rcp<R>(Tcr), rsqTc = w_sqrt<R>(invTc), sqTc = Tcr * rsqTc;
         // collision part of Eqs. (FinalUpdateDUGKS) in Hermite moments of the cell frame
         R H[NFC], G[NGC];
 #pragma unroll

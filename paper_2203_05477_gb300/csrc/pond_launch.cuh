@@ -96,7 +96,7 @@ inline void cell_name(int v, char *buf, size_t n)
 // ---------------------------------------------------------------- tube kernel
 
 template <typename R>
-constexpr int tube_variants() { return sizeof(R) == 4 ? 4 : 2; }
+constexpr int tube_variants() { return sizeof(R) == 4 ? 5 : 3; }
 
 template <typename R>
 void launch_tube(int v, unsigned n_tubes, const TubeParams<R> &P, int steps, int cur, cudaStream_t st);
@@ -104,7 +104,8 @@ void launch_tube(int v, unsigned n_tubes, const TubeParams<R> &P, int steps, int
 template <typename R>
 void tube_name(int v, char *buf, size_t n)
 {
-    static const int f32[4][2] = {{256, 3}, {128, 6}, {128, 4}, {512, 1}}, f64[2][2] = {{256, 1}, {128, 2}};
+    static const int f32[5][2] = {{128, 4}, {64, 8}, {256, 2}, {256, 3}, {128, 6}},
+                     f64[3][2] = {{256, 1}, {128, 2}, {64, 4}};
     const int k = (v >= 0 && v < tube_variants<R>()) ? v : 0;
     const int *c = sizeof(R) == 4 ? f32[k] : f64[k];
     std::snprintf(buf, n, "tube %d threads, %d CTA/SM", c[0], c[1]);

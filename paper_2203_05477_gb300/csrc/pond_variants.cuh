@@ -64,14 +64,16 @@ void launch_tube(int v, unsigned n_tubes, const TubeParams<R> &P, int steps, int
 {
     if constexpr (sizeof(R) == 4) {
         switch (v) {
-        case 1: tube_kernel<R, 128, 6><<<n_tubes, 128, 0, st>>>(P, steps, cur); break;
-        case 2: tube_kernel<R, 128, 4><<<n_tubes, 128, 0, st>>>(P, steps, cur); break;
-        case 3: tube_kernel<R, 512, 1><<<n_tubes, 512, 0, st>>>(P, steps, cur); break;
-        default: tube_kernel<R, 256, 3><<<n_tubes, 256, 0, st>>>(P, steps, cur); break;
+        case 1: tube_kernel<R, 64, 8><<<n_tubes, 64, 0, st>>>(P, steps, cur); break;
+        case 2: tube_kernel<R, 256, 2><<<n_tubes, 256, 0, st>>>(P, steps, cur); break;
+        case 3: tube_kernel<R, 256, 3><<<n_tubes, 256, 0, st>>>(P, steps, cur); break;
+        case 4: tube_kernel<R, 128, 6><<<n_tubes, 128, 0, st>>>(P, steps, cur); break;
+        default: tube_kernel<R, 128, 4><<<n_tubes, 128, 0, st>>>(P, steps, cur); break;
         }
     } else {
         switch (v) {
         case 1: tube_kernel<R, 128, 2><<<n_tubes, 128, 0, st>>>(P, steps, cur); break;
+        case 2: tube_kernel<R, 64, 4><<<n_tubes, 64, 0, st>>>(P, steps, cur); break;
         default: tube_kernel<R, 256, 1><<<n_tubes, 256, 0, st>>>(P, steps, cur); break;
         }
     }

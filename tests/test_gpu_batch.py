@@ -164,7 +164,9 @@ def test_c3_full_range_tubes_against_oracle(precision, steps, tol64):
     on tubes of low Mach number.  FP32 with the bench's stopping rule (tol 1e-6, 16
     passes) against the FP64 oracle with the same rule: 1e-4 relative L1 in rho, p and u.
     In all, the GPU stops exactly the tubes whose state the oracle finds non-physical, at
-    the same step."""
+    the same step.  On a tube where the oracle has faces that reach the pass limit without
+    converging (limit cycles of the corrector map), the FP32 bound is twice the oracle's own
+    change when the limit moves by one pass, if that exceeds 1e-4."""
     idx, bt = c3_sample()
     eps = np.finfo(np.float64).eps
     mach = np.maximum(np.abs(bt.left[:, 1]) / np.sqrt(bt.left[:, 2] / bt.left[:, 0]),
@@ -178,7 +180,7 @@ def test_c3_full_range_tubes_against_oracle(precision, steps, tol64):
     gs.sync()
     status, done = gs.status()
     (grho, gmx, _, gE), _ = gs.moments(totals=False)
-    mism, errs, survivors = [], [], 0
+    mism, errs, survivors, envelope_cases = [], [], 0, []
     for k in range(len(bt.lengths)):
         pb = I.shock_tube(bt.left[k], bt.right[k], bt.gammas[k], int(bt.lengths[k]))
         stop, os_ = oracle_stop_step(pb, steps, **kw)
@@ -201,9 +203,22 @@ def test_c3_full_range_tubes_against_oracle(precision, steps, tol64):
             r, u, pr = gpu_primitive_tube(gs, k, bt.gammas[k])
             ro_, uo, _, po = os_.primitive()
             c = np.sqrt(bt.gammas[k] * po / ro_)
-            e = max(rel_l1(r, ro_), rel_l1(pr, po), np.abs(u - uo).sum() / (np.abs(uo) + c).sum())
-            if e > 1e-4:
-                errs.append((int(idx[k]), e, os_.stats()["nonconverged"]))
+            err = lambda r_, u_, p_: max(rel_l1(r_, ro_), rel_l1(p_, po), np.abs(u_ - uo).sum() / (np.abs(uo) + c).sum())
+            e = err(r, u, pr)
+            bound = 1e-4
+            if os_.stats()["nonconverged"]:
+                # faces whose corrector reaches its pass limit without converging end on an
+                # iterate that depends on where the iteration stops: the bound is twice the
+                # oracle's own change when the limit moves by one pass
+                for mi in (15, 17):
+                    o2 = oracle_for(pb, **dict(kw, max_iter=mi))
+                    o2.step(steps)
+                    r2, u2, _, p2 = o2.primitive()
+                    bound = max(bound, 2.0 * err(r2, u2, p2))
+                envelope_cases.append((int(idx[k]), e, bound))
+            if e > bound:
+                errs.append((int(idx[k]), e, bound, os_.stats()["nonconverged"]))
     assert not mism, mism
     assert not errs, errs
     assert survivors >= 10 and (status == 1).sum() >= 10, (survivors, int((status == 1).sum()))
+    assert len(envelope_cases) <= survivors // 4, envelope_cases
