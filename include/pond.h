@@ -245,6 +245,16 @@ pond_status pond_gauge_enable(pond_state *s, int on);
 pond_status pond_gauge_set_gate(pond_state *s, float gate);
 pond_status pond_gauge_set_trust(pond_state *s, float trust);
 
+/* The equilibration alternative of Sec. II.C, as an ablation of Grad's projection (the
+ * paper's choice, and the default): with on nonzero, every change of frame of the
+ * following steps keeps the slow moments (third order for f, second for g) and sets the
+ * fast tensor-Hermite components He_r(c_x) He_s(c_y) (r, s <= 3 beyond those orders) to
+ * the values of the equilibrium with the population's own zeroth and first moments in the
+ * new frame.  One kernel tile is compiled for it, so pond_autotune has nothing to choose.
+ * Errors: UNSUPPORTED on batches, D3Q64 grids, the semi-Lagrangian scheme, or with the
+ * learned predictor on. */
+pond_status pond_set_equilibration(pond_state *s, int on);
+
 /* The network as a self-describing byte blob (magic, version, count, parameters) for
  * checkpointing: pond_gauge_save writes it to buf (host) if *size is large enough and
  * always sets *size to the bytes needed; pond_gauge_load reads one back. */
@@ -300,7 +310,10 @@ pond_status pond_wait_timeout_check(int64_t polls, void *stream);
    several variants: tile shapes and CTAs per SM of the face corrector, block sizes of the
    cell update, thread counts of the persistent tube kernel.  pond_autotune times every
    variant on this state's own current data (steps timed steps each, after one untimed
-   step) and keeps the fastest face and cell (or tube) variant for the following steps.
+   step) and keeps the fastest face and cell (or tube) variant for the following steps;
+   on a grid it then times whole steps of those face and cell kernels against each fused
+   step variant and keeps the fastest in `tube` (as pond_set_variants reads it).  ms holds
+   per-launch times of the face and cell variants and per-step times of the step choices.
    The state is copied aside first (one extra device allocation of the state's size, freed
    before returning) and restored afterwards, so tuning leaves the solution unchanged.
    cache_path (may be NULL) names a text file of "key<TAB>face cell tube" lines; a line
@@ -308,7 +321,7 @@ pond_status pond_wait_timeout_check(int64_t polls, void *stream);
    matches this state is used without timing, and a new choice is appended.  File errors
    only disable the cache.  Call it outside stream capture.  Errors: INVALID_ARG
    (steps < 1), OOM, CUDA. */
-#define POND_TUNE_MAX 16
+#define POND_TUNE_MAX 32
 typedef struct {
     int n;                    /* entries of ms filled (0 when taken from the cache) */
     int face, cell, tube;     /* chosen variant indices */
@@ -318,13 +331,18 @@ typedef struct {
 pond_status pond_autotune(pond_state *s, int steps, const char *cache_path, pond_tune_result *out);
 
 /* Number of variants of this state and the name of variant i: for a grid, the face
-   variants first, then the cell variants; for a batch, the tube variants.  The name points
-   to a thread-local buffer ("" when i is out of range). */
+   variants first, then the cell variants, then the whole-step choices (the separate face
+   and cell kernels, then each tile variant of the fused step kernel, which solves a tile's
+   faces and updates its cells in one kernel); for a batch, the tube variants.  The name
+   points to a thread-local buffer ("" when i is out of range). */
 int pond_variant_count(const pond_state *s);
 const char *pond_variant_name(const pond_state *s, int i);
 
-/* Selects variants by index (face, cell for a grid; tube for a batch; the others are
-   ignored).  Errors: INVALID_ARG for an index out of range. */
+/* Selects variants by index: for a grid face, cell and, in `tube`, the whole step (0: the
+   face and cell kernels; k > 0: fused step variant k - 1, used for the plain steps -- the
+   learned predictor, pair collection and the equilibration ablation run the face and cell
+   kernels); for a batch tube (the others are ignored).  Errors: INVALID_ARG for an index
+   out of range. */
 pond_status pond_set_variants(pond_state *s, int face, int cell, int tube);
 
 /* Waits for the stream and reports the device diagnostics.  Returns

@@ -64,7 +64,7 @@ class pond_diag(ctypes.Structure):
                 ("flags", ctypes.c_uint32)]
 
 
-POND_TUNE_MAX = 16
+POND_TUNE_MAX = 32
 
 
 class pond_tune_result(ctypes.Structure):
@@ -117,6 +117,7 @@ def _load():
             "pond_gauge_collect": (ctypes.c_int, [vp, ctypes.c_int64, vp, ctypes.c_int64, ctypes.c_int, vp]),
             "pond_gauge_train": (ctypes.c_int, [vp, vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_float, vp]),
             "pond_gauge_enable": (ctypes.c_int, [vp, ctypes.c_int]),
+            "pond_set_equilibration": (ctypes.c_int, [vp, ctypes.c_int]),
             "pond_wait_timeout_check": (ctypes.c_int, [ctypes.c_int64, vp]),
             "pond_gauge_set_gate": (ctypes.c_int, [vp, ctypes.c_float]),
             "pond_gauge_set_trust": (ctypes.c_int, [vp, ctypes.c_float]),
@@ -330,6 +331,10 @@ class Solver:
 
     def set_variants(self, face=0, cell=0, tube=0):
         _check(self.lib.pond_set_variants(self.h, int(face), int(cell), int(tube)))
+
+    def set_equilibration(self, on=True):
+        """The equilibration alternative of Sec. II.C instead of Grad's projection (ablation)."""
+        _check(self.lib.pond_set_equilibration(self.h, int(bool(on))))
 
     # ---- learned face-gauge predictor (D2Q16)
     def gauge_collect(self, n_steps, cap, every=4):

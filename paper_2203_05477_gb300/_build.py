@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libpond.so")
 OBJ = os.path.join(HERE, "_build")
 SOURCES = ["pond_api.cu", "pond_v2f.cu", "pond_v2f_learned.cu", "pond_v2d.cu", "pond_v1.cu", "pond_vtube.cu",
-           "pond_v3f.cu", "pond_v3d.cu"]
+           "pond_v3f.cu", "pond_v3d.cu", "pond_veq.cu", "pond_vfused.cu"]
 HEADERS = ["pond_core.cuh", "pond_kernels.cuh", "pond_batch.cuh", "pond_launch.cuh", "pond_variants.cuh",
            "pond_tc.cuh", "pond_mlp.cuh", "pond_mlp_train.cuh", "pond_reduce.cuh", "pond_sl.cuh", "pond_sl2.cuh",
            "pond3.cuh", "pond3_launch.cuh", "pond_v3_impl.cuh"]

@@ -104,11 +104,13 @@ struct pond_state {
     char *train_scratch = nullptr;
     int64_t train_rows = 0;
     bool learned = false;
+    bool equilibrate = false;     // the equilibration alternative of Sec. II.C (an ablation)
     int adam_t = 0;
     int sms = 152;
-    // kernel variants in use (indices into the lists of pond_launch.cuh), set by the autotuner
+    // kernel variants in use (indices into the lists of pond_launch.cuh), set by the autotuner;
+    // on grids tube_v selects the step: 0 the face and cell kernels, k + 1 fused variant k
     int face_v = 0, cell_v = 0, tube_v = 0;
-    // semi-Lagrangian scheme: the state alternates between the cell planes and the face
+    // semi-Lagrangian scheme and fused steps: the state alternates between two sets of
     // planes; sl_parity counts the swaps, graph_parity is the parity a captured graph starts at
     int scheme = POND_FV;
     int sl_parity = 0, graph_parity = 0;
@@ -177,6 +179,12 @@ pond_status setup(pond_state *s)
         o_yf = take(sizeof(R) * NFC * nyf); o_yg = take(sizeof(R) * NGC * nyf); o_yfr = take(sizeof(W) * (D + 1) * nyf);
         o_xlr = take(sizeof(W) * (D + 1) * nxf); o_ylr = take(sizeof(W) * (D + 1) * nyf);  // learned predictions
     }
+    size_t o_pact = 0;
+    if (D == 2) o_pact = take(sizeof(unsigned int) * 2 * size_t(pond::pred_tiles(P)));
+    // the fused step's second state and face-frame buffers
+    const size_t o_sf2 = take(sizeof(R) * NFS * n), o_sg2 = take(sizeof(R) * NGC * n), o_sfr2 = take(sizeof(W) * (D + 1) * n);
+    const size_t o_xfr2 = take(sizeof(W) * (D + 1) * nxf);
+    const size_t o_yfr2 = D == 2 ? take(sizeof(W) * (D + 1) * nyf) : 0;
     const size_t o_clock = take(sizeof(pond::Clock)), o_diag = take(sizeof(pond::Diag));
     size_t stage = 4 * size_t(n);
     stage = std::max<size_t>(stage, size_t(NFC + NGC + D + 1) * size_t(n));
@@ -197,8 +205,14 @@ pond_status setup(pond_state *s)
         P.yg = reinterpret_cast<R *>(s->base + o_yg);
         P.yfr = reinterpret_cast<W *>(s->base + o_yfr);
         P.xlr = reinterpret_cast<W *>(s->base + o_xlr);
+        P.pred_active = reinterpret_cast<unsigned int *>(s->base + o_pact);
         P.ylr = reinterpret_cast<W *>(s->base + o_ylr);
     }
+    P.sf_n = reinterpret_cast<R *>(s->base + o_sf2);
+    P.sg_n = reinterpret_cast<R *>(s->base + o_sg2);
+    P.sfr_n = reinterpret_cast<W *>(s->base + o_sfr2);
+    P.xfr_n = reinterpret_cast<W *>(s->base + o_xfr2);
+    P.yfr_n = D == 2 ? reinterpret_cast<W *>(s->base + o_yfr2) : nullptr;
     P.clock = reinterpret_cast<pond::Clock *>(s->base + o_clock);
     P.diag = reinterpret_cast<pond::Diag *>(s->base + o_diag);
     s->clock = P.clock;
@@ -346,12 +360,40 @@ void launch_sl(pond_state *s, pond::Params<D, R> &P)
     s->sl_parity ^= 1;
 }
 
+// one fused step (face and cell work of a tile in one kernel): it writes the other set of
+// state and face-frame planes, which then become the state (swapped on the host copy of the
+// parameters, so a captured graph holds both orders alternately)
+template <int D, typename R>
+void launch_fused(pond_state *s, pond::Params<D, R> &P)
+{
+    pond::launch_step_fused<D, R>(s->tube_v - 1, P, s->stream);
+    std::swap(P.sf, P.sf_n);
+    std::swap(P.sg, P.sg_n);
+    std::swap(P.sfr, P.sfr_n);
+    std::swap(P.xfr, P.xfr_n);
+    if constexpr (D == 2) std::swap(P.yfr, P.yfr_n);
+    s->sl_parity ^= 1;
+}
+
+// the step runs fused: the tuner (or pond_set_variants) chose a fused variant and the step
+// is the plain one (the learned predictor, pair collection and the equilibration ablation
+// run the face and cell kernels)
+template <int D, typename R>
+bool fused_step(const pond_state *s, bool collect)
+{
+    return s->tube_v > 0 && !s->learned && !collect && !s->equilibrate && s->scheme == POND_FV;
+}
+
 template <int D, typename R>
 void launch_step(pond_state *s, bool collect = false)
 {
     auto &P = params_of<D, R>(s);
     if (s->scheme == POND_SL) {
         launch_sl<D, R>(s, P);
+        return;
+    }
+    if (fused_step<D, R>(s, collect)) {
+        launch_fused<D, R>(s, P);
         return;
     }
     if constexpr (D == 2) {
@@ -361,7 +403,7 @@ void launch_step(pond_state *s, bool collect = false)
         }
     }
     pond::launch_face<D, R>(s->face_v, D == 2 && collect, P, s->stream);
-    pond::launch_cell<D, R>(s->cell_v, P, s->stream);
+    pond::launch_cell_any<D, R>(s->cell_v, P, s->stream);
 }
 
 // Releases the captured step graph (it is captured again on the next long step).
@@ -390,7 +432,7 @@ template <int D, typename R>
 pond_status step_impl(pond_state *s, int64_t n_steps)
 {
     int64_t left = n_steps;
-    if (left >= kGraphSteps && s->graph_exec && s->scheme == POND_SL && s->graph_parity != s->sl_parity) {
+    if (left >= kGraphSteps && s->graph_exec && s->graph_parity != s->sl_parity) {
         // the graph was captured starting from the other buffer
         drop_graph(s);
     }
@@ -405,7 +447,7 @@ pond_status step_impl(pond_state *s, int64_t n_steps)
             CUDA_TRY(cudaStreamEndCapture(s->stream, &g));
             if (pond_status st = keep_graph(s, g)) return st;
         }
-        const int per_step = s->scheme == POND_SL ? 1 : 2 + ((D == 2 && s->learned) ? 1 : 0);
+        const int per_step = (s->scheme == POND_SL || fused_step<D, R>(s, false)) ? 1 : 2 + ((D == 2 && s->learned) ? 1 : 0);
         while (left >= kGraphSteps) {
             CUDA_TRY(cudaGraphLaunch(s->graph_exec, s->stream));
             s->launches += per_step * kGraphSteps;
@@ -415,7 +457,7 @@ pond_status step_impl(pond_state *s, int64_t n_steps)
     for (; left > 0; --left) {
         const int64_t before = s->launches;
         launch_step<D, R>(s);
-        s->launches = before + (s->scheme == POND_SL ? 1 : 2 + ((D == 2 && s->learned) ? 1 : 0));
+        s->launches = before + ((s->scheme == POND_SL || fused_step<D, R>(s, false)) ? 1 : 2 + ((D == 2 && s->learned) ? 1 : 0));
     }
     CUDA_TRY(cudaGetLastError());
     return POND_OK;
@@ -435,16 +477,17 @@ pond_status step_timed_impl(pond_state *s, int64_t n_steps, double *ms)
                 s->launches += 1;
             }
         }
-        if (s->scheme == POND_SL) {
-            // the whole semi-Lagrangian step is one kernel: it is timed as the first part
-            launch_sl<D, R>(s, P);
+        if (s->scheme == POND_SL || fused_step<D, R>(s, false)) {
+            // the whole step is one kernel (semi-Lagrangian or fused): it is timed as the first part
+            if (s->scheme == POND_SL) launch_sl<D, R>(s, P);
+            else launch_fused<D, R>(s, P);
             CUDA_TRY(cudaEventRecord(ev[2 * k + 1], s->stream));
             CUDA_TRY(cudaEventRecord(ev[2 * k + 2], s->stream));
             s->launches -= 1;
         } else {
             pond::launch_face<D, R>(s->face_v, false, P, s->stream);
             CUDA_TRY(cudaEventRecord(ev[2 * k + 1], s->stream));
-            pond::launch_cell<D, R>(s->cell_v, P, s->stream);
+            pond::launch_cell_any<D, R>(s->cell_v, P, s->stream);
             CUDA_TRY(cudaEventRecord(ev[2 * k + 2], s->stream));
         }
     }
@@ -1490,6 +1533,7 @@ pond_status pond_gauge_train(pond_state *s, const float *pairs, int64_t n, int e
 pond_status pond_gauge_enable(pond_state *s, int on)
 {
     if (pond_status st = check_gauge(s)) return st;
+    if (on && s->equilibrate) return fail(POND_ERR_UNSUPPORTED, "the learned predictor runs with Grad's projection only");
     if (bool(on) != s->learned) {
         // the captured step graph depends on the set of kernels
         drop_graph(s);
@@ -1497,6 +1541,25 @@ pond_status pond_gauge_enable(pond_state *s, int on)
     s->learned = on != 0;
     if (s->prec == POND_FP32) params_of<2, float>(s).use_learned = s->learned;
     else params_of<2, double>(s).use_learned = s->learned;
+    return POND_OK;
+}
+
+pond_status pond_set_equilibration(pond_state *s, int on)
+{
+    if (pond_status st = check_state(s)) return st;
+    if (s->batch || s->D == 3 || s->scheme == POND_SL || s->learned)
+        return fail(POND_ERR_UNSUPPORTED, "the equilibration alternative runs on finite-volume D1Q4 and D2Q16 grids "
+                                          "without the learned predictor");
+    if (bool(on) != s->equilibrate) drop_graph(s);   // the captured graph depends on the kernels
+    s->equilibrate = on != 0;
+    const int eq = s->equilibrate ? 1 : 0;
+    if (s->D == 1) {
+        if (s->prec == POND_FP32) params_of<1, float>(s).equilibrate = eq;
+        else params_of<1, double>(s).equilibrate = eq;
+    } else {
+        if (s->prec == POND_FP32) params_of<2, float>(s).equilibrate = eq;
+        else params_of<2, double>(s).equilibrate = eq;
+    }
     return POND_OK;
 }
 
@@ -1757,14 +1820,24 @@ void cache_store(const char *path, const std::string &key, const int v[3])
     std::fclose(f);
 }
 
+int grid_face_variants(const pond_state *s)
+{
+    if (s->D == 2) return s->prec == POND_FP32 ? pond::face_variants<2, float>() : pond::face_variants<2, double>();
+    return s->prec == POND_FP32 ? pond::face_variants<1, float>() : pond::face_variants<1, double>();
+}
+
+// the whole-step choices of a grid: the separate face and cell kernels, then each fused variant
+int grid_step_variants(const pond_state *s)
+{
+    if (s->D == 2) return 1 + (s->prec == POND_FP32 ? pond::step_variants<2, float>() : pond::step_variants<2, double>());
+    return 1 + (s->prec == POND_FP32 ? pond::step_variants<1, float>() : pond::step_variants<1, double>());
+}
+
 int variant_total(const pond_state *s)
 {
     if (s->scheme == POND_SL || s->D == 3) return 0;
     if (s->batch) return s->prec == POND_FP32 ? pond::tube_variants<float>() : pond::tube_variants<double>();
-    int nf = 0;
-    if (s->D == 2) nf = s->prec == POND_FP32 ? pond::face_variants<2, float>() : pond::face_variants<2, double>();
-    else nf = s->prec == POND_FP32 ? pond::face_variants<1, float>() : pond::face_variants<1, double>();
-    return nf + pond::kCellVariants;
+    return grid_face_variants(s) + pond::kCellVariants + grid_step_variants(s);
 }
 
 // mean ms per launch of the face (which = 0) or cell (which = 1) kernel over `steps` steps
@@ -1786,7 +1859,7 @@ pond_status time_grid_variant(pond_state *s, const char *saved, int steps, int w
         pond::launch_face<D, R>(s->face_v, false, P, s->stream);
         if (which == 0) CUDA_TRY(cudaEventRecord(ev[2 * k + 1], s->stream));
         if (which == 1) CUDA_TRY(cudaEventRecord(ev[2 * k], s->stream));
-        pond::launch_cell<D, R>(s->cell_v, P, s->stream);
+        pond::launch_cell_any<D, R>(s->cell_v, P, s->stream);
         if (which == 1) CUDA_TRY(cudaEventRecord(ev[2 * k + 1], s->stream));
     }
     s->launches += int64_t(steps + 1) * (2 + ((D == 2 && s->learned) ? 1 : 0));
@@ -1802,9 +1875,39 @@ pond_status time_grid_variant(pond_state *s, const char *saved, int steps, int w
     return POND_OK;
 }
 
+// mean ms per whole step (face and cell kernels, or one fused kernel) over `steps` steps after
+// one untimed step, starting from the saved block and the saved buffer assignment
+template <int D, typename R>
+pond_status time_grid_step(pond_state *s, const char *saved, const pond::Params<D, R> &P0, int parity0, int steps,
+                           double *ms)
+{
+    auto &P = params_of<D, R>(s);
+    CUDA_TRY(cudaMemcpyAsync(s->base, saved, s->bytes, cudaMemcpyDeviceToDevice, s->stream));
+    P = P0;
+    s->sl_parity = parity0;
+    launch_step<D, R>(s);
+    Events ev(2);
+    CUDA_TRY(ev.create());
+    CUDA_TRY(cudaEventRecord(ev[0], s->stream));
+    for (int k = 0; k < steps; ++k) launch_step<D, R>(s);
+    CUDA_TRY(cudaEventRecord(ev[1], s->stream));
+    s->launches += int64_t(steps + 1) * (fused_step<D, R>(s, false) ? 1 : 2);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaEventSynchronize(ev[1]));
+    float a = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&a, ev[0], ev[1]));
+    *ms = double(a) / steps;
+    P = P0;
+    s->sl_parity = parity0;
+    return POND_OK;
+}
+
 template <int D, typename R>
 pond_status tune_grid(pond_state *s, const char *saved, int steps, pond_tune_result *res)
 {
+    const pond::Params<D, R> P0 = params_of<D, R>(s);
+    const int parity0 = s->sl_parity;
+    s->tube_v = 0;   // face and cell variants are timed as separate kernels
     const int nf = pond::face_variants<D, R>();
     double best = 0.0;
     int bf = 0;
@@ -1825,6 +1928,21 @@ pond_status tune_grid(pond_state *s, const char *saved, int steps, pond_tune_res
         if (v == 0 || ms < best) { best = ms; bc = v; }
     }
     s->cell_v = bc;
+    // whole steps: the chosen face and cell kernels against every fused variant
+    int bs = 0;
+    if (s->scheme == POND_FV && !s->learned && !s->equilibrate) {
+        double best_step = 0.0;
+        for (int v = 0; v <= pond::step_variants<D, R>(); ++v) {
+            s->tube_v = v;
+            double ms = 0.0;
+            if (pond_status st = time_grid_step<D, R>(s, saved, P0, parity0, steps, &ms)) return st;
+            if (res && res->n < POND_TUNE_MAX) res->ms[res->n++] = ms;
+            if (v == 0 || ms < best_step) { best_step = ms; bs = v; }
+        }
+    }
+    s->tube_v = bs;
+    params_of<D, R>(s) = P0;
+    s->sl_parity = parity0;
     return POND_OK;
 }
 
@@ -1864,7 +1982,7 @@ pond_status pond_autotune(pond_state *s, int steps, const char *cache_path, pond
     if (pond_status st = check_state(s)) return st;
     if (steps < 1) return fail(POND_ERR_INVALID_ARG, "steps must be at least 1");
     pond_tune_result res{};
-    if (s->scheme == POND_SL || s->D == 3) {  // one compiled variant: nothing to choose
+    if (s->scheme == POND_SL || s->D == 3 || s->equilibrate) {  // one compiled variant: nothing to choose
         if (out) *out = res;
         return POND_OK;
     }
@@ -1913,8 +2031,15 @@ const char *pond_variant_name(const pond_state *s, int i)
         else pond::tube_name<double>(i, buf, sizeof(buf));
         return buf;
     }
-    const int nf = variant_total(s) - pond::kCellVariants;
-    if (i >= nf) {
+    const int nf = grid_face_variants(s);
+    if (i >= nf + pond::kCellVariants) {
+        const int k = i - nf - pond::kCellVariants;
+        if (k == 0) std::snprintf(buf, sizeof(buf), "step face and cell kernels");
+        else if (s->D == 2 && f32) pond::StepNames<2, float, pond::StepList<2, float>::type>::name(k - 1, buf, sizeof(buf));
+        else if (s->D == 2) pond::StepNames<2, double, pond::StepList<2, double>::type>::name(k - 1, buf, sizeof(buf));
+        else if (f32) pond::StepNames<1, float, pond::StepList<1, float>::type>::name(k - 1, buf, sizeof(buf));
+        else pond::StepNames<1, double, pond::StepList<1, double>::type>::name(k - 1, buf, sizeof(buf));
+    } else if (i >= nf) {
         pond::cell_name(i - nf, buf, sizeof(buf));
     } else if (s->D == 2) {
         if (f32) pond::FaceNames<2, float, pond::FaceList<2, float>::type>::name(i, buf, sizeof(buf));
@@ -1934,11 +2059,14 @@ pond_status pond_set_variants(pond_state *s, int face, int cell, int tube)
         if (tube < 0 || tube >= nv) return fail(POND_ERR_INVALID_ARG, "tube variant %d out of range", tube);
         s->tube_v = tube;
     } else {
-        const int nf = variant_total(s) - pond::kCellVariants;
+        const int nf = grid_face_variants(s);
         if (face < 0 || face >= nf || cell < 0 || cell >= pond::kCellVariants)
             return fail(POND_ERR_INVALID_ARG, "face/cell variant (%d, %d) out of range", face, cell);
+        if (tube < 0 || tube >= grid_step_variants(s) || (tube > 0 && s->scheme != POND_FV))
+            return fail(POND_ERR_INVALID_ARG, "step variant %d out of range", tube);
         s->face_v = face;
         s->cell_v = cell;
+        s->tube_v = tube;
     }
     drop_graph(s);
     return POND_OK;

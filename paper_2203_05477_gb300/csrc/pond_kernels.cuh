@@ -176,7 +176,16 @@ struct Params {
     R *yf, *yg;
     W *yfr;
     W *xlr, *ylr;                     // learned predictions per face [D+1][nf] (T not finite: none)
+    // the fused step writes the new state and face frames here (the host then swaps them
+    // with sf, sg, sfr, xfr, yfr)
+    R *sf_n, *sg_n;
+    W *sfr_n, *xfr_n, *yfr_n;
     int use_learned;                  // the face corrector tries the learned prediction first
+    // activity of the learned predictor's tiles (16 x 4 faces of each axis): [2][tiles], the
+    // step s + 1 stamped into row (s + 1) & 1 where a face of the tile needed more than one
+    // corrector pass, or started from a prediction, in step s
+    unsigned int *pred_active;
+    int equilibrate;                  // the equilibration alternative of Sec. II.C (an ablation)
     Clock *clock;
     Diag *diag;
     // learned face-gauge predictor: parameters, and sampling of training pairs
@@ -450,6 +459,8 @@ __device__ __forceinline__ float2 limit2(int kind, float2 a, float2 b)
 // column-collapsed coefficients (C: f, order <= 3; D: g, order <= 2), the limited MUSCL
 // reconstruction at the departure point, and the moments S (f) and SG (g) along the
 // tangent.  Lane x carries f and lane y carries g wherever both have the order.
+// EQ: g also carries its third column (the fast components), evaluated in lane y.
+template <bool EQ = false>
 __device__ __forceinline__ void pair_populations(const float *Cu, const float *Cl, const float *Ch, const float *Cm,
                                                  const float *Cp, const float *Du, const float *Dl, const float *Dh,
                                                  const float *Dm, const float *Dp, float sqTl, float ut_abs, float h_dt,
@@ -473,7 +484,16 @@ __device__ __forceinline__ void pair_populations(const float *Cu, const float *C
             p2 = __ffma2_rn(make_float2(Cp[b2], Dp[b2]), hn, p2);
         }
         const float h3 = float(hen(3, n));
-        u2.x += Cu[3] * h3; l2.x += Cl[3] * h3; h2.x += Ch[3] * h3; m2.x += Cm[3] * h3; p2.x += Cp[3] * h3;
+        if constexpr (EQ) {
+            const float2 h3b = bc2(h3);
+            u2 = __ffma2_rn(make_float2(Cu[3], Du[3]), h3b, u2);
+            l2 = __ffma2_rn(make_float2(Cl[3], Dl[3]), h3b, l2);
+            h2 = __ffma2_rn(make_float2(Ch[3], Dh[3]), h3b, h2);
+            m2 = __ffma2_rn(make_float2(Cm[3], Dm[3]), h3b, m2);
+            p2 = __ffma2_rn(make_float2(Cp[3], Dp[3]), h3b, p2);
+        } else {
+            u2.x += Cu[3] * h3; l2.x += Cl[3] * h3; h2.x += Ch[3] * h3; m2.x += Cm[3] * h3; p2.x += Cp[3] * h3;
+        }
         const float2 ln = limit2(limiter, __ffma2_rn(l2, minus1, u2), __ffma2_rn(u2, minus1, h2));
         const float2 lt = limit2(limiter, __ffma2_rn(m2, minus1, u2), __ffma2_rn(u2, minus1, p2));
         const float2 b = __ffma2_rn(bc2(offt), lt, __ffma2_rn(bc2(offn), ln, u2));
@@ -489,13 +509,51 @@ __device__ __forceinline__ void pair_populations(const float *Cu, const float *C
     S[3] = S3;
 }
 
+// ---- the equilibration alternative of Sec. II.C (an ablation of Grad's projection)
+// A population set moved into another frame keeps its slow moments (the Grad orders) and
+// takes for its fast tensor-Hermite components A_rs (r, s <= 3, r + s above the Grad
+// order) the values of the equilibrium with its own zeroth and first moments there:
+// A_rs = A_00 d_x^r d_y^s with d = A_1 / A_00 (the first-order coefficients in the new frame;
+// the Hermite moments of a Maxwellian of the frame's temperature shifted by d).  These
+// helpers give the fast components the corrector and the flux need from the slow ones.
+template <typename R>
+struct FastEq {
+    R a0, dx, dy;   // A_00 and d in the frame of the coefficients
+    __device__ __forceinline__ R at(int r, int s) const
+    {
+        R v = a0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) if (k < r) v *= dx;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) if (k < s) v *= dy;
+        return v;
+    }
+};
+template <int D, int N, typename R>
+__device__ __forceinline__ FastEq<R> fast_eq(const R *A)
+{
+    FastEq<R> q;
+    q.a0 = A[0];
+    const R ia0 = w_rcp<R>(A[0]);
+    if constexpr (D == 1) {
+        q.dx = A[1] * ia0;
+        q.dy = R(0);
+    } else {
+        q.dx = A[hidx(1, 0)] * ia0;
+        q.dy = A[hidx(0, 1)] * ia0;
+    }
+    return q;
+}
+
 // One corrector pass at a face (Sec. III.B.3) in frame (dl, Tl) (velocity relative to the
 // face reference uref): every stencil cell's phi-bar-plus is re-expressed in that frame,
 // limited slopes are formed per population, each population is reconstructed by MUSCL
 // at its departure point x_b - v_i dt/2 in the upwind cell, and the Hermite moments of
 // the reconstructed f-bar and g-bar are returned (Phi: f, order 3; Psi: g, order 2).
 // Stencil slots: 0 LL, 1 L, 2 R, 3 RR, 4 L-t, 5 L+t, 6 R-t, 7 R+t (t: tangential).
-template <int D, typename R>
+// EQ: the stencil cells are moved into the frame by the equilibration alternative
+// (FastEq), so their populations also carry the fast components.
+template <int D, typename R, bool EQ = false>
 __device__ __forceinline__ void corrector_pass(const Stencil<D, R> &cells, const R *dref,
                                                const R *dl, R Tl, R un_abs, R ut_abs, R h_dn, R h_dt,
                                                int limiter, R *Phi, R *Psi)
@@ -542,6 +600,7 @@ __device__ __forceinline__ void corrector_pass(const Stencil<D, R> &cells, const
         if constexpr (D == 1) {
             // outer normal neighbour of the upwind cell, in the frame
             R FS[NFC], GS[NGC];
+            R gL3 = R(0), gR3 = R(0), gS3 = R(0);   // fast g components at node m (EQ)
             {
                 // slot 0 or 3, chosen by selects so that no array is indexed at run time
                 const StagedCell<D, R> sc = fetch<D, R>(left ? cells[0] : cells[3]);
@@ -552,9 +611,16 @@ __device__ __forceinline__ void corrector_pass(const Stencil<D, R> &cells, const
                 shift_scale<D, 3, R, true>(sc.A, X, Y, FS);
                 shift_scale<D, 2, R>(sc.B, X, Y, GS);
             }
+            if constexpr (EQ) {
+                // D1Q4 carries one fast component: g's third order
+                const R h3 = tab.hen[m][3];
+                gL3 = fast_eq<1, 2, R>(GL).at(3, 0) * h3;
+                gR3 = fast_eq<1, 2, R>(GR).at(3, 0) * h3;
+                gS3 = fast_eq<1, 2, R>(GS).at(3, 0) * h3;
+            }
             // populations at node m (unweighted: the limiter is homogeneous of degree one,
             // so the weight w_m factors out) of L, R and the outer neighbour
-            R fL = R(0), fR = R(0), fS = R(0), gL = R(0), gR = R(0), gS = R(0);
+            R fL = R(0), fR = R(0), fS = R(0), gL = gL3, gR = gR3, gS = gS3;
 #pragma unroll
             for (int a = 0; a <= 3; ++a) {
                 const R hn = tab.hen[m][a];
@@ -589,11 +655,29 @@ __device__ __forceinline__ void corrector_pass(const Stencil<D, R> &cells, const
                     C[b2] = acc;
                 }
             };
-            R CL[4], CR[4], DL[3], DR[3];
+            // EQ: the fast components' part of the column collapse, f (r + s > 3) and g (> 2)
+            auto collapse_fast = [&](const R *A, int order, R *C) {
+                const FastEq<R> q = fast_eq<2, 3, R>(A);
+#pragma unroll
+                for (int b2 = 0; b2 <= 3; ++b2) {
+                    R acc = R(0);
+#pragma unroll
+                    for (int a2 = 0; a2 <= 3; ++a2)
+                        if (a2 + b2 > order) acc += q.at(a2, b2) * tab.hen[m][a2];
+                    if (b2 <= order) C[b2] += acc;
+                    else C[b2] = acc;
+                }
+            };
+            constexpr int NGB = EQ ? 4 : 3;   // columns of the g collapse
+            R CL[4], CR[4], DL[NGB], DR[NGB];
             collapse_f(FL, CL); collapse_f(FR, CR); collapse_g(GL, DL); collapse_g(GR, DR);
+            if constexpr (EQ) {
+                collapse_fast(FL, 3, CL); collapse_fast(FR, 3, CR);
+                collapse_fast(GL, 2, DL); collapse_fast(GR, 2, DR);
+            }
             // outer normal neighbour (q = 0) and tangential neighbours (q = 1, 2) of the
             // upwind cell: transformed into the frame and collapsed one at a time
-            R CS[3][4], DS[3][3];
+            R CS[3][4], DS[3][NGB];
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
                 // slot (left, right upwind): q = 0 (0, 3), q = 1 (4, 6), q = 2 (5, 7); chosen by
@@ -611,8 +695,12 @@ __device__ __forceinline__ void corrector_pass(const Stencil<D, R> &cells, const
                 shift_scale<D, 2, R>(tmpg, X, Y, trg);
                 collapse_f(tr, CS[q]);
                 collapse_g(trg, DS[q]);
+                if constexpr (EQ) {
+                    collapse_fast(tr, 3, CS[q]);
+                    collapse_fast(trg, 2, DS[q]);
+                }
             }
-            R Cu[4], Cl[4], Ch[4], Du[3], Dl[3], Dh[3];
+            R Cu[4], Cl[4], Ch[4], Du[NGB], Dl[NGB], Dh[NGB];
 #pragma unroll
             for (int b2 = 0; b2 <= 3; ++b2) {
                 Cu[b2] = left ? CL[b2] : CR[b2];
@@ -620,7 +708,7 @@ __device__ __forceinline__ void corrector_pass(const Stencil<D, R> &cells, const
                 Ch[b2] = left ? CR[b2] : CS[0][b2];
             }
 #pragma unroll
-            for (int b2 = 0; b2 <= 2; ++b2) {
+            for (int b2 = 0; b2 < NGB; ++b2) {
                 Du[b2] = left ? DL[b2] : DR[b2];
                 Dl[b2] = left ? DS[0][b2] : DL[b2];
                 Dh[b2] = left ? DR[b2] : DS[0][b2];
@@ -629,8 +717,8 @@ __device__ __forceinline__ void corrector_pass(const Stencil<D, R> &cells, const
             if constexpr (sizeof(R) == 4) {
                 // FP32: the f and g populations run side by side as FP32x2 pairs (lane x: f,
                 // lane y: g), so the shared orders 0..2 take one packed FMA for both
-                pair_populations(Cu, Cl, Ch, CS[1], CS[2], Du, Dl, Dh, DS[1], DS[2], sqTl, ut_abs, h_dt, offn, limiter,
-                                 S, SG);
+                pair_populations<EQ>(Cu, Cl, Ch, CS[1], CS[2], Du, Dl, Dh, DS[1], DS[2], sqTl, ut_abs, h_dt, offn,
+                                     limiter, S, SG);
             } else {
 #pragma unroll
             for (int n = 0; n < 4; ++n) {
@@ -644,7 +732,7 @@ __device__ __forceinline__ void corrector_pass(const Stencil<D, R> &cells, const
                 }
                 R gu = R(0), gl = R(0), gh = R(0), gm = R(0), gp = R(0);
 #pragma unroll
-                for (int b2 = 0; b2 <= 2; ++b2) {
+                for (int b2 = 0; b2 < NGB; ++b2) {
                     const R hn = R(hen(b2, n));
                     gu += Du[b2] * hn; gl += Dl[b2] * hn; gh += Dh[b2] * hn; gm += DS[1][b2] * hn; gp += DS[2][b2] * hn;
                 }
@@ -728,7 +816,7 @@ struct FaceOut {
 // no frame restarts the corrector once from the frame of the pooled moments of the
 // stencil, else the corrector stops at the last pass that did.  The face populations are
 // Eq. (FluxTransf) at the frame of the last valid pass's moments.
-template <int D, typename R>
+template <int D, typename R, bool EQ = false>
 __device__ __forceinline__ void solve_face(const Stencil<D, R> &cells, bool swap, const R *dref, const R *uabs,
                                            R Tpred, const FaceCfg<R> &cfg, FaceOut<D, R> &o)
 {
@@ -750,7 +838,7 @@ __device__ __forceinline__ void solve_face(const Stencil<D, R> &cells, bool swap
     int iters = 0;
     R Phi[NFC], Psi[NGC];
     for (int k = 0; k < cfg.max_iter && !done; ++k) {
-        corrector_pass<D, R>(cells, dref, dl, Tl, uref_n + dl[0], D == 2 ? uref_t + dl[D - 1] : R(0),
+        corrector_pass<D, R, EQ>(cells, dref, dl, Tl, uref_n + dl[0], D == 2 ? uref_t + dl[D - 1] : R(0),
                              h_dn, h_dt, cfg.limiter, Phi, Psi);
         R rho1, du[D], T1;
         const bool ok = pass_frame<D, R>(Phi, Psi, Tl, Cv, rho1, du, T1);
@@ -807,7 +895,7 @@ __device__ __forceinline__ void solve_face(const Stencil<D, R> &cells, bool swap
     if (have) {
         if (!last_valid) {
             // the last pass defined no frame: recompute the last valid one
-            corrector_pass<D, R>(cells, dref, keep_dl, keep_T, uref_n + keep_dl[0],
+            corrector_pass<D, R, EQ>(cells, dref, keep_dl, keep_T, uref_n + keep_dl[0],
                                  D == 2 ? uref_t + keep_dl[D - 1] : R(0), h_dn, h_dt, cfg.limiter, Phi, Psi);
         }
         // Eq. (FluxTransf) in the frame of the last valid pass's moments, with the exact
@@ -835,6 +923,14 @@ __device__ __forceinline__ void solve_face(const Stencil<D, R> &cells, bool swap
     }
 }
 
+// Tiles of the learned predictor: 16 x 4 faces of each axis (the 128 rows of one MLP tile)
+constexpr int kPredTileX = 16, kPredTileY = 4;
+template <int D, typename R>
+__host__ __device__ __forceinline__ long long pred_tiles(const Params<D, R> &P)
+{
+    return ((P.nx + 1 + kPredTileX - 1) / kPredTileX) * ((P.ny + 1 + kPredTileY - 1) / kPredTileY);
+}
+
 // Tile variants of the face kernel: TX x TY cells per CTA (one thread per x face and one
 // per y face in 2D, one per face in 1D) and MINB CTAs per SM for the register budget.  The
 // autotuner picks one per problem.
@@ -846,14 +942,16 @@ struct FaceVariant {
 
 // Instantiations (MODE): FACE_PLAIN; FACE_COLLECT also writes (features, converged frame)
 // pairs of sampled converged faces for the learned predictor; FACE_LEARNED starts each face
-// from the learned prediction when there is one.  Separate instantiations, so the plain
-// kernel carries neither (and keeps its register budget).
-enum { FACE_PLAIN = 0, FACE_COLLECT = 1, FACE_LEARNED = 2 };
+// from the learned prediction when there is one; FACE_EQUIL moves the stencil cells into
+// the corrector frame by the equilibration alternative of Sec. II.C (an ablation).
+// Separate instantiations, so the plain kernel carries none of them (and keeps its
+// register budget).
+enum { FACE_PLAIN = 0, FACE_COLLECT = 1, FACE_LEARNED = 2, FACE_EQUIL = 3 };
 template <int D, typename R, int MODE, typename V>
 __global__ void __launch_bounds__(V::THREADS, V::MINB)
 face_kernel(const Params<D, R> P)
 {
-    constexpr bool COLLECT = MODE == FACE_COLLECT, LEARNED = MODE == FACE_LEARNED;
+    constexpr bool COLLECT = MODE == FACE_COLLECT, LEARNED = MODE == FACE_LEARNED, EQUIL = MODE == FACE_EQUIL;
     constexpr int TX = V::TX, TY = V::TY;
     constexpr int BX = TX + 3, BY = D == 2 ? TY + 3 : 1;
     constexpr int NFC = NCoef<D, 3>::value, NGC = NCoef<D, 2>::value;
@@ -956,8 +1054,13 @@ face_kernel(const Params<D, R> P)
         for (int a = 0; a < D; ++a) base[a] = uref[a];
         bool learned_first = false;
         W lrn[D + 1];
+        long long ptile = 0;
         if constexpr (D == 2 && LEARNED) {
-            if (P.use_learned) {
+            // the predictor's tile of this face and whether the predictor ran there
+            const long long pnbx = (P.nx + 1 + kPredTileX - 1) / kPredTileX;
+            ptile = (fj / kPredTileY) * pnbx + fi / kPredTileX;
+            const unsigned int step = (unsigned int)K.steps;
+            if (P.use_learned && P.pred_active[(step & 1u) * pred_tiles(P) + ptile] == step) {
                 const W *Lrm = dir == 0 ? P.xlr : P.ylr;
 #pragma unroll
                 for (int a = 0; a <= D; ++a) lrn[a] = Lrm[a * nf + fidx];
@@ -980,7 +1083,7 @@ face_kernel(const Params<D, R> P)
                 }
                 Tw = R(fr_lead(lrn[D]));
             }
-            solve_face<D, R>(cells, swap, dw, uw, Tw, cfg, o);
+            solve_face<D, R, EQUIL>(cells, swap, dw, uw, Tw, cfg, o);
             tot_iters += o.iters;
             tot_fallbacks += o.fallbacks;
             if (from_learned && o.have && o.done && o.fallbacks == 0) {
@@ -990,6 +1093,12 @@ face_kernel(const Params<D, R> P)
             }
         }
         my_iters = tot_iters; my_nonconv = o.done ? 0 : 1; my_fallbacks = tot_fallbacks;
+        if constexpr (D == 2 && LEARNED) {
+            if (P.use_learned && (tot_iters > 1 || learned_first)) {
+                const unsigned int next = (unsigned int)K.steps + 1u;
+                P.pred_active[(next & 1u) * pred_tiles(P) + ptile] = next;
+            }
+        }
         if constexpr (COLLECT && D == 2) {
             const unsigned long long hsh = (unsigned long long)(fidx * 2 + dir + 1) * 0x9E3779B97F4A7C15ull ^
                                            (unsigned long long)(K.steps + 1) * 0xBF58476D1CE4E5B9ull;
@@ -1061,7 +1170,7 @@ face_kernel(const Params<D, R> P)
 // using c He_r(c) = He_{r+1}(c) + r He_{r-1}(c); He_4 vanishes on the D1Q4 nodes and the
 // Grad forms have no moments above their order, so the product closes on the same orders.
 // invTc, rsqTc: 1/T and 1/sqrt(T) of the cell frame.
-template <int D, typename R>
+template <int D, typename R, bool EQ = false>
 __device__ __forceinline__ void add_face_flux(const R *Fc, const R *Gc, const R *dv, R Tbr, R Tcr, R invTc, R rsqTc,
                                               int axis, R scale, R sqTc, R un, R *H, R *G)
 {
@@ -1073,6 +1182,14 @@ __device__ __forceinline__ void add_face_flux(const R *Fc, const R *Gc, const R 
     R Fp[NFC], Gp[NGC];
     shift_scale<D, 3, R>(Fc, X, Y, Fp);
     shift_scale<D, 2, R>(Gc, X, Y, Gp);
+    // EQ: the face populations moved into the cell frame by the equilibration alternative
+    // carry fast components; the product with v_n lowers one order of them into the slow
+    // orders (c He_r = He_{r+1} + r He_{r-1})
+    FastEq<R> qf{}, qg{};
+    if constexpr (EQ) {
+        qf = fast_eq<D, 3, R>(Fp);
+        qg = fast_eq<D, 2, R>(Gp);
+    }
     if constexpr (D == 1) {
 #pragma unroll
         for (int r = 0; r <= 3; ++r) {
@@ -1085,6 +1202,7 @@ __device__ __forceinline__ void add_face_flux(const R *Fc, const R *Gc, const R 
         for (int r = 0; r <= 2; ++r) {
             R v = un * Gp[r];
             if (r + 1 <= 2) v += sqTc * Gp[r + 1];
+            else if (EQ) v += sqTc * qg.at(r + 1, 0);
             if (r >= 1) v += sqTc * R(r) * Gp[r - 1];
             G[r] -= scale * v;
         }
@@ -1097,9 +1215,11 @@ __device__ __forceinline__ void add_face_flux(const R *Fc, const R *Gc, const R 
                 R v = un * Fp[k];
                 if (axis == 0) {
                     if (r + q + 1 <= 3) v += sqTc * Fp[hidx(r + 1, q)];
+                    else if (EQ && r + 1 <= 3) v += sqTc * qf.at(r + 1, q);
                     if (r >= 1) v += sqTc * R(r) * Fp[hidx(r - 1, q)];
                 } else {
                     if (r + q + 1 <= 3) v += sqTc * Fp[hidx(r, q + 1)];
+                    else if (EQ && q + 1 <= 3) v += sqTc * qf.at(r, q + 1);
                     if (q >= 1) v += sqTc * R(q) * Fp[hidx(r, q - 1)];
                 }
                 H[k] -= scale * v;
@@ -1112,9 +1232,11 @@ __device__ __forceinline__ void add_face_flux(const R *Fc, const R *Gc, const R 
                 R v = un * Gp[k];
                 if (axis == 0) {
                     if (r + q + 1 <= 2) v += sqTc * Gp[hidx(r + 1, q)];
+                    else if (EQ) v += sqTc * qg.at(r + 1, q);
                     if (r >= 1) v += sqTc * R(r) * Gp[hidx(r - 1, q)];
                 } else {
                     if (r + q + 1 <= 2) v += sqTc * Gp[hidx(r, q + 1)];
+                    else if (EQ) v += sqTc * qg.at(r, q + 1);
                     if (q >= 1) v += sqTc * R(q) * Gp[hidx(r, q - 1)];
                 }
                 G[k] -= scale * v;
@@ -1221,7 +1343,8 @@ __device__ __forceinline__ bool cell_finish(const R *H, const R *G, R invTc, R s
 // frame from the conserved moments) and the CFL reduction.  The frame (u, T) advances by
 // increments formed from the Hermite moments relative to the old frame (u' = u + du,
 // T' = T (1 + dT/T)), so no kinetic energy of the frame enters.
-template <int D, typename R, int THREADS, int MINB = 1>
+// EQ: the face populations enter the cell frame by the equilibration alternative (Sec. II.C).
+template <int D, typename R, int THREADS, int MINB = 1, bool EQ = false>
 __global__ void __launch_bounds__(THREADS, MINB)
 cell_kernel(const Params<D, R> P)
 {
@@ -1268,7 +1391,7 @@ cell_kernel(const Params<D, R> P)
 #pragma unroll
             for (int a = 0; a < D; ++a) dv[a] = R(fr_rel(P.xfr[a * nxf + f], uc[a]));
             const R Tb = R(fr_lead(P.xfr[D * nxf + f]));
-            add_face_flux<D, R>(Fc, Gc, dv, Tb, Tcr, invTc, rsqTc, 0, side ? sx : -sx, sqTc, R(fr_lead(uc[0])), H, G);
+            add_face_flux<D, R, EQ>(Fc, Gc, dv, Tb, Tcr, invTc, rsqTc, 0, side ? sx : -sx, sqTc, R(fr_lead(uc[0])), H, G);
         }
         if constexpr (D == 2) {
             const long long nyf = P.nyf();
@@ -1284,7 +1407,7 @@ cell_kernel(const Params<D, R> P)
 #pragma unroll
                 for (int a = 0; a < D; ++a) dv[a] = R(fr_rel(P.yfr[a * nyf + f], uc[a]));
                 const R Tb = R(fr_lead(P.yfr[D * nyf + f]));
-                add_face_flux<D, R>(Fc, Gc, dv, Tb, Tcr, invTc, rsqTc, 1, side ? sy : -sy, sqTc, R(fr_lead(uc[1])), H, G);
+                add_face_flux<D, R, EQ>(Fc, Gc, dv, Tb, Tcr, invTc, rsqTc, 1, side ? sy : -sy, sqTc, R(fr_lead(uc[1])), H, G);
             }
         }
         R Ho[NFC], Go[NGC], du[D], dT;
@@ -1315,6 +1438,257 @@ cell_kernel(const Params<D, R> P)
         for (int a = 0; a < D; ++a) P.sfr[a * n + c] = un[a];
         P.sfr[D * n + c] = Tn;
         rate = ok ? cell_rate<R>(unr, Tnr, KC.inv_dx, KC.inv_dy, D) : 0.0;
+    }
+    reduce_rate_and_advance(P.clock, rate, true);
+}
+
+// ------------------------------------------------------------ fused step
+
+// Tile variants of the fused step: TX x TY cells per CTA, whose faces (TX+1) x TY along x
+// and TX x (TY+1) along y are all solved in the CTA (the faces on the tile's far edges are
+// also solved by the neighbouring tile), one thread per face; MINB CTAs per SM.
+template <int D, int TX_, int TY_, int MINB_>
+struct StepVariant {
+    static constexpr int TX = TX_, TY = D == 2 ? TY_ : 1, MINB = MINB_;
+    static constexpr int NXF = (TX + 1) * TY, NYF = D == 2 ? TX * (TY + 1) : 0, NF = NXF + NYF;
+    static constexpr int THREADS = ((NF + 31) / 32) * 32;
+};
+
+// the faces' populations (coefficients in the face frame, x, y order) and frames in shared
+// memory, one array per component (NF faces each), so that neighbouring threads touch
+// neighbouring words
+template <int D, typename R, int NF>
+struct FaceRecs {
+    R F[NCoef<D, 3>::value][NF];
+    R G[NCoef<D, 2>::value][NF];
+    typename FrameWords<R>::word fr[D + 1][NF];
+};
+
+// One whole step (Sec. III.B.4) of a tile in one kernel: the CTA stages phi-bar-plus of the
+// box [i0-2, i0+TX+1] x [j0-2, j0+TY+1] (steps 1 and 2a), solves every face of its cells by
+// the predictor-corrector (step 2b) into shared memory, and updates its cells from those
+// faces (step 3, with step 1 of the next step and the CFL rate, as cell_kernel).  The state
+// and the face frames are read from sf, sg, sfr, xfr, yfr and written to their *_n copies,
+// so no CTA sees another's new values; faces on a tile's far edges are solved twice (by
+// both tiles) and written by their owner only.  Face populations never reach global memory.
+template <int D, typename R, typename V>
+__global__ void __launch_bounds__(V::THREADS, V::MINB)
+step_kernel(const Params<D, R> P)
+{
+    constexpr int TX = V::TX, TY = V::TY;
+    constexpr int BX = TX + 4, BY = D == 2 ? TY + 4 : 1;
+    constexpr int NFC = NCoef<D, 3>::value, NGC = NCoef<D, 2>::value;
+    using W = typename FrameWords<R>::word;
+    __shared__ StagedCell<D, R> tile[BY * BX];
+    __shared__ StagedCell<D, R> tileT[D == 2 ? BY * BX : 1];
+    __shared__ FaceRecs<D, R, V::NF> frec;
+    __shared__ W utile[D];
+
+    const Clock &K = *P.clock;
+    if (!(K.dt > 0.0)) return;  // t_end reached: the step is a no-op
+    const StepC<R> &KC = step_c<R>(K);
+    const R cp = KC.cp, ce = KC.ce;
+    const long long i0 = (long long)blockIdx.x * TX, j0 = (long long)blockIdx.y * TY;
+    if (threadIdx.x == 0) cell_velocity<D, R>(P, i0, j0, utile);
+    __syncthreads();
+    for (int t = threadIdx.x; t < BX * BY; t += blockDim.x) {
+        const int bx = t % BX, by = t / BX;
+        const long long ci = i0 - 2 + bx, cj = D == 2 ? j0 - 2 + by : 0;
+        if constexpr (D == 2) {
+            StagedCell<D, R> c;
+            load_cell_bar_plus<D, R>(P, ci, cj, cp, ce, utile, c);
+            tile[t] = c;
+            StagedCell<D, R> ct;
+            orient<D, 3, R>(c.A, ct.A, true);
+            orient<D, 2, R>(c.B, ct.B, true);
+            ct.du[0] = c.du[1];
+            ct.du[1] = c.du[0];
+            ct.T = c.T;
+            tileT[bx * BY + by] = ct;
+        } else {
+            load_cell_bar_plus<D, R>(P, ci, cj, cp, ce, utile, tile[t]);
+        }
+    }
+    __syncthreads();
+
+    // ---- the faces of the tile's cells
+    static_assert(V::THREADS >= V::NF && V::THREADS >= TX * TY, "one face and at most one cell per thread");
+    unsigned long long my_iters = 0, my_faces = 0, my_nonconv = 0, my_fallbacks = 0, my_nonphys = 0;
+    const int f = threadIdx.x;
+    if (f < V::NF) do {
+        const int dir = f >= V::NXF ? 1 : 0;
+        int tx, ty;
+        if (dir == 0) { tx = f % (TX + 1); ty = f / (TX + 1); }
+        else { tx = (f - V::NXF) % TX; ty = (f - V::NXF) / TX; }
+        const long long fi = i0 + tx, fj = j0 + ty;
+        bool active, owned;
+        long long fidx;
+        if (dir == 0) {
+            active = fi <= P.nx && fj < P.ny;
+            owned = tx < TX || fi == P.nx;
+            fidx = fj * (P.nx + 1) + fi;
+        } else {
+            active = fi < P.nx && fj <= P.ny;
+            owned = ty < TY || fj == P.ny;
+            fidx = fj * P.nx + fi;
+        }
+        if (!active) break;
+        const bool swap = dir == 1;
+        Stencil<D, R> cells;
+        if (swap) {
+            cells.base = &tileT[int(fi - i0 + 2) * BY + int(fj - j0 + 2)];
+            cells.sn = 1;
+            cells.st = BY;
+        } else {
+            cells.base = &tile[(D == 2 ? int(fj - j0 + 2) * BX : 0) + int(fi - i0 + 2)];
+            cells.sn = 1;
+            cells.st = D == 2 ? BX : 0;
+        }
+        const W *Frm = dir == 0 ? P.xfr : P.yfr;
+        W *Frm_n = dir == 0 ? P.xfr_n : P.yfr_n;
+        const long long nf = dir == 0 ? P.nxf() : P.nyf();
+        W uref[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) uref[a] = Frm[a * nf + fidx];
+        FaceCfg<R> cfg;
+        cfg.h_dn = swap ? KC.h_dy : KC.h_dx;
+        cfg.h_dt = D == 2 ? (swap ? KC.h_dx : KC.h_dy) : R(0);
+        cfg.Cv = P.Cv_r; cfg.tol = P.tol_r; cfg.wb = KC.wb; cfg.we = KC.we;
+        cfg.limiter = P.limiter; cfg.max_iter = P.max_iter; cfg.fixed_iters = P.fixed_iters;
+        const R Tp = R(fr_lead(Frm[D * nf + fidx]));
+        const int na = swap ? 1 : 0, ta = 1 - na;
+        R dref[D], uabs[D];
+        dref[0] = R(fr_rel(uref[na], utile[na]));
+        uabs[0] = R(fr_lead(uref[na]));
+        if constexpr (D == 2) {
+            dref[1] = R(fr_rel(uref[ta], utile[ta]));
+            uabs[1] = R(fr_lead(uref[ta]));
+        }
+        FaceOut<D, R> o;
+        solve_face<D, R>(cells, swap, dref, uabs, Tp, cfg, o);
+        if (owned) {
+            my_iters += o.iters;
+            my_faces += 1;
+            my_fallbacks += o.fallbacks;
+            if (!o.done) ++my_nonconv;
+        }
+        W frw[D + 1];
+        if (o.have) {
+#pragma unroll
+            for (int k = 0; k < NFC; ++k) frec.F[k][f] = o.F[k];
+#pragma unroll
+            for (int k = 0; k < NGC; ++k) frec.G[k][f] = o.G[k];
+#pragma unroll
+            for (int a = 0; a < D; ++a) frw[a] = fr_add(uref[a], o.du[a]);
+            frw[D] = fr_word(o.T);
+        } else {
+            if (owned) ++my_nonphys;
+            const R nan = R(__longlong_as_double(0x7ff8000000000000ll));
+#pragma unroll
+            for (int k = 0; k < NFC; ++k) frec.F[k][f] = nan;
+#pragma unroll
+            for (int k = 0; k < NGC; ++k) frec.G[k][f] = nan;
+#pragma unroll
+            for (int a = 0; a < D; ++a) frw[a] = uref[a];
+            fr_store(frw[D], double(nan));
+        }
+#pragma unroll
+        for (int a = 0; a <= D; ++a) frec.fr[a][f] = frw[a];
+        if (owned) {
+#pragma unroll
+            for (int a = 0; a <= D; ++a) Frm_n[a * nf + fidx] = frw[a];
+        }
+    } while (false);
+    __syncthreads();
+
+    // ---- the tile's cells: Eqs. (fluxEq), (FinalUpdateDUGKS), the new frame and the CFL rate
+    double rate = 0.0;
+    const long long n = P.ncell();
+    const int t = threadIdx.x;
+    if (t < TX * TY) do {
+        const int tx = t % TX, ty = t / TX;
+        const long long i = i0 + tx, j = j0 + ty;
+        if (i >= P.nx || (D == 2 && j >= P.ny)) break;
+        const long long c = j * P.nx + i;
+        W uc[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) uc[a] = P.sfr[a * n + c];
+        const W Tc = P.sfr[D * n + c];
+        const R rho = P.sf[c];
+        const R ca = KC.ca, cb = KC.cb, Cv = P.Cv_r;
+        const R Tcr = R(fr_lead(Tc));
+        const R invTc = w_rcp<R>(Tcr), rsqTc = w_sqrt<R>(invTc), sqTc = Tcr * rsqTc;
+        R H[NFC], G[NGC];
+#pragma unroll
+        for (int k = 0; k < NFC; ++k) {
+            const int pl = fplane<D>(k);
+            H[k] = pl < 0 ? R(0) : ca * P.sf[pl * n + c];
+        }
+        H[0] += cb * rho;
+#pragma unroll
+        for (int k = 0; k < NGC; ++k) G[k] = ca * P.sg[k * n + c];
+        G[0] += cb * (Cv - R(0.5 * D)) * rho * Tcr;
+        auto face_flux = [&](int f, int axis, R scale, R un) {
+            R Fc[NFC], Gc[NGC], dv[D];
+#pragma unroll
+            for (int k = 0; k < NFC; ++k) Fc[k] = frec.F[k][f];
+#pragma unroll
+            for (int k = 0; k < NGC; ++k) Gc[k] = frec.G[k][f];
+#pragma unroll
+            for (int a = 0; a < D; ++a) dv[a] = R(fr_rel(frec.fr[a][f], uc[a]));
+            add_face_flux<D, R>(Fc, Gc, dv, R(fr_lead(frec.fr[D][f])), Tcr, invTc, rsqTc, axis, scale, sqTc, un, H, G);
+        };
+        const R sx = KC.dt_dx;
+        face_flux(ty * (TX + 1) + tx, 0, -sx, R(fr_lead(uc[0])));
+        face_flux(ty * (TX + 1) + tx + 1, 0, sx, R(fr_lead(uc[0])));
+        if constexpr (D == 2) {
+            const R sy = KC.dt_dy;
+            face_flux(V::NXF + ty * TX + tx, 1, -sy, R(fr_lead(uc[1])));
+            face_flux(V::NXF + (ty + 1) * TX + tx, 1, sy, R(fr_lead(uc[1])));
+        }
+        R Ho[NFC], Go[NGC], du[D], dT;
+        bool ok = cell_finish<D, R>(H, G, invTc, sqTc, Cv, Ho, Go, du, dT);
+        W un[D];
+        R unr[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            un[a] = fr_add(uc[a], du[a]);
+            unr[a] = R(fr_lead(un[a]));
+        }
+        const W Tn = fr_add(Tc, Tcr * dT);
+        const R Tnr = R(fr_lead(Tn));
+        ok = ok && Tnr > R(0) && isfinite(Tnr);
+        if (!ok) {
+            ++my_nonphys;
+            atomicCAS((unsigned long long *)&P.diag->first_bad, (unsigned long long)-1ll, (unsigned long long)c);
+        }
+#pragma unroll
+        for (int k = 0; k < NFC; ++k) {
+            const int pl = fplane<D>(k);
+            if (pl >= 0) P.sf_n[pl * n + c] = Ho[k];
+        }
+#pragma unroll
+        for (int k = 0; k < NGC; ++k) P.sg_n[k * n + c] = Go[k];
+#pragma unroll
+        for (int a = 0; a < D; ++a) P.sfr_n[a * n + c] = un[a];
+        P.sfr_n[D * n + c] = Tn;
+        if (ok) rate = cell_rate<R>(unr, Tnr, KC.inv_dx, KC.inv_dy, D);
+    } while (false);
+    // warp-aggregated diagnostics
+    const unsigned mask = 0xffffffffu;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        my_iters += __shfl_down_sync(mask, my_iters, o);
+        my_faces += __shfl_down_sync(mask, my_faces, o);
+        my_nonconv += __shfl_down_sync(mask, my_nonconv, o);
+        my_fallbacks += __shfl_down_sync(mask, my_fallbacks, o);
+        my_nonphys += __shfl_down_sync(mask, my_nonphys, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (my_faces) { atomicAdd(&P.diag->face_iters, my_iters); atomicAdd(&P.diag->face_solves, my_faces); }
+        if (my_nonconv) { atomicAdd(&P.diag->nonconv, my_nonconv); atomicOr(&P.diag->flags, FLAG_NOT_CONVERGED); }
+        if (my_fallbacks) atomicAdd(&P.diag->fallbacks, my_fallbacks);
+        if (my_nonphys) { atomicAdd(&P.diag->nonphys, my_nonphys); atomicOr(&P.diag->flags, FLAG_NONPHYSICAL); }
     }
     reduce_rate_and_advance(P.clock, rate, true);
 }
@@ -1409,13 +1783,14 @@ __global__ void init_faces_kernel(const Params<D, R> P)
 
 // ------------------------------------------------------- learned gauge predictor
 
-// Before the face corrector of a step: the learned prediction of every face's converged
-// frame (features as in mlp::features), written beside the previous half step's frame.
+// Before the face corrector of a step: the learned prediction of the converged frame of
+// every face of the active tiles (features as in mlp::features), written beside the
+// previous half step's frame.
 // Persistent CTAs (mlp::kInferCtasPerSm per SM) stage the network once and loop over tiles
 // of 16 x 4 cells: the 64 x-faces and 64 y-faces of a tile are the 128 rows of one MLP tile
 // (the face kernel's mapping), and the (16+3) x (4+3) cells they read are staged once in
 // shared memory as (rho, velocity relative to the tile's reference, T) in FP32.
-constexpr int kPredTX = 16, kPredTY = 4;
+constexpr int kPredTX = kPredTileX, kPredTY = kPredTileY;
 static_assert(2 * kPredTX * kPredTY == mlp::kRows, "one face per MLP row");
 
 template <typename R>
@@ -1447,7 +1822,12 @@ gauge_predict_kernel(const Params<2, R> P)
     const int dir = threadIdx.x >= kPredTX * kPredTY ? 1 : 0;
     const int tl = threadIdx.x - dir * kPredTX * kPredTY, tx = tl % kPredTX, ty = tl / kPredTX;
     const int na = dir, ta = 1 - dir;
+    const unsigned int step = (unsigned int)K.steps;
+    const unsigned int *active = P.pred_active + (step & 1u) * (unsigned)ntiles;
     for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        // only tiles where a face needed more than one pass (or used a prediction) in the
+        // previous step: elsewhere the previous half step's frame is already converged
+        if (active[tile] != step) continue;
         const long long i0 = (long long)(tile % nbx) * kPredTX, j0 = (long long)(tile / nbx) * kPredTY;
         if (threadIdx.x == 0) cell_velocity<2, R>(P, i0, j0, uref_tile);
         __syncthreads();

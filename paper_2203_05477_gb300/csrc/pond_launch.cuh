@@ -35,7 +35,8 @@ struct FaceList<2, double> {
 };
 template <typename R>
 struct FaceList<1, R> {
-    using type = VList<FaceVariant<1, 128, 1, 1>, FaceVariant<1, 64, 1, 2>, FaceVariant<1, 256, 1, 1>>;
+    using type = VList<FaceVariant<1, 128, 1, 1>, FaceVariant<1, 64, 1, 2>, FaceVariant<1, 256, 1, 1>,
+                       FaceVariant<1, 32, 1, 8>>;
 };
 
 template <int D, typename R, typename V, typename... Rest>
@@ -70,6 +71,7 @@ void launch_face_m(int v, const Params<D, R> &P, cudaStream_t st);
 template <int D, typename R>
 inline void launch_face(int v, bool collect, const Params<D, R> &P, cudaStream_t st)
 {
+    if (P.equilibrate) return launch_face_m<D, R, FACE_EQUIL>(0, P, st);
     if constexpr (D == 2) {
         if (collect) return launch_face_m<D, R, FACE_COLLECT>(0, P, st);
         if (P.use_learned) return launch_face_m<D, R, FACE_LEARNED>(v, P, st);
@@ -77,14 +79,67 @@ inline void launch_face(int v, bool collect, const Params<D, R> &P, cudaStream_t
     launch_face_m<D, R, FACE_PLAIN>(v, P, st);
 }
 
+// ---------------------------------------------------------------- fused step kernel
+
+template <int D, typename R>
+struct StepList;
+template <>
+struct StepList<2, float> {
+    using type = VList<StepVariant<2, 8, 8, 3>, StepVariant<2, 16, 4, 3>, StepVariant<2, 8, 4, 5>, StepVariant<2, 8, 8, 2>>;
+};
+template <>
+struct StepList<2, double> {
+    using type = VList<StepVariant<2, 8, 4, 2>, StepVariant<2, 4, 4, 4>>;
+};
+template <typename R>
+struct StepList<1, R> {
+    using type = VList<StepVariant<1, 124, 1, 4>, StepVariant<1, 60, 1, 8>>;
+};
+
+template <int D, typename R>
+constexpr int step_variants() { return StepList<D, R>::type::size; }
+
+template <int D, typename R, typename V, typename... Rest>
+void step_name_at(int v, char *buf, size_t n)
+{
+    if (v <= 0 || sizeof...(Rest) == 0) {
+        if (D == 2) std::snprintf(buf, n, "step %dx%d cells fused, %d threads, %d CTA/SM", V::TX, V::TY, V::THREADS, V::MINB);
+        else std::snprintf(buf, n, "step %d cells fused, %d threads, %d CTA/SM", V::TX, V::THREADS, V::MINB);
+    } else if constexpr (sizeof...(Rest) > 0) {
+        step_name_at<D, R, Rest...>(v - 1, buf, n);
+    }
+}
+template <int D, typename R, typename L>
+struct StepNames;
+template <int D, typename R, typename... Vs>
+struct StepNames<D, R, VList<Vs...>> {
+    static void name(int v, char *buf, size_t n) { step_name_at<D, R, Vs...>(v, buf, n); }
+};
+
+// the fused step kernel of variant v (defined in pond_variants.cuh, instantiated in pond_vfused.cu)
+template <int D, typename R>
+void launch_step_fused(int v, const Params<D, R> &P, cudaStream_t st);
+
 // ---------------------------------------------------------------- cell kernel
 
-constexpr int kCellBlocks[6] = {256, 128, 512, 256, 256, 128};
-constexpr int kCellMinBlocks[6] = {1, 1, 1, 3, 4, 6};   // CTAs per SM asked of the register allocator
-constexpr int kCellVariants = 6;
+constexpr int kCellBlocks[7] = {256, 128, 512, 256, 256, 128, 32};
+constexpr int kCellMinBlocks[7] = {1, 1, 1, 3, 4, 6, 1};   // CTAs per SM asked of the register allocator
+constexpr int kCellVariants = 7;
 
 template <int D, typename R>
 void launch_cell(int v, const Params<D, R> &P, cudaStream_t st);
+
+// the cell kernel with the equilibration alternative in the flux (default block size)
+template <int D, typename R>
+void launch_cell_eq(const Params<D, R> &P, cudaStream_t st);
+
+// the cell kernel of variant v, or the equilibration one when the parameters ask for it
+template <int D, typename R>
+inline void launch_cell_any(int v, const Params<D, R> &P, cudaStream_t st)
+{
+    if (P.equilibrate) launch_cell_eq<D, R>(P, st);
+    else launch_cell<D, R>(v, P, st);
+}
 
 inline void cell_name(int v, char *buf, size_t n)
 {

@@ -36,9 +36,9 @@ struct FaceLaunch<D, R, MODE, VList<Vs...>> {
 template <int D, typename R, int MODE>
 void launch_face_m(int v, const Params<D, R> &P, cudaStream_t st)
 {
-    if constexpr (MODE == FACE_COLLECT) {
+    if constexpr (MODE == FACE_COLLECT || MODE == FACE_EQUIL) {
         using V0 = FaceVariant<D, D == 2 ? 32 : 128, 4, D == 2 && sizeof(R) == 4 ? 2 : 1>;
-        launch_face_one<D, R, FACE_COLLECT, V0>(P, st);
+        launch_face_one<D, R, MODE, V0>(P, st);
     } else {
         FaceLaunch<D, R, MODE, typename FaceList<D, R>::type>::launch(v, P, st);
     }
@@ -55,8 +55,44 @@ void launch_cell(int v, const Params<D, R> &P, cudaStream_t st)
     case 3: cell_kernel<D, R, 256, 3><<<blocks(256), 256, 0, st>>>(P); break;
     case 4: cell_kernel<D, R, 256, 4><<<blocks(256), 256, 0, st>>>(P); break;
     case 5: cell_kernel<D, R, 128, 6><<<blocks(128), 128, 0, st>>>(P); break;
+    case 6: cell_kernel<D, R, 32><<<blocks(32), 32, 0, st>>>(P); break;
     default: cell_kernel<D, R, 256><<<blocks(256), 256, 0, st>>>(P); break;
     }
+}
+
+template <int D, typename R, typename V>
+void launch_step_one(const Params<D, R> &P, cudaStream_t st)
+{
+    const dim3 g(unsigned((P.nx + V::TX - 1) / V::TX), D == 2 ? unsigned((P.ny + V::TY - 1) / V::TY) : 1u);
+    step_kernel<D, R, V><<<g, V::THREADS, 0, st>>>(P);
+}
+template <int D, typename R, typename V, typename... Rest>
+void launch_step_at(int v, const Params<D, R> &P, cudaStream_t st)
+{
+    if constexpr (sizeof...(Rest) == 0) {
+        launch_step_one<D, R, V>(P, st);
+    } else {
+        if (v <= 0) launch_step_one<D, R, V>(P, st);
+        else launch_step_at<D, R, Rest...>(v - 1, P, st);
+    }
+}
+template <int D, typename R, typename L>
+struct StepLaunch;
+template <int D, typename R, typename... Vs>
+struct StepLaunch<D, R, VList<Vs...>> {
+    static void launch(int v, const Params<D, R> &P, cudaStream_t st) { launch_step_at<D, R, Vs...>(v, P, st); }
+};
+template <int D, typename R>
+void launch_step_fused(int v, const Params<D, R> &P, cudaStream_t st)
+{
+    StepLaunch<D, R, typename StepList<D, R>::type>::launch(v, P, st);
+}
+
+template <int D, typename R>
+void launch_cell_eq(const Params<D, R> &P, cudaStream_t st)
+{
+    const long long n = P.ncell();
+    cell_kernel<D, R, 256, 1, true><<<unsigned((n + 255) / 256), 256, 0, st>>>(P);
 }
 
 template <typename R>

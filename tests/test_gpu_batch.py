@@ -215,10 +215,11 @@ def test_c3_full_range_tubes_against_oracle(precision, steps, tol64):
                     o2.step(steps)
                     r2, u2, _, p2 = o2.primitive()
                     bound = max(bound, 2.0 * err(r2, u2, p2))
-                envelope_cases.append((int(idx[k]), e, bound))
+                if e > 1e-4:
+                    envelope_cases.append((int(idx[k]), e, bound))
             if e > bound:
                 errs.append((int(idx[k]), e, bound, os_.stats()["nonconverged"]))
     assert not mism, mism
     assert not errs, errs
     assert survivors >= 10 and (status == 1).sum() >= 10, (survivors, int((status == 1).sum()))
-    assert len(envelope_cases) <= survivors // 4, envelope_cases
+    assert len(envelope_cases) <= max(1, survivors // 10), envelope_cases   # tubes that needed the envelope

@@ -63,8 +63,8 @@ def test_training_fits_a_smooth_target():
 def test_learned_predictor_in_the_solver():
     """Collect pairs from the plain FP32 solver on one seed, train on the GPU, then run
     another seed with and without the learned predictor.  The corrector still decides
-    convergence: the learned run stays within 1e-4 relative L1 of the FP64 oracle (as the
-    plain FP32 run does), and the passes per face of both runs are reported."""
+    convergence: the learned run stays within 1e-4 relative L1 of the FP64 oracle, the bound
+    of the plain FP32 run, and the passes per face of both runs are reported."""
     from tests.common import oracle_for
     train_pb = I.quadrants_2d(256, seed=1)
     s = pond.Solver(train_pb, precision="fp32", tau=1e-5, cfl=0.2)
@@ -98,30 +98,21 @@ def test_learned_predictor_in_the_solver():
     # must not cost passes
     assert pass1 <= 1.03 * pass0
 
-    # accuracy on a draw whose corrector never needs the restart path: where it does (seed
-    # 2 has 169 such passes), the result depends discontinuously on rounding and on the
-    # stopping tolerance (the oracle alone moves by 3e-3 in p between tol 1e-10 and 1e-6)
-    small = I.quadrants_2d(48, seed=3)
-    os_ = oracle_for(small, tau=1e-5, cfl=0.2, tol=1e-10)
-    os_.step(40)
-    assert os_.stats()["fallbacks"] == 0
-    ro, uo, vo, po = os_.primitive()
-    # Faces whose corrector does not converge within max_iter (limit cycles) end on an
-    # iterate that depends on where the iteration started and stopped; the oracle alone
-    # moves by ~1e-3 when max_iter changes by one.  The plain FP32 run starts every face
-    # where the oracle does and stays within 1e-4; the learned run starts elsewhere and is
-    # held to that envelope of the method itself.
-    env_r, env_p = 0.0, 0.0
-    for mi in (15, 17):
-        oe = oracle_for(small, tau=1e-5, cfl=0.2, tol=1e-10, max_iter=mi)
-        oe.step(40)
-        re_, _, _, pe_ = oe.primitive()
-        env_r, env_p = max(env_r, rel_l1(re_, ro)), max(env_p, rel_l1(pe_, po))
-    (r, u, v, p), _, _ = run(small, False, 40)
-    assert rel_l1(r, ro) < 1e-4 and rel_l1(p, po) < 1e-4, (rel_l1(r, ro), rel_l1(p, po))
-    (r, u, v, p), _, _ = run(small, True, 40)
-    assert rel_l1(r, ro) <= max(1e-4, 2 * env_r) and rel_l1(p, po) <= max(1e-4, 2 * env_p), \
-        (rel_l1(r, ro), rel_l1(p, po), env_r, env_p)
+    # accuracy: the learned run is held to the plain FP32 run's bound, 1e-4 relative L1
+    # against the FP64 oracle with the same stopping rule, on draws whose corrector
+    # converges nearly everywhere (the oracle has 24 and 11 faces in 40 steps that reach the
+    # pass limit; a Mach-3 quadrant draw has 1000-4000, where any start other than the
+    # oracle's own ends elsewhere within the method's stopping-point envelope)
+    for pb in (I.quadrants_2d(48, seed=6, mach_max=1.0), I.smooth_periodic(2, 48, 48, seed=2, amp=0.15)):
+        os_ = oracle_for(pb, tau=1e-5, cfl=0.2, tol=1e-6)
+        os_.step(40)
+        assert os_.stats()["fallbacks"] == 0 and os_.stats()["nonconverged"] <= 30
+        ro, uo, vo, po = os_.primitive()
+        so = np.hypot(uo, vo)
+        for learned in (False, True):
+            (r, u, v, p), _, _ = run(pb, learned, 40)
+            err = (rel_l1(r, ro), rel_l1(p, po), np.abs(np.hypot(u, v) - so).sum() / so.sum())
+            assert max(err) < 1e-4, (learned, err)
 
 
 def _run_quadrants(params, steps, gate=None, trust=None, max_iter=16):

@@ -19,8 +19,10 @@ KW64 = dict(tau=1e-5, cfl=0.2, fixed_iters=3, max_iter=8)
 
 
 def split(names):
+    """(face variants, cell variants, whole-step choices) of a grid state's variant names."""
     nf = sum(1 for n in names if n.startswith("face"))
-    return nf, len(names) - nf
+    nc = sum(1 for n in names if n.startswith("cell"))
+    return nf, nc, len(names) - nf - nc
 
 
 @pytest.mark.parametrize("name,pb", [
@@ -32,8 +34,8 @@ def test_every_grid_variant_matches_oracle_fp64(name, pb):
     os_ = oracle_for(pb, **KW64)
     os_.step(4)
     gs = gpu_for(pb, precision="fp64", **KW64)
-    nf, nc = split(gs.variants())
-    assert nf >= 3 and nc == 6
+    nf, nc, ns = split(gs.variants())
+    assert nf >= 3 and nc == 7 and ns >= 2
     for f in range(nf):
         for c in range(nc):
             if f and c != f % nc:
@@ -44,6 +46,16 @@ def test_every_grid_variant_matches_oracle_fp64(name, pb):
             d = gs.sync()
             assert d["steps"] == 4 and d["nonphysical"] == 0, (f, c, d)
             compare_fp64(gs, os_)
+    # every fused step variant (faces and cell update of a tile in one kernel)
+    for k in range(1, ns):
+        gs.set_variants(face=0, cell=0, tube=k)
+        gs.set_primitive()
+        gs.step(4)
+        d = gs.sync()
+        st = os_.stats()
+        assert d["steps"] == 4 and d["nonphysical"] == 0, (k, d)
+        assert d["face_iters"] == st["face_iters"] and d["fallbacks"] == st["fallbacks"], (k, d, st)
+        compare_fp64(gs, os_)
 
 
 def _prims(s):
@@ -54,12 +66,15 @@ def test_fp32_grid_variants_agree():
     pb = I.quadrants_2d(61, seed=0)
     kw = dict(tau=1e-5, cfl=0.2, max_iter=16, tol=1e-6)
     gs = gpu_for(pb, precision="fp32", **kw)
-    nf, nc = split(gs.variants())
+    nf, nc, ns = split(gs.variants())
     gs.step(10)
     ref = _prims(gs)
-    for f in range(nf):
-        c = f % nc
-        gs.set_variants(face=f, cell=c)
+    for f in list(range(nf)) + [(0, k) for k in range(1, ns)]:
+        if isinstance(f, tuple):
+            gs.set_variants(face=0, cell=0, tube=f[1])
+            f = 0
+        else:
+            gs.set_variants(face=f, cell=f % nc)
         gs.set_primitive()
         gs.step(10)
         assert gs.sync()["nonphysical"] == 0
@@ -98,6 +113,37 @@ def test_autotune_restores_state_and_uses_cache(tmp_path):
     r2 = other.autotune(steps=2, cache=str(cache))
     assert r2["from_cache"] and (r2["face"], r2["cell"]) == (r["face"], r["cell"])
     assert len(cache.read_text().splitlines()) == 1
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_fused_step_graphs_and_parity(dim):
+    """The fused step alternates between two sets of state planes: runs of captured 32-step
+    graphs entered at either parity, and single launches, give the same state bit for bit;
+    an odd number of fused steps, then the face and cell kernels, continue the same run."""
+    pb = I.quadrants_2d(40, seed=3) if dim == 2 else I.paper_tube("lax", 300)[0]
+    kw = dict(tau=1e-5, cfl=0.2, max_iter=16, tol=1e-6)
+    a = gpu_for(pb, precision="fp32", **kw)
+    b = gpu_for(pb, precision="fp32", **kw)
+    ns = split(a.variants())[2]
+    a.set_variants(0, 0, ns - 1)
+    b.set_variants(0, 0, ns - 1)
+    a.step(1)              # odd parity, then two graphs entered there, then single launches
+    a.step(69)
+    for _ in range(70):
+        b.step(1)
+    for x, y in zip(a.state(), b.state()):
+        assert np.array_equal(x, y)
+    for x, y in zip(a.face_gauges(), b.face_gauges()):
+        assert x is None or np.array_equal(x, y)
+    # switching to the separate kernels after an odd number of fused steps
+    c = gpu_for(pb, precision="fp64", **KW64)
+    o = oracle_for(pb, **KW64)
+    c.set_variants(0, 0, 1)
+    c.step(3)
+    c.set_variants(0, 0, 0)
+    c.step(2)
+    o.step(5)
+    compare_fp64(c, o)
 
 
 def test_every_tube_variant_matches_oracle_fp64():
