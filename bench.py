@@ -35,7 +35,7 @@ FALLBACK_HBM_GBS = 6800.0
 N_SMS, FP32_LANES = 152, 128
 # ncu dram read + write of one face-kernel launch at 1024^2, for the tile variants measured
 # on the current kernel (profiles/face_kernel_quadrants1024_fp32.md); other variants: null
-FACE_KERNEL_DRAM_BYTES = {1: 136.3e6 + 178.1e6, 3: 136.4e6 + 172.4e6, 7: 136.2e6 + 182.8e6}
+FACE_KERNEL_DRAM_BYTES = {}
 # FP32 operations (FMA = 2) of one corrector pass at one D2Q16 face (per-face overhead
 # included), from the ncu instruction counts of the scalar face kernel; used for the ALU
 # roofline.  The packed FP32x2 form of the same algorithm executes ~4% more (differences
@@ -45,6 +45,10 @@ FLOPS_PER_FACE_PASS = 4550.0
 # cell state (8 + 6 FP32 coefficients + 3 float-float frame words = 80 B) and two face predictors
 # (2 x 24 B) and writes two faces (2 x (16 x 4 + 24) B)
 FACE_KERNEL_BYTES_PER_CELL = 80 + 48 + 176
+# algorithmic bytes per cell-update of the whole FP32 D2Q16 step in the population layout of
+# the method: the 16 f and 16 g populations in FP32 (128 B), the FP64 cell frame (24 B) and
+# the cell's two FP32 face gauges (24 B), each read once and written once
+STEP_BYTES_PER_CELL = 352
 
 
 def replica_seed(base_seed, rank):
@@ -162,6 +166,81 @@ def cpu_baseline(pb_full, steps, target_s=12.0):
     el = time.perf_counter() - t0
     return {"value": side * side * done / el / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
             "sample": "%dx%d centre patch of the workload, %d steps, FP64, single thread, %.1f s" % (side, side, done, el)}
+
+
+def host_cpu():
+    """Core count and CPU model of this host (the cores the CPU baselines run on)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as fh:
+                for ln in fh:
+                    if ln.lower().startswith("model name"):
+                        model = ln.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            pass
+    return {"nproc": os.cpu_count(), "model": model}
+
+
+def _oracle_patch_worker(job):
+    """One process: the FP64 oracle as it stands on one side x side patch of the quadrant
+    workload for `steps` steps; returns (cell-updates, seconds)."""
+    n, seed, i0, j0, side, steps = job
+    import oracle as O
+    from paper_2203_05477_gb300 import inputs as I
+    pb = I.quadrants_2d(n, seed=seed)
+    sub = lambda a: a.reshape(n, n)[j0:j0 + side, i0:i0 + side].ravel()
+    s = O.make_solver(2, side, side, dx=pb.dx, dy=pb.dy, gamma=pb.gamma, tau=1e-5, cfl=0.2, tol=1e-10, max_iter=16)
+    s.set_primitive(sub(pb.rho), sub(pb.ux), sub(pb.uy), sub(pb.p))
+    t0 = time.perf_counter()
+    s.step(steps)
+    return side * side * steps, time.perf_counter() - t0
+
+
+def cpu_baseline_parallel(n, seed, side=64, steps=8):
+    """The single-thread oracle run as one process per host core, each on its own patch of
+    the workload (patches along the domain's diagonal, all crossing the quadrant fronts):
+    whole-host throughput = all processes' cell-updates over the wall time of the slowest."""
+    from concurrent.futures import ProcessPoolExecutor
+    from multiprocessing import get_context
+    cores = os.cpu_count() or 1
+    jobs = []
+    for k in range(cores):
+        c = int((k + 0.5) * (n - side) / cores)
+        jobs.append((n, seed, c, n - side - c, side, steps))
+    with ProcessPoolExecutor(max_workers=cores, mp_context=get_context("spawn")) as pool:
+        list(pool.map(_oracle_patch_worker, [(n, seed, 0, 0, 8, 1)] * cores))   # start-up and build outside the timing
+        t0 = time.perf_counter()
+        res = list(pool.map(_oracle_patch_worker, jobs))
+        wall = time.perf_counter() - t0
+    updates = sum(r[0] for r in res)
+    return {"value": updates / wall / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": "%d processes of the single-thread oracle, each on its own %dx%d patch of the workload for %d steps, "
+                      "FP64, %.1f s wall" % (cores, side, side, steps, wall)}
+
+
+def cpu_baseline_sod(target_s=15.0):
+    """Configuration 1 on the oracle as it stands, single thread: the 400-cell Sod tube, FP64,
+    CFL 0.5, run to t = 0.2."""
+    import oracle as O
+    from paper_2203_05477_gb300 import inputs as I
+    pb = I.sod_400()
+    s = O.make_solver(1, pb.nx, dx=pb.dx, gamma=pb.gamma, tau=1e-5, cfl=0.5, t_end=0.2, tol=1e-10, max_iter=16)
+    s.set_primitive(pb.rho, pb.ux, None, pb.p)
+    t0 = time.perf_counter()
+    steps = s.step(100000)
+    el = time.perf_counter() - t0
+    return {"value": pb.ncell * steps / el / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle", "steps": steps,
+            "latency_ms": 1e3 * el, "sample": "the whole run to t = 0.2 (%d steps), FP64, single thread" % steps}
 
 
 TUBE_BYTES_PER_CELL = 96  # state (3+3 FP32 + 2 float-float frame words) and face predictor (2 FP32), read and written
@@ -311,6 +390,164 @@ def cpu_baseline_3d(pb, side=12, steps=3, target_s=10.0):
             "sample": "%d^3 patch across the spherical front, %d steps, FP64, single thread, %.1f s" % (side, done, el)}
 
 
+def bench_sod(args):
+    """Configuration 1: the 400-cell Sod tube on the D1Q4 lattice, FP64 (and FP32), CFL 0.5,
+    run to t = 0.2.  The whole problem fits in L2, so the figures are the latency of the run
+    and steps per second (graph replay of pond_step), not an HBM fraction."""
+    import torch
+    import paper_2203_05477_gb300 as pond
+    from paper_2203_05477_gb300 import inputs as I
+    pb = I.sod_400()
+    out = {"workload": "sod_400_t0.2", "cells": pb.ncell}
+    for prec in ("fp64", "fp32"):
+        s = pond.Solver(pb, precision=prec, tau=1e-5, cfl=0.5, t_end=0.2, max_iter=16)
+        s.set_primitive()
+        tuned = s.autotune(steps=20)
+        names = s.variants()
+        s.step(2000)                      # steps after t_end are no-ops; find the step count
+        n_steps = s.sync()["steps"]
+        reps = []
+        for _ in range(3):
+            s.set_primitive()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s.stream)
+            s.step(n_steps)
+            e1.record(s.stream)
+            e1.synchronize()
+            reps.append(e0.elapsed_time(e1))
+        d = s.sync()
+        ms = statistics.median(reps)
+        out[prec] = {"steps": int(n_steps), "latency_ms": ms, "steps_per_s": n_steps / (ms * 1e-3),
+                     "mlups": pb.ncell * n_steps / (ms * 1e-3) / 1e6, "t": d["t"], "status_ok": d["status"] == pond.POND_OK,
+                     "variants": [names[tuned["face"]], [nm for nm in names if nm.startswith("cell")][tuned["cell"]]]}
+        s.close()
+    return out
+
+
+def train_predictor(args):
+    """The learned face-gauge predictor, trained on the GPU from pairs the plain FP32 solver
+    collects on another seed of the quadrant workload (256^2, 100 steps)."""
+    import torch
+    import paper_2203_05477_gb300 as pond
+    from paper_2203_05477_gb300 import inputs as I
+    t0 = time.perf_counter()
+    tr = pond.Solver(I.quadrants_2d(256, seed=args.seed + 101), precision="fp32", tau=1e-5, cfl=0.2)
+    tr.set_primitive()
+    pairs = tr.gauge_collect(100, cap=300_000, every=2)
+    perm = torch.randperm(pairs.shape[0], device=pairs.device)
+    losses = tr.gauge_train(pairs[perm].contiguous(), epochs=6, batch=4096, lr=2e-3)
+    params = tr.gauge_params()
+    tr.close()
+    return params, {"pairs": int(pairs.shape[0]), "epochs": 6, "loss_first": float(losses[0]),
+                    "loss_last": float(losses[-1]), "seconds": time.perf_counter() - t0}
+
+
+def timed_run(pb, params, steps, warmup, learned, variants=None, tune=True):
+    """FP32 steps of one 2D workload (optionally with the learned predictor), device time of
+    `steps` graph-replayed steps after `warmup` steps; stops early at a non-physical state."""
+    import torch
+    import paper_2203_05477_gb300 as pond
+    s = pond.Solver(pb, precision="fp32", tau=1e-5, cfl=0.2, max_iter=16)
+    s.set_primitive()
+    if learned:
+        s.set_gauge_params(params)
+        s.gauge_enable(True)
+    tuned = None
+    if variants is not None:
+        s.set_variants(*variants)
+    elif tune:
+        tuned = s.autotune(steps=2)
+    s.step(warmup)
+    d0 = s.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s.stream)
+    s.step(steps)
+    e1.record(s.stream)
+    e1.synchronize()
+    d1 = s.sync()
+    ms = e0.elapsed_time(e1)
+    out = {"steps": steps, "mlups": pb.ncell * steps / (ms * 1e-3) / 1e6, "ms_per_step": ms / steps,
+           "passes_per_face": (d1["face_iters"] - d0["face_iters"]) / max(1, d1["face_solves"] - d0["face_solves"]),
+           "nonconverged_faces": d1["nonconverged"] - d0["nonconverged"], "status_ok": d1["status"] == pond.POND_OK}
+    if tuned is not None:
+        names = s.variants()
+        out["variants"] = [names[tuned["face"]], [n for n in names if n.startswith("cell")][tuned["cell"]],
+                           [n for n in names if n.startswith("step")][tuned["tube"]]]
+    s.close()
+    return out
+
+
+def bench_equilibration(pb, steps=50):
+    """The equilibration alternative of Sec. II.C against Grad's projection on the same
+    workload, FP32, both on the face tile and cell block the equilibration kernels are
+    compiled for (face variant 0, cell variant 0): device time per step and passes."""
+    import torch
+    import paper_2203_05477_gb300 as pond
+    out = {}
+    for name, eq in (("grad", False), ("equilibration", True)):
+        s = pond.Solver(pb, precision="fp32", tau=1e-5, cfl=0.2, max_iter=16)
+        s.set_primitive()
+        s.set_variants(0, 0)
+        if eq:
+            s.set_equilibration(True)
+        s.step(5)
+        d0 = s.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        s.step(steps)
+        e1.record(s.stream)
+        e1.synchronize()
+        d1 = s.sync()
+        ms = e0.elapsed_time(e1) / steps
+        out[name] = {"ms_per_step": ms, "mlups": pb.ncell / (ms * 1e-3) / 1e6,
+                     "passes_per_face": (d1["face_iters"] - d0["face_iters"]) / max(1, d1["face_solves"] - d0["face_solves"]),
+                     "status_ok": d1["status"] == pond.POND_OK}
+        s.close()
+    out["cost_ratio"] = out["equilibration"]["ms_per_step"] / out["grad"]["ms_per_step"]
+    out["note"] = "%d steps of the workload, FP32, face 32x4 cells / 2 CTA per SM, cell 256 threads for both" % steps
+    return out
+
+
+def first_nonphysical_step(pb, limit):
+    """Steps the plain FP32 solver takes on a workload before a non-physical state (0: none)."""
+    import paper_2203_05477_gb300 as pond
+    s = pond.Solver(pb, precision="fp32", tau=1e-5, cfl=0.2, max_iter=16)
+    s.set_primitive()
+    for k in range(1, limit + 1):
+        s.step(1)
+        if s.sync()["nonphysical"]:
+            s.close()
+            return k
+    s.close()
+    return 0
+
+
+def bench_interface_and_jet(args, params, hbm_peak):
+    """Configurations 4 and 5 at their stated sizes, FP32 with and without the learned
+    predictor: the shocked perturbed interface (4096 x 1024) over `c4_steps` of its 20 000
+    steps, and the Mach-80 jet (4096^2), which the method as read takes to a non-physical
+    state within its first steps: it is timed over the steps before that state."""
+    from paper_2203_05477_gb300 import inputs as I
+    c4 = I.shocked_interface_2d(4096, 1024, seed=args.seed)
+    out = {"c4": {"workload": "shocked_interface_4096x1024_seed%d" % args.seed, "cells": c4.ncell,
+                  "note": "%d of the stated 20000 steps (the run reaches 4000 steps without a non-physical state)"
+                          % args.c4_steps}}
+    plain = timed_run(c4, params, args.c4_steps, 5, False)
+    out["c4"]["fp32"] = plain
+    out["c4"]["fp32_learned"] = timed_run(c4, params, args.c4_steps, 5, True)
+    out["c4"]["fp32"]["hbm_frac_step"] = 352 * plain["mlups"] * 1e6 / (hbm_peak * 1e9)
+    c5 = I.jet_2d(4096, seed=args.seed)
+    stop = first_nonphysical_step(c5, 40)
+    out["c5"] = {"workload": "jet_4096_seed%d" % args.seed, "cells": c5.ncell, "first_nonphysical_step": stop}
+    if stop != 1:
+        k = (stop - 1) if stop else 40
+        out["c5"]["fp32"] = timed_run(c5, params, k, 0, False)
+        out["c5"]["fp32_learned"] = timed_run(c5, params, k, 0, True)
+        out["c5"]["note"] = "timed over the %d steps before the first non-physical state (graph-replayed, autotuned)" % k
+    return out
+
+
 def run_reference(args, rank, world):
     """Reference arm: the FP64 CPU oracle (the paper ships no code) on host cores."""
     if rank != 0:
@@ -356,9 +593,10 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="skip the kernel-variant autotuner (use the defaults)")
     ap.add_argument("--tune-cache", default=None,
                     help="autotuner cache file: choices found there are reused without timing (profiling runs)")
-    ap.add_argument("--workload", default="quadrants", choices=["quadrants", "tubes", "d3q64", "sl"],
-                    help="tubes / d3q64 / sl: only that measurement (profiling cases)")
+    ap.add_argument("--workload", default="quadrants", choices=["quadrants", "tubes", "d3q64", "sl", "learned"],
+                    help="tubes / d3q64 / sl / learned: only that measurement (profiling cases)")
     ap.add_argument("--d3-n", type=int, default=128, help="cells per side of the D3Q64 measurement")
+    ap.add_argument("--c4-steps", type=int, default=200, help="timed steps of the 4096 x 1024 interface leg")
     ap.add_argument("--quick", action="store_true",
                     help="FP32 timed steps only (no e2e, FP64 or CPU legs): the profiling case")
     args = ap.parse_args()
@@ -391,6 +629,15 @@ def main():
         if rank == 0:
             print(json.dumps(bench_sl_vs_fv(args)), flush=True)
         return
+    if args.workload == "learned":
+        # the learned predictor on the headline workload: training, then FP32 steps with it
+        if rank == 0:
+            params, train = train_predictor(args)
+            pbl = I.quadrants_2d(args.n, seed=args.seed)
+            out = timed_run(pbl, params, args.steps, args.warmup, True, tune=not args.no_tune)
+            out["train"] = train
+            print(json.dumps(out), flush=True)
+        return
     n = args.n
     pb = I.quadrants_2d(n, seed=replica_seed(args.seed, rank))
     ncell = n * n
@@ -408,7 +655,7 @@ def main():
     s.set_primitive()
     # the autotuner times every compiled face/cell variant on this state and restores it
     tune = None if args.no_tune else s.autotune(steps=3, cache=args.tune_cache)
-    fv, cv = (tune["face"], tune["cell"]) if tune else (0, 0)
+    fv, cv, sv = (tune["face"], tune["cell"], tune["tube"]) if tune else (0, 0, 0)
     variant_names = s.variants()
     s.step(args.warmup)
     d0 = s.sync()
@@ -442,7 +689,7 @@ def main():
     pin = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (pb.rho, pb.ux, pb.uy, pb.p)]
     outs = [torch.empty(ncell, dtype=torch.float64).pin_memory() for _ in range(4)]
     s2 = pond.Solver(pb, precision="fp32", tau=1e-5, cfl=0.2, max_iter=16)
-    s2.set_variants(fv, cv)
+    s2.set_variants(fv, cv, sv)
     barrier()
     t0 = time.perf_counter()
     s2.set_primitive(*[a.numpy() for a in pin])
@@ -459,18 +706,9 @@ def main():
                     "apart, so e2e can come out slightly above it" % args.steps)}
 
     # ---- FP32 with the learned face-gauge predictor (trained here on another seed)
-    learned = None
+    learned, params, train = None, None, None
     if not args.no_learned:
-        import torch as _t
-        t_tr = time.perf_counter()
-        tr = pond.Solver(I.quadrants_2d(256, seed=args.seed + 101), precision="fp32", tau=1e-5, cfl=0.2)
-        tr.set_primitive()
-        pairs = tr.gauge_collect(100, cap=300_000, every=2)
-        perm = _t.randperm(pairs.shape[0], device=pairs.device)
-        losses = tr.gauge_train(pairs[perm].contiguous(), epochs=6, batch=4096, lr=2e-3)
-        params = tr.gauge_params()
-        tr.close()
-        t_tr = time.perf_counter() - t_tr
+        params, train = train_predictor(args)
         sl = pond.Solver(pb, precision="fp32", tau=1e-5, cfl=0.2, max_iter=16)
         sl.set_variants(fv, cv)
         sl.set_primitive()
@@ -488,9 +726,7 @@ def main():
         lms = max_over_ranks_(l0e.elapsed_time(l1e))
         learned = {"value": world * ncell * args.steps / (lms * 1e-3) / 1e6, "unit": "MLUPS",
                    "passes_per_face": (dl1["face_iters"] - dl0["face_iters"]) / max(1, dl1["face_solves"] - dl0["face_solves"]),
-                   "predictor_and_face_ms": lf / args.steps, "cell_ms": lc / args.steps,
-                   "train": {"pairs": int(pairs.shape[0]), "epochs": 6, "loss_first": float(losses[0]),
-                             "loss_last": float(losses[-1]), "seconds": t_tr},
+                   "predictor_and_face_ms": lf / args.steps, "cell_ms": lc / args.steps, "train": train,
                    "status_ok": dl1["status"] == pond.POND_OK}
         sl.close()
 
@@ -520,6 +756,7 @@ def main():
     achieved = flops / (face_ms_avg * 1e-3) / 1e12
     hbm_peak = pk.get("hbm_gbs", FALLBACK_HBM_GBS)
     face_gbs = FACE_KERNEL_BYTES_PER_CELL * ncell / (face_ms_avg * 1e-3) / 1e9
+    step_gbs = STEP_BYTES_PER_CELL * value * 1e6 / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": el_ms / args.steps, "higher_is_better": True,
@@ -528,24 +765,38 @@ def main():
                    "precision": "fp32 populations, float-float frames", "cfl": 0.2, "tau": 1e-5,
                    "corrector": "tol 1e-6, max 16 passes", "l2": "working set %.0f MB > L2" % (
                        (ncell * (80 + 2 * 88)) / 1e6), "parallelism": "replicas" if world > 1 else "single"},
-        "fp64": {"value": fp64_value, "unit": "MLUPS", "steps": args.fp64_steps, "speedup_fp32": value / fp64_value},
-        "fp32_learned": learned,
-        "autotune": None if tune is None else {
-            "face": variant_names[fv], "cell": [n for n in variant_names if n.startswith("cell")][cv],
-            "ms_per_launch": tune["ms"],
-            "fp64": None if tune64 is None else {"face": tune64["face"], "cell": tune64["cell"]}},
-        "corrector": {"passes_per_face": face_passes / max(faces, 1), "status_ok": status_ok},
+        "fp32_learned_mlups": None if learned is None else learned["value"],
+        "fp64_mlups": fp64_value,
+        "hbm_frac_step": step_gbs / hbm_peak,
+        "passes_per_face": face_passes / max(faces, 1),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp32_peak, "traffic": FACE_KERNEL_DRAM_BYTES.get(fv),
-                     "kernel": "face_kernel<2,float> (%s)" % variant_names[fv],
+                     "frac": achieved / fp32_peak, "traffic": FACE_KERNEL_DRAM_BYTES.get(variant_names[fv]),
+                     "kernel": ("face_kernel<2,float> (%s)" % variant_names[fv]) if sv == 0 else
+                               ("step_kernel<2,float> (%s; faces and cell update)" % [nm for nm in variant_names if nm.startswith("step")][sv]),
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % sm_mhz,
                      "face_ms": face_ms_avg, "cell_ms": ms_cell / args.steps,
                      "hbm_gbs": face_gbs, "hbm_frac": face_gbs / hbm_peak,
+                     "step_hbm_gbs": step_gbs, "step_bytes_per_cell": STEP_BYTES_PER_CELL,
                      "hbm_peak": hbm_peak, "hbm_peak_source": pk_kind},
         "e2e": e2e,
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(pb, steps=20)
+        line["cpu_baseline"]["host"] = host_cpu()
+    line["fp64"] = {"value": fp64_value, "unit": "MLUPS", "steps": args.fp64_steps, "speedup_fp32": value / fp64_value}
+    line["fp32_learned"] = learned
+    line["corrector"] = {"passes_per_face": face_passes / max(faces, 1), "status_ok": status_ok}
+    line["autotune"] = None if tune is None else {
+        "face": variant_names[fv], "cell": [nm for nm in variant_names if nm.startswith("cell")][cv],
+        "step": [nm for nm in variant_names if nm.startswith("step")][sv],
+        "step_ms": {nm: round(ms, 4) for nm, ms in tune["ms"].items() if nm.startswith("step")},
+        "fp64": None if tune64 is None else {"face": tune64["face"], "cell": tune64["cell"]}}
+    line["sod_c1"] = bench_sod(args)
+    line["equilibration_ablation"] = bench_equilibration(pb)
+    if params is not None:
+        line.update(bench_interface_and_jet(args, params, hbm_peak))
     tubes = bench_tubes(args, rank=rank)
     tubes["hbm_frac"] = tubes["hbm_gbs"] / hbm_peak
     line["tubes"] = tubes
@@ -557,7 +808,8 @@ def main():
         line["sl_vs_fv"][leg]["sl"]["alu_frac"] = line["sl_vs_fv"][leg]["sl"]["tflops"] / fp32_peak
     line["d3q64"] = d3
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(pb, steps=20)
+        line["cpu_parallel"] = cpu_baseline_parallel(args.n, args.seed)
+        line["cpu_sod_c1"] = cpu_baseline_sod()
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

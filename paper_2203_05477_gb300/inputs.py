@@ -87,19 +87,26 @@ def sod_400():
     return shock_tube((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 1.4, 400, name="sod_400")
 
 
-def quadrants_2d(n, seed, gamma=1.4, mach_max=3.0):
+def quadrants_2d(n, seed, gamma=1.4, mach_max=3.0, direction="centre"):
     """2D four-quadrant Riemann problem on the unit square (n x n cells).
 
     Each quadrant draws rho and p log-uniform in [0.1, 10] and a Mach number uniform in
-    [0, mach_max]; its velocity points towards the domain centre within +-45 degrees, so
-    that neighbouring quadrants meet in shocks, contacts and slip lines."""
+    [0, mach_max].  direction "centre" (the workload): its velocity points towards the
+    domain centre within +-45 degrees, so that neighbouring quadrants meet in shocks,
+    contacts and slip lines.  direction "any": uniform in [0, 2 pi), which also makes
+    quadrants recede from one another."""
     rng = np.random.default_rng(seed)
     r4 = np.exp(rng.uniform(np.log(0.1), np.log(10.0), 4))
     p4 = np.exp(rng.uniform(np.log(0.1), np.log(10.0), 4))
     M = rng.uniform(0.0, mach_max, 4)
     cx = np.array([0.25, 0.75, 0.25, 0.75])
     cy = np.array([0.25, 0.25, 0.75, 0.75])
-    th = np.arctan2(0.5 - cy, 0.5 - cx) + rng.uniform(-np.pi / 4, np.pi / 4, 4)
+    if direction == "centre":
+        th = np.arctan2(0.5 - cy, 0.5 - cx) + rng.uniform(-np.pi / 4, np.pi / 4, 4)
+    elif direction == "any":
+        th = rng.uniform(0.0, 2.0 * np.pi, 4)
+    else:
+        raise ValueError(direction)
     c = np.sqrt(gamma * p4 / r4)
     u4, v4 = M * c * np.cos(th), M * c * np.sin(th)
     x = cell_centres(n, 0.0, 1.0)
