@@ -35,7 +35,7 @@ FALLBACK_HBM_GBS = 6800.0
 N_SMS, FP32_LANES = 152, 128
 # ncu dram read + write of one face-kernel launch at 1024^2, for the tile variants measured
 # on the current kernel (profiles/face_kernel_quadrants1024_fp32.md); other variants: null
-FACE_KERNEL_DRAM_BYTES = {}
+FACE_KERNEL_DRAM_BYTES = {"face 8x8 cells, 128 threads, 4 CTA/SM": 136.1e6 + 177.5e6}
 # FP32 operations (FMA = 2) of one corrector pass at one D2Q16 face (per-face overhead
 # included), from the ncu instruction counts of the scalar face kernel; used for the ALU
 # roofline.  The packed FP32x2 form of the same algorithm executes ~4% more (differences
