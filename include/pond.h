@@ -280,7 +280,7 @@ pond_status pond_mlp_gradient(const float *params, const float *x, int ldx, cons
  * device-wide synchronization cudaMalloc/cudaFree imply, or code on a path where a failed
  * allocation cannot be handled.  Inputs and outputs are as for pond_mlp_gradient (device
  * arrays owned by the caller).  The activation scratch lives in a fixed device array of
- * the library sized for POND_MLP_NOALLOC_MAX_ROWS rows (about 5 MB, held by every GPU that
+ * the library sized for POND_MLP_NOALLOC_MAX_ROWS rows (about 6.6 MB, held by every GPU that
  * loads the library until the process exits); n above that limit returns
  * POND_ERR_INVALID_ARG.  Every call looks up that array's device address in the current
  * context (no allocation); the first call on a device also sets the kernels' shared-memory

@@ -1429,16 +1429,23 @@ pond_status gauge_collect_impl(pond_state *s, int64_t n_steps, float *pairs, int
     return POND_OK;
 }
 
-// activation scratch of a training minibatch of `rows` rows: out, H1, H2, dOut, dZ1, dZ2
+// scratch of a training minibatch of `rows` rows: the activations out, H1, H2, dOut, dZ1,
+// dZ2, and the partial weight gradients of the split batch
+constexpr size_t kWgradPartBytes = size_t(pond::mlp::kWgradMaxSplit) * pond::mlp::kParams * 4;
 struct TrainScratch {
     float *out;
     __nv_bfloat16 *H1, *H2, *dOut, *dZ1, *dZ2;
-    static size_t bytes(int64_t rows) { return size_t(rows) * (16 * 4 + 2 * (64 + 64 + 16 + 64 + 64)) + 1024; }
+    float *part;
+    static constexpr size_t bytes(int64_t rows)
+    {
+        return size_t(rows) * (16 * 4 + 2 * (64 + 64 + 16 + 64 + 64)) + 1024 + kWgradPartBytes + 256;
+    }
     static TrainScratch carve(char *base, int64_t rows)
     {
         TrainScratch t;
         size_t off = 0;
         auto take = [&](size_t b) { size_t o = off; off = align_up(off + b, 256); return base + o; };
+        t.part = reinterpret_cast<float *>(take(kWgradPartBytes));
         t.out = reinterpret_cast<float *>(take(size_t(rows) * 64));
         t.H1 = reinterpret_cast<__nv_bfloat16 *>(take(size_t(rows) * 128));
         t.H2 = reinterpret_cast<__nv_bfloat16 *>(take(size_t(rows) * 128));
@@ -1457,7 +1464,10 @@ pond_status mlp_grad_launch(const float *prm, const float *x, int ldx, const flo
     const unsigned tiles = unsigned((n + M::kRows - 1) / M::kRows);
     M::tile_kernel<<<tiles, M::kThreads, M::kTileSmem, st>>>(prm, x, ldx, y, ldy, n, t.out, t.H1, t.H2, t.dOut, t.dZ1,
                                                                t.dZ2, loss, err);
-    M::wgrad_kernel<<<3, M::kThreads, 0, st>>>(x, ldx, t.H1, t.H2, t.dOut, t.dZ1, t.dZ2, n, grad, err);
+    const int nsplit = M::wgrad_splits(n);
+    M::wgrad_kernel<<<dim3(3, unsigned(nsplit)), M::kThreads, 0, st>>>(x, ldx, t.H1, t.H2, t.dOut, t.dZ1, t.dZ2, n, t.part,
+                                                                          err);
+    M::wgrad_reduce_kernel<<<(M::kParams + 255) / 256, 256, 0, st>>>(t.part, nsplit, grad, err);
     CUDA_TRY(cudaGetLastError());
     return POND_OK;
 }
@@ -1516,7 +1526,7 @@ pond_status pond_gauge_train(pond_state *s, const float *pairs, int64_t n, int e
             const float bc1 = 1.f - std::pow(b1, float(s->adam_t)), bc2 = 1.f - std::pow(b2, float(s->adam_t));
             M::adam_kernel<<<(M::kParams + 255) / 256, 256, 0, s->stream>>>(s->mlp, s->mlp_grad, s->mlp_m, s->mlp_v, lr, b1,
                                                                              b2, eps, bc1, bc2);
-            s->launches += 3;
+            s->launches += 4;   // tile, weight-gradient, reduction and Adam kernels
         }
         CUDA_TRY(cudaGetLastError());
         float l = 0.f;
@@ -1704,7 +1714,7 @@ namespace {
 // Scratch of pond_mlp_gradient_noalloc: the activations of up to POND_MLP_NOALLOC_MAX_ROWS
 // rows, followed by the error word.  In host code this name only stands for the symbol;
 // its device address comes from cudaGetSymbolAddress for the current device.
-constexpr size_t kNoallocScratch = align_up(size_t(POND_MLP_NOALLOC_MAX_ROWS) * (16 * 4 + 2 * (64 + 64 + 16 + 64 + 64)) + 1024, 256) + 256;
+constexpr size_t kNoallocScratch = align_up(TrainScratch::bytes(POND_MLP_NOALLOC_MAX_ROWS), 256) + 256;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratch];
 
 constexpr int kMaxDevices = 64;

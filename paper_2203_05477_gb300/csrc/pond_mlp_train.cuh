@@ -83,14 +83,30 @@ tile_kernel(const float *prm, const float *x, int ldx, const float *y, int ldy, 
     if (threadIdx.x < 32) tc::tmem_free(tmem, 128);
 }
 
-// Weight gradients, one CTA per matrix: dW[o][i] = sum_b A[b][o] B[b][i] over the batch,
-// with (A, B) = (dZ1, X), (dZ2, H1), (dOut, H2); bias gradients are the column sums of A.
-// The batch is consumed in chunks of 64 rows as the K dimension of D[128 x N] += A^T B.
+// Weight gradients: dW[o][i] = sum_b A[b][o] B[b][i] over the batch, with (A, B) = (dZ1, X),
+// (dZ2, H1), (dOut, H2), and bias gradients as the column sums of A.  CTA (which, split)
+// takes one matrix and one of nsplit contiguous ranges of 64-row chunks, which it consumes as
+// the K dimension of D[128 x N] += A^T B on the tensor cores, and writes its partial
+// gradient to part[split][kParams]; wgrad_reduce_kernel then sums the partials in split
+// order, so the result does not depend on scheduling.
+constexpr int kWgradChunk = 64;
+constexpr int kWgradMaxSplit = 48;
+
+// how many row ranges a batch of n rows is split into: at least four 64-row chunks each
+__host__ __device__ inline int wgrad_splits(long long n)
+{
+    const long long chunks = (n + kWgradChunk - 1) / kWgradChunk;
+    long long s = chunks / 4;
+    if (s < 1) s = 1;
+    if (s > kWgradMaxSplit) s = kWgradMaxSplit;
+    return int(s);
+}
+
 __global__ void __launch_bounds__(kThreads)
 wgrad_kernel(const float *x, int ldx, const __nv_bfloat16 *H1, const __nv_bfloat16 *H2, const __nv_bfloat16 *dOut,
-             const __nv_bfloat16 *dZ1, const __nv_bfloat16 *dZ2, long long n, float *grad, unsigned int *err)
+             const __nv_bfloat16 *dZ1, const __nv_bfloat16 *dZ2, long long n, float *part, unsigned int *err)
 {
-    constexpr int KC = 64;
+    constexpr int KC = kWgradChunk;
     __shared__ __align__(1024) unsigned char sA[kRows * KC * 2];
     __shared__ __align__(1024) unsigned char sB[kHid * KC * 2];
     __shared__ uint64_t mbar;
@@ -99,6 +115,9 @@ wgrad_kernel(const float *x, int ldx, const __nv_bfloat16 *H1, const __nv_bfloat
     // untouched (the call reports POND_ERR_TIMEOUT)
     if (*(volatile unsigned int *)err) return;
     const int which = blockIdx.x;  // 0: W1, 1: W2, 2: W3
+    const int split = blockIdx.y, nsplit = gridDim.y;
+    const long long nchunks = (n + KC - 1) / KC;
+    const long long c_begin = nchunks * split / nsplit, c_end = nchunks * (split + 1) / nsplit;
     const int Mr = which == 2 ? kOutP : kHid;
     const int N = which == 0 ? kIn : kHid;
     const int lda = which == 2 ? kOutP : kHid;
@@ -106,6 +125,14 @@ wgrad_kernel(const float *x, int ldx, const __nv_bfloat16 *H1, const __nv_bfloat
     const __nv_bfloat16 *Bh = which == 1 ? H1 : H2;
     const int ow = which == 0 ? oW1 : which == 1 ? oW2 : oW3;
     const int ob = which == 0 ? ob1 : which == 1 ? ob2 : ob3;
+    float *grad = part + size_t(split) * kParams;
+    if (c_begin >= c_end) {   // an empty range contributes zero
+        if (threadIdx.x < Mr) {
+            for (int i = 0; i < N; ++i) grad[ow + threadIdx.x * N + i] = 0.f;
+            grad[ob + threadIdx.x] = 0.f;
+        }
+        return;
+    }
     if (threadIdx.x < 32) tc::tmem_alloc(&tmem_base, 64);
     if (threadIdx.x == 0) tc::mbar_init(&mbar, 1);
     tc::fence_before_sync();
@@ -115,7 +142,8 @@ wgrad_kernel(const float *x, int ldx, const __nv_bfloat16 *H1, const __nv_bfloat
     uint32_t phase = 0;
     bool ok = true;
     float bsum = 0.f;
-    for (long long b0 = 0; b0 < n && ok; b0 += KC) {
+    for (long long ci = c_begin; ci < c_end && ok; ++ci) {
+        const long long b0 = ci * KC;
         // A^T chunk: row o (output unit, padded to 128), column k (sample b0 + k)
         for (int e = threadIdx.x; e < kRows * KC; e += blockDim.x) {
             const int o = e / KC, k = e % KC;
@@ -132,7 +160,7 @@ wgrad_kernel(const float *x, int ldx, const __nv_bfloat16 *H1, const __nv_bfloat
         }
         if (threadIdx.x < Mr)
             for (int k = 0; k < KC && b0 + k < n; ++k) bsum += __bfloat162float(A[(b0 + k) * lda + threadIdx.x]);
-        ok = run_gemm(tmem, sA, sB, KC, N, &mbar, phase, b0 > 0);
+        ok = run_gemm(tmem, sA, sB, KC, N, &mbar, phase, ci > c_begin);
     }
     if (ok) {
         float v[kHid];
@@ -148,6 +176,16 @@ wgrad_kernel(const float *x, int ldx, const __nv_bfloat16 *H1, const __nv_bfloat
     tc::fence_before_sync();
     __syncthreads();
     if (threadIdx.x < 32) tc::tmem_free(tmem, 64);
+}
+
+// grad[p] = sum over the splits of part[split][p], in split order (nothing on an error)
+__global__ void wgrad_reduce_kernel(const float *part, int nsplit, float *grad, const unsigned int *err)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= kParams || *(const volatile unsigned int *)err) return;
+    float acc = 0.f;
+    for (int sp = 0; sp < nsplit; ++sp) acc += part[size_t(sp) * kParams + p];
+    grad[p] = acc;
 }
 
 __global__ void adam_kernel(float *prm, const float *g, float *m, float *v, float lr, float b1, float b2, float eps,
