@@ -80,15 +80,93 @@ def peaks():
         return {"hbm_gbs": FALLBACK_HBM_GBS, "sm_max_mhz": 2070.0}, "fallback"
 
 
-class ClockSampler:
-    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+class _NvmlPoller:
+    """Reads the SM clock and the clock-event reasons through NVML's C API every millisecond
+    from a thread, so that a timed region of a few milliseconds still gets samples (the
+    nvidia-smi loop samples every 100 ms at best).  Read-only queries; None if NVML is not
+    loadable."""
 
-    def __init__(self, index, interval_ms=100):
-        self.index = index
+    SM = 1  # NVML_CLOCK_SM
+    # clock-event reason bits of the NVML API
+    BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20,
+            "hw_thermal_slowdown": 0x40, "hw_power_brake_slowdown": 0x80}
+
+    def __init__(self, index, period_s=0.001):
+        import ctypes
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        if isinstance(index, str):
+            rc = self.lib.nvmlDeviceGetHandleByUUID(index.encode(), ctypes.byref(self.h))
+        else:
+            rc = self.lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(self.h))
+        if rc != 0:
+            raise RuntimeError("no NVML handle for device %s" % index)
+        try:
+            self.reasons_fn = self.lib.nvmlDeviceGetCurrentClocksEventReasons
+        except AttributeError:
+            self.reasons_fn = self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        mx = ctypes.c_uint(0)
+        self.max_mhz = float(mx.value) if self.lib.nvmlDeviceGetMaxClockInfo(self.h, self.SM, ctypes.byref(mx)) == 0 else None
+        self.period = period_s
+        self.samples = []
+        self.stop = threading.Event()
+        self.thread = threading.Thread(target=self._run, daemon=True)
+
+    def read(self):
+        c, r = self.ct.c_uint(0), self.ct.c_ulonglong(0)
+        if self.lib.nvmlDeviceGetClockInfo(self.h, self.SM, self.ct.byref(c)) != 0:
+            return None
+        if self.reasons_fn(self.h, self.ct.byref(r)) != 0:
+            return None
+        return float(c.value), int(r.value)
+
+    def _run(self):
+        while not self.stop.is_set():
+            v = self.read()
+            if v is not None:
+                self.samples.append(v)
+            time.sleep(self.period)
+
+    def start(self):
+        self.thread.start()
+
+    def finish(self):
+        self.stop.set()
+        self.thread.join(timeout=2.0)
+        self.lib.nvmlShutdown()
+
+
+class ClockSampler:
+    """Samples the SM clock and throttle reasons while the timed region runs: NVML polled in
+    process every millisecond (the samples reported), and the nvidia-smi loop beside it,
+    whose samples are used when NVML cannot be loaded."""
+
+    def __init__(self, local, interval_ms=100):
+        self.index = self.device_id(local)
         self.interval_ms = interval_ms
         self.proc = None
         self.lines = []
         self.skip = 0
+        self.nvml = None
+
+    @staticmethod
+    def device_id(local):
+        """The CUDA device's UUID ("GPU-..."), which nvidia-smi and NVML accept whatever
+        CUDA_VISIBLE_DEVICES says; else the index that CUDA_VISIBLE_DEVICES maps it to."""
+        try:
+            import torch
+            u = str(torch.cuda.get_device_properties(local).uuid)
+            if u:
+                return u if u.startswith("GPU-") else "GPU-" + u
+        except Exception:
+            pass
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")
+        if local < len(vis) and vis[local].strip().isdigit():
+            return int(vis[local])
+        return local
 
     def __enter__(self):
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -108,6 +186,11 @@ class ClockSampler:
             self.skip = len(self.lines)
         except Exception:
             self.proc = None
+        try:
+            self.nvml = _NvmlPoller(self.index)
+            self.nvml.start()
+        except Exception:
+            self.nvml = None
         return self
 
     def _read(self):
@@ -115,6 +198,8 @@ class ClockSampler:
             self.lines.append(line.strip())
 
     def __exit__(self, *a):
+        if self.nvml:
+            self.nvml.finish()
         if self.proc:
             self.proc.terminate()
             try:
@@ -124,7 +209,16 @@ class ClockSampler:
 
     def summary(self, sm_max_default):
         """Median SM clock and the throttle reasons seen in the samples taken during the timed
-        region (the samples before it when the region was shorter than one interval)."""
+        region: NVML's when it was loadable, else nvidia-smi's (the samples before the region
+        when the region was shorter than one interval)."""
+        if self.nvml and self.nvml.samples:
+            sm = [c for c, _ in self.nvml.samples]
+            reasons = sorted(nm for nm, bit in _NvmlPoller.BITS.items()
+                             if any(r & bit for _, r in self.nvml.samples))
+            return {"sm_mhz": statistics.median(sm), "sm_min_mhz": min(sm),
+                    "sm_max_mhz": self.nvml.max_mhz or sm_max_default, "reasons": reasons,
+                    "samples": len(sm), "samples_in_region": len(sm),
+                    "source": "NVML polled in process every 1 ms during the timed region"}
         sms, maxs, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         in_region = self.lines[self.skip:]
@@ -143,7 +237,7 @@ class ClockSampler:
         if not sms:
             return {"sm_mhz": None, "sm_max_mhz": sm_max_default, "reasons": ["unsampled"]}
         return {"sm_mhz": statistics.median(sms), "sm_max_mhz": max(maxs), "reasons": sorted(reasons),
-                "samples": len(sms), "samples_in_region": len(in_region)}
+                "samples": len(sms), "samples_in_region": len(in_region), "source": "nvidia-smi -lms %d" % self.interval_ms}
 
 
 def cpu_baseline(pb_full, steps, target_s=12.0):
