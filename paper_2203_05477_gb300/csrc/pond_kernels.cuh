@@ -545,6 +545,49 @@ __device__ __forceinline__ FastEq<R> fast_eq(const R *A)
     return q;
 }
 
+// Per-thread scratch in shared memory (FP32, 2D): the two centre cells' coefficients in the
+// corrector frame (f: 10, g: 6 each; slots 0-7) and the pass's moment sums (slots 8-11),
+// 16-byte slots, thread-minor so that a warp's accesses are contiguous.  They are touched
+// once per normal node, so keeping them out of the registers across the node loop lowers
+// the kernel's register demand.  The accesses are
+// volatile so that the compiler neither hoists the loads out of the node loop nor moves
+// them ahead of the stores.
+struct FaceScratch {
+    float4 *p;      // this thread's slot 0
+    int stride;     // slots apart, in float4 (the block's thread count)
+    __device__ __forceinline__ void put(int slot, float a, float b, float c, float d) const
+    {
+        const unsigned addr = (unsigned)__cvta_generic_to_shared(p + slot * stride);
+        asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(a), "f"(b), "f"(c), "f"(d)
+                     : "memory");
+    }
+    __device__ __forceinline__ float4 get(int slot) const
+    {
+        const unsigned addr = (unsigned)__cvta_generic_to_shared(p + slot * stride);
+        float4 v;
+        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                     : "r"(addr) : "memory");
+        return v;
+    }
+    // f (10) and g (6) coefficients of one cell in slots base .. base + 3
+    __device__ __forceinline__ void store(int base, const float *F, const float *G) const
+    {
+        put(base + 0, F[0], F[1], F[2], F[3]);
+        put(base + 1, F[4], F[5], F[6], F[7]);
+        put(base + 2, F[8], F[9], G[0], G[1]);
+        put(base + 3, G[2], G[3], G[4], G[5]);
+    }
+    __device__ __forceinline__ void load(int base, float *F, float *G) const
+    {
+        const float4 a = get(base + 0), b = get(base + 1), c = get(base + 2), d = get(base + 3);
+        F[0] = a.x; F[1] = a.y; F[2] = a.z; F[3] = a.w;
+        F[4] = b.x; F[5] = b.y; F[6] = b.z; F[7] = b.w;
+        F[8] = c.x; F[9] = c.y; G[0] = c.z; G[1] = c.w;
+        G[2] = d.x; G[3] = d.y; G[4] = d.z; G[5] = d.w;
+    }
+};
+__host__ __device__ constexpr int face_scratch_slots(int level) { return level > 1 ? 12 : 8; }
+
 // One corrector pass at a face (Sec. III.B.3) in frame (dl, Tl) (velocity relative to the
 // face reference uref): every stencil cell's phi-bar-plus is re-expressed in that frame,
 // limited slopes are formed per population, each population is reconstructed by MUSCL
@@ -553,11 +596,15 @@ __device__ __forceinline__ FastEq<R> fast_eq(const R *A)
 // Stencil slots: 0 LL, 1 L, 2 R, 3 RR, 4 L-t, 5 L+t, 6 R-t, 7 R+t (t: tangential).
 // EQ: the stencil cells are moved into the frame by the equilibration alternative
 // (FastEq), so their populations also carry the fast components.
-template <int D, typename R, bool EQ = false>
+// SCR (FP32, 2D): 1, the centre cells' coefficients wait in the thread's shared scratch
+// between the nodes; 2, the moment sums Phi, Psi also accumulate there (same arithmetic,
+// same order).
+template <int D, typename R, bool EQ = false, int SCR = 0>
 __device__ __forceinline__ void corrector_pass(const Stencil<D, R> &cells, const R *dref,
                                                const R *dl, R Tl, R un_abs, R ut_abs, R h_dn, R h_dt,
-                                               int limiter, R *Phi, R *Psi)
+                                               int limiter, R *Phi, R *Psi, FaceScratch scr = FaceScratch{nullptr, 0})
 {
+    static_assert(!SCR || (D == 2 && sizeof(R) == 4 && !EQ), "the scratch variants are FP32 2D Grad passes");
     constexpr int NFC = NCoef<D, 3>::value, NGC = NCoef<D, 2>::value;
     const R invTl = w_rcp<R>(Tl);
     const R rsqTl = w_sqrt<R>(invTl);
@@ -583,10 +630,15 @@ __device__ __forceinline__ void corrector_pass(const Stencil<D, R> &cells, const
         shift_scale<D, 3, R, true>(tmp, X, Y, FR);
         shift_scale<D, 2, R>(tmpg, X, Y, GR);
     }
+    if constexpr (SCR > 0) {
+        scr.store(0, reinterpret_cast<const float *>(FL), reinterpret_cast<const float *>(GL));
+        scr.store(4, reinterpret_cast<const float *>(FR), reinterpret_cast<const float *>(GR));
+    }
 #pragma unroll
     for (int k = 0; k < NFC; ++k) Phi[k] = R(0);
 #pragma unroll
     for (int k = 0; k < NGC; ++k) Psi[k] = R(0);
+    if constexpr (SCR > 1) scr.store(8, reinterpret_cast<const float *>(Phi), reinterpret_cast<const float *>(Psi));
 
     const NodeTab<R> &tab = node_tab<R>();
     // normal node m: its populations, limited slopes and MUSCL values, summed into the
@@ -670,10 +722,12 @@ __device__ __forceinline__ void corrector_pass(const Stencil<D, R> &cells, const
             };
             constexpr int NGB = EQ ? 4 : 3;   // columns of the g collapse
             R CL[4], CR[4], DL[NGB], DR[NGB];
-            collapse_f(FL, CL); collapse_f(FR, CR); collapse_g(GL, DL); collapse_g(GR, DR);
-            if constexpr (EQ) {
-                collapse_fast(FL, 3, CL); collapse_fast(FR, 3, CR);
-                collapse_fast(GL, 2, DL); collapse_fast(GR, 2, DR);
+            if constexpr (SCR == 0) {
+                collapse_f(FL, CL); collapse_f(FR, CR); collapse_g(GL, DL); collapse_g(GR, DR);
+                if constexpr (EQ) {
+                    collapse_fast(FL, 3, CL); collapse_fast(FR, 3, CR);
+                    collapse_fast(GL, 2, DL); collapse_fast(GR, 2, DR);
+                }
             }
             // outer normal neighbour (q = 0) and tangential neighbours (q = 1, 2) of the
             // upwind cell: transformed into the frame and collapsed one at a time
@@ -699,6 +753,14 @@ __device__ __forceinline__ void corrector_pass(const Stencil<D, R> &cells, const
                     collapse_fast(tr, 3, CS[q]);
                     collapse_fast(trg, 2, DS[q]);
                 }
+            }
+            if constexpr (SCR > 0) {
+                // the centre cells from the scratch, after the neighbours (fewer live values)
+                float Fs[10], Gs[6];
+                scr.load(0, Fs, Gs);
+                collapse_f(Fs, CL); collapse_g(Gs, DL);
+                scr.load(4, Fs, Gs);
+                collapse_f(Fs, CR); collapse_g(Gs, DR);
             }
             R Cu[4], Cl[4], Ch[4], Du[NGB], Dl[NGB], Dh[NGB];
 #pragma unroll
@@ -754,9 +816,20 @@ __device__ __forceinline__ void corrector_pass(const Stencil<D, R> &cells, const
                 for (int b2 = 0; a2 + b2 <= 2; ++b2) Psi[hidx(a2, b2)] += tab.whe[m][a2] * SG[b2];
         }
     };
+    // SCR 2: the node adds its moments to the sums waiting in the scratch
+    auto node_scr = [&](const int m) {
+        if constexpr (SCR > 1) {
+            scr.load(8, reinterpret_cast<float *>(Phi), reinterpret_cast<float *>(Psi));
+            node(m);
+            scr.store(8, reinterpret_cast<const float *>(Phi), reinterpret_cast<const float *>(Psi));
+        }
+    };
     if constexpr (D == 1) {
 #pragma unroll
         for (int m = 0; m < 4; ++m) node(m);
+    } else if constexpr (SCR > 1) {
+#pragma unroll 1
+        for (int m = 0; m < 4; ++m) node_scr(m);
     } else {
 #pragma unroll 1
         for (int m = 0; m < 4; ++m) node(m);
@@ -796,6 +869,15 @@ struct FaceCfg {
     int limiter, max_iter, fixed_iters;
 };
 
+// a[k], k = 0 or 1, of a small register array by a select: an index known only at run time
+// would put the array in local memory
+template <typename T, int N>
+__device__ __forceinline__ T sel(const T (&a)[N], int k)
+{
+    if constexpr (N == 1) return a[0];
+    else return k ? a[1] : a[0];
+}
+
 template <int D, typename R>
 struct FaceOut {
     R F[NCoef<D, 3>::value];   // f, g coefficients of phi(x_b, t_{n+1/2}) in the face frame (x, y order)
@@ -816,9 +898,10 @@ struct FaceOut {
 // no frame restarts the corrector once from the frame of the pooled moments of the
 // stencil, else the corrector stops at the last pass that did.  The face populations are
 // Eq. (FluxTransf) at the frame of the last valid pass's moments.
-template <int D, typename R, bool EQ = false>
+template <int D, typename R, bool EQ = false, int SCR = 0>
 __device__ __forceinline__ void solve_face(const Stencil<D, R> &cells, bool swap, const R *dref, const R *uabs,
-                                           R Tpred, const FaceCfg<R> &cfg, FaceOut<D, R> &o)
+                                           R Tpred, const FaceCfg<R> &cfg, FaceOut<D, R> &o,
+                                           FaceScratch scr = FaceScratch{nullptr, 0})
 {
     o.fallbacks = 0;
     constexpr int NCELL = D == 2 ? 8 : 4;
@@ -838,8 +921,8 @@ __device__ __forceinline__ void solve_face(const Stencil<D, R> &cells, bool swap
     int iters = 0;
     R Phi[NFC], Psi[NGC];
     for (int k = 0; k < cfg.max_iter && !done; ++k) {
-        corrector_pass<D, R, EQ>(cells, dref, dl, Tl, uref_n + dl[0], D == 2 ? uref_t + dl[D - 1] : R(0),
-                             h_dn, h_dt, cfg.limiter, Phi, Psi);
+        corrector_pass<D, R, EQ, SCR>(cells, dref, dl, Tl, uref_n + dl[0], D == 2 ? uref_t + dl[D - 1] : R(0),
+                                      h_dn, h_dt, cfg.limiter, Phi, Psi, scr);
         R rho1, du[D], T1;
         const bool ok = pass_frame<D, R>(Phi, Psi, Tl, Cv, rho1, du, T1);
         iters = k + 1;
@@ -895,8 +978,9 @@ __device__ __forceinline__ void solve_face(const Stencil<D, R> &cells, bool swap
     if (have) {
         if (!last_valid) {
             // the last pass defined no frame: recompute the last valid one
-            corrector_pass<D, R, EQ>(cells, dref, keep_dl, keep_T, uref_n + keep_dl[0],
-                                 D == 2 ? uref_t + keep_dl[D - 1] : R(0), h_dn, h_dt, cfg.limiter, Phi, Psi);
+            corrector_pass<D, R, EQ, SCR>(cells, dref, keep_dl, keep_T, uref_n + keep_dl[0],
+                                          D == 2 ? uref_t + keep_dl[D - 1] : R(0), h_dn, h_dt, cfg.limiter, Phi,
+                                          Psi, scr);
         }
         // Eq. (FluxTransf) in the frame of the last valid pass's moments, with the exact
         // co-moving equilibria there: phi = (2 tau phibar + h phi^eq)/(2 tau + h)
@@ -917,8 +1001,13 @@ __device__ __forceinline__ void solve_face(const Stencil<D, R> &cells, bool swap
         for (int k = 1; k < NGC; ++k) Go[k] = wb * Go[k];
         orient<D, 3, R>(Fo, o.F, swap);
         orient<D, 2, R>(Go, o.G, swap);
-        o.du[na] = keep_dl[0] + out_du[0];
-        if constexpr (D == 2) o.du[ta] = keep_dl[1] + out_du[1];
+        if constexpr (D == 2) {
+            const R dn = keep_dl[0] + out_du[0], dt = keep_dl[1] + out_du[1];
+            o.du[0] = na ? dt : dn;
+            o.du[1] = na ? dn : dt;
+        } else {
+            o.du[0] = keep_dl[0] + out_du[0];
+        }
         o.T = out_T;
     }
 }
@@ -934,10 +1023,11 @@ __host__ __device__ __forceinline__ long long pred_tiles(const Params<D, R> &P)
 // Tile variants of the face kernel: TX x TY cells per CTA (one thread per x face and one
 // per y face in 2D, one per face in 1D) and MINB CTAs per SM for the register budget.  The
 // autotuner picks one per problem.
-template <int D, int TX_, int TY_, int MINB_>
+template <int D, int TX_, int TY_, int MINB_, int SCR_ = 0>
 struct FaceVariant {
     static constexpr int TX = TX_, TY = D == 2 ? TY_ : 1, MINB = MINB_;
     static constexpr int THREADS = D == 2 ? 2 * TX_ * TY_ : TX_;
+    static constexpr int SCR = SCR_;   // shared scratch level of the corrector (FP32 2D, not EQUIL)
 };
 
 // Instantiations (MODE): FACE_PLAIN; FACE_COLLECT also writes (features, converged frame)
@@ -962,6 +1052,8 @@ face_kernel(const Params<D, R> P)
     __shared__ StagedCell<D, R> tile[BY * BX];
     __shared__ StagedCell<D, R> tileT[D == 2 ? BY * BX : 1];
     __shared__ W utile[D];
+    constexpr int SCR = D == 2 && sizeof(R) == 4 && MODE != FACE_EQUIL ? V::SCR : 0;
+    __shared__ float4 scratch[SCR ? face_scratch_slots(SCR) * V::THREADS : 1];
 
     const Clock &K = *P.clock;
     if (!(K.dt > 0.0)) return;  // t_end reached: the step is a no-op
@@ -1039,11 +1131,11 @@ face_kernel(const Params<D, R> P)
         const R Tp = R(fr_lead(Tpw));
         const int na = swap ? 1 : 0, ta = 1 - na;
         R dref[D], uabs[D];
-        dref[0] = R(fr_rel(uref[na], utile[na]));
-        uabs[0] = R(fr_lead(uref[na]));
+        dref[0] = R(fr_rel(sel(uref, na), utile[na]));
+        uabs[0] = R(fr_lead(sel(uref, na)));
         if constexpr (D == 2) {
-            dref[1] = R(fr_rel(uref[ta], utile[ta]));
-            uabs[1] = R(fr_lead(uref[ta]));
+            dref[1] = R(fr_rel(sel(uref, ta), utile[ta]));
+            uabs[1] = R(fr_lead(sel(uref, ta)));
         }
         // With the learned predictor on, the corrector starts from the network's prediction
         // and keeps that result only if it converges without a restart; otherwise the face
@@ -1075,15 +1167,16 @@ face_kernel(const Params<D, R> P)
 #pragma unroll
             for (int a = 0; a < D; ++a) { dw[a] = dref[a]; uw[a] = uabs[a]; }
             if (from_learned) {
-                dw[0] = R(fr_rel(lrn[na], utile[na]));
-                uw[0] = R(fr_lead(lrn[na]));
+                dw[0] = R(fr_rel(sel(lrn, na), utile[na]));
+                uw[0] = R(fr_lead(sel(lrn, na)));
                 if constexpr (D == 2) {
-                    dw[1] = R(fr_rel(lrn[ta], utile[ta]));
-                    uw[1] = R(fr_lead(lrn[ta]));
+                    dw[1] = R(fr_rel(sel(lrn, ta), utile[ta]));
+                    uw[1] = R(fr_lead(sel(lrn, ta)));
                 }
                 Tw = R(fr_lead(lrn[D]));
             }
-            solve_face<D, R, EQUIL>(cells, swap, dw, uw, Tw, cfg, o);
+            solve_face<D, R, EQUIL, SCR>(cells, swap, dw, uw, Tw, cfg, o,
+                                         FaceScratch{scratch + (SCR ? threadIdx.x : 0), int(V::THREADS)});
             tot_iters += o.iters;
             tot_fallbacks += o.fallbacks;
             if (from_learned && o.have && o.done && o.fallbacks == 0) {
@@ -1117,8 +1210,8 @@ face_kernel(const Params<D, R> P)
 #pragma unroll
                     for (int q = 0; q < mlp::kIn; ++q) row[q] = f[q];
                     const double rs = 1.0 / sqrt(double(Tp));
-                    row[mlp::kIn + 0] = float(double(o.du[na]) * rs);
-                    row[mlp::kIn + 1] = float(double(o.du[ta]) * rs);
+                    row[mlp::kIn + 0] = float(double(sel(o.du, na)) * rs);
+                    row[mlp::kIn + 1] = float(double(sel(o.du, ta)) * rs);
                     row[mlp::kIn + 2] = float(log(double(o.T) / double(Tp)));
                     row[mlp::kIn + 3] = float(o.iters);
                 }
@@ -1558,11 +1651,11 @@ step_kernel(const Params<D, R> P)
         const R Tp = R(fr_lead(Frm[D * nf + fidx]));
         const int na = swap ? 1 : 0, ta = 1 - na;
         R dref[D], uabs[D];
-        dref[0] = R(fr_rel(uref[na], utile[na]));
-        uabs[0] = R(fr_lead(uref[na]));
+        dref[0] = R(fr_rel(sel(uref, na), utile[na]));
+        uabs[0] = R(fr_lead(sel(uref, na)));
         if constexpr (D == 2) {
-            dref[1] = R(fr_rel(uref[ta], utile[ta]));
-            uabs[1] = R(fr_lead(uref[ta]));
+            dref[1] = R(fr_rel(sel(uref, ta), utile[ta]));
+            uabs[1] = R(fr_lead(sel(uref, ta)));
         }
         FaceOut<D, R> o;
         solve_face<D, R>(cells, swap, dref, uabs, Tp, cfg, o);
