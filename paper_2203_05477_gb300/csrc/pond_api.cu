@@ -166,6 +166,7 @@ pond_status setup(pond_state *s)
     P.tol_r = R(P.tol);
     P.max_iter = s->opts.max_iter;
     P.fixed_iters = s->opts.fixed_iters;
+    P.sms = s->sms;
     const long long n = P.ncell(), nxf = P.nxf(), nyf = D == 2 ? P.nyf() : 0;
     using W = typename P_t::W;
     constexpr int NFC = P_t::NFC, NGC = P_t::NGC, NFS = P_t::NFS;
@@ -1105,6 +1106,8 @@ pond_status pond_init(const pond_grid *grid, pond_velset velset, double gamma, d
     s->tau = tau;
     cudaError_t e = cudaGetDevice(&s->device);
     if (e != cudaSuccess) { delete s; return fail(POND_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e)); }
+    e = cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device);
+    if (e != cudaSuccess) { delete s; return fail(POND_ERR_CUDA, "cudaDeviceGetAttribute: %s", cudaGetErrorString(e)); }
     if (opts->stream) {
         s->stream = static_cast<cudaStream_t>(opts->stream);
     } else {
@@ -1179,6 +1182,8 @@ pond_status pond_init3(const pond_grid3 *grid, double gamma, double tau, const p
     s->tau = tau;
     cudaError_t e = cudaGetDevice(&s->device);
     if (e != cudaSuccess) { delete s; return fail(POND_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e)); }
+    e = cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device);
+    if (e != cudaSuccess) { delete s; return fail(POND_ERR_CUDA, "cudaDeviceGetAttribute: %s", cudaGetErrorString(e)); }
     if (opts->stream) {
         s->stream = static_cast<cudaStream_t>(opts->stream);
     } else {
@@ -1358,6 +1363,8 @@ pond_status pond_init_batch(int64_t n_tubes, const int64_t *lengths, const doubl
     s->n_tubes = n_tubes;
     cudaError_t e = cudaGetDevice(&s->device);
     if (e != cudaSuccess) { delete s; return fail(POND_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e)); }
+    e = cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device);
+    if (e != cudaSuccess) { delete s; return fail(POND_ERR_CUDA, "cudaDeviceGetAttribute: %s", cudaGetErrorString(e)); }
     if (opts->stream) {
         s->stream = static_cast<cudaStream_t>(opts->stream);
     } else {

@@ -198,6 +198,7 @@ struct Params {
     float gauge_trust;                // ... and does not exceed this (the corrector's basin of the
                                       // previous frame; larger moves may reach another fixed point)
     unsigned int *mlp_err;
+    int sms;                          // SMs of the device (grid sizes of the grid-stride kernels)
     __host__ __device__ long long ncell() const { return nx * ny; }
     __host__ __device__ long long nxf() const { return (nx + 1) * ny; }
     __host__ __device__ long long nyf() const { return nx * (ny + 1); }
@@ -1340,41 +1341,62 @@ __device__ __forceinline__ void add_face_flux(const R *Fc, const R *Gc, const R 
 
 // CFL rate of a cell frame: max over axes of (|u_a| + sqrt(T/T_L) max|c|)/dx_a, in the
 // working precision (FP32 populations: the rate in FP32 is enough)
+// v through a volatile move: the compiler treats the result as unknown at every use, so
+// nothing derived from it is hoisted out of a loop
+__device__ __forceinline__ long long opaque(long long v)
+{
+    long long r;
+    asm volatile("mov.b64 %0, %1;" : "=l"(r) : "l"(v));
+    return r;
+}
+
 template <typename R>
-__device__ __forceinline__ double cell_rate(const R *u, R T, R inv_dx, R inv_dy, int D)
+__device__ __forceinline__ R cell_rate_r(const R *u, R T, R inv_dx, R inv_dy, int D)
 {
     const R c = sqrt(T) * R(kCHi);
     R r = (fabs(u[0]) + c) * inv_dx;
     if (D == 2) r = max(r, (fabs(u[1]) + c) * inv_dy);
-    return double(r);
+    return r;
+}
+template <typename R>
+__device__ __forceinline__ double cell_rate(const R *u, R T, R inv_dx, R inv_dy, int D)
+{
+    return double(cell_rate_r<R>(u, T, inv_dx, inv_dy, D));
 }
 
 // block max of a non-negative double, then the last block turns the grid max into the
 // next time step (CFL condition, clipped to t_end) and advances the clock
+// Non-negative doubles order like their bit patterns, so the maximum is taken on the
+// patterns with integer operations (no FP64 instructions).  Only thread 0 waits for the
+// grid-wide atomics; the other warps leave after the block's maximum is formed.
+__device__ __forceinline__ unsigned long long warp_max_bits(unsigned long long b)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long x = __shfl_down_sync(0xffffffffu, b, o);
+        b = x > b ? x : b;
+    }
+    return b;
+}
 __device__ __forceinline__ void reduce_rate_and_advance(Clock *clock, double rate, bool advance)
 {
-    __shared__ double red[32];
-    __shared__ bool last;
-    double r = rate;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_down_sync(0xffffffffu, r, o));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = r;
+    __shared__ unsigned long long red[32];
+    unsigned long long b = (unsigned long long)__double_as_longlong(rate);
+    if (b > 0x7ff0000000000000ull) b = 0ull;   // a NaN (or a negative) rate counts as none
+    b = warp_max_bits(b);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = b;
     __syncthreads();
-    if (threadIdx.x < 32) {
-        const int nw = (blockDim.x + 31) >> 5;
-        r = threadIdx.x < nw ? red[threadIdx.x] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_down_sync(0xffffffffu, r, o));
-        if (threadIdx.x == 0) {
-            // non-negative doubles order like their bit patterns
-            atomicMax(&clock->rate_bits, (unsigned long long)__double_as_longlong(r));
-            __threadfence();
-            const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
-            last = atomicAdd(&clock->blocks_done, 1u) == nb - 1;
-        }
+    if (threadIdx.x >= 32) return;
+    const int nw = (blockDim.x + 31) >> 5;
+    b = warp_max_bits(threadIdx.x < nw ? red[threadIdx.x] : 0ull);
+    bool last = false;
+    if (threadIdx.x == 0) {
+        atomicMax(&clock->rate_bits, b);
+        __threadfence();
+        const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
+        last = atomicAdd(&clock->blocks_done, 1u) == nb - 1;
     }
-    __syncthreads();
-    if (last && threadIdx.x == 0) {
+    if (last) {
         __threadfence();
         const double rmax = __longlong_as_double((long long)atomicAdd(&clock->rate_bits, 0ull));
         double t = clock->t;
@@ -1437,7 +1459,7 @@ __device__ __forceinline__ bool cell_finish(const R *H, const R *G, R invTc, R s
 // increments formed from the Hermite moments relative to the old frame (u' = u + du,
 // T' = T (1 + dT/T)), so no kinetic energy of the frame enters.
 // EQ: the face populations enter the cell frame by the equilibration alternative (Sec. II.C).
-template <int D, typename R, int THREADS, int MINB = 1, bool EQ = false>
+template <int D, typename R, int THREADS, int MINB = 1, bool EQ = false, bool GS = false>
 __global__ void __launch_bounds__(THREADS, MINB)
 cell_kernel(const Params<D, R> P)
 {
@@ -1445,11 +1467,13 @@ cell_kernel(const Params<D, R> P)
     const Clock &K = *P.clock;
     if (!(K.dt > 0.0)) return;
     const long long n = P.ncell();
-    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    double rate = 0.0;
+    R rate = R(0);
     using W = typename FrameWords<R>::word;
     const StepC<R> &KC = step_c<R>(K);
-    if (c < n) {
+    auto update = [&](const long long c) {
+        // GS: the plane strides pass through an opaque copy, so that the compiler forms the
+        // planes' offsets per cell instead of holding them all in registers across cells
+        const long long n = GS ? opaque(P.ncell()) : P.ncell();
         const long long i = c % P.nx, j = c / P.nx;
         W uc[D];
 #pragma unroll
@@ -1471,7 +1495,7 @@ cell_kernel(const Params<D, R> P)
         for (int k = 0; k < NGC; ++k) G[k] = ca * P.sg[k * n + c];
         G[0] += cb * (Cv - R(0.5 * D)) * rho * Tcr;
         // fluxes through the 2D faces
-        const long long nxf = P.nxf();
+        const long long nxf = GS ? opaque(P.nxf()) : P.nxf();
         const R sx = KC.dt_dx;
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
@@ -1487,7 +1511,7 @@ cell_kernel(const Params<D, R> P)
             add_face_flux<D, R, EQ>(Fc, Gc, dv, Tb, Tcr, invTc, rsqTc, 0, side ? sx : -sx, sqTc, R(fr_lead(uc[0])), H, G);
         }
         if constexpr (D == 2) {
-            const long long nyf = P.nyf();
+            const long long nyf = GS ? opaque(P.nyf()) : P.nyf();
             const R sy = KC.dt_dy;
 #pragma unroll
             for (int side = 0; side < 2; ++side) {
@@ -1530,9 +1554,17 @@ cell_kernel(const Params<D, R> P)
 #pragma unroll
         for (int a = 0; a < D; ++a) P.sfr[a * n + c] = un[a];
         P.sfr[D * n + c] = Tn;
-        rate = ok ? cell_rate<R>(unr, Tnr, KC.inv_dx, KC.inv_dy, D) : 0.0;
+        if (ok) rate = max(rate, cell_rate_r<R>(unr, Tnr, KC.inv_dx, KC.inv_dy, D));
+    };
+    const long long c0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if constexpr (GS) {
+        // grid-stride over the cells (the launch caps the grid), so that the block's rate
+        // reduction and the time-step atomics serve several cells per thread
+        for (long long c = c0; c < n; c += (long long)gridDim.x * blockDim.x) update(c);
+    } else if (c0 < n) {
+        update(c0);
     }
-    reduce_rate_and_advance(P.clock, rate, true);
+    reduce_rate_and_advance(P.clock, double(rate), true);
 }
 
 // ------------------------------------------------------------ fused step

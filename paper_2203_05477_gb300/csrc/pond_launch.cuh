@@ -127,9 +127,10 @@ void launch_step_fused(int v, const Params<D, R> &P, cudaStream_t st);
 
 // ---------------------------------------------------------------- cell kernel
 
-constexpr int kCellBlocks[7] = {256, 128, 512, 256, 256, 128, 32};
-constexpr int kCellMinBlocks[7] = {1, 1, 1, 3, 4, 6, 1};   // CTAs per SM asked of the register allocator
-constexpr int kCellVariants = 7;
+constexpr int kCellBlocks[9] = {256, 128, 512, 256, 256, 128, 32, 128, 128};
+constexpr int kCellMinBlocks[9] = {1, 1, 1, 3, 4, 6, 1, 3, 1};   // CTAs per SM asked of the register allocator
+constexpr bool kCellGridStride[9] = {false, false, false, false, false, false, false, true, true};
+constexpr int kCellVariants = 9;
 
 template <int D, typename R>
 void launch_cell(int v, const Params<D, R> &P, cudaStream_t st);
@@ -149,8 +150,9 @@ inline void launch_cell_any(int v, const Params<D, R> &P, cudaStream_t st)
 inline void cell_name(int v, char *buf, size_t n)
 {
     const int k = (v >= 0 && v < kCellVariants) ? v : 0;
-    if (kCellMinBlocks[k] > 1) std::snprintf(buf, n, "cell %d threads, %d CTA/SM", kCellBlocks[k], kCellMinBlocks[k]);
-    else std::snprintf(buf, n, "cell %d threads", kCellBlocks[k]);
+    const char *gs = kCellGridStride[k] ? ", grid-stride" : "";
+    if (kCellMinBlocks[k] > 1) std::snprintf(buf, n, "cell %d threads, %d CTA/SM%s", kCellBlocks[k], kCellMinBlocks[k], gs);
+    else std::snprintf(buf, n, "cell %d threads%s", kCellBlocks[k], gs);
 }
 
 // ---------------------------------------------------------------- tube kernel

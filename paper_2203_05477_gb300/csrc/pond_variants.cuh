@@ -49,7 +49,14 @@ void launch_cell(int v, const Params<D, R> &P, cudaStream_t st)
 {
     const long long n = P.ncell();
     auto blocks = [&](int t) { return unsigned((n + t - 1) / t); };
+    // grid-stride variants: at most one wave at full thread occupancy (2048 threads per SM)
+    auto gs_blocks = [&](int t) {
+        const long long need = (n + t - 1) / t, cap = (long long)(P.sms > 0 ? P.sms : 1) * (2048 / t);
+        return unsigned(need < cap ? need : cap);
+    };
     switch (v) {
+    case 7: cell_kernel<D, R, 128, 3, false, true><<<gs_blocks(128), 128, 0, st>>>(P); break;
+    case 8: cell_kernel<D, R, 128, 1, false, true><<<gs_blocks(128), 128, 0, st>>>(P); break;
     case 1: cell_kernel<D, R, 128><<<blocks(128), 128, 0, st>>>(P); break;
     case 2: cell_kernel<D, R, 512><<<blocks(512), 512, 0, st>>>(P); break;
     case 3: cell_kernel<D, R, 256, 3><<<blocks(256), 256, 0, st>>>(P); break;

@@ -35,7 +35,7 @@ def test_every_grid_variant_matches_oracle_fp64(name, pb):
     os_.step(4)
     gs = gpu_for(pb, precision="fp64", **KW64)
     nf, nc, ns = split(gs.variants())
-    assert nf >= 3 and nc == 7 and ns >= 2
+    assert nf >= 3 and nc == 9 and ns >= 2
     for f in range(nf):
         for c in range(nc):
             if f and c != f % nc:
