@@ -1057,34 +1057,13 @@ face_kernel(const Params<D, R> P)
     __shared__ float4 scratch[SCR ? face_scratch_slots(SCR) * V::THREADS : 1];
 
     const Clock &K = *P.clock;
-    if (!(K.dt > 0.0)) return;  // t_end reached: the step is a no-op
+    // t_end reached (dt = 0): the step is a no-op; tested after the staging loads, so that
+    // this load's latency overlaps theirs
+    const double step_dt = K.dt;
     const StepC<R> &KC = step_c<R>(K);
     const R cp = KC.cp, ce = KC.ce;
 
     const long long i0 = (long long)blockIdx.x * TX, j0 = (long long)blockIdx.y * TY;
-    // reference velocity of the tile: staged velocities are differences from it
-    if (threadIdx.x == 0) cell_velocity<D, R>(P, i0, j0, utile);
-    __syncthreads();
-    // stage phi-bar-plus of the box [i0-2, i0+TX] x [j0-2, j0+TY] (1D: [i0-2, i0+TX])
-    for (int t = threadIdx.x; t < BX * BY; t += blockDim.x) {
-        const int bx = t % BX, by = t / BX;
-        const long long ci = i0 - 2 + bx, cj = D == 2 ? j0 - 2 + by : 0;
-        if constexpr (D == 2) {
-            StagedCell<D, R> c;
-            load_cell_bar_plus<D, R>(P, ci, cj, cp, ce, utile, c);
-            tile[t] = c;
-            StagedCell<D, R> ct;
-            orient<D, 3, R>(c.A, ct.A, true);
-            orient<D, 2, R>(c.B, ct.B, true);
-            ct.du[0] = c.du[1];
-            ct.du[1] = c.du[0];
-            ct.T = c.T;
-            tileT[bx * BY + by] = ct;
-        } else {
-            load_cell_bar_plus<D, R>(P, ci, cj, cp, ce, utile, tile[t]);
-        }
-    }
-    __syncthreads();
 
     // face of this thread
     int dir = 0, tx = threadIdx.x, ty = 0;
@@ -1099,6 +1078,43 @@ face_kernel(const Params<D, R> P)
     long long fidx;
     if (dir == 0) { active = fi <= P.nx && fj < P.ny; fidx = fj * (P.nx + 1) + fi; }
     else { active = fi < P.nx && fj <= P.ny; fidx = fj * P.nx + fi; }
+    W *Frm = dir == 0 ? P.xfr : P.yfr;
+    const long long nf = dir == 0 ? P.nxf() : P.nyf();
+    // the face's predictor frame, loaded before the staging so that the loads overlap
+    W uref[D], Tpw;
+#pragma unroll
+    for (int a = 0; a < D; ++a) uref[a] = active ? Frm[a * nf + fidx] : fr_word(R(0));
+    Tpw = active ? Frm[D * nf + fidx] : fr_word(R(1));
+
+    // reference velocity of the tile (staged velocities are differences from it): every
+    // thread reads it (the same words), so the staging needs no barrier before it
+    W ut[D];
+    cell_velocity<D, R>(P, i0, j0, ut);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) utile[a] = ut[a];
+    }
+    // stage phi-bar-plus of the box [i0-2, i0+TX] x [j0-2, j0+TY] (1D: [i0-2, i0+TX])
+    for (int t = threadIdx.x; t < BX * BY; t += blockDim.x) {
+        const int bx = t % BX, by = t / BX;
+        const long long ci = i0 - 2 + bx, cj = D == 2 ? j0 - 2 + by : 0;
+        if constexpr (D == 2) {
+            StagedCell<D, R> c;
+            load_cell_bar_plus<D, R>(P, ci, cj, cp, ce, ut, c);
+            tile[t] = c;
+            StagedCell<D, R> ct;
+            orient<D, 3, R>(c.A, ct.A, true);
+            orient<D, 2, R>(c.B, ct.B, true);
+            ct.du[0] = c.du[1];
+            ct.du[1] = c.du[0];
+            ct.T = c.T;
+            tileT[bx * BY + by] = ct;
+        } else {
+            load_cell_bar_plus<D, R>(P, ci, cj, cp, ce, ut, tile[t]);
+        }
+    }
+    if (!(step_dt > 0.0)) return;   // the same value in every thread
+    __syncthreads();
 
     unsigned long long my_iters = 0, my_nonconv = 0, my_fallbacks = 0, my_nonphys = 0;
     if (active) {
@@ -1117,18 +1133,12 @@ face_kernel(const Params<D, R> P)
         }
         R *Fout = dir == 0 ? P.xf : P.yf;
         R *Gout = dir == 0 ? P.xg : P.yg;
-        W *Frm = dir == 0 ? P.xfr : P.yfr;
-        const long long nf = dir == 0 ? P.nxf() : P.nyf();
-        W uref[D];
-#pragma unroll
-        for (int a = 0; a < D; ++a) uref[a] = Frm[a * nf + fidx];
         FaceOut<D, R> o;
         FaceCfg<R> cfg;
         cfg.h_dn = swap ? KC.h_dy : KC.h_dx;
         cfg.h_dt = D == 2 ? (swap ? KC.h_dx : KC.h_dy) : R(0);
         cfg.Cv = P.Cv_r; cfg.tol = P.tol_r; cfg.wb = KC.wb; cfg.we = KC.we;
         cfg.limiter = P.limiter; cfg.max_iter = P.max_iter; cfg.fixed_iters = P.fixed_iters;
-        const W Tpw = Frm[D * nf + fidx];
         const R Tp = R(fr_lead(Tpw));
         const int na = swap ? 1 : 0, ta = 1 - na;
         R dref[D], uabs[D];
