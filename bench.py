@@ -35,7 +35,10 @@ FALLBACK_HBM_GBS = 6800.0
 N_SMS, FP32_LANES = 152, 128
 # ncu dram read + write of one face-kernel launch at 1024^2, for the tile variants measured
 # on the current kernel (profiles/face_kernel_quadrants1024_fp32.md); other variants: null
-FACE_KERNEL_DRAM_BYTES = {"face 8x8 cells, 128 threads, 4 CTA/SM": 136.1e6 + 177.5e6}
+FACE_KERNEL_DRAM_BYTES = {
+    "face 8x8 cells, 128 threads, 4 CTA/SM, centre cells in shared scratch": 134.708e6 + 136.232e6,
+    "face 8x8 cells, 128 threads, 4 CTA/SM, centre cells and moment sums in shared scratch": 134.678e6 + 136.447e6,
+}
 # FP32 operations (FMA = 2) of one corrector pass at one D2Q16 face (per-face overhead
 # included), from the ncu instruction counts of the scalar face kernel; used for the ALU
 # roofline.  The packed FP32x2 form of the same algorithm executes ~4% more (differences
@@ -691,6 +694,8 @@ def main():
                     help="tubes / d3q64 / sl / learned: only that measurement (profiling cases)")
     ap.add_argument("--d3-n", type=int, default=128, help="cells per side of the D3Q64 measurement")
     ap.add_argument("--c4-steps", type=int, default=200, help="timed steps of the 4096 x 1024 interface leg")
+    ap.add_argument("--face-variant", default=None,
+                    help="run the headline with this face-kernel variant (its full name) instead of the tuner's")
     ap.add_argument("--quick", action="store_true",
                     help="FP32 timed steps only (no e2e, FP64 or CPU legs): the profiling case")
     args = ap.parse_args()
@@ -751,6 +756,9 @@ def main():
     tune = None if args.no_tune else s.autotune(steps=3, cache=args.tune_cache)
     fv, cv, sv = (tune["face"], tune["cell"], tune["tube"]) if tune else (0, 0, 0)
     variant_names = s.variants()
+    if args.face_variant is not None:
+        fv = variant_names.index(args.face_variant)
+        s.set_variants(fv, cv, sv)
     s.step(args.warmup)
     d0 = s.sync()
     l0 = s.launch_count()
