@@ -179,7 +179,7 @@ tube_kernel(const TubeParams<R> P, int steps, int cur0)
                 const R dref[1] = {R(fr_rel(fu_in[f_off + k], utile))};
                 const R uabs[1] = {R(fr_lead(fu_in[f_off + k]))};
                 FaceOut<1, R> o;
-                solve_face<1, R>(cells, false, dref, uabs, R(fT_in[f_off + k]), cfg, o);
+                solve_face<1, R, false, 0, false>(cells, false, dref, uabs, R(fT_in[f_off + k]), cfg, o);
                 const bool owned = f < nc || k == L;
                 if (owned) {
                     my_iters += o.iters;

@@ -600,7 +600,7 @@ __host__ __device__ constexpr int face_scratch_slots(int level) { return level >
 // SCR (FP32, 2D): 1, the centre cells' coefficients wait in the thread's shared scratch
 // between the nodes; 2, the moment sums Phi, Psi also accumulate there (same arithmetic,
 // same order).
-template <int D, typename R, bool EQ = false, int SCR = 0>
+template <int D, typename R, bool EQ = false, int SCR = 0, bool OUTER_ONCE = true>
 __device__ __forceinline__ void corrector_pass(const Stencil<D, R> &cells, const R *dref,
                                                const R *dl, R Tl, R un_abs, R ut_abs, R h_dn, R h_dt,
                                                int limiter, R *Phi, R *Psi, FaceScratch scr = FaceScratch{nullptr, 0})
@@ -640,6 +640,22 @@ __device__ __forceinline__ void corrector_pass(const Stencil<D, R> &cells, const
 #pragma unroll
     for (int k = 0; k < NGC; ++k) Psi[k] = R(0);
     if constexpr (SCR > 1) scr.store(8, reinterpret_cast<const float *>(Phi), reinterpret_cast<const float *>(Psi));
+    // 1D, OUTER_ONCE: the outer neighbours LL and RR in the frame, once per pass (each node
+    // takes the one on its upwind side); else each node transforms its own (fewer live
+    // registers, for kernels that run at a register cap)
+    R FLL[D == 1 ? NFC : 1], GLL[D == 1 ? NGC : 1], FRR[D == 1 ? NFC : 1], GRR[D == 1 ? NGC : 1];
+    if constexpr (D == 1 && OUTER_ONCE) {
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            const StagedCell<D, R> sc = fetch<D, R>(cells[side ? 3 : 0]);
+            R dcs[1];
+            rel_velocity<D, R>(&sc, dref, false, dcs);
+            Map1<R> X(R(1), R(0), R(0)), Y(R(1), R(0), R(0));
+            cell_maps<D, R>(sc.T, dcs, Tl, invTl, rsqTl, dl, X, Y);
+            shift_scale<D, 3, R, true>(sc.A, X, Y, side ? FRR : FLL);
+            shift_scale<D, 2, R>(sc.B, X, Y, side ? GRR : GLL);
+        }
+    }
 
     const NodeTab<R> &tab = node_tab<R>();
     // normal node m: its populations, limited slopes and MUSCL values, summed into the
@@ -651,11 +667,16 @@ __device__ __forceinline__ void corrector_pass(const Stencil<D, R> &cells, const
         // departure point along the normal, in cells, from the upwind cell centre
         const R offn = (left ? R(0.5) : R(-0.5)) - vn * h_dn;
         if constexpr (D == 1) {
-            // outer normal neighbour of the upwind cell, in the frame
+            // outer normal neighbour of the upwind cell, in the frame (chosen by selects so
+            // that no array is indexed at run time)
             R FS[NFC], GS[NGC];
             R gL3 = R(0), gR3 = R(0), gS3 = R(0);   // fast g components at node m (EQ)
-            {
-                // slot 0 or 3, chosen by selects so that no array is indexed at run time
+            if constexpr (OUTER_ONCE) {
+#pragma unroll
+                for (int k = 0; k < NFC; ++k) FS[k] = left ? FLL[k] : FRR[k];
+#pragma unroll
+                for (int k = 0; k < NGC; ++k) GS[k] = left ? GLL[k] : GRR[k];
+            } else {
                 const StagedCell<D, R> sc = fetch<D, R>(left ? cells[0] : cells[3]);
                 R dcs[1];
                 rel_velocity<D, R>(&sc, dref, false, dcs);
@@ -899,7 +920,7 @@ struct FaceOut {
 // no frame restarts the corrector once from the frame of the pooled moments of the
 // stencil, else the corrector stops at the last pass that did.  The face populations are
 // Eq. (FluxTransf) at the frame of the last valid pass's moments.
-template <int D, typename R, bool EQ = false, int SCR = 0>
+template <int D, typename R, bool EQ = false, int SCR = 0, bool OUTER_ONCE = true>
 __device__ __forceinline__ void solve_face(const Stencil<D, R> &cells, bool swap, const R *dref, const R *uabs,
                                            R Tpred, const FaceCfg<R> &cfg, FaceOut<D, R> &o,
                                            FaceScratch scr = FaceScratch{nullptr, 0})
@@ -922,7 +943,7 @@ __device__ __forceinline__ void solve_face(const Stencil<D, R> &cells, bool swap
     int iters = 0;
     R Phi[NFC], Psi[NGC];
     for (int k = 0; k < cfg.max_iter && !done; ++k) {
-        corrector_pass<D, R, EQ, SCR>(cells, dref, dl, Tl, uref_n + dl[0], D == 2 ? uref_t + dl[D - 1] : R(0),
+        corrector_pass<D, R, EQ, SCR, OUTER_ONCE>(cells, dref, dl, Tl, uref_n + dl[0], D == 2 ? uref_t + dl[D - 1] : R(0),
                                       h_dn, h_dt, cfg.limiter, Phi, Psi, scr);
         R rho1, du[D], T1;
         const bool ok = pass_frame<D, R>(Phi, Psi, Tl, Cv, rho1, du, T1);
@@ -979,7 +1000,7 @@ __device__ __forceinline__ void solve_face(const Stencil<D, R> &cells, bool swap
     if (have) {
         if (!last_valid) {
             // the last pass defined no frame: recompute the last valid one
-            corrector_pass<D, R, EQ, SCR>(cells, dref, keep_dl, keep_T, uref_n + keep_dl[0],
+            corrector_pass<D, R, EQ, SCR, OUTER_ONCE>(cells, dref, keep_dl, keep_T, uref_n + keep_dl[0],
                                           D == 2 ? uref_t + keep_dl[D - 1] : R(0), h_dn, h_dt, cfg.limiter, Phi,
                                           Psi, scr);
         }
@@ -1700,7 +1721,7 @@ step_kernel(const Params<D, R> P)
             uabs[1] = R(fr_lead(sel(uref, ta)));
         }
         FaceOut<D, R> o;
-        solve_face<D, R>(cells, swap, dref, uabs, Tp, cfg, o);
+        solve_face<D, R, false, 0, sizeof(R) == 4>(cells, swap, dref, uabs, Tp, cfg, o);
         if (owned) {
             my_iters += o.iters;
             my_faces += 1;
