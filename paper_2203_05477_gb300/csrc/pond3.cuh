@@ -720,22 +720,40 @@ face3_kernel(const Params3<R> P)
     __shared__ W utile[3];
 
     const Clock &K = *P.clock;
-    if (!(K.dt > 0.0)) return;
+    // t_end reached (dt = 0): the step is a no-op; tested after the staging loads, so that
+    // this load's latency overlaps theirs
+    const double step_dt = K.dt;
     const StepC<R> &KC = step_c<R>(K);
     const long long i0 = (long long)blockIdx.x * TX, j0 = (long long)blockIdx.y * TY, k0 = (long long)blockIdx.z * TZ;
-    if (threadIdx.x == 0) cell_velocity3<R>(P, i0, j0, k0, utile);
-    __syncthreads();
-    for (int t = threadIdx.x; t < BX * BY * BZ; t += blockDim.x) {
-        const int bx = t % BX, by = (t / BX) % BY, bz = t / (BX * BY);
-        load_cell3<R>(P, i0 - 2 + bx, j0 - 2 + by, k0 - 2 + bz, KC.cp, KC.ce, utile, tile[t]);
-    }
-    __syncthreads();
 
     const int dir = threadIdx.x / (TX * TY * TZ);
     const int tl = threadIdx.x - dir * TX * TY * TZ;
     const int tx = tl % TX, ty = (tl / TX) % TY, tz = tl / (TX * TY);
     const long long fi = i0 + tx, fj = j0 + ty, fk = k0 + tz;
     const bool active = fi < P.nx + (dir == 0) && fj < P.ny + (dir == 1) && fk < P.nz + (dir == 2);
+    const long long nf = P.nf(dir), f = active ? P.fidx(dir, fi, fj, fk) : 0;
+    // selects: a run-time index into the parameter arrays would copy them to local memory
+    W *Frm = dir == 0 ? P.ffr[0] : (dir == 1 ? P.ffr[1] : P.ffr[2]);
+    // the face's predictor frame, loaded before the staging so that the loads overlap
+    W uref[3], Tpw;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) uref[a] = active ? Frm[a * nf + f] : fr_word(R(0));
+    Tpw = active ? Frm[3 * nf + f] : fr_word(R(1));
+    // the tile's reference velocity: every thread reads it (the same words), so the
+    // staging needs no barrier before it
+    W ut[3];
+    cell_velocity3<R>(P, i0, j0, k0, ut);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) utile[a] = ut[a];
+    }
+    for (int t = threadIdx.x; t < BX * BY * BZ; t += blockDim.x) {
+        const int bx = t % BX, by = (t / BX) % BY, bz = t / (BX * BY);
+        load_cell3<R>(P, i0 - 2 + bx, j0 - 2 + by, k0 - 2 + bz, KC.cp, KC.ce, ut, tile[t]);
+    }
+    if (!(step_dt > 0.0)) return;   // the same value in every thread
+    __syncthreads();
+
     unsigned long long my_iters = 0, my_nonconv = 0, my_fallbacks = 0, my_nonphys = 0;
     if (active) {
         FaceBox<R> box;
@@ -746,15 +764,9 @@ face3_kernel(const Params3<R> P)
         box.by = ty + 2;
         box.bz = tz + 2;
         box.dir = dir;
-        const long long nf = P.nf(dir), f = P.fidx(dir, fi, fj, fk);
-        // selects: a run-time index into the parameter arrays would copy them to local memory
         R *Fout = dir == 0 ? P.ff[0] : (dir == 1 ? P.ff[1] : P.ff[2]);
         R *Gout = dir == 0 ? P.fg[0] : (dir == 1 ? P.fg[1] : P.fg[2]);
-        W *Frm = dir == 0 ? P.ffr[0] : (dir == 1 ? P.ffr[1] : P.ffr[2]);
-        W uref[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) uref[a] = Frm[a * nf + f];
-        const R Tp = R(fr_lead(Frm[3 * nf + f]));
+        const R Tp = R(fr_lead(Tpw));
         // the predictor in face axes (selects: no run-time indexed array)
         const W un_w = dir == 0 ? uref[0] : (dir == 1 ? uref[1] : uref[2]);
         const W u1_w = dir == 0 ? uref[1] : uref[0];
