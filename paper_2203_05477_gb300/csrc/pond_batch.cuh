@@ -71,6 +71,16 @@ __device__ __forceinline__ void tube_stage(const TubeParams<R> &P, int cur, long
     o.T = T;
 }
 
+// volatile reads of a parked value (the compiler may not forward the stored registers)
+template <typename R>
+__device__ __forceinline__ R vload(const R *p) { return *reinterpret_cast<const volatile R *>(p); }
+__device__ __forceinline__ double vload_word(const double *p) { return vload(p); }
+__device__ __forceinline__ ffloat vload_word(const ffloat *p)
+{
+    const volatile float *q = reinterpret_cast<const volatile float *>(p);
+    return ffloat{q[0], q[1]};
+}
+
 // per-step constants of one tube (Eqs. FinalUpdateDUGKS, Fbarplus, FluxTransf), formed in
 // FP64 by one thread and kept in the working precision
 template <typename R>
@@ -95,6 +105,10 @@ tube_kernel(const TubeParams<R> P, int steps, int cur0)
     __shared__ R faceG[NW][kTubeChunk + 1][3];
     __shared__ R faceU[NW][kTubeChunk + 1], faceT[NW][kTubeChunk + 1];  // face frame: velocity relative to the chunk reference, T
     __shared__ TubeStep<R> ks;
+    // the raw state of the cell each lane stages and later updates, parked here across the
+    // face solves (read back with volatile loads) instead of held in registers
+    __shared__ R raw[NW][6][32];
+    __shared__ CellW raww[NW][2][32];
     __shared__ R red[NW];
     __shared__ int tube_bad;
 
@@ -107,7 +121,8 @@ tube_kernel(const TubeParams<R> P, int steps, int cur0)
     const double Cv = P.Cv[tube], dx = P.dx[tube];
     const double tau = P.tau;
     const R CvR = R(Cv), tolR = R(P.tol);
-    unsigned long long my_iters = 0, my_faces = 0, my_nonconv = 0, my_fallbacks = 0, my_nonphys = 0;
+    // per-thread counts (32-bit: a thread's counts over a call stay far below 2^32 / 32)
+    unsigned int my_iters = 0, my_faces = 0, my_nonconv = 0, my_fallbacks = 0, my_nonphys = 0;
     StagedCell<1, R> *wt = tile[warp];
 
     for (int step = 0; step < steps; ++step) {
@@ -165,6 +180,9 @@ tube_kernel(const TubeParams<R> P, int steps, int cur0)
                 o.du[0] = R(fr_rel(uc, utile));
                 o.T = Tcr;
             }
+            raw[warp][0][lane] = rho; raw[warp][1][lane] = a2; raw[warp][2][lane] = a3;
+            raw[warp][3][lane] = b0; raw[warp][4][lane] = b1; raw[warp][5][lane] = b2;
+            raww[warp][0][lane] = uc; raww[warp][1][lane] = Tc;
             if (lane < 2) tube_stage<R>(P, cur, c_off + min(c0 + kTubeChunk + lane, L - 1), Cvh, cp, ce, utile, wt[32 + lane]);
             __syncwarp();
             // faces c0 .. c0+nc: face k lies between cells k-1 and k; the last one is also the
@@ -219,6 +237,11 @@ tube_kernel(const TubeParams<R> P, int steps, int cur0)
             // lane l = 2 .. nc+1 updates the cell it staged, c0 + l - 2, between faces l-2 and l-1
             if (lane >= 2 && lane < nc + 2) {
                 const int t = lane - 2;
+                const R rho = vload(&raw[warp][0][lane]), a2 = vload(&raw[warp][1][lane]), a3 = vload(&raw[warp][2][lane]);
+                const R b0 = vload(&raw[warp][3][lane]), b1 = vload(&raw[warp][4][lane]), b2 = vload(&raw[warp][5][lane]);
+                const CellW uc = vload_word(&raww[warp][0][lane]), Tc = vload_word(&raww[warp][1][lane]);
+                const R Tcr = R(fr_lead(Tc));
+                const long long c = c_off + min(max(c0 - 2 + lane, 0), L - 1);
                 const R duc = wt[lane].du[0];
                 const R invTc = w_rcp<R>(Tcr), rsqTc = w_sqrt<R>(invTc), sqTc = Tcr * rsqTc;
                 R H[4], G[3];
@@ -291,10 +314,11 @@ tube_kernel(const TubeParams<R> P, int steps, int cur0)
         my_nonphys += __shfl_down_sync(0xffffffffu, my_nonphys, o);
     }
     if (lane == 0) {
-        if (my_faces) { atomicAdd(&P.diag->face_iters, my_iters); atomicAdd(&P.diag->face_solves, my_faces); }
-        if (my_nonconv) { atomicAdd(&P.diag->nonconv, my_nonconv); atomicOr(&P.diag->flags, FLAG_NOT_CONVERGED); }
-        if (my_fallbacks) atomicAdd(&P.diag->fallbacks, my_fallbacks);
-        if (my_nonphys) { atomicAdd(&P.diag->nonphys, my_nonphys); atomicOr(&P.diag->flags, FLAG_NONPHYSICAL); }
+        using U = unsigned long long;
+        if (my_faces) { atomicAdd(&P.diag->face_iters, U(my_iters)); atomicAdd(&P.diag->face_solves, U(my_faces)); }
+        if (my_nonconv) { atomicAdd(&P.diag->nonconv, U(my_nonconv)); atomicOr(&P.diag->flags, FLAG_NOT_CONVERGED); }
+        if (my_fallbacks) atomicAdd(&P.diag->fallbacks, U(my_fallbacks));
+        if (my_nonphys) { atomicAdd(&P.diag->nonphys, U(my_nonphys)); atomicOr(&P.diag->flags, FLAG_NONPHYSICAL); }
     }
 }
 
