@@ -356,6 +356,10 @@ def bench_tubes(args, n_tubes=4096, seed=0, rank=0):
     # tuned over the full step count: as tubes stop, the longest tubes set the launch's
     # length, so a short window from the initial state does not rank the variants right
     tune = None if args.no_tune else s.autotune(steps=args.tube_steps, cache=args.tune_cache)
+    tv = tune["tube"] if tune else 0
+    if args.tube_variant is not None:
+        tv = s.variants().index(args.tube_variant)
+        s.set_variants(0, 0, tv)
     s.step(max(1, args.warmup))
     d0 = s.sync()
     torch.cuda.synchronize()
@@ -373,7 +377,7 @@ def bench_tubes(args, n_tubes=4096, seed=0, rank=0):
            "launches": 1, "passes_per_face": (d1["face_iters"] - d0["face_iters"]) / max(1, d1["face_solves"] - d0["face_solves"]),
            "tubes_stopped": int(status.sum()), "cell_updates": updates,
            "note": "tubes that reach a non-physical state stop and are reported; throughput counts performed updates",
-           "variant": s.variants()[tune["tube"] if tune else 0], "autotune_ms": tune["ms"] if tune else None}
+           "variant": s.variants()[tv], "autotune_ms": tune["ms"] if tune else None}
     s.close()
     return out
 
@@ -694,6 +698,8 @@ def main():
                     help="tubes / d3q64 / sl / learned: only that measurement (profiling cases)")
     ap.add_argument("--d3-n", type=int, default=128, help="cells per side of the D3Q64 measurement")
     ap.add_argument("--c4-steps", type=int, default=200, help="timed steps of the 4096 x 1024 interface leg")
+    ap.add_argument("--tube-variant", default=None,
+                    help="run the tube workload with this tube-kernel variant (its full name) instead of the tuner's")
     ap.add_argument("--face-variant", default=None,
                     help="run the headline with this face-kernel variant (its full name) instead of the tuner's")
     ap.add_argument("--quick", action="store_true",
