@@ -395,7 +395,8 @@ def test_fp32_configurations_4_and_5_against_fp64_oracle(name, pb, steps):
     the bench's stopping rule against the FP64 oracle with the same rule: relative L1 of rho,
     p and speed within 1e-4, or within twice the oracle's own change when the pass limit
     moves by one where that is larger (faces that reach the limit without converging end on
-    an iterate that depends on where the iteration stops)."""
+    an iterate that depends on where the iteration stops); the steepest density jump of each
+    row and column within one cell of the oracle's."""
     kw = dict(tau=1e-5, cfl=0.2, tol=1e-6, max_iter=16)
     gs = gpu_for(pb, precision="fp32", **kw)
     gs.step(steps)
@@ -409,7 +410,19 @@ def test_fp32_configurations_4_and_5_against_fp64_oracle(name, pb, steps):
     def err(r, ux, uy, p):
         return max(rel_l1(r, ro), rel_l1(p, po), np.abs(np.hypot(ux, uy) - so).sum() / max(so.sum(), 1e-300))
 
-    e = err(*gpu_primitive(gs))
+    prim = gpu_primitive(gs)
+    e = err(*prim)
+    # shock positions: the steepest density jump of every row and every column, within one
+    # cell of the oracle's (rows or columns whose two steepest jumps are within 1% of each
+    # other have no unique position and are skipped)
+    r2, ro2 = prim[0].reshape(pb.ny, pb.nx), ro.reshape(pb.ny, pb.nx)
+    off = 0
+    for a, b in ((r2, ro2), (r2.T, ro2.T)):
+        g, go = np.abs(np.diff(a, axis=1)), np.abs(np.diff(b, axis=1))
+        top2 = np.sort(go, axis=1)[:, -2:]
+        unique = top2[:, 0] < 0.99 * top2[:, 1]
+        off = max(off, int(np.abs(np.argmax(g, axis=1) - np.argmax(go, axis=1))[unique].max(initial=0)))
+    assert off <= 1, off
     bound = 1e-4
     if os_.stats()["nonconverged"]:
         for mi in (15, 17):
