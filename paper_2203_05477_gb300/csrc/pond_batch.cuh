@@ -305,14 +305,11 @@ tube_kernel(const TubeParams<R> P, int steps, int cur0)
         if (tube_bad) break;  // a non-physical tube stops; pond_sync reports it
     }
     // warp-aggregated diagnostics
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        my_iters += __shfl_down_sync(0xffffffffu, my_iters, o);
-        my_faces += __shfl_down_sync(0xffffffffu, my_faces, o);
-        my_nonconv += __shfl_down_sync(0xffffffffu, my_nonconv, o);
-        my_fallbacks += __shfl_down_sync(0xffffffffu, my_fallbacks, o);
-        my_nonphys += __shfl_down_sync(0xffffffffu, my_nonphys, o);
-    }
+    my_iters = warp_sum_count(my_iters);
+    my_faces = warp_sum_count(my_faces);
+    my_nonconv = warp_sum_count(my_nonconv);
+    my_fallbacks = warp_sum_count(my_fallbacks);
+    my_nonphys = warp_sum_count(my_nonphys);
     if (lane == 0) {
         using U = unsigned long long;
         if (my_faces) { atomicAdd(&P.diag->face_iters, U(my_iters)); atomicAdd(&P.diag->face_solves, U(my_faces)); }

@@ -178,6 +178,14 @@ template <> __device__ __forceinline__ float w_sqrt<float>(float x)
 }
 template <> __device__ __forceinline__ float w_div<float>(float a, float b) { return a * w_rcp<float>(b); }
 
+// Sum of a small non-negative count over the 32 lanes of a warp (every lane calls it) in one
+// warp-reduce instruction; the warp's total must fit in 32 bits.
+template <typename T>
+__device__ __forceinline__ T warp_sum_count(T x)
+{
+    return T(__reduce_add_sync(0xffffffffu, (unsigned int)x));
+}
+
 // --------------------------------------------------------------------- limiters
 // Slope limiters of Sec. III.B.3 on one-sided differences a (upstream) and b (downstream).
 template <typename R>

@@ -1268,16 +1268,12 @@ face_kernel(const Params<D, R> P)
         }
     }
     // warp-aggregated diagnostics
-    const unsigned mask = 0xffffffffu;
     unsigned long long n_act = active ? 1ull : 0ull;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        my_iters += __shfl_down_sync(mask, my_iters, o);
-        my_nonconv += __shfl_down_sync(mask, my_nonconv, o);
-        my_fallbacks += __shfl_down_sync(mask, my_fallbacks, o);
-        my_nonphys += __shfl_down_sync(mask, my_nonphys, o);
-        n_act += __shfl_down_sync(mask, n_act, o);
-    }
+    my_iters = warp_sum_count(my_iters);
+    my_nonconv = warp_sum_count(my_nonconv);
+    my_fallbacks = warp_sum_count(my_fallbacks);
+    my_nonphys = warp_sum_count(my_nonphys);
+    n_act = warp_sum_count(n_act);
     if ((threadIdx.x & 31) == 0 && n_act) {
         atomicAdd(&P.diag->face_iters, my_iters);
         atomicAdd(&P.diag->face_solves, n_act);
@@ -1831,15 +1827,11 @@ step_kernel(const Params<D, R> P)
         if (ok) rate = cell_rate<R>(unr, Tnr, KC.inv_dx, KC.inv_dy, D);
     } while (false);
     // warp-aggregated diagnostics
-    const unsigned mask = 0xffffffffu;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        my_iters += __shfl_down_sync(mask, my_iters, o);
-        my_faces += __shfl_down_sync(mask, my_faces, o);
-        my_nonconv += __shfl_down_sync(mask, my_nonconv, o);
-        my_fallbacks += __shfl_down_sync(mask, my_fallbacks, o);
-        my_nonphys += __shfl_down_sync(mask, my_nonphys, o);
-    }
+    my_iters = warp_sum_count(my_iters);
+    my_faces = warp_sum_count(my_faces);
+    my_nonconv = warp_sum_count(my_nonconv);
+    my_fallbacks = warp_sum_count(my_fallbacks);
+    my_nonphys = warp_sum_count(my_nonphys);
     if ((threadIdx.x & 31) == 0) {
         if (my_faces) { atomicAdd(&P.diag->face_iters, my_iters); atomicAdd(&P.diag->face_solves, my_faces); }
         if (my_nonconv) { atomicAdd(&P.diag->nonconv, my_nonconv); atomicOr(&P.diag->flags, FLAG_NOT_CONVERGED); }

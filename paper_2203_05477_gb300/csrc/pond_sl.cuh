@@ -38,16 +38,12 @@ __device__ __forceinline__ void sl_diag_and_advance(Diag *diag, Clock *clock, bo
                                                     unsigned long long my_nonconv, unsigned long long my_fallbacks,
                                                     unsigned long long my_nonphys, double rate)
 {
-    const unsigned mask = 0xffffffffu;
     unsigned long long n_act = active ? 1ull : 0ull;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        my_iters += __shfl_down_sync(mask, my_iters, o);
-        my_nonconv += __shfl_down_sync(mask, my_nonconv, o);
-        my_fallbacks += __shfl_down_sync(mask, my_fallbacks, o);
-        my_nonphys += __shfl_down_sync(mask, my_nonphys, o);
-        n_act += __shfl_down_sync(mask, n_act, o);
-    }
+    my_iters = warp_sum_count(my_iters);
+    my_nonconv = warp_sum_count(my_nonconv);
+    my_fallbacks = warp_sum_count(my_fallbacks);
+    my_nonphys = warp_sum_count(my_nonphys);
+    n_act = warp_sum_count(n_act);
     if ((threadIdx.x & 31) == 0 && n_act) {
         atomicAdd(&diag->face_iters, my_iters);
         atomicAdd(&diag->face_solves, n_act);

@@ -395,8 +395,8 @@ def test_fp32_configurations_4_and_5_against_fp64_oracle(name, pb, steps):
     the bench's stopping rule against the FP64 oracle with the same rule: relative L1 of rho,
     p and speed within 1e-4, or within twice the oracle's own change when the pass limit
     moves by one where that is larger (faces that reach the limit without converging end on
-    an iterate that depends on where the iteration stops); the steepest density jump of each
-    row and column within one cell of the oracle's."""
+    an iterate that depends on where the iteration stops); where a row or column has one
+    clearly steepest density jump, the FP32 run's lies within one cell of the oracle's."""
     kw = dict(tau=1e-5, cfl=0.2, tol=1e-6, max_iter=16)
     gs = gpu_for(pb, precision="fp32", **kw)
     gs.step(steps)
@@ -412,17 +412,22 @@ def test_fp32_configurations_4_and_5_against_fp64_oracle(name, pb, steps):
 
     prim = gpu_primitive(gs)
     e = err(*prim)
-    # shock positions: the steepest density jump of every row and every column, within one
-    # cell of the oracle's (rows or columns whose two steepest jumps are within 1% of each
-    # other have no unique position and are skipped)
+    # shock positions: in every row and column where the oracle's steepest density jump
+    # stands out (every jump more than 3 cells away from it is below 80% of it), the FP32
+    # run's steepest jump lies within one cell of it
     r2, ro2 = prim[0].reshape(pb.ny, pb.nx), ro.reshape(pb.ny, pb.nx)
-    off = 0
+    off, used = 0, 0
     for a, b in ((r2, ro2), (r2.T, ro2.T)):
         g, go = np.abs(np.diff(a, axis=1)), np.abs(np.diff(b, axis=1))
-        top2 = np.sort(go, axis=1)[:, -2:]
-        unique = top2[:, 0] < 0.99 * top2[:, 1]
-        off = max(off, int(np.abs(np.argmax(g, axis=1) - np.argmax(go, axis=1))[unique].max(initial=0)))
-    assert off <= 1, off
+        for k in range(go.shape[0]):
+            i = int(np.argmax(go[k]))
+            rest = np.concatenate([go[k, :max(0, i - 3)], go[k, i + 4:]])
+            if rest.size and rest.max() >= 0.8 * go[k, i]:
+                continue
+            used += 1
+            off = max(off, abs(int(np.argmax(g[k])) - i))
+    print("%s: shock positions checked in %d rows and columns, largest offset %d" % (name, used, off))
+    assert used >= 10 and off <= 1, (used, off)
     bound = 1e-4
     if os_.stats()["nonconverged"]:
         for mi in (15, 17):
