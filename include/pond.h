@@ -116,6 +116,8 @@ typedef struct {
     int64_t nonphysical;        /* non-physical cells or faces */
     int64_t first_bad_cell;     /* index of the first non-physical cell, or -1 */
     uint32_t flags;             /* bit 0 non-physical, bit 1 not converged, bit 2 timeout */
+    int64_t staged_tma;         /* face-kernel tiles whose box was staged by tensor-map (TMA)
+                                   copies (the TMA variant of the D2Q16 FP32 face kernel) */
 } pond_diag;
 
 /* Creates a solver for the problem statement of the paper's benchmarks (Sec. IV): grid and

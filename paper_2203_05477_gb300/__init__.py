@@ -61,7 +61,7 @@ class pond_diag(ctypes.Structure):
                 ("face_solves", ctypes.c_int64), ("face_iters", ctypes.c_int64),
                 ("nonconverged", ctypes.c_int64), ("fallbacks", ctypes.c_int64),
                 ("nonphysical", ctypes.c_int64), ("first_bad_cell", ctypes.c_int64),
-                ("flags", ctypes.c_uint32)]
+                ("flags", ctypes.c_uint32), ("staged_tma", ctypes.c_int64)]
 
 
 POND_TUNE_MAX = 32

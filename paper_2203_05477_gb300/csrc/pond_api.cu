@@ -5,6 +5,8 @@
 // kernel launches (face corrector, cell update) that read the time step from the device,
 // so runs of steps are captured once into a CUDA graph and replayed.
 #include <cuda_runtime.h>
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
 #include <cstdarg>
 #include <cstdio>
@@ -110,6 +112,8 @@ struct pond_state {
     // kernel variants in use (indices into the lists of pond_launch.cuh), set by the autotuner;
     // on grids tube_v selects the step: 0 the face and cell kernels, k + 1 fused variant k
     int face_v = 0, cell_v = 0, tube_v = 0;
+    // tensor maps of the two state buffers for the TMA-staged face variant (D2Q16, FP32)
+    pond::StageMaps stage_maps[2] = {};
     // semi-Lagrangian scheme and fused steps: the state alternates between two sets of
     // planes; sl_parity counts the swaps, graph_parity is the parity a captured graph starts at
     int scheme = POND_FV;
@@ -138,6 +142,58 @@ void dev_free(pond_state *s, void *p)
     if (!p) return;
     if (s->opts.free) s->opts.free(p, s->opts.alloc_ctx);
     else cudaFree(p);
+}
+
+// cuTensorMapEncodeTiled from the driver, through the runtime (no link against libcuda)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// Tensor maps of the state planes (f: NFS planes, g: NGC planes, frame words: D + 1 planes)
+// of both state buffers, as [planes][ny][nx] tensors copied in boxes of kTmaBoxX x (TY + 3)
+// x planes for the 8 x 8 TMA face variant.  They need rows that are multiples of 16 bytes
+// (nx a multiple of 4); false (no maps, the variant stages per thread) otherwise or when the
+// driver refuses a map.
+template <typename R>
+bool encode_stage_maps(pond_state *s, long long nx, long long ny, const R *sf0, const R *sg0, const void *sfr0,
+                       const R *sf1, const R *sg1, const void *sfr1)
+{
+    constexpr int NFS = pond::Params<2, R>::NFS, NGC = pond::Params<2, R>::NGC, BY = 8 + 3;
+    if (nx % 4 != 0 || nx < 16 || ny < BY || nx > (1ll << 31) || ny > (1ll << 31)) return false;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    auto one = [&](CUtensorMap *m, const void *ptr, int planes, size_t es, CUtensorMapDataType ty) {
+        const cuuint64_t dims[3] = {cuuint64_t(nx), cuuint64_t(ny), cuuint64_t(planes)};
+        const cuuint64_t strides[2] = {cuuint64_t(nx) * es, cuuint64_t(nx) * cuuint64_t(ny) * es};
+        const cuuint32_t box[3] = {cuuint32_t(pond::kTmaBoxX), cuuint32_t(BY), cuuint32_t(planes)};
+        const cuuint32_t estr[3] = {1, 1, 1};
+        return enc(m, ty, 3, const_cast<void *>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    const R *sf[2] = {sf0, sf1}, *sg[2] = {sg0, sg1};
+    const void *sfr[2] = {sfr0, sfr1};
+    for (int b = 0; b < 2; ++b) {
+        pond::StageMaps &m = s->stage_maps[b];
+        if (!one(&m.sf, sf[b], NFS, sizeof(R), CU_TENSOR_MAP_DATA_TYPE_FLOAT32) ||
+            !one(&m.sg, sg[b], NGC, sizeof(R), CU_TENSOR_MAP_DATA_TYPE_FLOAT32) ||
+            !one(&m.sfr, sfr[b], 3, 8, CU_TENSOR_MAP_DATA_TYPE_FLOAT64))
+            return false;
+        m.key = sf[b];
+    }
+    return true;
 }
 
 template <int D, typename R>
@@ -221,6 +277,10 @@ pond_status setup(pond_state *s)
     s->stage = reinterpret_cast<double *>(s->base + o_stage);
     s->stage_doubles = stage;
     CUDA_TRY(cudaMemsetAsync(s->base, 0, off, s->stream));
+    P.stage_maps = nullptr;
+    if constexpr (D == 2 && sizeof(R) == 4) {
+        if (encode_stage_maps<R>(s, P.nx, P.ny, P.sf, P.sg, P.sfr, P.sf_n, P.sg_n, P.sfr_n)) P.stage_maps = s->stage_maps;
+    }
     new (s->params) P_t(P);
     return POND_OK;
 }
@@ -1325,12 +1385,14 @@ pond_status pond_sync(pond_state *s, pond_diag *diag)
         diag->nonphysical = (int64_t)d.nonphys;
         diag->first_bad_cell = d.first_bad;
         diag->flags = d.flags;
+        diag->staged_tma = (int64_t)d.tma_tiles;
     }
     if (d.flags & pond::FLAG_NONPHYSICAL) return fail(POND_ERR_NONPHYSICAL, "non-physical state: %llu cells/faces, first cell %lld",
                                                       (unsigned long long)d.nonphys, (long long)d.first_bad);
     if (d.flags & pond::FLAG_TIMEOUT)
-        return fail(POND_ERR_TIMEOUT, "a tensor-core wait of the learned predictor expired; its faces started from the "
-                                      "previous half step's frame");
+        return fail(POND_ERR_TIMEOUT, "a bounded device-side wait expired: a tensor-core wait of the learned predictor "
+                                      "(its faces started from the previous half step's frame) or a face tile's TMA "
+                                      "staging (the tile was staged per thread)");
     if (s->opts.strict_convergence && (d.flags & pond::FLAG_NOT_CONVERGED))
         return fail(POND_ERR_NOT_CONVERGED, "%llu faces stopped at max_iter", (unsigned long long)d.nonconv);
     return POND_OK;

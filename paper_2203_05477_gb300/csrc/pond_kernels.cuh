@@ -16,6 +16,8 @@
 // step 1 of the next step and the CFL time step of Sec. IV).
 #pragma once
 
+#include <cuda.h>   // CUtensorMap (the type only; maps are encoded through the runtime's driver entry point)
+
 #include "pond_core.cuh"
 #include "pond_mlp.cuh"
 
@@ -150,6 +152,18 @@ struct Diag {
     long long first_bad;
     unsigned int flags;
     unsigned int pad;
+    unsigned long long tma_tiles;   // face-kernel tiles whose box was staged by tensor-map copies
+};
+
+// Tensor maps of the cell-state planes for the face kernel's TMA staging (D2Q16, FP32): the
+// stored f planes [NFS][ny][nx], the g planes [NGC][ny][nx] and the frame words [D+1][ny][nx]
+// as three-dimensional tensors, each copied as one box of kTmaBoxX x (TY + 3) x planes per
+// tile.  key is the f-plane pointer they describe (the state planes alternate between two
+// buffers under the fused step), so a launch uses them only while P.sf equals it.
+constexpr int kTmaBoxX = 16;          // x extent of a copied box (cells i0 - 4 .. i0 + 11)
+struct alignas(64) StageMaps {
+    CUtensorMap sf, sg, sfr;
+    const void *key;
 };
 
 template <int D, typename R>
@@ -199,6 +213,9 @@ struct Params {
                                       // previous frame; larger moves may reach another fixed point)
     unsigned int *mlp_err;
     int sms;                          // SMs of the device (grid sizes of the grid-stride kernels)
+    // host memory: tensor maps of the two state buffers for the TMA-staged face variant (null
+    // where the grid does not allow them); read by the launcher, never by a kernel
+    const StageMaps *stage_maps;
     __host__ __device__ long long ncell() const { return nx * ny; }
     __host__ __device__ long long nxf() const { return (nx + 1) * ny; }
     __host__ __device__ long long nyf() const { return nx * (ny + 1); }
@@ -324,6 +341,27 @@ __device__ __forceinline__ void cell_velocity(const Params<D, R> &P, long long i
         if (flip & (1 << a)) u[a] = fr_neg(u[a]);
 }
 
+// phi-bar-plus of a loaded cell record (stored coefficients in c.A, c.B, frame u, T): the
+// frame velocity relative to the tile reference and Eq. (Fbarplus) with the co-moving
+// equilibria (rho, 0, ...) and ((Cv - D/2) rho T, 0, ...)
+template <int D, typename R>
+__device__ __forceinline__ void finish_bar_plus(const Params<D, R> &P, R cp, R ce,
+                                                const typename FrameWords<R>::word *utile,
+                                                const typename FrameWords<R>::word *u, R T, StagedCell<D, R> &c)
+{
+    constexpr int NFC = NCoef<D, 3>::value, NGC = NCoef<D, 2>::value;
+#pragma unroll
+    for (int a = 0; a < D; ++a) c.du[a] = R(fr_rel(u[a], utile[a]));
+    const R r = c.A[0];
+    c.A[0] = cp * r + ce * r;
+#pragma unroll
+    for (int k = 1; k < NFC; ++k) c.A[k] = cp * c.A[k];
+    c.B[0] = cp * c.B[0] + ce * (P.Cvh_r * r * T);
+#pragma unroll
+    for (int k = 1; k < NGC; ++k) c.B[k] = cp * c.B[k];
+    c.T = T;
+}
+
 template <int D, typename R>
 __device__ __forceinline__ void load_cell_bar_plus(const Params<D, R> &P, long long i, long long j, R cp, R ce,
                                                    const typename FrameWords<R>::word *utile, StagedCell<D, R> &c)
@@ -371,16 +409,7 @@ __device__ __forceinline__ void load_cell_bar_plus(const Params<D, R> &P, long l
         for (int a = 0; a < D; ++a)
             if (flip & (1 << a)) u[a] = fr_neg(u[a]);
     }
-#pragma unroll
-    for (int a = 0; a < D; ++a) c.du[a] = R(fr_rel(u[a], utile[a]));
-    const R r = c.A[0];
-    c.A[0] = cp * r + ce * r;
-#pragma unroll
-    for (int k = 1; k < NFC; ++k) c.A[k] = cp * c.A[k];
-    c.B[0] = cp * c.B[0] + ce * (P.Cvh_r * r * T);
-#pragma unroll
-    for (int k = 1; k < NGC; ++k) c.B[k] = cp * c.B[k];
-    c.T = T;
+    finish_bar_plus<D, R>(P, cp, ce, utile, u, T, c);
 }
 
 // ------------------------------------------------------------------ face corrector
@@ -1045,11 +1074,14 @@ __host__ __device__ __forceinline__ long long pred_tiles(const Params<D, R> &P)
 // Tile variants of the face kernel: TX x TY cells per CTA (one thread per x face and one
 // per y face in 2D, one per face in 1D) and MINB CTAs per SM for the register budget.  The
 // autotuner picks one per problem.
-template <int D, int TX_, int TY_, int MINB_, int SCR_ = 0>
+template <int D, int TX_, int TY_, int MINB_, int SCR_ = 0, bool TMA_ = false>
 struct FaceVariant {
     static constexpr int TX = TX_, TY = D == 2 ? TY_ : 1, MINB = MINB_;
     static constexpr int THREADS = D == 2 ? 2 * TX_ * TY_ : TX_;
     static constexpr int SCR = SCR_;   // shared scratch level of the corrector (FP32 2D, not EQUIL)
+    // interior tiles stage their box from tensor-map copies (FP32 2D with a scratch level;
+    // the copies land in the corrector's scratch before the corrector uses it)
+    static constexpr bool TMA = TMA_;
 };
 
 // Instantiations (MODE): FACE_PLAIN; FACE_COLLECT also writes (features, converged frame)
@@ -1059,9 +1091,25 @@ struct FaceVariant {
 // Separate instantiations, so the plain kernel carries none of them (and keeps its
 // register budget).
 enum { FACE_PLAIN = 0, FACE_COLLECT = 1, FACE_LEARNED = 2, FACE_EQUIL = 3 };
+
+// one tensor-map copy of a three-dimensional box into shared memory, completing on mbar
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *mbar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+            "r"(tc::smem_addr(dst)), "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z),
+        "r"(tc::smem_addr(mbar))
+        : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *mbar, unsigned int bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_addr(mbar)), "r"(bytes) : "memory");
+}
+
+// The face kernel's body; maps (the TMA variants' tensor maps, in kernel-parameter space)
+// is null for the plain launches.
 template <int D, typename R, int MODE, typename V>
-__global__ void __launch_bounds__(V::THREADS, V::MINB)
-face_kernel(const Params<D, R> P)
+__device__ __forceinline__ void face_body(const Params<D, R> &P, const StageMaps *maps)
 {
     constexpr bool COLLECT = MODE == FACE_COLLECT, LEARNED = MODE == FACE_LEARNED, EQUIL = MODE == FACE_EQUIL;
     constexpr int TX = V::TX, TY = V::TY;
@@ -1075,7 +1123,10 @@ face_kernel(const Params<D, R> P)
     __shared__ StagedCell<D, R> tileT[D == 2 ? BY * BX : 1];
     __shared__ W utile[D];
     constexpr int SCR = D == 2 && sizeof(R) == 4 && MODE != FACE_EQUIL ? V::SCR : 0;
-    __shared__ float4 scratch[SCR ? face_scratch_slots(SCR) * V::THREADS : 1];
+    // TMA staging: the copied planes land in the scratch, which the corrector takes over
+    // after the staging barrier
+    constexpr bool TMA = V::TMA && D == 2 && sizeof(R) == 4 && SCR > 0;
+    __shared__ alignas(TMA ? 128 : 16) float4 scratch[SCR ? face_scratch_slots(SCR) * V::THREADS : 1];
 
     const Clock &K = *P.clock;
     // t_end reached (dt = 0): the step is a no-op; tested after the staging loads, so that
@@ -1115,14 +1166,11 @@ face_kernel(const Params<D, R> P)
 #pragma unroll
         for (int a = 0; a < D; ++a) utile[a] = ut[a];
     }
-    // stage phi-bar-plus of the box [i0-2, i0+TX] x [j0-2, j0+TY] (1D: [i0-2, i0+TX])
-    for (int t = threadIdx.x; t < BX * BY; t += blockDim.x) {
-        const int bx = t % BX, by = t / BX;
-        const long long ci = i0 - 2 + bx, cj = D == 2 ? j0 - 2 + by : 0;
+    // a staged cell into the box and (2D) its transpose
+    auto put_staged = [&](int t, const StagedCell<D, R> &c) {
+        tile[t] = c;
         if constexpr (D == 2) {
-            StagedCell<D, R> c;
-            load_cell_bar_plus<D, R>(P, ci, cj, cp, ce, ut, c);
-            tile[t] = c;
+            const int bx = t % BX, by = t / BX;
             StagedCell<D, R> ct;
             orient<D, 3, R>(c.A, ct.A, true);
             orient<D, 2, R>(c.B, ct.B, true);
@@ -1130,8 +1178,70 @@ face_kernel(const Params<D, R> P)
             ct.du[1] = c.du[0];
             ct.T = c.T;
             tileT[bx * BY + by] = ct;
-        } else {
-            load_cell_bar_plus<D, R>(P, ci, cj, cp, ce, ut, tile[t]);
+        }
+    };
+    bool staged = false;
+    if constexpr (TMA) {
+        // Interior tile (the box [i0-2, i0+TX] x [j0-2, j0+TY] inside the grid, so no ghost
+        // rule applies): one elected thread copies the f, g and frame planes of the box
+        // [i0-4, i0+11] x [j0-2, j0+TY] (x rounded down to a 16-byte boundary) with three
+        // tensor-map loads; the threads then form phi-bar-plus from shared memory, with the
+        // arithmetic of the per-thread staging.  The wait is bounded: on time-out the tile
+        // is flagged, the copies in flight are waited for once more, and the tile is staged
+        // per thread.
+        __shared__ uint64_t tma_bar;
+        if (maps && i0 >= 2 && i0 + TX <= P.nx - 1 && j0 >= 2 && j0 + TY <= P.ny - 1) {
+            static_assert(TX % 4 == 0 && BX + 2 <= kTmaBoxX, "the copied box covers the staged one");
+            constexpr int NFS = NFC - D, PL = BY * kTmaBoxX;
+            constexpr unsigned int BYTES = unsigned(PL * (NFS + NGC) * sizeof(R) + PL * (D + 1) * sizeof(W));
+            static_assert(BYTES <= sizeof(float4) * face_scratch_slots(SCR) * V::THREADS, "the copies fit the scratch");
+            R *raw_f = reinterpret_cast<R *>(scratch);   // [NFS][BY][kTmaBoxX]
+            R *raw_g = raw_f + NFS * PL;                 // [NGC][BY][kTmaBoxX]
+            W *raw_w = reinterpret_cast<W *>(raw_g + NGC * PL);   // [D+1][BY][kTmaBoxX]
+            if (threadIdx.x == 0) {
+                tc::mbar_init(&tma_bar, 1);
+                mbar_expect_tx(&tma_bar, BYTES);
+                const int x = int(i0) - 4, y = int(j0) - 2;
+                tma_load_3d(raw_f, &maps->sf, x, y, 0, &tma_bar);
+                tma_load_3d(raw_g, &maps->sg, x, y, 0, &tma_bar);
+                tma_load_3d(raw_w, &maps->sfr, x, y, 0, &tma_bar);
+            }
+            __syncthreads();   // the barrier is initialised before any thread waits on it
+            const bool ok = __syncthreads_and(tc::mbar_wait(&tma_bar, 0, mlp::kPolls)) != 0;
+            if (ok) {
+                for (int t = threadIdx.x; t < BX * BY; t += blockDim.x) {
+                    const int o = (t / BX) * kTmaBoxX + t % BX + 2;
+                    StagedCell<D, R> c;
+#pragma unroll
+                    for (int k = 0; k < NFC; ++k) {
+                        const int pl = fplane<D>(k);
+                        c.A[k] = pl < 0 ? R(0) : raw_f[pl * PL + o];
+                    }
+#pragma unroll
+                    for (int k = 0; k < NGC; ++k) c.B[k] = raw_g[k * PL + o];
+                    W u[D];
+#pragma unroll
+                    for (int a = 0; a < D; ++a) u[a] = raw_w[a * PL + o];
+                    const R T = R(fr_lead(raw_w[D * PL + o]));
+                    finish_bar_plus<D, R>(P, cp, ce, ut, u, T, c);
+                    put_staged(t, c);
+                }
+                if (threadIdx.x == 0) atomicAdd(&P.diag->tma_tiles, 1ull);
+                staged = true;
+            } else {
+                if (threadIdx.x == 0) atomicOr(&P.diag->flags, FLAG_TIMEOUT);
+                tc::mbar_wait(&tma_bar, 0, mlp::kPolls);
+            }
+        }
+    }
+    // stage phi-bar-plus of the box [i0-2, i0+TX] x [j0-2, j0+TY] (1D: [i0-2, i0+TX])
+    if (!staged) {
+        for (int t = threadIdx.x; t < BX * BY; t += blockDim.x) {
+            const int bx = t % BX, by = t / BX;
+            const long long ci = i0 - 2 + bx, cj = D == 2 ? j0 - 2 + by : 0;
+            StagedCell<D, R> c;
+            load_cell_bar_plus<D, R>(P, ci, cj, cp, ce, ut, c);
+            put_staged(t, c);
         }
     }
     if (!(step_dt > 0.0)) return;   // the same value in every thread
@@ -1281,6 +1391,22 @@ face_kernel(const Params<D, R> P)
         if (my_fallbacks) atomicAdd(&P.diag->fallbacks, my_fallbacks);
         if (my_nonphys) { atomicAdd(&P.diag->nonphys, my_nonphys); atomicOr(&P.diag->flags, FLAG_NONPHYSICAL); }
     }
+}
+
+template <int D, typename R, int MODE, typename V>
+__global__ void __launch_bounds__(V::THREADS, V::MINB)
+face_kernel(const Params<D, R> P)
+{
+    face_body<D, R, MODE, V>(P, nullptr);
+}
+
+// the TMA-staged face variants: the tensor maps travel as a grid-constant kernel parameter,
+// whose address the copies take
+template <int D, typename R, int MODE, typename V>
+__global__ void __launch_bounds__(V::THREADS, V::MINB)
+face_tma_kernel(const Params<D, R> P, const __grid_constant__ StageMaps maps)
+{
+    face_body<D, R, MODE, V>(P, &maps);
 }
 
 // ---------------------------------------------------------------- cell update

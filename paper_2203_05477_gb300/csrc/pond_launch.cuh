@@ -28,7 +28,7 @@ struct FaceList<2, float> {
     using type = VList<FaceVariant<2, 32, 4, 2>, FaceVariant<2, 16, 8, 2>, FaceVariant<2, 64, 2, 2>,
                        FaceVariant<2, 16, 4, 4>, FaceVariant<2, 32, 4, 1>, FaceVariant<2, 16, 8, 3>,
                        FaceVariant<2, 16, 4, 6>, FaceVariant<2, 8, 8, 4>, FaceVariant<2, 8, 8, 4, 1>,
-                       FaceVariant<2, 8, 8, 4, 2>, FaceVariant<2, 16, 4, 4, 2>>;
+                       FaceVariant<2, 8, 8, 4, 2>, FaceVariant<2, 16, 4, 4, 2>, FaceVariant<2, 8, 8, 4, 1, true>>;
 };
 template <>
 struct FaceList<2, double> {
@@ -45,9 +45,10 @@ void face_name_at(int v, char *buf, size_t n)
 {
     if (v <= 0 || sizeof...(Rest) == 0) {
         if (D == 2)
-            std::snprintf(buf, n, "face %dx%d cells, %d threads, %d CTA/SM%s", V::TX, V::TY, V::THREADS, V::MINB,
+            std::snprintf(buf, n, "face %dx%d cells, %d threads, %d CTA/SM%s%s", V::TX, V::TY, V::THREADS, V::MINB,
                           V::SCR == 1 ? ", centre cells in shared scratch"
-                                      : V::SCR == 2 ? ", centre cells and moment sums in shared scratch" : "");
+                                      : V::SCR == 2 ? ", centre cells and moment sums in shared scratch" : "",
+                          V::TMA ? ", TMA staging" : "");
         else std::snprintf(buf, n, "face %d cells, %d threads, %d CTA/SM", V::TX, V::THREADS, V::MINB);
     } else if constexpr (sizeof...(Rest) > 0) {
         face_name_at<D, R, Rest...>(v - 1, buf, n);

@@ -11,6 +11,17 @@ template <int D, typename R, int MODE, typename V>
 void launch_face_one(const Params<D, R> &P, cudaStream_t st)
 {
     const dim3 g(unsigned((P.nx + 1 + V::TX - 1) / V::TX), D == 2 ? unsigned((P.ny + 1 + V::TY - 1) / V::TY) : 1u);
+    if constexpr (V::TMA) {
+        // the tensor maps of the buffer that holds the state now; without them (a grid whose
+        // rows are not 16-byte multiples) the same tile stages every cell per thread
+        if (P.stage_maps) {
+            for (int b = 0; b < 2; ++b)
+                if (P.stage_maps[b].key == P.sf) {
+                    face_tma_kernel<D, R, MODE, V><<<g, V::THREADS, 0, st>>>(P, P.stage_maps[b]);
+                    return;
+                }
+        }
+    }
     face_kernel<D, R, MODE, V><<<g, V::THREADS, 0, st>>>(P);
 }
 
