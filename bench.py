@@ -40,10 +40,13 @@ FACE_KERNEL_DRAM_BYTES = {
     "face 8x8 cells, 128 threads, 4 CTA/SM, centre cells and moment sums in shared scratch": 134.678e6 + 136.447e6,
 }
 # FP32 operations (FMA = 2) of one corrector pass at one D2Q16 face (per-face overhead
-# included), from the ncu instruction counts of the scalar face kernel; used for the ALU
-# roofline.  The packed FP32x2 form of the same algorithm executes ~4% more (differences
-# formed as fused multiply-adds by -1), which is not counted.
-FLOPS_PER_FACE_PASS = 4550.0
+# included), from the ncu instruction counts of the scalar face kernel (4550), less the
+# operations the current kernel no longer executes: the 140 multiplications by He_0 = 1 of
+# the column collapses and the 64 doublings of the van Leer slopes (their factor 2 now
+# scales the departure offsets, 8 multiplications per pass); used for the ALU roofline.  The
+# packed FP32x2 form executes more (differences formed as fused multiply-adds by -1), which
+# is not counted.
+FLOPS_PER_FACE_PASS = 4550.0 - 140.0 - 64.0 + 8.0
 # algorithmic bytes per cell-update of the FP32 D2Q16 layout: the face kernel reads the
 # cell state (8 + 6 FP32 coefficients + 3 float-float frame words = 80 B) and two face predictors
 # (2 x 24 B) and writes two faces (2 x (16 x 4 + 24) B)

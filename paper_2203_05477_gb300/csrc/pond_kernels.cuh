@@ -474,6 +474,17 @@ __device__ __forceinline__ void rel_velocity(const StagedCell<D, R> *c, const R 
 // ---- FP32x2 helpers (packed FP32 arithmetic of sm_100 and later: one instruction, two lanes)
 __device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
 
+// The limited slope of each lane divided by sc = limit_scale(kind): van Leer's 2ab/(a+b) as
+// ab/(a+b) (the factor 2 goes into the departure offsets, an exact scaling), minmod as it is
+__device__ __forceinline__ float limit_scale(int kind) { return kind == 1 ? 1.f : 2.f; }
+__device__ __forceinline__ float2 limit2_scaled(int kind, float2 a, float2 b)
+{
+    const float2 ab = __fmul2_rn(a, b);
+    if (kind == 1) return make_float2(minmod<float>(a.x, b.x), minmod<float>(a.y, b.y));
+    const float2 den = __fadd2_rn(a, b);
+    return make_float2(ab.x > 0.f ? __fdividef(ab.x, den.x) : 0.f, ab.y > 0.f ? __fdividef(ab.y, den.y) : 0.f);
+}
+
 // limited slope of each lane (van Leer or minmod), the products and sums packed
 __device__ __forceinline__ float2 limit2(int kind, float2 a, float2 b)
 {
@@ -499,13 +510,17 @@ __device__ __forceinline__ void pair_populations(const float *Cu, const float *C
     const float2 minus1 = bc2(-1.f);
     float2 SS[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
     float S3 = 0.f;
+    // the limited slopes come divided by sc, the offsets multiplied by it
+    const float sc = limit_scale(limiter), offn_s = sc * offn, h_dt_s = sc * h_dt;
 #pragma unroll
     for (int n = 0; n < 4; ++n) {
         const float vt = sqTl * float(node_c(n)) + ut_abs;
-        const float offt = -vt * h_dt;
-        float2 u2 = make_float2(0.f, 0.f), l2 = u2, h2 = u2, m2 = u2, p2 = u2;
+        const float offt_s = -vt * h_dt_s;
+        // order 0: He_0 = 1
+        float2 u2 = make_float2(Cu[0], Du[0]), l2 = make_float2(Cl[0], Dl[0]), h2 = make_float2(Ch[0], Dh[0]),
+               m2 = make_float2(Cm[0], Dm[0]), p2 = make_float2(Cp[0], Dp[0]);
 #pragma unroll
-        for (int b2 = 0; b2 <= 2; ++b2) {
+        for (int b2 = 1; b2 <= 2; ++b2) {
             const float2 hn = bc2(float(hen(b2, n)));
             u2 = __ffma2_rn(make_float2(Cu[b2], Du[b2]), hn, u2);
             l2 = __ffma2_rn(make_float2(Cl[b2], Dl[b2]), hn, l2);
@@ -524,9 +539,9 @@ __device__ __forceinline__ void pair_populations(const float *Cu, const float *C
         } else {
             u2.x += Cu[3] * h3; l2.x += Cl[3] * h3; h2.x += Ch[3] * h3; m2.x += Cm[3] * h3; p2.x += Cp[3] * h3;
         }
-        const float2 ln = limit2(limiter, __ffma2_rn(l2, minus1, u2), __ffma2_rn(u2, minus1, h2));
-        const float2 lt = limit2(limiter, __ffma2_rn(m2, minus1, u2), __ffma2_rn(u2, minus1, p2));
-        const float2 b = __ffma2_rn(bc2(offt), lt, __ffma2_rn(bc2(offn), ln, u2));
+        const float2 ln = limit2_scaled(limiter, __ffma2_rn(l2, minus1, u2), __ffma2_rn(u2, minus1, h2));
+        const float2 lt = limit2_scaled(limiter, __ffma2_rn(m2, minus1, u2), __ffma2_rn(u2, minus1, p2));
+        const float2 b = __ffma2_rn(bc2(offt_s), lt, __ffma2_rn(bc2(offn_s), ln, u2));
 #pragma unroll
         for (int b2 = 0; b2 <= 2; ++b2) SS[b2] = __ffma2_rn(bc2(float(node_w(n) * he(b2, n))), b, SS[b2]);
         S3 += float(node_w(n) * he(3, n)) * b.x;
@@ -740,21 +755,22 @@ __device__ __forceinline__ void corrector_pass(const Stencil<D, R> &cells, const
             for (int a = 0; a <= 2; ++a) Psi[a] += tab.whe[m][a] * gb;
         } else {
             // column collapse C_b = sum_a A_ab He_a(c_m)/a! of a coefficient set
+            // (He_0 = 1: the order-0 term is the coefficient itself)
             auto collapse_f = [&](const R *A, R *C) {
 #pragma unroll
                 for (int b2 = 0; b2 <= 3; ++b2) {
-                    R acc = R(0);
+                    R acc = A[hidx(0, b2)];
 #pragma unroll
-                    for (int a2 = 0; a2 + b2 <= 3; ++a2) acc += A[hidx(a2, b2)] * tab.hen[m][a2];
+                    for (int a2 = 1; a2 + b2 <= 3; ++a2) acc += A[hidx(a2, b2)] * tab.hen[m][a2];
                     C[b2] = acc;
                 }
             };
             auto collapse_g = [&](const R *A, R *C) {
 #pragma unroll
                 for (int b2 = 0; b2 <= 2; ++b2) {
-                    R acc = R(0);
+                    R acc = A[hidx(0, b2)];
 #pragma unroll
-                    for (int a2 = 0; a2 + b2 <= 2; ++a2) acc += A[hidx(a2, b2)] * tab.hen[m][a2];
+                    for (int a2 = 1; a2 + b2 <= 2; ++a2) acc += A[hidx(a2, b2)] * tab.hen[m][a2];
                     C[b2] = acc;
                 }
             };
