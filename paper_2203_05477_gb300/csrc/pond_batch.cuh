@@ -127,18 +127,29 @@ tube_kernel(const TubeParams<R> P, int steps, int cur0)
 
     for (int step = 0; step < steps; ++step) {
         const int cur = (cur0 + step) & 1, nxt = cur ^ 1;
-        if (threadIdx.x == 0) {
+        if (threadIdx.x < 32) {
+            // the nine quotients side by side, one per lane of warp 0 (one FP64 division
+            // instead of nine in a row on the step's critical path)
             const double dt = P.dt[tube], h = 0.5 * dt;
-            ks.dt = dt;
-            ks.ca = R((2.0 * tau - dt) / (2.0 * tau + dt));
-            ks.cb = R(2.0 * dt / (2.0 * tau + dt));
-            ks.cp = R((2.0 * tau - h) / (2.0 * tau + dt));
-            ks.ce = R(3.0 * h / (2.0 * tau + dt));
-            ks.wb = R(2.0 * tau / (2.0 * tau + h));
-            ks.we = R(h / (2.0 * tau + h));
-            ks.h_dx = R(h / dx);
-            ks.dt_dx = R(dt / dx);
-            ks.inv_dx = R(1.0 / dx);
+            double num = 1.0, den = dx;   // lane 8 (and idle lanes): 1/dx
+            if (lane == 0) { num = 2.0 * tau - dt; den = 2.0 * tau + dt; }
+            if (lane == 1) { num = 2.0 * dt; den = 2.0 * tau + dt; }
+            if (lane == 2) { num = 2.0 * tau - h; den = 2.0 * tau + dt; }
+            if (lane == 3) { num = 3.0 * h; den = 2.0 * tau + dt; }
+            if (lane == 4) { num = 2.0 * tau; den = 2.0 * tau + h; }
+            if (lane == 5) { num = h; den = 2.0 * tau + h; }
+            if (lane == 6) { num = h; den = dx; }
+            if (lane == 7) { num = dt; den = dx; }
+            const R q = R(num / den);
+            if (lane == 0) { ks.dt = dt; ks.ca = q; }
+            if (lane == 1) ks.cb = q;
+            if (lane == 2) ks.cp = q;
+            if (lane == 3) ks.ce = q;
+            if (lane == 4) ks.wb = q;
+            if (lane == 5) ks.we = q;
+            if (lane == 6) ks.h_dx = q;
+            if (lane == 7) ks.dt_dx = q;
+            if (lane == 8) ks.inv_dx = q;
         }
         __syncthreads();
         const R cp = ks.cp, ce = ks.ce, ca = ks.ca, cb = ks.cb;

@@ -736,6 +736,34 @@ __device__ __forceinline__ void corrector_pass(const Stencil<D, R> &cells, const
                 gR3 = fast_eq<1, 2, R>(GR).at(3, 0) * h3;
                 gS3 = fast_eq<1, 2, R>(GS).at(3, 0) * h3;
             }
+            if constexpr (sizeof(R) == 4 && !EQ) {
+                // FP32: f (lane x) and g (lane y) side by side as FP32x2 pairs for the orders
+                // they share; the same operations in the same order as the scalar form below
+                // (van Leer's factor 2 scales the departure offset, an exact scaling)
+                // (the 1D node loop is unrolled: m, and so these factors, are constants)
+                const float h1 = float(hen(1, m)), h2 = float(hen(2, m)), h3 = float(hen(3, m));
+                float2 pL = make_float2(FL[0], GL[0]), pR = make_float2(FR[0], GR[0]), pS = make_float2(FS[0], GS[0]);
+                pL = __ffma2_rn(make_float2(FL[1], GL[1]), bc2(h1), pL);
+                pR = __ffma2_rn(make_float2(FR[1], GR[1]), bc2(h1), pR);
+                pS = __ffma2_rn(make_float2(FS[1], GS[1]), bc2(h1), pS);
+                pL = __ffma2_rn(make_float2(FL[2], GL[2]), bc2(h2), pL);
+                pR = __ffma2_rn(make_float2(FR[2], GR[2]), bc2(h2), pR);
+                pS = __ffma2_rn(make_float2(FS[2], GS[2]), bc2(h2), pS);
+                pL.x += FL[3] * h3; pR.x += FR[3] * h3; pS.x += FS[3] * h3;
+                const float2 pu = left ? pL : pR, pl = left ? pS : pL, ph = left ? pR : pS;
+                const float2 minus1 = bc2(-1.f);
+                const float2 sl = limit2_scaled(limiter, __ffma2_rn(pl, minus1, pu), __ffma2_rn(pu, minus1, ph));
+                const float2 pb = __ffma2_rn(bc2(limit_scale(limiter) * float(offn)), sl, pu);
+#pragma unroll
+                for (int a = 0; a <= 2; ++a) {
+                    const float2 w = bc2(float(node_w(m) * he(a, m)));
+                    const float2 acc = __ffma2_rn(w, pb, make_float2(Phi[a], Psi[a]));
+                    Phi[a] = acc.x;
+                    Psi[a] = acc.y;
+                }
+                Phi[3] += float(node_w(m) * he(3, m)) * pb.x;
+                return;
+            }
             // populations at node m (unweighted: the limiter is homogeneous of degree one,
             // so the weight w_m factors out) of L, R and the outer neighbour
             R fL = R(0), fR = R(0), fS = R(0), gL = gL3, gR = gR3, gS = gS3;
@@ -1609,7 +1637,7 @@ __device__ __forceinline__ bool cell_finish(const R *H, const R *G, R invTc, R s
     }
     // T'/T - 1 = (1/2 tr H + G0/T - (Cv - D/2) rho' - rho' |du|^2/(2T)) / (Cv rho')
     dT = w_div<R>(R(0.5) * trH + G[0] * invTc - (Cv - R(0.5 * D)) * rn - R(0.5) * rn * k2 * invTc, Cv * rn);
-    const bool ok = rn > R(0) && R(1) + dT > R(0) && isfinite(double(rn)) && isfinite(double(dT));
+    const bool ok = rn > R(0) && R(1) + dT > R(0) && isfinite(rn) && isfinite(dT);
     // s^2 = T/T' = 1/(1 + dT/T), e = s^2 - 1, d = -du/sqrt(T')
     const R s2 = w_rcp<R>(R(1) + dT);
     const R sc = w_sqrt<R>(s2), e = -dT * s2;
