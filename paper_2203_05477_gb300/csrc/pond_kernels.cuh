@@ -161,7 +161,7 @@ struct Diag {
 // tile.  key is the f-plane pointer they describe (the state planes alternate between two
 // buffers under the fused step), so a launch uses them only while P.sf equals it.
 constexpr int kTmaBoxX = 16;          // x extent of a copied box (cells i0 - 4 .. i0 + 11)
-struct alignas(64) StageMaps {
+struct StageMaps {
     CUtensorMap sf, sg, sfr;
     const void *key;
 };

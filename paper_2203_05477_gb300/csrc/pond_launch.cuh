@@ -28,7 +28,8 @@ struct FaceList<2, float> {
     using type = VList<FaceVariant<2, 32, 4, 2>, FaceVariant<2, 16, 8, 2>, FaceVariant<2, 64, 2, 2>,
                        FaceVariant<2, 16, 4, 4>, FaceVariant<2, 32, 4, 1>, FaceVariant<2, 16, 8, 3>,
                        FaceVariant<2, 16, 4, 6>, FaceVariant<2, 8, 8, 4>, FaceVariant<2, 8, 8, 4, 1>,
-                       FaceVariant<2, 8, 8, 4, 2>, FaceVariant<2, 16, 4, 4, 2>, FaceVariant<2, 8, 8, 4, 1, true>>;
+                       FaceVariant<2, 8, 8, 4, 2>, FaceVariant<2, 16, 4, 4, 2>, FaceVariant<2, 8, 8, 4, 1, true>,
+                       FaceVariant<2, 8, 8, 3, 1, true>>;
 };
 template <>
 struct FaceList<2, double> {
