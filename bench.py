@@ -694,7 +694,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
-    ap.add_argument("--tube-steps", type=int, default=100)
+    ap.add_argument("--tube-steps", type=int, default=1000)
     ap.add_argument("--no-tune", action="store_true", help="skip the kernel-variant autotuner (use the defaults)")
     ap.add_argument("--tune-cache", default=None,
                     help="autotuner cache file: choices found there are reused without timing (profiling runs)")
