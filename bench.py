@@ -691,7 +691,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--fp64-steps", type=int, default=6)
+    ap.add_argument("--fp64-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--tube-steps", type=int, default=1000)

@@ -591,7 +591,9 @@ __device__ __forceinline__ FastEq<R> fast_eq(const R *A)
 }
 
 // Per-thread scratch in shared memory (FP32, 2D): the two centre cells' coefficients in the
-// corrector frame (f: 10, g: 6 each; slots 0-7) and the pass's moment sums (slots 8-11),
+// corrector frame (f: 10, g: 6 each; slots 0-7), the pass's moment sums (level 2: slots
+// 8-11), the frames of the last valid pass (two slots after those) and, at level 2, the
+// constants of the face output (one more slot),
 // 16-byte slots, thread-minor so that a warp's accesses are contiguous.  They are touched
 // once per normal node, so keeping them out of the registers across the node loop lowers
 // the kernel's register demand.  The accesses are
@@ -631,7 +633,9 @@ struct FaceScratch {
         G[2] = d.x; G[3] = d.y; G[4] = d.z; G[5] = d.w;
     }
 };
-__host__ __device__ constexpr int face_scratch_slots(int level) { return level > 1 ? 12 : 8; }
+__host__ __device__ constexpr int face_scratch_slots(int level) { return level > 1 ? 15 : 10; }
+// slots of the last valid pass's frames (kept across the passes, read after the loop)
+__host__ __device__ constexpr int face_keep_slot(int level) { return level > 1 ? 12 : 8; }
 
 // One corrector pass at a face (Sec. III.B.3) in frame (dl, Tl) (velocity relative to the
 // face reference uref): every stencil cell's phi-bar-plus is re-expressed in that frame,
@@ -1012,6 +1016,8 @@ __device__ __forceinline__ void solve_face(const Stencil<D, R> &cells, bool swap
 #pragma unroll
     for (int a = 0; a < D; ++a) dl[a] = R(0);
     R keep_dl[D], keep_T = R(0), out_du[D], out_T = R(0), out_rho = R(0);
+    // level 2: the face output's constants wait in the scratch too
+    if constexpr (SCR > 1) scr.put(face_keep_slot(SCR) + 2, float(cfg.wb), float(cfg.we), float(cfg.Cv), 0.f);
     bool have = false, done = false, restarted = false, last_valid = false;
     int iters = 0;
     R Phi[NFC], Psi[NGC];
@@ -1051,9 +1057,15 @@ __device__ __forceinline__ void solve_face(const Stencil<D, R> &cells, bool swap
         }
         have = true;
         last_valid = true;
+        if constexpr (SCR > 0) {
+            // the kept frames wait in the scratch while the next pass runs
+            scr.put(face_keep_slot(SCR), float(dl[0]), float(dl[D - 1]), float(Tl), float(rho1));
+            scr.put(face_keep_slot(SCR) + 1, float(du[0]), float(du[D - 1]), float(T1), 0.f);
+        } else {
 #pragma unroll
-        for (int a = 0; a < D; ++a) { keep_dl[a] = dl[a]; out_du[a] = du[a]; }
-        keep_T = Tl; out_T = T1; out_rho = rho1;
+            for (int a = 0; a < D; ++a) { keep_dl[a] = dl[a]; out_du[a] = du[a]; }
+            keep_T = Tl; out_T = T1; out_rho = rho1;
+        }
         if (cfg.fixed_iters > 0) {
             done = iters >= cfg.fixed_iters;
         } else {
@@ -1070,6 +1082,13 @@ __device__ __forceinline__ void solve_face(const Stencil<D, R> &cells, bool swap
     o.iters = iters;
     o.done = done;
     o.have = have;
+    if constexpr (SCR > 0) {
+        if (have) {
+            const float4 a = scr.get(face_keep_slot(SCR)), b = scr.get(face_keep_slot(SCR) + 1);
+            keep_dl[0] = R(a.x); keep_dl[D - 1] = R(a.y); keep_T = R(a.z); out_rho = R(a.w);
+            out_du[0] = R(b.x); out_du[D - 1] = R(b.y); out_T = R(b.z);
+        }
+    }
     if (have) {
         if (!last_valid) {
             // the last pass defined no frame: recompute the last valid one
@@ -1087,11 +1106,16 @@ __device__ __forceinline__ void solve_face(const Stencil<D, R> &cells, bool swap
         R Fo[NFC], Go[NGC];
         shift_scale<D, 3, R>(Phi, X, Y, Fo);
         shift_scale<D, 2, R>(Psi, X, Y, Go);
-        const R wb = cfg.wb, we = cfg.we;
-        Fo[0] = wb * Fo[0] + we * out_rho;
+        R wb = cfg.wb, we = cfg.we, Cvf = Cv;
+        if constexpr (SCR > 1) {
+            const float4 w = scr.get(face_keep_slot(SCR) + 2);
+            wb = R(w.x); we = R(w.y); Cvf = R(w.z);
+        }
+        // (the contractions written out, so that every variant rounds these alike)
+        Fo[0] = fma(wb, Fo[0], we * out_rho);
 #pragma unroll
         for (int k = 1; k < NFC; ++k) Fo[k] = wb * Fo[k];
-        Go[0] = wb * Go[0] + we * (Cv - R(0.5 * D)) * out_rho * out_T;
+        Go[0] = fma(wb, Go[0], we * (Cvf - R(0.5 * D)) * out_rho * out_T);
 #pragma unroll
         for (int k = 1; k < NGC; ++k) Go[k] = wb * Go[k];
         orient<D, 3, R>(Fo, o.F, swap);

@@ -29,7 +29,7 @@ struct FaceList<2, float> {
                        FaceVariant<2, 16, 4, 4>, FaceVariant<2, 32, 4, 1>, FaceVariant<2, 16, 8, 3>,
                        FaceVariant<2, 16, 4, 6>, FaceVariant<2, 8, 8, 4>, FaceVariant<2, 8, 8, 4, 1>,
                        FaceVariant<2, 8, 8, 4, 2>, FaceVariant<2, 16, 4, 4, 2>, FaceVariant<2, 8, 8, 4, 1, true>,
-                       FaceVariant<2, 8, 8, 3, 1, true>>;
+                       FaceVariant<2, 8, 8, 3, 1, true>, FaceVariant<2, 8, 8, 4, 2, true>>;
 };
 template <>
 struct FaceList<2, double> {

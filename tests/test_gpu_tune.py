@@ -221,40 +221,41 @@ def _quadrants_64x48():
     ("smooth_periodic_64x40", lambda: I.smooth_periodic(2, 64, 40, seed=1)),
 ], ids=lambda x: x if isinstance(x, str) else "")
 def test_tma_staging_is_the_same_arithmetic(name, make):
-    """The TMA variant of the 8 x 8 face tile copies the state planes of an interior tile's box
-    into shared memory with tensor-map loads and forms phi-bar-plus there, with the arithmetic
-    of the per-thread staging; tiles that touch a side (ghost rules) stage per thread.  Over
-    twelve steps of transmissive, inflow, reflective and periodic problems its state and face
-    frames equal those of the per-thread variant of the same tile bit for bit, and the
-    diagnostics count the tiles it staged by TMA (every interior tile of every step)."""
+    """The TMA variants of the 8 x 8 face tile (both scratch levels) copy the state planes of
+    an interior tile's box into shared memory with tensor-map loads and form phi-bar-plus
+    there, with the arithmetic of the per-thread staging; tiles that touch a side (ghost
+    rules) stage per thread.  Over twelve steps of transmissive, inflow, reflective and
+    periodic problems their states and face frames equal those of the per-thread variants of
+    the same tile bit for bit, and the diagnostics count the tiles staged by TMA (every
+    interior tile of every step)."""
     pb = make()
     kw = dict(tau=1e-5, cfl=0.2, max_iter=16, tol=1e-6)
-    names = None
-    out = {}
     steps = 12
-    for which in ("per-thread", "TMA"):
-        gs = gpu_for(pb, precision="fp32", **kw)
-        names = gs.variants()
-        base = "face 8x8 cells, 128 threads, 4 CTA/SM, centre cells in shared scratch"
-        f = names.index(base + (", TMA staging" if which == "TMA" else ""))
-        gs.set_variants(face=f, cell=0)
-        gs.set_primitive()
-        gs.step(steps)
-        d = gs.sync()
-        assert d["nonphysical"] == 0 and d["steps"] == steps, (which, d)
-        out[which] = ([np.asarray(a) for a in gs.state()], [a for a in gs.face_gauges()], d)
-        gs.close()
-    (sa, fa, da), (sb, fb, db) = out["per-thread"], out["TMA"]
-    for a, b in zip(sa, sb):
-        assert np.array_equal(a, b)
-    for a, b in zip(fa, fb):
-        assert a is None or np.array_equal(a, b)
-    assert da["face_iters"] == db["face_iters"] and da["fallbacks"] == db["fallbacks"]
     # interior tiles: x origin i0 = 8 bx with 2 <= i0 and i0 + 8 <= nx - 1, likewise in y
     nxt = sum(1 for i0 in range(0, pb.nx + 1, 8) if i0 >= 2 and i0 + 8 <= pb.nx - 1)
     nyt = sum(1 for j0 in range(0, pb.ny + 1, 8) if j0 >= 2 and j0 + 8 <= pb.ny - 1)
-    assert da["staged_tma"] == 0
-    assert db["staged_tma"] == steps * nxt * nyt > 0, (db["staged_tma"], nxt, nyt)
+    for level in ("centre cells in shared scratch", "centre cells and moment sums in shared scratch"):
+        out = {}
+        for which in ("per-thread", "TMA"):
+            gs = gpu_for(pb, precision="fp32", **kw)
+            names = gs.variants()
+            base = "face 8x8 cells, 128 threads, 4 CTA/SM, " + level
+            f = names.index(base + (", TMA staging" if which == "TMA" else ""))
+            gs.set_variants(face=f, cell=0)
+            gs.set_primitive()
+            gs.step(steps)
+            d = gs.sync()
+            assert d["nonphysical"] == 0 and d["steps"] == steps, (level, which, d)
+            out[which] = ([np.asarray(a) for a in gs.state()], [a for a in gs.face_gauges()], d)
+            gs.close()
+        (sa, fa, da), (sb, fb, db) = out["per-thread"], out["TMA"]
+        for a, b in zip(sa, sb):
+            assert np.array_equal(a, b), level
+        for a, b in zip(fa, fb):
+            assert a is None or np.array_equal(a, b), level
+        assert da["face_iters"] == db["face_iters"] and da["fallbacks"] == db["fallbacks"]
+        assert da["staged_tma"] == 0
+        assert db["staged_tma"] == steps * nxt * nyt > 0, (level, db["staged_tma"], nxt, nyt)
 
 
 def test_tma_variant_stages_per_thread_without_maps():
