@@ -111,6 +111,8 @@ tube_kernel(const TubeParams<R> P, int steps, int cur0)
     __shared__ CellW raww[NW][2][32];
     __shared__ R red[NW];
     __shared__ int tube_bad;
+    // FP32: per-thread scratch of the face solve (the last valid pass's frames), thread-minor
+    __shared__ float4 kept[sizeof(R) == 4 ? 2 * THREADS : 1];
 
     const int tube = P.order[blockIdx.x];
     if (P.status[tube] != 0) return;  // stopped earlier: its state is not advanced any more
@@ -208,7 +210,8 @@ tube_kernel(const TubeParams<R> P, int steps, int cur0)
                 const R dref[1] = {R(fr_rel(fu_in[f_off + k], utile))};
                 const R uabs[1] = {R(fr_lead(fu_in[f_off + k]))};
                 FaceOut<1, R> o;
-                solve_face<1, R, false, 0, false>(cells, false, dref, uabs, R(fT_in[f_off + k]), cfg, o);
+                solve_face<1, R, false, 0, false, sizeof(R) == 4 ? 1 : 0>(cells, false, dref, uabs, R(fT_in[f_off + k]), cfg, o,
+                                                               FaceScratch{kept + (sizeof(R) == 4 ? threadIdx.x : 0), THREADS});
                 const bool owned = f < nc || k == L;
                 if (owned) {
                     my_iters += o.iters;

@@ -997,11 +997,16 @@ struct FaceOut {
 // no frame restarts the corrector once from the frame of the pooled moments of the
 // stencil, else the corrector stops at the last pass that did.  The face populations are
 // Eq. (FluxTransf) at the frame of the last valid pass's moments.
-template <int D, typename R, bool EQ = false, int SCR = 0, bool OUTER_ONCE = true>
+// KEEP (FP32): 1, the last valid pass's frames wait in two slots of the thread's scratch
+// (after the corrector's own slots) instead of staying live across the next pass; 2, the
+// constants of the face output wait in one more slot
+template <int D, typename R, bool EQ = false, int SCR = 0, bool OUTER_ONCE = true, int KEEP = (SCR > 1 ? 2 : SCR)>
 __device__ __forceinline__ void solve_face(const Stencil<D, R> &cells, bool swap, const R *dref, const R *uabs,
                                            R Tpred, const FaceCfg<R> &cfg, FaceOut<D, R> &o,
                                            FaceScratch scr = FaceScratch{nullptr, 0})
 {
+    static_assert(KEEP == 0 || sizeof(R) == 4, "the kept frames are FP32 scratch words");
+    constexpr int KS = SCR > 0 ? face_keep_slot(SCR) : 0;   // first slot of the kept frames
     o.fallbacks = 0;
     constexpr int NCELL = D == 2 ? 8 : 4;
     constexpr int NFC = NCoef<D, 3>::value, NGC = NCoef<D, 2>::value;
@@ -1017,7 +1022,7 @@ __device__ __forceinline__ void solve_face(const Stencil<D, R> &cells, bool swap
     for (int a = 0; a < D; ++a) dl[a] = R(0);
     R keep_dl[D], keep_T = R(0), out_du[D], out_T = R(0), out_rho = R(0);
     // level 2: the face output's constants wait in the scratch too
-    if constexpr (SCR > 1) scr.put(face_keep_slot(SCR) + 2, float(cfg.wb), float(cfg.we), float(cfg.Cv), 0.f);
+    if constexpr (KEEP > 1) scr.put(KS + 2, float(cfg.wb), float(cfg.we), float(cfg.Cv), 0.f);
     bool have = false, done = false, restarted = false, last_valid = false;
     int iters = 0;
     R Phi[NFC], Psi[NGC];
@@ -1057,10 +1062,10 @@ __device__ __forceinline__ void solve_face(const Stencil<D, R> &cells, bool swap
         }
         have = true;
         last_valid = true;
-        if constexpr (SCR > 0) {
+        if constexpr (KEEP > 0) {
             // the kept frames wait in the scratch while the next pass runs
-            scr.put(face_keep_slot(SCR), float(dl[0]), float(dl[D - 1]), float(Tl), float(rho1));
-            scr.put(face_keep_slot(SCR) + 1, float(du[0]), float(du[D - 1]), float(T1), 0.f);
+            scr.put(KS, float(dl[0]), float(dl[D - 1]), float(Tl), float(rho1));
+            scr.put(KS + 1, float(du[0]), float(du[D - 1]), float(T1), 0.f);
         } else {
 #pragma unroll
             for (int a = 0; a < D; ++a) { keep_dl[a] = dl[a]; out_du[a] = du[a]; }
@@ -1082,9 +1087,9 @@ __device__ __forceinline__ void solve_face(const Stencil<D, R> &cells, bool swap
     o.iters = iters;
     o.done = done;
     o.have = have;
-    if constexpr (SCR > 0) {
+    if constexpr (KEEP > 0) {
         if (have) {
-            const float4 a = scr.get(face_keep_slot(SCR)), b = scr.get(face_keep_slot(SCR) + 1);
+            const float4 a = scr.get(KS), b = scr.get(KS + 1);
             keep_dl[0] = R(a.x); keep_dl[D - 1] = R(a.y); keep_T = R(a.z); out_rho = R(a.w);
             out_du[0] = R(b.x); out_du[D - 1] = R(b.y); out_T = R(b.z);
         }
@@ -1107,8 +1112,8 @@ __device__ __forceinline__ void solve_face(const Stencil<D, R> &cells, bool swap
         shift_scale<D, 3, R>(Phi, X, Y, Fo);
         shift_scale<D, 2, R>(Psi, X, Y, Go);
         R wb = cfg.wb, we = cfg.we, Cvf = Cv;
-        if constexpr (SCR > 1) {
-            const float4 w = scr.get(face_keep_slot(SCR) + 2);
+        if constexpr (KEEP > 1) {
+            const float4 w = scr.get(KS + 2);
             wb = R(w.x); we = R(w.y); Cvf = R(w.z);
         }
         // (the contractions written out, so that every variant rounds these alike)
