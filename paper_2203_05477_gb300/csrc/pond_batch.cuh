@@ -111,6 +111,7 @@ tube_kernel(const TubeParams<R> P, int steps, int cur0)
     __shared__ CellW raww[NW][2][32];
     __shared__ R red[NW];
     __shared__ int tube_bad;
+    __shared__ int next_chunk;   // the next chunk of the step that no warp has taken yet
     // FP32: per-thread scratch of the face solve (the last valid pass's frames), thread-minor
     __shared__ float4 kept[sizeof(R) == 4 ? 2 * THREADS : 1];
 
@@ -152,6 +153,7 @@ tube_kernel(const TubeParams<R> P, int steps, int cur0)
             if (lane == 6) ks.h_dx = q;
             if (lane == 7) ks.dt_dx = q;
             if (lane == 8) ks.inv_dx = q;
+            if (lane == 9) next_chunk = NW;   // chunks 0 .. NW-1 go to warps 0 .. NW-1
         }
         __syncthreads();
         const R cp = ks.cp, ce = ks.ce, ca = ks.ca, cb = ks.cb;
@@ -170,7 +172,11 @@ tube_kernel(const TubeParams<R> P, int steps, int cur0)
         R rate = R(0);
         const long long n = P.ncell;
         const R Cvh = CvR - R(0.5);
-        for (int c0 = warp * kTubeChunk; c0 < L; c0 += NW * kTubeChunk) {
+        // chunks are dealt dynamically: a warp that finishes one takes the next free one, so
+        // a warp held up by a chunk whose faces need many corrector passes does fewer chunks
+        // (the state and predictors are double-buffered, so the order does not matter)
+        for (int ci = warp; ci * kTubeChunk < L;) {
+            const int c0 = ci * kTubeChunk;
             const int nc = min(kTubeChunk, L - c0);
             // reference velocity of the chunk: its first cell's frame velocity
             const CellW utile = P.sfr[cur][c_off + c0];
@@ -300,6 +306,9 @@ tube_kernel(const TubeParams<R> P, int steps, int cur0)
                 }
             }
             __syncwarp();   // the chunk's shared records are read before the next chunk restages them
+            int nxt_c = 0;
+            if (lane == 0) nxt_c = atomicAdd(&next_chunk, 1);
+            ci = __shfl_sync(0xffffffffu, nxt_c, 0);
         }
         // the tube's next time step from its CFL maximum (Sec. IV)
         R r = rate;
