@@ -42,14 +42,12 @@ FACE_KERNEL_DRAM_BYTES = {
     "face 8x8 cells, 128 threads, 4 CTA/SM, centre cells and moment sums in shared scratch, TMA staging":
         134.643e6 + 133.277e6,
 }
-# FP32 operations (FMA = 2) of one corrector pass at one D2Q16 face (per-face overhead
-# included), from the ncu instruction counts of the scalar face kernel (4550), less the
-# operations the current kernel no longer executes: the 140 multiplications by He_0 = 1 of
-# the column collapses and the 64 doublings of the van Leer slopes (their factor 2 now
-# scales the departure offsets, 8 multiplications per pass); used for the ALU roofline.  The
-# packed FP32x2 form executes more (differences formed as fused multiply-adds by -1), which
-# is not counted.
-FLOPS_PER_FACE_PASS = 4550.0 - 140.0 - 64.0 + 8.0
+# FP32 operations of one corrector pass at one D2Q16 face (per-face overhead included),
+# counted by ncu on one launch of the headline face variant at 1024^2 (level-2 scratch, TMA
+# staging): FFMA x 2 + FFMA2 x 4 + FMUL + FMUL2 x 2 + FADD + FADD2 x 2 = 8.417 GFLOP over
+# 2,099,200 faces x 1.028 passes (profiles/face_kernel_quadrants1024_fp32.md); used for the
+# ALU roofline.  (The scalar kernel of earlier builds executed 4550 per pass.)
+FLOPS_PER_FACE_PASS = 3900.0
 # algorithmic bytes per cell-update of the FP32 D2Q16 layout: the face kernel reads the
 # cell state (8 + 6 FP32 coefficients + 3 float-float frame words = 80 B) and two face predictors
 # (2 x 24 B) and writes two faces (2 x (16 x 4 + 24) B)
