@@ -1565,20 +1565,6 @@ __device__ __forceinline__ void add_face_flux(const R *Fc, const R *Gc, const R 
 }
 
 
-// (i, j) of cell c on rows of nx cells: a 32-bit division where the values allow it (a
-// 64-bit division is a long emulated sequence)
-__device__ __forceinline__ void cell_ij(long long c, long long nx, long long &i, long long &j)
-{
-    if (c < (1ll << 32) && nx < (1ll << 32)) {
-        const unsigned int cu = unsigned(c), nu = unsigned(nx), q = cu / nu;
-        j = q;
-        i = cu - q * nu;
-    } else {
-        j = c / nx;
-        i = c - j * nx;
-    }
-}
-
 // CFL rate of a cell frame: max over axes of (|u_a| + sqrt(T/T_L) max|c|)/dx_a, in the
 // working precision (FP32 populations: the rate in FP32 is enough)
 // v through a volatile move: the compiler treats the result as unknown at every use, so
@@ -1710,10 +1696,11 @@ cell_kernel(const Params<D, R> P)
     R rate = R(0);
     using W = typename FrameWords<R>::word;
     const StepC<R> &KC = step_c<R>(K);
-    auto update = [&](const long long c, const long long i, const long long j) {
+    auto update = [&](const long long c) {
         // GS: the plane strides pass through an opaque copy, so that the compiler forms the
         // planes' offsets per cell instead of holding them all in registers across cells
         const long long n = GS ? opaque(P.ncell()) : P.ncell();
+        const long long i = c % P.nx, j = c / P.nx;
         W uc[D];
 #pragma unroll
         for (int a = 0; a < D; ++a) uc[a] = P.sfr[a * n + c];
@@ -1796,23 +1783,12 @@ cell_kernel(const Params<D, R> P)
         if (ok) rate = max(rate, cell_rate_r<R>(unr, Tnr, KC.inv_dx, KC.inv_dy, D));
     };
     const long long c0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    long long i, j;
-    cell_ij(c0, P.nx, i, j);
     if constexpr (GS) {
         // grid-stride over the cells (the launch caps the grid), so that the block's rate
-        // reduction and the time-step atomics serve several cells per thread; the cell's
-        // (i, j) advance by the stride's own (i, j) with a carry, not by a division per cell
-        const long long S = (long long)gridDim.x * blockDim.x;
-        long long si, sj;
-        cell_ij(S, P.nx, si, sj);
-        for (long long c = c0; c < n; c += S) {
-            update(c, i, j);
-            i += si;
-            j += sj;
-            if (i >= P.nx) { i -= P.nx; ++j; }
-        }
+        // reduction and the time-step atomics serve several cells per thread
+        for (long long c = c0; c < n; c += (long long)gridDim.x * blockDim.x) update(c);
     } else if (c0 < n) {
-        update(c0, i, j);
+        update(c0);
     }
     reduce_rate_and_advance(P.clock, double(rate), true);
 }
