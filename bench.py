@@ -876,7 +876,9 @@ def main():
         "config": {"workload": "quadrants_2d_1024_seed%d" % args.seed, "lattice": "D2Q16", "cells": ncell,
                    "precision": "fp32 populations, float-float frames", "cfl": 0.2, "tau": 1e-5,
                    "corrector": "tol 1e-6, max 16 passes", "l2": "working set %.0f MB > L2" % (
-                       (ncell * (80 + 2 * 88)) / 1e6), "parallelism": "replicas" if world > 1 else "single"},
+                       (ncell * (80 + 2 * 88)) / 1e6), "parallelism": "replicas" if world > 1 else "single",
+                   "value_path": "plain FP32 corrector (the faster path here); FP32 + learned predictor in "
+                                 "fp32_learned_mlups, plain FP64 in fp64_mlups"},
         "fp32_learned_mlups": None if learned is None else learned["value"],
         "fp64_mlups": fp64_value,
         "hbm_frac_step": step_gbs / hbm_peak,
