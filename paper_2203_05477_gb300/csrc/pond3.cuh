@@ -580,13 +580,19 @@ struct FaceOut3 {
 // The predictor-corrector of one face (the readings of the D2Q16 kernel: convergence rule,
 // restart once from the pooled moments of the stencil, the last valid pass's moments
 // Grad-projected into the frame they define, then Eq. FluxTransf).
+constexpr int kKeep3 = 3 * 16;   // first scratch slot of the kept frames (after the corrector's)
+
 template <typename R, int NT>
 __device__ __forceinline__ void solve_face3(const FaceBox<R> &box, const R *dref, const R *uabs, R Tpred, R h_dn, R h_d1,
                                             R h_d2, R Cv, R tol, R wb, R we, int limiter, int max_iter, int fixed_iters,
                                             R *scr, FaceOut3<R> &o)
 {
     R dl[3] = {R(0), R(0), R(0)}, Tl = Tpred;
-    R keep_dl[3] = {R(0), R(0), R(0)}, keep_T = R(0), out_du[3] = {R(0), R(0), R(0)}, out_T = R(0), out_rho = R(0);
+    // the last valid pass's frames (its frame dl, Tl, and the frame its moments define: du,
+    // T1, rho1) wait in the thread's scratch after the corrector's 3 x 16 values, read and
+    // written with volatile accesses, instead of staying live in registers across the passes
+    auto kput = [&](int q, R v) { *reinterpret_cast<volatile R *>(&scr[(kKeep3 + q) * NT]) = v; };
+    auto kget = [&](int q) -> R { return *reinterpret_cast<volatile R *>(&scr[(kKeep3 + q) * NT]); };
     bool have = false, done = false, restarted = false, last_valid = false, recompute = false;
     int iters = 0;
     o.fallbacks = 0;
@@ -602,8 +608,13 @@ __device__ __forceinline__ void solve_face3(const FaceBox<R> &box, const R *dref
             }
             break;
         }
-        const R dlp[3] = {recompute ? keep_dl[0] : dl[0], recompute ? keep_dl[1] : dl[1], recompute ? keep_dl[2] : dl[2]};
-        corrector_pass3<R, NT>(box, dref, uabs, dlp, recompute ? keep_T : Tl, h_dn, h_d1, h_d2, limiter, scr, Phi, Psi);
+        R dlp[3] = {dl[0], dl[1], dl[2]}, Tlp = Tl;
+        if (recompute) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) dlp[a] = kget(a);
+            Tlp = kget(6);
+        }
+        corrector_pass3<R, NT>(box, dref, uabs, dlp, Tlp, h_dn, h_d1, h_d2, limiter, scr, Phi, Psi);
         if (recompute) break;
         R rho1, du[3], T1;
         const bool ok = pass_frame3<R>(Phi, Psi, Tl, Cv, rho1, du, T1);
@@ -649,12 +660,12 @@ __device__ __forceinline__ void solve_face3(const FaceBox<R> &box, const R *dref
         last_valid = true;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            keep_dl[a] = dl[a];
-            out_du[a] = du[a];
+            kput(a, dl[a]);
+            kput(3 + a, du[a]);
         }
-        keep_T = Tl;
-        out_T = T1;
-        out_rho = rho1;
+        kput(6, Tl);
+        kput(7, T1);
+        kput(8, rho1);
         if (fixed_iters > 0) {
             done = iters >= fixed_iters;
         } else {
@@ -669,6 +680,13 @@ __device__ __forceinline__ void solve_face3(const FaceBox<R> &box, const R *dref
     o.done = done;
     o.have = have;
     if (!have) return;
+    R keep_dl[3], out_du[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        keep_dl[a] = kget(a);
+        out_du[a] = kget(3 + a);
+    }
+    const R keep_T = kget(6), out_T = kget(7), out_rho = kget(8);
     const R invT = R(1) / out_T, rs = sqrt(invT);
     const R sc = sqrt(keep_T * invT), e = (keep_T - out_T) * invT;
     Map1<R> X(sc, e, -out_du[0] * rs), Y(sc, e, -out_du[1] * rs), Z(sc, e, -out_du[2] * rs);
@@ -694,8 +712,8 @@ __device__ __forceinline__ void solve_face3(const FaceBox<R> &box, const R *dref
 
 // Tiles of the 3D face kernel: TX x TY x TZ cells per CTA, one thread per face of each axis
 // (3 TX TY TZ threads), the box [i0-2, i0+TX] x [j0-2, j0+TY] x [k0-2, k0+TZ] staged in
-// dynamic shared memory, followed by the per-thread corrector scratch (3 x 16 values); two
-// CTAs per SM.
+// dynamic shared memory, followed by the per-thread scratch (the corrector's 3 x 16 values and
+// the 9 kept-frame values); two CTAs per SM.
 template <typename R>
 struct Face3Tile {
     static constexpr int TX = 4, TY = 4, TZ = sizeof(R) == 4 ? 4 : 2;
@@ -703,7 +721,7 @@ struct Face3Tile {
     static constexpr int MINB = 2;
     static constexpr int BX = TX + 3, BY = TY + 3, BZ = TZ + 3;
     static constexpr size_t tile_bytes = sizeof(StagedCell3<R>) * BX * BY * BZ;
-    static constexpr size_t scratch_bytes = sizeof(R) * 3 * 16 * THREADS;
+    static constexpr size_t scratch_bytes = sizeof(R) * (kKeep3 + 9) * THREADS;
     static constexpr size_t smem = tile_bytes + scratch_bytes;
 };
 
