@@ -452,6 +452,7 @@ def bench_d3q64(args, n=128, steps=20, fp64_steps=3, rank=0):
     for prec, k in (("fp32", steps), ("fp64", fp64_steps)):
         s = pond.Solver3(pb, precision=prec, tau=1e-5, cfl=0.3, max_iter=16)
         s.set_primitive()
+        tune = None if args.no_tune or prec == "fp64" else s.autotune(steps=2, cache=args.tune_cache)
         s.step(2)
         d0 = s.sync()
         ms_face, ms_cell = s.step_timed(k)
@@ -461,6 +462,10 @@ def bench_d3q64(args, n=128, steps=20, fp64_steps=3, rank=0):
                      "cell_ms": ms_cell / k, "steps": k,
                      "passes_per_face": (d1["face_iters"] - d0["face_iters"]) / max(1, d1["face_solves"] - d0["face_solves"]),
                      "status_ok": d1["status"] == pond.POND_OK}
+        if tune is not None:
+            names = s.variants()
+            out[prec]["variants"] = [names[tune["face"]], [n for n in names if n.startswith("cell3")][tune["cell"]]]
+            out[prec]["autotune_ms"] = tune["ms"]
         s.close()
         if prec == "fp32":
             out[prec]["face_passes_per_step"] = (d1["face_iters"] - d0["face_iters"]) / k

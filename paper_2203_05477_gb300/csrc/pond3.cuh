@@ -714,22 +714,23 @@ __device__ __forceinline__ void solve_face3(const FaceBox<R> &box, const R *dref
 // (3 TX TY TZ threads), the box [i0-2, i0+TX] x [j0-2, j0+TY] x [k0-2, k0+TZ] staged in
 // dynamic shared memory, followed by the per-thread scratch (the corrector's 3 x 16 values and
 // the 9 kept-frame values); two CTAs per SM.
-template <typename R>
+template <typename R, int TX_ = 4, int TY_ = 4, int TZ_ = (sizeof(R) == 4 ? 4 : 2), int MINB_ = 2>
 struct Face3Tile {
-    static constexpr int TX = 4, TY = 4, TZ = sizeof(R) == 4 ? 4 : 2;
+    static constexpr int TX = TX_, TY = TY_, TZ = TZ_;
     static constexpr int THREADS = 3 * TX * TY * TZ;
-    static constexpr int MINB = 2;
+    static constexpr int MINB = MINB_;
     static constexpr int BX = TX + 3, BY = TY + 3, BZ = TZ + 3;
     static constexpr size_t tile_bytes = sizeof(StagedCell3<R>) * BX * BY * BZ;
     static constexpr size_t scratch_bytes = sizeof(R) * (kKeep3 + 9) * THREADS;
     static constexpr size_t smem = tile_bytes + scratch_bytes;
+    static_assert(smem <= 227 * 1024, "the tile and scratch fit one CTA's shared memory");
 };
 
-template <typename R>
-__global__ void __launch_bounds__(Face3Tile<R>::THREADS, Face3Tile<R>::MINB)
+template <typename R, typename V = Face3Tile<R>>
+__global__ void __launch_bounds__(V::THREADS, V::MINB)
 face3_kernel(const Params3<R> P)
 {
-    using Tl_ = Face3Tile<R>;
+    using Tl_ = V;
     constexpr int TX = Tl_::TX, TY = Tl_::TY, TZ = Tl_::TZ, BX = Tl_::BX, BY = Tl_::BY, BZ = Tl_::BZ, NT = Tl_::THREADS;
     using W = typename FrameWords<R>::word;
     extern __shared__ __align__(16) unsigned char f3_dyn[];
@@ -899,8 +900,8 @@ __device__ __forceinline__ double cell_rate3(const R *u, R T, const StepC<R> &KC
 // Step 3 of Sec. III.B.4 (Eqs. fluxEq, FinalUpdateDUGKS) through the six faces, fused with
 // step 1 of the next step (the new co-moving frame from the conserved moments and the Grad
 // projection into it) and the CFL reduction.
-template <typename R>
-__global__ void __launch_bounds__(128)
+template <typename R, int THREADS = 128>
+__global__ void __launch_bounds__(THREADS)
 cell3_kernel(const Params3<R> P)
 {
     const Clock &K = *P.clock;

@@ -974,8 +974,8 @@ template <typename R>
 void launch_step3(pond_state *s)
 {
     auto &P = params3_of<R>(s);
-    pond::launch_face3<R>(P, s->stream);
-    pond::launch_cell3<R>(P, s->stream);
+    pond::launch_face3<R>(s->face_v, P, s->stream);
+    pond::launch_cell3<R>(s->cell_v, P, s->stream);
 }
 
 template <typename R>
@@ -1012,9 +1012,9 @@ pond_status step3_timed_impl(pond_state *s, int64_t n_steps, double *ms)
     CUDA_TRY(ev.create());
     CUDA_TRY(cudaEventRecord(ev[0], s->stream));
     for (int64_t k = 0; k < n_steps; ++k) {
-        pond::launch_face3<R>(P, s->stream);
+        pond::launch_face3<R>(s->face_v, P, s->stream);
         CUDA_TRY(cudaEventRecord(ev[2 * k + 1], s->stream));
-        pond::launch_cell3<R>(P, s->stream);
+        pond::launch_cell3<R>(s->cell_v, P, s->stream);
         CUDA_TRY(cudaEventRecord(ev[2 * k + 2], s->stream));
     }
     s->launches += 2 * n_steps;
@@ -1861,6 +1861,10 @@ std::string tune_key(const pond_state *s)
     if (s->batch)
         std::snprintf(buf, sizeof(buf), "%s|sm%d|tubes|%s|%lld|%lld", prop.name, prop.multiProcessorCount,
                       s->prec == POND_FP32 ? "fp32" : "fp64", (long long)s->n_tubes, (long long)s->ncell);
+    else if (s->D == 3)
+        std::snprintf(buf, sizeof(buf), "%s|sm%d|D3|%s|%lldx%lldx%lld", prop.name, prop.multiProcessorCount,
+                      s->prec == POND_FP32 ? "fp32" : "fp64", (long long)s->grid3.nx, (long long)s->grid3.ny,
+                      (long long)s->grid3.nz);
     else
         std::snprintf(buf, sizeof(buf), "%s|sm%d|D%d|%s|%lldx%lld|learned%d", prop.name, prop.multiProcessorCount, s->D,
                       s->prec == POND_FP32 ? "fp32" : "fp64", (long long)s->grid.nx, (long long)s->grid.ny,
@@ -1914,7 +1918,8 @@ int grid_step_variants(const pond_state *s)
 
 int variant_total(const pond_state *s)
 {
-    if (s->scheme == POND_SL || s->D == 3) return 0;
+    if (s->D == 3) return pond::face3_variant_count + pond::cell3_variant_count;
+    if (s->scheme == POND_SL) return 0;
     if (s->batch) return s->prec == POND_FP32 ? pond::tube_variants<float>() : pond::tube_variants<double>();
     return grid_face_variants(s) + pond::kCellVariants + grid_step_variants(s);
 }
@@ -2052,6 +2057,62 @@ pond_status tune_batch(pond_state *s, const char *saved, int steps, pond_tune_re
     return POND_OK;
 }
 
+// D3Q64 grids: every face tile variant with the current cell kernel, then every cell block
+// variant with the chosen face kernel, each timed from the saved block
+template <typename R>
+pond_status time_3d_variant(pond_state *s, const char *saved, int steps, int which, double *ms)
+{
+    auto &P = params3_of<R>(s);
+    CUDA_TRY(cudaMemcpyAsync(s->base, saved, s->bytes, cudaMemcpyDeviceToDevice, s->stream));
+    launch_step3<R>(s);
+    Events ev(size_t(2 * steps));
+    CUDA_TRY(ev.create());
+    for (int k = 0; k < steps; ++k) {
+        if (which == 0) CUDA_TRY(cudaEventRecord(ev[2 * k], s->stream));
+        pond::launch_face3<R>(s->face_v, P, s->stream);
+        if (which == 0) CUDA_TRY(cudaEventRecord(ev[2 * k + 1], s->stream));
+        if (which == 1) CUDA_TRY(cudaEventRecord(ev[2 * k], s->stream));
+        pond::launch_cell3<R>(s->cell_v, P, s->stream);
+        if (which == 1) CUDA_TRY(cudaEventRecord(ev[2 * k + 1], s->stream));
+    }
+    s->launches += int64_t(steps + 1) * 2;
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaEventSynchronize(ev.back()));
+    double sum = 0.0;
+    for (int k = 0; k < steps; ++k) {
+        float a = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&a, ev[2 * k], ev[2 * k + 1]));
+        sum += a;
+    }
+    *ms = sum / steps;
+    return POND_OK;
+}
+
+template <typename R>
+pond_status tune_3d(pond_state *s, const char *saved, int steps, pond_tune_result *res)
+{
+    double best = 0.0;
+    int bf = 0, bc = 0;
+    for (int v = 0; v < pond::face3_variant_count; ++v) {
+        s->face_v = v;
+        double ms = 0.0;
+        if (pond_status st = time_3d_variant<R>(s, saved, steps, 0, &ms)) return st;
+        if (res && res->n < POND_TUNE_MAX) res->ms[res->n++] = ms;
+        if (v == 0 || ms < best) { best = ms; bf = v; }
+    }
+    s->face_v = bf;
+    for (int v = 0; v < pond::cell3_variant_count; ++v) {
+        s->cell_v = v;
+        double ms = 0.0;
+        if (pond_status st = time_3d_variant<R>(s, saved, steps, 1, &ms)) return st;
+        if (res && res->n < POND_TUNE_MAX) res->ms[res->n++] = ms;
+        if (v == 0 || ms < best) { best = ms; bc = v; }
+    }
+    s->cell_v = bc;
+    s->tube_v = 0;
+    return POND_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -2061,7 +2122,7 @@ pond_status pond_autotune(pond_state *s, int steps, const char *cache_path, pond
     if (pond_status st = check_state(s)) return st;
     if (steps < 1) return fail(POND_ERR_INVALID_ARG, "steps must be at least 1");
     pond_tune_result res{};
-    if (s->scheme == POND_SL || s->D == 3 || s->equilibrate) {  // one compiled variant: nothing to choose
+    if (s->D != 3 && (s->scheme == POND_SL || s->equilibrate)) {  // one compiled variant: nothing to choose
         if (out) *out = res;
         return POND_OK;
     }
@@ -2078,6 +2139,8 @@ pond_status pond_autotune(pond_state *s, int steps, const char *cache_path, pond
             st = fail(POND_ERR_CUDA, "saving the state for tuning failed");
         if (st == POND_OK) {
             if (s->batch) st = dispatch_batch(s, [&](auto r) { return tune_batch<decltype(r)>(s, saved, steps, &res); });
+            else if (s->D == 3)
+                st = s->prec == POND_FP32 ? tune_3d<float>(s, saved, steps, &res) : tune_3d<double>(s, saved, steps, &res);
             else st = dispatch(s, [&](auto d, auto r) { return tune_grid<decltype(d)::value, decltype(r)>(s, saved, steps, &res); });
         }
         // put the state back whatever happened, then release the copy
@@ -2110,6 +2173,12 @@ const char *pond_variant_name(const pond_state *s, int i)
         else pond::tube_name<double>(i, buf, sizeof(buf));
         return buf;
     }
+    if (s->D == 3) {
+        if (i >= pond::face3_variant_count) pond::cell3_name(i - pond::face3_variant_count, buf, sizeof(buf));
+        else if (f32) pond::face3_name<float>(i, buf, sizeof(buf));
+        else pond::face3_name<double>(i, buf, sizeof(buf));
+        return buf;
+    }
     const int nf = grid_face_variants(s);
     if (i >= nf + pond::kCellVariants) {
         const int k = i - nf - pond::kCellVariants;
@@ -2137,6 +2206,12 @@ pond_status pond_set_variants(pond_state *s, int face, int cell, int tube)
         const int nv = s->prec == POND_FP32 ? pond::tube_variants<float>() : pond::tube_variants<double>();
         if (tube < 0 || tube >= nv) return fail(POND_ERR_INVALID_ARG, "tube variant %d out of range", tube);
         s->tube_v = tube;
+    } else if (s->D == 3) {
+        if (face < 0 || face >= pond::face3_variant_count || cell < 0 || cell >= pond::cell3_variant_count || tube != 0)
+            return fail(POND_ERR_INVALID_ARG, "D3Q64 face/cell variant (%d, %d, %d) out of range", face, cell, tube);
+        s->face_v = face;
+        s->cell_v = cell;
+        s->tube_v = 0;
     } else {
         const int nf = grid_face_variants(s);
         if (face < 0 || face >= nf || cell < 0 || cell >= pond::kCellVariants)
