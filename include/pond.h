@@ -313,8 +313,9 @@ pond_status pond_wait_timeout_check(int64_t polls, void *stream);
    cell update, thread counts of the persistent tube kernel.  pond_autotune times every
    variant on this state's own current data (steps timed steps each, after one untimed
    step) and keeps the fastest face and cell (or tube) variant for the following steps;
-   on a grid it then times whole steps of those face and cell kernels against each fused
-   step variant and keeps the fastest in `tube` (as pond_set_variants reads it).  ms holds
+   on a 1D or 2D grid it then times whole steps of those face and cell kernels against each
+   fused step variant and keeps the fastest in `tube` (as pond_set_variants reads it); a
+   D3Q64 grid has face tile and cell block variants only (`tube` stays 0).  ms holds
    per-launch times of the face and cell variants and per-step times of the step choices.
    The state is copied aside first (one extra device allocation of the state's size, freed
    before returning) and restored afterwards, so tuning leaves the solution unchanged.
@@ -332,10 +333,11 @@ typedef struct {
 } pond_tune_result;
 pond_status pond_autotune(pond_state *s, int steps, const char *cache_path, pond_tune_result *out);
 
-/* Number of variants of this state and the name of variant i: for a grid, the face
-   variants first, then the cell variants, then the whole-step choices (the separate face
-   and cell kernels, then each tile variant of the fused step kernel, which solves a tile's
-   faces and updates its cells in one kernel); for a batch, the tube variants.  The name
+/* Number of variants of this state and the name of variant i: for a 1D or 2D grid, the
+   face variants first, then the cell variants, then the whole-step choices (the separate
+   face and cell kernels, then each tile variant of the fused step kernel, which solves a
+   tile's faces and updates its cells in one kernel); for a D3Q64 grid, the face tile
+   variants, then the cell block variants; for a batch, the tube variants.  The name
    points to a thread-local buffer ("" when i is out of range). */
 int pond_variant_count(const pond_state *s);
 const char *pond_variant_name(const pond_state *s, int i);
@@ -343,8 +345,8 @@ const char *pond_variant_name(const pond_state *s, int i);
 /* Selects variants by index: for a grid face, cell and, in `tube`, the whole step (0: the
    face and cell kernels; k > 0: fused step variant k - 1, used for the plain steps -- the
    learned predictor, pair collection and the equilibration ablation run the face and cell
-   kernels); for a batch tube (the others are ignored).  Errors: INVALID_ARG for an index
-   out of range. */
+   kernels); for a D3Q64 grid face and cell (`tube` must be 0); for a batch tube (the others
+   are ignored).  Errors: INVALID_ARG for an index out of range. */
 pond_status pond_set_variants(pond_state *s, int face, int cell, int tube);
 
 /* Waits for the stream and reports the device diagnostics.  Returns
