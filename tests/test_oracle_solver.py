@@ -168,6 +168,9 @@ def test_sod_converges_under_refinement():
 @pytest.mark.parametrize("name,n,tol_rho,tol_p", [
     ("lax", 300, 2.5e-2, 1e-2),
     ("strong_shock", 400, 8e-2, 2e-2),
+    # the Mach-80 1D jet of Sec. IV.C (gamma 5/3, [0, 2], t = 0.06) at half the paper's 1500
+    # points: rho 2.1e-2, p 9.3e-3, u 1.2e-3 relative L1 (1500 points: 1.3e-2, 3.0e-3, 5e-4)
+    ("jet_1d", 750, 3e-2, 1.5e-2),
 ])
 def test_paper_tubes_against_exact_solution(name, n, tol_rho, tol_p):
     st, r, u, p, re, ue, pe, _ = _tube_error(name, n)
